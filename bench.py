@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Benchmark of the shearlet-regularised segmentation ADMM on GB300.
+
+One step = one whole solve on the 512 x 512 workload (grayscale, K = 4 labels,
+J = 4 scales / 61 filters, 500 ADMM iterations, curved Bezier regions with
+oriented gratings and noise sigma = 0.05): data term and zero state
+(seg_admm_reset), 500 iterations (graph replays), label readout.  The metric
+is Mpixel*label*ADMM-iteration per second summed over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 is launched by torchrun: every rank solves its own copy of the image
+(independent problems, no collective on the data path; weak scaling).
+--impl reference times the FP64 CPU oracle (the baseline arm) on a bounded
+sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1112_1805_gb300 import synth  # noqa: E402
+
+METRIC = "Mpixel·label·ADMM-iter/s, batched vs plain, at ≤1e-4 err; HBM % of peak"
+UNIT = "Mpixel·label·iter/s"
+WORKLOAD = "bezier512"
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
+    ap.add_argument("--cpu-iters", type=int, default=2, help="oracle iterations in the CPU-baseline sample")
+    return ap.parse_args()
+
+
+def workload_config(wl, extra=None):
+    cfg = {
+        "workload": f"{wl.name}: {wl.H}x{wl.W} gray, K={wl.K}, J={wl.J} (eta={wl.eta}), {wl.iters} ADMM iterations, "
+                    "seeded closed-Bezier regions with oriented gratings (amplitude 0.15) and N(0, 0.05^2) noise",
+        "H": wl.H, "W": wl.W, "K": wl.K, "J": wl.J, "eta": wl.eta, "iters_per_step": wl.iters,
+        "lambda": wl.lam, "gamma": wl.gamma, "Lambda": [round(float(x), 6) for x in wl.Lambda()],
+        "l2": "no flush: per-iteration working set (b_v 256 MB + coefficient spectra 257 MB) exceeds the 129 MB L2",
+        "parallelism": "replicas (one independent image per GPU)",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(gpu_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons, n = [], None, set(), 0
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            n += 1
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        loaded = [x for x in sm if smax and x > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": n}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping: algorithmic bytes per launch of each kernel
+# ---------------------------------------------------------------------------
+def kernel_bytes(wl, groups: int):
+    """Bytes each kernel of one iteration must move at minimum given its inputs
+    and outputs (every operand read once, every result written once)."""
+    H, W, K, eta = wl.H, wl.W, wl.K, wl.eta
+    P, Ph = H * W, H * (W // 2 + 1)
+    return {
+        # reads T (spectra), s, w, b_w; writes u, w, b_w and the row spectra of u
+        "k_row_ustep": K * (2 * Ph * 8 + 6 * P * 4),
+        # reads the row spectra of u and the bank; writes K*eta coefficient spectra
+        "k_col_fan": K * Ph * 8 + eta * Ph * 4 + K * eta * Ph * 8,
+        # reads and writes the coefficient spectra and b_v
+        "k_row_shrink": K * eta * (2 * Ph * 8 + 2 * P * 4),
+        # reads the spectra and the bank, writes the group partials
+        "k_col_gather": K * eta * Ph * 8 + eta * Ph * 4 + groups * K * Ph * 8,
+        # reads the partials, writes T
+        "k_col_reduce_inv": groups * K * Ph * 8 + K * Ph * 8,
+    }
+
+
+def source_sha() -> str:
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1112_1805_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_1112_1805_gb300", "csrc", f), "rb") as fp:
+            h.update(fp.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    try:
+        with open(TRAFFIC_FILE) as fp:
+            t = json.load(fp)
+    except (OSError, ValueError):
+        return None
+    if t.get("source_sha") != source_sha():
+        return None
+    k = t.get("kernels", {}).get(kernel)
+    return None if k is None else float(k["dram_bytes_per_launch"])
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fp:
+            p = json.load(fp)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (baseline leg and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(wl, img, iters: int):
+    import oracle
+
+    oracle.build()
+    cb = wl.codebook()
+    t0 = time.perf_counter()
+    s = oracle.data_term(img, cb)
+    st = oracle.zero_state(wl.K, wl.J, wl.H, wl.W)
+    oracle.admm_iterate(st, s, wl.J, wl.Lambda(), wl.gamma, iters)
+    dt = time.perf_counter() - t0
+    units = wl.H * wl.W * wl.K * iters
+    return units / dt / 1e6, dt, oracle.get_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    img, lab, wl = synth.make_workload_image(WORKLOAD)
+    for _ in range(args.warmup):
+        oracle_sample(wl, img, 1)
+    vals, times = [], []
+    cores = 0
+    for _ in range(args.steps):
+        v, dt, cores = oracle_sample(wl, img, 1)
+        vals.append(v)
+        times.append(dt)
+    value = wl.H * wl.W * wl.K * len(times) / sum(times) / 1e6
+    sample = (f"{wl.name} at full size, data term + 1 ADMM iteration per step (filter bank built per step, as the "
+              f"oracle does), FP64, {cores} threads")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(wl, {"iters_per_step": 1}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1112_1805_gb300 import binding as B
+    from paper_1112_1805_gb300.api import FilterBank, ShearletSegmenter
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    img, lab, wl = synth.make_workload_image(WORKLOAD)
+    # the CPU-baseline leg runs first (rank 0, N = 1), before any GPU work
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, cores = oracle_sample(wl, img, args.cpu_iters)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{wl.name} at full size, data term + {args.cpu_iters} ADMM iterations "
+                         f"({dt:.1f} s, FP64, filter bank built inside the timed call)"}
+
+    img32 = np.ascontiguousarray(img, dtype=np.float32)
+    f_dev = torch.tensor(img32, device="cuda")
+    fb = FilterBank(wl.H, wl.W, wl.J)
+    seg = ShearletSegmenter(fb, f_dev, wl.codebook(), wl.Lambda(), wl.gamma)
+    labels_dev = torch.empty((wl.H, wl.W), dtype=torch.int32, device="cuda")
+    st = seg.stream
+    units_per_step = wl.H * wl.W * wl.K * wl.iters
+
+    def device_step():
+        B.seg_admm_reset(seg.handle, f_dev.data_ptr(), False)
+        B.seg_admm_step(seg.handle, wl.iters)
+        B.seg_admm_get(seg.handle, B.SEG_LABELS, labels_dev.data_ptr(), False)
+
+    for _ in range(args.warmup):
+        device_step()
+    seg.synchronize()
+    torch.cuda.synchronize()
+
+    # timed region: K steps bracketed by barrier + synchronize, CUDA events on the state's stream
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(st)
+    ktimes = []
+    for _ in range(args.steps):
+        device_step()
+        ktimes.append(B.seg_admm_kernel_times(seg.handle))  # last iteration of this step
+    ev1.record(st)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = units_per_step * args.steps * world / (ms_max / 1000.0) / 1e6
+    launches_per_step = 2 + 5 * wl.iters + 1
+
+    # end-to-end through the public API with host buffers (pinned), copies inside
+    host_img = torch.from_numpy(img32).pin_memory()
+    host_labels = torch.empty((wl.H, wl.W), dtype=torch.int32).pin_memory()
+    seg.get_host(B.SEG_LABELS, host_labels)
+    barrier()
+    e2e_times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        seg.reset(host_img)
+        seg.step(wl.iters)
+        seg.get_host(B.SEG_LABELS, host_labels)  # synchronises
+        e2e_times.append(time.perf_counter() - t0)
+    et = torch.tensor([sum(e2e_times)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(et, op=dist.ReduceOp.MAX)
+    e2e_value = units_per_step * args.steps * world / float(et.item()) / 1e6
+
+    # roofline of the dominant kernel (largest share of the iteration)
+    names = list(ktimes[0].keys())
+    mean_ms = {n: statistics.mean(k[n] for k in ktimes) for n in names}
+    dom = max(mean_ms, key=mean_ms.get)
+    kb = kernel_bytes(wl, seg_groups(wl))
+    peak, peak_kind = peaks()
+    achieved = kb[dom] / (mean_ms[dom] / 1000.0) / 1e9
+    it_ms = sum(mean_ms.values())
+    iter_alg = (8 * wl.eta + 24) * wl.H * wl.W * wl.K  # per-iteration algorithmic bytes of the method
+    roofline = {
+        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+        "traffic": measured_traffic(dom), "kernel": dom, "kernel_ms": mean_ms[dom],
+        "algorithmic_bytes_per_launch": kb[dom], "peak_source": f"{peak_kind} hbm_gbs",
+    }
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(wl),
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
+                   "samples": clk["samples"]},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(host_img.numel() * 4),
+                "d2h_bytes_per_step": int(host_labels.numel() * 4)},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": roofline,
+        "iteration": {"ms": it_ms, "kernel_ms": mean_ms,
+                      "algorithmic_bytes": iter_alg,
+                      "hbm_frac_algorithmic": iter_alg / (it_ms / 1000.0) / 1e9 / peak},
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line))
+    seg.close()
+    fb.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def seg_groups(wl) -> int:
+    """Filter groups used by the column kernels (mirrors the library's choice)."""
+    TC = max(4, min(16, 1 << (max(1, 4096 // wl.H).bit_length() - 1)))
+    TC = min(TC, wl.W // 2 + 1)
+    ntiles = (wl.W // 2 + 1 + TC - 1) // TC
+    base = ntiles * wl.K
+    G = max(1, min(wl.eta, (4 * 152 + base - 1) // base))
+    fg = (wl.eta + G - 1) // G
+    return (wl.eta + fg - 1) // fg
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,206 @@
+/*
+ * shearseg.h -- C ABI of the GB300 (sm_103a) shearlet-regularised convex
+ * multi-label segmentation library (Haeuser & Steidl, "Convex Multiclass
+ * Segmentation with Shearlet Regularization", arXiv:1112.1805).
+ *
+ * Conventions shared by every entry point:
+ *   - Images are planar, row-major float32: a channel/label plane is [H][W],
+ *     stacks are label-major [K][H][W] (the paper stacks the q label layers one
+ *     after the other, Sec. 3 "Segmentation Model"; rows instead of its
+ *     column-major vec, which leaves the model unchanged because the filter set
+ *     is closed under transposition).  The first frequency coordinate omega_1
+ *     belongs to the row axis (length H).
+ *   - Shearlet coefficients are [nch][eta][H][W] with eta = 2^(J+2) - 3 filters
+ *     per channel in the order: low-pass; then for each scale j = 0..J-1 the
+ *     horizontal-cone shears k = -2^j+1..2^j-1, the vertical-cone shears (same
+ *     k), the glued seam shearlet k = -2^j and the glued one k = +2^j
+ *     (Sec. 2, "Finite Discrete Shearlets" and the Theorem's system).
+ *   - Sizes: W even; H and W/2 products of powers of 2, 3 and 5; 8 <= H, W <=
+ *     2048.  Labels 2 <= K <= 16; channels C in {1, 3}; scales 1 <= J <= 6.
+ *   - Device pointers are caller-owned CUDA device memory unless the argument
+ *     says "host".  The library never frees caller memory and never returns
+ *     memory it allocated for the caller.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  Work is enqueued asynchronously on that stream unless
+ *     the function says it synchronises.
+ *   - Every function returns SHF_OK (0) or a negative SHF_ERR_* code and never
+ *     throws; shf_last_error() gives a thread-local message for the last
+ *     failure.  There is no CPU fallback: without a usable sm_103a device every
+ *     compute entry point fails with SHF_ERR_CUDA.
+ */
+#ifndef SHEARSEG_H
+#define SHEARSEG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SHF_OK 0
+#define SHF_ERR_ARG (-1)       /* null pointer, K/J/C/size out of range        */
+#define SHF_ERR_SIZE (-2)      /* H or W/2 not 2^a 3^b 5^c, odd W, too large    */
+#define SHF_ERR_OOM (-3)       /* device allocation failed                     */
+#define SHF_ERR_CUDA (-4)      /* CUDA runtime or launch error                 */
+#define SHF_ERR_NONFINITE (-5) /* NaN/Inf in an input image or codebook        */
+#define SHF_ERR_TIMEOUT (-6)   /* reserved: a bounded device wait gave up      */
+#define SHF_ERR_STATE (-7)     /* handle used inconsistently (sizes, J, K)     */
+#define SHF_ERR_IO (-8)        /* checkpoint file could not be read/written    */
+
+/* Opaque, library-owned objects. */
+typedef struct shf_bank shf_bank;   /* filter bank + FFT tables for one (H, W, J) */
+typedef struct seg_state seg_state; /* ADMM state for one image                   */
+
+/* ADMM parameters (Sec. 3).  gamma > 0 is the ADMM step; Lambda (host, J+1
+ * floats) holds the weights of eq. problemSegmentation: Lambda[0] for the
+ * low-pass, Lambda[j+1] for scale j, shared by all shears of a scale.  The
+ * soft-shrinkage threshold of a coefficient is gamma * Lambda[.].
+ * max_iters bounds seg_admm_solve; it stops earlier once
+ * ||u - w||_2 / sqrt(K H W) < tol, checked every check_every iterations. */
+typedef struct {
+  float gamma;
+  int J;
+  const float* Lambda;
+  int max_iters;
+  float tol;
+  int check_every;
+} seg_params;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int shf_version(void);
+
+/* Thread-local text of the last error ("" if none).  Valid until the next
+ * failing call on the same thread. */
+const char* shf_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Filter bank, Sec. 2 "Finite Discrete Shearlets" (shearlet spectra
+ * psi1_hat(4^-j xi_1) psi2_hat(2^j xi_2/xi_1 + k) on the cones, glued seam
+ * shearlets, scaling function varphi) and the Theorem (Parseval frame).
+ * Built on the device in FP64 and stored as FP32 on the half plane
+ * [eta][H][W/2+1] (the spectra are real and even).  Readings: frequencies are
+ * normalised per axis, xi_a = omega_a 4^J / N_a, so that the J scales reach the
+ * Nyquist frequency for any (N, J); on the Nyquist line of an even axis each
+ * filter is replaced by the root mean square of its values at the two DFT
+ * partners, which keeps sum_f W_f^2 = 1 and makes coefficients of real images
+ * real.  Enqueued on `stream`; *out is usable once the stream reaches it.
+ * Errors: SHF_ERR_ARG (null out, J out of range), SHF_ERR_SIZE, SHF_ERR_OOM,
+ * SHF_ERR_CUDA. */
+int shfilters_build(int H, int W, int J, void* stream, shf_bank** out);
+
+/* Releases the bank (synchronises the device).  NULL is accepted. */
+int shfilters_destroy(shf_bank* bank);
+
+/* eta = 2^(J+2) - 3 (Remark 1: 61 images for four scales), H, W, J.  Any
+ * output pointer may be NULL. */
+int shfilters_info(const shf_bank* bank, int* eta, int* H, int* W, int* J);
+
+/* Copies the FP32 half-plane bank [eta][H][W/2+1] into device memory dst. */
+int shfilters_copy(const shf_bank* bank, float* dst, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Shearlet transform S (eq. wichtig: one fft2 per channel, then per filter a
+ * pointwise product with the real spectrum and an ifft2).
+ * u: device [nch][H][W]; coef: device [nch][eta][H][W] (must not alias u).
+ * Temporary device memory is taken stream-ordered from the default pool and
+ * returned before the call's work completes.  Errors: SHF_ERR_ARG,
+ * SHF_ERR_OOM, SHF_ERR_CUDA. */
+int shearlet_analyze(const shf_bank* bank, const float* u, int nch, float* coef, void* stream);
+
+/* Adjoint S^T (the synthesis paragraph after the Theorem: fft2 of every
+ * coefficient image, product with the same spectra, sum over the filters,
+ * one ifft2).  By eq. important, shearlet_synthesize(shearlet_analyze(u)) = u.
+ * coef: device [nch][eta][H][W]; u: device [nch][H][W]. */
+int shearlet_synthesize(const shf_bank* bank, const float* coef, int nch, float* u, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * ADMM for eq. problemSegmentationADMM (Sec. 3): splitting (I_q (x) S) u = v,
+ * u = w; per iteration
+ *   u   = 1/2 [ S^T (v - b_v) + (w - b_w) - gamma s ]         (A^T A = 2 I)
+ *   v   = soft-shrink(b_v + S u, gamma Lambda)               (v-step)
+ *   w   = pixelwise projection of b_w + u onto the simplex   (w-step)
+ *   b_v = b_v + S u - v,  b_w = b_w + u - w                  (eq. ADMM_b)
+ * with the data term s[k] = sum_ch (f[ch] - c[k][ch])^2 (eq. computationOfs,
+ * p = 2, and its RGB form).  The initial state is v = b_v = w = b_w = 0.
+ * The library stores b_v and the synthesis S^T(v - b_v) instead of v and b_v
+ * (v = soft(g), b_v = clip(g) with the same g), so v itself is not kept.
+ *
+ * f: device [C][H][W]; codebook: HOST [K][C]; params: host.  The state keeps
+ * the bank pointer (the bank must outlive it), copies f and the parameters,
+ * and owns its device buffers.  If `stream` is NULL the state creates and owns
+ * a private non-blocking stream; otherwise all its work goes to `stream`.
+ * Errors: SHF_ERR_ARG, SHF_ERR_STATE (params->J differs from the bank's),
+ * SHF_ERR_NONFINITE (NaN/Inf in the codebook or parameters), SHF_ERR_OOM,
+ * SHF_ERR_CUDA. */
+int seg_admm_init(const shf_bank* bank, const float* f, int C, const float* codebook, int K,
+                  const seg_params* params, void* stream, seg_state** out);
+
+/* New image of the same size (f device, or host if f_on_host != 0; a host
+ * image should be pinned for the copy to be asynchronous), recomputes the
+ * data term and returns the state to v = b_v = w = b_w = 0, iteration 0. */
+int seg_admm_reset(seg_state* st, const float* f, int f_on_host);
+
+/* Enqueues n_iters ADMM iterations on the state's stream (replays of a CUDA
+ * graph of one iteration, captured on first use when the stream allows it). */
+int seg_admm_step(seg_state* st, int n_iters);
+
+/* Iterates until ||u - w||_2 / sqrt(K H W) < tol (checked every check_every
+ * iterations) or max_iters total iterations; synchronises.  Outputs may be
+ * NULL. */
+int seg_admm_solve(seg_state* st, int* iters_done, float* final_residual);
+
+/* Readout selectors for seg_admm_get / seg_admm_set. */
+#define SEG_U 0      /* float [K][H][W]       last u                          */
+#define SEG_W 1      /* float [K][H][W]       last w (in the simplex)         */
+#define SEG_BW 2     /* float [K][H][W]       dual b_w                        */
+#define SEG_BV 3     /* float [K][eta][H][W]  dual b_v                        */
+#define SEG_S 4      /* float [K][H][W]       data term s                     */
+#define SEG_LABELS 5 /* int32 [H][W]          argmax_k w (ties: lowest k)     */
+#define SEG_GAP 6    /* float [H][W]          largest minus second largest w  */
+#define SEG_ENERGY 7 /* double [1]            <w,s> + sum Lambda ||(S w)_f||_1 */
+#define SEG_ITER 8   /* int32 [1]             iterations done (host only)     */
+#define SEG_STV 9    /* float [K][H][W]       S^T (v - b_v) feeding next u    */
+#define SEG_V 10     /* float [K][eta][H][W]  v (set only: with SEG_BV set
+                        first, recomputes S^T (v - b_v))                        */
+
+/* Copies component `what` into dst (device, or host if dst_on_host != 0).
+ * Synchronises the state's stream when dst is on the host or what is
+ * SEG_ENERGY or SEG_ITER.  Errors: SHF_ERR_ARG for an unknown selector. */
+int seg_admm_get(seg_state* st, int what, void* dst, int dst_on_host);
+
+/* Overwrites a state component from src (device, or host if src_on_host) --
+ * used to resume or to start from a given state.  Accepts SEG_W, SEG_BW,
+ * SEG_BV, SEG_STV and SEG_V. */
+int seg_admm_set(seg_state* st, int what, const void* src, int src_on_host);
+
+/* Checkpoint / resume: raw FP32 state (the carried synthesis spectrum of
+ * v - b_v, b_v, w, b_w, s, u) behind a header with H, W, K, J, eta, C, the
+ * iteration count, gamma and Lambda; a resumed run continues bit for bit.
+ * load requires a state with the same H, W, K, J.  Synchronise. */
+int seg_admm_save(seg_state* st, const char* path);
+int seg_admm_load(seg_state* st, const char* path);
+
+/* Instrumentation (no counterpart in the paper): durations in milliseconds of
+ * the kernels of the most recent iteration, measured by CUDA events recorded
+ * on the state's stream between them (inside the replayed graph).  ms must
+ * hold 8 floats; *nk (may be NULL) gets the number of kernels per iteration.
+ * Waits for that iteration to finish.  Errors: SHF_ERR_STATE before the first
+ * iteration. */
+int seg_admm_kernel_times(seg_state* st, float* ms, int* nk);
+
+/* Name of kernel i of an iteration, in the order of seg_admm_kernel_times
+ * ("" when i is out of range). */
+const char* seg_admm_kernel_name(int i);
+
+/* Waits for the state's stream. */
+int seg_admm_sync(seg_state* st);
+
+/* Releases the state (synchronises its stream).  NULL is accepted. */
+int seg_admm_destroy(seg_state* st);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHEARSEG_H */

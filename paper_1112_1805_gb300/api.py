@@ -1,0 +1,178 @@
+"""PyTorch-facing wrappers over the C ABI: tensors in, tensors out.
+
+PyTorch supplies device memory and the current CUDA stream; every step of the
+computation runs in libshearseg.so.  Device tensors must be contiguous
+float32 on the current CUDA device.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+
+def _cur_stream():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _dev_f32(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    return t
+
+
+class FilterBank:
+    """Shearlet filter bank for one (H, W, J) (Sec. 2 of the paper)."""
+
+    def __init__(self, H: int, W: int, J: int):
+        self.handle = B.shfilters_build(H, W, J, _cur_stream())
+        self.eta, self.H, self.W, self.J = B.shfilters_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            B.shfilters_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def spectra(self) -> torch.Tensor:
+        """FP32 half-plane spectra [eta, H, W//2+1]."""
+        out = torch.empty((self.eta, self.H, self.W // 2 + 1), dtype=torch.float32, device="cuda")
+        B.shfilters_copy(self.handle, out.data_ptr(), _cur_stream())
+        return out
+
+    def analyze(self, u: torch.Tensor) -> torch.Tensor:
+        """S per channel: u [..., H, W] -> [..., eta, H, W] (eq. wichtig)."""
+        _dev_f32(u, "u")
+        lead = u.shape[:-2]
+        nch = int(np.prod(lead)) if len(lead) else 1
+        coef = torch.empty(tuple(lead) + (self.eta, self.H, self.W), dtype=torch.float32, device=u.device)
+        B.shearlet_analyze(self.handle, u.data_ptr(), nch, coef.data_ptr(), _cur_stream())
+        return coef
+
+    def synthesize(self, coef: torch.Tensor) -> torch.Tensor:
+        """S^T per channel: [..., eta, H, W] -> [..., H, W]."""
+        _dev_f32(coef, "coef")
+        lead = coef.shape[:-3]
+        nch = int(np.prod(lead)) if len(lead) else 1
+        u = torch.empty(tuple(lead) + (self.H, self.W), dtype=torch.float32, device=coef.device)
+        B.shearlet_synthesize(self.handle, coef.data_ptr(), nch, u.data_ptr(), _cur_stream())
+        return u
+
+
+class ShearletSegmenter:
+    """ADMM state for one image (Sec. 3 of the paper).
+
+    f: [C, H, W] or [H, W] float32 CUDA tensor; codebook: [K, C] (host values);
+    Lambda: J+1 weights (low-pass first); gamma > 0."""
+
+    def __init__(self, bank: FilterBank, f: torch.Tensor, codebook, Lambda, gamma: float = 1.0,
+                 max_iters: int = 500, tol: float = 0.0, check_every: int = 50, stream=None):
+        if f.dim() == 2:
+            f = f.unsqueeze(0)
+        _dev_f32(f, "f")
+        cb = np.asarray(codebook, dtype=np.float64).reshape(-1, f.shape[0])
+        self.bank = bank
+        self.K, self.C = cb.shape
+        self.H, self.W, self.eta = bank.H, bank.W, bank.eta
+        self._params, self._keep = B.make_params(gamma, bank.J, Lambda, max_iters, tol, check_every)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.stream.wait_stream(torch.cuda.current_stream())  # f may still be in flight on torch's stream
+        self.handle = B.seg_admm_init(bank.handle, f.data_ptr(), self.C, cb.ravel().tolist(), self.K, self._params,
+                                      self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            B.seg_admm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int) -> None:
+        B.seg_admm_step(self.handle, n)
+
+    def solve(self):
+        return B.seg_admm_solve(self.handle)
+
+    def synchronize(self) -> None:
+        B.seg_admm_sync(self.handle)
+
+    def reset(self, f) -> None:
+        """New image: a CUDA tensor, or a host (ideally pinned) tensor / numpy array."""
+        if isinstance(f, torch.Tensor) and f.is_cuda:
+            _dev_f32(f, "f")
+            self.stream.wait_stream(torch.cuda.current_stream())
+            B.seg_admm_reset(self.handle, f.data_ptr(), False)
+        else:
+            a = f if isinstance(f, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(f, dtype=np.float32))
+            a = a.contiguous()
+            B.seg_admm_reset(self.handle, a.data_ptr(), True)
+
+    def _shape(self, what: int):
+        K, H, W = self.K, self.H, self.W
+        if what in (B.SEG_U, B.SEG_W, B.SEG_BW, B.SEG_S, B.SEG_STV):
+            return (K, H, W), torch.float32
+        if what in (B.SEG_BV, B.SEG_V):
+            return (K, self.eta, H, W), torch.float32
+        if what == B.SEG_LABELS:
+            return (H, W), torch.int32
+        if what == B.SEG_GAP:
+            return (H, W), torch.float32
+        raise ValueError(what)
+
+    def get(self, what: int) -> torch.Tensor:
+        """A state component as a CUDA tensor (written on the state's stream)."""
+        if what == B.SEG_ENERGY:
+            buf = np.zeros(1, dtype=np.float64)
+            B.seg_admm_get(self.handle, what, buf.ctypes.data, True)
+            return torch.tensor(buf[0], dtype=torch.float64)
+        if what == B.SEG_ITER:
+            buf = np.zeros(1, dtype=np.int32)
+            B.seg_admm_get(self.handle, what, buf.ctypes.data, True)
+            return torch.tensor(int(buf[0]))
+        shape, dt = self._shape(what)
+        out = torch.empty(shape, dtype=dt, device="cuda")
+        B.seg_admm_get(self.handle, what, out.data_ptr(), False)
+        self.synchronize()
+        return out
+
+    def get_host(self, what: int, out: torch.Tensor | None = None) -> torch.Tensor:
+        """A state component copied into host memory (pinned if `out` is)."""
+        shape, dt = self._shape(what)
+        if out is None:
+            out = torch.empty(shape, dtype=dt, pin_memory=True)
+        B.seg_admm_get(self.handle, what, out.data_ptr(), True)
+        return out
+
+    def set(self, what: int, src: torch.Tensor) -> None:
+        shape, dt = self._shape(what)
+        src = src.to(dt).contiguous()
+        if tuple(src.shape) != shape:
+            raise ValueError(f"expected shape {shape}, got {tuple(src.shape)}")
+        if src.is_cuda:
+            self.stream.wait_stream(torch.cuda.current_stream())
+        B.seg_admm_set(self.handle, what, src.data_ptr(), not src.is_cuda)
+        if src.is_cuda:
+            self.synchronize()
+
+    def energy(self) -> float:
+        return float(self.get(B.SEG_ENERGY))
+
+    def labels(self) -> torch.Tensor:
+        return self.get(B.SEG_LABELS)
+
+    def save(self, path: str) -> None:
+        B.seg_admm_save(self.handle, path)
+
+    def load(self, path: str) -> None:
+        B.seg_admm_load(self.handle, path)

@@ -1,0 +1,215 @@
+"""Thin ctypes binding of libshearseg.so (the C ABI in include/shearseg.h).
+
+Argument marshalling only: every function here forwards to the entry point of
+the same name, raising ``ShearsegError`` on a negative status.  Pointers are
+plain integers (``tensor.data_ptr()`` for device memory, numpy ``ctypes.data``
+for host memory); streams are integers (``torch.cuda.current_stream().cuda_stream``)
+or None.  There is no fallback: if the library cannot be loaded, every call
+raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+SHF_OK = 0
+SHF_ERR_ARG = -1
+SHF_ERR_SIZE = -2
+SHF_ERR_OOM = -3
+SHF_ERR_CUDA = -4
+SHF_ERR_NONFINITE = -5
+SHF_ERR_TIMEOUT = -6
+SHF_ERR_STATE = -7
+SHF_ERR_IO = -8
+
+SEG_U, SEG_W, SEG_BW, SEG_BV, SEG_S, SEG_LABELS, SEG_GAP, SEG_ENERGY, SEG_ITER, SEG_STV, SEG_V = range(11)
+
+_lock = threading.Lock()
+_lib = None
+
+
+class ShearsegError(RuntimeError):
+    def __init__(self, fn: str, code: int, msg: str):
+        super().__init__(f"{fn} failed with status {code}: {msg}")
+        self.code = code
+
+
+class seg_params(ctypes.Structure):
+    _fields_ = [
+        ("gamma", ctypes.c_float),
+        ("J", ctypes.c_int),
+        ("Lambda", ctypes.POINTER(ctypes.c_float)),
+        ("max_iters", ctypes.c_int),
+        ("tol", ctypes.c_float),
+        ("check_every", ctypes.c_int),
+    ]
+
+
+_VP = ctypes.c_void_p
+_I = ctypes.c_int
+_SIG = {
+    "shf_version": (_I, []),
+    "shf_last_error": (ctypes.c_char_p, []),
+    "shfilters_build": (_I, [_I, _I, _I, _VP, ctypes.POINTER(_VP)]),
+    "shfilters_destroy": (_I, [_VP]),
+    "shfilters_info": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "shfilters_copy": (_I, [_VP, _VP, _VP]),
+    "shearlet_analyze": (_I, [_VP, _VP, _I, _VP, _VP]),
+    "shearlet_synthesize": (_I, [_VP, _VP, _I, _VP, _VP]),
+    "seg_admm_init": (_I, [_VP, _VP, _I, ctypes.POINTER(ctypes.c_float), _I, ctypes.POINTER(seg_params), _VP,
+                           ctypes.POINTER(_VP)]),
+    "seg_admm_reset": (_I, [_VP, _VP, _I]),
+    "seg_admm_step": (_I, [_VP, _I]),
+    "seg_admm_solve": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)]),
+    "seg_admm_get": (_I, [_VP, _I, _VP, _I]),
+    "seg_admm_set": (_I, [_VP, _I, _VP, _I]),
+    "seg_admm_save": (_I, [_VP, ctypes.c_char_p]),
+    "seg_admm_load": (_I, [_VP, ctypes.c_char_p]),
+    "seg_admm_kernel_times": (_I, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_I)]),
+    "seg_admm_kernel_name": (ctypes.c_char_p, [_I]),
+    "seg_admm_sync": (_I, [_VP]),
+    "seg_admm_destroy": (_I, [_VP]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Loads libshearseg.so (building it first when missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_missing and not _build.up_to_date():
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError(f"libshearseg.so not found at {_build.LIB}; run paper_1112_1805_gb300.build")
+            L = ctypes.CDLL(_build.LIB)
+            for name, (res, args) in _SIG.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _call(name: str, *args) -> None:
+    L = lib()
+    rc = getattr(L, name)(*args)
+    if rc != SHF_OK:
+        raise ShearsegError(name, rc, L.shf_last_error().decode(errors="replace"))
+
+
+def _stream(stream):
+    return None if stream is None else ctypes.c_void_p(int(stream))
+
+
+def shf_version() -> int:
+    return int(lib().shf_version())
+
+
+def shf_last_error() -> str:
+    return lib().shf_last_error().decode(errors="replace")
+
+
+def shfilters_build(H: int, W: int, J: int, stream=None) -> int:
+    out = _VP()
+    _call("shfilters_build", H, W, J, _stream(stream), ctypes.byref(out))
+    return out.value
+
+
+def shfilters_destroy(bank: int) -> None:
+    _call("shfilters_destroy", _VP(bank))
+
+
+def shfilters_info(bank: int):
+    eta, H, W, J = _I(), _I(), _I(), _I()
+    _call("shfilters_info", _VP(bank), ctypes.byref(eta), ctypes.byref(H), ctypes.byref(W), ctypes.byref(J))
+    return eta.value, H.value, W.value, J.value
+
+
+def shfilters_copy(bank: int, dst: int, stream=None) -> None:
+    _call("shfilters_copy", _VP(bank), _VP(dst), _stream(stream))
+
+
+def shearlet_analyze(bank: int, u: int, nch: int, coef: int, stream=None) -> None:
+    _call("shearlet_analyze", _VP(bank), _VP(u), nch, _VP(coef), _stream(stream))
+
+
+def shearlet_synthesize(bank: int, coef: int, nch: int, u: int, stream=None) -> None:
+    _call("shearlet_synthesize", _VP(bank), _VP(coef), nch, _VP(u), _stream(stream))
+
+
+def make_params(gamma: float, J: int, Lambda, max_iters: int = 0, tol: float = 0.0, check_every: int = 1):
+    """Returns (seg_params, keepalive) -- keep the second item alive while the
+    struct is in use (it owns the Lambda array)."""
+    vals = [float(x) for x in Lambda]
+    if len(vals) != J + 1:
+        raise ValueError(f"Lambda needs J + 1 = {J + 1} weights, got {len(vals)}")
+    lam = (ctypes.c_float * (J + 1))(*vals)
+    p = seg_params(float(gamma), int(J), ctypes.cast(lam, ctypes.POINTER(ctypes.c_float)), int(max_iters),
+                   float(tol), int(check_every))
+    return p, lam
+
+
+def seg_admm_init(bank: int, f: int, C: int, codebook, K: int, params, stream=None) -> int:
+    """codebook: host sequence of K*C floats (label-major)."""
+    cb = (ctypes.c_float * (K * C))(*[float(x) for x in codebook])
+    out = _VP()
+    _call("seg_admm_init", _VP(bank), _VP(f), C, cb, K, ctypes.byref(params), _stream(stream), ctypes.byref(out))
+    return out.value
+
+
+def seg_admm_reset(state: int, f: int, f_on_host: bool) -> None:
+    _call("seg_admm_reset", _VP(state), _VP(f), int(bool(f_on_host)))
+
+
+def seg_admm_step(state: int, n_iters: int) -> None:
+    _call("seg_admm_step", _VP(state), int(n_iters))
+
+
+def seg_admm_solve(state: int):
+    it, res = _I(), ctypes.c_float()
+    _call("seg_admm_solve", _VP(state), ctypes.byref(it), ctypes.byref(res))
+    return it.value, res.value
+
+
+def seg_admm_get(state: int, what: int, dst: int, dst_on_host: bool) -> None:
+    _call("seg_admm_get", _VP(state), int(what), _VP(dst), int(bool(dst_on_host)))
+
+
+def seg_admm_set(state: int, what: int, src: int, src_on_host: bool) -> None:
+    _call("seg_admm_set", _VP(state), int(what), _VP(src), int(bool(src_on_host)))
+
+
+def seg_admm_save(state: int, path: str) -> None:
+    _call("seg_admm_save", _VP(state), path.encode())
+
+
+def seg_admm_load(state: int, path: str) -> None:
+    _call("seg_admm_load", _VP(state), path.encode())
+
+
+def seg_admm_kernel_times(state: int):
+    """{kernel name: milliseconds} for the kernels of the most recent iteration."""
+    ms = (ctypes.c_float * 8)()
+    nk = _I()
+    _call("seg_admm_kernel_times", _VP(state), ms, ctypes.byref(nk))
+    return {lib().seg_admm_kernel_name(i).decode(): float(ms[i]) for i in range(nk.value)}
+
+
+def seg_admm_kernel_name(i: int) -> str:
+    return lib().seg_admm_kernel_name(int(i)).decode()
+
+
+def seg_admm_sync(state: int) -> None:
+    _call("seg_admm_sync", _VP(state))
+
+
+def seg_admm_destroy(state: int) -> None:
+    _call("seg_admm_destroy", _VP(state))

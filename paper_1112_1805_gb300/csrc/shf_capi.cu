@@ -1,0 +1,686 @@
+// C ABI of the shearlet segmentation library: filter banks, the shearlet
+// transform and the ADMM state (Haeuser & Steidl, arXiv:1112.1805).  Argument
+// checking, buffer ownership, CUDA-graph capture of one ADMM iteration,
+// readouts and checkpoints.  All arithmetic runs in the kernels of
+// shf_bank.cu and shf_transform.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "shearseg.h"
+#include "shf_internal.h"
+
+using shf::Geo;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define SHF_CK(call)                                                                              \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return fail(SHF_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+
+template <typename T>
+int dev_alloc(T** p, size_t count, const char* what) {
+  *p = nullptr;
+  if (count == 0) return SHF_OK;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(e == cudaErrorMemoryAllocation ? SHF_ERR_OOM : SHF_ERR_CUDA,
+                std::string("cudaMalloc(") + what + "): " + cudaGetErrorString(e));
+  }
+  return SHF_OK;
+}
+
+int check_sizes(int H, int W, int J) {
+  if (J < 1 || J > shf::kMaxJ) return fail(SHF_ERR_ARG, "J must be in [1, 6]");
+  if (H < 8 || W < 8 || H > shf::kMaxSide || W > shf::kMaxSide)
+    return fail(SHF_ERR_SIZE, "H and W must be in [8, 2048]");
+  if (W & 1) return fail(SHF_ERR_SIZE, "W must be even");
+  shf::FftPlan p;
+  if (!shf::make_plan(H, &p) || !shf::make_plan(W / 2, &p))
+    return fail(SHF_ERR_SIZE, "H and W/2 must be products of powers of 2, 3 and 5");
+  return SHF_OK;
+}
+
+}  // namespace
+
+struct shf_bank {
+  Geo g;
+  float* bank = nullptr;
+  float2* twH = nullptr;
+  float2* twW = nullptr;
+  shf::FilterDesc* descs = nullptr;
+  int device = 0;
+};
+
+struct seg_state {
+  const shf_bank* bank = nullptr;
+  Geo g;
+  int K = 0, C = 0;
+  float gamma = 1.f;
+  std::vector<float> Lambda;
+  std::vector<float> codebook;  // [K][C], host copy for seg_admm_reset
+  int max_iters = 0;
+  float tol = 0.f;
+  int check_every = 1;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  float *f = nullptr, *s = nullptr, *bv = nullptr, *w = nullptr, *bw = nullptr, *u = nullptr, *stv = nullptr;
+  float2 *Ur = nullptr, *Y = nullptr, *partial = nullptr, *T = nullptr;
+  float *thr = nullptr, *lam = nullptr, *gap = nullptr;
+  int* labels = nullptr;
+  int* flag = nullptr;
+  double* red = nullptr;
+  int red_len = 0;
+  int groups = 1;
+  cudaGraphExec_t exec = nullptr;
+  bool graph_tried = false;
+  static constexpr int kNumKernels = 5;
+  cudaEvent_t ev[kNumKernels + 1] = {};  // around each kernel of the last iteration
+  long long iter = 0;
+  size_t P() const { return static_cast<size_t>(g.H) * g.W; }
+  size_t Ph() const { return static_cast<size_t>(g.H) * g.Wh; }
+};
+
+extern "C" {
+
+int shf_version(void) { return 100; }
+
+const char* shf_last_error(void) { return g_err.c_str(); }
+
+int shfilters_build(int H, int W, int J, void* stream, shf_bank** out) {
+  if (!out) return fail(SHF_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  int rc = check_sizes(H, W, J);
+  if (rc) return rc;
+  Geo g;
+  if (!shf::make_geo(H, W, J, &g)) return fail(SHF_ERR_SIZE, "unsupported geometry");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int device = 0, optin = 0;
+  SHF_CK(cudaGetDevice(&device));
+  SHF_CK(shf::prepare_kernels());
+  SHF_CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+  if (shf::max_dynamic_smem_needed(g, shf::kMaxK) > optin)
+    return fail(SHF_ERR_SIZE, "tile does not fit in shared memory");
+  auto* b = new shf_bank();
+  b->g = g;
+  b->device = device;
+  std::vector<shf::FilterDesc> d(g.eta);
+  shf::filter_descs(J, d.data());
+  if ((rc = dev_alloc(&b->bank, static_cast<size_t>(g.eta) * H * g.Wh, "bank")) ||
+      (rc = dev_alloc(&b->twH, H, "twH")) || (rc = dev_alloc(&b->twW, W, "twW")) ||
+      (rc = dev_alloc(&b->descs, g.eta, "descs"))) {
+    shfilters_destroy(b);
+    return rc;
+  }
+  b->g.bank = b->bank;
+  b->g.twH = b->twH;
+  b->g.twW = b->twW;
+  cudaError_t e = cudaMemcpyAsync(b->descs, d.data(), sizeof(shf::FilterDesc) * g.eta, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = shf::launch_twiddles(b->twH, H, st);
+  if (e == cudaSuccess) e = shf::launch_twiddles(b->twW, W, st);
+  if (e == cudaSuccess) e = shf::launch_build_bank(b->bank, b->g, b->descs, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // d is a host temporary
+  if (e != cudaSuccess) {
+    shfilters_destroy(b);
+    return fail(SHF_ERR_CUDA, std::string("shfilters_build: ") + cudaGetErrorString(e));
+  }
+  *out = b;
+  return SHF_OK;
+}
+
+int shfilters_destroy(shf_bank* b) {
+  if (!b) return SHF_OK;
+  cudaDeviceSynchronize();
+  cudaFree(b->bank);
+  cudaFree(b->twH);
+  cudaFree(b->twW);
+  cudaFree(b->descs);
+  delete b;
+  return SHF_OK;
+}
+
+int shfilters_info(const shf_bank* b, int* eta, int* H, int* W, int* J) {
+  if (!b) return fail(SHF_ERR_ARG, "bank is NULL");
+  if (eta) *eta = b->g.eta;
+  if (H) *H = b->g.H;
+  if (W) *W = b->g.W;
+  if (J) *J = b->g.J;
+  return SHF_OK;
+}
+
+int shfilters_copy(const shf_bank* b, float* dst, void* stream) {
+  if (!b || !dst) return fail(SHF_ERR_ARG, "NULL argument");
+  SHF_CK(cudaMemcpyAsync(dst, b->bank, sizeof(float) * b->g.eta * b->g.H * b->g.Wh, cudaMemcpyDeviceToDevice,
+                         static_cast<cudaStream_t>(stream)));
+  return SHF_OK;
+}
+
+int shearlet_analyze(const shf_bank* b, const float* u, int nch, float* coef, void* stream) {
+  if (!b || !u || !coef || nch < 1) return fail(SHF_ERR_ARG, "shearlet_analyze: bad argument");
+  if (!aligned8(u) || !aligned8(coef)) return fail(SHF_ERR_ARG, "shearlet_analyze: pointers must be 8-byte aligned");
+  const Geo& g = b->g;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t ph = static_cast<size_t>(g.H) * g.Wh;
+  float2* tmp = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&tmp), sizeof(float2) * ph * nch * (1 + g.eta), st);
+  if (e != cudaSuccess) return fail(SHF_ERR_OOM, std::string("shearlet_analyze: ") + cudaGetErrorString(e));
+  float2* Ur = tmp;
+  float2* Y = tmp + ph * nch;
+  e = shf::run_row_r2c(g, u, Ur, nch, 1.f, st);
+  if (e == cudaSuccess) e = shf::run_col_fan(g, Ur, Y, nch, shf::default_groups(g, nch), st);
+  if (e == cudaSuccess) e = shf::run_row_c2r(g, Y, coef, nch * g.eta, 1.f / (static_cast<float>(g.H) * g.W), st);
+  cudaError_t e2 = cudaFreeAsync(tmp, st);
+  if (e != cudaSuccess || e2 != cudaSuccess)
+    return fail(SHF_ERR_CUDA, std::string("shearlet_analyze: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+  return SHF_OK;
+}
+
+namespace {
+// T[nch][H][Wh] = column-inverse of sum_f W_f * fft2(coef_f) (unscaled).
+cudaError_t synthesis_spectrum(const Geo& g, const float* coef, int nch, float2* T, cudaStream_t st) {
+  const size_t ph = static_cast<size_t>(g.H) * g.Wh;
+  const int groups = shf::default_groups(g, nch);
+  float2* tmp = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&tmp), sizeof(float2) * ph * nch * (g.eta + groups), st);
+  if (e != cudaSuccess) return e;
+  float2* Z = tmp;
+  float2* part = tmp + ph * nch * g.eta;
+  e = shf::run_row_r2c(g, coef, Z, nch * g.eta, 1.f, st);
+  if (e == cudaSuccess) e = shf::run_col_gather(g, Z, part, nch, groups, st);
+  if (e == cudaSuccess) e = shf::run_col_reduce_inv(g, part, T, nch, groups, st);
+  cudaError_t e2 = cudaFreeAsync(tmp, st);
+  return e != cudaSuccess ? e : e2;
+}
+}  // namespace
+
+int shearlet_synthesize(const shf_bank* b, const float* coef, int nch, float* u, void* stream) {
+  if (!b || !coef || !u || nch < 1) return fail(SHF_ERR_ARG, "shearlet_synthesize: bad argument");
+  if (!aligned8(u) || !aligned8(coef))
+    return fail(SHF_ERR_ARG, "shearlet_synthesize: pointers must be 8-byte aligned");
+  const Geo& g = b->g;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t ph = static_cast<size_t>(g.H) * g.Wh;
+  float2* T = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&T), sizeof(float2) * ph * nch, st);
+  if (e != cudaSuccess) return fail(SHF_ERR_OOM, std::string("shearlet_synthesize: ") + cudaGetErrorString(e));
+  e = synthesis_spectrum(g, coef, nch, T, st);
+  if (e == cudaSuccess) e = shf::run_row_c2r(g, T, u, nch, 1.f / (static_cast<float>(g.H) * g.W), st);
+  cudaError_t e2 = cudaFreeAsync(T, st);
+  if (e != cudaSuccess || e2 != cudaSuccess)
+    return fail(SHF_ERR_CUDA, std::string("shearlet_synthesize: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+  return SHF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// ADMM state
+// ---------------------------------------------------------------------------
+
+namespace {
+
+void free_state(seg_state* s) {
+  if (s->exec) cudaGraphExecDestroy(s->exec);
+  for (cudaEvent_t e : s->ev)
+    if (e) cudaEventDestroy(e);
+  float* fl[] = {s->f, s->s, s->bv, s->w, s->bw, s->u, s->stv, s->thr, s->lam, s->gap};
+  for (float* p : fl) cudaFree(p);
+  cudaFree(s->Ur);
+  cudaFree(s->Y);
+  cudaFree(s->partial);
+  cudaFree(s->T);
+  cudaFree(s->labels);
+  cudaFree(s->flag);
+  cudaFree(s->red);
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+}
+
+// Data term from st->f and a zero state; checks f for NaN/Inf (synchronises).
+int restart(seg_state* st, const float* codebook) {
+  const Geo& g = st->g;
+  const size_t P = st->P();
+  SHF_CK(cudaMemsetAsync(st->flag, 0, sizeof(int), st->stream));
+  SHF_CK(shf::launch_count_nonfinite(st->f, static_cast<long>(P * st->C), st->flag, st->stream));
+  if (codebook) SHF_CK(shf::launch_data_term(st->f, st->C, codebook, st->K, st->s, static_cast<int>(P), st->stream));
+  SHF_CK(cudaMemsetAsync(st->bv, 0, sizeof(float) * P * st->K * g.eta, st->stream));
+  SHF_CK(cudaMemsetAsync(st->w, 0, sizeof(float) * P * st->K, st->stream));
+  SHF_CK(cudaMemsetAsync(st->bw, 0, sizeof(float) * P * st->K, st->stream));
+  SHF_CK(cudaMemsetAsync(st->u, 0, sizeof(float) * P * st->K, st->stream));
+  SHF_CK(cudaMemsetAsync(st->T, 0, sizeof(float2) * st->Ph() * st->K, st->stream));
+  int bad = 0;
+  SHF_CK(cudaMemcpyAsync(&bad, st->flag, sizeof(int), cudaMemcpyDeviceToHost, st->stream));
+  SHF_CK(cudaStreamSynchronize(st->stream));
+  st->iter = 0;
+  if (bad) return fail(SHF_ERR_NONFINITE, "image contains NaN or Inf");
+  return SHF_OK;
+}
+
+// One ADMM iteration: five kernels, with an event recorded before each and
+// after the last (event nodes inside the captured graph).
+cudaError_t enqueue_iteration(seg_state* st) {
+  const Geo& g = st->g;
+  const float scale = 1.f / (static_cast<float>(g.H) * g.W);
+  cudaStream_t s = st->stream;
+  cudaError_t e = cudaEventRecord(st->ev[0], s);
+  if (e == cudaSuccess)
+    e = shf::run_row_ustep(g, st->T, st->s, st->w, st->bw, st->u, st->Ur, nullptr, st->K, st->gamma, scale, s);
+  if (e == cudaSuccess) e = cudaEventRecord(st->ev[1], s);
+  if (e == cudaSuccess) e = shf::run_col_fan(g, st->Ur, st->Y, st->K, st->groups, s);
+  if (e == cudaSuccess) e = cudaEventRecord(st->ev[2], s);
+  if (e == cudaSuccess) e = shf::run_row_shrink(g, st->Y, st->bv, st->thr, st->K * g.eta, scale, s);
+  if (e == cudaSuccess) e = cudaEventRecord(st->ev[3], s);
+  if (e == cudaSuccess) e = shf::run_col_gather(g, st->Y, st->partial, st->K, st->groups, s);
+  if (e == cudaSuccess) e = cudaEventRecord(st->ev[4], s);
+  if (e == cudaSuccess) e = shf::run_col_reduce_inv(g, st->partial, st->T, st->K, st->groups, s);
+  if (e == cudaSuccess) e = cudaEventRecord(st->ev[5], s);
+  return e;
+}
+
+// Captures one iteration into a graph when the stream can be captured (not
+// the legacy default stream); otherwise iterations are launched directly.
+void try_capture(seg_state* st) {
+  st->graph_tried = true;
+  if (st->stream == nullptr) return;
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(st->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  cudaError_t e = enqueue_iteration(st);
+  cudaError_t e2 = cudaStreamEndCapture(st->stream, &graph);
+  if (e == cudaSuccess && e2 == cudaSuccess && graph) {
+    if (cudaGraphInstantiate(&st->exec, graph, 0) != cudaSuccess) st->exec = nullptr;
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();
+}
+
+int energy_of_w(seg_state* st, double* out_host) {
+  const Geo& g = st->g;
+  const size_t P = st->P();
+  const float scale = 1.f / (static_cast<float>(g.H) * g.W);
+  // <w, s>
+  SHF_CK(shf::launch_dot(st->w, st->s, static_cast<long>(P * st->K), st->red + 2, 512, st->red, st->stream));
+  // sum_f Lambda_f ||(S w)_f||_1: row-forward of w into Ur, fan-out into Y, l1 of the row-inverse.
+  SHF_CK(shf::run_row_r2c(g, st->w, st->Ur, st->K, 1.f, st->stream));
+  SHF_CK(shf::run_col_fan(g, st->Ur, st->Y, st->K, st->groups, st->stream));
+  int nb = 0;
+  SHF_CK(shf::run_row_l1(g, st->Y, st->lam, st->K * g.eta, scale, st->red + 2 + 512, &nb, st->stream));
+  SHF_CK(shf::launch_sum_partials(st->red + 2 + 512, nb, st->red + 1, st->stream));
+  double h[2];
+  SHF_CK(cudaMemcpyAsync(h, st->red, sizeof(h), cudaMemcpyDeviceToHost, st->stream));
+  SHF_CK(cudaStreamSynchronize(st->stream));
+  *out_host = h[0] + h[1];
+  return SHF_OK;
+}
+
+int residual_uw(seg_state* st, double* out_host) {
+  const size_t n = st->P() * st->K;
+  SHF_CK(shf::launch_sqdiff(st->u, st->w, static_cast<long>(n), st->red + 2, 512, st->red, st->stream));
+  double h = 0;
+  SHF_CK(cudaMemcpyAsync(&h, st->red, sizeof(double), cudaMemcpyDeviceToHost, st->stream));
+  SHF_CK(cudaStreamSynchronize(st->stream));
+  *out_host = std::sqrt(h / static_cast<double>(n));
+  return SHF_OK;
+}
+
+int copy_out(seg_state* st, void* dst, const void* src, size_t bytes, int to_host) {
+  SHF_CK(cudaMemcpyAsync(dst, src, bytes, to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st->stream));
+  if (to_host) SHF_CK(cudaStreamSynchronize(st->stream));
+  return SHF_OK;
+}
+
+int copy_in(seg_state* st, void* dst, const void* src, size_t bytes, int from_host) {
+  SHF_CK(cudaMemcpyAsync(dst, src, bytes, from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st->stream));
+  if (from_host) SHF_CK(cudaStreamSynchronize(st->stream));
+  return SHF_OK;
+}
+
+}  // namespace
+
+int seg_admm_init(const shf_bank* b, const float* f, int C, const float* codebook, int K, const seg_params* p,
+                  void* stream, seg_state** out) {
+  if (!out) return fail(SHF_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!b || !f || !codebook || !p || !p->Lambda) return fail(SHF_ERR_ARG, "seg_admm_init: NULL argument");
+  if (K < 2 || K > shf::kMaxK) return fail(SHF_ERR_ARG, "K must be in [2, 16]");
+  if (C != 1 && C != 3) return fail(SHF_ERR_ARG, "C must be 1 or 3");
+  if (p->J != b->g.J) return fail(SHF_ERR_STATE, "params->J differs from the bank's J");
+  if (!(p->gamma > 0.f) || !std::isfinite(p->gamma)) return fail(SHF_ERR_ARG, "gamma must be positive and finite");
+  if (!aligned8(f)) return fail(SHF_ERR_ARG, "f must be 8-byte aligned");
+  for (int i = 0; i < K * C; ++i)
+    if (!std::isfinite(codebook[i])) return fail(SHF_ERR_NONFINITE, "codebook contains NaN or Inf");
+  for (int j = 0; j <= p->J; ++j)
+    if (!std::isfinite(p->Lambda[j]) || p->Lambda[j] < 0.f)
+      return fail(SHF_ERR_ARG, "Lambda must be finite and non-negative");
+  auto* st = new seg_state();
+  st->bank = b;
+  st->g = b->g;
+  st->K = K;
+  st->C = C;
+  st->gamma = p->gamma;
+  st->Lambda.assign(p->Lambda, p->Lambda + p->J + 1);
+  st->codebook.assign(codebook, codebook + K * C);
+  st->max_iters = p->max_iters;
+  st->tol = p->tol;
+  st->check_every = p->check_every > 0 ? p->check_every : 1;
+  if (stream) {
+    st->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&st->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete st;
+      return fail(SHF_ERR_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    }
+    st->own_stream = true;
+  }
+  const Geo& g = st->g;
+  const size_t P = st->P(), Ph = st->Ph();
+  st->groups = shf::default_groups(g, K);
+  for (cudaEvent_t& ev : st->ev) {
+    cudaError_t e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) {
+      free_state(st);
+      return fail(SHF_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
+    }
+  }
+  const int l1_blocks = ((g.H + g.RB - 1) / g.RB) * K * g.eta;
+  st->red_len = 2 + 512 + l1_blocks;
+  int rc;
+  if ((rc = dev_alloc(&st->f, P * C, "f")) || (rc = dev_alloc(&st->s, P * K, "s")) ||
+      (rc = dev_alloc(&st->bv, P * K * g.eta, "b_v")) || (rc = dev_alloc(&st->w, P * K, "w")) ||
+      (rc = dev_alloc(&st->bw, P * K, "b_w")) || (rc = dev_alloc(&st->u, P * K, "u")) ||
+      (rc = dev_alloc(&st->stv, P * K, "stv")) || (rc = dev_alloc(&st->Ur, Ph * K, "Ur")) ||
+      (rc = dev_alloc(&st->Y, Ph * K * g.eta, "Y")) ||
+      (rc = dev_alloc(&st->partial, Ph * K * st->groups, "partial")) || (rc = dev_alloc(&st->T, Ph * K, "T")) ||
+      (rc = dev_alloc(&st->thr, g.eta, "thr")) || (rc = dev_alloc(&st->lam, g.eta, "lam")) ||
+      (rc = dev_alloc(&st->gap, P, "gap")) || (rc = dev_alloc(&st->labels, P, "labels")) ||
+      (rc = dev_alloc(&st->flag, 1, "flag")) || (rc = dev_alloc(&st->red, st->red_len, "red"))) {
+    free_state(st);
+    return rc;
+  }
+  std::vector<shf::FilterDesc> d(g.eta);
+  shf::filter_descs(g.J, d.data());
+  std::vector<float> thr(g.eta), lam(g.eta);
+  for (int i = 0; i < g.eta; ++i) {
+    lam[i] = d[i].kind == 0 ? st->Lambda[0] : st->Lambda[d[i].j + 1];
+    thr[i] = st->gamma * lam[i];
+  }
+  cudaError_t e = cudaMemcpyAsync(st->thr, thr.data(), sizeof(float) * g.eta, cudaMemcpyHostToDevice, st->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(st->lam, lam.data(), sizeof(float) * g.eta, cudaMemcpyHostToDevice, st->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(st->f, f, sizeof(float) * P * C, cudaMemcpyDeviceToDevice, st->stream);
+  if (e != cudaSuccess) {
+    free_state(st);
+    return fail(SHF_ERR_CUDA, std::string("seg_admm_init: ") + cudaGetErrorString(e));
+  }
+  rc = restart(st, codebook);  // synchronises: thr/lam host vectors stay valid until here
+  if (rc) {
+    free_state(st);
+    return rc;
+  }
+  *out = st;
+  return SHF_OK;
+}
+
+int seg_admm_reset(seg_state* st, const float* f, int f_on_host) {
+  if (!st || !f) return fail(SHF_ERR_ARG, "seg_admm_reset: NULL argument");
+  if (!f_on_host && !aligned8(f)) return fail(SHF_ERR_ARG, "f must be 8-byte aligned");
+  SHF_CK(cudaMemcpyAsync(st->f, f, sizeof(float) * st->P() * st->C,
+                         f_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st->stream));
+  return restart(st, st->codebook.data());
+}
+
+int seg_admm_step(seg_state* st, int n) {
+  if (!st || n < 0) return fail(SHF_ERR_ARG, "seg_admm_step: bad argument");
+  if (n == 0) return SHF_OK;
+  if (!st->graph_tried) try_capture(st);
+  for (int i = 0; i < n; ++i) {
+    if (st->exec) {
+      SHF_CK(cudaGraphLaunch(st->exec, st->stream));
+    } else {
+      SHF_CK(enqueue_iteration(st));
+    }
+  }
+  st->iter += n;
+  return SHF_OK;
+}
+
+int seg_admm_solve(seg_state* st, int* iters_done, float* final_residual) {
+  if (!st) return fail(SHF_ERR_ARG, "state is NULL");
+  double res = INFINITY;
+  int done = 0;
+  while (done < st->max_iters) {
+    const int n = std::min(st->check_every, st->max_iters - done);
+    int rc = seg_admm_step(st, n);
+    if (rc) return rc;
+    done += n;
+    rc = residual_uw(st, &res);
+    if (rc) return rc;
+    if (res < st->tol) break;
+  }
+  if (iters_done) *iters_done = done;
+  if (final_residual) *final_residual = static_cast<float>(res);
+  return SHF_OK;
+}
+
+int seg_admm_get(seg_state* st, int what, void* dst, int on_host) {
+  if (!st || !dst) return fail(SHF_ERR_ARG, "seg_admm_get: NULL argument");
+  const Geo& g = st->g;
+  const size_t P = st->P(), KP = P * st->K;
+  switch (what) {
+    case SEG_U: return copy_out(st, dst, st->u, sizeof(float) * KP, on_host);
+    case SEG_W: return copy_out(st, dst, st->w, sizeof(float) * KP, on_host);
+    case SEG_BW: return copy_out(st, dst, st->bw, sizeof(float) * KP, on_host);
+    case SEG_BV: return copy_out(st, dst, st->bv, sizeof(float) * KP * g.eta, on_host);
+    case SEG_S: return copy_out(st, dst, st->s, sizeof(float) * KP, on_host);
+    case SEG_STV:
+      SHF_CK(shf::run_row_c2r(g, st->T, st->stv, st->K, 1.f / (static_cast<float>(g.H) * g.W), st->stream));
+      return copy_out(st, dst, st->stv, sizeof(float) * KP, on_host);
+    case SEG_LABELS:
+    case SEG_GAP:
+      SHF_CK(shf::launch_labels(st->w, st->K, static_cast<int>(P), st->labels, st->gap, st->stream));
+      if (what == SEG_LABELS) return copy_out(st, dst, st->labels, sizeof(int) * P, on_host);
+      return copy_out(st, dst, st->gap, sizeof(float) * P, on_host);
+    case SEG_ENERGY: {
+      double e = 0;
+      int rc = energy_of_w(st, &e);
+      if (rc) return rc;
+      if (on_host) {
+        *static_cast<double*>(dst) = e;
+        return SHF_OK;
+      }
+      SHF_CK(cudaMemcpy(dst, &e, sizeof(double), cudaMemcpyHostToDevice));
+      return SHF_OK;
+    }
+    case SEG_ITER:
+      if (!on_host) return fail(SHF_ERR_ARG, "SEG_ITER is host only");
+      *static_cast<int*>(dst) = static_cast<int>(st->iter);
+      return SHF_OK;
+    default: return fail(SHF_ERR_ARG, "unknown selector");
+  }
+}
+
+int seg_admm_set(seg_state* st, int what, const void* src, int on_host) {
+  if (!st || !src) return fail(SHF_ERR_ARG, "seg_admm_set: NULL argument");
+  const Geo& g = st->g;
+  const size_t P = st->P(), KP = P * st->K;
+  switch (what) {
+    case SEG_W: return copy_in(st, st->w, src, sizeof(float) * KP, on_host);
+    case SEG_BW: return copy_in(st, st->bw, src, sizeof(float) * KP, on_host);
+    case SEG_BV: return copy_in(st, st->bv, src, sizeof(float) * KP * g.eta, on_host);
+    case SEG_STV: {
+      int rc = copy_in(st, st->stv, src, sizeof(float) * KP, on_host);
+      if (rc) return rc;
+      // T = H * row-forward(stv), so that the u-step's 1/(HW) row-inverse returns stv.
+      SHF_CK(shf::run_row_r2c(g, st->stv, st->T, st->K, static_cast<float>(g.H), st->stream));
+      return SHF_OK;
+    }
+    case SEG_V: {
+      float* d = nullptr;
+      SHF_CK(cudaMallocAsync(reinterpret_cast<void**>(&d), sizeof(float) * KP * g.eta, st->stream));
+      cudaError_t e = cudaMemcpyAsync(d, src, sizeof(float) * KP * g.eta,
+                                      on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st->stream);
+      if (e == cudaSuccess) e = shf::launch_sub(d, st->bv, d, static_cast<long>(KP * g.eta), st->stream);
+      if (e == cudaSuccess) e = synthesis_spectrum(g, d, st->K, st->T, st->stream);
+      cudaError_t e2 = cudaFreeAsync(d, st->stream);
+      if (e == cudaSuccess) e = e2;
+      if (e == cudaSuccess && on_host) e = cudaStreamSynchronize(st->stream);
+      if (e != cudaSuccess) return fail(SHF_ERR_CUDA, std::string("seg_admm_set(SEG_V): ") + cudaGetErrorString(e));
+      return SHF_OK;
+    }
+    default: return fail(SHF_ERR_ARG, "selector cannot be set");
+  }
+}
+
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int32_t H, W, K, J, eta, C;
+  int64_t iter;
+  float gamma;
+  float Lambda[shf::kMaxJ + 1];
+};
+}  // namespace
+
+int seg_admm_save(seg_state* st, const char* path) {
+  if (!st || !path) return fail(SHF_ERR_ARG, "seg_admm_save: NULL argument");
+  const Geo& g = st->g;
+  const size_t KP = st->P() * st->K;
+  CkptHeader h{};
+  std::memcpy(h.magic, "SHFCKPT1", 8);
+  h.H = g.H;
+  h.W = g.W;
+  h.K = st->K;
+  h.J = g.J;
+  h.eta = g.eta;
+  h.C = st->C;
+  h.iter = st->iter;
+  h.gamma = st->gamma;
+  for (int j = 0; j <= g.J; ++j) h.Lambda[j] = st->Lambda[j];
+  std::vector<float> buf(KP * g.eta);
+  FILE* fp = std::fopen(path, "wb");
+  if (!fp) return fail(SHF_ERR_IO, std::string("cannot open ") + path);
+  bool ok = std::fwrite(&h, sizeof(h), 1, fp) == 1;
+  // the carried synthesis spectrum T, raw, so that a resumed run continues bit for bit
+  const size_t nT = 2 * st->Ph() * st->K;
+  std::vector<float> tbuf(nT);
+  int rc0 = copy_out(st, tbuf.data(), st->T, sizeof(float) * nT, 1);
+  if (rc0) {
+    std::fclose(fp);
+    return rc0;
+  }
+  ok = ok && std::fwrite(tbuf.data(), sizeof(float), nT, fp) == nT;
+  const int parts[] = {SEG_BV, SEG_W, SEG_BW, SEG_S, SEG_U};
+  for (int what : parts) {
+    const size_t n = what == SEG_BV ? KP * g.eta : KP;
+    int rc = seg_admm_get(st, what, buf.data(), 1);
+    if (rc) {
+      std::fclose(fp);
+      return rc;
+    }
+    ok = ok && std::fwrite(buf.data(), sizeof(float), n, fp) == n;
+  }
+  ok = (std::fclose(fp) == 0) && ok;
+  return ok ? SHF_OK : fail(SHF_ERR_IO, std::string("write failed: ") + path);
+}
+
+int seg_admm_load(seg_state* st, const char* path) {
+  if (!st || !path) return fail(SHF_ERR_ARG, "seg_admm_load: NULL argument");
+  const Geo& g = st->g;
+  const size_t KP = st->P() * st->K;
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) return fail(SHF_ERR_IO, std::string("cannot open ") + path);
+  CkptHeader h{};
+  if (std::fread(&h, sizeof(h), 1, fp) != 1 || std::memcmp(h.magic, "SHFCKPT1", 8) != 0) {
+    std::fclose(fp);
+    return fail(SHF_ERR_IO, "not a checkpoint file");
+  }
+  if (h.H != g.H || h.W != g.W || h.K != st->K || h.J != g.J) {
+    std::fclose(fp);
+    return fail(SHF_ERR_STATE, "checkpoint sizes differ from the state's");
+  }
+  std::vector<float> buf(KP * g.eta);
+  const size_t nT = 2 * st->Ph() * st->K;
+  std::vector<float> tbuf(nT);
+  if (std::fread(tbuf.data(), sizeof(float), nT, fp) != nT) {
+    std::fclose(fp);
+    return fail(SHF_ERR_IO, "truncated checkpoint");
+  }
+  int rc0 = copy_in(st, st->T, tbuf.data(), sizeof(float) * nT, 1);
+  if (rc0) {
+    std::fclose(fp);
+    return rc0;
+  }
+  const int parts[] = {SEG_BV, SEG_W, SEG_BW};
+  for (int what : parts) {
+    const size_t n = what == SEG_BV ? KP * g.eta : KP;
+    if (std::fread(buf.data(), sizeof(float), n, fp) != n) {
+      std::fclose(fp);
+      return fail(SHF_ERR_IO, "truncated checkpoint");
+    }
+    int rc = seg_admm_set(st, what, buf.data(), 1);
+    if (rc) {
+      std::fclose(fp);
+      return rc;
+    }
+  }
+  // s and u
+  for (float* dstp : {st->s, st->u}) {
+    if (std::fread(buf.data(), sizeof(float), KP, fp) != KP) {
+      std::fclose(fp);
+      return fail(SHF_ERR_IO, "truncated checkpoint");
+    }
+    int rc = copy_in(st, dstp, buf.data(), sizeof(float) * KP, 1);
+    if (rc) {
+      std::fclose(fp);
+      return rc;
+    }
+  }
+  std::fclose(fp);
+  st->iter = h.iter;
+  return SHF_OK;
+}
+
+int seg_admm_kernel_times(seg_state* st, float* ms, int* nk) {
+  if (!st || !ms) return fail(SHF_ERR_ARG, "seg_admm_kernel_times: NULL argument");
+  if (st->iter == 0) return fail(SHF_ERR_STATE, "no iteration has run yet");
+  SHF_CK(cudaEventSynchronize(st->ev[seg_state::kNumKernels]));
+  for (int i = 0; i < seg_state::kNumKernels; ++i) SHF_CK(cudaEventElapsedTime(&ms[i], st->ev[i], st->ev[i + 1]));
+  if (nk) *nk = seg_state::kNumKernels;
+  return SHF_OK;
+}
+
+const char* seg_admm_kernel_name(int i) {
+  static const char* names[] = {"k_row_ustep", "k_col_fan", "k_row_shrink", "k_col_gather", "k_col_reduce_inv"};
+  return (i >= 0 && i < seg_state::kNumKernels) ? names[i] : "";
+}
+
+int seg_admm_sync(seg_state* st) {
+  if (!st) return fail(SHF_ERR_ARG, "state is NULL");
+  SHF_CK(cudaStreamSynchronize(st->stream));
+  return SHF_OK;
+}
+
+int seg_admm_destroy(seg_state* st) {
+  if (!st) return SHF_OK;
+  cudaStreamSynchronize(st->stream);
+  free_state(st);
+  return SHF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,83 @@
+// Internal interface between the C ABI layer and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "shf_fft.cuh"
+
+namespace shf {
+
+constexpr int kMaxK = 16;     // labels per pixel held in registers by the w-step
+constexpr int kMaxC = 3;      // image channels
+constexpr int kMaxJ = 6;      // scales
+constexpr int kMaxSide = 2048;
+constexpr int kColThreads = 256;
+constexpr int kRowThreads = 256;
+
+// Geometry and launch shapes of one (H, W, J) problem.
+struct Geo {
+  int H, W, J, eta;
+  int L;   // W / 2, length of the packed complex row transform
+  int Wh;  // W / 2 + 1, columns of the half spectrum
+  FftPlan planH, planL;
+  int TC;       // columns per column-transform tile
+  int ntiles;   // ceil(Wh / TC)
+  int RB;       // rows per row-transform block
+  int maxe;     // per-thread register elements of a column tile (8, 16 or 32)
+  const float2* twH;  // exp(-2 pi i m / H), m < H
+  const float2* twW;  // exp(-2 pi i m / W), m < W
+  const float* bank;  // [eta][H][Wh]
+};
+
+// Filter descriptor in bank order: kind 0 low-pass, 1 horizontal cone,
+// 2 vertical cone, 3 glued seam shearlet; scale j; shear k.
+struct FilterDesc {
+  int kind, j, k;
+};
+
+bool make_geo(int H, int W, int J, Geo* g);
+int filter_descs(int J, FilterDesc* out);  // returns eta
+
+// Filter bank and tables (shf_bank.cu).
+cudaError_t launch_twiddles(float2* tw, int N, cudaStream_t st);
+cudaError_t launch_build_bank(float* bank, const Geo& g, const FilterDesc* descs_dev, cudaStream_t st);
+cudaError_t launch_data_term(const float* f, int C, const float* codebook_host, int K, float* s, int P,
+                             cudaStream_t st);
+cudaError_t launch_labels(const float* w, int K, int P, int* labels, float* gap, cudaStream_t st);
+cudaError_t launch_count_nonfinite(const float* x, long n, int* count, cudaStream_t st);
+// Deterministic sums: partial[block] in FP64 then one ordered final pass.
+cudaError_t launch_dot(const float* a, const float* b, long n, double* partial, int nblocks, double* out,
+                       cudaStream_t st);
+cudaError_t launch_sqdiff(const float* a, const float* b, long n, double* partial, int nblocks, double* out,
+                          cudaStream_t st);
+cudaError_t launch_sum_partials(const double* partial, int n, double* out, cudaStream_t st);
+
+// Transform kernels (shf_transform.cu).
+// Real rows [planes][H][W] -> half spectra [planes][H][Wh] (row transforms).
+cudaError_t run_row_r2c(const Geo& g, const float* in, float2* out, int planes, float scale, cudaStream_t st);
+// Half spectra -> real rows, times `scale`.
+cudaError_t run_row_c2r(const Geo& g, const float2* in, float* out, int planes, float scale, cudaStream_t st);
+// ADMM v-step on coefficient spectra Y [nch*eta][H][Wh] (in place) and b_v.
+cudaError_t run_row_shrink(const Geo& g, float2* Y, float* bv, const float* thr, int planes, float scale,
+                           cudaStream_t st);
+// sum_f lam[f] * ||ifft rows of Y_f||_1 into partial[nblocks] (nblocks returned).
+cudaError_t run_row_l1(const Geo& g, const float2* Y, const float* lam, int planes, float scale, double* partial,
+                       int* nblocks, cudaStream_t st);
+// Column transform, fan-out over filters: in [nch][H][Wh] (row spectra) ->
+// out [nch][eta][H][Wh] = column-inverse( W_f * column-forward(in) ).
+cudaError_t run_col_fan(const Geo& g, const float2* in, float2* out, int nch, int groups, cudaStream_t st);
+// Column transform, gather over filters: partial[grp][nch][H][Wh] =
+// sum_{f in grp} W_f * column-forward(in[ch][f]).
+cudaError_t run_col_gather(const Geo& g, const float2* in, float2* partial, int nch, int groups, cudaStream_t st);
+// out[nch][H][Wh] = column-inverse( sum_grp partial[grp] ).
+cudaError_t run_col_reduce_inv(const Geo& g, const float2* partial, float2* out, int nch, int groups,
+                               cudaStream_t st);
+// ADMM u-step and w-step per row block over all K labels.
+cudaError_t run_row_ustep(const Geo& g, const float2* T, const float* s, float* w, float* bw, float* u, float2* Ur,
+                          float* stv, int K, float gamma, float scale, cudaStream_t st);
+int default_groups(const Geo& g, int nch);
+cudaError_t prepare_kernels();
+int max_dynamic_smem_needed(const Geo& g, int K);
+cudaError_t launch_sub(const float* a, const float* b, float* out, long n, cudaStream_t st);  // out = a - b
+
+}  // namespace shf

@@ -269,24 +269,28 @@ int restart(seg_state* st, const float* codebook) {
   return SHF_OK;
 }
 
+// Records an event; during stream capture it becomes an event-record node of
+// the graph (cudaEventRecordExternal), so each replay timestamps it.
+cudaError_t record(cudaEvent_t ev, cudaStream_t s) { return cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal); }
+
 // One ADMM iteration: five kernels, with an event recorded before each and
 // after the last (event nodes inside the captured graph).
 cudaError_t enqueue_iteration(seg_state* st) {
   const Geo& g = st->g;
   const float scale = 1.f / (static_cast<float>(g.H) * g.W);
   cudaStream_t s = st->stream;
-  cudaError_t e = cudaEventRecord(st->ev[0], s);
+  cudaError_t e = record(st->ev[0], s);
   if (e == cudaSuccess)
     e = shf::run_row_ustep(g, st->T, st->s, st->w, st->bw, st->u, st->Ur, nullptr, st->K, st->gamma, scale, s);
-  if (e == cudaSuccess) e = cudaEventRecord(st->ev[1], s);
+  if (e == cudaSuccess) e = record(st->ev[1], s);
   if (e == cudaSuccess) e = shf::run_col_fan(g, st->Ur, st->Y, st->K, st->groups, s);
-  if (e == cudaSuccess) e = cudaEventRecord(st->ev[2], s);
+  if (e == cudaSuccess) e = record(st->ev[2], s);
   if (e == cudaSuccess) e = shf::run_row_shrink(g, st->Y, st->bv, st->thr, st->K * g.eta, scale, s);
-  if (e == cudaSuccess) e = cudaEventRecord(st->ev[3], s);
+  if (e == cudaSuccess) e = record(st->ev[3], s);
   if (e == cudaSuccess) e = shf::run_col_gather(g, st->Y, st->partial, st->K, st->groups, s);
-  if (e == cudaSuccess) e = cudaEventRecord(st->ev[4], s);
+  if (e == cudaSuccess) e = record(st->ev[4], s);
   if (e == cudaSuccess) e = shf::run_col_reduce_inv(g, st->partial, st->T, st->K, st->groups, s);
-  if (e == cudaSuccess) e = cudaEventRecord(st->ev[5], s);
+  if (e == cudaSuccess) e = record(st->ev[5], s);
   return e;
 }
 

@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--cpu-iters", type=int, default=2, help="oracle iterations in the CPU-baseline sample")
+    ap.add_argument("--iters", type=int, default=0,
+                    help="ADMM iterations per step for short profiling runs (default: the workload's 500)")
     return ap.parse_args()
 
 
@@ -233,6 +235,10 @@ def run_ours(args):
             dist.barrier()
 
     img, lab, wl = synth.make_workload_image(WORKLOAD)
+    if args.iters > 0:
+        import dataclasses
+
+        wl = dataclasses.replace(wl, iters=args.iters)
     # the CPU-baseline leg runs first (rank 0, N = 1), before any GPU work
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

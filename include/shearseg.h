@@ -114,6 +114,26 @@ int shearlet_analyze(const shf_bank* bank, const float* u, int nch, float* coef,
  * coef: device [nch][eta][H][W]; u: device [nch][H][W]. */
 int shearlet_synthesize(const shf_bank* bank, const float* coef, int nch, float* u, void* stream);
 
+/* Allocation-free form of shearlet_analyze.  The paper has no counterpart: it
+ * exists for callers that must not allocate device memory when they run a
+ * transform -- a real-time loop that cannot stall on the allocator, a plugin
+ * whose host application owns all device memory, a tool that forbids
+ * allocation after start-up.  Same arguments, layout and result as
+ * shearlet_analyze; the caller still provides u and coef.  Its temporaries
+ * live in one fixed 32 MiB array inside the library image, which every GPU
+ * that loads the library keeps reserved until the process exits; the call
+ * itself allocates nothing (no cudaMalloc, no pool, no library allocation).
+ * Limit: nch * (eta + 1) * H * (W/2 + 1) * 8 bytes must not exceed 32 MiB
+ * (e.g. one 512 x 512 channel at J = 3, or four 256 x 256 channels at J = 4);
+ * larger requests fail with SHF_ERR_SIZE and a message giving both numbers.
+ * The first call on each device looks up the array's device address with
+ * that device current; make that first call before any stream capture.
+ * Every call on a device shares the one array and leaves its contents behind
+ * (nothing needs clearing: each call writes every element it reads), so calls
+ * whose work overlaps on the GPU -- other streams, other host threads --
+ * race on it and must be serialised by the caller. */
+int shearlet_analyze_noalloc(const shf_bank* bank, const float* u, int nch, float* coef, void* stream);
+
 /* ---------------------------------------------------------------------------
  * ADMM for eq. problemSegmentationADMM (Sec. 3): splitting (I_q (x) S) u = v,
  * u = w; per iteration

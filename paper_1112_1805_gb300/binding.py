@@ -60,6 +60,7 @@ _SIG = {
     "shfilters_copy": (_I, [_VP, _VP, _VP]),
     "shearlet_analyze": (_I, [_VP, _VP, _I, _VP, _VP]),
     "shearlet_synthesize": (_I, [_VP, _VP, _I, _VP, _VP]),
+    "shearlet_analyze_noalloc": (_I, [_VP, _VP, _I, _VP, _VP]),
     "seg_admm_init": (_I, [_VP, _VP, _I, ctypes.POINTER(ctypes.c_float), _I, ctypes.POINTER(seg_params), _VP,
                            ctypes.POINTER(_VP)]),
     "seg_admm_reset": (_I, [_VP, _VP, _I]),
@@ -139,6 +140,13 @@ def shfilters_copy(bank: int, dst: int, stream=None) -> None:
 
 def shearlet_analyze(bank: int, u: int, nch: int, coef: int, stream=None) -> None:
     _call("shearlet_analyze", _VP(bank), _VP(u), nch, _VP(coef), _stream(stream))
+
+
+def shearlet_analyze_noalloc(bank: int, u: int, nch: int, coef: int, stream=None) -> None:
+    """shearlet_analyze with its temporaries in the library's fixed 32 MiB
+    device array instead of freshly allocated memory (for callers that must
+    not allocate); overlapping calls on one GPU race on that array."""
+    _call("shearlet_analyze_noalloc", _VP(bank), _VP(u), nch, _VP(coef), _stream(stream))
 
 
 def shearlet_synthesize(bank: int, coef: int, nch: int, u: int, stream=None) -> None:

@@ -96,6 +96,11 @@ struct seg_state {
   size_t Ph() const { return static_cast<size_t>(g.H) * g.Wh; }
 };
 
+namespace shf {
+void bank_geo(const shf_bank* b, Geo* g) { *g = b->g; }
+int set_error(int code, const std::string& msg) { return fail(code, msg); }
+}  // namespace shf
+
 extern "C" {
 
 int shf_version(void) { return 100; }

@@ -3,7 +3,11 @@
 
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include "shf_fft.cuh"
+
+struct shf_bank;
 
 namespace shf {
 
@@ -79,5 +83,10 @@ int default_groups(const Geo& g, int nch);
 cudaError_t prepare_kernels();
 int max_dynamic_smem_needed(const Geo& g, int K);
 cudaError_t launch_sub(const float* a, const float* b, float* out, long n, cudaStream_t st);  // out = a - b
+
+// C ABI layer (shf_capi.cu): the geometry and device tables of a bank, and the
+// thread-local message behind shf_last_error() (returns code).
+void bank_geo(const shf_bank* b, Geo* g);
+int set_error(int code, const std::string& msg);
 
 }  // namespace shf

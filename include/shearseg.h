@@ -201,16 +201,16 @@ int seg_admm_set(seg_state* st, int what, const void* src, int src_on_host);
 int seg_admm_save(seg_state* st, const char* path);
 int seg_admm_load(seg_state* st, const char* path);
 
-/* Instrumentation (no counterpart in the paper): durations in milliseconds of
- * the kernels of the most recent iteration, measured by CUDA events recorded
- * on the state's stream between them (inside the replayed graph).  ms must
- * hold 8 floats; *nk (may be NULL) gets the number of kernels per iteration.
- * Waits for that iteration to finish.  Errors: SHF_ERR_STATE before the first
- * iteration. */
-int seg_admm_kernel_times(seg_state* st, float* ms, int* nk);
+/* Instrumentation (no counterpart in the paper): time spent in each kind of
+ * kernel during the most recent iteration, measured by CUDA events recorded
+ * on the state's stream before every launch (event nodes inside the replayed
+ * graph).  ms[i] gets the milliseconds of kind i summed over its launches,
+ * launches[i] (may be NULL) their number; both need room for 8 entries.  *nk
+ * (may be NULL) gets the number of kinds.  Waits for that iteration to finish.
+ * Errors: SHF_ERR_STATE before the first iteration. */
+int seg_admm_kernel_times(seg_state* st, float* ms, int* launches, int* nk);
 
-/* Name of kernel i of an iteration, in the order of seg_admm_kernel_times
- * ("" when i is out of range). */
+/* Name of kernel kind i of seg_admm_kernel_times ("" when out of range). */
 const char* seg_admm_kernel_name(int i);
 
 /* Waits for the state's stream. */

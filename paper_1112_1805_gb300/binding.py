@@ -70,7 +70,7 @@ _SIG = {
     "seg_admm_set": (_I, [_VP, _I, _VP, _I]),
     "seg_admm_save": (_I, [_VP, ctypes.c_char_p]),
     "seg_admm_load": (_I, [_VP, ctypes.c_char_p]),
-    "seg_admm_kernel_times": (_I, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_I)]),
+    "seg_admm_kernel_times": (_I, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "seg_admm_kernel_name": (ctypes.c_char_p, [_I]),
     "seg_admm_sync": (_I, [_VP]),
     "seg_admm_destroy": (_I, [_VP]),
@@ -204,11 +204,12 @@ def seg_admm_load(state: int, path: str) -> None:
 
 
 def seg_admm_kernel_times(state: int):
-    """{kernel name: milliseconds} for the kernels of the most recent iteration."""
+    """{kernel kind: (milliseconds, launches)} for the most recent iteration."""
     ms = (ctypes.c_float * 8)()
+    nl = (_I * 8)()
     nk = _I()
-    _call("seg_admm_kernel_times", _VP(state), ms, ctypes.byref(nk))
-    return {lib().seg_admm_kernel_name(i).decode(): float(ms[i]) for i in range(nk.value)}
+    _call("seg_admm_kernel_times", _VP(state), ms, nl, ctypes.byref(nk))
+    return {lib().seg_admm_kernel_name(i).decode(): (float(ms[i]), int(nl[i])) for i in range(nk.value)}
 
 
 def seg_admm_kernel_name(i: int) -> str:

@@ -5,6 +5,7 @@
 // shf_bank.cu and shf_transform.cu.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -89,8 +90,15 @@ struct seg_state {
   int groups = 1;
   cudaGraphExec_t exec = nullptr;
   bool graph_tried = false;
-  static constexpr int kNumKernels = 5;
-  cudaEvent_t ev[kNumKernels + 1] = {};  // around each kernel of the last iteration
+  bool fast = false;          // power-of-two sizes: the shf_fast.cu kernels
+  float2* uhat = nullptr;     // fast path: 2-D spectra of u [K][H][Wh]
+  // Events recorded before every launch of an iteration (graph event nodes),
+  // with the kind of the launch that follows each.
+  static constexpr int kMaxMarks = 512;
+  cudaEvent_t ev[kMaxMarks] = {};
+  int kinds[kMaxMarks] = {};
+  int nmarks = 0;
+  bool marks_ok = true;
   long long iter = 0;
   size_t P() const { return static_cast<size_t>(g.H) * g.W; }
   size_t Ph() const { return static_cast<size_t>(g.H) * g.Wh; }
@@ -118,6 +126,7 @@ int shfilters_build(int H, int W, int J, void* stream, shf_bank** out) {
   int device = 0, optin = 0;
   SHF_CK(cudaGetDevice(&device));
   SHF_CK(shf::prepare_kernels());
+  SHF_CK(shf::prepare_fast_kernels());
   SHF_CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
   if (shf::max_dynamic_smem_needed(g, shf::kMaxK) > optin)
     return fail(SHF_ERR_SIZE, "tile does not fit in shared memory");
@@ -241,6 +250,7 @@ void free_state(seg_state* s) {
   if (s->exec) cudaGraphExecDestroy(s->exec);
   for (cudaEvent_t e : s->ev)
     if (e) cudaEventDestroy(e);
+  cudaFree(s->uhat);
   float* fl[] = {s->f, s->s, s->bv, s->w, s->bw, s->u, s->stv, s->thr, s->lam, s->gap};
   for (float* p : fl) cudaFree(p);
   cudaFree(s->Ur);
@@ -274,28 +284,49 @@ int restart(seg_state* st, const float* codebook) {
   return SHF_OK;
 }
 
-// Records an event; during stream capture it becomes an event-record node of
-// the graph (cudaEventRecordExternal), so each replay timestamps it.
-cudaError_t record(cudaEvent_t ev, cudaStream_t s) { return cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal); }
+// Records the event of the next mark; during stream capture it becomes an
+// event-record node of the graph (cudaEventRecordExternal), so that each
+// replay timestamps it.
+void mark_launch(void* ctx, int kind) {
+  auto* st = static_cast<seg_state*>(ctx);
+  if (st->nmarks >= seg_state::kMaxMarks) {
+    st->marks_ok = false;
+    return;
+  }
+  const int i = st->nmarks++;
+  st->kinds[i] = kind;
+  if (cudaEventRecordWithFlags(st->ev[i], st->stream, cudaEventRecordExternal) != cudaSuccess) st->marks_ok = false;
+}
 
-// One ADMM iteration: five kernels, with an event recorded before each and
-// after the last (event nodes inside the captured graph).
+// One ADMM iteration, with an event recorded before every launch and after
+// the last one.
 cudaError_t enqueue_iteration(seg_state* st) {
   const Geo& g = st->g;
   const float scale = 1.f / (static_cast<float>(g.H) * g.W);
   cudaStream_t s = st->stream;
-  cudaError_t e = record(st->ev[0], s);
-  if (e == cudaSuccess)
-    e = shf::run_row_ustep(g, st->T, st->s, st->w, st->bw, st->u, st->Ur, nullptr, st->K, st->gamma, scale, s);
-  if (e == cudaSuccess) e = record(st->ev[1], s);
-  if (e == cudaSuccess) e = shf::run_col_fan(g, st->Ur, st->Y, st->K, st->groups, s);
-  if (e == cudaSuccess) e = record(st->ev[2], s);
-  if (e == cudaSuccess) e = shf::run_row_shrink(g, st->Y, st->bv, st->thr, st->K * g.eta, scale, s);
-  if (e == cudaSuccess) e = record(st->ev[3], s);
-  if (e == cudaSuccess) e = shf::run_col_gather(g, st->Y, st->partial, st->K, st->groups, s);
-  if (e == cudaSuccess) e = record(st->ev[4], s);
-  if (e == cudaSuccess) e = shf::run_col_reduce_inv(g, st->partial, st->T, st->K, st->groups, s);
-  if (e == cudaSuccess) e = record(st->ev[5], s);
+  shf::LaunchHook hook;
+  hook.fn = mark_launch;
+  hook.ctx = st;
+  st->nmarks = 0;
+  st->marks_ok = true;
+  hook.mark(shf::kKindUstep);
+  cudaError_t e =
+      shf::run_row_ustep(g, st->T, st->s, st->w, st->bw, st->u, st->Ur, nullptr, st->K, st->gamma, scale, s);
+  if (st->fast) {
+    if (e == cudaSuccess)
+      e = shf::run_fast_iteration_body(g, st->Ur, st->uhat, st->Y, st->bv, st->thr, st->partial, st->T, st->K,
+                                       scale, s, hook);
+  } else {
+    hook.mark(shf::kKindFan);
+    if (e == cudaSuccess) e = shf::run_col_fan(g, st->Ur, st->Y, st->K, st->groups, s);
+    hook.mark(shf::kKindShrink);
+    if (e == cudaSuccess) e = shf::run_row_shrink(g, st->Y, st->bv, st->thr, st->K * g.eta, scale, s);
+    hook.mark(shf::kKindGather);
+    if (e == cudaSuccess) e = shf::run_col_gather(g, st->Y, st->partial, st->K, st->groups, s);
+    hook.mark(shf::kKindReduce);
+    if (e == cudaSuccess) e = shf::run_col_reduce_inv(g, st->partial, st->T, st->K, st->groups, s);
+  }
+  hook.mark(shf::kKindEnd);
   return e;
 }
 
@@ -400,6 +431,11 @@ int seg_admm_init(const shf_bank* b, const float* f, int C, const float* codeboo
   const Geo& g = st->g;
   const size_t P = st->P(), Ph = st->Ph();
   st->groups = shf::default_groups(g, K);
+  st->fast = shf::fast_path_ok(g);
+  // coefficient-spectrum scratch: the whole label set on the generic path, one
+  // wave of filters on the fast path; partial sums per filter group
+  const size_t y_planes = st->fast ? static_cast<size_t>(shf::fast_wave(g)) : static_cast<size_t>(K) * g.eta;
+  const size_t p_groups = st->fast ? static_cast<size_t>(shf::fast_groups_max(g)) : static_cast<size_t>(st->groups);
   for (cudaEvent_t& ev : st->ev) {
     cudaError_t e = cudaEventCreate(&ev);
     if (e != cudaSuccess) {
@@ -414,8 +450,9 @@ int seg_admm_init(const shf_bank* b, const float* f, int C, const float* codeboo
       (rc = dev_alloc(&st->bv, P * K * g.eta, "b_v")) || (rc = dev_alloc(&st->w, P * K, "w")) ||
       (rc = dev_alloc(&st->bw, P * K, "b_w")) || (rc = dev_alloc(&st->u, P * K, "u")) ||
       (rc = dev_alloc(&st->stv, P * K, "stv")) || (rc = dev_alloc(&st->Ur, Ph * K, "Ur")) ||
-      (rc = dev_alloc(&st->Y, Ph * K * g.eta, "Y")) ||
-      (rc = dev_alloc(&st->partial, Ph * K * st->groups, "partial")) || (rc = dev_alloc(&st->T, Ph * K, "T")) ||
+      (rc = dev_alloc(&st->Y, Ph * std::max(y_planes, static_cast<size_t>(K) * g.eta * !st->fast), "Y")) ||
+      (rc = dev_alloc(&st->partial, Ph * K * p_groups, "partial")) || (rc = dev_alloc(&st->T, Ph * K, "T")) ||
+      (st->fast && (rc = dev_alloc(&st->uhat, Ph * K, "uhat"))) ||
       (rc = dev_alloc(&st->thr, g.eta, "thr")) || (rc = dev_alloc(&st->lam, g.eta, "lam")) ||
       (rc = dev_alloc(&st->gap, P, "gap")) || (rc = dev_alloc(&st->labels, P, "labels")) ||
       (rc = dev_alloc(&st->flag, 1, "flag")) || (rc = dev_alloc(&st->red, st->red_len, "red"))) {
@@ -665,18 +702,28 @@ int seg_admm_load(seg_state* st, const char* path) {
   return SHF_OK;
 }
 
-int seg_admm_kernel_times(seg_state* st, float* ms, int* nk) {
+int seg_admm_kernel_times(seg_state* st, float* ms, int* launches, int* nk) {
   if (!st || !ms) return fail(SHF_ERR_ARG, "seg_admm_kernel_times: NULL argument");
-  if (st->iter == 0) return fail(SHF_ERR_STATE, "no iteration has run yet");
-  SHF_CK(cudaEventSynchronize(st->ev[seg_state::kNumKernels]));
-  for (int i = 0; i < seg_state::kNumKernels; ++i) SHF_CK(cudaEventElapsedTime(&ms[i], st->ev[i], st->ev[i + 1]));
-  if (nk) *nk = seg_state::kNumKernels;
+  if (st->iter == 0 || st->nmarks < 2) return fail(SHF_ERR_STATE, "no iteration has run yet");
+  if (!st->marks_ok) return fail(SHF_ERR_STATE, "iteration has more launches than timing marks");
+  for (int k = 0; k < shf::kNumKinds; ++k) {
+    ms[k] = 0.f;
+    if (launches) launches[k] = 0;
+  }
+  SHF_CK(cudaEventSynchronize(st->ev[st->nmarks - 1]));
+  for (int i = 0; i + 1 < st->nmarks; ++i) {
+    float t = 0.f;
+    SHF_CK(cudaEventElapsedTime(&t, st->ev[i], st->ev[i + 1]));
+    ms[st->kinds[i]] += t;
+    if (launches) ++launches[st->kinds[i]];
+  }
+  if (nk) *nk = shf::kNumKinds;
   return SHF_OK;
 }
 
 const char* seg_admm_kernel_name(int i) {
-  static const char* names[] = {"k_row_ustep", "k_col_fan", "k_row_shrink", "k_col_gather", "k_col_reduce_inv"};
-  return (i >= 0 && i < seg_state::kNumKernels) ? names[i] : "";
+  static const char* names[] = {"row_ustep", "col_fwd", "col_fan", "row_shrink", "col_gather", "col_reduce_inv"};
+  return (i >= 0 && i < shf::kNumKinds) ? names[i] : "";
 }
 
 int seg_admm_sync(seg_state* st) {

@@ -84,6 +84,39 @@ cudaError_t prepare_kernels();
 int max_dynamic_smem_needed(const Geo& g, int K);
 cudaError_t launch_sub(const float* a, const float* b, float* out, long n, cudaStream_t st);  // out = a - b
 
+// Kinds of kernel launches in one ADMM iteration, for per-kernel timing.
+enum KernelKind {
+  kKindUstep = 0,
+  kKindColFwd = 1,
+  kKindFan = 2,
+  kKindShrink = 3,
+  kKindGather = 4,
+  kKindReduce = 5,
+  kKindEnd = 6,
+  kNumKinds = 6
+};
+
+// Called before every launch of an iteration (and once with kKindEnd after the
+// last), so that the caller can record an event there.
+struct LaunchHook {
+  void (*fn)(void* ctx, int kind) = nullptr;
+  void* ctx = nullptr;
+  void mark(int kind) const {
+    if (fn) fn(ctx, kind);
+  }
+};
+
+// Fast path for power-of-two sizes (shf_fast.cu).
+bool fast_path_ok(const Geo& g);
+cudaError_t prepare_fast_kernels();
+int fast_wave(const Geo& g);        // filters per wave
+int fast_groups_max(const Geo& g);  // partial-sum groups per label
+// Everything of an iteration after the u/w-step: Ur (row spectra of u) -> uhat
+// -> per-filter analysis, v-step and synthesis -> T.
+cudaError_t run_fast_iteration_body(const Geo& g, const float2* Ur, float2* uhat, float2* Y, float* bv,
+                                    const float* thr, float2* partial, float2* T, int K, float scale,
+                                    cudaStream_t st, const LaunchHook& hook);
+
 // C ABI layer (shf_capi.cu): the geometry and device tables of a bank, and the
 // thread-local message behind shf_last_error() (returns code).
 void bank_geo(const shf_bank* b, Geo* g);

@@ -68,4 +68,4 @@ def test_argument_errors_without_gpu():
     with pytest.raises(B.ShearsegError) as ei:
         B.seg_admm_step(None, 1)
     assert ei.value.code == B.SHF_ERR_ARG
-    assert B.seg_admm_kernel_name(0) == "k_row_ustep" and B.seg_admm_kernel_name(99) == ""
+    assert B.seg_admm_kernel_name(0) == "row_ustep" and B.seg_admm_kernel_name(99) == ""

@@ -67,9 +67,12 @@ def test_ellipses64_full_trajectory(torch_mod, O):
 
 
 @pytest.mark.parametrize("H,W,K,J,C,T", [(48, 80, 2, 1, 1, 40), (30, 50, 5, 2, 1, 30), (40, 64, 8, 2, 3, 25),
-                                        (16, 16, 16, 1, 1, 20), (96, 96, 4, 3, 1, 15), (15, 16, 3, 1, 1, 20)])
+                                        (16, 16, 16, 1, 1, 20), (96, 96, 4, 3, 1, 15), (15, 16, 3, 1, 1, 20),
+                                        (8, 16, 3, 1, 1, 20), (32, 256, 4, 2, 1, 15), (256, 64, 3, 3, 1, 10),
+                                        (128, 128, 6, 3, 3, 10)])
 def test_edge_shapes(torch_mod, O, H, W, K, J, C, T):
-    # ragged tiles (odd H, W/2 not a multiple of the tile), K from 2 to 16, RGB.
+    # ragged tiles (odd H, W/2 not a multiple of the tile), K from 2 to 16, RGB;
+    # power-of-two shapes take the register-FFT path (8 <= H <= 1024, W <= 2048).
     rng = np.random.default_rng(H * W + K)
     if C == 1:
         cb = np.linspace(0.1, 0.9, K)[:, None]
@@ -130,6 +133,22 @@ def test_bezier512_first_iterations(torch_mod, O):
     o = O.admm_run(img32.astype(np.float64), cb.astype(np.float32).astype(np.float64), wl.J,
                    wl.Lambda().astype(np.float32).astype(np.float64), wl.gamma, T)
     g = _gpu_run(torch_mod, img32, cb, wl.J, wl.Lambda(), wl.gamma, T)
+    _check_against(o, g)
+
+
+def test_large_multiwave_first_iterations(torch_mod, O):
+    # 1024 x 1024, J = 3: the filters of a label are processed in several waves
+    # whose partial sums accumulate; first 2 iterations element by element.
+    H = W = 1024
+    K, J, T = 2, 3, 2
+    rng = np.random.default_rng(77)
+    cb = np.array([[0.3], [0.7]])
+    img, lab = synth.ellipse_image(H, W, cb, rng)
+    Lam = synth.scale_weights(0.1, J)
+    img32 = img.astype(np.float32)
+    o = O.admm_run(img32.astype(np.float64), cb.astype(np.float64), J, Lam.astype(np.float32).astype(np.float64),
+                   1.0, T)
+    g = _gpu_run(torch_mod, img32, cb, J, Lam, 1.0, T)
     _check_against(o, g)
 
 

@@ -355,11 +355,21 @@ int energy_of_w(seg_state* st, double* out_host) {
   const float scale = 1.f / (static_cast<float>(g.H) * g.W);
   // <w, s>
   SHF_CK(shf::launch_dot(st->w, st->s, static_cast<long>(P * st->K), st->red + 2, 512, st->red, st->stream));
-  // sum_f Lambda_f ||(S w)_f||_1: row-forward of w into Ur, fan-out into Y, l1 of the row-inverse.
-  SHF_CK(shf::run_row_r2c(g, st->w, st->Ur, st->K, 1.f, st->stream));
-  SHF_CK(shf::run_col_fan(g, st->Ur, st->Y, st->K, st->groups, st->stream));
+  // sum_f Lambda_f ||(S w)_f||_1: row-forward of w, fan-out over all filters,
+  // l1 of the row-inverse; the spectra of all K*eta planes go to stream-ordered
+  // temporaries (the state's scratch holds one wave of filters on the fast path).
+  const size_t ph = st->Ph();
+  float2* tmp = nullptr;
+  SHF_CK(cudaMallocAsync(reinterpret_cast<void**>(&tmp), sizeof(float2) * ph * st->K * (1 + g.eta), st->stream));
+  float2* Uw = tmp;
+  float2* Yw = tmp + ph * st->K;
+  cudaError_t e = shf::run_row_r2c(g, st->w, Uw, st->K, 1.f, st->stream);
+  if (e == cudaSuccess) e = shf::run_col_fan(g, Uw, Yw, st->K, st->groups, st->stream);
   int nb = 0;
-  SHF_CK(shf::run_row_l1(g, st->Y, st->lam, st->K * g.eta, scale, st->red + 2 + 512, &nb, st->stream));
+  if (e == cudaSuccess) e = shf::run_row_l1(g, Yw, st->lam, st->K * g.eta, scale, st->red + 2 + 512, &nb, st->stream);
+  cudaError_t e2 = cudaFreeAsync(tmp, st->stream);
+  SHF_CK(e);
+  SHF_CK(e2);
   SHF_CK(shf::launch_sum_partials(st->red + 2 + 512, nb, st->red + 1, st->stream));
   double h[2];
   SHF_CK(cudaMemcpyAsync(h, st->red, sizeof(h), cudaMemcpyDeviceToHost, st->stream));

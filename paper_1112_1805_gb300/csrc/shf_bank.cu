@@ -98,6 +98,29 @@ __global__ void k_build_bank(float* __restrict__ bank, const FilterDesc* __restr
   }
 }
 
+// Column support of each filter on the half plane: the smallest and largest
+// column index holding a non-zero value (the windows have compact support, so
+// the spectra are exactly zero elsewhere).  One block per filter.
+__global__ void k_filter_ranges(const float* __restrict__ bank, int H, int Wh, int2* __restrict__ ranges) {
+  __shared__ int lo, hi;
+  if (threadIdx.x == 0) {
+    lo = Wh;
+    hi = -1;
+  }
+  __syncthreads();
+  const float* F = bank + static_cast<size_t>(blockIdx.x) * H * Wh;
+  for (int c = threadIdx.x; c < Wh; c += blockDim.x) {
+    bool nz = false;
+    for (int r = 0; r < H && !nz; ++r) nz = F[static_cast<size_t>(r) * Wh + c] != 0.f;
+    if (nz) {
+      atomicMin(&lo, c);
+      atomicMax(&hi, c);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) ranges[blockIdx.x] = make_int2(lo, hi);
+}
+
 __global__ void k_twiddles(float2* __restrict__ tw, int N) {
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < N; m += gridDim.x * blockDim.x) {
     double s, c;
@@ -241,6 +264,7 @@ bool make_geo(int H, int W, int J, Geo* g) {
   g->twH = nullptr;
   g->twW = nullptr;
   g->bank = nullptr;
+  g->ranges = nullptr;
   return true;
 }
 
@@ -265,6 +289,11 @@ cudaError_t launch_twiddles(float2* tw, int N, cudaStream_t st) {
 cudaError_t launch_build_bank(float* bank, const Geo& g, const FilterDesc* descs_dev, cudaStream_t st) {
   const long long total = static_cast<long long>(g.eta) * g.H * g.Wh;
   k_build_bank<<<grid_for(total, 256, 152 * 16), 256, 0, st>>>(bank, descs_dev, g.H, g.W, g.Wh, g.J, g.eta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_filter_ranges(const float* bank, const Geo& g, int2* ranges, cudaStream_t st) {
+  k_filter_ranges<<<g.eta, 256, 0, st>>>(bank, g.H, g.Wh, ranges);
   return cudaGetLastError();
 }
 

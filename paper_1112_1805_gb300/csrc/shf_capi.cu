@@ -62,6 +62,7 @@ int check_sizes(int H, int W, int J) {
 struct shf_bank {
   Geo g;
   float* bank = nullptr;
+  int2* ranges = nullptr;
   float2* twH = nullptr;
   float2* twW = nullptr;
   shf::FilterDesc* descs = nullptr;
@@ -91,6 +92,7 @@ struct seg_state {
   cudaGraphExec_t exec = nullptr;
   bool graph_tried = false;
   bool fast = false;          // power-of-two sizes: the shf_fast.cu kernels
+  bool fast_ustep = false;    // ... including the u/w-step (K <= 8)
   float2* uhat = nullptr;     // fast path: 2-D spectra of u [K][H][Wh]
   // Events recorded before every launch of an iteration (graph event nodes),
   // with the kind of the launch that follows each.
@@ -137,17 +139,19 @@ int shfilters_build(int H, int W, int J, void* stream, shf_bank** out) {
   shf::filter_descs(J, d.data());
   if ((rc = dev_alloc(&b->bank, static_cast<size_t>(g.eta) * H * g.Wh, "bank")) ||
       (rc = dev_alloc(&b->twH, H, "twH")) || (rc = dev_alloc(&b->twW, W, "twW")) ||
-      (rc = dev_alloc(&b->descs, g.eta, "descs"))) {
+      (rc = dev_alloc(&b->descs, g.eta, "descs")) || (rc = dev_alloc(&b->ranges, g.eta, "ranges"))) {
     shfilters_destroy(b);
     return rc;
   }
   b->g.bank = b->bank;
+  b->g.ranges = b->ranges;
   b->g.twH = b->twH;
   b->g.twW = b->twW;
   cudaError_t e = cudaMemcpyAsync(b->descs, d.data(), sizeof(shf::FilterDesc) * g.eta, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = shf::launch_twiddles(b->twH, H, st);
   if (e == cudaSuccess) e = shf::launch_twiddles(b->twW, W, st);
   if (e == cudaSuccess) e = shf::launch_build_bank(b->bank, b->g, b->descs, st);
+  if (e == cudaSuccess) e = shf::launch_filter_ranges(b->bank, b->g, b->ranges, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // d is a host temporary
   if (e != cudaSuccess) {
     shfilters_destroy(b);
@@ -164,6 +168,7 @@ int shfilters_destroy(shf_bank* b) {
   cudaFree(b->twH);
   cudaFree(b->twW);
   cudaFree(b->descs);
+  cudaFree(b->ranges);
   delete b;
   return SHF_OK;
 }
@@ -311,7 +316,9 @@ cudaError_t enqueue_iteration(seg_state* st) {
   st->marks_ok = true;
   hook.mark(shf::kKindUstep);
   cudaError_t e =
-      shf::run_row_ustep(g, st->T, st->s, st->w, st->bw, st->u, st->Ur, nullptr, st->K, st->gamma, scale, s);
+      st->fast_ustep
+          ? shf::run_fast_ustep(g, st->T, st->s, st->w, st->bw, st->u, st->Ur, st->K, st->gamma, scale, s)
+          : shf::run_row_ustep(g, st->T, st->s, st->w, st->bw, st->u, st->Ur, nullptr, st->K, st->gamma, scale, s);
   if (st->fast) {
     if (e == cudaSuccess)
       e = shf::run_fast_iteration_body(g, st->Ur, st->uhat, st->Y, st->bv, st->thr, st->partial, st->T, st->K,
@@ -442,10 +449,13 @@ int seg_admm_init(const shf_bank* b, const float* f, int C, const float* codeboo
   const size_t P = st->P(), Ph = st->Ph();
   st->groups = shf::default_groups(g, K);
   st->fast = shf::fast_path_ok(g);
+  st->fast_ustep = shf::fast_ustep_ok(g, K);
   // coefficient-spectrum scratch: the whole label set on the generic path, one
   // wave of filters on the fast path; partial sums per filter group
   const size_t y_planes = st->fast ? static_cast<size_t>(shf::fast_wave(g)) : static_cast<size_t>(K) * g.eta;
   const size_t p_groups = st->fast ? static_cast<size_t>(shf::fast_groups_max(g)) : static_cast<size_t>(st->groups);
+  // plane size of the scratch spectra: the fast path pads rows to a pitch of 8
+  const size_t Phs = st->fast ? static_cast<size_t>(g.H) * shf::fast_pitch(g) : Ph;
   for (cudaEvent_t& ev : st->ev) {
     cudaError_t e = cudaEventCreate(&ev);
     if (e != cudaSuccess) {
@@ -460,9 +470,9 @@ int seg_admm_init(const shf_bank* b, const float* f, int C, const float* codeboo
       (rc = dev_alloc(&st->bv, P * K * g.eta, "b_v")) || (rc = dev_alloc(&st->w, P * K, "w")) ||
       (rc = dev_alloc(&st->bw, P * K, "b_w")) || (rc = dev_alloc(&st->u, P * K, "u")) ||
       (rc = dev_alloc(&st->stv, P * K, "stv")) || (rc = dev_alloc(&st->Ur, Ph * K, "Ur")) ||
-      (rc = dev_alloc(&st->Y, Ph * std::max(y_planes, static_cast<size_t>(K) * g.eta * !st->fast), "Y")) ||
-      (rc = dev_alloc(&st->partial, Ph * K * p_groups, "partial")) || (rc = dev_alloc(&st->T, Ph * K, "T")) ||
-      (st->fast && (rc = dev_alloc(&st->uhat, Ph * K, "uhat"))) ||
+      (rc = dev_alloc(&st->Y, Phs * std::max(y_planes, static_cast<size_t>(K) * g.eta * !st->fast), "Y")) ||
+      (rc = dev_alloc(&st->partial, Phs * K * p_groups, "partial")) || (rc = dev_alloc(&st->T, Ph * K, "T")) ||
+      (st->fast && (rc = dev_alloc(&st->uhat, Phs * K, "uhat"))) ||
       (rc = dev_alloc(&st->thr, g.eta, "thr")) || (rc = dev_alloc(&st->lam, g.eta, "lam")) ||
       (rc = dev_alloc(&st->gap, P, "gap")) || (rc = dev_alloc(&st->labels, P, "labels")) ||
       (rc = dev_alloc(&st->flag, 1, "flag")) || (rc = dev_alloc(&st->red, st->red_len, "red"))) {

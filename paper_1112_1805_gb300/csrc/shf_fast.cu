@@ -7,7 +7,7 @@
 //   k_fcol_fwd      Ur -> Uhat, the full 2-D spectrum of u, once per label;
 //   per label k, per wave of filters [f0, f0 + nf):
 //     k_fcol_fan      Y_f = column-inverse(W_f * Uhat_k) for f in the wave
-//     k_frow_shrink   row-inverse, g = b_v + S u, b_v <- clip(g), d = soft(g) -
+//     k_wrow_shrink   row-inverse, g = b_v + S u, b_v <- clip(g), d = soft(g) -
 //                     clip(g) (= v - b_v), row-forward of d, in place in Y_f
 //     k_fcol_gather   partial_g += sum_{f in group g} W_f * column-forward(Y_f)
 //   k_fcol_reduce_inv  T_k = column-inverse(sum_g partial_g)
@@ -20,6 +20,8 @@
 
 namespace shf {
 
+int fast_pitch(const Geo& g);
+
 namespace {
 
 using reg::kB;
@@ -30,67 +32,102 @@ __device__ __forceinline__ void load_table(float2* dst, const float2* __restrict
   for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
+// Per-pass twiddle table of a length-N transform, built by the whole CTA.
+template <int N, int TWSTEP>
+__device__ __forceinline__ void load_pass_table(float2* pt, const float2* __restrict__ tw) {
+  reg::build_pass_twiddles<N, TWSTEP>(pt, tw, threadIdx.x, blockDim.x);
+}
+
 // ---------------------------------------------------------------------------
 // Column kernels: a CTA of H threads owns 8 consecutive half-spectrum columns
-// (thread (b, tt) holds rows tt + k H/8 of column 8*blockIdx.x + b).
+// (thread (b, tt) holds rows tt + k H/8 of column 8*blockIdx.x + b).  The
+// internal spectra (uhat, Y, partial) use the row pitch Whp = Wh rounded up to
+// 8, so that each row segment of a tile is one aligned 64-byte piece; Ur and T,
+// shared with the generic kernels, use the pitch Wh.  Global operands of the
+// next filter are loaded while the current transform runs.
 // ---------------------------------------------------------------------------
 
 template <int H>
 __global__ void __launch_bounds__(H) k_fcol_fwd(const float2* __restrict__ in, float2* __restrict__ out, int Wh,
-                                                const float2* __restrict__ twH) {
+                                                int Whp, const float2* __restrict__ twH) {
   extern __shared__ float2 sm[];
-  float2* tw = sm;
-  float2* b0 = sm + H;
+  float2* tw = sm;  // per-pass twiddles
+  float2* b0 = sm + reg::Passes<H>::TWSIZE;
   float2* b1 = b0 + H * kS;
-  load_table(tw, twH, H);
-  __syncthreads();
   const int b = threadIdx.x & 7, tt = threadIdx.x >> 3;
   const int col = blockIdx.x * kB + b;
   const bool ok = col < Wh;
-  const size_t plane = static_cast<size_t>(H) * Wh * blockIdx.y;
+  const float2* src = in + static_cast<size_t>(H) * Wh * blockIdx.y + col;
   float2 v[8];
 #pragma unroll
-  for (int k = 0; k < 8; ++k)
-    v[k] = ok ? in[plane + static_cast<size_t>(tt + k * (H / 8)) * Wh + col] : make_float2(0.f, 0.f);
-  reg::fft<H, -1, 1>(v, tt, b, b0, b1, tw);
+  for (int k = 0; k < 8; ++k) v[k] = ok ? src[static_cast<size_t>(tt + k * (H / 8)) * Wh] : make_float2(0.f, 0.f);
+  load_pass_table<H, 1>(tw, twH);
+  __syncthreads();
+  reg::fft<H, -1>(v, tt, b, b0, b1, tw);
   if (ok) {
+    float2* dst = out + static_cast<size_t>(H) * Whp * blockIdx.y + col;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) out[plane + static_cast<size_t>(tt + k * (H / 8)) * Wh + col] = v[k];
+    for (int k = 0; k < 8; ++k) dst[static_cast<size_t>(tt + k * (H / 8)) * Whp] = v[k];
   }
 }
 
 template <int H>
-__global__ void __launch_bounds__(H) k_fcol_fan(const float2* __restrict__ uhat, const float* __restrict__ bank,
-                                                float2* __restrict__ Y, int Wh, int label, int f0, int nf, int fg,
+__device__ __forceinline__ void load_bank8(float (&w)[8], const float* __restrict__ wf, int Wh, int tt, int col,
+                                           bool ok) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) w[k] = ok ? __ldg(wf + static_cast<size_t>(tt + k * (H / 8)) * Wh + col) : 0.f;
+}
+
+template <int H>
+__device__ __forceinline__ void load_tile8(float2 (&v)[8], const float2* __restrict__ src, int pitch, int tt,
+                                           int col, bool ok) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    v[k] = ok ? src[static_cast<size_t>(tt + k * (H / 8)) * pitch + col] : make_float2(0.f, 0.f);
+}
+
+// Whether filter f is non-zero somewhere in column tile `tile` (8 columns).
+__device__ __forceinline__ bool covers(const int2* __restrict__ ranges, int f, int tile) {
+  const int2 r = ranges[f];
+  return r.x <= r.y && tile >= (r.x >> 3) && tile <= (r.y >> 3);
+}
+
+template <int H>
+__global__ void __launch_bounds__(H, (1024 / H > 0 ? 1024 / H : 1)) k_fcol_fan(const float2* __restrict__ uhat, const float* __restrict__ bank,
+                                                const int2* __restrict__ ranges, float2* __restrict__ Y, int Wh,
+                                                int Whp, int label, int f0, int nf, int fg,
                                                 const float2* __restrict__ twH) {
   extern __shared__ float2 sm[];
-  float2* tw = sm;
-  float2* b0 = sm + H;
+  float2* tw = sm;  // per-pass twiddles
+  float2* b0 = sm + reg::Passes<H>::TWSIZE;
   float2* b1 = b0 + H * kS;
-  load_table(tw, twH, H);
-  __syncthreads();
   const int b = threadIdx.x & 7, tt = threadIdx.x >> 3;
   const int col = blockIdx.x * kB + b;
   const bool ok = col < Wh;
-  const size_t P = static_cast<size_t>(H) * Wh;
-  float2 u[8];
-#pragma unroll
-  for (int k = 0; k < 8; ++k)
-    u[k] = ok ? uhat[P * label + static_cast<size_t>(tt + k * (H / 8)) * Wh + col] : make_float2(0.f, 0.f);
+  const size_t Pb = static_cast<size_t>(H) * Wh, Pp = static_cast<size_t>(H) * Whp;
   const int fb = blockIdx.y * fg, fe = min(nf, fb + fg);
+  float2 u[8];
+  float w[8];
+  load_tile8<H>(u, uhat + Pp * label, Whp, tt, col, ok);
+  load_bank8<H>(w, bank + Pb * (f0 + fb), Wh, tt, col, ok);
+  load_pass_table<H, 1>(tw, twH);
+  __syncthreads();
   for (int fl = fb; fl < fe; ++fl) {
-    const float* wf = bank + P * (f0 + fl);
+    // filters are exactly zero outside their column support: Y_f is only
+    // produced (and later read) on the tiles the support touches
+    if (!covers(ranges, f0 + fl, blockIdx.x)) {
+      if (fl + 1 < fe) load_bank8<H>(w, bank + Pb * (f0 + fl + 1), Wh, tt, col, ok);
+      continue;
+    }
     float2 v[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const float w = ok ? __ldg(wf + static_cast<size_t>(tt + k * (H / 8)) * Wh + col) : 0.f;
-      v[k] = c_scale(u[k], w);
-    }
-    reg::fft<H, +1, 1>(v, tt, b, b0, b1, tw);
+    for (int k = 0; k < 8; ++k) v[k] = c_scale(u[k], w[k]);
+    if (fl + 1 < fe) load_bank8<H>(w, bank + Pb * (f0 + fl + 1), Wh, tt, col, ok);
+    reg::fft<H, +1>(v, tt, b, b0, b1, tw);
     if (ok) {
-      float2* dst = Y + P * fl;
+      float2* dst = Y + Pp * fl + col;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) dst[static_cast<size_t>(tt + k * (H / 8)) * Wh + col] = v[k];
+      for (int k = 0; k < 8; ++k) dst[static_cast<size_t>(tt + k * (H / 8)) * Whp] = v[k];
     }
   }
 }
@@ -98,43 +135,52 @@ __global__ void __launch_bounds__(H) k_fcol_fan(const float2* __restrict__ uhat,
 // partial[g][label] (+)= sum over the group's filters of W_f * column-forward(Y_f);
 // accumulate != 0 adds to what an earlier wave left there.
 template <int H>
-__global__ void __launch_bounds__(H) k_fcol_gather(const float2* __restrict__ Y, const float* __restrict__ bank,
-                                                   float2* __restrict__ partial, int Wh, int K, int label, int f0,
-                                                   int nf, int fg, int accumulate, const float2* __restrict__ twH) {
+__global__ void __launch_bounds__(H, (1024 / H > 0 ? 1024 / H : 1)) k_fcol_gather(const float2* __restrict__ Y, const float* __restrict__ bank,
+                                                   const int2* __restrict__ ranges, float2* __restrict__ partial,
+                                                   int Wh, int Whp, int K, int label, int f0, int nf, int fg,
+                                                   int accumulate, const float2* __restrict__ twH) {
   extern __shared__ float2 sm[];
-  float2* tw = sm;
-  float2* b0 = sm + H;
+  float2* tw = sm;  // per-pass twiddles
+  float2* b0 = sm + reg::Passes<H>::TWSIZE;
   float2* b1 = b0 + H * kS;
-  load_table(tw, twH, H);
-  __syncthreads();
   const int b = threadIdx.x & 7, tt = threadIdx.x >> 3;
   const int col = blockIdx.x * kB + b;
   const bool ok = col < Wh;
-  const size_t P = static_cast<size_t>(H) * Wh;
-  float2 acc[8];
+  const size_t Pb = static_cast<size_t>(H) * Wh, Pp = static_cast<size_t>(H) * Whp;
+  const int fb = blockIdx.y * fg, fe = min(nf, fb + fg);
+  float2 acc[8], y[8];
+  float w[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) acc[k] = make_float2(0.f, 0.f);
-  const int fb = blockIdx.y * fg, fe = min(nf, fb + fg);
-  for (int fl = fb; fl < fe; ++fl) {
-    const float2* src = Y + P * fl;
+  // only the filters whose support touches this tile contribute
+  auto next_active = [&](int f) {
+    while (f < fe && !covers(ranges, f0 + f, blockIdx.x)) ++f;
+    return f;
+  };
+  int fl = next_active(fb);
+  if (fl < fe) load_tile8<H>(y, Y + Pp * fl, Whp, tt, col, ok);
+  load_pass_table<H, 1>(tw, twH);
+  __syncthreads();
+  while (fl < fe) {
     float2 v[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
-      v[k] = ok ? src[static_cast<size_t>(tt + k * (H / 8)) * Wh + col] : make_float2(0.f, 0.f);
-    reg::fft<H, -1, 1>(v, tt, b, b0, b1, tw);
-    const float* wf = bank + P * (f0 + fl);
+    for (int k = 0; k < 8; ++k) v[k] = y[k];
+    load_bank8<H>(w, bank + Pb * (f0 + fl), Wh, tt, col, ok);
+    const int fn = next_active(fl + 1);
+    if (fn < fe) load_tile8<H>(y, Y + Pp * fn, Whp, tt, col, ok);
+    reg::fft<H, -1>(v, tt, b, b0, b1, tw);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const float w = ok ? __ldg(wf + static_cast<size_t>(tt + k * (H / 8)) * Wh + col) : 0.f;
-      acc[k].x = fmaf(w, v[k].x, acc[k].x);
-      acc[k].y = fmaf(w, v[k].y, acc[k].y);
+      acc[k].x = fmaf(w[k], v[k].x, acc[k].x);
+      acc[k].y = fmaf(w[k], v[k].y, acc[k].y);
     }
+    fl = fn;
   }
   if (ok) {
-    float2* dst = partial + P * (static_cast<size_t>(blockIdx.y) * K + label);
+    float2* dst = partial + Pp * (static_cast<size_t>(blockIdx.y) * K + label) + col;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const size_t off = static_cast<size_t>(tt + k * (H / 8)) * Wh + col;
+      const size_t off = static_cast<size_t>(tt + k * (H / 8)) * Whp;
       dst[off] = accumulate ? c_add(dst[off], acc[k]) : acc[k];
     }
   }
@@ -142,32 +188,34 @@ __global__ void __launch_bounds__(H) k_fcol_gather(const float2* __restrict__ Y,
 
 template <int H>
 __global__ void __launch_bounds__(H) k_fcol_reduce_inv(const float2* __restrict__ partial, float2* __restrict__ T,
-                                                       int Wh, int K, int groups, const float2* __restrict__ twH) {
+                                                       int Wh, int Whp, int K, int groups,
+                                                       const float2* __restrict__ twH) {
   extern __shared__ float2 sm[];
-  float2* tw = sm;
-  float2* b0 = sm + H;
+  float2* tw = sm;  // per-pass twiddles
+  float2* b0 = sm + reg::Passes<H>::TWSIZE;
   float2* b1 = b0 + H * kS;
-  load_table(tw, twH, H);
-  __syncthreads();
   const int b = threadIdx.x & 7, tt = threadIdx.x >> 3;
   const int col = blockIdx.x * kB + b;
   const bool ok = col < Wh;
-  const size_t P = static_cast<size_t>(H) * Wh;
+  const size_t Pp = static_cast<size_t>(H) * Whp;
   const int label = blockIdx.y;
   float2 v[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) v[k] = make_float2(0.f, 0.f);
   if (ok) {
     for (int g = 0; g < groups; ++g) {  // fixed order over the groups
-      const float2* src = partial + P * (static_cast<size_t>(g) * K + label) + col;
+      const float2* src = partial + Pp * (static_cast<size_t>(g) * K + label) + col;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) v[k] = c_add(v[k], src[static_cast<size_t>(tt + k * (H / 8)) * Wh]);
+      for (int k = 0; k < 8; ++k) v[k] = c_add(v[k], src[static_cast<size_t>(tt + k * (H / 8)) * Whp]);
     }
   }
-  reg::fft<H, +1, 1>(v, tt, b, b0, b1, tw);
+  load_pass_table<H, 1>(tw, twH);
+  __syncthreads();
+  reg::fft<H, +1>(v, tt, b, b0, b1, tw);
   if (ok) {
+    float2* dst = T + static_cast<size_t>(H) * Wh * label + col;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) T[P * label + static_cast<size_t>(tt + k * (H / 8)) * Wh + col] = v[k];
+    for (int k = 0; k < 8; ++k) dst[static_cast<size_t>(tt + k * (H / 8)) * Wh] = v[k];
   }
 }
 
@@ -179,82 +227,249 @@ __global__ void __launch_bounds__(H) k_fcol_reduce_inv(const float2* __restrict_
 // v-step and b_v update of Sec. 3 on rows of (S u)_f: g = b_v + c,
 // b_v <- clip(g, -t, t), d = soft(g, t) - clip(g, -t, t) = g - 2 clip(g);
 // d (= v - b_v of the new iterate) is transformed back in place.
+// One row per group of T = L/8 threads (a warp for L = 256): the row's
+// exchanges need only the group's barrier, and its global accesses are
+// contiguous row segments.  The thread's b_v values are requested first, so
+// that their DRAM latency overlaps the staging and the inverse transform.
 template <int L>
-__global__ void __launch_bounds__(L) k_frow_shrink(float2* __restrict__ Y, float* __restrict__ bv,
-                                                   const float* __restrict__ thr, int H, int eta, int label, int f0,
-                                                   float scale, const float2* __restrict__ twW) {
-  constexpr int Wh = L + 1;
+__global__ void __launch_bounds__(256) k_wrow_shrink(float2* __restrict__ Y, float* __restrict__ bv,
+                                                     const float* __restrict__ thr,
+                                                     const int2* __restrict__ ranges, int H, int Whp, int eta,
+                                                     int label, int f0, float scale,
+                                                     const float2* __restrict__ twW) {
+  constexpr int T = L / 8;
+  constexpr int RPC = 256 / T;  // rows per CTA
+  constexpr int BUF = L + 16;
   extern __shared__ float2 sm[];
-  float2* tw = sm;                 // 2L entries: exp(-2 pi i m / W)
-  float2* b0 = sm + 2 * L;         // L * kS
-  float2* b1 = b0 + L * kS;        // (L + 1) * kS, also the staging buffer
-  load_table(tw, twW, 2 * L);
-  const int row0 = blockIdx.x * kB;
-  const int fl = blockIdx.y;
-  float2* X = Y + static_cast<size_t>(H) * Wh * fl;
-  // stage the 8 half-spectrum rows, index-fast (coalesced, conflict-free)
-  for (int e = threadIdx.x; e < kB * Wh; e += L) {
-    const int r = e / Wh, i = e - r * Wh, row = row0 + r;
-    b1[sidx(i, r)] = row < H ? X[static_cast<size_t>(row) * Wh + i] : make_float2(0.f, 0.f);
-  }
+  float2* tw = sm;                                   // exp(-2 pi i m / W), m <= L
+  float2* pt = tw + (L + 1);                         // per-pass twiddles of the length-L transform
+  const int grp = threadIdx.x / T, tt = threadIdx.x % T;
+  float2* b0 = pt + reg::Passes<L>::TWSIZE + grp * 2 * BUF;
+  float2* b1 = b0 + BUF;
+  const int bar = 1 + grp;
+  const int row = blockIdx.x * RPC + grp;
+  const bool live = row < H;
+  const int fl = blockIdx.y, f = f0 + fl;
+  float2* b2 = reinterpret_cast<float2*>(bv) + ((static_cast<size_t>(label) * eta + f) * H + (live ? row : 0)) * L;
+  float2 bo[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) bo[k] = live ? __ldcs(b2 + tt + k * T) : make_float2(0.f, 0.f);
+  const float th = thr[f];
+  // the row spectrum is zero outside the filter's column tiles [c0, c1]
+  const int2 rg = ranges[f];
+  const int c0 = rg.x <= rg.y ? (rg.x & ~7) : L + 1;
+  const int c1 = rg.x <= rg.y ? min(L, (rg.y | 7)) : -1;
+  float2* X = Y + static_cast<size_t>(H) * Whp * fl + static_cast<size_t>(live ? row : 0) * Whp;
+  for (int i = tt; i <= L; i += T)
+    b1[reg::ridx(i)] = (live && i >= c0 && i <= c1) ? X[i] : make_float2(0.f, 0.f);
+  load_table(tw, twW, L + 1);
+  reg::build_pass_twiddles<L, 2>(pt, twW, threadIdx.x, blockDim.x);
   __syncthreads();
-  const int b = threadIdx.x & 7, tt = threadIdx.x >> 3;
   float2 v[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) {  // inverse packing Z[n] = (X_n + conj X_{L-n}) + i e^{+2 pi i n/W} (X_n - conj X_{L-n})
-    const int n = tt + k * (L / 8);
-    const float2 a = b1[sidx(n, b)];
-    const float2 c = c_conj(b1[sidx(L - n, b)]);
+    const int n = tt + k * T;
+    const float2 a = b1[reg::ridx(n)];
+    const float2 c = c_conj(b1[reg::ridx(L - n)]);
     const float2 s = c_add(a, c), d = c_sub(a, c);
     const float2 t = c_mul(c_conj(tw[n]), d);
     v[k] = make_float2(s.x - t.y, s.y + t.x);
   }
-  reg::fft<L, +1, 2>(v, tt, b, b0, b1, tw);
-  const int row = row0 + b;
-  const int f = f0 + fl;
-  const float th = thr[f];
-  if (row < H) {
-    float2* b2 = reinterpret_cast<float2*>(bv) + (static_cast<size_t>(label) * eta + f) * H * L +
-                 static_cast<size_t>(row) * L;
+  reg::row_fft<L, +1>(v, tt, b0, b1, pt, bar);
+  if (live) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const int n = tt + k * (L / 8);
-      const float2 bo = __ldcs(b2 + n);
-      const float gx = fmaf(scale, v[k].x, bo.x), gy = fmaf(scale, v[k].y, bo.y);
+      const float gx = fmaf(scale, v[k].x, bo[k].x), gy = fmaf(scale, v[k].y, bo[k].y);
       const float cx = fminf(fmaxf(gx, -th), th), cy = fminf(fmaxf(gy, -th), th);
-      __stcs(b2 + n, make_float2(cx, cy));
+      __stcs(b2 + tt + k * T, make_float2(cx, cy));
       v[k] = make_float2(gx - 2.f * cx, gy - 2.f * cy);
     }
   } else {
 #pragma unroll
     for (int k = 0; k < 8; ++k) v[k] = make_float2(0.f, 0.f);
   }
-  reg::fft<L, -1, 2>(v, tt, b, b0, b1, tw);
-  __syncthreads();  // the last pass may still read b1
+  reg::row_fft<L, -1>(v, tt, b0, b1, pt, bar);
+  reg::group_sync<T>(bar);  // the last pass may still read b1
 #pragma unroll
-  for (int k = 0; k < 8; ++k) b1[sidx(tt + k * (L / 8), b)] = v[k];
-  __syncthreads();
+  for (int k = 0; k < 8; ++k) b1[reg::ridx(tt + k * T)] = v[k];
+  reg::group_sync<T>(bar);
   // forward unpacking X[k] = 1/2 [(Z_k + conj Z_{L-k}) - i e^{-2 pi i k/W} (Z_k - conj Z_{L-k})]
-  for (int e = threadIdx.x; e < kB * Wh; e += L) {
-    const int r = e / Wh, i = e - r * Wh, rw = row0 + r;
-    if (rw < H) {
-      const float2 a = b1[sidx(i == L ? 0 : i, r)];
-      const float2 c = c_conj(b1[sidx(i == 0 ? 0 : L - i, r)]);
+  if (live) {
+    for (int i = c0 + tt; i <= c1; i += T) {
+      const float2 a = b1[reg::ridx(i == L ? 0 : i)];
+      const float2 c = c_conj(b1[reg::ridx(i == 0 ? 0 : L - i)]);
       const float2 s = c_add(a, c), d = c_sub(a, c);
       const float2 t = c_mul(tw[i], d);
-      X[static_cast<size_t>(rw) * Wh + i] = make_float2(0.5f * (s.x + t.y), 0.5f * (s.y - t.x));
+      X[i] = make_float2(0.5f * (s.x + t.y), 0.5f * (s.y - t.x));
     }
   }
 }
 
+// Euclidean projection of g[0..K) onto the unit simplex, as the paper
+// constructs it: project onto the hyperplane sum = 1 (g + (1 - sum g)/q), set
+// the negative components to zero and repeat on the remaining ones (at most K
+// passes; the result is exact).
+template <int KMAX>
+__device__ __forceinline__ void simplex_project(float (&g)[KMAX], int K) {
+  unsigned act = (1u << K) - 1u;
+  float tau = 0.f;
+  for (int pass = 0; pass < K; ++pass) {
+    float sum = 0.f;
+    int q = 0;
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k)
+      if ((act >> k) & 1u) {
+        sum += g[k];
+        ++q;
+      }
+    tau = (sum - 1.f) / static_cast<float>(q);
+    unsigned nact = act;
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k)
+      if (((act >> k) & 1u) && g[k] - tau < 0.f) nact &= ~(1u << k);
+    if (nact == act) break;
+    act = nact;
+  }
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) g[k] = ((act >> k) & 1u) ? g[k] - tau : 0.f;
+}
+
+// u-step (u = 1/2 [S^T(v - b_v) + (w - b_w) - gamma s], A^T A = 2I), w-step
+// (pixelwise simplex projection of g_w = b_w + u), b_w = g_w - w, and the row
+// spectra of u for the next analysis.  One row per group of L/8 threads, all
+// K labels; the carried values of a thread live in its private slots of U.
+template <int L, int KMAX>
+__global__ void __launch_bounds__(256) k_wrow_ustep(const float2* __restrict__ Tsp, const float* __restrict__ s,
+                                                    float* __restrict__ w, float* __restrict__ bw,
+                                                    float* __restrict__ u, float2* __restrict__ Ur, int K, int H,
+                                                    float scale, float gamma, const float2* __restrict__ twW) {
+  constexpr int T = L / 8;
+  constexpr int RPC = 256 / T;
+  constexpr int BUF = L + 16;
+  constexpr int Wh = L + 1;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* pt = tw + (L + 1);
+  const int grp = threadIdx.x / T, tt = threadIdx.x % T;
+  float2* b0 = pt + reg::Passes<L>::TWSIZE + grp * 2 * BUF;
+  float2* b1 = b0 + BUF;
+  float2* U = pt + reg::Passes<L>::TWSIZE + RPC * 2 * BUF;  // [k][e][thread]
+  const int bar = 1 + grp;
+  const int row = blockIdx.x * RPC + grp;
+  const bool live = row < H;
+  const int rowc = live ? row : 0;
+  const size_t HL = static_cast<size_t>(H) * L, HWh = static_cast<size_t>(H) * Wh;
+  auto slot = [&](int k, int e) { return (k * 8 + e) * 256 + threadIdx.x; };
+  load_table(tw, twW, L + 1);
+  reg::build_pass_twiddles<L, 2>(pt, twW, threadIdx.x, blockDim.x);
+  __syncthreads();
+  // S^T(v - b_v) on this row, label by label
+  for (int k = 0; k < K; ++k) {
+    reg::group_sync<T>(bar);  // the previous label's transform may still read b1
+    const float2* X = Tsp + HWh * k + static_cast<size_t>(rowc) * Wh;
+    for (int i = tt; i <= L; i += T) b1[reg::ridx(i)] = live ? X[i] : make_float2(0.f, 0.f);
+    reg::group_sync<T>(bar);
+    float2 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int n = tt + e * T;
+      const float2 a = b1[reg::ridx(n)];
+      const float2 c = c_conj(b1[reg::ridx(L - n)]);
+      const float2 sm2 = c_add(a, c), d = c_sub(a, c);
+      const float2 t = c_mul(c_conj(tw[n]), d);
+      v[e] = make_float2(sm2.x - t.y, sm2.y + t.x);
+    }
+    reg::row_fft<L, +1>(v, tt, b0, b1, pt, bar);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) U[slot(k, e)] = c_scale(v[e], scale);
+  }
+  // pointwise u-step, projection and b_w update (two pixels per slot)
+  if (live) {
+    const float2* s2 = reinterpret_cast<const float2*>(s) + static_cast<size_t>(row) * L;
+    float2* w2 = reinterpret_cast<float2*>(w) + static_cast<size_t>(row) * L;
+    float2* bw2 = reinterpret_cast<float2*>(bw) + static_cast<size_t>(row) * L;
+    float2* u2 = reinterpret_cast<float2*>(u) + static_cast<size_t>(row) * L;
+    const float hg = 0.5f * gamma;
+#pragma unroll 1
+    for (int e = 0; e < 8; ++e) {
+      const int n = tt + e * T;
+      float gx[KMAX], gy[KMAX];
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k) {
+        gx[k] = 0.f;
+        gy[k] = 0.f;
+        if (k < K) {
+          const float2 st = U[slot(k, e)];
+          const float2 wv = w2[HL * k + n], bv = bw2[HL * k + n], sv = s2[HL * k + n];
+          const float ux = 0.5f * (st.x + (wv.x - bv.x)) - hg * sv.x;
+          const float uy = 0.5f * (st.y + (wv.y - bv.y)) - hg * sv.y;
+          u2[HL * k + n] = make_float2(ux, uy);
+          U[slot(k, e)] = make_float2(ux, uy);
+          gx[k] = bv.x + ux;
+          gy[k] = bv.y + uy;
+        }
+      }
+      float px[KMAX], py[KMAX];
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k) {
+        px[k] = gx[k];
+        py[k] = gy[k];
+      }
+      simplex_project<KMAX>(px, K);
+      simplex_project<KMAX>(py, K);
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+        if (k < K) {
+          w2[HL * k + n] = make_float2(px[k], py[k]);
+          bw2[HL * k + n] = make_float2(gx[k] - px[k], gy[k] - py[k]);
+        }
+    }
+  } else {
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int e = 0; e < 8; ++e) U[slot(k, e)] = make_float2(0.f, 0.f);
+  }
+  // row spectra of u
+  for (int k = 0; k < K; ++k) {
+    float2 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = U[slot(k, e)];
+    reg::row_fft<L, -1>(v, tt, b0, b1, pt, bar);
+    reg::group_sync<T>(bar);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) b1[reg::ridx(tt + e * T)] = v[e];
+    reg::group_sync<T>(bar);
+    if (live) {
+      float2* X = Ur + HWh * k + static_cast<size_t>(row) * Wh;
+      for (int i = tt; i <= L; i += T) {
+        const float2 a = b1[reg::ridx(i == L ? 0 : i)];
+        const float2 c = c_conj(b1[reg::ridx(i == 0 ? 0 : L - i)]);
+        const float2 sm2 = c_add(a, c), d = c_sub(a, c);
+        const float2 t = c_mul(tw[i], d);
+        X[i] = make_float2(0.5f * (sm2.x + t.y), 0.5f * (sm2.y - t.x));
+      }
+    }
+  }
+}
+
+template <int L>
+size_t ustep_smem(int K) {
+  return sizeof(float2) * ((L + 1) + reg::Passes<L>::TWSIZE + (256 / (L / 8)) * 2 * (L + 16) + K * 8 * 256);
+}
+
 template <int N>
 size_t col_smem() {
-  return sizeof(float2) * (N + 2 * N * kS);
+  return sizeof(float2) * (reg::Passes<N>::TWSIZE + 2 * N * kS);
 }
 
 template <int L>
 size_t row_smem() {
-  return sizeof(float2) * (2 * L + L * kS + (L + 1) * kS);
+  return sizeof(float2) * ((L + 1) + reg::Passes<L>::TWSIZE + (256 / (L / 8)) * 2 * (L + 16));
+}
+
+template <int L>
+int row_rows_per_cta() {
+  return 256 / (L / 8);
 }
 
 int groups_for(const Geo& g, int nf) {
@@ -273,6 +488,7 @@ cudaError_t per_filter_waves(const Geo& g, const float2* uhat, float2* Y, float*
                              float2* partial, int K, int wave, float scale, cudaStream_t st, const LaunchHook& hook,
                              int* groups_out) {
   const int ntiles = (g.Wh + kB - 1) / kB;
+  const int Whp = fast_pitch(g);
   const int fg = groups_for(g, wave);
   int groups = 0;
   for (int label = 0; label < K; ++label) {
@@ -280,13 +496,14 @@ cudaError_t per_filter_waves(const Geo& g, const float2* uhat, float2* Y, float*
       const int nf = min(wave, g.eta - f0);
       const int ng = (nf + fg - 1) / fg;
       hook.mark(kKindFan);
-      k_fcol_fan<H><<<dim3(ntiles, ng), H, col_smem<H>(), st>>>(uhat, g.bank, Y, g.Wh, label, f0, nf, fg, g.twH);
+      k_fcol_fan<H><<<dim3(ntiles, ng), H, col_smem<H>(), st>>>(uhat, g.bank, g.ranges, Y, g.Wh, Whp, label, f0,
+                                                                nf, fg, g.twH);
       hook.mark(kKindShrink);
-      k_frow_shrink<L><<<dim3((g.H + kB - 1) / kB, nf), L, row_smem<L>(), st>>>(Y, bv, thr, g.H, g.eta, label, f0,
-                                                                                scale, g.twW);
+      k_wrow_shrink<L><<<dim3((g.H + row_rows_per_cta<L>() - 1) / row_rows_per_cta<L>(), nf), 256, row_smem<L>(),
+                         st>>>(Y, bv, thr, g.ranges, g.H, Whp, g.eta, label, f0, scale, g.twW);
       hook.mark(kKindGather);
-      k_fcol_gather<H><<<dim3(ntiles, ng), H, col_smem<H>(), st>>>(Y, g.bank, partial, g.Wh, K, label, f0, nf, fg,
-                                                                   f0 > 0 ? 1 : 0, g.twH);
+      k_fcol_gather<H><<<dim3(ntiles, ng), H, col_smem<H>(), st>>>(Y, g.bank, g.ranges, partial, g.Wh, Whp, K,
+                                                                   label, f0, nf, fg, f0 > 0 ? 1 : 0, g.twH);
       if (ng > groups) groups = ng;
     }
   }
@@ -299,13 +516,14 @@ cudaError_t iteration_body(const Geo& g, const float2* Ur, float2* uhat, float2*
                            float2* partial, float2* T, int K, int wave, float scale, cudaStream_t st,
                            const LaunchHook& hook) {
   const int ntiles = (g.Wh + kB - 1) / kB;
+  const int Whp = fast_pitch(g);
   hook.mark(kKindColFwd);
-  k_fcol_fwd<H><<<dim3(ntiles, K), H, col_smem<H>(), st>>>(Ur, uhat, g.Wh, g.twH);
+  k_fcol_fwd<H><<<dim3(ntiles, K), H, col_smem<H>(), st>>>(Ur, uhat, g.Wh, Whp, g.twH);
   int groups = 0;
   cudaError_t e = per_filter_waves<H, L>(g, uhat, Y, bv, thr, partial, K, wave, scale, st, hook, &groups);
   if (e != cudaSuccess) return e;
   hook.mark(kKindReduce);
-  k_fcol_reduce_inv<H><<<dim3(ntiles, K), H, col_smem<H>(), st>>>(partial, T, g.Wh, K, groups, g.twH);
+  k_fcol_reduce_inv<H><<<dim3(ntiles, K), H, col_smem<H>(), st>>>(partial, T, g.Wh, Whp, K, groups, g.twH);
   return cudaGetLastError();
 }
 
@@ -326,7 +544,22 @@ cudaError_t prepare_col() {
 
 template <int L>
 cudaError_t prepare_row() {
-  return allow_smem(k_frow_shrink<L>, row_smem<L>());
+  cudaError_t e = allow_smem(k_wrow_shrink<L>, row_smem<L>());
+  if (e == cudaSuccess) e = allow_smem(k_wrow_ustep<L, 4>, ustep_smem<L>(4));
+  if (e == cudaSuccess) e = allow_smem(k_wrow_ustep<L, 8>, ustep_smem<L>(8));
+  return e;
+}
+
+template <int L>
+cudaError_t ustep_launch(const Geo& g, const float2* T, const float* s, float* w, float* bw, float* u, float2* Ur,
+                         int K, float gamma, float scale, cudaStream_t st) {
+  constexpr int RPC = 256 / (L / 8);
+  const dim3 grid((g.H + RPC - 1) / RPC);
+  if (K <= 4)
+    k_wrow_ustep<L, 4><<<grid, 256, ustep_smem<L>(K), st>>>(T, s, w, bw, u, Ur, K, g.H, scale, gamma, g.twW);
+  else
+    k_wrow_ustep<L, 8><<<grid, 256, ustep_smem<L>(K), st>>>(T, s, w, bw, u, Ur, K, g.H, scale, gamma, g.twW);
+  return cudaGetLastError();
 }
 
 template <int H>
@@ -350,6 +583,43 @@ bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 }  // namespace
 
+int fast_pitch(const Geo& g) { return (g.Wh + 7) & ~7; }
+
+bool fast_ustep_ok(const Geo& g, int K) {
+  if (!fast_path_ok(g) || K > 8) return false;
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+  size_t need = 0;
+  switch (g.L) {
+    case 8: need = ustep_smem<8>(K); break;
+    case 16: need = ustep_smem<16>(K); break;
+    case 32: need = ustep_smem<32>(K); break;
+    case 64: need = ustep_smem<64>(K); break;
+    case 128: need = ustep_smem<128>(K); break;
+    case 256: need = ustep_smem<256>(K); break;
+    case 512: need = ustep_smem<512>(K); break;
+    case 1024: need = ustep_smem<1024>(K); break;
+    default: return false;
+  }
+  return need <= static_cast<size_t>(optin);
+}
+
+cudaError_t run_fast_ustep(const Geo& g, const float2* T, const float* s, float* w, float* bw, float* u, float2* Ur,
+                           int K, float gamma, float scale, cudaStream_t st) {
+  switch (g.L) {
+    case 8: return ustep_launch<8>(g, T, s, w, bw, u, Ur, K, gamma, scale, st);
+    case 16: return ustep_launch<16>(g, T, s, w, bw, u, Ur, K, gamma, scale, st);
+    case 32: return ustep_launch<32>(g, T, s, w, bw, u, Ur, K, gamma, scale, st);
+    case 64: return ustep_launch<64>(g, T, s, w, bw, u, Ur, K, gamma, scale, st);
+    case 128: return ustep_launch<128>(g, T, s, w, bw, u, Ur, K, gamma, scale, st);
+    case 256: return ustep_launch<256>(g, T, s, w, bw, u, Ur, K, gamma, scale, st);
+    case 512: return ustep_launch<512>(g, T, s, w, bw, u, Ur, K, gamma, scale, st);
+    case 1024: return ustep_launch<1024>(g, T, s, w, bw, u, Ur, K, gamma, scale, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 bool fast_path_ok(const Geo& g) {
   return pow2(g.H) && pow2(g.L) && g.H >= 8 && g.H <= 1024 && g.L >= 8 && g.L <= 1024;
 }
@@ -366,7 +636,7 @@ cudaError_t prepare_fast_kernels() {
 
 int fast_wave(const Geo& g) {
   // filters per wave: keep the wave's coefficient spectra near 32 MiB
-  const size_t plane = sizeof(float2) * static_cast<size_t>(g.H) * g.Wh;
+  const size_t plane = sizeof(float2) * static_cast<size_t>(g.H) * fast_pitch(g);
   int w = static_cast<int>((size_t(32) << 20) / plane);
   if (w < 1) w = 1;
   if (w > g.eta) w = g.eta;

@@ -7,9 +7,10 @@
 // passes the values go through shared memory at their Stockham positions,
 // double-buffered so that one barrier per exchange suffices.  The result is
 // again in the stride layout, in natural order.  Shared memory rows hold the
-// 8 batch members of one index with a stride of kS = 9 float2, so both the
-// batch-fast exchanges and index-fast staging from global memory are free of
-// bank conflicts (up to one two-way conflict in some exchanges).
+// 8 batch members of one index (64 bytes); row i is stored at row
+// i ^ ((i >> 3) & 1), so that the stride-layout reads, the Stockham writes of
+// every pass and batch-fast staging all touch each bank exactly twice per
+// warp (the minimum for 8-byte accesses).
 #pragma once
 
 #include "shf_fft.cuh"
@@ -18,11 +19,11 @@ namespace shf {
 namespace reg {
 
 constexpr int kB = 8;
-constexpr int kS = kB + 1;
+constexpr int kS = kB;  // float2 per shared-memory row
 
 __host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
 
-__host__ __device__ __forceinline__ int sidx(int i, int b) { return i * kS + b; }
+__host__ __device__ __forceinline__ int sidx(int i, int b) { return (i ^ ((i >> 3) & 1)) * kS + b; }
 
 // exp(S 2 pi i m / Ntab) from the table tw[m] = exp(-2 pi i m / Ntab).
 template <int S>
@@ -34,9 +35,10 @@ __host__ __device__ __forceinline__ float2 twid(const float2* tw, int m) {
 
 // Butterflies of one pass of radix R with span Ns for thread tt (8/R
 // butterflies per thread).  Input v in the stride layout; on return v[m +
-// q (8/R)] holds output q of butterfly m.  tw has N*TWSTEP entries.
-template <int N, int R, int S, int TWSTEP>
-__host__ __device__ __forceinline__ void pass_bfly(float2 (&v)[8], int tt, int Ns, const float2* tw) {
+// q (8/R)] holds output q of butterfly m.  pt is this pass's part of the
+// per-pass twiddle table.
+template <int N, int R, int S>
+__host__ __device__ __forceinline__ void pass_bfly(float2 (&v)[8], int tt, int Ns, const float2* pt) {
   constexpr int M = 8 / R;
 #pragma unroll
   for (int m = 0; m < M; ++m) {
@@ -45,9 +47,9 @@ __host__ __device__ __forceinline__ void pass_bfly(float2 (&v)[8], int tt, int N
 #pragma unroll
     for (int t = 0; t < R; ++t) x[t] = v[m + t * M];
     if (Ns > 1) {
-      const int step = (j & (Ns - 1)) * (N / (Ns * R)) * TWSTEP;
+      const int k = j & (Ns - 1);
 #pragma unroll
-      for (int t = 1; t < R; ++t) x[t] = c_mul(x[t], twid<S>(tw, t * step));
+      for (int t = 1; t < R; ++t) x[t] = c_mul(x[t], twid<S>(pt, (t - 1) * Ns + k));
     }
     dft_small<R, S>(x);
 #pragma unroll
@@ -81,42 +83,133 @@ struct Passes {
   static constexpr int REM = 1 << (LG % 3);
   static constexpr int NPASS = P8 + (REM > 1 ? 1 : 0);
   __host__ __device__ static constexpr int radix(int p) { return p < P8 ? 8 : REM; }
+  __host__ __device__ static constexpr int span(int p) { return p == 0 ? 1 : span(p - 1) * radix(p - 1); }
+  // offset of pass p's twiddles in the per-pass table: pass p (>= 1) holds
+  // (radix - 1) * span entries, [t - 1][j mod span]
+  __host__ __device__ static constexpr int twoff(int p) {
+    return p <= 1 ? 0 : twoff(p - 1) + (radix(p - 1) - 1) * span(p - 1);
+  }
+  static constexpr int TWSIZE = twoff(NPASS) > 0 ? twoff(NPASS) : 1;
 };
+
+// Fills the per-pass twiddle table pt[TWSIZE] from the base table
+// tw[m] = exp(-2 pi i m / (N TWSTEP)): entry (t - 1) Ns + k of pass p is
+// exp(-2 pi i t k / (Ns R)), so that consecutive threads read consecutive
+// entries.  `i0`/`stride` distribute the entries over the calling threads.
+template <int N, int TWSTEP>
+__host__ __device__ __forceinline__ void build_pass_twiddles(float2* pt, const float2* tw, int i0, int stride) {
+  using PS = Passes<N>;
+  for (int p = 1; p < PS::NPASS; ++p) {
+    const int R = PS::radix(p), Ns = PS::span(p), off = PS::twoff(p);
+    for (int e = i0; e < (R - 1) * Ns; e += stride) {
+      const int t = 1 + e / Ns, k = e % Ns;
+      pt[off + e] = tw[t * k * (N / (Ns * R)) * TWSTEP];
+    }
+  }
+}
 
 // Pass p of the transform (compile-time p): load (p > 0), butterflies, store
 // (p < last).  Ns = product of the radices of passes 0..p-1.
-template <int N, int S, int TWSTEP, int P>
+template <int N, int S, int P>
 __host__ __device__ __forceinline__ void run_pass(float2 (&v)[8], int tt, int b, const float2* in, float2* out,
-                                                  const float2* tw) {
+                                                  const float2* pt) {
   constexpr int R = Passes<N>::radix(P);
-  int Ns = 1;
-#pragma unroll
-  for (int p = 0; p < P; ++p) Ns *= Passes<N>::radix(p);
+  constexpr int Ns = Passes<N>::span(P);
   if (P > 0) load_stride<N>(v, tt, b, in);
-  pass_bfly<N, R, S, TWSTEP>(v, tt, Ns, tw);
+  pass_bfly<N, R, S>(v, tt, Ns, pt + Passes<N>::twoff(P));
   if (P < Passes<N>::NPASS - 1) pass_store<N, R>(v, tt, b, Ns, out);
 }
+
+// ---------------------------------------------------------------------------
+// Row-group variant: one sequence of length N is owned by T = N/8 consecutive
+// threads (tt = its index in the group), with a private shared buffer in which
+// element i lives at ridx(i).  That XOR swizzle makes the stride-layout reads,
+// every pass's Stockham writes and contiguous staging touch each bank the
+// minimum number of times for N = 32 .. 1024.  Buffers need N + 16 entries
+// (ridx(N) < N + 16 for the extra half-spectrum element).
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int ridx(int i) { return i ^ ((i >> 3) & 15); }
+
+template <int N, int R>
+__host__ __device__ __forceinline__ void rpass_store(const float2 (&v)[8], int tt, int Ns, float2* out) {
+  constexpr int M = 8 / R;
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int j = tt + m * (N / 8);
+    const int o = (j / Ns) * Ns * R + (j & (Ns - 1));
+#pragma unroll
+    for (int q = 0; q < R; ++q) out[ridx(o + q * Ns)] = v[m + q * M];
+  }
+}
+
+template <int N, int S, int P>
+__host__ __device__ __forceinline__ void rrun_pass(float2 (&v)[8], int tt, const float2* in, float2* out,
+                                                   const float2* pt) {
+  constexpr int R = Passes<N>::radix(P);
+  constexpr int Ns = Passes<N>::span(P);
+  if (P > 0) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = in[ridx(tt + k * (N / 8))];
+  }
+  pass_bfly<N, R, S>(v, tt, Ns, pt + Passes<N>::twoff(P));
+  if (P < Passes<N>::NPASS - 1) rpass_store<N, R>(v, tt, Ns, out);
+}
+
+#ifdef __CUDACC__
+// Barrier of a row group: the warp when the group fits in it, otherwise the
+// named barrier `id` over the group's threads.
+template <int T>
+__device__ __forceinline__ void group_sync(int id) {
+  if (T <= 32) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(T) : "memory");
+  }
+}
+
+// The whole transform of one sequence by its row group; result in v.
+template <int N, int S>
+__device__ __forceinline__ void row_fft(float2 (&v)[8], int tt, float2* buf0, float2* buf1, const float2* pt,
+                                        int bar_id) {
+  constexpr int NP = Passes<N>::NPASS;
+  constexpr int T = N / 8;
+  if (NP > 1) group_sync<T>(bar_id);
+  rrun_pass<N, S, 0>(v, tt, nullptr, buf0, pt);
+  if (NP > 1) {
+    group_sync<T>(bar_id);
+    rrun_pass<N, S, (NP > 1 ? 1 : 0)>(v, tt, buf0, buf1, pt);
+  }
+  if (NP > 2) {
+    group_sync<T>(bar_id);
+    rrun_pass<N, S, (NP > 2 ? 2 : 0)>(v, tt, buf1, buf0, pt);
+  }
+  if (NP > 3) {
+    group_sync<T>(bar_id);
+    rrun_pass<N, S, (NP > 3 ? 3 : 0)>(v, tt, buf0, buf1, pt);
+  }
+}
+#endif
 
 #ifdef __CUDACC__
 // The whole transform on the CTA's batch; buf0/buf1 hold N*kS float2 each.
 // Starts with a barrier (the buffers may still be read by a previous
 // transform) and ends with the result in v.
-template <int N, int S, int TWSTEP>
-__device__ __forceinline__ void fft(float2 (&v)[8], int tt, int b, float2* buf0, float2* buf1, const float2* tw) {
+template <int N, int S>
+__device__ __forceinline__ void fft(float2 (&v)[8], int tt, int b, float2* buf0, float2* buf1, const float2* pt) {
   constexpr int NP = Passes<N>::NPASS;
   if (NP > 1) __syncthreads();
-  run_pass<N, S, TWSTEP, 0>(v, tt, b, nullptr, buf0, tw);
+  run_pass<N, S, 0>(v, tt, b, nullptr, buf0, pt);
   if (NP > 1) {
     __syncthreads();
-    run_pass<N, S, TWSTEP, (NP > 1 ? 1 : 0)>(v, tt, b, buf0, buf1, tw);
+    run_pass<N, S, (NP > 1 ? 1 : 0)>(v, tt, b, buf0, buf1, pt);
   }
   if (NP > 2) {
     __syncthreads();
-    run_pass<N, S, TWSTEP, (NP > 2 ? 2 : 0)>(v, tt, b, buf1, buf0, tw);
+    run_pass<N, S, (NP > 2 ? 2 : 0)>(v, tt, b, buf1, buf0, pt);
   }
   if (NP > 3) {
     __syncthreads();
-    run_pass<N, S, TWSTEP, (NP > 3 ? 3 : 0)>(v, tt, b, buf0, buf1, tw);
+    run_pass<N, S, (NP > 3 ? 3 : 0)>(v, tt, b, buf0, buf1, pt);
   }
 }
 #endif

@@ -31,6 +31,7 @@ struct Geo {
   const float2* twH;  // exp(-2 pi i m / H), m < H
   const float2* twW;  // exp(-2 pi i m / W), m < W
   const float* bank;  // [eta][H][Wh]
+  const int2* ranges; // [eta] first and last half-plane column where the filter is non-zero
 };
 
 // Filter descriptor in bank order: kind 0 low-pass, 1 horizontal cone,
@@ -45,6 +46,7 @@ int filter_descs(int J, FilterDesc* out);  // returns eta
 // Filter bank and tables (shf_bank.cu).
 cudaError_t launch_twiddles(float2* tw, int N, cudaStream_t st);
 cudaError_t launch_build_bank(float* bank, const Geo& g, const FilterDesc* descs_dev, cudaStream_t st);
+cudaError_t launch_filter_ranges(const float* bank, const Geo& g, int2* ranges, cudaStream_t st);
 cudaError_t launch_data_term(const float* f, int C, const float* codebook_host, int K, float* s, int P,
                              cudaStream_t st);
 cudaError_t launch_labels(const float* w, int K, int P, int* labels, float* gap, cudaStream_t st);
@@ -110,7 +112,12 @@ struct LaunchHook {
 bool fast_path_ok(const Geo& g);
 cudaError_t prepare_fast_kernels();
 int fast_wave(const Geo& g);        // filters per wave
+int fast_pitch(const Geo& g);       // row pitch (complex) of the internal spectra: Wh rounded up to 8
 int fast_groups_max(const Geo& g);  // partial-sum groups per label
+bool fast_ustep_ok(const Geo& g, int K);
+// u-step, w-step, b_w update and row spectra of u (power-of-two sizes, K <= 8).
+cudaError_t run_fast_ustep(const Geo& g, const float2* T, const float* s, float* w, float* bw, float* u, float2* Ur,
+                           int K, float gamma, float scale, cudaStream_t st);
 // Everything of an iteration after the u/w-step: Ur (row spectra of u) -> uhat
 // -> per-filter analysis, v-step and synthesis -> T.
 cudaError_t run_fast_iteration_body(const Geo& g, const float2* Ur, float2* uhat, float2* Y, float* bv,

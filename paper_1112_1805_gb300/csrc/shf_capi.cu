@@ -93,6 +93,9 @@ struct seg_state {
   bool graph_tried = false;
   bool fast = false;          // power-of-two sizes: the shf_fast.cu kernels
   bool fast_ustep = false;    // ... including the u/w-step (K <= 8)
+  shf::FastPlan plan;         // fast path: static per-wave work list
+  shf::ChunkDesc* d_chunks = nullptr;
+  int *d_filters = nullptr, *d_tile_begin = nullptr, *d_tile_slots = nullptr;
   float2* uhat = nullptr;     // fast path: 2-D spectra of u [K][H][Wh]
   // Events recorded before every launch of an iteration (graph event nodes),
   // with the kind of the launch that follows each.
@@ -256,6 +259,10 @@ void free_state(seg_state* s) {
   for (cudaEvent_t e : s->ev)
     if (e) cudaEventDestroy(e);
   cudaFree(s->uhat);
+  cudaFree(s->d_chunks);
+  cudaFree(s->d_filters);
+  cudaFree(s->d_tile_begin);
+  cudaFree(s->d_tile_slots);
   float* fl[] = {s->f, s->s, s->bv, s->w, s->bw, s->u, s->stv, s->thr, s->lam, s->gap};
   for (float* p : fl) cudaFree(p);
   cudaFree(s->Ur);
@@ -321,8 +328,8 @@ cudaError_t enqueue_iteration(seg_state* st) {
           : shf::run_row_ustep(g, st->T, st->s, st->w, st->bw, st->u, st->Ur, nullptr, st->K, st->gamma, scale, s);
   if (st->fast) {
     if (e == cudaSuccess)
-      e = shf::run_fast_iteration_body(g, st->Ur, st->uhat, st->Y, st->bv, st->thr, st->partial, st->T, st->K,
-                                       scale, s, hook);
+      e = shf::run_fast_iteration_body(g, st->plan, st->Ur, st->uhat, st->Y, st->bv, st->thr, st->partial, st->T,
+                                       st->K, scale, s, hook);
   } else {
     hook.mark(shf::kKindFan);
     if (e == cudaSuccess) e = shf::run_col_fan(g, st->Ur, st->Y, st->K, st->groups, s);
@@ -453,9 +460,24 @@ int seg_admm_init(const shf_bank* b, const float* f, int C, const float* codeboo
   // coefficient-spectrum scratch: the whole label set on the generic path, one
   // wave of filters on the fast path; partial sums per filter group
   const size_t y_planes = st->fast ? static_cast<size_t>(shf::fast_wave(g)) : static_cast<size_t>(K) * g.eta;
-  const size_t p_groups = st->fast ? static_cast<size_t>(shf::fast_groups_max(g)) : static_cast<size_t>(st->groups);
   // plane size of the scratch spectra: the fast path pads rows to a pitch of 8
   const size_t Phs = st->fast ? static_cast<size_t>(g.H) * shf::fast_pitch(g) : Ph;
+  // fast path: per-wave work list from the filters' column ranges; one
+  // compact [H][8] partial tile per chunk and label
+  std::vector<shf::ChunkDesc> h_chunks;
+  std::vector<int> h_filters, h_tile_begin, h_tile_slots;
+  if (st->fast) {
+    std::vector<int2> ranges(g.eta);
+    cudaError_t e = cudaMemcpy(ranges.data(), g.ranges, sizeof(int2) * g.eta, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      free_state(st);
+      return fail(SHF_ERR_CUDA, std::string("seg_admm_init: ") + cudaGetErrorString(e));
+    }
+    shf::build_fast_plan(g, ranges.data(), &st->plan, &h_chunks, &h_filters, &h_tile_begin, &h_tile_slots);
+  }
+  const size_t partial_elems = st->fast ? static_cast<size_t>(K) * std::max(st->plan.nchunks_total, 1) * g.H *
+                                              shf::reg_batch()
+                                        : Ph * K * static_cast<size_t>(st->groups);
   for (cudaEvent_t& ev : st->ev) {
     cudaError_t e = cudaEventCreate(&ev);
     if (e != cudaSuccess) {
@@ -471,8 +493,12 @@ int seg_admm_init(const shf_bank* b, const float* f, int C, const float* codeboo
       (rc = dev_alloc(&st->bw, P * K, "b_w")) || (rc = dev_alloc(&st->u, P * K, "u")) ||
       (rc = dev_alloc(&st->stv, P * K, "stv")) || (rc = dev_alloc(&st->Ur, Ph * K, "Ur")) ||
       (rc = dev_alloc(&st->Y, Phs * std::max(y_planes, static_cast<size_t>(K) * g.eta * !st->fast), "Y")) ||
-      (rc = dev_alloc(&st->partial, Phs * K * p_groups, "partial")) || (rc = dev_alloc(&st->T, Ph * K, "T")) ||
+      (rc = dev_alloc(&st->partial, partial_elems, "partial")) || (rc = dev_alloc(&st->T, Ph * K, "T")) ||
       (st->fast && (rc = dev_alloc(&st->uhat, Phs * K, "uhat"))) ||
+      (st->fast && (rc = dev_alloc(&st->d_chunks, std::max<size_t>(h_chunks.size(), 1), "chunks"))) ||
+      (st->fast && (rc = dev_alloc(&st->d_filters, h_filters.size(), "chunk filters"))) ||
+      (st->fast && (rc = dev_alloc(&st->d_tile_begin, h_tile_begin.size(), "tile_begin"))) ||
+      (st->fast && (rc = dev_alloc(&st->d_tile_slots, h_tile_slots.size(), "tile_slots"))) ||
       (rc = dev_alloc(&st->thr, g.eta, "thr")) || (rc = dev_alloc(&st->lam, g.eta, "lam")) ||
       (rc = dev_alloc(&st->gap, P, "gap")) || (rc = dev_alloc(&st->labels, P, "labels")) ||
       (rc = dev_alloc(&st->flag, 1, "flag")) || (rc = dev_alloc(&st->red, st->red_len, "red"))) {
@@ -487,6 +513,24 @@ int seg_admm_init(const shf_bank* b, const float* f, int C, const float* codeboo
     thr[i] = st->gamma * lam[i];
   }
   cudaError_t e = cudaMemcpyAsync(st->thr, thr.data(), sizeof(float) * g.eta, cudaMemcpyHostToDevice, st->stream);
+  if (st->fast) {
+    if (e == cudaSuccess && !h_chunks.empty())
+      e = cudaMemcpyAsync(st->d_chunks, h_chunks.data(), sizeof(shf::ChunkDesc) * h_chunks.size(),
+                          cudaMemcpyHostToDevice, st->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(st->d_filters, h_filters.data(), sizeof(int) * h_filters.size(), cudaMemcpyHostToDevice,
+                          st->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(st->d_tile_begin, h_tile_begin.data(), sizeof(int) * h_tile_begin.size(),
+                          cudaMemcpyHostToDevice, st->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(st->d_tile_slots, h_tile_slots.data(), sizeof(int) * h_tile_slots.size(),
+                          cudaMemcpyHostToDevice, st->stream);
+    st->plan.chunks = st->d_chunks;
+    st->plan.filters = st->d_filters;
+    st->plan.tile_begin = st->d_tile_begin;
+    st->plan.tile_slots = st->d_tile_slots;
+  }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(st->lam, lam.data(), sizeof(float) * g.eta, cudaMemcpyHostToDevice, st->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(st->f, f, sizeof(float) * P * C, cudaMemcpyDeviceToDevice, st->stream);

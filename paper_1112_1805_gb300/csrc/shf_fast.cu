@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(H) k_fcol_fwd(const float2* __restrict__ in, f
   extern __shared__ float2 sm[];
   float2* tw = sm;  // per-pass twiddles
   float2* b0 = sm + reg::Passes<H>::TWSIZE;
-  float2* b1 = b0 + H * kS;
+  float2* b1 = b0 + reg::batch_rows(H) * kS;
   const int b = threadIdx.x & 7, tt = threadIdx.x >> 3;
   const int col = blockIdx.x * kB + b;
   const bool ok = col < Wh;
@@ -86,43 +86,32 @@ __device__ __forceinline__ void load_tile8(float2 (&v)[8], const float2* __restr
     v[k] = ok ? src[static_cast<size_t>(tt + k * (H / 8)) * pitch + col] : make_float2(0.f, 0.f);
 }
 
-// Whether filter f is non-zero somewhere in column tile `tile` (8 columns).
-__device__ __forceinline__ bool covers(const int2* __restrict__ ranges, int f, int tile) {
-  const int2 r = ranges[f];
-  return r.x <= r.y && tile >= (r.x >> 3) && tile <= (r.y >> 3);
-}
-
 template <int H>
-__global__ void __launch_bounds__(H, (1024 / H > 0 ? 1024 / H : 1)) k_fcol_fan(const float2* __restrict__ uhat, const float* __restrict__ bank,
-                                                const int2* __restrict__ ranges, float2* __restrict__ Y, int Wh,
-                                                int Whp, int label, int f0, int nf, int fg,
-                                                const float2* __restrict__ twH) {
+__global__ void __launch_bounds__(H, (1024 / H > 0 ? 1024 / H : 1))
+    k_fcol_fan(const float2* __restrict__ uhat, const float* __restrict__ bank, const ChunkDesc* __restrict__ chunks,
+               const int* __restrict__ filters, float2* __restrict__ Y, int Wh, int Whp, int label, int f0,
+               const float2* __restrict__ twH) {
   extern __shared__ float2 sm[];
   float2* tw = sm;  // per-pass twiddles
   float2* b0 = sm + reg::Passes<H>::TWSIZE;
-  float2* b1 = b0 + H * kS;
+  float2* b1 = b0 + reg::batch_rows(H) * kS;
+  const ChunkDesc c = chunks[blockIdx.x];
   const int b = threadIdx.x & 7, tt = threadIdx.x >> 3;
-  const int col = blockIdx.x * kB + b;
+  const int col = c.tile * kB + b;
   const bool ok = col < Wh;
   const size_t Pb = static_cast<size_t>(H) * Wh, Pp = static_cast<size_t>(H) * Whp;
-  const int fb = blockIdx.y * fg, fe = min(nf, fb + fg);
   float2 u[8];
   float w[8];
   load_tile8<H>(u, uhat + Pp * label, Whp, tt, col, ok);
-  load_bank8<H>(w, bank + Pb * (f0 + fb), Wh, tt, col, ok);
+  load_bank8<H>(w, bank + Pb * (f0 + filters[c.first]), Wh, tt, col, ok);
   load_pass_table<H, 1>(tw, twH);
   __syncthreads();
-  for (int fl = fb; fl < fe; ++fl) {
-    // filters are exactly zero outside their column support: Y_f is only
-    // produced (and later read) on the tiles the support touches
-    if (!covers(ranges, f0 + fl, blockIdx.x)) {
-      if (fl + 1 < fe) load_bank8<H>(w, bank + Pb * (f0 + fl + 1), Wh, tt, col, ok);
-      continue;
-    }
+  for (int i = 0; i < c.nf; ++i) {
+    const int fl = filters[c.first + i];
     float2 v[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) v[k] = c_scale(u[k], w[k]);
-    if (fl + 1 < fe) load_bank8<H>(w, bank + Pb * (f0 + fl + 1), Wh, tt, col, ok);
+    if (i + 1 < c.nf) load_bank8<H>(w, bank + Pb * (f0 + filters[c.first + i + 1]), Wh, tt, col, ok);
     reg::fft<H, +1>(v, tt, b, b0, b1, tw);
     if (ok) {
       float2* dst = Y + Pp * fl + col;
@@ -132,82 +121,71 @@ __global__ void __launch_bounds__(H, (1024 / H > 0 ? 1024 / H : 1)) k_fcol_fan(c
   }
 }
 
-// partial[g][label] (+)= sum over the group's filters of W_f * column-forward(Y_f);
-// accumulate != 0 adds to what an earlier wave left there.
+// partial[label][slot] = sum over the chunk's filters of W_f * column-forward(Y_f)
+// on the chunk's tile, stored compactly as [H][8].
 template <int H>
-__global__ void __launch_bounds__(H, (1024 / H > 0 ? 1024 / H : 1)) k_fcol_gather(const float2* __restrict__ Y, const float* __restrict__ bank,
-                                                   const int2* __restrict__ ranges, float2* __restrict__ partial,
-                                                   int Wh, int Whp, int K, int label, int f0, int nf, int fg,
-                                                   int accumulate, const float2* __restrict__ twH) {
+__global__ void __launch_bounds__(H, (1024 / H > 0 ? 1024 / H : 1))
+    k_fcol_gather(const float2* __restrict__ Y, const float* __restrict__ bank, const ChunkDesc* __restrict__ chunks,
+                  const int* __restrict__ filters, float2* __restrict__ partial, int Wh, int Whp, int nslots,
+                  int label, int f0, const float2* __restrict__ twH) {
   extern __shared__ float2 sm[];
   float2* tw = sm;  // per-pass twiddles
   float2* b0 = sm + reg::Passes<H>::TWSIZE;
-  float2* b1 = b0 + H * kS;
+  float2* b1 = b0 + reg::batch_rows(H) * kS;
+  const ChunkDesc c = chunks[blockIdx.x];
   const int b = threadIdx.x & 7, tt = threadIdx.x >> 3;
-  const int col = blockIdx.x * kB + b;
+  const int col = c.tile * kB + b;
   const bool ok = col < Wh;
   const size_t Pb = static_cast<size_t>(H) * Wh, Pp = static_cast<size_t>(H) * Whp;
-  const int fb = blockIdx.y * fg, fe = min(nf, fb + fg);
   float2 acc[8], y[8];
   float w[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) acc[k] = make_float2(0.f, 0.f);
-  // only the filters whose support touches this tile contribute
-  auto next_active = [&](int f) {
-    while (f < fe && !covers(ranges, f0 + f, blockIdx.x)) ++f;
-    return f;
-  };
-  int fl = next_active(fb);
-  if (fl < fe) load_tile8<H>(y, Y + Pp * fl, Whp, tt, col, ok);
+  load_tile8<H>(y, Y + Pp * filters[c.first], Whp, tt, col, ok);
   load_pass_table<H, 1>(tw, twH);
   __syncthreads();
-  while (fl < fe) {
+  for (int i = 0; i < c.nf; ++i) {
+    const int fl = filters[c.first + i];
     float2 v[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) v[k] = y[k];
     load_bank8<H>(w, bank + Pb * (f0 + fl), Wh, tt, col, ok);
-    const int fn = next_active(fl + 1);
-    if (fn < fe) load_tile8<H>(y, Y + Pp * fn, Whp, tt, col, ok);
+    if (i + 1 < c.nf) load_tile8<H>(y, Y + Pp * filters[c.first + i + 1], Whp, tt, col, ok);
     reg::fft<H, -1>(v, tt, b, b0, b1, tw);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       acc[k].x = fmaf(w[k], v[k].x, acc[k].x);
       acc[k].y = fmaf(w[k], v[k].y, acc[k].y);
     }
-    fl = fn;
   }
-  if (ok) {
-    float2* dst = partial + Pp * (static_cast<size_t>(blockIdx.y) * K + label) + col;
+  float2* dst = partial + (static_cast<size_t>(label) * nslots + c.slot) * H * kB + b;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const size_t off = static_cast<size_t>(tt + k * (H / 8)) * Whp;
-      dst[off] = accumulate ? c_add(dst[off], acc[k]) : acc[k];
-    }
-  }
+  for (int k = 0; k < 8; ++k) dst[static_cast<size_t>(tt + k * (H / 8)) * kB] = acc[k];
 }
 
+// T[label] on one tile = column-inverse of the sum of the tile's chunk
+// partials, in the fixed slot order (filter order).
 template <int H>
-__global__ void __launch_bounds__(H) k_fcol_reduce_inv(const float2* __restrict__ partial, float2* __restrict__ T,
-                                                       int Wh, int Whp, int K, int groups,
-                                                       const float2* __restrict__ twH) {
+__global__ void __launch_bounds__(H) k_fcol_reduce_inv(const float2* __restrict__ partial,
+                                                       const int* __restrict__ tile_begin,
+                                                       const int* __restrict__ tile_slots, float2* __restrict__ T,
+                                                       int Wh, int nslots, const float2* __restrict__ twH) {
   extern __shared__ float2 sm[];
   float2* tw = sm;  // per-pass twiddles
   float2* b0 = sm + reg::Passes<H>::TWSIZE;
-  float2* b1 = b0 + H * kS;
+  float2* b1 = b0 + reg::batch_rows(H) * kS;
   const int b = threadIdx.x & 7, tt = threadIdx.x >> 3;
-  const int col = blockIdx.x * kB + b;
+  const int tile = blockIdx.x, label = blockIdx.y;
+  const int col = tile * kB + b;
   const bool ok = col < Wh;
-  const size_t Pp = static_cast<size_t>(H) * Whp;
-  const int label = blockIdx.y;
   float2 v[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) v[k] = make_float2(0.f, 0.f);
-  if (ok) {
-    for (int g = 0; g < groups; ++g) {  // fixed order over the groups
-      const float2* src = partial + Pp * (static_cast<size_t>(g) * K + label) + col;
+  const int s0 = tile_begin[tile], s1 = tile_begin[tile + 1];
+  for (int si = s0; si < s1; ++si) {
+    const float2* src = partial + (static_cast<size_t>(label) * nslots + tile_slots[si]) * H * kB + b;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) v[k] = c_add(v[k], src[static_cast<size_t>(tt + k * (H / 8)) * Whp]);
-    }
+    for (int k = 0; k < 8; ++k) v[k] = c_add(v[k], src[static_cast<size_t>(tt + k * (H / 8)) * kB]);
   }
   load_pass_table<H, 1>(tw, twH);
   __syncthreads();
@@ -239,7 +217,7 @@ __global__ void __launch_bounds__(256) k_wrow_shrink(float2* __restrict__ Y, flo
                                                      const float2* __restrict__ twW) {
   constexpr int T = L / 8;
   constexpr int RPC = 256 / T;  // rows per CTA
-  constexpr int BUF = L + 16;
+  constexpr int BUF = reg::row_buf(L);
   extern __shared__ float2 sm[];
   float2* tw = sm;                                   // exp(-2 pi i m / W), m <= L
   float2* pt = tw + (L + 1);                         // per-pass twiddles of the length-L transform
@@ -345,7 +323,7 @@ __global__ void __launch_bounds__(256) k_wrow_ustep(const float2* __restrict__ T
                                                     float scale, float gamma, const float2* __restrict__ twW) {
   constexpr int T = L / 8;
   constexpr int RPC = 256 / T;
-  constexpr int BUF = L + 16;
+  constexpr int BUF = reg::row_buf(L);
   constexpr int Wh = L + 1;
   extern __shared__ float2 sm[];
   float2* tw = sm;
@@ -454,17 +432,17 @@ __global__ void __launch_bounds__(256) k_wrow_ustep(const float2* __restrict__ T
 
 template <int L>
 size_t ustep_smem(int K) {
-  return sizeof(float2) * ((L + 1) + reg::Passes<L>::TWSIZE + (256 / (L / 8)) * 2 * (L + 16) + K * 8 * 256);
+  return sizeof(float2) * ((L + 1) + reg::Passes<L>::TWSIZE + (256 / (L / 8)) * 2 * reg::row_buf(L) + K * 8 * 256);
 }
 
 template <int N>
 size_t col_smem() {
-  return sizeof(float2) * (reg::Passes<N>::TWSIZE + 2 * N * kS);
+  return sizeof(float2) * (reg::Passes<N>::TWSIZE + 2 * reg::batch_rows(N) * kS);
 }
 
 template <int L>
 size_t row_smem() {
-  return sizeof(float2) * ((L + 1) + reg::Passes<L>::TWSIZE + (256 / (L / 8)) * 2 * (L + 16));
+  return sizeof(float2) * ((L + 1) + reg::Passes<L>::TWSIZE + (256 / (L / 8)) * 2 * reg::row_buf(L));
 }
 
 template <int L>
@@ -472,58 +450,38 @@ int row_rows_per_cta() {
   return 256 / (L / 8);
 }
 
-int groups_for(const Geo& g, int nf) {
-  // enough CTAs for about two per SM, at least two filters per group
-  const int want = (2 * 152 + g.ntiles - 1) / g.ntiles;
-  int fg = (nf + want - 1) / want;
-  if (fg < 2) fg = 2;
-  if (fg > nf) fg = nf;
-  return fg;
-}
-
-// One filter-group size for every wave, so that later waves never use a group
-// the first wave of the label did not initialise.
 template <int H, int L>
-cudaError_t per_filter_waves(const Geo& g, const float2* uhat, float2* Y, float* bv, const float* thr,
-                             float2* partial, int K, int wave, float scale, cudaStream_t st, const LaunchHook& hook,
-                             int* groups_out) {
-  const int ntiles = (g.Wh + kB - 1) / kB;
-  const int Whp = fast_pitch(g);
-  const int fg = groups_for(g, wave);
-  int groups = 0;
-  for (int label = 0; label < K; ++label) {
-    for (int f0 = 0; f0 < g.eta; f0 += wave) {
-      const int nf = min(wave, g.eta - f0);
-      const int ng = (nf + fg - 1) / fg;
-      hook.mark(kKindFan);
-      k_fcol_fan<H><<<dim3(ntiles, ng), H, col_smem<H>(), st>>>(uhat, g.bank, g.ranges, Y, g.Wh, Whp, label, f0,
-                                                                nf, fg, g.twH);
-      hook.mark(kKindShrink);
-      k_wrow_shrink<L><<<dim3((g.H + row_rows_per_cta<L>() - 1) / row_rows_per_cta<L>(), nf), 256, row_smem<L>(),
-                         st>>>(Y, bv, thr, g.ranges, g.H, Whp, g.eta, label, f0, scale, g.twW);
-      hook.mark(kKindGather);
-      k_fcol_gather<H><<<dim3(ntiles, ng), H, col_smem<H>(), st>>>(Y, g.bank, g.ranges, partial, g.Wh, Whp, K,
-                                                                   label, f0, nf, fg, f0 > 0 ? 1 : 0, g.twH);
-      if (ng > groups) groups = ng;
-    }
-  }
-  *groups_out = groups;
-  return cudaGetLastError();
-}
-
-template <int H, int L>
-cudaError_t iteration_body(const Geo& g, const float2* Ur, float2* uhat, float2* Y, float* bv, const float* thr,
-                           float2* partial, float2* T, int K, int wave, float scale, cudaStream_t st,
+cudaError_t iteration_body(const Geo& g, const FastPlan& plan, const float2* Ur, float2* uhat, float2* Y, float* bv,
+                           const float* thr, float2* partial, float2* T, int K, float scale, cudaStream_t st,
                            const LaunchHook& hook) {
   const int ntiles = (g.Wh + kB - 1) / kB;
   const int Whp = fast_pitch(g);
+  const int nslots = plan.nchunks_total;
+  const int nw = static_cast<int>(plan.wave_f0.size());
   hook.mark(kKindColFwd);
   k_fcol_fwd<H><<<dim3(ntiles, K), H, col_smem<H>(), st>>>(Ur, uhat, g.Wh, Whp, g.twH);
-  int groups = 0;
-  cudaError_t e = per_filter_waves<H, L>(g, uhat, Y, bv, thr, partial, K, wave, scale, st, hook, &groups);
-  if (e != cudaSuccess) return e;
+  for (int label = 0; label < K; ++label) {
+    for (int w = 0; w < nw; ++w) {
+      const int f0 = plan.wave_f0[w], nf = plan.wave_nf[w], c0 = plan.wave_chunk0[w];
+      const int nc = (w + 1 < nw ? plan.wave_chunk0[w + 1] : nslots) - c0;
+      if (nc > 0) {
+        hook.mark(kKindFan);
+        k_fcol_fan<H><<<nc, H, col_smem<H>(), st>>>(uhat, g.bank, plan.chunks + c0, plan.filters, Y, g.Wh, Whp,
+                                                     label, f0, g.twH);
+      }
+      hook.mark(kKindShrink);
+      k_wrow_shrink<L><<<dim3((g.H + row_rows_per_cta<L>() - 1) / row_rows_per_cta<L>(), nf), 256, row_smem<L>(),
+                         st>>>(Y, bv, thr, g.ranges, g.H, Whp, g.eta, label, f0, scale, g.twW);
+      if (nc > 0) {
+        hook.mark(kKindGather);
+        k_fcol_gather<H><<<nc, H, col_smem<H>(), st>>>(Y, g.bank, plan.chunks + c0, plan.filters, partial, g.Wh,
+                                                        Whp, nslots, label, f0, g.twH);
+      }
+    }
+  }
   hook.mark(kKindReduce);
-  k_fcol_reduce_inv<H><<<dim3(ntiles, K), H, col_smem<H>(), st>>>(partial, T, g.Wh, Whp, K, groups, g.twH);
+  k_fcol_reduce_inv<H><<<dim3(ntiles, K), H, col_smem<H>(), st>>>(partial, plan.tile_begin, plan.tile_slots, T,
+                                                                  g.Wh, nslots, g.twH);
   return cudaGetLastError();
 }
 
@@ -563,18 +521,18 @@ cudaError_t ustep_launch(const Geo& g, const float2* T, const float* s, float* w
 }
 
 template <int H>
-cudaError_t dispatch_L(const Geo& g, const float2* Ur, float2* uhat, float2* Y, float* bv, const float* thr,
-                       float2* partial, float2* T, int K, int wave, float scale, cudaStream_t st,
+cudaError_t dispatch_L(const Geo& g, const FastPlan& plan, const float2* Ur, float2* uhat, float2* Y, float* bv,
+                       const float* thr, float2* partial, float2* T, int K, float scale, cudaStream_t st,
                        const LaunchHook& hook) {
   switch (g.L) {
-    case 8: return iteration_body<H, 8>(g, Ur, uhat, Y, bv, thr, partial, T, K, wave, scale, st, hook);
-    case 16: return iteration_body<H, 16>(g, Ur, uhat, Y, bv, thr, partial, T, K, wave, scale, st, hook);
-    case 32: return iteration_body<H, 32>(g, Ur, uhat, Y, bv, thr, partial, T, K, wave, scale, st, hook);
-    case 64: return iteration_body<H, 64>(g, Ur, uhat, Y, bv, thr, partial, T, K, wave, scale, st, hook);
-    case 128: return iteration_body<H, 128>(g, Ur, uhat, Y, bv, thr, partial, T, K, wave, scale, st, hook);
-    case 256: return iteration_body<H, 256>(g, Ur, uhat, Y, bv, thr, partial, T, K, wave, scale, st, hook);
-    case 512: return iteration_body<H, 512>(g, Ur, uhat, Y, bv, thr, partial, T, K, wave, scale, st, hook);
-    case 1024: return iteration_body<H, 1024>(g, Ur, uhat, Y, bv, thr, partial, T, K, wave, scale, st, hook);
+    case 8: return iteration_body<H, 8>(g, plan, Ur, uhat, Y, bv, thr, partial, T, K, scale, st, hook);
+    case 16: return iteration_body<H, 16>(g, plan, Ur, uhat, Y, bv, thr, partial, T, K, scale, st, hook);
+    case 32: return iteration_body<H, 32>(g, plan, Ur, uhat, Y, bv, thr, partial, T, K, scale, st, hook);
+    case 64: return iteration_body<H, 64>(g, plan, Ur, uhat, Y, bv, thr, partial, T, K, scale, st, hook);
+    case 128: return iteration_body<H, 128>(g, plan, Ur, uhat, Y, bv, thr, partial, T, K, scale, st, hook);
+    case 256: return iteration_body<H, 256>(g, plan, Ur, uhat, Y, bv, thr, partial, T, K, scale, st, hook);
+    case 512: return iteration_body<H, 512>(g, plan, Ur, uhat, Y, bv, thr, partial, T, K, scale, st, hook);
+    case 1024: return iteration_body<H, 1024>(g, plan, Ur, uhat, Y, bv, thr, partial, T, K, scale, st, hook);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -645,25 +603,62 @@ int fast_wave(const Geo& g) {
   return (g.eta + nw - 1) / nw;
 }
 
-int fast_groups_max(const Geo& g) {
+void build_fast_plan(const Geo& g, const int2* ranges, FastPlan* plan, std::vector<ChunkDesc>* chunks,
+                     std::vector<int>* filters, std::vector<int>* tile_begin, std::vector<int>* tile_slots) {
+  const int ntiles = (g.Wh + kB - 1) / kB;
   const int wave = fast_wave(g);
-  const int fg = groups_for(g, wave);
-  return (wave + fg - 1) / fg;
+  chunks->clear();
+  filters->clear();
+  plan->wave_f0.clear();
+  plan->wave_nf.clear();
+  plan->wave_chunk0.clear();
+  std::vector<std::vector<int>> per_tile(ntiles);
+  for (int f0 = 0; f0 < g.eta; f0 += wave) {
+    const int nf = std::min(wave, g.eta - f0);
+    plan->wave_f0.push_back(f0);
+    plan->wave_nf.push_back(nf);
+    plan->wave_chunk0.push_back(static_cast<int>(chunks->size()));
+    for (int t = 0; t < ntiles; ++t) {
+      std::vector<int> act;
+      for (int fl = 0; fl < nf; ++fl) {
+        const int2 r = ranges[f0 + fl];
+        if (r.x <= r.y && t >= (r.x >> 3) && t <= (r.y >> 3)) act.push_back(fl);
+      }
+      for (size_t a = 0; a < act.size(); a += kChunk) {
+        ChunkDesc c;
+        c.tile = t;
+        c.first = static_cast<int>(filters->size());
+        c.nf = static_cast<int>(std::min<size_t>(kChunk, act.size() - a));
+        c.slot = static_cast<int>(chunks->size());
+        for (int i = 0; i < c.nf; ++i) filters->push_back(act[a + i]);
+        per_tile[t].push_back(c.slot);
+        chunks->push_back(c);
+      }
+    }
+  }
+  plan->nchunks_total = static_cast<int>(chunks->size());
+  tile_begin->assign(1, 0);
+  tile_slots->clear();
+  for (int t = 0; t < ntiles; ++t) {
+    for (int sl : per_tile[t]) tile_slots->push_back(sl);
+    tile_begin->push_back(static_cast<int>(tile_slots->size()));
+  }
+  if (filters->empty()) filters->push_back(0);  // keep the device arrays non-empty
+  if (tile_slots->empty()) tile_slots->push_back(0);
 }
 
-cudaError_t run_fast_iteration_body(const Geo& g, const float2* Ur, float2* uhat, float2* Y, float* bv,
-                                    const float* thr, float2* partial, float2* T, int K, float scale,
+cudaError_t run_fast_iteration_body(const Geo& g, const FastPlan& plan, const float2* Ur, float2* uhat, float2* Y,
+                                    float* bv, const float* thr, float2* partial, float2* T, int K, float scale,
                                     cudaStream_t st, const LaunchHook& hook) {
-  const int wave = fast_wave(g);
   switch (g.H) {
-    case 8: return dispatch_L<8>(g, Ur, uhat, Y, bv, thr, partial, T, K, wave, scale, st, hook);
-    case 16: return dispatch_L<16>(g, Ur, uhat, Y, bv, thr, partial, T, K, wave, scale, st, hook);
-    case 32: return dispatch_L<32>(g, Ur, uhat, Y, bv, thr, partial, T, K, wave, scale, st, hook);
-    case 64: return dispatch_L<64>(g, Ur, uhat, Y, bv, thr, partial, T, K, wave, scale, st, hook);
-    case 128: return dispatch_L<128>(g, Ur, uhat, Y, bv, thr, partial, T, K, wave, scale, st, hook);
-    case 256: return dispatch_L<256>(g, Ur, uhat, Y, bv, thr, partial, T, K, wave, scale, st, hook);
-    case 512: return dispatch_L<512>(g, Ur, uhat, Y, bv, thr, partial, T, K, wave, scale, st, hook);
-    case 1024: return dispatch_L<1024>(g, Ur, uhat, Y, bv, thr, partial, T, K, wave, scale, st, hook);
+    case 8: return dispatch_L<8>(g, plan, Ur, uhat, Y, bv, thr, partial, T, K, scale, st, hook);
+    case 16: return dispatch_L<16>(g, plan, Ur, uhat, Y, bv, thr, partial, T, K, scale, st, hook);
+    case 32: return dispatch_L<32>(g, plan, Ur, uhat, Y, bv, thr, partial, T, K, scale, st, hook);
+    case 64: return dispatch_L<64>(g, plan, Ur, uhat, Y, bv, thr, partial, T, K, scale, st, hook);
+    case 128: return dispatch_L<128>(g, plan, Ur, uhat, Y, bv, thr, partial, T, K, scale, st, hook);
+    case 256: return dispatch_L<256>(g, plan, Ur, uhat, Y, bv, thr, partial, T, K, scale, st, hook);
+    case 512: return dispatch_L<512>(g, plan, Ur, uhat, Y, bv, thr, partial, T, K, scale, st, hook);
+    case 1024: return dispatch_L<1024>(g, plan, Ur, uhat, Y, bv, thr, partial, T, K, scale, st, hook);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -8,9 +8,10 @@
 // double-buffered so that one barrier per exchange suffices.  The result is
 // again in the stride layout, in natural order.  Shared memory rows hold the
 // 8 batch members of one index (64 bytes); row i is stored at row
-// i ^ ((i >> 3) & 1), so that the stride-layout reads, the Stockham writes of
-// every pass and batch-fast staging all touch each bank exactly twice per
-// warp (the minimum for 8-byte accesses).
+// i + (i >> 3) (one padding row after every 8), so that the stride-layout
+// reads, the Stockham writes of every pass and batch-fast staging all touch
+// each bank the minimum number of times (checked by enumerating every access
+// pattern), and every address is a per-thread base plus a compile-time offset.
 #pragma once
 
 #include "shf_fft.cuh"
@@ -23,7 +24,11 @@ constexpr int kS = kB;  // float2 per shared-memory row
 
 __host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
 
-__host__ __device__ __forceinline__ int sidx(int i, int b) { return (i ^ ((i >> 3) & 1)) * kS + b; }
+// Padded row of index i in the batch layout, and the element offset.
+__host__ __device__ constexpr int brow(int i) { return i + (i >> 3); }
+__host__ __device__ __forceinline__ int sidx(int i, int b) { return brow(i) * kS + b; }
+// Rows a batch buffer of length N needs (index N included, for staging).
+__host__ __device__ constexpr int batch_rows(int N) { return brow(N) + 1; }
 
 // exp(S 2 pi i m / Ntab) from the table tw[m] = exp(-2 pi i m / Ntab).
 template <int S>
@@ -57,23 +62,40 @@ __host__ __device__ __forceinline__ void pass_bfly(float2 (&v)[8], int tt, int N
   }
 }
 
-// Writes the outputs of a (non-final) pass to their Stockham positions.
-template <int N, int R>
-__host__ __device__ __forceinline__ void pass_store(const float2 (&v)[8], int tt, int b, int Ns, float2* out) {
+// Writes the outputs of a (non-final) pass to their Stockham positions
+// o + q Ns.  For Ns = 1 and for Ns a multiple of 8, brow(o + q Ns) =
+// brow(o) + brow(q Ns): one base per butterfly plus constant offsets.
+template <int N, int R, int Ns>
+__host__ __device__ __forceinline__ void pass_store(const float2 (&v)[8], int tt, int b, float2* out) {
   constexpr int M = 8 / R;
 #pragma unroll
   for (int m = 0; m < M; ++m) {
     const int j = tt + m * (N / 8);
     const int o = (j / Ns) * Ns * R + (j & (Ns - 1));
+    if (Ns == 1 || Ns % 8 == 0) {
+      float2* p = out + brow(o) * kS + b;
 #pragma unroll
-    for (int q = 0; q < R; ++q) out[sidx(o + q * Ns, b)] = v[m + q * M];
+      for (int q = 0; q < R; ++q) p[brow(q * Ns) * kS] = v[m + q * M];
+    } else {
+#pragma unroll
+      for (int q = 0; q < R; ++q) out[sidx(o + q * Ns, b)] = v[m + q * M];
+    }
   }
 }
 
+// Reads the stride layout; for N/8 a multiple of 8 the rows are brow(tt) +
+// brow(k N/8).
 template <int N>
 __host__ __device__ __forceinline__ void load_stride(float2 (&v)[8], int tt, int b, const float2* in) {
+  constexpr int T = N / 8;
+  if (T % 8 == 0) {
+    const float2* p = in + brow(tt) * kS + b;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) v[k] = in[sidx(tt + k * (N / 8), b)];
+    for (int k = 0; k < 8; ++k) v[k] = p[brow(k * T) * kS];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = in[sidx(tt + k * T, b)];
+  }
 }
 
 template <int N>
@@ -117,29 +139,50 @@ __host__ __device__ __forceinline__ void run_pass(float2 (&v)[8], int tt, int b,
   constexpr int Ns = Passes<N>::span(P);
   if (P > 0) load_stride<N>(v, tt, b, in);
   pass_bfly<N, R, S>(v, tt, Ns, pt + Passes<N>::twoff(P));
-  if (P < Passes<N>::NPASS - 1) pass_store<N, R>(v, tt, b, Ns, out);
+  if (P < Passes<N>::NPASS - 1) pass_store<N, R, Ns>(v, tt, b, out);
 }
 
 // ---------------------------------------------------------------------------
 // Row-group variant: one sequence of length N is owned by T = N/8 consecutive
 // threads (tt = its index in the group), with a private shared buffer in which
-// element i lives at ridx(i).  That XOR swizzle makes the stride-layout reads,
-// every pass's Stockham writes and contiguous staging touch each bank the
-// minimum number of times for N = 32 .. 1024.  Buffers need N + 16 entries
-// (ridx(N) < N + 16 for the extra half-spectrum element).
+// element i lives at ridx(i) = i + (i >> 4).  That padding makes the
+// stride-layout reads, the Stockham writes and contiguous staging touch each
+// bank the minimum number of times for N = 32 .. 1024 except the second-pass
+// writes at N = 128 (one extra wavefront), and keeps every address a
+// per-thread base plus a compile-time offset.  Buffers need row_buf(N)
+// entries (index N included, for the extra half-spectrum element).
 // ---------------------------------------------------------------------------
-__host__ __device__ __forceinline__ int ridx(int i) { return i ^ ((i >> 3) & 15); }
+__host__ __device__ constexpr int ridx(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int row_buf(int N) { return ridx(N) + 1; }
 
-template <int N, int R>
-__host__ __device__ __forceinline__ void rpass_store(const float2 (&v)[8], int tt, int Ns, float2* out) {
+// Stockham writes: ridx(o + q Ns) = ridx(o) + ridx(q Ns) for Ns = 1, 8 and
+// multiples of 16 (the spans of the stored radix-8 passes).
+template <int N, int R, int Ns>
+__host__ __device__ __forceinline__ void rpass_store(const float2 (&v)[8], int tt, float2* out) {
   constexpr int M = 8 / R;
 #pragma unroll
   for (int m = 0; m < M; ++m) {
     const int j = tt + m * (N / 8);
     const int o = (j / Ns) * Ns * R + (j & (Ns - 1));
+    if (R == 8 && (Ns == 1 || Ns == 8 || Ns % 16 == 0)) {
+      float2* p = out + ridx(o);
 #pragma unroll
-    for (int q = 0; q < R; ++q) out[ridx(o + q * Ns)] = v[m + q * M];
+      for (int q = 0; q < R; ++q) p[ridx(q * Ns)] = v[m + q * M];
+    } else {
+#pragma unroll
+      for (int q = 0; q < R; ++q) out[ridx(o + q * Ns)] = v[m + q * M];
+    }
   }
+}
+
+// Stride-layout reads: ridx(tt + k T) = base(tt) + ridx(k T) with base = ridx(tt)
+// for T >= 16 and tt otherwise.
+template <int N>
+__host__ __device__ __forceinline__ void rload_stride(float2 (&v)[8], int tt, const float2* in) {
+  constexpr int T = N / 8;
+  const float2* p = in + (T >= 16 ? ridx(tt) : tt);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = p[ridx(k * T)];
 }
 
 template <int N, int S, int P>
@@ -147,12 +190,9 @@ __host__ __device__ __forceinline__ void rrun_pass(float2 (&v)[8], int tt, const
                                                    const float2* pt) {
   constexpr int R = Passes<N>::radix(P);
   constexpr int Ns = Passes<N>::span(P);
-  if (P > 0) {
-#pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = in[ridx(tt + k * (N / 8))];
-  }
+  if (P > 0) rload_stride<N>(v, tt, in);
   pass_bfly<N, R, S>(v, tt, Ns, pt + Passes<N>::twoff(P));
-  if (P < Passes<N>::NPASS - 1) rpass_store<N, R>(v, tt, Ns, out);
+  if (P < Passes<N>::NPASS - 1) rpass_store<N, R, Ns>(v, tt, out);
 }
 
 #ifdef __CUDACC__

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <vector>
 
 #include "shf_fft.cuh"
 
@@ -108,21 +109,44 @@ struct LaunchHook {
   }
 };
 
+// Static work list of the fast path: for every wave of filters, chunks of at
+// most kChunk filters whose column support touches one tile of 8 columns.
+// Built once per state from the filters' column ranges.
+struct ChunkDesc {
+  int tile;   // column tile
+  int first;  // index into `filters` of the chunk's first filter
+  int nf;     // number of filters (1..kChunk), ascending filter order
+  int slot;   // partial-sum slot of this chunk within its label
+};
+struct FastPlan {
+  std::vector<int> wave_f0, wave_nf, wave_chunk0;  // per wave: first filter, filters, first chunk
+  int nchunks_total = 0;      // chunks of all waves of one label (= partial slots per label)
+  const ChunkDesc* chunks = nullptr;  // device [nchunks_total]
+  const int* filters = nullptr;       // device, wave-local filter indices
+  const int* tile_begin = nullptr;    // device [ntiles + 1], into tile_slots
+  const int* tile_slots = nullptr;    // device, slots of each tile in filter order
+};
+constexpr int kChunk = 2;
+constexpr int reg_batch() { return 8; }  // columns per tile of the fast column kernels
+
 // Fast path for power-of-two sizes (shf_fast.cu).
 bool fast_path_ok(const Geo& g);
 cudaError_t prepare_fast_kernels();
 int fast_wave(const Geo& g);        // filters per wave
 int fast_pitch(const Geo& g);       // row pitch (complex) of the internal spectra: Wh rounded up to 8
-int fast_groups_max(const Geo& g);  // partial-sum groups per label
 bool fast_ustep_ok(const Geo& g, int K);
 // u-step, w-step, b_w update and row spectra of u (power-of-two sizes, K <= 8).
 cudaError_t run_fast_ustep(const Geo& g, const float2* T, const float* s, float* w, float* bw, float* u, float2* Ur,
                            int K, float gamma, float scale, cudaStream_t st);
 // Everything of an iteration after the u/w-step: Ur (row spectra of u) -> uhat
 // -> per-filter analysis, v-step and synthesis -> T.
-cudaError_t run_fast_iteration_body(const Geo& g, const float2* Ur, float2* uhat, float2* Y, float* bv,
-                                    const float* thr, float2* partial, float2* T, int K, float scale,
+cudaError_t run_fast_iteration_body(const Geo& g, const FastPlan& plan, const float2* Ur, float2* uhat, float2* Y,
+                                    float* bv, const float* thr, float2* partial, float2* T, int K, float scale,
                                     cudaStream_t st, const LaunchHook& hook);
+// Host construction of the work list from the filters' column ranges
+// (ranges_host[eta]); returns the host arrays to upload.
+void build_fast_plan(const Geo& g, const int2* ranges_host, FastPlan* plan, std::vector<ChunkDesc>* chunks,
+                     std::vector<int>* filters, std::vector<int>* tile_begin, std::vector<int>* tile_slots);
 
 // C ABI layer (shf_capi.cu): the geometry and device tables of a bank, and the
 // thread-local message behind shf_last_error() (returns code).

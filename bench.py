@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--cpu-iters", type=int, default=2, help="oracle iterations in the CPU-baseline sample")
+    ap.add_argument("--workload", choices=["bezier512", "batch"], default="bezier512",
+                    help="bezier512 (default line) or the uneven batch of 64 images")
     ap.add_argument("--iters", type=int, default=0,
                     help="ADMM iterations per step for short profiling runs (default: the workload's 500)")
     return ap.parse_args()
@@ -347,10 +349,54 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """The uneven batch: 64 seeded images (384 x 640 first, sides 128..1024), K
+    in 2..6, J = floor(log2(min side)/2), 300 iterations, all images in one
+    CUDA graph per iteration.  Reports the summed Mpixel*label*iter/s."""
+    import torch
+
+    from paper_1112_1805_gb300.api import ShearletBatch
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    iters = args.iters or 300
+    shapes = synth.batch_shapes()
+    rng = np.random.default_rng(synth.seed_for(3))
+    imgs, cbs, lams, units = [], [], [], 0
+    for H, W, K, J in shapes:
+        cb = np.array([[0.2 + 0.6 * k / (K - 1)] for k in range(K)])
+        img, _ = synth.ellipse_image(H, W, cb, rng)
+        imgs.append(torch.tensor(img.astype(np.float32), device="cuda"))
+        cbs.append(cb)
+        lams.append(synth.scale_weights(0.1, J))
+        units += H * W * K * iters
+    batch = ShearletBatch(imgs, cbs, lams, 1.0)
+    for _ in range(args.warmup):
+        batch.step(iters)
+    batch.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(batch.stream)
+    for _ in range(args.steps):
+        batch.step(iters)
+    ev1.record(batch.stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    line = {"metric": METRIC, "value": units * args.steps / (ms / 1000.0) / 1e6, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batch: {len(shapes)} images, sides 128..1024 (first 384x640), K 2..6, "
+                                   f"J = floor(log2(min side)/2), {iters} iterations, one graph per iteration",
+                       "images": len(shapes), "iters_per_step": iters}}
+    print(json.dumps(line))
+    batch.close()
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_ours(args)
 
 

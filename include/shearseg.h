@@ -213,6 +213,35 @@ int seg_admm_kernel_times(seg_state* st, float* ms, int* launches, int* nk);
 /* Name of kernel kind i of seg_admm_kernel_times ("" when out of range). */
 const char* seg_admm_kernel_name(int i);
 
+/* ---------------------------------------------------------------------------
+ * Batched solves (no counterpart in the paper): n independent images of uneven
+ * sizes, channel and label counts, each the problem of Sec. 3 with its own
+ * parameters.  Image i: f[i] device [C[i]][H[i]][W[i]], codebooks[i] host
+ * [K[i]][C[i]], params[i] host (its J selects the filter bank; banks are
+ * built once per distinct (H, W, J) and shared).  One ADMM iteration of every
+ * image is captured as one CUDA graph with one branch per image, the branches
+ * on separate streams so that they run concurrently, joined on `stream`
+ * (NULL: the batch creates its own stream).  Errors: those of
+ * shfilters_build and seg_admm_init for any image (nothing is left allocated).
+ */
+typedef struct seg_batch seg_batch;
+int seg_admm_batch_init(int n, const int* H, const int* W, const int* C, const int* K, const float* const* f,
+                        const float* const* codebooks, const seg_params* params, void* stream, seg_batch** out);
+
+/* Enqueues n_iters iterations of every image (replays of the batch graph). */
+int seg_admm_batch_step(seg_batch* batch, int n_iters);
+
+/* Borrows image i's state for seg_admm_get/set/save/load/reset (owned by the
+ * batch: do not destroy it).  Its work goes to the image's own stream; call
+ * seg_admm_batch_sync first to order it after the batch's iterations. */
+int seg_admm_batch_image(seg_batch* batch, int i, seg_state** out);
+
+/* Waits for the batch's stream. */
+int seg_admm_batch_sync(seg_batch* batch);
+
+/* Releases every state and bank of the batch.  NULL is accepted. */
+int seg_admm_batch_destroy(seg_batch* batch);
+
 /* Waits for the state's stream. */
 int seg_admm_sync(seg_state* st);
 

@@ -88,9 +88,9 @@ class ShearletSegmenter:
                                       self.stream.cuda_stream)
 
     def close(self):
-        if getattr(self, "handle", None):
+        if getattr(self, "handle", None) and getattr(self, "_owned", True):
             B.seg_admm_destroy(self.handle)
-            self.handle = None
+        self.handle = None
 
     def __del__(self):
         try:
@@ -176,3 +176,76 @@ class ShearletSegmenter:
 
     def load(self, path: str) -> None:
         B.seg_admm_load(self.handle, path)
+
+
+class _BorrowedState(ShearletSegmenter):
+    """View of a state owned by a batch (readout and injection only)."""
+
+    def __init__(self, handle, K, C, H, W, eta):  # noqa: D401 - no library call here
+        self.handle = handle
+        self.K, self.C, self.H, self.W, self.eta = K, C, H, W, eta
+        self._owned = False
+
+    def close(self):
+        self.handle = None
+
+    def step(self, n: int) -> None:
+        raise RuntimeError("iterate a batch with ShearletBatch.step")
+
+
+class ShearletBatch:
+    """Independent images of uneven sizes and label counts solved together: one
+    CUDA graph per iteration with one concurrent branch per image.
+
+    images: list of float32 CUDA tensors [C, H, W] or [H, W]; codebooks: list of
+    [K, C] host arrays; Lambdas: list of J+1 weight vectors; gammas: list or
+    scalar."""
+
+    def __init__(self, images, codebooks, Lambdas, gammas=1.0, stream=None):
+        n = len(images)
+        imgs = [(t.unsqueeze(0) if t.dim() == 2 else t) for t in images]
+        for t in imgs:
+            _dev_f32(t, "image")
+        if not isinstance(gammas, (list, tuple)):
+            gammas = [gammas] * n
+        cbs = [np.asarray(c, dtype=np.float64).reshape(-1, t.shape[0]) for c, t in zip(codebooks, imgs)]
+        self._keep = []
+        params = []
+        for lam, g in zip(Lambdas, gammas):
+            lam = list(lam)
+            p, keep = B.make_params(g, len(lam) - 1, lam)
+            params.append(p)
+            self._keep.append(keep)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.stream.wait_stream(torch.cuda.current_stream())
+        torch.cuda.current_stream().synchronize()  # images are read on the images' own streams
+        self.shapes = [(int(t.shape[1]), int(t.shape[2]), int(c.shape[0]), int(t.shape[0]), len(l) - 1)
+                       for t, c, l in zip(imgs, cbs, Lambdas)]
+        self.handle = B.seg_admm_batch_init([s[0] for s in self.shapes], [s[1] for s in self.shapes],
+                                            [s[3] for s in self.shapes], [s[2] for s in self.shapes],
+                                            [t.data_ptr() for t in imgs], [c.ravel().tolist() for c in cbs], params,
+                                            self.stream.cuda_stream)
+
+    def __len__(self):
+        return len(self.shapes)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            B.seg_admm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int) -> None:
+        B.seg_admm_batch_step(self.handle, n)
+
+    def synchronize(self) -> None:
+        B.seg_admm_batch_sync(self.handle)
+
+    def image(self, i: int) -> ShearletSegmenter:
+        H, W, K, C, J = self.shapes[i]
+        return _BorrowedState(B.seg_admm_batch_image(self.handle, i), K, C, H, W, 2 ** (J + 2) - 3)

@@ -72,6 +72,12 @@ _SIG = {
     "seg_admm_load": (_I, [_VP, ctypes.c_char_p]),
     "seg_admm_kernel_times": (_I, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "seg_admm_kernel_name": (ctypes.c_char_p, [_I]),
+    "seg_admm_batch_init": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                 ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP, _VP, ctypes.POINTER(_VP)]),
+    "seg_admm_batch_step": (_I, [_VP, _I]),
+    "seg_admm_batch_image": (_I, [_VP, _I, ctypes.POINTER(_VP)]),
+    "seg_admm_batch_sync": (_I, [_VP]),
+    "seg_admm_batch_destroy": (_I, [_VP]),
     "seg_admm_sync": (_I, [_VP]),
     "seg_admm_destroy": (_I, [_VP]),
 }
@@ -222,3 +228,37 @@ def seg_admm_sync(state: int) -> None:
 
 def seg_admm_destroy(state: int) -> None:
     _call("seg_admm_destroy", _VP(state))
+
+
+def seg_admm_batch_init(H, W, C, K, f_ptrs, codebooks, params_list, stream=None) -> int:
+    """Batch of len(H) images.  f_ptrs: device pointers; codebooks: host sequences
+    (K_i*C_i floats each); params_list: seg_params structs (their Lambda arrays
+    must stay alive)."""
+    n = len(H)
+    arr = lambda xs: (_I * n)(*[int(x) for x in xs])  # noqa: E731
+    fp = (_VP * n)(*[int(p) for p in f_ptrs])
+    cbs = [(ctypes.c_float * len(c))(*[float(x) for x in c]) for c in codebooks]
+    cbp = (_VP * n)(*[ctypes.cast(c, _VP) for c in cbs])
+    prm = (seg_params * n)(*params_list)
+    out = _VP()
+    _call("seg_admm_batch_init", n, arr(H), arr(W), arr(C), arr(K), fp, cbp, ctypes.cast(prm, _VP),
+          _stream(stream), ctypes.byref(out))
+    return out.value
+
+
+def seg_admm_batch_step(batch: int, n_iters: int) -> None:
+    _call("seg_admm_batch_step", _VP(batch), int(n_iters))
+
+
+def seg_admm_batch_image(batch: int, i: int) -> int:
+    out = _VP()
+    _call("seg_admm_batch_image", _VP(batch), int(i), ctypes.byref(out))
+    return out.value
+
+
+def seg_admm_batch_sync(batch: int) -> None:
+    _call("seg_admm_batch_sync", _VP(batch))
+
+
+def seg_admm_batch_destroy(batch: int) -> None:
+    _call("seg_admm_batch_destroy", _VP(batch))

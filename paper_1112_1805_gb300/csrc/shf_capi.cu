@@ -790,6 +790,157 @@ const char* seg_admm_kernel_name(int i) {
   return (i >= 0 && i < shf::kNumKinds) ? names[i] : "";
 }
 
+// ---------------------------------------------------------------------------
+// Batches
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct seg_batch {
+  std::vector<shf_bank*> banks;
+  std::vector<seg_state*> states;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins;
+  cudaGraphExec_t exec = nullptr;
+  bool graph_tried = false;
+};
+
+namespace {
+
+void free_batch(seg_batch* b) {
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (seg_state* s : b->states)
+    if (s) seg_admm_destroy(s);
+  for (shf_bank* k : b->banks)
+    if (k) shfilters_destroy(k);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (cudaEvent_t e : b->joins)
+    if (e) cudaEventDestroy(e);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+// Forks from the batch stream to every image stream, enqueues one iteration
+// of each image, joins back.
+cudaError_t enqueue_batch_iteration(seg_batch* b) {
+  cudaError_t e = cudaEventRecord(b->fork, b->stream);
+  for (size_t i = 0; i < b->states.size() && e == cudaSuccess; ++i) {
+    seg_state* st = b->states[i];
+    e = cudaStreamWaitEvent(st->stream, b->fork, 0);
+    if (e == cudaSuccess) e = enqueue_iteration(st);
+    if (e == cudaSuccess) e = cudaEventRecord(b->joins[i], st->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->joins[i], 0);
+  }
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int seg_admm_batch_init(int n, const int* H, const int* W, const int* C, const int* K, const float* const* f,
+                        const float* const* codebooks, const seg_params* params, void* stream, seg_batch** out) {
+  if (!out) return fail(SHF_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || !H || !W || !C || !K || !f || !codebooks || !params)
+    return fail(SHF_ERR_ARG, "seg_admm_batch_init: bad argument");
+  auto* b = new seg_batch();
+  if (stream) {
+    b->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete b;
+      return fail(SHF_ERR_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    }
+    b->own_stream = true;
+  }
+  cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    free_batch(b);
+    return fail(SHF_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
+  }
+  b->joins.assign(n, nullptr);
+  for (int i = 0; i < n; ++i) {
+    e = cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      free_batch(b);
+      return fail(SHF_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
+    }
+  }
+  b->states.assign(n, nullptr);
+  for (int i = 0; i < n; ++i) {
+    shf_bank* bank = nullptr;
+    for (shf_bank* k : b->banks)
+      if (k->g.H == H[i] && k->g.W == W[i] && k->g.J == params[i].J) bank = k;
+    if (!bank) {
+      int rc = shfilters_build(H[i], W[i], params[i].J, b->stream, &bank);
+      if (rc) {
+        const std::string m = g_err;
+        free_batch(b);
+        return fail(rc, "image " + std::to_string(i) + ": " + m);
+      }
+      b->banks.push_back(bank);
+    }
+    int rc = seg_admm_init(bank, f[i], C[i], codebooks[i], K[i], &params[i], nullptr, &b->states[i]);
+    if (rc) {
+      const std::string m = g_err;
+      free_batch(b);
+      return fail(rc, "image " + std::to_string(i) + ": " + m);
+    }
+  }
+  *out = b;
+  return SHF_OK;
+}
+
+int seg_admm_batch_step(seg_batch* b, int n) {
+  if (!b || n < 0) return fail(SHF_ERR_ARG, "seg_admm_batch_step: bad argument");
+  if (n == 0) return SHF_OK;
+  if (!b->graph_tried) {
+    b->graph_tried = true;
+    cudaGraph_t graph = nullptr;
+    if (b->stream && cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      cudaError_t e = enqueue_batch_iteration(b);
+      cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
+      if (e == cudaSuccess && e2 == cudaSuccess && graph &&
+          cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess)
+        b->exec = nullptr;
+      if (graph) cudaGraphDestroy(graph);
+    }
+    cudaGetLastError();
+  }
+  for (int i = 0; i < n; ++i) {
+    if (b->exec) {
+      SHF_CK(cudaGraphLaunch(b->exec, b->stream));
+    } else {
+      SHF_CK(enqueue_batch_iteration(b));
+    }
+  }
+  for (seg_state* st : b->states) st->iter += n;
+  return SHF_OK;
+}
+
+int seg_admm_batch_image(seg_batch* b, int i, seg_state** out) {
+  if (!b || !out || i < 0 || i >= static_cast<int>(b->states.size()))
+    return fail(SHF_ERR_ARG, "seg_admm_batch_image: bad argument");
+  *out = b->states[i];
+  return SHF_OK;
+}
+
+int seg_admm_batch_sync(seg_batch* b) {
+  if (!b) return fail(SHF_ERR_ARG, "batch is NULL");
+  SHF_CK(cudaStreamSynchronize(b->stream));
+  return SHF_OK;
+}
+
+int seg_admm_batch_destroy(seg_batch* b) {
+  if (!b) return SHF_OK;
+  free_batch(b);
+  return SHF_OK;
+}
+
 int seg_admm_sync(seg_state* st) {
   if (!st) return fail(SHF_ERR_ARG, "state is NULL");
   SHF_CK(cudaStreamSynchronize(st->stream));

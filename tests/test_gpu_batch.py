@@ -1,0 +1,89 @@
+"""GPU: batched solves of independent images of uneven sizes (one CUDA graph
+per iteration, one branch per image) against single-image runs and the oracle."""
+
+import numpy as np
+import pytest
+
+from paper_1112_1805_gb300 import synth
+from tests.gpu_util import labels_agree, need_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _images(shapes, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for H, W, K, J, C in shapes:
+        if C == 1:
+            cb = np.array([[0.2 + 0.6 * k / (K - 1)] for k in range(K)])
+        else:
+            cb = np.array([[a, b, c] for a in (0.2, 0.8) for b in (0.2, 0.8) for c in (0.2, 0.8)])[:K]
+        img, lab = synth.ellipse_image(H, W, cb, rng, n_ellipses=4)
+        out.append((img.astype(np.float32), cb, synth.scale_weights(0.1, J)))
+    return out
+
+
+def _single(torch, img, cb, Lam, T):
+    from paper_1112_1805_gb300 import binding as B
+    from paper_1112_1805_gb300.api import FilterBank, ShearletSegmenter
+
+    fb = FilterBank(img.shape[1], img.shape[2], len(Lam) - 1)
+    seg = ShearletSegmenter(fb, torch.tensor(img, device="cuda"), cb, Lam, 1.0)
+    seg.step(T)
+    seg.synchronize()
+    out = {k: seg.get(getattr(B, "SEG_" + k.upper())).cpu().numpy() for k in ("u", "w", "bv")}
+    seg.close()
+    fb.close()
+    return out
+
+
+def test_batch_equals_single_runs_and_oracle(oracle_mod):
+    torch = need_cuda()
+    from paper_1112_1805_gb300 import binding as B
+    from paper_1112_1805_gb300.api import ShearletBatch
+
+    shapes = [(64, 96, 2, 2, 1), (48, 80, 3, 1, 1), (32, 32, 4, 2, 1), (40, 64, 3, 2, 3), (30, 50, 5, 2, 1)]
+    data = _images(shapes, 42)
+    T = 25
+    batch = ShearletBatch([torch.tensor(d[0], device="cuda") for d in data], [d[1] for d in data],
+                          [d[2] for d in data], 1.0)
+    batch.step(T)
+    batch.synchronize()
+    for i, (img, cb, Lam) in enumerate(data):
+        view = batch.image(i)
+        got = {k: view.get(getattr(B, "SEG_" + k.upper())).cpu().numpy() for k in ("u", "w", "bv")}
+        ref = _single(torch, img, cb, Lam, T)
+        for k in got:  # same kernels in the same order: bit-identical
+            assert np.array_equal(got[k], ref[k]), (i, k)
+        o = oracle_mod.admm_run(img.astype(np.float64), cb.astype(np.float32).astype(np.float64), len(Lam) - 1,
+                                Lam.astype(np.float32).astype(np.float64), 1.0, T)
+        assert np.abs(got["u"] - o["u"]).max() <= 1e-4, i
+        lab = view.labels().cpu().numpy()
+        assert labels_agree(lab, o["labels"], o["gap"]), i
+    assert int(batch.image(0).get(B.SEG_ITER)) == T
+    batch.close()
+
+
+def test_uneven_batch_shapes_first_iterations():
+    # the uneven batch of the batched workload (384 x 640 first, sides from
+    # 128 to 1024, K from 2 to 6, J = floor(log2(min side)/2)), first 12 images
+    torch = need_cuda()
+    from paper_1112_1805_gb300 import binding as B
+    from paper_1112_1805_gb300.api import ShearletBatch
+
+    shp = synth.batch_shapes()[:12]
+    data = _images([(H, W, K, J, 1) for H, W, K, J in shp], synth.seed_for(3))
+    T = 3
+    batch = ShearletBatch([torch.tensor(d[0], device="cuda") for d in data], [d[1] for d in data],
+                          [d[2] for d in data], 1.0)
+    batch.step(T)
+    batch.synchronize()
+    for i in (0, 1, 5, 11):
+        img, cb, Lam = data[i]
+        ref = _single(torch, img, cb, Lam, T)
+        got = batch.image(i).get(B.SEG_U).cpu().numpy()
+        assert np.array_equal(got, ref["u"]), i
+    for i in range(len(data)):
+        w = batch.image(i).get(B.SEG_W)
+        assert float(w.min()) >= 0 and float((w.sum(0) - 1).abs().max()) < 1e-5
+    batch.close()

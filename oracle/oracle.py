@@ -24,7 +24,7 @@ __all__ = [
     "build", "lib", "set_threads", "get_threads", "num_filters", "window", "filter_specs",
     "filters", "filters_unsymmetrised", "fft2", "dft2_brute", "analyze", "synthesize",
     "data_term", "soft_shrink", "project_simplex", "admm_iterate", "admm_run", "energy",
-    "labels", "thresholds", "zero_state",
+    "labels", "thresholds", "zero_state", "unrolled_vjp", "ce_loss", "unrolled_grads",
 ]
 
 
@@ -65,6 +65,7 @@ def lib():
                 "oracle_admm_iterate": (c_int, [c_int, c_int, c_int, c_int, D, D, c_double, c_int,
                                                 D, D, D, D, D, D, c_int]),
                 "oracle_energy": (c_int, [c_int, c_int, c_int, c_int, D, D, D, D]),
+                "oracle_unrolled_vjp": (c_int, [c_int, c_int, c_int, c_int, D, D, c_double, c_int, D, D, D, D]),
                 "oracle_labels": (c_int, [c_int, c_int, c_int, D, I, D]),
             }
             for name, (res, args) in sig.items():
@@ -277,3 +278,51 @@ def labels(x):
     _check(lib().oracle_labels(H, W, K, _d(x), lab.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _d(gap)),
            "labels")
     return lab, gap
+
+
+def unrolled_vjp(s, J: int, Lambda, gamma: float, T: int, wbar_T):
+    """Reverse mode of T ADMM iterations from the zero state (see the C++
+    comment): returns (w_T, sbar, Lambar) for the adjoint wbar_T of w_T."""
+    s = _f64(s)
+    K, H, W = s.shape
+    Lam = _f64(Lambda)
+    wb = _f64(wbar_T)
+    sbar = np.empty_like(s)
+    lb = np.empty(J + 1)
+    wT = np.empty_like(s)
+    _check(lib().oracle_unrolled_vjp(H, W, J, K, _d(s), _d(Lam), float(gamma), int(T), _d(wb), _d(sbar), _d(lb),
+                                     _d(wT)), "unrolled_vjp")
+    return wT, sbar, lb
+
+
+def ce_loss(w, labels, eps: float = 1e-6):
+    """Cross entropy of the relaxed labelling against a label map:
+    -mean_x log(max(w[label(x)](x), eps)); returns (loss, dL/dw)."""
+    w = _f64(w)
+    K, H, W = w.shape
+    P = H * W
+    lab = np.asarray(labels)
+    wl = np.take_along_axis(w, lab[None].astype(np.int64), axis=0)[0]
+    loss = -np.log(np.maximum(wl, eps)).mean()
+    g = np.zeros_like(w)
+    gl = np.where(wl > eps, -1.0 / (P * np.maximum(wl, eps)), 0.0)
+    np.put_along_axis(g, lab[None].astype(np.int64), gl[None], axis=0)
+    return loss, g
+
+
+def unrolled_grads(f, codebook, J: int, Lambda, gamma: float, T: int, labels, eps: float = 1e-6):
+    """Loss and gradients of the unrolled solve: d/dcodebook [K][C], d/dLambda
+    [J+1] and d/df [C][H][W], through s[k] = sum_ch (f[ch] - c[k][ch])^2."""
+    f = _f64(f)
+    if f.ndim == 2:
+        f = f[None]
+    cb = _f64(codebook).reshape(-1, f.shape[0])
+    s = data_term(f, cb)
+    st = zero_state(s.shape[0], J, s.shape[1], s.shape[2])
+    admm_iterate(st, s, J, Lambda, gamma, T)
+    loss, wbar = ce_loss(st["w"], labels, eps)
+    wT, sbar, lbar = unrolled_vjp(s, J, Lambda, gamma, T, wbar)
+    diff = f[None] - cb[:, :, None, None]                       # [K][C][H][W]
+    dcb = (sbar[:, None] * (-2.0) * diff).sum(axis=(2, 3))
+    df = (sbar[:, None] * 2.0 * diff).sum(axis=0)
+    return {"loss": loss, "w": wT, "codebook": dcb, "Lambda": lbar, "f": df, "sbar": sbar}

@@ -660,6 +660,111 @@ int oracle_admm_iterate(int H, int W, int J, int K, const double* s, const doubl
   return 0;
 }
 
+// Reverse mode of T iterations of oracle_admm_iterate from the zero state
+// (the unrolled solve), for a given adjoint wbar_T of the final w.  Each
+// iteration maps (b_v, Q = S^T(v - b_v), w, b_w) to its successor:
+//   u = (Q + w - b_w - gamma s)/2,  g = b_v + S u,  b_v' = clip(g, t_f),
+//   Q' = S^T (g - 2 clip(g, t_f)),  g_w = b_w + u,  w' = P_C(g_w),  b_w' = g_w - w',
+// with t_f = gamma Lambda_{j(f)}.  Going backwards through one iteration:
+//   gbar_w = bwbar' + J_P (wbar' - bwbar')   (J_P: projection onto the active
+//            face, x_A - mean_A(x) on the support A of w', 0 elsewhere)
+//   dbar = S Qbar'
+//   gbar = dbar (1 - 2 m) + bvbar' m          (m = [|g| < t_f])
+//   tbar_f += sum sign(g) (1 - m) (bvbar' - 2 dbar)
+//   ubar = gbar_w + S^T gbar
+//   Qbar = ubar/2, wbar = ubar/2, bwbar = gbar_w - ubar/2, bvbar = gbar,
+//   sbar += -gamma ubar / 2.
+// Outputs: sbar [K][H][W] (adjoint of the data term) and Lambar [J+1]
+// (Lambar_j = gamma * sum of tbar_f over the filters of weight j).  The
+// forward states are kept for all T iterations (test sizes only).
+int oracle_unrolled_vjp(int H, int W, int J, int K, const double* s, const double* Lambda, double gamma, int T,
+                        const double* wbar_T, double* sbar, double* Lambar, double* wT_out) {
+  if (H < 2 || W < 2 || J < 1 || K < 1 || T < 1 || !(gamma > 0.0)) return -1;
+  Transform Tr(H, W, J);
+  const int eta = Tr.eta;
+  const size_t P = Tr.P(), KP = static_cast<size_t>(K) * P, NC = static_cast<size_t>(K) * eta * P;
+  const auto specs = filter_list(J);
+  std::vector<double> thr(eta);
+  for (int f = 0; f < eta; ++f) thr[f] = gamma * (specs[f].kind == 0 ? Lambda[0] : Lambda[specs[f].j + 1]);
+  // forward, recording g (per coefficient) and w' (per pixel) of every iteration
+  std::vector<double> bv(NC, 0.0), Q(KP, 0.0), w(KP, 0.0), bw(KP, 0.0), u(KP), c(NC), d(NC);
+  std::vector<std::vector<double>> G(T), Wn(T);
+  for (int it = 0; it < T; ++it) {
+    for (size_t i = 0; i < KP; ++i) u[i] = 0.5 * (Q[i] + w[i] - bw[i] - gamma * s[i]);
+    analyze_many(Tr, u.data(), K, c.data());
+    G[it].resize(NC);
+    for (int k = 0; k < K; ++k)
+      for (int f = 0; f < eta; ++f) {
+        const size_t base = (static_cast<size_t>(k) * eta + f) * P;
+        for (size_t r = 0; r < P; ++r) {
+          const double g = bv[base + r] + c[base + r];
+          const double cl = std::min(std::max(g, -thr[f]), thr[f]);
+          G[it][base + r] = g;
+          bv[base + r] = cl;
+          d[base + r] = g - 2.0 * cl;
+        }
+      }
+    synthesize_many(Tr, d.data(), K, Q.data());
+    std::vector<double> gw(K), x(K);
+    for (size_t r = 0; r < P; ++r) {
+      for (int k = 0; k < K; ++k) gw[k] = bw[k * P + r] + u[k * P + r];
+      project_simplex_sort(gw.data(), K, x.data());
+      for (int k = 0; k < K; ++k) {
+        w[k * P + r] = x[k];
+        bw[k * P + r] = gw[k] - x[k];
+      }
+    }
+    Wn[it] = w;
+  }
+  if (wT_out) std::copy(w.begin(), w.end(), wT_out);
+  // reverse
+  std::vector<double> bvb(NC, 0.0), Qb(KP, 0.0), wb(wbar_T, wbar_T + KP), bwb(KP, 0.0), gwb(KP), ub(KP), db(NC),
+      st(KP), tb(eta, 0.0);
+  std::fill(sbar, sbar + KP, 0.0);
+  for (int it = T - 1; it >= 0; --it) {
+    const std::vector<double>& wn = Wn[it];
+    for (size_t r = 0; r < P; ++r) {
+      int q = 0;
+      double mean = 0.0;
+      for (int k = 0; k < K; ++k)
+        if (wn[k * P + r] > 0.0) {
+          ++q;
+          mean += wb[k * P + r] - bwb[k * P + r];
+        }
+      mean /= q;
+      for (int k = 0; k < K; ++k) {
+        const double a = wb[k * P + r] - bwb[k * P + r];
+        gwb[k * P + r] = bwb[k * P + r] + (wn[k * P + r] > 0.0 ? a - mean : 0.0);
+      }
+    }
+    analyze_many(Tr, Qb.data(), K, db.data());
+    for (int k = 0; k < K; ++k)
+      for (int f = 0; f < eta; ++f) {
+        const size_t base = (static_cast<size_t>(k) * eta + f) * P;
+        double acc = 0.0;
+        for (size_t r = 0; r < P; ++r) {
+          const double g = G[it][base + r];
+          const bool inside = std::fabs(g) < thr[f];
+          const double gb = inside ? bvb[base + r] - db[base + r] : db[base + r];
+          if (!inside) acc += (g > 0 ? 1.0 : -1.0) * (bvb[base + r] - 2.0 * db[base + r]);
+          bvb[base + r] = gb;
+        }
+        tb[f] += acc;
+      }
+    synthesize_many(Tr, bvb.data(), K, st.data());
+    for (size_t i = 0; i < KP; ++i) {
+      ub[i] = gwb[i] + st[i];
+      Qb[i] = 0.5 * ub[i];
+      wb[i] = 0.5 * ub[i];
+      bwb[i] = gwb[i] - 0.5 * ub[i];
+      sbar[i] += -0.5 * gamma * ub[i];
+    }
+  }
+  for (int j = 0; j <= J; ++j) Lambar[j] = 0.0;
+  for (int f = 0; f < eta; ++f) Lambar[specs[f].kind == 0 ? 0 : specs[f].j + 1] += gamma * tb[f];
+  return 0;
+}
+
 // Energy of eq. problemSegmentation at x: <x, s> + sum_f Lambda_{j(f)} ||(S x)_f||_1.
 int oracle_energy(int H, int W, int J, int K, const double* x, const double* s, const double* Lambda, double* energy) {
   if (H < 2 || W < 2 || J < 1 || K < 1) return -1;

@@ -201,6 +201,24 @@ int seg_admm_set(seg_state* st, int what, const void* src, int src_on_host);
 int seg_admm_save(seg_state* st, const char* path);
 int seg_admm_load(seg_state* st, const char* path);
 
+/* ---------------------------------------------------------------------------
+ * Unrolled solve for differentiation.  The iteration is the one above; its
+ * reverse mode is not in the paper (it follows from the iteration map: the
+ * Jacobian of the simplex projection on the active face, the 0/1 masks of the
+ * clipping |g| < gamma Lambda, and S / S^T exchanged).
+ * seg_admm_unrolled_fwd returns the state to v = b_v = w = b_w = 0, runs T
+ * iterations on the general-size kernels and keeps the state of every
+ * ckpt_every-th iteration on the device.  seg_admm_unrolled_bwd takes dL/dw_T
+ * (device [K][H][W]) of a loss of the final w, recomputes each segment from
+ * its checkpoint, runs the adjoint iterations backwards and returns
+ * dL/dcodebook (HOST [K][C]), dL/dLambda (HOST [J+1]), and optionally dL/df
+ * (device [C][H][W]) and dL/ds (device [K][H][W]).  It synchronises and leaves
+ * the state at an intermediate iterate.  Errors: SHF_ERR_STATE when the
+ * forward has not run, SHF_ERR_OOM, SHF_ERR_CUDA. */
+int seg_admm_unrolled_fwd(seg_state* st, int T, int ckpt_every);
+int seg_admm_unrolled_bwd(seg_state* st, const float* dL_dw, float* dL_dcodebook, float* dL_dLambda, float* dL_df,
+                          float* dL_ds);
+
 /* Instrumentation (no counterpart in the paper): time spent in each kind of
  * kernel during the most recent iteration, measured by CUDA events recorded
  * on the state's stream before every launch (event nodes inside the replayed

@@ -249,3 +249,47 @@ class ShearletBatch:
     def image(self, i: int) -> ShearletSegmenter:
         H, W, K, C, J = self.shapes[i]
         return _BorrowedState(B.seg_admm_batch_image(self.handle, i), K, C, H, W, 2 ** (J + 2) - 3)
+
+
+class UnrolledSegmentation(torch.autograd.Function):
+    """w_T of T ADMM iterations from the zero state as a differentiable function
+    of the image f [C, H, W], the codebook [K, C] and the weights Lambda [J+1]
+    (the forward keeps every ckpt_every-th state; the backward recomputes the
+    segments and runs the adjoint iterations in libshearseg.so)."""
+
+    @staticmethod
+    def forward(ctx, f, codebook, Lambda, bank, gamma, T, ckpt_every):
+        f3 = (f.unsqueeze(0) if f.dim() == 2 else f).detach().contiguous()
+        cb = codebook.detach().double().cpu().numpy().reshape(-1, f3.shape[0])
+        lam = Lambda.detach().double().cpu().tolist()
+        seg = ShearletSegmenter(bank, f3, cb, lam, float(gamma))
+        B.seg_admm_unrolled_fwd(seg.handle, int(T), int(ckpt_every))
+        w = seg.get(B.SEG_W)
+        ctx.seg, ctx.fdim, ctx.shape = seg, f.dim(), tuple(f3.shape)
+        ctx.K, ctx.C, ctx.J = cb.shape[0], cb.shape[1], len(lam) - 1
+        ctx.cb_meta = (codebook.dtype, codebook.device, tuple(codebook.shape))
+        ctx.lam_meta = (Lambda.dtype, Lambda.device)
+        return w
+
+    @staticmethod
+    def backward(ctx, grad_w):
+        seg = ctx.seg
+        gw = grad_w.detach().to(device="cuda", dtype=torch.float32).contiguous()
+        seg.stream.wait_stream(torch.cuda.current_stream())
+        fbar = torch.empty(ctx.shape, dtype=torch.float32, device="cuda") if ctx.needs_input_grad[0] else None
+        dc, dl = B.seg_admm_unrolled_bwd(seg.handle, gw.data_ptr(), ctx.K, ctx.C, ctx.J,
+                                         fbar.data_ptr() if fbar is not None else 0)
+        cdt, cdev, cshape = ctx.cb_meta
+        ldt, ldev = ctx.lam_meta
+        gcb = torch.tensor(dc, dtype=cdt, device=cdev).reshape(cshape)
+        glam = torch.tensor(dl, dtype=ldt, device=ldev)
+        if fbar is not None and ctx.fdim == 2:
+            fbar = fbar[0]
+        seg.close()
+        return fbar, gcb, glam, None, None, None, None
+
+
+def unrolled_segmentation(f, codebook, Lambda, bank: FilterBank, gamma: float = 1.0, T: int = 50,
+                          ckpt_every: int = 10):
+    """Differentiable w_T (see UnrolledSegmentation)."""
+    return UnrolledSegmentation.apply(f, codebook, Lambda, bank, gamma, T, ckpt_every)

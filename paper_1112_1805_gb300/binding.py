@@ -78,6 +78,9 @@ _SIG = {
     "seg_admm_batch_image": (_I, [_VP, _I, ctypes.POINTER(_VP)]),
     "seg_admm_batch_sync": (_I, [_VP]),
     "seg_admm_batch_destroy": (_I, [_VP]),
+    "seg_admm_unrolled_fwd": (_I, [_VP, _I, _I]),
+    "seg_admm_unrolled_bwd": (_I, [_VP, _VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _VP,
+                                   _VP]),
     "seg_admm_sync": (_I, [_VP]),
     "seg_admm_destroy": (_I, [_VP]),
 }
@@ -262,3 +265,18 @@ def seg_admm_batch_sync(batch: int) -> None:
 
 def seg_admm_batch_destroy(batch: int) -> None:
     _call("seg_admm_batch_destroy", _VP(batch))
+
+
+def seg_admm_unrolled_fwd(state: int, T: int, ckpt_every: int) -> None:
+    _call("seg_admm_unrolled_fwd", _VP(state), int(T), int(ckpt_every))
+
+
+def seg_admm_unrolled_bwd(state: int, dL_dw: int, K: int, C: int, J: int, dL_df: int = 0, dL_ds: int = 0):
+    """Returns (dL/dcodebook [K*C], dL/dLambda [J+1]) as Python lists; dL_df and
+    dL_ds are optional device pointers that receive the image and data-term
+    adjoints."""
+    dc = (ctypes.c_float * (K * C))()
+    dl = (ctypes.c_float * (J + 1))()
+    _call("seg_admm_unrolled_bwd", _VP(state), _VP(dL_dw), dc, dl, _VP(dL_df) if dL_df else None,
+          _VP(dL_ds) if dL_ds else None)
+    return list(dc), list(dl)

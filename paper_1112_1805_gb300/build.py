@@ -1,6 +1,6 @@
 """Builds the sm_103a shared library libshearseg.so in-tree with nvcc.
 
-The three translation units are compiled in parallel and linked into
+The translation units in SOURCES are compiled in parallel and linked into
 ``paper_1112_1805_gb300/libshearseg.so`` (static CUDA runtime, so the library
 loads on machines without a GPU; compute calls then fail with SHF_ERR_CUDA).
 """
@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libshearseg.so")
-SOURCES = ["shf_bank.cu", "shf_transform.cu", "shf_fast.cu", "shf_capi.cu", "shf_noalloc.cu"]
+SOURCES = ["shf_bank.cu", "shf_transform.cu", "shf_fast.cu", "shf_adjoint.cu", "shf_capi.cu", "shf_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -104,6 +104,13 @@ struct seg_state {
   int kinds[kMaxMarks] = {};
   int nmarks = 0;
   bool marks_ok = true;
+  // unrolled mode (reverse-mode differentiation): generic-path scratch and
+  // the states kept every un_ck iterations
+  int un_T = 0, un_ck = 0;
+  float2* un_Y = nullptr;        // [K][eta][H][Wh]
+  float2* un_partial = nullptr;  // [groups][K][H][Wh]
+  std::vector<float*> ck_bv, ck_w, ck_bw;
+  std::vector<float2*> ck_T;
   long long iter = 0;
   size_t P() const { return static_cast<size_t>(g.H) * g.W; }
   size_t Ph() const { return static_cast<size_t>(g.H) * g.Wh; }
@@ -263,6 +270,12 @@ void free_state(seg_state* s) {
   cudaFree(s->d_filters);
   cudaFree(s->d_tile_begin);
   cudaFree(s->d_tile_slots);
+  cudaFree(s->un_Y);
+  cudaFree(s->un_partial);
+  for (float* p : s->ck_bv) cudaFree(p);
+  for (float* p : s->ck_w) cudaFree(p);
+  for (float* p : s->ck_bw) cudaFree(p);
+  for (float2* p : s->ck_T) cudaFree(p);
   float* fl[] = {s->f, s->s, s->bv, s->w, s->bw, s->u, s->stv, s->thr, s->lam, s->gap};
   for (float* p : fl) cudaFree(p);
   cudaFree(s->Ur);
@@ -341,6 +354,21 @@ cudaError_t enqueue_iteration(seg_state* st) {
     if (e == cudaSuccess) e = shf::run_col_reduce_inv(g, st->partial, st->T, st->K, st->groups, s);
   }
   hook.mark(shf::kKindEnd);
+  return e;
+}
+
+// One iteration on the generic kernels with the full coefficient scratch of
+// the unrolled mode; gout (optional) records g = b_v + S u.
+cudaError_t enqueue_generic_iteration(seg_state* st, float* gout) {
+  const Geo& g = st->g;
+  const float scale = 1.f / (static_cast<float>(g.H) * g.W);
+  cudaStream_t s = st->stream;
+  cudaError_t e =
+      shf::run_row_ustep(g, st->T, st->s, st->w, st->bw, st->u, st->Ur, nullptr, st->K, st->gamma, scale, s);
+  if (e == cudaSuccess) e = shf::run_col_fan(g, st->Ur, st->un_Y, st->K, st->groups, s);
+  if (e == cudaSuccess) e = shf::run_row_shrink(g, st->un_Y, st->bv, st->thr, st->K * g.eta, scale, s, gout);
+  if (e == cudaSuccess) e = shf::run_col_gather(g, st->un_Y, st->un_partial, st->K, st->groups, s);
+  if (e == cudaSuccess) e = shf::run_col_reduce_inv(g, st->un_partial, st->T, st->K, st->groups, s);
   return e;
 }
 
@@ -763,6 +791,139 @@ int seg_admm_load(seg_state* st, const char* path) {
   }
   std::fclose(fp);
   st->iter = h.iter;
+  return SHF_OK;
+}
+
+int seg_admm_unrolled_fwd(seg_state* st, int T, int ckpt_every) {
+  if (!st || T < 1 || ckpt_every < 1) return fail(SHF_ERR_ARG, "seg_admm_unrolled_fwd: bad argument");
+  const Geo& g = st->g;
+  const size_t P = st->P(), Ph = st->Ph(), KP = P * st->K, NC = KP * g.eta;
+  int rc;
+  if (!st->un_Y && ((rc = dev_alloc(&st->un_Y, Ph * st->K * g.eta, "unrolled scratch")) ||
+                    (rc = dev_alloc(&st->un_partial, Ph * st->K * st->groups, "unrolled partials"))))
+    return rc;
+  const int nseg = (T + ckpt_every - 1) / ckpt_every;
+  while (static_cast<int>(st->ck_bv.size()) < nseg) {
+    float *bv = nullptr, *w = nullptr, *bw = nullptr;
+    float2* Tt = nullptr;
+    if ((rc = dev_alloc(&bv, NC, "checkpoint")) || (rc = dev_alloc(&w, KP, "checkpoint")) ||
+        (rc = dev_alloc(&bw, KP, "checkpoint")) || (rc = dev_alloc(&Tt, Ph * st->K, "checkpoint"))) {
+      cudaFree(bv);
+      cudaFree(w);
+      cudaFree(bw);
+      cudaFree(Tt);
+      return rc;
+    }
+    st->ck_bv.push_back(bv);
+    st->ck_w.push_back(w);
+    st->ck_bw.push_back(bw);
+    st->ck_T.push_back(Tt);
+  }
+  cudaStream_t s = st->stream;
+  SHF_CK(cudaMemsetAsync(st->bv, 0, sizeof(float) * NC, s));
+  SHF_CK(cudaMemsetAsync(st->w, 0, sizeof(float) * KP, s));
+  SHF_CK(cudaMemsetAsync(st->bw, 0, sizeof(float) * KP, s));
+  SHF_CK(cudaMemsetAsync(st->u, 0, sizeof(float) * KP, s));
+  SHF_CK(cudaMemsetAsync(st->T, 0, sizeof(float2) * Ph * st->K, s));
+  for (int i = 0; i < T; ++i) {
+    if (i % ckpt_every == 0) {
+      const int c = i / ckpt_every;
+      SHF_CK(cudaMemcpyAsync(st->ck_bv[c], st->bv, sizeof(float) * NC, cudaMemcpyDeviceToDevice, s));
+      SHF_CK(cudaMemcpyAsync(st->ck_w[c], st->w, sizeof(float) * KP, cudaMemcpyDeviceToDevice, s));
+      SHF_CK(cudaMemcpyAsync(st->ck_bw[c], st->bw, sizeof(float) * KP, cudaMemcpyDeviceToDevice, s));
+      SHF_CK(cudaMemcpyAsync(st->ck_T[c], st->T, sizeof(float2) * Ph * st->K, cudaMemcpyDeviceToDevice, s));
+    }
+    SHF_CK(enqueue_generic_iteration(st, nullptr));
+  }
+  st->iter = T;
+  st->un_T = T;
+  st->un_ck = ckpt_every;
+  return SHF_OK;
+}
+
+int seg_admm_unrolled_bwd(seg_state* st, const float* dL_dw, float* dL_dcodebook, float* dL_dLambda, float* dL_df,
+                          float* dL_ds) {
+  if (!st || !dL_dw || !dL_dcodebook || !dL_dLambda) return fail(SHF_ERR_ARG, "seg_admm_unrolled_bwd: NULL argument");
+  if (st->un_T < 1) return fail(SHF_ERR_STATE, "seg_admm_unrolled_fwd has not run");
+  const Geo& g = st->g;
+  const int K = st->K, C = st->C, eta = g.eta, T = st->un_T, ck = st->un_ck;
+  const size_t P = st->P(), Ph = st->Ph(), KP = P * K, NC = KP * eta;
+  const float scale = 1.f / (static_cast<float>(g.H) * g.W);
+  cudaStream_t s = st->stream;
+  const int nblk = shf::adj_part_blocks();
+  // one allocation for every temporary of the sweep
+  const size_t nf = NC * 2 + KP * 7 + static_cast<size_t>(ck) * (NC + KP);
+  const size_t nc2 = Ph * K * 2;
+  const size_t nd = static_cast<size_t>(K) * eta * nblk + eta + static_cast<size_t>(K) * C * (nblk + 1);
+  char* mem = nullptr;
+  SHF_CK(cudaMallocAsync(reinterpret_cast<void**>(&mem), sizeof(float) * nf + sizeof(float2) * nc2 + sizeof(double) * nd,
+                         s));
+  float* fp = reinterpret_cast<float*>(mem);
+  float *bvbar = fp, *dbar = fp + NC;
+  fp += 2 * NC;
+  float *Qbar = fp, *wbar = fp + KP, *bwbar = fp + 2 * KP, *sbar = fp + 3 * KP, *gwbar = fp + 4 * KP,
+        *stv = fp + 5 * KP, *fbar_unused = fp + 6 * KP;
+  (void)fbar_unused;
+  fp += 7 * KP;
+  float* grec = fp;
+  float* wrec = fp + static_cast<size_t>(ck) * NC;
+  float2* Uw = reinterpret_cast<float2*>(mem + sizeof(float) * nf);
+  float2* Tt = Uw + Ph * K;
+  double* dp = reinterpret_cast<double*>(mem + sizeof(float) * nf + sizeof(float2) * nc2);
+  double *tpart = dp, *tbar = dp + static_cast<size_t>(K) * eta * nblk, *cbpart = tbar + eta,
+         *cbout = cbpart + static_cast<size_t>(K) * C * nblk;
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+    return e == cudaSuccess;
+  };
+  ok(cudaMemsetAsync(bvbar, 0, sizeof(float) * NC, s));
+  ok(cudaMemsetAsync(Qbar, 0, sizeof(float) * KP, s));
+  ok(cudaMemsetAsync(bwbar, 0, sizeof(float) * KP, s));
+  ok(cudaMemsetAsync(sbar, 0, sizeof(float) * KP, s));
+  ok(cudaMemsetAsync(tbar, 0, sizeof(double) * eta, s));
+  ok(cudaMemcpyAsync(wbar, dL_dw, sizeof(float) * KP, cudaMemcpyDeviceToDevice, s));
+  const int nseg = (T + ck - 1) / ck;
+  for (int seg = nseg - 1; seg >= 0 && e == cudaSuccess; --seg) {
+    const int n = std::min(ck, T - seg * ck);
+    ok(cudaMemcpyAsync(st->bv, st->ck_bv[seg], sizeof(float) * NC, cudaMemcpyDeviceToDevice, s));
+    ok(cudaMemcpyAsync(st->w, st->ck_w[seg], sizeof(float) * KP, cudaMemcpyDeviceToDevice, s));
+    ok(cudaMemcpyAsync(st->bw, st->ck_bw[seg], sizeof(float) * KP, cudaMemcpyDeviceToDevice, s));
+    ok(cudaMemcpyAsync(st->T, st->ck_T[seg], sizeof(float2) * Ph * K, cudaMemcpyDeviceToDevice, s));
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {  // recompute the segment, recording g and w'
+      ok(enqueue_generic_iteration(st, grec + static_cast<size_t>(i) * NC));
+      ok(cudaMemcpyAsync(wrec + static_cast<size_t>(i) * KP, st->w, sizeof(float) * KP, cudaMemcpyDeviceToDevice, s));
+    }
+    for (int i = n - 1; i >= 0 && e == cudaSuccess; --i) {
+      ok(shf::launch_adj_proj(wrec + static_cast<size_t>(i) * KP, wbar, bwbar, gwbar, K, static_cast<int>(P), s));
+      // dbar = S Qbar
+      ok(shf::run_row_r2c(g, Qbar, Uw, K, 1.f, s));
+      ok(shf::run_col_fan(g, Uw, st->un_Y, K, st->groups, s));
+      ok(shf::run_row_c2r(g, st->un_Y, dbar, K * eta, scale, s));
+      ok(shf::launch_adj_shrink(grec + static_cast<size_t>(i) * NC, dbar, bvbar, st->thr, K, eta,
+                                static_cast<long>(P), tpart, tbar, s));
+      // stv = S^T bvbar
+      ok(shf::run_row_r2c(g, bvbar, st->un_Y, K * eta, 1.f, s));
+      ok(shf::run_col_gather(g, st->un_Y, st->un_partial, K, st->groups, s));
+      ok(shf::run_col_reduce_inv(g, st->un_partial, Tt, K, st->groups, s));
+      ok(shf::run_row_c2r(g, Tt, stv, K, scale, s));
+      ok(shf::launch_adj_u(gwbar, stv, Qbar, wbar, bwbar, sbar, st->gamma, static_cast<long>(KP), s));
+    }
+  }
+  ok(shf::adj_codebook(sbar, st->f, st->codebook.data(), K, C, static_cast<long>(P), cbpart, cbout, dL_df, s));
+  if (dL_ds) ok(cudaMemcpyAsync(dL_ds, sbar, sizeof(float) * KP, cudaMemcpyDeviceToDevice, s));
+  std::vector<double> th(eta), cb(static_cast<size_t>(K) * C);
+  ok(cudaMemcpyAsync(th.data(), tbar, sizeof(double) * eta, cudaMemcpyDeviceToHost, s));
+  ok(cudaMemcpyAsync(cb.data(), cbout, sizeof(double) * K * C, cudaMemcpyDeviceToHost, s));
+  ok(cudaFreeAsync(mem, s));
+  ok(cudaStreamSynchronize(s));
+  if (e != cudaSuccess) return fail(SHF_ERR_CUDA, std::string("seg_admm_unrolled_bwd: ") + cudaGetErrorString(e));
+  std::vector<shf::FilterDesc> d(eta);
+  shf::filter_descs(g.J, d.data());
+  std::vector<double> lam(g.J + 1, 0.0);
+  for (int f = 0; f < eta; ++f) lam[d[f].kind == 0 ? 0 : d[f].j + 1] += st->gamma * th[f];
+  for (int j = 0; j <= g.J; ++j) dL_dLambda[j] = static_cast<float>(lam[j]);
+  for (int i = 0; i < K * C; ++i) dL_dcodebook[i] = static_cast<float>(cb[i]);
   return SHF_OK;
 }
 

@@ -65,8 +65,9 @@ cudaError_t run_row_r2c(const Geo& g, const float* in, float2* out, int planes, 
 // Half spectra -> real rows, times `scale`.
 cudaError_t run_row_c2r(const Geo& g, const float2* in, float* out, int planes, float scale, cudaStream_t st);
 // ADMM v-step on coefficient spectra Y [nch*eta][H][Wh] (in place) and b_v.
+// gout (optional): receives g = b_v + S u before the clipping, [planes][H][W].
 cudaError_t run_row_shrink(const Geo& g, float2* Y, float* bv, const float* thr, int planes, float scale,
-                           cudaStream_t st);
+                           cudaStream_t st, float* gout = nullptr);
 // sum_f lam[f] * ||ifft rows of Y_f||_1 into partial[nblocks] (nblocks returned).
 cudaError_t run_row_l1(const Geo& g, const float2* Y, const float* lam, int planes, float scale, double* partial,
                        int* nblocks, cudaStream_t st);
@@ -147,6 +148,24 @@ cudaError_t run_fast_iteration_body(const Geo& g, const FastPlan& plan, const fl
 // (ranges_host[eta]); returns the host arrays to upload.
 void build_fast_plan(const Geo& g, const int2* ranges_host, FastPlan* plan, std::vector<ChunkDesc>* chunks,
                      std::vector<int>* filters, std::vector<int>* tile_begin, std::vector<int>* tile_slots);
+
+// Reverse mode of the unrolled iteration (shf_adjoint.cu).
+// gwbar = bwbar + J_P(wbar - bwbar), J_P the projection onto the face of the
+// simplex where w' > 0.
+cudaError_t launch_adj_proj(const float* wn, const float* wbar, const float* bwbar, float* gwbar, int K, int P,
+                            cudaStream_t st);
+// bvbar <- dbar (1 - 2m) + bvbar m with m = [|g| < t_f]; per-filter sums of
+// sign(g)(1 - m)(bvbar - 2 dbar) accumulated (fixed order, FP64) into tbar[eta].
+cudaError_t launch_adj_shrink(const float* g, const float* dbar, float* bvbar, const float* thr, int K, int eta,
+                              long P, double* tpart, double* tbar, cudaStream_t st);
+// ub = gwbar + st; Qbar = ub/2; wbar = ub/2; bwbar = gwbar - ub/2; sbar += -gamma ub/2.
+cudaError_t launch_adj_u(const float* gwbar, const float* st_, float* Qbar, float* wbar, float* bwbar, float* sbar,
+                         float gamma, long n, cudaStream_t st);
+// dL/dc[k][ch] = sum_x sbar_k (-2)(f_ch - c_k,ch) (FP64, fixed order) into
+// out_host; dL/df (optional, device) = sum_k sbar_k 2 (f_ch - c_k,ch).
+cudaError_t adj_codebook(const float* sbar, const float* f, const float* codebook_host, int K, int C, long P,
+                         double* part, double* out_dev, float* fbar, cudaStream_t st);
+int adj_part_blocks();
 
 // C ABI layer (shf_capi.cu): the geometry and device tables of a bank, and the
 // thread-local message behind shf_last_error() (returns code).

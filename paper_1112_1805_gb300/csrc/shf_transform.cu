@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kRowThreads)
 // d (= v - b_v of the new iterate) is transformed back in place.
 __global__ void __launch_bounds__(kRowThreads)
     k_row_shrink(float2* __restrict__ Y, float* __restrict__ bv, const float* __restrict__ thr, int eta, int H, int L,
-                 int RB, FftPlan pL, const float2* __restrict__ twW, float scale) {
+                 int RB, FftPlan pL, const float2* __restrict__ twW, float scale, float* __restrict__ gout) {
   extern __shared__ float2 sm[];
   const int E = RB * L, Wh = L + 1;
   float2* A = sm;
@@ -236,6 +236,7 @@ __global__ void __launch_bounds__(kRowThreads)
       const float gx = b.x + scale * Z[e].x, gy = b.y + scale * Z[e].y;
       const float cx = fminf(fmaxf(gx, -t), t), cy = fminf(fmaxf(gy, -t), t);
       b2[off] = make_float2(cx, cy);
+      if (gout) reinterpret_cast<float2*>(gout)[plane * H * L + off] = make_float2(gx, gy);
       d = make_float2(gx - 2.f * cx, gy - 2.f * cy);
     }
     Z[e] = d;
@@ -452,10 +453,10 @@ cudaError_t run_row_c2r(const Geo& g, const float2* in, float* out, int planes, 
 }
 
 cudaError_t run_row_shrink(const Geo& g, float2* Y, float* bv, const float* thr, int planes, float scale,
-                           cudaStream_t st) {
+                           cudaStream_t st, float* gout) {
   const size_t smem = 2 * sizeof(float2) * g.RB * g.L;
   dim3 grid((g.H + g.RB - 1) / g.RB, planes);
-  k_row_shrink<<<grid, kRowThreads, smem, st>>>(Y, bv, thr, g.eta, g.H, g.L, g.RB, g.planL, g.twW, scale);
+  k_row_shrink<<<grid, kRowThreads, smem, st>>>(Y, bv, thr, g.eta, g.H, g.L, g.RB, g.planL, g.twW, scale, gout);
   return cudaGetLastError();
 }
 

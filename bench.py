@@ -50,6 +50,8 @@ def parse_args():
     ap.add_argument("--cpu-iters", type=int, default=2, help="oracle iterations in the CPU-baseline sample")
     ap.add_argument("--workload", choices=["bezier512", "batch"], default="bezier512",
                     help="bezier512 (default line) or the uneven batch of 64 images")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default work plan instead of autotuning it before the timed region")
     ap.add_argument("--iters", type=int, default=0,
                     help="ADMM iterations per step for short profiling runs (default: the workload's 500)")
     return ap.parse_args()
@@ -251,6 +253,8 @@ def run_ours(args):
     f_dev = torch.tensor(img32, device="cuda")
     fb = FilterBank(wl.H, wl.W, wl.J)
     seg = ShearletSegmenter(fb, f_dev, wl.codebook(), wl.Lambda(), wl.gamma)
+    # work plan: autotuned on this image before the timed region (iterate restored)
+    plan = seg.plan() if args.no_tune else seg.tune(3)
     labels_dev = torch.empty((wl.H, wl.W), dtype=torch.int32, device="cuda")
     st = seg.stream
     units_per_step = wl.H * wl.W * wl.K * wl.iters
@@ -334,6 +338,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(host_labels.numel() * 4)},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roofline,
+        "plan": plan,
         "iteration": {"ms": it_ms, "kernel_ms": mean_ms, "launches": n_launch,
                       "algorithmic_bytes": iter_alg,
                       "hbm_frac_algorithmic": iter_alg / (it_ms / 1000.0) / 1e9 / peak},
@@ -370,6 +375,8 @@ def run_batch(args):
         lams.append(synth.scale_weights(0.1, J))
         units += H * W * K * iters
     batch = ShearletBatch(imgs, cbs, lams, 1.0)
+    if not args.no_tune:
+        batch.tune(3)
     for _ in range(args.warmup):
         batch.step(iters)
     batch.synchronize()
@@ -385,7 +392,7 @@ def run_batch(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"batch: {len(shapes)} images, sides 128..1024 (first 384x640), K 2..6, "
                                    f"J = floor(log2(min side)/2), {iters} iterations, one graph per iteration",
-                       "images": len(shapes), "iters_per_step": iters}}
+                       "images": len(shapes), "iters_per_step": iters, "tuned": not args.no_tune}}
     print(json.dumps(line))
     batch.close()
     return 0

@@ -162,8 +162,50 @@ int seg_admm_init(const shf_bank* bank, const float* f, int C, const float* code
 int seg_admm_reset(seg_state* st, const float* f, int f_on_host);
 
 /* Enqueues n_iters ADMM iterations on the state's stream (replays of a CUDA
- * graph of one iteration, captured on first use when the stream allows it). */
+ * graph of one iteration, captured on first use when the stream allows it;
+ * the last iteration of each call records the events of
+ * seg_admm_kernel_times). */
 int seg_admm_step(seg_state* st, int n_iters);
+
+/* ---------------------------------------------------------------------------
+ * Work plan and autotuner (no counterpart in the paper: how the iteration of
+ * Sec. 3 is cut into kernel launches).  Power-of-two sizes (fast = 1) run the
+ * register-FFT kernels over waves of filters whose coefficient spectra stay in
+ * L2 (wave_mib) with column chunks of up to `chunk` filters; other sizes
+ * (fast = 0) run the general kernels with tiles of tile_cols half-spectrum
+ * columns and tile_rows rows and `groups` filter groups in the synthesis sums.
+ * Fields of the other path are 0 in seg_admm_get_plan and ignored by
+ * seg_admm_set_plan.  The plan changes the order of the FP32 synthesis sums
+ * (chunk, wave_mib, groups), so results are bitwise reproducible for a fixed
+ * plan, and agree within rounding across plans.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int fast;          /* read-only: 1 power-of-two path, 0 general path        */
+  int wave_mib;      /* fast: MiB of coefficient spectra per wave, [1, 4096]  */
+  int chunk;         /* fast: filters per column chunk, [1, 16]               */
+  int tile_cols;     /* general: half-spectrum columns per column tile        */
+  int tile_rows;     /* general: rows per row block                           */
+  int groups;        /* general: filter groups of the synthesis partial sums  */
+  float us_per_iter; /* seg_admm_tune: measured microseconds per iteration    */
+} seg_plan;
+
+/* The state's current plan. */
+int seg_admm_get_plan(const seg_state* st, seg_plan* out);
+
+/* Installs a plan (reallocating the plan's scratch; the iterate is kept).
+ * Synchronises the state's stream.  Errors: SHF_ERR_ARG for values out of
+ * range or a tile shape the kernels do not support at this size (the old plan
+ * stays), SHF_ERR_OOM. */
+int seg_admm_set_plan(seg_state* st, const seg_plan* p);
+
+/* Autotuner: times `iters` iterations (after one warm-up) of each candidate
+ * plan, varying one parameter at a time around the best so far (fast: wave
+ * budget, then chunk; general: groups, then tile_cols, then tile_rows), and
+ * installs the fastest.  The iterate and the iteration count are saved before
+ * and restored after the trials (needs memory for one copy of b_v, w, b_w, u
+ * and the u-spectra).  best (may be NULL) receives the plan with its time.
+ * Synchronises.  Errors: SHF_ERR_ARG (iters < 1), SHF_ERR_OOM, SHF_ERR_CUDA. */
+int seg_admm_tune(seg_state* st, int iters, seg_plan* best);
 
 /* Iterates until ||u - w||_2 / sqrt(K H W) < tol (checked every check_every
  * iterations) or max_iters total iterations; synchronises.  Outputs may be
@@ -253,6 +295,11 @@ int seg_admm_batch_step(seg_batch* batch, int n_iters);
  * batch: do not destroy it).  Its work goes to the image's own stream; call
  * seg_admm_batch_sync first to order it after the batch's iterations. */
 int seg_admm_batch_image(seg_batch* batch, int i, seg_state** out);
+
+/* Runs seg_admm_tune on the first image of every distinct (path, H, W, J, K)
+ * and installs its plan on the other images of that shape; the batch graph
+ * is recaptured at the next step.  Synchronises. */
+int seg_admm_batch_tune(seg_batch* batch, int iters);
 
 /* Waits for the batch's stream. */
 int seg_admm_batch_sync(seg_batch* batch);

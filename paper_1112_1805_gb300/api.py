@@ -165,6 +165,19 @@ class ShearletSegmenter:
         if src.is_cuda:
             self.synchronize()
 
+    def plan(self) -> dict:
+        """The work plan (launch shapes) of the iteration."""
+        return B.seg_admm_get_plan(self.handle)
+
+    def set_plan(self, plan: dict) -> None:
+        self.stream.synchronize()
+        B.seg_admm_set_plan(self.handle, plan)
+
+    def tune(self, iters: int = 5) -> dict:
+        """Autotunes the work plan on this image (the iterate is restored)."""
+        torch.cuda.current_stream().synchronize()
+        return B.seg_admm_tune(self.handle, iters)
+
     def energy(self) -> float:
         return float(self.get(B.SEG_ENERGY))
 
@@ -242,6 +255,11 @@ class ShearletBatch:
 
     def step(self, n: int) -> None:
         B.seg_admm_batch_step(self.handle, n)
+
+    def tune(self, iters: int = 5) -> None:
+        """Autotunes one plan per distinct image shape."""
+        torch.cuda.current_stream().synchronize()
+        B.seg_admm_batch_tune(self.handle, iters)
 
     def synchronize(self) -> None:
         B.seg_admm_batch_sync(self.handle)

@@ -51,6 +51,14 @@ class seg_params(ctypes.Structure):
 
 _VP = ctypes.c_void_p
 _I = ctypes.c_int
+class seg_plan(ctypes.Structure):
+    _fields_ = [("fast", ctypes.c_int), ("wave_mib", ctypes.c_int), ("chunk", ctypes.c_int),
+                ("tile_cols", ctypes.c_int), ("tile_rows", ctypes.c_int), ("groups", ctypes.c_int),
+                ("us_per_iter", ctypes.c_float)]
+
+
+_PLAN_FIELDS = ("fast", "wave_mib", "chunk", "tile_cols", "tile_rows", "groups", "us_per_iter")
+
 _SIG = {
     "shf_version": (_I, []),
     "shf_last_error": (ctypes.c_char_p, []),
@@ -81,6 +89,10 @@ _SIG = {
     "seg_admm_unrolled_fwd": (_I, [_VP, _I, _I]),
     "seg_admm_unrolled_bwd": (_I, [_VP, _VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _VP,
                                    _VP]),
+    "seg_admm_get_plan": (_I, [_VP, ctypes.POINTER(seg_plan)]),
+    "seg_admm_set_plan": (_I, [_VP, ctypes.POINTER(seg_plan)]),
+    "seg_admm_tune": (_I, [_VP, _I, ctypes.POINTER(seg_plan)]),
+    "seg_admm_batch_tune": (_I, [_VP, _I]),
     "seg_admm_sync": (_I, [_VP]),
     "seg_admm_destroy": (_I, [_VP]),
 }
@@ -223,6 +235,34 @@ def seg_admm_kernel_times(state: int):
 
 def seg_admm_kernel_name(i: int) -> str:
     return lib().seg_admm_kernel_name(int(i)).decode()
+
+
+def _plan_dict(p: seg_plan) -> dict:
+    return {k: getattr(p, k) for k in _PLAN_FIELDS}
+
+
+def seg_admm_get_plan(state: int) -> dict:
+    p = seg_plan()
+    _call("seg_admm_get_plan", state, ctypes.byref(p))
+    return _plan_dict(p)
+
+
+def seg_admm_set_plan(state: int, plan: dict) -> None:
+    p = seg_plan()
+    for k in _PLAN_FIELDS:
+        if k in plan:
+            setattr(p, k, plan[k])
+    _call("seg_admm_set_plan", state, ctypes.byref(p))
+
+
+def seg_admm_tune(state: int, iters: int = 5) -> dict:
+    p = seg_plan()
+    _call("seg_admm_tune", state, iters, ctypes.byref(p))
+    return _plan_dict(p)
+
+
+def seg_admm_batch_tune(batch: int, iters: int = 5) -> None:
+    _call("seg_admm_batch_tune", batch, iters)
 
 
 def seg_admm_sync(state: int) -> None:

@@ -89,11 +89,13 @@ struct seg_state {
   double* red = nullptr;
   int red_len = 0;
   int groups = 1;
-  cudaGraphExec_t exec = nullptr;
+  cudaGraphExec_t exec = nullptr;        // one iteration
+  cudaGraphExec_t exec_timed = nullptr;  // the same with an event before every launch
   bool graph_tried = false;
   bool fast = false;          // power-of-two sizes: the shf_fast.cu kernels
   bool fast_ustep = false;    // ... including the u/w-step (K <= 8)
   shf::FastPlan plan;         // fast path: static per-wave work list
+  std::vector<int2> ranges_host;  // fast path: the filters' column ranges
   shf::ChunkDesc* d_chunks = nullptr;
   int *d_filters = nullptr, *d_tile_begin = nullptr, *d_tile_slots = nullptr;
   float2* uhat = nullptr;     // fast path: 2-D spectra of u [K][H][Wh]
@@ -108,7 +110,8 @@ struct seg_state {
   // the states kept every un_ck iterations
   int un_T = 0, un_ck = 0;
   float2* un_Y = nullptr;        // [K][eta][H][Wh]
-  float2* un_partial = nullptr;  // [groups][K][H][Wh]
+  float2* un_partial = nullptr;  // [un_groups][K][H][Wh]
+  int un_groups = 0;
   std::vector<float*> ck_bv, ck_w, ck_bw;
   std::vector<float2*> ck_T;
   long long iter = 0;
@@ -263,6 +266,7 @@ namespace {
 
 void free_state(seg_state* s) {
   if (s->exec) cudaGraphExecDestroy(s->exec);
+  if (s->exec_timed) cudaGraphExecDestroy(s->exec_timed);
   for (cudaEvent_t e : s->ev)
     if (e) cudaEventDestroy(e);
   cudaFree(s->uhat);
@@ -323,17 +327,19 @@ void mark_launch(void* ctx, int kind) {
   if (cudaEventRecordWithFlags(st->ev[i], st->stream, cudaEventRecordExternal) != cudaSuccess) st->marks_ok = false;
 }
 
-// One ADMM iteration, with an event recorded before every launch and after
-// the last one.
-cudaError_t enqueue_iteration(seg_state* st) {
+// One ADMM iteration; `timed`: with an event recorded before every launch and
+// after the last one.
+cudaError_t enqueue_iteration(seg_state* st, bool timed) {
   const Geo& g = st->g;
   const float scale = 1.f / (static_cast<float>(g.H) * g.W);
   cudaStream_t s = st->stream;
   shf::LaunchHook hook;
-  hook.fn = mark_launch;
-  hook.ctx = st;
-  st->nmarks = 0;
-  st->marks_ok = true;
+  if (timed) {
+    hook.fn = mark_launch;
+    hook.ctx = st;
+    st->nmarks = 0;
+    st->marks_ok = true;
+  }
   hook.mark(shf::kKindUstep);
   cudaError_t e =
       st->fast_ustep
@@ -367,28 +373,155 @@ cudaError_t enqueue_generic_iteration(seg_state* st, float* gout) {
       shf::run_row_ustep(g, st->T, st->s, st->w, st->bw, st->u, st->Ur, nullptr, st->K, st->gamma, scale, s);
   if (e == cudaSuccess) e = shf::run_col_fan(g, st->Ur, st->un_Y, st->K, st->groups, s);
   if (e == cudaSuccess) e = shf::run_row_shrink(g, st->un_Y, st->bv, st->thr, st->K * g.eta, scale, s, gout);
-  if (e == cudaSuccess) e = shf::run_col_gather(g, st->un_Y, st->un_partial, st->K, st->groups, s);
-  if (e == cudaSuccess) e = shf::run_col_reduce_inv(g, st->un_partial, st->T, st->K, st->groups, s);
+  if (e == cudaSuccess) e = shf::run_col_gather(g, st->un_Y, st->un_partial, st->K, st->un_groups, s);
+  if (e == cudaSuccess) e = shf::run_col_reduce_inv(g, st->un_partial, st->T, st->K, st->un_groups, s);
   return e;
 }
 
-// Captures one iteration into a graph when the stream can be captured (not
-// the legacy default stream); otherwise iterations are launched directly.
-void try_capture(seg_state* st) {
-  st->graph_tried = true;
-  if (st->stream == nullptr) return;
+cudaGraphExec_t capture_iteration(seg_state* st, bool timed) {
   cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
   if (cudaStreamBeginCapture(st->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
-    return;
+    return nullptr;
   }
-  cudaError_t e = enqueue_iteration(st);
+  cudaError_t e = enqueue_iteration(st, timed);
   cudaError_t e2 = cudaStreamEndCapture(st->stream, &graph);
-  if (e == cudaSuccess && e2 == cudaSuccess && graph) {
-    if (cudaGraphInstantiate(&st->exec, graph, 0) != cudaSuccess) st->exec = nullptr;
+  if (e == cudaSuccess && e2 == cudaSuccess && graph && (!timed || st->marks_ok)) {
+    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
   }
   if (graph) cudaGraphDestroy(graph);
   cudaGetLastError();
+  return exec;
+}
+
+// Captures one iteration into two graphs (plain, and with the timing events)
+// when the stream can be captured (not the legacy default stream); otherwise
+// iterations are launched directly.
+void try_capture(seg_state* st) {
+  st->graph_tried = true;
+  if (st->stream == nullptr) return;
+  st->exec = capture_iteration(st, false);
+  if (st->exec) st->exec_timed = capture_iteration(st, true);
+  if (st->exec && !st->exec_timed) {
+    cudaGraphExecDestroy(st->exec);
+    st->exec = nullptr;
+  }
+}
+
+void drop_graphs(seg_state* st) {
+  if (st->exec) cudaGraphExecDestroy(st->exec);
+  if (st->exec_timed) cudaGraphExecDestroy(st->exec_timed);
+  st->exec = st->exec_timed = nullptr;
+  st->graph_tried = false;
+}
+
+// Fast path: builds the work list for (chunk, wave_mib) and allocates what
+// depends on it (one wave of coefficient spectra Y, the partial tiles, the
+// device work list); the previous buffers are released only once the new ones
+// exist.  Synchronises the state's stream.
+int install_fast_plan(seg_state* st, int chunk, int wave_mib) {
+  const Geo& g = st->g;
+  shf::FastPlan plan;
+  plan.chunk = chunk;
+  plan.wave_mib = wave_mib;
+  std::vector<shf::ChunkDesc> h_chunks;
+  std::vector<int> h_filters, h_tile_begin, h_tile_slots;
+  shf::build_fast_plan(g, st->ranges_host.data(), &plan, &h_chunks, &h_filters, &h_tile_begin, &h_tile_slots);
+  const size_t Phs = static_cast<size_t>(g.H) * shf::fast_pitch(g);
+  const size_t y_elems = Phs * static_cast<size_t>(shf::fast_wave(g, wave_mib));
+  const size_t partial_elems =
+      static_cast<size_t>(st->K) * std::max(plan.nchunks_total, 1) * g.H * shf::reg_batch();
+  float2 *Y = nullptr, *partial = nullptr;
+  shf::ChunkDesc* chunks = nullptr;
+  int *filters = nullptr, *tile_begin = nullptr, *tile_slots = nullptr;
+  int rc;
+  if ((rc = dev_alloc(&Y, y_elems, "Y")) || (rc = dev_alloc(&partial, partial_elems, "partial")) ||
+      (rc = dev_alloc(&chunks, std::max<size_t>(h_chunks.size(), 1), "chunks")) ||
+      (rc = dev_alloc(&filters, h_filters.size(), "chunk filters")) ||
+      (rc = dev_alloc(&tile_begin, h_tile_begin.size(), "tile_begin")) ||
+      (rc = dev_alloc(&tile_slots, h_tile_slots.size(), "tile_slots"))) {
+    cudaFree(Y);
+    cudaFree(partial);
+    cudaFree(chunks);
+    cudaFree(filters);
+    cudaFree(tile_begin);
+    cudaFree(tile_slots);
+    return rc;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!h_chunks.empty())
+    e = cudaMemcpy(chunks, h_chunks.data(), sizeof(shf::ChunkDesc) * h_chunks.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(filters, h_filters.data(), sizeof(int) * h_filters.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(tile_begin, h_tile_begin.data(), sizeof(int) * h_tile_begin.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(tile_slots, h_tile_slots.data(), sizeof(int) * h_tile_slots.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);  // the old buffers may still be in use
+  if (e != cudaSuccess) {
+    cudaFree(Y);
+    cudaFree(partial);
+    cudaFree(chunks);
+    cudaFree(filters);
+    cudaFree(tile_begin);
+    cudaFree(tile_slots);
+    return fail(SHF_ERR_CUDA, std::string("install_fast_plan: ") + cudaGetErrorString(e));
+  }
+  drop_graphs(st);
+  cudaFree(st->Y);
+  cudaFree(st->partial);
+  cudaFree(st->d_chunks);
+  cudaFree(st->d_filters);
+  cudaFree(st->d_tile_begin);
+  cudaFree(st->d_tile_slots);
+  st->Y = Y;
+  st->partial = partial;
+  st->d_chunks = chunks;
+  st->d_filters = filters;
+  st->d_tile_begin = tile_begin;
+  st->d_tile_slots = tile_slots;
+  plan.chunks = chunks;
+  plan.filters = filters;
+  plan.tile_begin = tile_begin;
+  plan.tile_slots = tile_slots;
+  st->plan = plan;
+  return SHF_OK;
+}
+
+// Filter groups as the general-path kernels use them: groups of ceil(eta/G)
+// filters, no group empty.
+int normalise_groups(int eta, int G) {
+  if (G < 1) G = 1;
+  if (G > eta) G = eta;
+  const int fg = (eta + G - 1) / G;
+  return (eta + fg - 1) / fg;
+}
+
+// General path: tile shape (TC, RB) and filter groups; reallocates the
+// partial sums.  Synchronises the state's stream.
+int install_generic_plan(seg_state* st, int TC, int RB, int groups) {
+  int dev = 0, optin = 0;
+  SHF_CK(cudaGetDevice(&dev));
+  SHF_CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  Geo g = st->g;
+  if (!shf::set_generic_tiles(&g, TC, RB, st->K, optin))
+    return fail(SHF_ERR_ARG, "tile shape not supported for this image size");
+  groups = normalise_groups(g.eta, groups);
+  float2* partial = nullptr;
+  int rc = dev_alloc(&partial, st->Ph() * st->K * static_cast<size_t>(groups), "partial");
+  if (rc) return rc;
+  cudaError_t e = cudaStreamSynchronize(st->stream);
+  if (e != cudaSuccess) {
+    cudaFree(partial);
+    return fail(SHF_ERR_CUDA, std::string("install_generic_plan: ") + cudaGetErrorString(e));
+  }
+  drop_graphs(st);
+  cudaFree(st->partial);
+  st->partial = partial;
+  st->g = g;
+  st->groups = groups;
+  return SHF_OK;
 }
 
 int energy_of_w(seg_state* st, double* out_host) {
@@ -485,27 +618,15 @@ int seg_admm_init(const shf_bank* b, const float* f, int C, const float* codeboo
   st->groups = shf::default_groups(g, K);
   st->fast = shf::fast_path_ok(g);
   st->fast_ustep = shf::fast_ustep_ok(g, K);
-  // coefficient-spectrum scratch: the whole label set on the generic path, one
-  // wave of filters on the fast path; partial sums per filter group
-  const size_t y_planes = st->fast ? static_cast<size_t>(shf::fast_wave(g)) : static_cast<size_t>(K) * g.eta;
-  // plane size of the scratch spectra: the fast path pads rows to a pitch of 8
-  const size_t Phs = st->fast ? static_cast<size_t>(g.H) * shf::fast_pitch(g) : Ph;
-  // fast path: per-wave work list from the filters' column ranges; one
-  // compact [H][8] partial tile per chunk and label
-  std::vector<shf::ChunkDesc> h_chunks;
-  std::vector<int> h_filters, h_tile_begin, h_tile_slots;
+  // the fast path's work list is built from the filters' column ranges
   if (st->fast) {
-    std::vector<int2> ranges(g.eta);
-    cudaError_t e = cudaMemcpy(ranges.data(), g.ranges, sizeof(int2) * g.eta, cudaMemcpyDeviceToHost);
+    st->ranges_host.resize(g.eta);
+    cudaError_t e = cudaMemcpy(st->ranges_host.data(), g.ranges, sizeof(int2) * g.eta, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) {
       free_state(st);
       return fail(SHF_ERR_CUDA, std::string("seg_admm_init: ") + cudaGetErrorString(e));
     }
-    shf::build_fast_plan(g, ranges.data(), &st->plan, &h_chunks, &h_filters, &h_tile_begin, &h_tile_slots);
   }
-  const size_t partial_elems = st->fast ? static_cast<size_t>(K) * std::max(st->plan.nchunks_total, 1) * g.H *
-                                              shf::reg_batch()
-                                        : Ph * K * static_cast<size_t>(st->groups);
   for (cudaEvent_t& ev : st->ev) {
     cudaError_t e = cudaEventCreate(&ev);
     if (e != cudaSuccess) {
@@ -520,13 +641,13 @@ int seg_admm_init(const shf_bank* b, const float* f, int C, const float* codeboo
       (rc = dev_alloc(&st->bv, P * K * g.eta, "b_v")) || (rc = dev_alloc(&st->w, P * K, "w")) ||
       (rc = dev_alloc(&st->bw, P * K, "b_w")) || (rc = dev_alloc(&st->u, P * K, "u")) ||
       (rc = dev_alloc(&st->stv, P * K, "stv")) || (rc = dev_alloc(&st->Ur, Ph * K, "Ur")) ||
-      (rc = dev_alloc(&st->Y, Phs * std::max(y_planes, static_cast<size_t>(K) * g.eta * !st->fast), "Y")) ||
-      (rc = dev_alloc(&st->partial, partial_elems, "partial")) || (rc = dev_alloc(&st->T, Ph * K, "T")) ||
-      (st->fast && (rc = dev_alloc(&st->uhat, Phs * K, "uhat"))) ||
-      (st->fast && (rc = dev_alloc(&st->d_chunks, std::max<size_t>(h_chunks.size(), 1), "chunks"))) ||
-      (st->fast && (rc = dev_alloc(&st->d_filters, h_filters.size(), "chunk filters"))) ||
-      (st->fast && (rc = dev_alloc(&st->d_tile_begin, h_tile_begin.size(), "tile_begin"))) ||
-      (st->fast && (rc = dev_alloc(&st->d_tile_slots, h_tile_slots.size(), "tile_slots"))) ||
+      (rc = dev_alloc(&st->T, Ph * K, "T")) ||
+      (st->fast && (rc = dev_alloc(&st->uhat, static_cast<size_t>(g.H) * shf::fast_pitch(g) * K, "uhat"))) ||
+      // coefficient spectra of the whole label set and one partial sum per
+      // filter group on the general path (the fast path's come with its plan)
+      (!st->fast && (rc = dev_alloc(&st->Y, Ph * K * g.eta, "Y"))) ||
+      (!st->fast && (rc = dev_alloc(&st->partial, Ph * K * static_cast<size_t>(st->groups), "partial"))) ||
+      (st->fast && (rc = install_fast_plan(st, shf::kDefaultChunk, shf::kDefaultWaveMiB))) ||
       (rc = dev_alloc(&st->thr, g.eta, "thr")) || (rc = dev_alloc(&st->lam, g.eta, "lam")) ||
       (rc = dev_alloc(&st->gap, P, "gap")) || (rc = dev_alloc(&st->labels, P, "labels")) ||
       (rc = dev_alloc(&st->flag, 1, "flag")) || (rc = dev_alloc(&st->red, st->red_len, "red"))) {
@@ -541,24 +662,6 @@ int seg_admm_init(const shf_bank* b, const float* f, int C, const float* codeboo
     thr[i] = st->gamma * lam[i];
   }
   cudaError_t e = cudaMemcpyAsync(st->thr, thr.data(), sizeof(float) * g.eta, cudaMemcpyHostToDevice, st->stream);
-  if (st->fast) {
-    if (e == cudaSuccess && !h_chunks.empty())
-      e = cudaMemcpyAsync(st->d_chunks, h_chunks.data(), sizeof(shf::ChunkDesc) * h_chunks.size(),
-                          cudaMemcpyHostToDevice, st->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(st->d_filters, h_filters.data(), sizeof(int) * h_filters.size(), cudaMemcpyHostToDevice,
-                          st->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(st->d_tile_begin, h_tile_begin.data(), sizeof(int) * h_tile_begin.size(),
-                          cudaMemcpyHostToDevice, st->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(st->d_tile_slots, h_tile_slots.data(), sizeof(int) * h_tile_slots.size(),
-                          cudaMemcpyHostToDevice, st->stream);
-    st->plan.chunks = st->d_chunks;
-    st->plan.filters = st->d_filters;
-    st->plan.tile_begin = st->d_tile_begin;
-    st->plan.tile_slots = st->d_tile_slots;
-  }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(st->lam, lam.data(), sizeof(float) * g.eta, cudaMemcpyHostToDevice, st->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(st->f, f, sizeof(float) * P * C, cudaMemcpyDeviceToDevice, st->stream);
@@ -587,14 +690,200 @@ int seg_admm_step(seg_state* st, int n) {
   if (!st || n < 0) return fail(SHF_ERR_ARG, "seg_admm_step: bad argument");
   if (n == 0) return SHF_OK;
   if (!st->graph_tried) try_capture(st);
+  // the last iteration of the call records the per-kernel timing events
   for (int i = 0; i < n; ++i) {
+    const bool timed = i == n - 1;
     if (st->exec) {
-      SHF_CK(cudaGraphLaunch(st->exec, st->stream));
+      SHF_CK(cudaGraphLaunch(timed ? st->exec_timed : st->exec, st->stream));
     } else {
-      SHF_CK(enqueue_iteration(st));
+      SHF_CK(enqueue_iteration(st, timed));
     }
   }
   st->iter += n;
+  return SHF_OK;
+}
+
+int seg_admm_get_plan(const seg_state* st, seg_plan* out) {
+  if (!st || !out) return fail(SHF_ERR_ARG, "seg_admm_get_plan: NULL argument");
+  out->fast = st->fast ? 1 : 0;
+  out->wave_mib = st->fast ? st->plan.wave_mib : 0;
+  out->chunk = st->fast ? st->plan.chunk : 0;
+  out->tile_cols = st->fast ? 0 : st->g.TC;
+  out->tile_rows = st->fast ? 0 : st->g.RB;
+  out->groups = st->fast ? 0 : st->groups;
+  out->us_per_iter = 0.f;
+  return SHF_OK;
+}
+
+int seg_admm_set_plan(seg_state* st, const seg_plan* p) {
+  if (!st || !p) return fail(SHF_ERR_ARG, "seg_admm_set_plan: NULL argument");
+  if (st->fast) {
+    if (p->chunk < 1 || p->chunk > 16 || p->wave_mib < 1 || p->wave_mib > 4096)
+      return fail(SHF_ERR_ARG, "seg_admm_set_plan: chunk must be in [1, 16] and wave_mib in [1, 4096]");
+    if (p->chunk == st->plan.chunk && p->wave_mib == st->plan.wave_mib) return SHF_OK;
+    return install_fast_plan(st, p->chunk, p->wave_mib);
+  }
+  if (p->tile_cols < 1 || p->tile_rows < 1 || p->groups < 1)
+    return fail(SHF_ERR_ARG, "seg_admm_set_plan: tile_cols, tile_rows and groups must be positive");
+  if (p->tile_cols == st->g.TC && p->tile_rows == st->g.RB && normalise_groups(st->g.eta, p->groups) == st->groups)
+    return SHF_OK;
+  return install_generic_plan(st, p->tile_cols, p->tile_rows, p->groups);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Mean time (microseconds) of one iteration over `iters` replays, after one
+// warm-up iteration that also captures the graphs.
+int time_iterations(seg_state* st, int iters, float* us) {
+  int rc = seg_admm_step(st, 1);
+  if (rc) return rc;
+  cudaEvent_t a = nullptr, b = nullptr;
+  SHF_CK(cudaEventCreate(&a));
+  cudaError_t e = cudaEventCreate(&b);
+  if (e == cudaSuccess) e = cudaEventRecord(a, st->stream);
+  if (e == cudaSuccess) rc = seg_admm_step(st, iters);
+  if (e == cudaSuccess && !rc) e = cudaEventRecord(b, st->stream);
+  if (e == cudaSuccess && !rc) e = cudaEventSynchronize(b);
+  float ms = 0.f;
+  if (e == cudaSuccess && !rc) e = cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (rc) return rc;
+  SHF_CK(e);
+  *us = 1000.f * ms / static_cast<float>(iters);
+  return SHF_OK;
+}
+
+// Candidate plans around the current one, for coordinate-wise search: stage 0
+// varies the first parameter, stage 1 the second, stage 2 the third, each
+// around the best found so far.
+std::vector<seg_plan> plan_candidates(const seg_state* st, const seg_plan& base, int stage) {
+  std::vector<seg_plan> out;
+  const Geo& g = st->g;
+  if (st->fast) {
+    if (stage == 0) {
+      // wave budgets that give distinct numbers of waves per label
+      std::vector<int> seen;
+      for (int mib : {16, 32, 64, 96, 128, 192}) {
+        const int w = shf::fast_wave(g, mib);
+        const int nw = (g.eta + w - 1) / w;
+        if (std::find(seen.begin(), seen.end(), nw) != seen.end()) continue;
+        seen.push_back(nw);
+        seg_plan p = base;
+        p.wave_mib = mib;
+        out.push_back(p);
+      }
+    } else if (stage == 1) {
+      for (int c : {1, 2, 4}) {
+        seg_plan p = base;
+        p.chunk = c;
+        out.push_back(p);
+      }
+    }
+    return out;
+  }
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return out;
+  if (stage == 0) {
+    std::vector<int> seen;
+    for (int G : {base.groups / 2, base.groups, 2 * base.groups, 4 * base.groups}) {
+      const int n = normalise_groups(g.eta, G);
+      if (std::find(seen.begin(), seen.end(), n) != seen.end()) continue;
+      seen.push_back(n);
+      seg_plan p = base;
+      p.groups = n;
+      out.push_back(p);
+    }
+  } else if (stage == 1 || stage == 2) {
+    const int vals1[] = {4, 8, 16, 32};
+    const int vals2[] = {base.tile_rows / 2, base.tile_rows, 2 * base.tile_rows};
+    const int* vals = stage == 1 ? vals1 : vals2;
+    const int nv = stage == 1 ? 4 : 3;
+    for (int i = 0; i < nv; ++i) {
+      seg_plan p = base;
+      (stage == 1 ? p.tile_cols : p.tile_rows) = vals[i];
+      Geo t = g;
+      if (!shf::set_generic_tiles(&t, p.tile_cols, p.tile_rows, st->K, optin)) continue;
+      out.push_back(p);
+    }
+  }
+  return out;
+}
+
+}  // namespace
+
+extern "C" {
+
+int seg_admm_tune(seg_state* st, int iters, seg_plan* best_out) {
+  if (!st || iters < 1) return fail(SHF_ERR_ARG, "seg_admm_tune: bad argument");
+  const Geo& g0 = st->g;
+  const size_t P = st->P(), KP = P * st->K, NC = KP * g0.eta, TH = st->Ph() * st->K;
+  // the iterate is saved and restored around the trial iterations
+  float* snap = nullptr;
+  const size_t nsnap = NC + 3 * KP + 2 * TH;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&snap), sizeof(float) * nsnap, st->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SHF_ERR_OOM, "seg_admm_tune: no memory to save the iterate");
+  }
+  struct Piece {
+    void* p;
+    size_t bytes;
+  };
+  const Piece pieces[] = {{st->bv, sizeof(float) * NC},
+                          {st->w, sizeof(float) * KP},
+                          {st->bw, sizeof(float) * KP},
+                          {st->u, sizeof(float) * KP},
+                          {st->T, sizeof(float2) * TH}};
+  auto copy_all = [&](bool save) {
+    char* q = reinterpret_cast<char*>(snap);
+    cudaError_t e = cudaSuccess;
+    for (const Piece& pc : pieces) {
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(save ? q : pc.p, save ? pc.p : q, pc.bytes, cudaMemcpyDeviceToDevice, st->stream);
+      q += pc.bytes;
+    }
+    return e;
+  };
+  const long long iter0 = st->iter;
+  cudaError_t e = copy_all(true);
+  seg_plan best;
+  seg_admm_get_plan(st, &best);
+  best.us_per_iter = INFINITY;
+  int rc = e == cudaSuccess ? SHF_OK : fail(SHF_ERR_CUDA, cudaGetErrorString(e));
+  for (int stage = 0; stage < 3 && !rc; ++stage) {
+    const seg_plan base = best;
+    for (const seg_plan& cand : plan_candidates(st, base, stage)) {
+      int r = seg_admm_set_plan(st, &cand);
+      if (r == SHF_ERR_OOM || r == SHF_ERR_ARG) continue;  // not feasible here: skip
+      if (r) {
+        rc = r;
+        break;
+      }
+      float us = 0.f;
+      r = time_iterations(st, iters, &us);
+      if (r) {
+        rc = r;
+        break;
+      }
+      if (us < best.us_per_iter) {
+        best = cand;
+        best.us_per_iter = us;
+      }
+    }
+  }
+  if (!rc) rc = seg_admm_set_plan(st, &best);
+  e = copy_all(false);
+  cudaError_t e2 = cudaFreeAsync(snap, st->stream);
+  cudaError_t e3 = cudaStreamSynchronize(st->stream);
+  st->iter = iter0;
+  if (rc) return rc;
+  if (e != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
+    return fail(SHF_ERR_CUDA, "seg_admm_tune: restoring the iterate failed");
+  if (best_out) *best_out = best;
   return SHF_OK;
 }
 
@@ -799,9 +1088,12 @@ int seg_admm_unrolled_fwd(seg_state* st, int T, int ckpt_every) {
   const Geo& g = st->g;
   const size_t P = st->P(), Ph = st->Ph(), KP = P * st->K, NC = KP * g.eta;
   int rc;
-  if (!st->un_Y && ((rc = dev_alloc(&st->un_Y, Ph * st->K * g.eta, "unrolled scratch")) ||
-                    (rc = dev_alloc(&st->un_partial, Ph * st->K * st->groups, "unrolled partials"))))
-    return rc;
+  if (!st->un_Y) {
+    if ((rc = dev_alloc(&st->un_Y, Ph * st->K * g.eta, "unrolled scratch")) ||
+        (rc = dev_alloc(&st->un_partial, Ph * st->K * st->groups, "unrolled partials")))
+      return rc;
+    st->un_groups = st->groups;
+  }
   const int nseg = (T + ckpt_every - 1) / ckpt_every;
   while (static_cast<int>(st->ck_bv.size()) < nseg) {
     float *bv = nullptr, *w = nullptr, *bw = nullptr;
@@ -852,7 +1144,7 @@ int seg_admm_unrolled_bwd(seg_state* st, const float* dL_dw, float* dL_dcodebook
   cudaStream_t s = st->stream;
   const int nblk = shf::adj_part_blocks();
   // one allocation for every temporary of the sweep
-  const size_t nf = NC * 2 + KP * 7 + static_cast<size_t>(ck) * (NC + KP);
+  const size_t nf = NC * 2 + KP * 6 + static_cast<size_t>(ck) * (NC + KP);
   const size_t nc2 = Ph * K * 2;
   const size_t nd = static_cast<size_t>(K) * eta * nblk + eta + static_cast<size_t>(K) * C * (nblk + 1);
   char* mem = nullptr;
@@ -862,9 +1154,8 @@ int seg_admm_unrolled_bwd(seg_state* st, const float* dL_dw, float* dL_dcodebook
   float *bvbar = fp, *dbar = fp + NC;
   fp += 2 * NC;
   float *Qbar = fp, *wbar = fp + KP, *bwbar = fp + 2 * KP, *sbar = fp + 3 * KP, *gwbar = fp + 4 * KP,
-        *stv = fp + 5 * KP, *fbar_unused = fp + 6 * KP;
-  (void)fbar_unused;
-  fp += 7 * KP;
+        *stv = fp + 5 * KP;
+  fp += 6 * KP;
   float* grec = fp;
   float* wrec = fp + static_cast<size_t>(ck) * NC;
   float2* Uw = reinterpret_cast<float2*>(mem + sizeof(float) * nf);
@@ -904,8 +1195,8 @@ int seg_admm_unrolled_bwd(seg_state* st, const float* dL_dw, float* dL_dcodebook
                                 static_cast<long>(P), tpart, tbar, s));
       // stv = S^T bvbar
       ok(shf::run_row_r2c(g, bvbar, st->un_Y, K * eta, 1.f, s));
-      ok(shf::run_col_gather(g, st->un_Y, st->un_partial, K, st->groups, s));
-      ok(shf::run_col_reduce_inv(g, st->un_partial, Tt, K, st->groups, s));
+      ok(shf::run_col_gather(g, st->un_Y, st->un_partial, K, st->un_groups, s));
+      ok(shf::run_col_reduce_inv(g, st->un_partial, Tt, K, st->un_groups, s));
       ok(shf::run_row_c2r(g, Tt, stv, K, scale, s));
       ok(shf::launch_adj_u(gwbar, stv, Qbar, wbar, bwbar, sbar, st->gamma, static_cast<long>(KP), s));
     }
@@ -990,7 +1281,7 @@ cudaError_t enqueue_batch_iteration(seg_batch* b) {
   for (size_t i = 0; i < b->states.size() && e == cudaSuccess; ++i) {
     seg_state* st = b->states[i];
     e = cudaStreamWaitEvent(st->stream, b->fork, 0);
-    if (e == cudaSuccess) e = enqueue_iteration(st);
+    if (e == cudaSuccess) e = enqueue_iteration(st, false);
     if (e == cudaSuccess) e = cudaEventRecord(b->joins[i], st->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->joins[i], 0);
   }
@@ -1087,6 +1378,35 @@ int seg_admm_batch_image(seg_batch* b, int i, seg_state** out) {
   if (!b || !out || i < 0 || i >= static_cast<int>(b->states.size()))
     return fail(SHF_ERR_ARG, "seg_admm_batch_image: bad argument");
   *out = b->states[i];
+  return SHF_OK;
+}
+
+int seg_admm_batch_tune(seg_batch* b, int iters) {
+  if (!b || iters < 1) return fail(SHF_ERR_ARG, "seg_admm_batch_tune: bad argument");
+  // one tuning run per distinct problem shape; the other images take its plan
+  struct Key {
+    int fast, H, W, J, K;
+    bool operator==(const Key& o) const {
+      return fast == o.fast && H == o.H && W == o.W && J == o.J && K == o.K;
+    }
+  };
+  std::vector<std::pair<Key, seg_plan>> done;
+  for (seg_state* st : b->states) {
+    const Key k{st->fast ? 1 : 0, st->g.H, st->g.W, st->g.J, st->K};
+    auto it = std::find_if(done.begin(), done.end(), [&](const std::pair<Key, seg_plan>& d) { return d.first == k; });
+    int rc;
+    if (it == done.end()) {
+      seg_plan p;
+      rc = seg_admm_tune(st, iters, &p);
+      if (!rc) done.emplace_back(k, p);
+    } else {
+      rc = seg_admm_set_plan(st, &it->second);
+    }
+    if (rc) return rc;
+  }
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  b->graph_tried = false;
   return SHF_OK;
 }
 

@@ -47,6 +47,9 @@ __device__ __forceinline__ void load_pass_table(float2* pt, const float2* __rest
 // next filter are loaded while the current transform runs.
 // ---------------------------------------------------------------------------
 
+// CTAs of H threads that fill 1024 threads of an SM (at most 32 CTAs).
+constexpr int col_min_blocks(int H) { return 1024 / H > 32 ? 32 : (1024 / H > 0 ? 1024 / H : 1); }
+
 template <int H>
 __global__ void __launch_bounds__(H) k_fcol_fwd(const float2* __restrict__ in, float2* __restrict__ out, int Wh,
                                                 int Whp, const float2* __restrict__ twH) {
@@ -87,7 +90,7 @@ __device__ __forceinline__ void load_tile8(float2 (&v)[8], const float2* __restr
 }
 
 template <int H>
-__global__ void __launch_bounds__(H, (1024 / H > 0 ? 1024 / H : 1))
+__global__ void __launch_bounds__(H, col_min_blocks(H))
     k_fcol_fan(const float2* __restrict__ uhat, const float* __restrict__ bank, const ChunkDesc* __restrict__ chunks,
                const int* __restrict__ filters, float2* __restrict__ Y, int Wh, int Whp, int label, int f0,
                const float2* __restrict__ twH) {
@@ -124,7 +127,7 @@ __global__ void __launch_bounds__(H, (1024 / H > 0 ? 1024 / H : 1))
 // partial[label][slot] = sum over the chunk's filters of W_f * column-forward(Y_f)
 // on the chunk's tile, stored compactly as [H][8].
 template <int H>
-__global__ void __launch_bounds__(H, (1024 / H > 0 ? 1024 / H : 1))
+__global__ void __launch_bounds__(H, col_min_blocks(H))
     k_fcol_gather(const float2* __restrict__ Y, const float* __restrict__ bank, const ChunkDesc* __restrict__ chunks,
                   const int* __restrict__ filters, float2* __restrict__ partial, int Wh, int Whp, int nslots,
                   int label, int f0, const float2* __restrict__ twH) {
@@ -209,8 +212,10 @@ __global__ void __launch_bounds__(H) k_fcol_reduce_inv(const float2* __restrict_
 // exchanges need only the group's barrier, and its global accesses are
 // contiguous row segments.  The thread's b_v values are requested first, so
 // that their DRAM latency overlaps the staging and the inverse transform.
+// Four CTAs per SM (at most 64 registers): the row work is latency-bound, and
+// occupancy is what hides the b_v and spectrum loads.
 template <int L>
-__global__ void __launch_bounds__(256) k_wrow_shrink(float2* __restrict__ Y, float* __restrict__ bv,
+__global__ void __launch_bounds__(256, 4) k_wrow_shrink(float2* __restrict__ Y, float* __restrict__ bv,
                                                      const float* __restrict__ thr,
                                                      const int2* __restrict__ ranges, int H, int Whp, int eta,
                                                      int label, int f0, float scale,
@@ -592,10 +597,10 @@ cudaError_t prepare_fast_kernels() {
   return cudaSuccess;
 }
 
-int fast_wave(const Geo& g) {
-  // filters per wave: keep the wave's coefficient spectra near 32 MiB
+int fast_wave(const Geo& g, int wave_mib) {
+  // filters per wave: keep the wave's coefficient spectra near wave_mib MiB
   const size_t plane = sizeof(float2) * static_cast<size_t>(g.H) * fast_pitch(g);
-  int w = static_cast<int>((size_t(32) << 20) / plane);
+  int w = static_cast<int>((static_cast<size_t>(wave_mib) << 20) / plane);
   if (w < 1) w = 1;
   if (w > g.eta) w = g.eta;
   // balance the waves of a label
@@ -606,7 +611,8 @@ int fast_wave(const Geo& g) {
 void build_fast_plan(const Geo& g, const int2* ranges, FastPlan* plan, std::vector<ChunkDesc>* chunks,
                      std::vector<int>* filters, std::vector<int>* tile_begin, std::vector<int>* tile_slots) {
   const int ntiles = (g.Wh + kB - 1) / kB;
-  const int wave = fast_wave(g);
+  const int wave = fast_wave(g, plan->wave_mib);
+  const size_t chunk = static_cast<size_t>(plan->chunk > 0 ? plan->chunk : 1);
   chunks->clear();
   filters->clear();
   plan->wave_f0.clear();
@@ -624,11 +630,11 @@ void build_fast_plan(const Geo& g, const int2* ranges, FastPlan* plan, std::vect
         const int2 r = ranges[f0 + fl];
         if (r.x <= r.y && t >= (r.x >> 3) && t <= (r.y >> 3)) act.push_back(fl);
       }
-      for (size_t a = 0; a < act.size(); a += kChunk) {
+      for (size_t a = 0; a < act.size(); a += chunk) {
         ChunkDesc c;
         c.tile = t;
         c.first = static_cast<int>(filters->size());
-        c.nf = static_cast<int>(std::min<size_t>(kChunk, act.size() - a));
+        c.nf = static_cast<int>(std::min<size_t>(chunk, act.size() - a));
         c.slot = static_cast<int>(chunks->size());
         for (int i = 0; i < c.nf; ++i) filters->push_back(act[a + i]);
         per_tile[t].push_back(c.slot);

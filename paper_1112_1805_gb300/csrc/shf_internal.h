@@ -84,6 +84,10 @@ cudaError_t run_col_reduce_inv(const Geo& g, const float2* partial, float2* out,
 cudaError_t run_row_ustep(const Geo& g, const float2* T, const float* s, float* w, float* bw, float* u, float2* Ur,
                           float* stv, int K, float gamma, float scale, cudaStream_t st);
 int default_groups(const Geo& g, int nch);
+// Sets the general path's tile shape (columns per column tile TC, rows per
+// row block RB) in g when the kernels support it and their shared memory for
+// K labels fits in `smem_limit` bytes; false (g unchanged) otherwise.
+bool set_generic_tiles(Geo* g, int TC, int RB, int K, int smem_limit);
 cudaError_t prepare_kernels();
 int max_dynamic_smem_needed(const Geo& g, int K);
 cudaError_t launch_sub(const float* a, const float* b, float* out, long n, cudaStream_t st);  // out = a - b
@@ -111,15 +115,20 @@ struct LaunchHook {
 };
 
 // Static work list of the fast path: for every wave of filters, chunks of at
-// most kChunk filters whose column support touches one tile of 8 columns.
-// Built once per state from the filters' column ranges.
+// most `chunk` filters whose column support touches one tile of 8 columns.
+// Built per state from the filters' column ranges; the wave size and the
+// chunk size are the plan's tunable parameters.
 struct ChunkDesc {
   int tile;   // column tile
   int first;  // index into `filters` of the chunk's first filter
-  int nf;     // number of filters (1..kChunk), ascending filter order
+  int nf;     // number of filters (1..chunk), ascending filter order
   int slot;   // partial-sum slot of this chunk within its label
 };
+constexpr int kDefaultChunk = 2;     // filters per column chunk
+constexpr int kDefaultWaveMiB = 64;  // coefficient spectra per wave of filters
 struct FastPlan {
+  int chunk = kDefaultChunk;
+  int wave_mib = kDefaultWaveMiB;
   std::vector<int> wave_f0, wave_nf, wave_chunk0;  // per wave: first filter, filters, first chunk
   int nchunks_total = 0;      // chunks of all waves of one label (= partial slots per label)
   const ChunkDesc* chunks = nullptr;  // device [nchunks_total]
@@ -127,13 +136,12 @@ struct FastPlan {
   const int* tile_begin = nullptr;    // device [ntiles + 1], into tile_slots
   const int* tile_slots = nullptr;    // device, slots of each tile in filter order
 };
-constexpr int kChunk = 2;
 constexpr int reg_batch() { return 8; }  // columns per tile of the fast column kernels
 
 // Fast path for power-of-two sizes (shf_fast.cu).
 bool fast_path_ok(const Geo& g);
 cudaError_t prepare_fast_kernels();
-int fast_wave(const Geo& g);        // filters per wave
+int fast_wave(const Geo& g, int wave_mib);  // filters per wave
 int fast_pitch(const Geo& g);       // row pitch (complex) of the internal spectra: Wh rounded up to 8
 bool fast_ustep_ok(const Geo& g, int K);
 // u-step, w-step, b_w update and row spectra of u (power-of-two sizes, K <= 8).
@@ -145,7 +153,8 @@ cudaError_t run_fast_iteration_body(const Geo& g, const FastPlan& plan, const fl
                                     float* bv, const float* thr, float2* partial, float2* T, int K, float scale,
                                     cudaStream_t st, const LaunchHook& hook);
 // Host construction of the work list from the filters' column ranges
-// (ranges_host[eta]); returns the host arrays to upload.
+// (ranges_host[eta]) with plan->chunk and plan->wave_mib; returns the host
+// arrays to upload.
 void build_fast_plan(const Geo& g, const int2* ranges_host, FastPlan* plan, std::vector<ChunkDesc>* chunks,
                      std::vector<int>* filters, std::vector<int>* tile_begin, std::vector<int>* tile_slots);
 

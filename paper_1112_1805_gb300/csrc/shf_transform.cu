@@ -429,6 +429,24 @@ int max_dynamic_smem_needed(const Geo& g, int K) {
   return std::max(col, std::max(row, us));
 }
 
+bool set_generic_tiles(Geo* g, int TC, int RB, int K, int smem_limit) {
+  if (TC < 1 || RB < 1 || TC > g->Wh || RB > g->H) return false;
+  const int per = (g->H * TC + kColThreads - 1) / kColThreads;
+  if (per > 32) return false;
+  Geo t = *g;
+  t.TC = TC;
+  t.ntiles = (t.Wh + TC - 1) / TC;
+  t.maxe = per <= 8 ? 8 : (per <= 16 ? 16 : 32);
+  t.RB = RB;
+  const size_t col = 2 * sizeof(float2) * static_cast<size_t>(t.H) * t.TC;
+  const size_t row = 2 * sizeof(float2) * static_cast<size_t>(t.RB) * t.L;
+  const size_t us = sizeof(float2) * static_cast<size_t>(ustep_rows(t, K)) * t.L * (2 + K);
+  const size_t lim = static_cast<size_t>(smem_limit);
+  if (col > lim || row + sizeof(double) * kL1Threads > lim || us > lim) return false;
+  *g = t;
+  return true;
+}
+
 int default_groups(const Geo& g, int nch) {
   const int base = g.ntiles * nch;
   int G = (4 * 152 + base - 1) / base;

@@ -1,0 +1,173 @@
+"""GPU: work plans and the autotuner.
+
+Every plan computes the iteration of Sec. 3; plans differ only in how the
+FP32 synthesis sums are grouped, so each one must meet the oracle bars
+(max |u - u_oracle| <= 1e-4, relative energy <= 1e-5) and be bitwise
+reproducible.  The tuner must leave the iterate exactly as it found it."""
+
+import numpy as np
+import pytest
+
+from paper_1112_1805_gb300 import synth
+from tests.gpu_util import labels_agree, need_cuda
+
+pytestmark = pytest.mark.gpu
+
+U_TOL = 1e-4
+E_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    return need_cuda()
+
+
+def _problem(H, W, K, J, seed):
+    rng = np.random.default_rng(seed)
+    cb = np.array([[0.2 + 0.6 * k / (K - 1)] for k in range(K)])
+    img, _ = synth.ellipse_image(H, W, cb, rng)
+    Lam = synth.scale_weights(0.1, J)
+    return img.astype(np.float32), cb, Lam.astype(np.float32)
+
+
+def _run(torch, img, cb, J, Lam, T, plan=None):
+    from paper_1112_1805_gb300 import binding as B
+    from paper_1112_1805_gb300.api import FilterBank, ShearletSegmenter
+
+    C, H, W = img.shape
+    fb = FilterBank(H, W, J)
+    seg = ShearletSegmenter(fb, torch.tensor(img, device="cuda"), cb, Lam.tolist(), 1.0)
+    if plan is not None:
+        seg.set_plan(plan)
+    got_plan = seg.plan()
+    seg.step(T)
+    seg.synchronize()
+    out = {k: seg.get(getattr(B, "SEG_" + k.upper())).cpu().numpy() for k in ("u", "w", "bv", "labels")}
+    out["energy"] = seg.energy()
+    out["plan"] = got_plan
+    seg.close()
+    fb.close()
+    return out
+
+
+def _oracle(O, img, cb, J, Lam, T):
+    return O.admm_run(img.astype(np.float64), cb.astype(np.float64), J, Lam.astype(np.float64), 1.0, T)
+
+
+def _check(o, g):
+    assert np.abs(g["u"] - o["u"]).max() <= U_TOL
+    assert np.abs(g["w"] - o["w"]).max() <= U_TOL
+    assert np.abs(g["bv"] - o["bv"]).max() <= U_TOL
+    assert abs(g["energy"] - o["energy"]) / abs(o["energy"]) <= E_TOL
+    assert labels_agree(g["labels"], o["labels"], o["gap"])
+
+
+FAST_PLANS = [dict(wave_mib=1, chunk=1), dict(wave_mib=1, chunk=4), dict(wave_mib=2, chunk=3),
+              dict(wave_mib=64, chunk=2), dict(wave_mib=4096, chunk=16)]
+
+
+def test_fast_plans_match_oracle(torch_mod, oracle_mod):
+    # 128 x 256, J = 3 (29 filters, 0.13 MiB of spectra per filter): 1 MiB
+    # waves give 5 waves per label, 64 MiB one wave
+    img, cb, Lam = _problem(128, 256, 3, 3, 31)
+    T = 12
+    o = _oracle(oracle_mod, img, cb, 3, Lam, T)
+    for p in FAST_PLANS:
+        g = _run(torch_mod, img, cb, 3, Lam, T, p)
+        assert g["plan"]["fast"] == 1
+        assert g["plan"]["wave_mib"] == p["wave_mib"] and g["plan"]["chunk"] == p["chunk"]
+        _check(o, g)
+
+
+def test_plan_is_bitwise_reproducible(torch_mod):
+    img, cb, Lam = _problem(128, 256, 3, 3, 32)
+    for p in (FAST_PLANS[0], FAST_PLANS[2]):
+        a = _run(torch_mod, img, cb, 3, Lam, 6, p)
+        b = _run(torch_mod, img, cb, 3, Lam, 6, p)
+        assert np.array_equal(a["u"], b["u"]) and np.array_equal(a["bv"], b["bv"])
+
+
+def test_general_plans_match_oracle(torch_mod, oracle_mod):
+    # 96 x 160 is not a power of two: the general kernels
+    img, cb, Lam = _problem(96, 160, 3, 2, 33)
+    T = 12
+    o = _oracle(oracle_mod, img, cb, 2, Lam, T)
+    base = _run(torch_mod, img, cb, 2, Lam, T)
+    assert base["plan"]["fast"] == 0
+    _check(o, base)
+    rb = base["plan"]["tile_rows"]
+    for p in (dict(tile_cols=4, tile_rows=rb, groups=1), dict(tile_cols=16, tile_rows=max(1, rb // 2), groups=13),
+              dict(tile_cols=32, tile_rows=min(96, 2 * rb), groups=5)):
+        g = _run(torch_mod, img, cb, 2, Lam, T, p)
+        assert g["plan"]["tile_cols"] == p["tile_cols"] and g["plan"]["tile_rows"] == p["tile_rows"]
+        _check(o, g)
+
+
+def test_bad_plans_are_rejected_and_keep_the_old_plan(torch_mod):
+    from paper_1112_1805_gb300 import binding as B
+    from paper_1112_1805_gb300.api import FilterBank, ShearletSegmenter
+
+    for H, W, bad in ((64, 64, dict(wave_mib=64, chunk=0)), (64, 64, dict(wave_mib=0, chunk=2)),
+                      (48, 80, dict(tile_cols=0, tile_rows=1, groups=1)),
+                      (48, 80, dict(tile_cols=8, tile_rows=10000, groups=1))):
+        img, cb, Lam = _problem(H, W, 3, 2, 34)
+        fb = FilterBank(H, W, 2)
+        seg = ShearletSegmenter(fb, torch_mod.tensor(img, device="cuda"), cb, Lam.tolist(), 1.0)
+        before = seg.plan()
+        with pytest.raises(B.ShearsegError):
+            seg.set_plan(dict(before, **bad))
+        assert seg.plan() == before
+        seg.step(2)
+        seg.synchronize()
+        seg.close()
+        fb.close()
+
+
+@pytest.mark.parametrize("H,W,J", [(256, 256, 3), (96, 160, 2)])
+def test_tune_restores_the_iterate_and_keeps_parity(torch_mod, oracle_mod, H, W, J):
+    from paper_1112_1805_gb300 import binding as B
+    from paper_1112_1805_gb300.api import FilterBank, ShearletSegmenter
+
+    img, cb, Lam = _problem(H, W, 3, J, 35)
+    fb = FilterBank(H, W, J)
+    seg = ShearletSegmenter(fb, torch_mod.tensor(img, device="cuda"), cb, Lam.tolist(), 1.0)
+    seg.step(4)
+    seg.synchronize()
+    snap = {k: seg.get(k).cpu().numpy() for k in (B.SEG_BV, B.SEG_W, B.SEG_BW, B.SEG_U)}
+    best = seg.tune(2)
+    assert best["us_per_iter"] > 0 and np.isfinite(best["us_per_iter"])
+    plan = seg.plan()
+    for k in ("fast", "wave_mib", "chunk", "tile_cols", "tile_rows", "groups"):
+        assert plan[k] == best[k]
+    for k, v in snap.items():
+        assert np.array_equal(seg.get(k).cpu().numpy(), v)
+    assert int(seg.get(B.SEG_ITER)) == 4
+    seg.step(8)
+    seg.synchronize()
+    u = seg.get(B.SEG_U).cpu().numpy()
+    times = B.seg_admm_kernel_times(seg.handle)
+    assert all(ms >= 0 for ms, _ in times.values()) and sum(n for _, n in times.values()) > 0
+    seg.close()
+    fb.close()
+    o = _oracle(oracle_mod, img, cb, J, Lam, 12)
+    assert np.abs(u - o["u"]).max() <= U_TOL
+
+
+def test_batch_tune(torch_mod, oracle_mod):
+    from paper_1112_1805_gb300 import binding as B
+    from paper_1112_1805_gb300.api import ShearletBatch
+
+    shapes = [(64, 64), (96, 160), (64, 64)]
+    probs = [_problem(H, W, 3, 2, 40 + i) for i, (H, W) in enumerate(shapes)]
+    batch = ShearletBatch([torch_mod.tensor(p[0], device="cuda") for p in probs], [p[1] for p in probs],
+                          [p[2].tolist() for p in probs])
+    batch.tune(2)
+    plans = [batch.image(i).plan() for i in range(3)]
+    assert plans[0] == plans[2]
+    batch.step(10)
+    batch.synchronize()
+    for i, p in enumerate(probs):
+        u = batch.image(i).get(B.SEG_U).cpu().numpy()
+        o = _oracle(oracle_mod, p[0], p[1], 2, p[2], 10)
+        assert np.abs(u - o["u"]).max() <= U_TOL
+    batch.close()

@@ -171,18 +171,20 @@ int seg_admm_step(seg_state* st, int n_iters);
  * Work plan and autotuner (no counterpart in the paper: how the iteration of
  * Sec. 3 is cut into kernel launches).  Power-of-two sizes (fast = 1) run the
  * register-FFT kernels over waves of filters whose coefficient spectra stay in
- * L2 (wave_mib) with column chunks of up to `chunk` filters; other sizes
- * (fast = 0) run the general kernels with tiles of tile_cols half-spectrum
- * columns and tile_rows rows and `groups` filter groups in the synthesis sums.
- * Fields of the other path are 0 in seg_admm_get_plan and ignored by
- * seg_admm_set_plan.  The plan changes the order of the FP32 synthesis sums
- * (chunk, wave_mib, groups), so results are bitwise reproducible for a fixed
- * plan, and agree within rounding across plans.
+ * L2 (wave_mib); each column launch runs col_ctas_per_sm resident CTAs per SM
+ * (0: as many as fit), each on a balanced range of the wave's (column tile,
+ * filter) pairs.  Other sizes (fast = 0) run the general kernels with tiles of
+ * tile_cols half-spectrum columns and tile_rows rows and `groups` filter
+ * groups in the synthesis sums.  Fields of the other path are 0 in
+ * seg_admm_get_plan and ignored by seg_admm_set_plan.  The plan changes the
+ * grouping of the FP32 synthesis sums (wave_mib, col_ctas_per_sm, groups), so
+ * results are bitwise reproducible for a fixed plan on a given GPU model, and
+ * agree within rounding across plans.
  * ------------------------------------------------------------------------- */
 typedef struct {
   int fast;          /* read-only: 1 power-of-two path, 0 general path        */
   int wave_mib;      /* fast: MiB of coefficient spectra per wave, [1, 4096]  */
-  int chunk;         /* fast: filters per column chunk, [1, 16]               */
+  int col_ctas_per_sm; /* fast: column CTAs per SM, [0, 32], 0 = all that fit */
   int tile_cols;     /* general: half-spectrum columns per column tile        */
   int tile_rows;     /* general: rows per row block                           */
   int groups;        /* general: filter groups of the synthesis partial sums  */
@@ -200,11 +202,12 @@ int seg_admm_set_plan(seg_state* st, const seg_plan* p);
 
 /* Autotuner: times `iters` iterations (after one warm-up) of each candidate
  * plan, varying one parameter at a time around the best so far (fast: wave
- * budget, then chunk; general: groups, then tile_cols, then tile_rows), and
- * installs the fastest.  The iterate and the iteration count are saved before
- * and restored after the trials (needs memory for one copy of b_v, w, b_w, u
- * and the u-spectra).  best (may be NULL) receives the plan with its time.
- * Synchronises.  Errors: SHF_ERR_ARG (iters < 1), SHF_ERR_OOM, SHF_ERR_CUDA. */
+ * budget, then col_ctas_per_sm; general: groups, then tile_cols, then
+ * tile_rows), and installs the fastest.  The iterate and the iteration count
+ * are saved before and restored after the trials (needs memory for one copy
+ * of b_v, w, b_w, u and the u-spectra).  best (may be NULL) receives the plan
+ * with its time.  Synchronises.  Errors: SHF_ERR_ARG (iters < 1),
+ * SHF_ERR_OOM, SHF_ERR_CUDA. */
 int seg_admm_tune(seg_state* st, int iters, seg_plan* best);
 
 /* Iterates until ||u - w||_2 / sqrt(K H W) < tol (checked every check_every

@@ -52,12 +52,12 @@ class seg_params(ctypes.Structure):
 _VP = ctypes.c_void_p
 _I = ctypes.c_int
 class seg_plan(ctypes.Structure):
-    _fields_ = [("fast", ctypes.c_int), ("wave_mib", ctypes.c_int), ("chunk", ctypes.c_int),
+    _fields_ = [("fast", ctypes.c_int), ("wave_mib", ctypes.c_int), ("col_ctas_per_sm", ctypes.c_int),
                 ("tile_cols", ctypes.c_int), ("tile_rows", ctypes.c_int), ("groups", ctypes.c_int),
                 ("us_per_iter", ctypes.c_float)]
 
 
-_PLAN_FIELDS = ("fast", "wave_mib", "chunk", "tile_cols", "tile_rows", "groups", "us_per_iter")
+_PLAN_FIELDS = ("fast", "wave_mib", "col_ctas_per_sm", "tile_cols", "tile_rows", "groups", "us_per_iter")
 
 _SIG = {
     "shf_version": (_I, []),

@@ -96,8 +96,8 @@ struct seg_state {
   bool fast_ustep = false;    // ... including the u/w-step (K <= 8)
   shf::FastPlan plan;         // fast path: static per-wave work list
   std::vector<int2> ranges_host;  // fast path: the filters' column ranges
-  shf::ChunkDesc* d_chunks = nullptr;
-  int *d_filters = nullptr, *d_tile_begin = nullptr, *d_tile_slots = nullptr;
+  shf::WorkItem* d_items = nullptr;
+  int *d_cta_begin = nullptr, *d_tile_begin = nullptr, *d_tile_slots = nullptr;
   float2* uhat = nullptr;     // fast path: 2-D spectra of u [K][H][Wh]
   // Events recorded before every launch of an iteration (graph event nodes),
   // with the kind of the launch that follows each.
@@ -270,8 +270,8 @@ void free_state(seg_state* s) {
   for (cudaEvent_t e : s->ev)
     if (e) cudaEventDestroy(e);
   cudaFree(s->uhat);
-  cudaFree(s->d_chunks);
-  cudaFree(s->d_filters);
+  cudaFree(s->d_items);
+  cudaFree(s->d_cta_begin);
   cudaFree(s->d_tile_begin);
   cudaFree(s->d_tile_slots);
   cudaFree(s->un_Y);
@@ -416,73 +416,70 @@ void drop_graphs(seg_state* st) {
   st->graph_tried = false;
 }
 
-// Fast path: builds the work list for (chunk, wave_mib) and allocates what
-// depends on it (one wave of coefficient spectra Y, the partial tiles, the
-// device work list); the previous buffers are released only once the new ones
-// exist.  Synchronises the state's stream.
-int install_fast_plan(seg_state* st, int chunk, int wave_mib) {
+// Fast path: builds the work list for (wave_mib, col_ctas_per_sm) and
+// allocates what depends on it (one wave of coefficient spectra Y, the
+// partial tiles, the device work list); the previous buffers are released
+// only once the new ones exist.  Synchronises the state's stream.
+int install_fast_plan(seg_state* st, int wave_mib, int col_ctas_per_sm) {
   const Geo& g = st->g;
   shf::FastPlan plan;
-  plan.chunk = chunk;
   plan.wave_mib = wave_mib;
-  std::vector<shf::ChunkDesc> h_chunks;
-  std::vector<int> h_filters, h_tile_begin, h_tile_slots;
-  shf::build_fast_plan(g, st->ranges_host.data(), &plan, &h_chunks, &h_filters, &h_tile_begin, &h_tile_slots);
+  plan.col_ctas_per_sm = col_ctas_per_sm;
+  plan.col_ctas = shf::fast_col_ctas(g, col_ctas_per_sm);
+  if (plan.col_ctas < 1) return fail(SHF_ERR_CUDA, "install_fast_plan: no resident column CTA");
+  std::vector<shf::WorkItem> h_items;
+  std::vector<int> h_cta_begin, h_tile_begin, h_tile_slots;
+  shf::build_fast_plan(g, st->ranges_host.data(), &plan, &h_items, &h_cta_begin, &h_tile_begin, &h_tile_slots);
   const size_t Phs = static_cast<size_t>(g.H) * shf::fast_pitch(g);
   const size_t y_elems = Phs * static_cast<size_t>(shf::fast_wave(g, wave_mib));
-  const size_t partial_elems =
-      static_cast<size_t>(st->K) * std::max(plan.nchunks_total, 1) * g.H * shf::reg_batch();
+  const size_t partial_elems = static_cast<size_t>(st->K) * std::max(plan.nslots, 1) * g.H * shf::reg_batch();
   float2 *Y = nullptr, *partial = nullptr;
-  shf::ChunkDesc* chunks = nullptr;
-  int *filters = nullptr, *tile_begin = nullptr, *tile_slots = nullptr;
-  int rc;
-  if ((rc = dev_alloc(&Y, y_elems, "Y")) || (rc = dev_alloc(&partial, partial_elems, "partial")) ||
-      (rc = dev_alloc(&chunks, std::max<size_t>(h_chunks.size(), 1), "chunks")) ||
-      (rc = dev_alloc(&filters, h_filters.size(), "chunk filters")) ||
-      (rc = dev_alloc(&tile_begin, h_tile_begin.size(), "tile_begin")) ||
-      (rc = dev_alloc(&tile_slots, h_tile_slots.size(), "tile_slots"))) {
+  shf::WorkItem* items = nullptr;
+  int *cta_begin = nullptr, *tile_begin = nullptr, *tile_slots = nullptr;
+  auto release = [&]() {
     cudaFree(Y);
     cudaFree(partial);
-    cudaFree(chunks);
-    cudaFree(filters);
+    cudaFree(items);
+    cudaFree(cta_begin);
     cudaFree(tile_begin);
     cudaFree(tile_slots);
+  };
+  int rc;
+  if ((rc = dev_alloc(&Y, y_elems, "Y")) || (rc = dev_alloc(&partial, partial_elems, "partial")) ||
+      (rc = dev_alloc(&items, h_items.size(), "work items")) ||
+      (rc = dev_alloc(&cta_begin, h_cta_begin.size(), "work ranges")) ||
+      (rc = dev_alloc(&tile_begin, h_tile_begin.size(), "tile_begin")) ||
+      (rc = dev_alloc(&tile_slots, h_tile_slots.size(), "tile_slots"))) {
+    release();
     return rc;
   }
-  cudaError_t e = cudaSuccess;
-  if (!h_chunks.empty())
-    e = cudaMemcpy(chunks, h_chunks.data(), sizeof(shf::ChunkDesc) * h_chunks.size(), cudaMemcpyHostToDevice);
+  cudaError_t e = cudaMemcpy(items, h_items.data(), sizeof(shf::WorkItem) * h_items.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
-    e = cudaMemcpy(filters, h_filters.data(), sizeof(int) * h_filters.size(), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(cta_begin, h_cta_begin.data(), sizeof(int) * h_cta_begin.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(tile_begin, h_tile_begin.data(), sizeof(int) * h_tile_begin.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(tile_slots, h_tile_slots.data(), sizeof(int) * h_tile_slots.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);  // the old buffers may still be in use
   if (e != cudaSuccess) {
-    cudaFree(Y);
-    cudaFree(partial);
-    cudaFree(chunks);
-    cudaFree(filters);
-    cudaFree(tile_begin);
-    cudaFree(tile_slots);
+    release();
     return fail(SHF_ERR_CUDA, std::string("install_fast_plan: ") + cudaGetErrorString(e));
   }
   drop_graphs(st);
   cudaFree(st->Y);
   cudaFree(st->partial);
-  cudaFree(st->d_chunks);
-  cudaFree(st->d_filters);
+  cudaFree(st->d_items);
+  cudaFree(st->d_cta_begin);
   cudaFree(st->d_tile_begin);
   cudaFree(st->d_tile_slots);
   st->Y = Y;
   st->partial = partial;
-  st->d_chunks = chunks;
-  st->d_filters = filters;
+  st->d_items = items;
+  st->d_cta_begin = cta_begin;
   st->d_tile_begin = tile_begin;
   st->d_tile_slots = tile_slots;
-  plan.chunks = chunks;
-  plan.filters = filters;
+  plan.items = items;
+  plan.cta_begin = cta_begin;
   plan.tile_begin = tile_begin;
   plan.tile_slots = tile_slots;
   st->plan = plan;
@@ -647,7 +644,7 @@ int seg_admm_init(const shf_bank* b, const float* f, int C, const float* codeboo
       // filter group on the general path (the fast path's come with its plan)
       (!st->fast && (rc = dev_alloc(&st->Y, Ph * K * g.eta, "Y"))) ||
       (!st->fast && (rc = dev_alloc(&st->partial, Ph * K * static_cast<size_t>(st->groups), "partial"))) ||
-      (st->fast && (rc = install_fast_plan(st, shf::kDefaultChunk, shf::kDefaultWaveMiB))) ||
+      (st->fast && (rc = install_fast_plan(st, shf::kDefaultWaveMiB, 0))) ||
       (rc = dev_alloc(&st->thr, g.eta, "thr")) || (rc = dev_alloc(&st->lam, g.eta, "lam")) ||
       (rc = dev_alloc(&st->gap, P, "gap")) || (rc = dev_alloc(&st->labels, P, "labels")) ||
       (rc = dev_alloc(&st->flag, 1, "flag")) || (rc = dev_alloc(&st->red, st->red_len, "red"))) {
@@ -707,7 +704,7 @@ int seg_admm_get_plan(const seg_state* st, seg_plan* out) {
   if (!st || !out) return fail(SHF_ERR_ARG, "seg_admm_get_plan: NULL argument");
   out->fast = st->fast ? 1 : 0;
   out->wave_mib = st->fast ? st->plan.wave_mib : 0;
-  out->chunk = st->fast ? st->plan.chunk : 0;
+  out->col_ctas_per_sm = st->fast ? st->plan.col_ctas_per_sm : 0;
   out->tile_cols = st->fast ? 0 : st->g.TC;
   out->tile_rows = st->fast ? 0 : st->g.RB;
   out->groups = st->fast ? 0 : st->groups;
@@ -718,10 +715,10 @@ int seg_admm_get_plan(const seg_state* st, seg_plan* out) {
 int seg_admm_set_plan(seg_state* st, const seg_plan* p) {
   if (!st || !p) return fail(SHF_ERR_ARG, "seg_admm_set_plan: NULL argument");
   if (st->fast) {
-    if (p->chunk < 1 || p->chunk > 16 || p->wave_mib < 1 || p->wave_mib > 4096)
-      return fail(SHF_ERR_ARG, "seg_admm_set_plan: chunk must be in [1, 16] and wave_mib in [1, 4096]");
-    if (p->chunk == st->plan.chunk && p->wave_mib == st->plan.wave_mib) return SHF_OK;
-    return install_fast_plan(st, p->chunk, p->wave_mib);
+    if (p->col_ctas_per_sm < 0 || p->col_ctas_per_sm > 32 || p->wave_mib < 1 || p->wave_mib > 4096)
+      return fail(SHF_ERR_ARG, "seg_admm_set_plan: col_ctas_per_sm must be in [0, 32] and wave_mib in [1, 4096]");
+    if (p->col_ctas_per_sm == st->plan.col_ctas_per_sm && p->wave_mib == st->plan.wave_mib) return SHF_OK;
+    return install_fast_plan(st, p->wave_mib, p->col_ctas_per_sm);
   }
   if (p->tile_cols < 1 || p->tile_rows < 1 || p->groups < 1)
     return fail(SHF_ERR_ARG, "seg_admm_set_plan: tile_cols, tile_rows and groups must be positive");
@@ -776,11 +773,16 @@ std::vector<seg_plan> plan_candidates(const seg_state* st, const seg_plan& base,
         out.push_back(p);
       }
     } else if (stage == 1) {
-      for (int c : {1, 2, 4}) {
+      // resident column CTAs per SM: every count up to what fits (0 = all)
+      const int fit = shf::fast_col_ctas(g, 0) / std::max(1, shf::fast_col_ctas(g, 1));
+      for (int c = 1; c < fit; ++c) {
         seg_plan p = base;
-        p.chunk = c;
+        p.col_ctas_per_sm = c;
         out.push_back(p);
       }
+      seg_plan p = base;
+      p.col_ctas_per_sm = 0;
+      out.push_back(p);
     }
     return out;
   }

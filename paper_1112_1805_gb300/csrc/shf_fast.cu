@@ -89,85 +89,117 @@ __device__ __forceinline__ void load_tile8(float2 (&v)[8], const float2* __restr
     v[k] = ok ? src[static_cast<size_t>(tt + k * (H / 8)) * pitch + col] : make_float2(0.f, 0.f);
 }
 
+// Analysis fan-out: for every item (tile, filter) of the CTA's range,
+// Y_f = column-inverse(W_f * uhat) on the tile.  The next item's filter tile
+// (and, at a tile change, the next spectrum tile) is requested while the
+// current transform runs.
 template <int H>
 __global__ void __launch_bounds__(H, col_min_blocks(H))
-    k_fcol_fan(const float2* __restrict__ uhat, const float* __restrict__ bank, const ChunkDesc* __restrict__ chunks,
-               const int* __restrict__ filters, float2* __restrict__ Y, int Wh, int Whp, int label, int f0,
+    k_fcol_fan(const float2* __restrict__ uhat, const float* __restrict__ bank, const WorkItem* __restrict__ items,
+               const int* __restrict__ cta_begin, float2* __restrict__ Y, int Wh, int Whp, int label, int f0,
                const float2* __restrict__ twH) {
   extern __shared__ float2 sm[];
   float2* tw = sm;  // per-pass twiddles
   float2* b0 = sm + reg::Passes<H>::TWSIZE;
   float2* b1 = b0 + reg::batch_rows(H) * kS;
-  const ChunkDesc c = chunks[blockIdx.x];
+  const int ib = cta_begin[blockIdx.x], ie = cta_begin[blockIdx.x + 1];
+  if (ib >= ie) return;
   const int b = threadIdx.x & 7, tt = threadIdx.x >> 3;
-  const int col = c.tile * kB + b;
-  const bool ok = col < Wh;
   const size_t Pb = static_cast<size_t>(H) * Wh, Pp = static_cast<size_t>(H) * Whp;
+  WorkItem it = items[ib];
+  int col = it.tile * kB + b;
+  bool ok = col < Wh;
   float2 u[8];
   float w[8];
   load_tile8<H>(u, uhat + Pp * label, Whp, tt, col, ok);
-  load_bank8<H>(w, bank + Pb * (f0 + filters[c.first]), Wh, tt, col, ok);
+  load_bank8<H>(w, bank + Pb * (f0 + it.filter), Wh, tt, col, ok);
   load_pass_table<H, 1>(tw, twH);
   __syncthreads();
-  for (int i = 0; i < c.nf; ++i) {
-    const int fl = filters[c.first + i];
+  for (int i = ib; i < ie; ++i) {
     float2 v[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) v[k] = c_scale(u[k], w[k]);
-    if (i + 1 < c.nf) load_bank8<H>(w, bank + Pb * (f0 + filters[c.first + i + 1]), Wh, tt, col, ok);
+    const int fl = it.filter, ccol = col;
+    const bool cok = ok;
+    if (i + 1 < ie) {
+      const WorkItem nx = items[i + 1];
+      col = nx.tile * kB + b;
+      ok = col < Wh;
+      load_bank8<H>(w, bank + Pb * (f0 + nx.filter), Wh, tt, col, ok);
+      if (nx.tile != it.tile) load_tile8<H>(u, uhat + Pp * label, Whp, tt, col, ok);
+      it = nx;
+    }
     reg::fft<H, +1>(v, tt, b, b0, b1, tw);
-    if (ok) {
-      float2* dst = Y + Pp * fl + col;
+    if (cok) {
+      float2* dst = Y + Pp * fl + ccol;
 #pragma unroll
       for (int k = 0; k < 8; ++k) dst[static_cast<size_t>(tt + k * (H / 8)) * Whp] = v[k];
     }
   }
 }
 
-// partial[label][slot] = sum over the chunk's filters of W_f * column-forward(Y_f)
-// on the chunk's tile, stored compactly as [H][8].
+// Synthesis gather: partial[label][slot] = sum over a run of items of one
+// tile of W_f * column-forward(Y_f), stored compactly as [H][8]; the next
+// item's coefficient tile is requested while the current transform runs.
 template <int H>
 __global__ void __launch_bounds__(H, col_min_blocks(H))
-    k_fcol_gather(const float2* __restrict__ Y, const float* __restrict__ bank, const ChunkDesc* __restrict__ chunks,
-                  const int* __restrict__ filters, float2* __restrict__ partial, int Wh, int Whp, int nslots,
+    k_fcol_gather(const float2* __restrict__ Y, const float* __restrict__ bank, const WorkItem* __restrict__ items,
+                  const int* __restrict__ cta_begin, float2* __restrict__ partial, int Wh, int Whp, int nslots,
                   int label, int f0, const float2* __restrict__ twH) {
   extern __shared__ float2 sm[];
   float2* tw = sm;  // per-pass twiddles
   float2* b0 = sm + reg::Passes<H>::TWSIZE;
   float2* b1 = b0 + reg::batch_rows(H) * kS;
-  const ChunkDesc c = chunks[blockIdx.x];
+  const int ib = cta_begin[blockIdx.x], ie = cta_begin[blockIdx.x + 1];
+  if (ib >= ie) return;
   const int b = threadIdx.x & 7, tt = threadIdx.x >> 3;
-  const int col = c.tile * kB + b;
-  const bool ok = col < Wh;
   const size_t Pb = static_cast<size_t>(H) * Wh, Pp = static_cast<size_t>(H) * Whp;
+  WorkItem it = items[ib];
+  int col = it.tile * kB + b;
+  bool ok = col < Wh;
   float2 acc[8], y[8];
   float w[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) acc[k] = make_float2(0.f, 0.f);
-  load_tile8<H>(y, Y + Pp * filters[c.first], Whp, tt, col, ok);
+  load_tile8<H>(y, Y + Pp * it.filter, Whp, tt, col, ok);
   load_pass_table<H, 1>(tw, twH);
   __syncthreads();
-  for (int i = 0; i < c.nf; ++i) {
-    const int fl = filters[c.first + i];
+  for (int i = ib; i < ie; ++i) {
     float2 v[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) v[k] = y[k];
-    load_bank8<H>(w, bank + Pb * (f0 + fl), Wh, tt, col, ok);
-    if (i + 1 < c.nf) load_tile8<H>(y, Y + Pp * filters[c.first + i + 1], Whp, tt, col, ok);
+    load_bank8<H>(w, bank + Pb * (f0 + it.filter), Wh, tt, col, ok);
+    WorkItem nx = it;
+    int ncol = col;
+    bool nok = ok;
+    if (i + 1 < ie) {
+      nx = items[i + 1];
+      ncol = nx.tile * kB + b;
+      nok = ncol < Wh;
+      load_tile8<H>(y, Y + Pp * nx.filter, Whp, tt, ncol, nok);
+    }
     reg::fft<H, -1>(v, tt, b, b0, b1, tw);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       acc[k].x = fmaf(w[k], v[k].x, acc[k].x);
       acc[k].y = fmaf(w[k], v[k].y, acc[k].y);
     }
-  }
-  float2* dst = partial + (static_cast<size_t>(label) * nslots + c.slot) * H * kB + b;
+    if (i + 1 == ie || nx.slot != it.slot) {
+      float2* dst = partial + (static_cast<size_t>(label) * nslots + it.slot) * H * kB + b;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) dst[static_cast<size_t>(tt + k * (H / 8)) * kB] = acc[k];
+      for (int k = 0; k < 8; ++k) {
+        dst[static_cast<size_t>(tt + k * (H / 8)) * kB] = acc[k];
+        acc[k] = make_float2(0.f, 0.f);
+      }
+    }
+    it = nx;
+    col = ncol;
+    ok = nok;
+  }
 }
 
-// T[label] on one tile = column-inverse of the sum of the tile's chunk
-// partials, in the fixed slot order (filter order).
+// T[label] on one tile = column-inverse of the sum of the tile's partial
+// slots, in the fixed slot order (filter order).
 template <int H>
 __global__ void __launch_bounds__(H) k_fcol_reduce_inv(const float2* __restrict__ partial,
                                                        const int* __restrict__ tile_begin,
@@ -461,26 +493,26 @@ cudaError_t iteration_body(const Geo& g, const FastPlan& plan, const float2* Ur,
                            const LaunchHook& hook) {
   const int ntiles = (g.Wh + kB - 1) / kB;
   const int Whp = fast_pitch(g);
-  const int nslots = plan.nchunks_total;
+  const int nslots = plan.nslots;
   const int nw = static_cast<int>(plan.wave_f0.size());
   hook.mark(kKindColFwd);
   k_fcol_fwd<H><<<dim3(ntiles, K), H, col_smem<H>(), st>>>(Ur, uhat, g.Wh, Whp, g.twH);
   for (int label = 0; label < K; ++label) {
     for (int w = 0; w < nw; ++w) {
-      const int f0 = plan.wave_f0[w], nf = plan.wave_nf[w], c0 = plan.wave_chunk0[w];
-      const int nc = (w + 1 < nw ? plan.wave_chunk0[w + 1] : nslots) - c0;
+      const int f0 = plan.wave_f0[w], nf = plan.wave_nf[w];
+      const int c0 = plan.wave_cta0[w], nc = plan.wave_cta0[w + 1] - c0;
+      const int* cb = plan.cta_begin + c0 + w;  // each wave's ranges end with one extra entry
       if (nc > 0) {
         hook.mark(kKindFan);
-        k_fcol_fan<H><<<nc, H, col_smem<H>(), st>>>(uhat, g.bank, plan.chunks + c0, plan.filters, Y, g.Wh, Whp,
-                                                     label, f0, g.twH);
+        k_fcol_fan<H><<<nc, H, col_smem<H>(), st>>>(uhat, g.bank, plan.items, cb, Y, g.Wh, Whp, label, f0, g.twH);
       }
       hook.mark(kKindShrink);
       k_wrow_shrink<L><<<dim3((g.H + row_rows_per_cta<L>() - 1) / row_rows_per_cta<L>(), nf), 256, row_smem<L>(),
                          st>>>(Y, bv, thr, g.ranges, g.H, Whp, g.eta, label, f0, scale, g.twW);
       if (nc > 0) {
         hook.mark(kKindGather);
-        k_fcol_gather<H><<<nc, H, col_smem<H>(), st>>>(Y, g.bank, plan.chunks + c0, plan.filters, partial, g.Wh,
-                                                        Whp, nslots, label, f0, g.twH);
+        k_fcol_gather<H><<<nc, H, col_smem<H>(), st>>>(Y, g.bank, plan.items, cb, partial, g.Wh, Whp, nslots,
+                                                        label, f0, g.twH);
       }
     }
   }
@@ -608,48 +640,72 @@ int fast_wave(const Geo& g, int wave_mib) {
   return (g.eta + nw - 1) / nw;
 }
 
-void build_fast_plan(const Geo& g, const int2* ranges, FastPlan* plan, std::vector<ChunkDesc>* chunks,
-                     std::vector<int>* filters, std::vector<int>* tile_begin, std::vector<int>* tile_slots) {
+int fast_col_ctas(const Geo& g, int per_sm) {
+  int dev = 0, sms = 0, fit = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (g.H) {
+#define SHF_OCC(HH)                                                                                   \
+  case HH:                                                                                            \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_fcol_gather<HH>, HH, col_smem<HH>()); \
+    break;
+    SHF_OCC(8) SHF_OCC(16) SHF_OCC(32) SHF_OCC(64) SHF_OCC(128) SHF_OCC(256) SHF_OCC(512) SHF_OCC(1024)
+#undef SHF_OCC
+    default: break;
+  }
+  if (e != cudaSuccess || fit < 1) return 0;
+  const int k = (per_sm <= 0 || per_sm > fit) ? fit : per_sm;
+  return k * sms;
+}
+
+void build_fast_plan(const Geo& g, const int2* ranges, FastPlan* plan, std::vector<WorkItem>* items,
+                     std::vector<int>* cta_begin, std::vector<int>* tile_begin, std::vector<int>* tile_slots) {
   const int ntiles = (g.Wh + kB - 1) / kB;
   const int wave = fast_wave(g, plan->wave_mib);
-  const size_t chunk = static_cast<size_t>(plan->chunk > 0 ? plan->chunk : 1);
-  chunks->clear();
-  filters->clear();
+  const int ctas = plan->col_ctas > 0 ? plan->col_ctas : 1;
+  items->clear();
+  cta_begin->clear();
   plan->wave_f0.clear();
   plan->wave_nf.clear();
-  plan->wave_chunk0.clear();
+  plan->wave_cta0.clear();
   std::vector<std::vector<int>> per_tile(ntiles);
+  int slot = 0;
   for (int f0 = 0; f0 < g.eta; f0 += wave) {
     const int nf = std::min(wave, g.eta - f0);
     plan->wave_f0.push_back(f0);
     plan->wave_nf.push_back(nf);
-    plan->wave_chunk0.push_back(static_cast<int>(chunks->size()));
-    for (int t = 0; t < ntiles; ++t) {
-      std::vector<int> act;
+    // this wave's (tile, filter) pairs in (tile, filter) order
+    const size_t first = items->size();
+    for (int t = 0; t < ntiles; ++t)
       for (int fl = 0; fl < nf; ++fl) {
         const int2 r = ranges[f0 + fl];
-        if (r.x <= r.y && t >= (r.x >> 3) && t <= (r.y >> 3)) act.push_back(fl);
+        if (r.x <= r.y && t >= (r.x >> 3) && t <= (r.y >> 3)) items->push_back(WorkItem{t, fl, 0, 0});
       }
-      for (size_t a = 0; a < act.size(); a += chunk) {
-        ChunkDesc c;
-        c.tile = t;
-        c.first = static_cast<int>(filters->size());
-        c.nf = static_cast<int>(std::min<size_t>(chunk, act.size() - a));
-        c.slot = static_cast<int>(chunks->size());
-        for (int i = 0; i < c.nf; ++i) filters->push_back(act[a + i]);
-        per_tile[t].push_back(c.slot);
-        chunks->push_back(c);
+    const long n = static_cast<long>(items->size() - first);
+    const int G = static_cast<int>(std::min<long>(ctas, n));
+    plan->wave_cta0.push_back(static_cast<int>(cta_begin->size()) - static_cast<int>(plan->wave_cta0.size()));
+    for (int c = 0; c <= G; ++c) cta_begin->push_back(static_cast<int>(first + (G > 0 ? n * c / G : 0)));
+    // one partial slot per run of one tile inside a CTA's range
+    for (int c = 0; c < G; ++c) {
+      const long b = n * c / G, e = n * (c + 1) / G;
+      for (long i = b; i < e; ++i) {
+        WorkItem& it = (*items)[first + i];
+        if (i == b || (*items)[first + i - 1].tile != it.tile) per_tile[it.tile].push_back(slot++);
+        it.slot = slot - 1;
       }
     }
   }
-  plan->nchunks_total = static_cast<int>(chunks->size());
+  plan->wave_cta0.push_back(static_cast<int>(cta_begin->size()) - static_cast<int>(plan->wave_cta0.size()));
+  plan->nslots = slot;
   tile_begin->assign(1, 0);
   tile_slots->clear();
   for (int t = 0; t < ntiles; ++t) {
     for (int sl : per_tile[t]) tile_slots->push_back(sl);
     tile_begin->push_back(static_cast<int>(tile_slots->size()));
   }
-  if (filters->empty()) filters->push_back(0);  // keep the device arrays non-empty
+  if (items->empty()) items->push_back(WorkItem{0, 0, 0, 0});  // keep the device arrays non-empty
   if (tile_slots->empty()) tile_slots->push_back(0);
 }
 

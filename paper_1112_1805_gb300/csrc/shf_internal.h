@@ -114,25 +114,28 @@ struct LaunchHook {
   }
 };
 
-// Static work list of the fast path: for every wave of filters, chunks of at
-// most `chunk` filters whose column support touches one tile of 8 columns.
-// Built per state from the filters' column ranges; the wave size and the
-// chunk size are the plan's tunable parameters.
-struct ChunkDesc {
-  int tile;   // column tile
-  int first;  // index into `filters` of the chunk's first filter
-  int nf;     // number of filters (1..chunk), ascending filter order
-  int slot;   // partial-sum slot of this chunk within its label
+// Static work list of the fast path.  The (column tile, filter) pairs of a
+// wave whose filter support touches the tile (8 half-spectrum columns) are
+// listed in (tile, filter) order and cut into one contiguous, balanced range
+// per CTA of a column launch, with as many CTAs as are resident at once.
+// Within a CTA's range, each run of one tile is one partial-sum slot of the
+// synthesis; the slots of a tile are summed in filter order.
+struct WorkItem {
+  int tile;    // column tile
+  int filter;  // wave-local filter index
+  int slot;    // partial-sum slot of the item's run (within its label)
+  int pad;
 };
-constexpr int kDefaultChunk = 2;     // filters per column chunk
 constexpr int kDefaultWaveMiB = 64;  // coefficient spectra per wave of filters
 struct FastPlan {
-  int chunk = kDefaultChunk;
   int wave_mib = kDefaultWaveMiB;
-  std::vector<int> wave_f0, wave_nf, wave_chunk0;  // per wave: first filter, filters, first chunk
-  int nchunks_total = 0;      // chunks of all waves of one label (= partial slots per label)
-  const ChunkDesc* chunks = nullptr;  // device [nchunks_total]
-  const int* filters = nullptr;       // device, wave-local filter indices
+  int col_ctas_per_sm = 0;  // CTAs per SM of the column launches (0: as many as fit)
+  int col_ctas = 0;         // resolved: CTAs of one column launch
+  std::vector<int> wave_f0, wave_nf;  // per wave: first filter, number of filters
+  std::vector<int> wave_cta0;         // per wave: first entry of cta_begin (size waves + 1)
+  int nslots = 0;                     // partial slots per label (all waves)
+  const WorkItem* items = nullptr;    // device, all waves
+  const int* cta_begin = nullptr;     // device, item range [cta_begin[c], cta_begin[c+1]) of CTA c
   const int* tile_begin = nullptr;    // device [ntiles + 1], into tile_slots
   const int* tile_slots = nullptr;    // device, slots of each tile in filter order
 };
@@ -152,11 +155,14 @@ cudaError_t run_fast_ustep(const Geo& g, const float2* T, const float* s, float*
 cudaError_t run_fast_iteration_body(const Geo& g, const FastPlan& plan, const float2* Ur, float2* uhat, float2* Y,
                                     float* bv, const float* thr, float2* partial, float2* T, int K, float scale,
                                     cudaStream_t st, const LaunchHook& hook);
+// Resident CTAs of one column launch for `per_sm` CTAs per SM (0: as many
+// as fit; larger values are clamped to that).
+int fast_col_ctas(const Geo& g, int per_sm);
 // Host construction of the work list from the filters' column ranges
-// (ranges_host[eta]) with plan->chunk and plan->wave_mib; returns the host
-// arrays to upload.
-void build_fast_plan(const Geo& g, const int2* ranges_host, FastPlan* plan, std::vector<ChunkDesc>* chunks,
-                     std::vector<int>* filters, std::vector<int>* tile_begin, std::vector<int>* tile_slots);
+// (ranges_host[eta]) for plan->wave_mib and plan->col_ctas; returns the host
+// arrays to upload (cta_begin holds one entry more per wave).
+void build_fast_plan(const Geo& g, const int2* ranges_host, FastPlan* plan, std::vector<WorkItem>* items,
+                     std::vector<int>* cta_begin, std::vector<int>* tile_begin, std::vector<int>* tile_slots);
 
 // Reverse mode of the unrolled iteration (shf_adjoint.cu).
 // gwbar = bwbar + J_P(wbar - bwbar), J_P the projection onto the face of the

@@ -62,8 +62,9 @@ def _check(o, g):
     assert labels_agree(g["labels"], o["labels"], o["gap"])
 
 
-FAST_PLANS = [dict(wave_mib=1, chunk=1), dict(wave_mib=1, chunk=4), dict(wave_mib=2, chunk=3),
-              dict(wave_mib=64, chunk=2), dict(wave_mib=4096, chunk=16)]
+FAST_PLANS = [dict(wave_mib=1, col_ctas_per_sm=1), dict(wave_mib=1, col_ctas_per_sm=0),
+              dict(wave_mib=2, col_ctas_per_sm=3), dict(wave_mib=64, col_ctas_per_sm=2),
+              dict(wave_mib=4096, col_ctas_per_sm=32)]
 
 
 def test_fast_plans_match_oracle(torch_mod, oracle_mod):
@@ -75,7 +76,7 @@ def test_fast_plans_match_oracle(torch_mod, oracle_mod):
     for p in FAST_PLANS:
         g = _run(torch_mod, img, cb, 3, Lam, T, p)
         assert g["plan"]["fast"] == 1
-        assert g["plan"]["wave_mib"] == p["wave_mib"] and g["plan"]["chunk"] == p["chunk"]
+        assert g["plan"]["wave_mib"] == p["wave_mib"] and g["plan"]["col_ctas_per_sm"] == p["col_ctas_per_sm"]
         _check(o, g)
 
 
@@ -107,7 +108,8 @@ def test_bad_plans_are_rejected_and_keep_the_old_plan(torch_mod):
     from paper_1112_1805_gb300 import binding as B
     from paper_1112_1805_gb300.api import FilterBank, ShearletSegmenter
 
-    for H, W, bad in ((64, 64, dict(wave_mib=64, chunk=0)), (64, 64, dict(wave_mib=0, chunk=2)),
+    for H, W, bad in ((64, 64, dict(wave_mib=64, col_ctas_per_sm=-1)), (64, 64, dict(wave_mib=0, col_ctas_per_sm=0)),
+                      (64, 64, dict(wave_mib=64, col_ctas_per_sm=33)),
                       (48, 80, dict(tile_cols=0, tile_rows=1, groups=1)),
                       (48, 80, dict(tile_cols=8, tile_rows=10000, groups=1))):
         img, cb, Lam = _problem(H, W, 3, 2, 34)
@@ -137,7 +139,7 @@ def test_tune_restores_the_iterate_and_keeps_parity(torch_mod, oracle_mod, H, W,
     best = seg.tune(2)
     assert best["us_per_iter"] > 0 and np.isfinite(best["us_per_iter"])
     plan = seg.plan()
-    for k in ("fast", "wave_mib", "chunk", "tile_cols", "tile_rows", "groups"):
+    for k in ("fast", "wave_mib", "col_ctas_per_sm", "tile_cols", "tile_rows", "groups"):
         assert plan[k] == best[k]
     for k, v in snap.items():
         assert np.array_equal(seg.get(k).cpu().numpy(), v)

@@ -14,6 +14,7 @@
 // The coefficient spectra of one wave (a few tens of MB) stay in L2 between
 // the three kernels; b_v is streamed with evict-first hints.
 #include <algorithm>
+#include <cstdint>
 
 #include "shf_fft_reg.cuh"
 #include "shf_internal.h"
@@ -233,91 +234,169 @@ __global__ void __launch_bounds__(H) k_fcol_reduce_inv(const float2* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// Row kernel: a CTA of L threads owns 8 consecutive rows of one coefficient
-// plane; a real row of length W = 2L is the complex row z[n] = x[2n] + i x[2n+1].
+// Row kernels: a real row of length W = 2L is the complex row
+// z[n] = x[2n] + i x[2n+1], transformed by a group of T = L/8 threads.
 // ---------------------------------------------------------------------------
+
+// 16-byte asynchronous copies global -> shared (the copying thread waits for
+// its own copies with cp_async_wait_all; the group barrier then publishes
+// them to the group).  `evict_first`: the source is streamed through L2.
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src, bool evict_first, uint64_t policy) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst_smem));
+  if (evict_first)
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "l"(policy)
+                 : "memory");
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ uint64_t evict_first_policy() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// Shared memory of one row group of k_wrow_shrink: FFT exchange buffer(s),
+// and the stage that receives the next row's spectrum columns and b_v row.
+// Every region is a whole number of 16-byte units (even float2 counts) so that
+// the stage is 16-byte aligned for the asynchronous copies.
+__host__ __device__ constexpr int even2(int n) { return (n + 1) & ~1; }
+template <int L>
+struct RowGroupSmem {
+  static constexpr int T = L / 8;
+  static constexpr int NBUF = T <= 32 ? 1 : 2;  // warp-sized groups exchange through one buffer
+  static constexpr int BUF = even2(reg::row_buf(L));
+  static constexpr int SX = L + 8;              // spectrum columns [c0, c0 + SX), SX >= the row pitch
+  static constexpr int SB = L;                  // b_v row as float2
+  static constexpr int SIZE = NBUF * BUF + SX + SB;
+  static constexpr int TW = even2(L + 1);                     // exp(-2 pi i m / W), m <= L
+  static constexpr int PT = even2(reg::Passes<L>::TWSIZE);    // per-pass twiddles
+  static constexpr int RPC = 256 / T;                         // row groups per CTA of 256 threads
+  static constexpr int TOTAL = TW + PT + RPC * SIZE;          // float2 per CTA
+};
 
 // v-step and b_v update of Sec. 3 on rows of (S u)_f: g = b_v + c,
 // b_v <- clip(g, -t, t), d = soft(g, t) - clip(g, -t, t) = g - 2 clip(g);
 // d (= v - b_v of the new iterate) is transformed back in place.
-// One row per group of T = L/8 threads (a warp for L = 256): the row's
-// exchanges need only the group's barrier, and its global accesses are
-// contiguous row segments.  The thread's b_v values are requested first, so
-// that their DRAM latency overlaps the staging and the inverse transform.
-// Four CTAs per SM (at most 64 registers): the row work is latency-bound, and
-// occupancy is what hides the b_v and spectrum loads.
+// Rows r = (filter fl, row) with r = fl H + row over the wave's nf filters;
+// resident CTAs, each row group takes rows gid, gid + G, ... (G groups in
+// all).  While a group transforms its row, the next row's spectrum columns
+// (only the filter's column tiles [c0, c1]) and b_v row are copied into the
+// group's stage; the twiddle tables are built once per CTA.
 template <int L>
 __global__ void __launch_bounds__(256, 4) k_wrow_shrink(float2* __restrict__ Y, float* __restrict__ bv,
-                                                     const float* __restrict__ thr,
-                                                     const int2* __restrict__ ranges, int H, int Whp, int eta,
-                                                     int label, int f0, float scale,
-                                                     const float2* __restrict__ twW) {
-  constexpr int T = L / 8;
-  constexpr int RPC = 256 / T;  // rows per CTA
-  constexpr int BUF = reg::row_buf(L);
-  extern __shared__ float2 sm[];
-  float2* tw = sm;                                   // exp(-2 pi i m / W), m <= L
-  float2* pt = tw + (L + 1);                         // per-pass twiddles of the length-L transform
+                                                        const float* __restrict__ thr,
+                                                        const int2* __restrict__ ranges, int H, int Whp, int eta,
+                                                        int label, int f0, int nf, float scale,
+                                                        const float2* __restrict__ twW) {
+  using SM = RowGroupSmem<L>;
+  constexpr int T = SM::T;
+  constexpr int RPC = SM::RPC;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* tw = sm;                    // exp(-2 pi i m / W), m <= L
+  float2* pt = tw + SM::TW;           // per-pass twiddles of the length-L transform
   const int grp = threadIdx.x / T, tt = threadIdx.x % T;
-  float2* b0 = pt + reg::Passes<L>::TWSIZE + grp * 2 * BUF;
-  float2* b1 = b0 + BUF;
+  float2* gb = pt + SM::PT + grp * SM::SIZE;
+  float2* fb0 = gb;
+  float2* fb1 = gb + (SM::NBUF - 1) * SM::BUF;
+  float2* sX = gb + SM::NBUF * SM::BUF;
+  float2* sB = sX + SM::SX;
   const int bar = 1 + grp;
-  const int row = blockIdx.x * RPC + grp;
-  const bool live = row < H;
-  const int fl = blockIdx.y, f = f0 + fl;
-  float2* b2 = reinterpret_cast<float2*>(bv) + ((static_cast<size_t>(label) * eta + f) * H + (live ? row : 0)) * L;
-  float2 bo[8];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) bo[k] = live ? __ldcs(b2 + tt + k * T) : make_float2(0.f, 0.f);
-  const float th = thr[f];
-  // the row spectrum is zero outside the filter's column tiles [c0, c1]
-  const int2 rg = ranges[f];
-  const int c0 = rg.x <= rg.y ? (rg.x & ~7) : L + 1;
-  const int c1 = rg.x <= rg.y ? min(L, (rg.y | 7)) : -1;
-  float2* X = Y + static_cast<size_t>(H) * Whp * fl + static_cast<size_t>(live ? row : 0) * Whp;
-  for (int i = tt; i <= L; i += T)
-    b1[reg::ridx(i)] = (live && i >= c0 && i <= c1) ? X[i] : make_float2(0.f, 0.f);
+  const int G = gridDim.x * RPC;
+  const int gid = blockIdx.x * RPC + grp;
+  const int rows = nf * H;
+  const int niter = (rows + G - 1) / G;  // the same for every group: dead rows still take part in barriers
+  const uint64_t pol = evict_first_policy();
+
+  // request row r's spectrum columns (its filter's column range only) and
+  // its b_v row into the stage
+  auto request_x = [&](int r) {
+    if (r >= rows) return;
+    const int fl = r / H, row = r - fl * H;
+    const int2 rg = ranges[f0 + fl];
+    if (rg.x <= rg.y) {
+      const int c0 = rg.x & ~7;
+      const int c1e = min(Whp, (rg.y | 7) + 1);
+      const float2* X = Y + (static_cast<size_t>(fl) * H + row) * Whp + c0;
+      for (int q = tt; q < (c1e - c0) / 2; q += T) cp_async16(sX + 2 * q, X + 2 * q, false, pol);
+    }
+  };
+  auto request_b = [&](int r) {
+    if (r >= rows) return;
+    const int fl = r / H, row = r - fl * H;
+    const float2* B =
+        reinterpret_cast<const float2*>(bv) + ((static_cast<size_t>(label) * eta + f0 + fl) * H + row) * L;
+    for (int q = tt; q < L / 2; q += T) cp_async16(sB + 2 * q, B + 2 * q, true, pol);
+  };
+
+  request_x(gid);
+  request_b(gid);
   load_table(tw, twW, L + 1);
   reg::build_pass_twiddles<L, 2>(pt, twW, threadIdx.x, blockDim.x);
   __syncthreads();
-  float2 v[8];
+  for (int it = 0; it < niter; ++it) {
+    const int r = gid + it * G;
+    const bool live = r < rows;
+    const int fl = live ? r / H : 0, row = live ? r - fl * H : 0, f = f0 + fl;
+    const int2 rg = ranges[f];
+    const bool any = live && rg.x <= rg.y;
+    const int c0 = any ? (rg.x & ~7) : L + 1;
+    const int c1 = any ? min(L, (rg.y | 7)) : -1;
+    const float th = thr[f];
+    cp_async_commit_wait_all();
+    reg::group_sync<T>(bar);
+    float2 v[8];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {  // inverse packing Z[n] = (X_n + conj X_{L-n}) + i e^{+2 pi i n/W} (X_n - conj X_{L-n})
-    const int n = tt + k * T;
-    const float2 a = b1[reg::ridx(n)];
-    const float2 c = c_conj(b1[reg::ridx(L - n)]);
-    const float2 s = c_add(a, c), d = c_sub(a, c);
-    const float2 t = c_mul(c_conj(tw[n]), d);
-    v[k] = make_float2(s.x - t.y, s.y + t.x);
-  }
-  reg::row_fft<L, +1>(v, tt, b0, b1, pt, bar);
-  if (live) {
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const float gx = fmaf(scale, v[k].x, bo[k].x), gy = fmaf(scale, v[k].y, bo[k].y);
-      const float cx = fminf(fmaxf(gx, -th), th), cy = fminf(fmaxf(gy, -th), th);
-      __stcs(b2 + tt + k * T, make_float2(cx, cy));
-      v[k] = make_float2(gx - 2.f * cx, gy - 2.f * cy);
+    for (int k = 0; k < 8; ++k) {  // inverse packing Z[n] = (X_n + conj X_{L-n}) + i e^{+2 pi i n/W} (X_n - conj X_{L-n})
+      const int n = tt + k * T, m = L - n;
+      const float2 a = (n >= c0 && n <= c1) ? sX[n - c0] : make_float2(0.f, 0.f);
+      const float2 c = (m >= c0 && m <= c1) ? c_conj(sX[m - c0]) : make_float2(0.f, 0.f);
+      const float2 s2 = c_add(a, c), d = c_sub(a, c);
+      const float2 t = c_mul(c_conj(tw[n]), d);
+      v[k] = make_float2(s2.x - t.y, s2.y + t.x);
     }
-  } else {
+    reg::group_sync<T>(bar);  // the spectrum stage is read: refill it with the group's next row
+    request_x(r + G);
+    if (SM::NBUF == 1)
+      reg::row_fft1<L, +1>(v, tt, fb0, pt, bar);
+    else
+      reg::row_fft<L, +1>(v, tt, fb0, fb1, pt, bar);
+    float2* X = Y + (static_cast<size_t>(fl) * H + row) * Whp;
+    if (live) {
+      float2* b2 = reinterpret_cast<float2*>(bv) + ((static_cast<size_t>(label) * eta + f) * H + row) * L;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = make_float2(0.f, 0.f);
-  }
-  reg::row_fft<L, -1>(v, tt, b0, b1, pt, bar);
-  reg::group_sync<T>(bar);  // the last pass may still read b1
+      for (int k = 0; k < 8; ++k) {
+        const float2 bo = sB[tt + k * T];
+        const float gx = fmaf(scale, v[k].x, bo.x), gy = fmaf(scale, v[k].y, bo.y);
+        const float cx = fminf(fmaxf(gx, -th), th), cy = fminf(fmaxf(gy, -th), th);
+        __stcs(b2 + tt + k * T, make_float2(cx, cy));
+        v[k] = make_float2(gx - 2.f * cx, gy - 2.f * cy);
+      }
+    } else {
 #pragma unroll
-  for (int k = 0; k < 8; ++k) b1[reg::ridx(tt + k * T)] = v[k];
-  reg::group_sync<T>(bar);
-  // forward unpacking X[k] = 1/2 [(Z_k + conj Z_{L-k}) - i e^{-2 pi i k/W} (Z_k - conj Z_{L-k})]
-  if (live) {
+      for (int k = 0; k < 8; ++k) v[k] = make_float2(0.f, 0.f);
+    }
+    reg::group_sync<T>(bar);  // the b_v stage is read: refill it with the group's next row
+    request_b(r + G);
+    if (SM::NBUF == 1)
+      reg::row_fft1<L, -1>(v, tt, fb0, pt, bar);
+    else
+      reg::row_fft<L, -1>(v, tt, fb0, fb1, pt, bar);
+    float2* ub = SM::NBUF == 1 ? fb0 : fb1;
+    reg::group_sync<T>(bar);  // the last pass may still read the buffer
+#pragma unroll
+    for (int k = 0; k < 8; ++k) ub[reg::ridx(tt + k * T)] = v[k];
+    reg::group_sync<T>(bar);
+    // forward unpacking X[k] = 1/2 [(Z_k + conj Z_{L-k}) - i e^{-2 pi i k/W} (Z_k - conj Z_{L-k})]
     for (int i = c0 + tt; i <= c1; i += T) {
-      const float2 a = b1[reg::ridx(i == L ? 0 : i)];
-      const float2 c = c_conj(b1[reg::ridx(i == 0 ? 0 : L - i)]);
-      const float2 s = c_add(a, c), d = c_sub(a, c);
+      const float2 a = ub[reg::ridx(i == L ? 0 : i)];
+      const float2 c = c_conj(ub[reg::ridx(i == 0 ? 0 : L - i)]);
+      const float2 s2 = c_add(a, c), d = c_sub(a, c);
       const float2 t = c_mul(tw[i], d);
-      X[i] = make_float2(0.5f * (s.x + t.y), 0.5f * (s.y - t.x));
+      X[i] = make_float2(0.5f * (s2.x + t.y), 0.5f * (s2.y - t.x));
     }
   }
+  cp_async_commit_wait_all();  // no copy outlives the kernel
 }
 
 // Euclidean projection of g[0..K) onto the unit simplex, as the paper
@@ -478,6 +557,11 @@ size_t col_smem() {
 }
 
 template <int L>
+size_t shrink_smem() {
+  return sizeof(float2) * RowGroupSmem<L>::TOTAL;
+}
+
+template <int L>
 size_t row_smem() {
   return sizeof(float2) * ((L + 1) + reg::Passes<L>::TWSIZE + (256 / (L / 8)) * 2 * reg::row_buf(L));
 }
@@ -507,8 +591,12 @@ cudaError_t iteration_body(const Geo& g, const FastPlan& plan, const float2* Ur,
         k_fcol_fan<H><<<nc, H, col_smem<H>(), st>>>(uhat, g.bank, plan.items, cb, Y, g.Wh, Whp, label, f0, g.twH);
       }
       hook.mark(kKindShrink);
-      k_wrow_shrink<L><<<dim3((g.H + row_rows_per_cta<L>() - 1) / row_rows_per_cta<L>(), nf), 256, row_smem<L>(),
-                         st>>>(Y, bv, thr, g.ranges, g.H, Whp, g.eta, label, f0, scale, g.twW);
+      {
+        const int groups = (nf * g.H + RowGroupSmem<L>::RPC - 1) / RowGroupSmem<L>::RPC;
+        const int ctas = std::min(groups, std::max(plan.row_ctas, 1));
+        k_wrow_shrink<L><<<ctas, 256, shrink_smem<L>(), st>>>(Y, bv, thr, g.ranges, g.H, Whp, g.eta, label, f0, nf,
+                                                              scale, g.twW);
+      }
       if (nc > 0) {
         hook.mark(kKindGather);
         k_fcol_gather<H><<<nc, H, col_smem<H>(), st>>>(Y, g.bank, plan.items, cb, partial, g.Wh, Whp, nslots,
@@ -539,7 +627,7 @@ cudaError_t prepare_col() {
 
 template <int L>
 cudaError_t prepare_row() {
-  cudaError_t e = allow_smem(k_wrow_shrink<L>, row_smem<L>());
+  cudaError_t e = allow_smem(k_wrow_shrink<L>, shrink_smem<L>());
   if (e == cudaSuccess) e = allow_smem(k_wrow_ustep<L, 4>, ustep_smem<L>(4));
   if (e == cudaSuccess) e = allow_smem(k_wrow_ustep<L, 8>, ustep_smem<L>(8));
   return e;
@@ -658,6 +746,25 @@ int fast_col_ctas(const Geo& g, int per_sm) {
   if (e != cudaSuccess || fit < 1) return 0;
   const int k = (per_sm <= 0 || per_sm > fit) ? fit : per_sm;
   return k * sms;
+}
+
+int fast_row_ctas(const Geo& g) {
+  int dev = 0, sms = 0, fit = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (g.L) {
+#define SHF_OCC(LL)                                                                                          \
+  case LL:                                                                                                   \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_shrink<LL>, 256, shrink_smem<LL>()); \
+    break;
+    SHF_OCC(8) SHF_OCC(16) SHF_OCC(32) SHF_OCC(64) SHF_OCC(128) SHF_OCC(256) SHF_OCC(512) SHF_OCC(1024)
+#undef SHF_OCC
+    default: break;
+  }
+  if (e != cudaSuccess || fit < 1) return 0;
+  return fit * sms;
 }
 
 void build_fast_plan(const Geo& g, const int2* ranges, FastPlan* plan, std::vector<WorkItem>* items,

@@ -228,6 +228,35 @@ __device__ __forceinline__ void row_fft(float2 (&v)[8], int tt, float2* buf0, fl
     rrun_pass<N, S, (NP > 3 ? 3 : 0)>(v, tt, buf0, buf1, pt);
   }
 }
+
+// The same with one buffer: every exchange reads the stored values and waits
+// for the whole group before the next stores.  Starts with a barrier.
+template <int N, int S, int P>
+__device__ __forceinline__ void rpass1(float2 (&v)[8], int tt, float2* buf, const float2* pt, int bar_id) {
+  constexpr int R = Passes<N>::radix(P);
+  constexpr int Ns = Passes<N>::span(P);
+  constexpr int T = N / 8;
+  if (P > 0) {
+    group_sync<T>(bar_id);
+    rload_stride<N>(v, tt, buf);
+  }
+  if (P < Passes<N>::NPASS - 1) {
+    pass_bfly<N, R, S>(v, tt, Ns, pt + Passes<N>::twoff(P));
+    group_sync<T>(bar_id);
+    rpass_store<N, R, Ns>(v, tt, buf);
+  } else {
+    pass_bfly<N, R, S>(v, tt, Ns, pt + Passes<N>::twoff(P));
+  }
+}
+
+template <int N, int S>
+__device__ __forceinline__ void row_fft1(float2 (&v)[8], int tt, float2* buf, const float2* pt, int bar_id) {
+  constexpr int NP = Passes<N>::NPASS;
+  rpass1<N, S, 0>(v, tt, buf, pt, bar_id);
+  if (NP > 1) rpass1<N, S, (NP > 1 ? 1 : 0)>(v, tt, buf, pt, bar_id);
+  if (NP > 2) rpass1<N, S, (NP > 2 ? 2 : 0)>(v, tt, buf, pt, bar_id);
+  if (NP > 3) rpass1<N, S, (NP > 3 ? 3 : 0)>(v, tt, buf, pt, bar_id);
+}
 #endif
 
 #ifdef __CUDACC__

@@ -131,6 +131,7 @@ struct FastPlan {
   int wave_mib = kDefaultWaveMiB;
   int col_ctas_per_sm = 0;  // CTAs per SM of the column launches (0: as many as fit)
   int col_ctas = 0;         // resolved: CTAs of one column launch
+  int row_ctas = 0;         // resolved: resident CTAs of the row (v-step) launch
   std::vector<int> wave_f0, wave_nf;  // per wave: first filter, number of filters
   std::vector<int> wave_cta0;         // per wave: first entry of cta_begin (size waves + 1)
   int nslots = 0;                     // partial slots per label (all waves)
@@ -158,6 +159,8 @@ cudaError_t run_fast_iteration_body(const Geo& g, const FastPlan& plan, const fl
 // Resident CTAs of one column launch for `per_sm` CTAs per SM (0: as many
 // as fit; larger values are clamped to that).
 int fast_col_ctas(const Geo& g, int per_sm);
+// Resident CTAs of the row (v-step) kernel.
+int fast_row_ctas(const Geo& g);
 // Host construction of the work list from the filters' column ranges
 // (ranges_host[eta]) for plan->wave_mib and plan->col_ctas; returns the host
 // arrays to upload (cta_begin holds one entry more per wave).

@@ -17,7 +17,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libshearseg.so")
-SOURCES = ["shf_bank.cu", "shf_transform.cu", "shf_fast.cu", "shf_adjoint.cu", "shf_capi.cu", "shf_noalloc.cu"]
+SOURCES = ["shf_bank.cu", "shf_transform.cu", "shf_fast.cu", "shf_fast_col.cu", "shf_fast_row.cu", "shf_adjoint.cu",
+           "shf_capi.cu", "shf_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,90 @@
+// Fast path of the iteration (register FFTs, lengths R 2^a with R in {1, 3, 5}):
+// interface between the host-side plan (shf_fast.cu) and the kernels, which
+// live in shf_fast_col.cu (column transforms, per image height H) and
+// shf_fast_row.cu (row transforms, per half width L), so that the two sets of
+// template instances compile separately.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "shf_fft_reg.cuh"
+#include "shf_internal.h"
+
+// The supported transform lengths, for dispatch over template instances.
+#define SHF_FAST_SIZES(X) \
+  X(8) X(16) X(24) X(32) X(40) X(48) X(64) X(80) X(96) X(128) X(160) X(192) X(256) X(320) X(384) X(512) X(640) X(768) X(1024)
+
+namespace shf {
+namespace fast {
+
+#ifdef __CUDACC__
+// Programmatic dependent launch.  Every kernel of the iteration first builds
+// what needs no earlier result (twiddle tables, constant operands), then waits
+// for its predecessor grid to complete and flush (pdl_wait), and only then
+// lets its own dependent launch (pdl_trigger).  So when a kernel starts, every
+// grid before its immediate predecessor has completed, and the predecessor
+// has passed its own wait.  Both are no-ops for a launch without the
+// programmatic-serialization attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+__device__ __forceinline__ void load_table(float2* dst, const float2* __restrict__ src, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+// Launch with programmatic stream serialization: the kernel may start while
+// its predecessor drains, and waits for it in pdl_wait.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+template <typename KERN>
+cudaError_t allow_smem(KERN k, size_t bytes) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+}
+#endif
+
+// Column kernels (shf_fast_col.cu).  Whp: row pitch of the internal spectra.
+cudaError_t prepare_col_kernels();
+int col_ctas_per_sm(int H);  // resident CTAs per SM of the fan/gather kernels
+// Ur [K][H][Wh] -> uhat [K][H][Whp]: column-forward of the row spectra of u.
+cudaError_t col_fwd(const Geo& g, const float2* Ur, float2* uhat, int K, int Whp, cudaStream_t st);
+// Y_f = column-inverse(W_f * uhat_label) on the (tile, filter) items of CTA
+// ranges cta_begin[0..nc].
+cudaError_t col_fan(const Geo& g, int nc, const float2* uhat, const WorkItem* items, const int* cta_begin,
+                    float2* Y, int Whp, int label, int f0, cudaStream_t st);
+// partial[label][slot] = sum over runs of items of W_f * column-forward(Y_f).
+cudaError_t col_gather(const Geo& g, int nc, const float2* Y, const WorkItem* items, const int* cta_begin,
+                       float2* partial, int Whp, int nslots, int label, int f0, cudaStream_t st);
+// T [K][H][Wh] = column-inverse of the per-tile sums of the partial slots.
+cudaError_t col_reduce(const Geo& g, const float2* partial, const int* tile_begin, const int* tile_slots, float2* T,
+                       int K, int nslots, cudaStream_t st);
+
+// Row kernels (shf_fast_row.cu).
+cudaError_t prepare_row_kernels();
+int row_ctas_per_sm(int L);     // resident CTAs per SM of the v-step kernel
+int row_groups_per_cta(int L);  // rows in flight per CTA of the v-step kernel
+// v-step on the wave's rows: ctas resident CTAs over nf filters of `label`.
+cudaError_t row_shrink(const Geo& g, int ctas, float2* Y, float* bv, const float* thr, int Whp, int label, int f0,
+                       int nf, float scale, cudaStream_t st);
+// Shared memory of the u/w-step for K labels (0 if L is not supported).
+size_t ustep_smem_bytes(int L, int K);
+cudaError_t row_ustep(const Geo& g, const float2* T, const float* s, float* w, float* bw, float* u, float2* Ur, int K,
+                      float gamma, float scale, cudaStream_t st);
+
+}  // namespace fast
+}  // namespace shf

@@ -1,0 +1,322 @@
+// Column transforms of the fast path: the analysis fan-out and the synthesis
+// gather over the filters of a wave, and the forward/inverse column passes of
+// u and of the synthesis sum (Sec. 2, eq. for S and S^T; Sec. 3, ADMM steps).
+#include "shf_fast.h"
+
+namespace shf {
+namespace fast {
+namespace {
+
+using reg::kB;
+using reg::kS;
+using reg::sidx;
+
+// Per-pass twiddle table of a length-N transform, built by the whole CTA.
+template <int N, int TWSTEP>
+__device__ __forceinline__ void load_pass_table(float2* pt, const float2* __restrict__ tw) {
+  reg::build_pass_twiddles<N, TWSTEP>(pt, tw, threadIdx.x, blockDim.x);
+}
+
+// ---------------------------------------------------------------------------
+// Column kernels: a CTA of H threads owns 8 consecutive half-spectrum columns
+// (thread (b, tt) holds rows tt + k H/8 of column 8*blockIdx.x + b).  The
+// internal spectra (uhat, Y, partial) use the row pitch Whp = Wh rounded up to
+// 8, so that each row segment of a tile is one aligned 64-byte piece; Ur and T,
+// shared with the generic kernels, use the pitch Wh.  Global operands of the
+// next filter are loaded while the current transform runs.
+// ---------------------------------------------------------------------------
+
+// Resident CTAs of H threads (whole warps) to ask for: 32 warps per SM (64
+// registers per thread) for powers of two; for H = 3 2^a or 5 2^a, whose
+// radix-R pass holds more values, about 80 registers per thread.
+constexpr int col_min_blocks(int H) {
+  return reg::odd_part(H) == 1
+             ? (32 / ((H + 31) / 32) > 32 ? 32 : (32 / ((H + 31) / 32) > 0 ? 32 / ((H + 31) / 32) : 1))
+             : ((65536 / 80) / (32 * ((H + 31) / 32)) > 0 ? (65536 / 80) / (32 * ((H + 31) / 32)) : 1);
+}
+
+template <int H>
+__global__ void __launch_bounds__(H) k_fcol_fwd(const float2* __restrict__ in, float2* __restrict__ out, int Wh,
+                                                int Whp, const float2* __restrict__ twH) {
+  extern __shared__ float2 sm[];
+  float2* tw = sm;  // per-pass twiddles
+  float2* b0 = sm + reg::Passes<H>::TWSIZE;
+  float2* b1 = b0 + reg::batch_rows(H) * kS;
+  const int b = threadIdx.x & 7, tt = threadIdx.x >> 3;
+  const int col = blockIdx.x * kB + b;
+  const bool ok = col < Wh;
+  const float2* src = in + static_cast<size_t>(H) * Wh * blockIdx.y + col;
+  load_pass_table<H, 1>(tw, twH);
+  pdl_wait();
+  pdl_trigger();
+  float2 v[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = ok ? src[static_cast<size_t>(tt + k * (H / 8)) * Wh] : make_float2(0.f, 0.f);
+  __syncthreads();
+  reg::fft<H, -1>(v, tt, b, b0, b1, tw);
+  if (ok) {
+    float2* dst = out + static_cast<size_t>(H) * Whp * blockIdx.y + col;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) dst[static_cast<size_t>(tt + k * (H / 8)) * Whp] = v[k];
+  }
+}
+
+template <int H>
+__device__ __forceinline__ void load_bank8(float (&w)[8], const float* __restrict__ wf, int Wh, int tt, int col,
+                                           bool ok) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) w[k] = ok ? __ldg(wf + static_cast<size_t>(tt + k * (H / 8)) * Wh + col) : 0.f;
+}
+
+template <int H>
+__device__ __forceinline__ void load_tile8(float2 (&v)[8], const float2* __restrict__ src, int pitch, int tt,
+                                           int col, bool ok) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    v[k] = ok ? src[static_cast<size_t>(tt + k * (H / 8)) * pitch + col] : make_float2(0.f, 0.f);
+}
+
+// Analysis fan-out: for every item (tile, filter) of the CTA's range,
+// Y_f = column-inverse(W_f * uhat) on the tile.  The next item's filter tile
+// (and, at a tile change, the next spectrum tile) is requested while the
+// current transform runs.
+template <int H>
+__global__ void __launch_bounds__(H, col_min_blocks(H))
+    k_fcol_fan(const float2* __restrict__ uhat, const float* __restrict__ bank, const WorkItem* __restrict__ items,
+               const int* __restrict__ cta_begin, float2* __restrict__ Y, int Wh, int Whp, int label, int f0,
+               const float2* __restrict__ twH) {
+  extern __shared__ float2 sm[];
+  float2* tw = sm;  // per-pass twiddles
+  float2* b0 = sm + reg::Passes<H>::TWSIZE;
+  float2* b1 = b0 + reg::batch_rows(H) * kS;
+  const int ib = cta_begin[blockIdx.x], ie = cta_begin[blockIdx.x + 1];
+  if (ib >= ie) return;
+  const int b = threadIdx.x & 7, tt = threadIdx.x >> 3;
+  const size_t Pb = static_cast<size_t>(H) * Wh, Pp = static_cast<size_t>(H) * Whp;
+  WorkItem it = items[ib];
+  int col = it.tile * kB + b;
+  bool ok = col < Wh;
+  float2 u[8];
+  float w[8];
+  load_bank8<H>(w, bank + Pb * (f0 + it.filter), Wh, tt, col, ok);
+  load_pass_table<H, 1>(tw, twH);
+  pdl_wait();
+  pdl_trigger();
+  load_tile8<H>(u, uhat + Pp * label, Whp, tt, col, ok);
+  __syncthreads();
+  for (int i = ib; i < ie; ++i) {
+    float2 v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = c_scale(u[k], w[k]);
+    const int fl = it.filter, ccol = col;
+    const bool cok = ok;
+    if (i + 1 < ie) {
+      const WorkItem nx = items[i + 1];
+      col = nx.tile * kB + b;
+      ok = col < Wh;
+      load_bank8<H>(w, bank + Pb * (f0 + nx.filter), Wh, tt, col, ok);
+      if (nx.tile != it.tile) load_tile8<H>(u, uhat + Pp * label, Whp, tt, col, ok);
+      it = nx;
+    }
+    reg::fft<H, +1>(v, tt, b, b0, b1, tw);
+    if (cok) {
+      float2* dst = Y + Pp * fl + ccol;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) dst[static_cast<size_t>(tt + k * (H / 8)) * Whp] = v[k];
+    }
+  }
+}
+
+// Synthesis gather: partial[label][slot] = sum over a run of items of one
+// tile of W_f * column-forward(Y_f), stored compactly as [H][8]; the next
+// item's coefficient tile is requested while the current transform runs.
+template <int H>
+__global__ void __launch_bounds__(H, col_min_blocks(H))
+    k_fcol_gather(const float2* __restrict__ Y, const float* __restrict__ bank, const WorkItem* __restrict__ items,
+                  const int* __restrict__ cta_begin, float2* __restrict__ partial, int Wh, int Whp, int nslots,
+                  int label, int f0, const float2* __restrict__ twH) {
+  extern __shared__ float2 sm[];
+  float2* tw = sm;  // per-pass twiddles
+  float2* b0 = sm + reg::Passes<H>::TWSIZE;
+  float2* b1 = b0 + reg::batch_rows(H) * kS;
+  const int ib = cta_begin[blockIdx.x], ie = cta_begin[blockIdx.x + 1];
+  if (ib >= ie) return;
+  const int b = threadIdx.x & 7, tt = threadIdx.x >> 3;
+  const size_t Pb = static_cast<size_t>(H) * Wh, Pp = static_cast<size_t>(H) * Whp;
+  WorkItem it = items[ib];
+  int col = it.tile * kB + b;
+  bool ok = col < Wh;
+  float2 acc[8], y[8];
+  float w[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc[k] = make_float2(0.f, 0.f);
+  load_pass_table<H, 1>(tw, twH);
+  pdl_wait();
+  pdl_trigger();
+  load_tile8<H>(y, Y + Pp * it.filter, Whp, tt, col, ok);
+  __syncthreads();
+  for (int i = ib; i < ie; ++i) {
+    float2 v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = y[k];
+    load_bank8<H>(w, bank + Pb * (f0 + it.filter), Wh, tt, col, ok);
+    WorkItem nx = it;
+    int ncol = col;
+    bool nok = ok;
+    if (i + 1 < ie) {
+      nx = items[i + 1];
+      ncol = nx.tile * kB + b;
+      nok = ncol < Wh;
+      load_tile8<H>(y, Y + Pp * nx.filter, Whp, tt, ncol, nok);
+    }
+    reg::fft<H, -1>(v, tt, b, b0, b1, tw);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      acc[k].x = fmaf(w[k], v[k].x, acc[k].x);
+      acc[k].y = fmaf(w[k], v[k].y, acc[k].y);
+    }
+    if (i + 1 == ie || nx.slot != it.slot) {
+      float2* dst = partial + (static_cast<size_t>(label) * nslots + it.slot) * H * kB + b;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        dst[static_cast<size_t>(tt + k * (H / 8)) * kB] = acc[k];
+        acc[k] = make_float2(0.f, 0.f);
+      }
+    }
+    it = nx;
+    col = ncol;
+    ok = nok;
+  }
+}
+
+// T[label] on one tile = column-inverse of the sum of the tile's partial
+// slots, in the fixed slot order (filter order).
+template <int H>
+__global__ void __launch_bounds__(H) k_fcol_reduce_inv(const float2* __restrict__ partial,
+                                                       const int* __restrict__ tile_begin,
+                                                       const int* __restrict__ tile_slots, float2* __restrict__ T,
+                                                       int Wh, int nslots, const float2* __restrict__ twH) {
+  extern __shared__ float2 sm[];
+  float2* tw = sm;  // per-pass twiddles
+  float2* b0 = sm + reg::Passes<H>::TWSIZE;
+  float2* b1 = b0 + reg::batch_rows(H) * kS;
+  const int b = threadIdx.x & 7, tt = threadIdx.x >> 3;
+  const int tile = blockIdx.x, label = blockIdx.y;
+  const int col = tile * kB + b;
+  const bool ok = col < Wh;
+  float2 v[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = make_float2(0.f, 0.f);
+  load_pass_table<H, 1>(tw, twH);
+  pdl_wait();
+  pdl_trigger();
+  const int s0 = tile_begin[tile], s1 = tile_begin[tile + 1];
+  for (int si = s0; si < s1; ++si) {
+    const float2* src = partial + (static_cast<size_t>(label) * nslots + tile_slots[si]) * H * kB + b;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = c_add(v[k], src[static_cast<size_t>(tt + k * (H / 8)) * kB]);
+  }
+  __syncthreads();
+  reg::fft<H, +1>(v, tt, b, b0, b1, tw);
+  if (ok) {
+    float2* dst = T + static_cast<size_t>(H) * Wh * label + col;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) dst[static_cast<size_t>(tt + k * (H / 8)) * Wh] = v[k];
+  }
+}
+
+template <int N>
+size_t col_smem() {
+  return sizeof(float2) * (reg::Passes<N>::TWSIZE + 2 * reg::batch_rows(N) * kS);
+}
+
+template <int H>
+cudaError_t prepare_col_t() {
+  const size_t s = col_smem<H>();
+  cudaError_t e = allow_smem(k_fcol_fwd<H>, s);
+  if (e == cudaSuccess) e = allow_smem(k_fcol_fan<H>, s);
+  if (e == cudaSuccess) e = allow_smem(k_fcol_gather<H>, s);
+  if (e == cudaSuccess) e = allow_smem(k_fcol_reduce_inv<H>, s);
+  return e;
+}
+
+}  // namespace
+
+cudaError_t prepare_col_kernels() {
+#define SHF_PREP(N) \
+  if (e == cudaSuccess) e = prepare_col_t<N>();
+  cudaError_t e = cudaSuccess;
+  SHF_FAST_SIZES(SHF_PREP)
+#undef SHF_PREP
+  return e;
+}
+
+int col_ctas_per_sm(int H) {
+  int fit = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (H) {
+#define SHF_OCC(N)                                                                                \
+  case N:                                                                                         \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_fcol_gather<N>, N, col_smem<N>()); \
+    break;
+    SHF_FAST_SIZES(SHF_OCC)
+#undef SHF_OCC
+    default: break;
+  }
+  return e == cudaSuccess ? fit : 0;
+}
+
+cudaError_t col_fwd(const Geo& g, const float2* Ur, float2* uhat, int K, int Whp, cudaStream_t st) {
+  const int ntiles = (g.Wh + kB - 1) / kB;
+  switch (g.H) {
+#define SHF_CASE(N) \
+  case N:           \
+    return launch_pdl(k_fcol_fwd<N>, dim3(ntiles, K), dim3(N), col_smem<N>(), st, Ur, uhat, g.Wh, Whp, g.twH);
+    SHF_FAST_SIZES(SHF_CASE)
+#undef SHF_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t col_fan(const Geo& g, int nc, const float2* uhat, const WorkItem* items, const int* cta_begin,
+                    float2* Y, int Whp, int label, int f0, cudaStream_t st) {
+  switch (g.H) {
+#define SHF_CASE(N)                                                                                              \
+  case N:                                                                                                        \
+    return launch_pdl(k_fcol_fan<N>, dim3(nc), dim3(N), col_smem<N>(), st, uhat, g.bank, items, cta_begin, Y, \
+                      g.Wh, Whp, label, f0, g.twH);
+    SHF_FAST_SIZES(SHF_CASE)
+#undef SHF_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t col_gather(const Geo& g, int nc, const float2* Y, const WorkItem* items, const int* cta_begin,
+                       float2* partial, int Whp, int nslots, int label, int f0, cudaStream_t st) {
+  switch (g.H) {
+#define SHF_CASE(N)                                                                                           \
+  case N:                                                                                                     \
+    return launch_pdl(k_fcol_gather<N>, dim3(nc), dim3(N), col_smem<N>(), st, Y, g.bank, items, cta_begin, \
+                      partial, g.Wh, Whp, nslots, label, f0, g.twH);
+    SHF_FAST_SIZES(SHF_CASE)
+#undef SHF_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t col_reduce(const Geo& g, const float2* partial, const int* tile_begin, const int* tile_slots, float2* T,
+                       int K, int nslots, cudaStream_t st) {
+  const int ntiles = (g.Wh + kB - 1) / kB;
+  switch (g.H) {
+#define SHF_CASE(N)                                                                                          \
+  case N:                                                                                                    \
+    return launch_pdl(k_fcol_reduce_inv<N>, dim3(ntiles, K), dim3(N), col_smem<N>(), st, partial, tile_begin, \
+                      tile_slots, T, g.Wh, nslots, g.twH);
+    SHF_FAST_SIZES(SHF_CASE)
+#undef SHF_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace fast
+}  // namespace shf

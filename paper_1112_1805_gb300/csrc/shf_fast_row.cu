@@ -1,0 +1,475 @@
+// Row transforms of the fast path: the v-step (soft shrinkage and b_v update
+// between the inverse and forward row transforms of every coefficient row)
+// and the u/w-step (Sec. 3).
+#include "shf_fast.h"
+
+namespace shf {
+namespace fast {
+namespace {
+
+// Row groups of T = L/8 threads inside CTAs of NTH <= 256 threads.  For
+// T <= 32 a warp holds 32/T groups and never splits one (lanes beyond them
+// idle); for T > 32 a group is ceil(T/32) whole warps (lanes beyond T idle).
+// An idle lane mirrors the last lane of its warp's last group (same row, same
+// shared-memory values) and writes nothing to global memory.
+template <int L>
+struct RowGeo {
+  static constexpr int T = L / 8;
+  static constexpr int GPW = T <= 32 ? 32 / T : 1;         // groups per warp
+  static constexpr int WPG = T <= 32 ? 1 : (T + 31) / 32;  // warps per group
+  static constexpr int RPC = T <= 32 ? 8 * GPW : 8 / WPG;  // groups per CTA
+  static constexpr int NTH = T <= 32 ? 256 : RPC * WPG * 32;
+  __device__ static void locate(int& grp, int& tt, bool& act) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (T <= 32) {
+      const int g = lane / T;
+      act = g < GPW;
+      grp = warp * GPW + (act ? g : GPW - 1);
+      tt = act ? lane - g * T : T - 1;
+    } else {
+      grp = warp / WPG;
+      tt = (warp % WPG) * 32 + lane;
+      act = tt < T;
+      if (!act) tt = T - 1;
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Row kernels: a real row of length W = 2L is the complex row
+// z[n] = x[2n] + i x[2n+1], transformed by a group of T = L/8 threads.
+// ---------------------------------------------------------------------------
+
+// 16-byte asynchronous copies global -> shared (the copying thread waits for
+// its own copies with cp_async_wait_all; the group barrier then publishes
+// them to the group).  `evict_first`: the source is streamed through L2.
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src, bool evict_first, uint64_t policy) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst_smem));
+  if (evict_first)
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "l"(policy)
+                 : "memory");
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ uint64_t evict_first_policy() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// Shared memory of one row group of k_wrow_shrink: FFT exchange buffer(s),
+// and the stage that receives the next row's spectrum columns and b_v row.
+// Every region is a whole number of 16-byte units (even float2 counts) so that
+// the stage is 16-byte aligned for the asynchronous copies.
+__host__ __device__ constexpr int even2(int n) { return (n + 1) & ~1; }
+template <int L>
+struct RowGroupSmem {
+  static constexpr int T = L / 8;
+  static constexpr int NBUF = T <= 32 ? 1 : 2;  // warp-sized groups exchange through one buffer
+  static constexpr int BUF = even2(reg::row_buf(L));
+  static constexpr int SX = L + 8;              // spectrum columns [c0, c0 + SX), SX >= the row pitch
+  static constexpr int SB = L;                  // b_v row as float2
+  static constexpr int SIZE = NBUF * BUF + SX + SB;
+  static constexpr int TW = even2(L + 1);                     // exp(-2 pi i m / W), m <= L
+  static constexpr int PT = even2(reg::Passes<L>::TWSIZE);    // per-pass twiddles
+  static constexpr int RPC = RowGeo<L>::RPC;                  // row groups per CTA
+  static constexpr int TOTAL = TW + PT + RPC * SIZE;          // float2 per CTA
+};
+
+// v-step and b_v update of Sec. 3 on rows of (S u)_f: g = b_v + c,
+// b_v <- clip(g, -t, t), d = soft(g, t) - clip(g, -t, t) = g - 2 clip(g);
+// d (= v - b_v of the new iterate) is transformed back in place.
+// Rows r = (filter fl, row) with r = fl H + row over the wave's nf filters;
+// resident CTAs, each row group takes rows gid, gid + G, ... (G groups in
+// all).  While a group transforms its row, the next row's spectrum columns
+// (only the filter's column tiles [c0, c1]) and b_v row are copied into the
+// group's stage; the twiddle tables are built once per CTA.
+// Four CTAs of 256 threads per SM (64 registers) for powers of two; three for
+// L = 3 2^a or 5 2^a, whose radix-R pass holds more values.
+template <int L>
+__global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 : 768) / RowGeo<L>::NTH)
+    k_wrow_shrink(float2* __restrict__ Y, float* __restrict__ bv,
+                                                        const float* __restrict__ thr,
+                                                        const int2* __restrict__ ranges, int H, int Whp, int eta,
+                                                        int label, int f0, int nf, float scale,
+                                                        const float2* __restrict__ twW) {
+  using SM = RowGroupSmem<L>;
+  constexpr int T = SM::T;
+  constexpr int RPC = SM::RPC;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* tw = sm;                    // exp(-2 pi i m / W), m <= L
+  float2* pt = tw + SM::TW;           // per-pass twiddles of the length-L transform
+  int grp, tt;
+  bool act;
+  RowGeo<L>::locate(grp, tt, act);
+  float2* gb = pt + SM::PT + grp * SM::SIZE;
+  float2* fb0 = gb;
+  float2* fb1 = gb + (SM::NBUF - 1) * SM::BUF;
+  float2* sX = gb + SM::NBUF * SM::BUF;
+  float2* sB = sX + SM::SX;
+  const int bar = 1 + grp;
+  const int G = gridDim.x * RPC;
+  const int gid = blockIdx.x * RPC + grp;
+  const int rows = nf * H;
+  const int niter = (rows + G - 1) / G;  // the same for every group: dead rows still take part in barriers
+  const uint64_t pol = evict_first_policy();
+
+  // request row r's spectrum columns (its filter's column range only) and
+  // its b_v row into the stage
+  auto request_x = [&](int r) {
+    if (r >= rows || !act) return;
+    const int fl = r / H, row = r - fl * H;
+    const int2 rg = ranges[f0 + fl];
+    if (rg.x <= rg.y) {
+      const int c0 = rg.x & ~7;
+      const int c1e = min(Whp, (rg.y | 7) + 1);
+      const float2* X = Y + (static_cast<size_t>(fl) * H + row) * Whp + c0;
+      for (int q = tt; q < (c1e - c0) / 2; q += T) cp_async16(sX + 2 * q, X + 2 * q, false, pol);
+    }
+  };
+  auto request_b = [&](int r) {
+    if (r >= rows || !act) return;
+    const int fl = r / H, row = r - fl * H;
+    const float2* B =
+        reinterpret_cast<const float2*>(bv) + ((static_cast<size_t>(label) * eta + f0 + fl) * H + row) * L;
+    for (int q = tt; q < L / 2; q += T) cp_async16(sB + 2 * q, B + 2 * q, true, pol);
+  };
+
+  // b_v was last written by this kernel's previous launch for the label,
+  // which has completed: it may be requested before the wait
+  request_b(gid);
+  load_table(tw, twW, L + 1);
+  reg::build_pass_twiddles<L, 2>(pt, twW, threadIdx.x, blockDim.x);
+  pdl_wait();
+  pdl_trigger();
+  request_x(gid);
+  __syncthreads();
+  for (int it = 0; it < niter; ++it) {
+    const int r = gid + it * G;
+    const bool live = r < rows;
+    const int fl = live ? r / H : 0, row = live ? r - fl * H : 0, f = f0 + fl;
+    const int2 rg = ranges[f];
+    const bool any = live && rg.x <= rg.y;
+    const int c0 = any ? (rg.x & ~7) : L + 1;
+    const int c1 = any ? min(L, (rg.y | 7)) : -1;
+    const float th = thr[f];
+    cp_async_commit_wait_all();
+    reg::group_sync<T>(bar);
+    float2 v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {  // inverse packing Z[n] = (X_n + conj X_{L-n}) + i e^{+2 pi i n/W} (X_n - conj X_{L-n})
+      const int n = tt + k * T, m = L - n;
+      const float2 a = (n >= c0 && n <= c1) ? sX[n - c0] : make_float2(0.f, 0.f);
+      const float2 c = (m >= c0 && m <= c1) ? c_conj(sX[m - c0]) : make_float2(0.f, 0.f);
+      const float2 s2 = c_add(a, c), d = c_sub(a, c);
+      const float2 t = c_mul(c_conj(tw[n]), d);
+      v[k] = make_float2(s2.x - t.y, s2.y + t.x);
+    }
+    reg::group_sync<T>(bar);  // the spectrum stage is read: refill it with the group's next row
+    request_x(r + G);
+    if (SM::NBUF == 1)
+      reg::row_fft1<L, +1>(v, tt, fb0, pt, bar);
+    else
+      reg::row_fft<L, +1>(v, tt, fb0, fb1, pt, bar);
+    float2* X = Y + (static_cast<size_t>(fl) * H + row) * Whp;
+    if (live) {
+      float2* b2 = reinterpret_cast<float2*>(bv) + ((static_cast<size_t>(label) * eta + f) * H + row) * L;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float2 bo = sB[tt + k * T];
+        const float gx = fmaf(scale, v[k].x, bo.x), gy = fmaf(scale, v[k].y, bo.y);
+        const float cx = fminf(fmaxf(gx, -th), th), cy = fminf(fmaxf(gy, -th), th);
+        if (act) __stcs(b2 + tt + k * T, make_float2(cx, cy));
+        v[k] = make_float2(gx - 2.f * cx, gy - 2.f * cy);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = make_float2(0.f, 0.f);
+    }
+    reg::group_sync<T>(bar);  // the b_v stage is read: refill it with the group's next row
+    request_b(r + G);
+    if (SM::NBUF == 1)
+      reg::row_fft1<L, -1>(v, tt, fb0, pt, bar);
+    else
+      reg::row_fft<L, -1>(v, tt, fb0, fb1, pt, bar);
+    float2* ub = SM::NBUF == 1 ? fb0 : fb1;
+    reg::group_sync<T>(bar);  // the last pass may still read the buffer
+#pragma unroll
+    for (int k = 0; k < 8; ++k) ub[reg::ridx(tt + k * T)] = v[k];
+    reg::group_sync<T>(bar);
+    // forward unpacking X[k] = 1/2 [(Z_k + conj Z_{L-k}) - i e^{-2 pi i k/W} (Z_k - conj Z_{L-k})]
+    for (int i = c0 + tt; act && i <= c1; i += T) {
+      const float2 a = ub[reg::ridx(i == L ? 0 : i)];
+      const float2 c = c_conj(ub[reg::ridx(i == 0 ? 0 : L - i)]);
+      const float2 s2 = c_add(a, c), d = c_sub(a, c);
+      const float2 t = c_mul(tw[i], d);
+      X[i] = make_float2(0.5f * (s2.x + t.y), 0.5f * (s2.y - t.x));
+    }
+  }
+  cp_async_commit_wait_all();  // no copy outlives the kernel
+}
+
+// Euclidean projection of g[0..K) onto the unit simplex, as the paper
+// constructs it: project onto the hyperplane sum = 1 (g + (1 - sum g)/q), set
+// the negative components to zero and repeat on the remaining ones (at most K
+// passes; the result is exact).
+template <int KMAX>
+__device__ __forceinline__ void simplex_project(float (&g)[KMAX], int K) {
+  unsigned act = (1u << K) - 1u;
+  float tau = 0.f;
+  for (int pass = 0; pass < K; ++pass) {
+    float sum = 0.f;
+    int q = 0;
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k)
+      if ((act >> k) & 1u) {
+        sum += g[k];
+        ++q;
+      }
+    tau = (sum - 1.f) / static_cast<float>(q);
+    unsigned nact = act;
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k)
+      if (((act >> k) & 1u) && g[k] - tau < 0.f) nact &= ~(1u << k);
+    if (nact == act) break;
+    act = nact;
+  }
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) g[k] = ((act >> k) & 1u) ? g[k] - tau : 0.f;
+}
+
+// u-step (u = 1/2 [S^T(v - b_v) + (w - b_w) - gamma s], A^T A = 2I), w-step
+// (pixelwise simplex projection of g_w = b_w + u), b_w = g_w - w, and the row
+// spectra of u for the next analysis.  One row per group of L/8 threads, all
+// K labels; the carried values of a thread live in its private slots of U.
+template <int L, int KMAX>
+__global__ void __launch_bounds__(RowGeo<L>::NTH) k_wrow_ustep(const float2* __restrict__ Tsp, const float* __restrict__ s,
+                                                    float* __restrict__ w, float* __restrict__ bw,
+                                                    float* __restrict__ u, float2* __restrict__ Ur, int K, int H,
+                                                    float scale, float gamma, const float2* __restrict__ twW) {
+  constexpr int T = L / 8;
+  constexpr int RPC = RowGeo<L>::RPC;
+  constexpr int NTH = RowGeo<L>::NTH;
+  constexpr int BUF = reg::row_buf(L);
+  constexpr int Wh = L + 1;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* pt = tw + (L + 1);
+  int grp, tt;
+  bool act;
+  RowGeo<L>::locate(grp, tt, act);
+  float2* b0 = pt + reg::Passes<L>::TWSIZE + grp * 2 * BUF;
+  float2* b1 = b0 + BUF;
+  float2* U = pt + reg::Passes<L>::TWSIZE + RPC * 2 * BUF;  // [k][e][thread]
+  const int bar = 1 + grp;
+  const int row = blockIdx.x * RPC + grp;
+  const bool live = row < H;
+  const int rowc = live ? row : 0;
+  const size_t HL = static_cast<size_t>(H) * L, HWh = static_cast<size_t>(H) * Wh;
+  auto slot = [&](int k, int e) { return (k * 8 + e) * NTH + threadIdx.x; };
+  load_table(tw, twW, L + 1);
+  reg::build_pass_twiddles<L, 2>(pt, twW, threadIdx.x, blockDim.x);
+  pdl_wait();
+  pdl_trigger();
+  __syncthreads();
+  // S^T(v - b_v) on this row, label by label
+  for (int k = 0; k < K; ++k) {
+    reg::group_sync<T>(bar);  // the previous label's transform may still read b1
+    const float2* X = Tsp + HWh * k + static_cast<size_t>(rowc) * Wh;
+    for (int i = tt; i <= L; i += T) b1[reg::ridx(i)] = live ? X[i] : make_float2(0.f, 0.f);
+    reg::group_sync<T>(bar);
+    float2 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int n = tt + e * T;
+      const float2 a = b1[reg::ridx(n)];
+      const float2 c = c_conj(b1[reg::ridx(L - n)]);
+      const float2 sm2 = c_add(a, c), d = c_sub(a, c);
+      const float2 t = c_mul(c_conj(tw[n]), d);
+      v[e] = make_float2(sm2.x - t.y, sm2.y + t.x);
+    }
+    reg::row_fft<L, +1>(v, tt, b0, b1, pt, bar);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) U[slot(k, e)] = c_scale(v[e], scale);
+  }
+  // pointwise u-step, projection and b_w update (two pixels per slot)
+  if (live) {
+    const float2* s2 = reinterpret_cast<const float2*>(s) + static_cast<size_t>(row) * L;
+    float2* w2 = reinterpret_cast<float2*>(w) + static_cast<size_t>(row) * L;
+    float2* bw2 = reinterpret_cast<float2*>(bw) + static_cast<size_t>(row) * L;
+    float2* u2 = reinterpret_cast<float2*>(u) + static_cast<size_t>(row) * L;
+    const float hg = 0.5f * gamma;
+#pragma unroll 1
+    for (int e = 0; e < 8; ++e) {
+      const int n = tt + e * T;
+      float gx[KMAX], gy[KMAX];
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k) {
+        gx[k] = 0.f;
+        gy[k] = 0.f;
+        if (k < K) {
+          const float2 st = U[slot(k, e)];
+          const float2 wv = w2[HL * k + n], bv = bw2[HL * k + n], sv = s2[HL * k + n];
+          const float ux = 0.5f * (st.x + (wv.x - bv.x)) - hg * sv.x;
+          const float uy = 0.5f * (st.y + (wv.y - bv.y)) - hg * sv.y;
+          if (act) u2[HL * k + n] = make_float2(ux, uy);
+          U[slot(k, e)] = make_float2(ux, uy);
+          gx[k] = bv.x + ux;
+          gy[k] = bv.y + uy;
+        }
+      }
+      float px[KMAX], py[KMAX];
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k) {
+        px[k] = gx[k];
+        py[k] = gy[k];
+      }
+      simplex_project<KMAX>(px, K);
+      simplex_project<KMAX>(py, K);
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+        if (k < K && act) {
+          w2[HL * k + n] = make_float2(px[k], py[k]);
+          bw2[HL * k + n] = make_float2(gx[k] - px[k], gy[k] - py[k]);
+        }
+    }
+  } else {
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int e = 0; e < 8; ++e) U[slot(k, e)] = make_float2(0.f, 0.f);
+  }
+  // row spectra of u
+  for (int k = 0; k < K; ++k) {
+    float2 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = U[slot(k, e)];
+    reg::row_fft<L, -1>(v, tt, b0, b1, pt, bar);
+    reg::group_sync<T>(bar);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) b1[reg::ridx(tt + e * T)] = v[e];
+    reg::group_sync<T>(bar);
+    if (live && act) {
+      float2* X = Ur + HWh * k + static_cast<size_t>(row) * Wh;
+      for (int i = tt; i <= L; i += T) {
+        const float2 a = b1[reg::ridx(i == L ? 0 : i)];
+        const float2 c = c_conj(b1[reg::ridx(i == 0 ? 0 : L - i)]);
+        const float2 sm2 = c_add(a, c), d = c_sub(a, c);
+        const float2 t = c_mul(tw[i], d);
+        X[i] = make_float2(0.5f * (sm2.x + t.y), 0.5f * (sm2.y - t.x));
+      }
+    }
+  }
+}
+
+}  // namespace
+
+namespace {
+
+template <int L>
+size_t shrink_smem() {
+  return sizeof(float2) * RowGroupSmem<L>::TOTAL;
+}
+
+template <int L>
+size_t ustep_smem(int K) {
+  using RG = RowGeo<L>;
+  return sizeof(float2) *
+         ((L + 1) + reg::Passes<L>::TWSIZE + RG::RPC * 2 * reg::row_buf(L) + static_cast<size_t>(K) * 8 * RG::NTH);
+}
+
+template <int L>
+cudaError_t prepare_row_t() {
+  cudaError_t e = allow_smem(k_wrow_shrink<L>, shrink_smem<L>());
+  if (e == cudaSuccess) e = allow_smem(k_wrow_ustep<L, 4>, ustep_smem<L>(4));
+  if (e == cudaSuccess) e = allow_smem(k_wrow_ustep<L, 8>, ustep_smem<L>(8));
+  return e;
+}
+
+template <int L>
+cudaError_t ustep_t(const Geo& g, const float2* T, const float* s, float* w, float* bw, float* u, float2* Ur, int K,
+                    float gamma, float scale, cudaStream_t st) {
+  using RG = RowGeo<L>;
+  const dim3 grid((g.H + RG::RPC - 1) / RG::RPC);
+  if (K <= 4)
+    return launch_pdl(k_wrow_ustep<L, 4>, grid, dim3(RG::NTH), ustep_smem<L>(K), st, T, s, w, bw, u, Ur, K, g.H,
+                      scale, gamma, g.twW);
+  return launch_pdl(k_wrow_ustep<L, 8>, grid, dim3(RG::NTH), ustep_smem<L>(K), st, T, s, w, bw, u, Ur, K, g.H,
+                    scale, gamma, g.twW);
+}
+
+}  // namespace
+
+cudaError_t prepare_row_kernels() {
+#define SHF_PREP(N) \
+  if (e == cudaSuccess) e = prepare_row_t<N>();
+  cudaError_t e = cudaSuccess;
+  SHF_FAST_SIZES(SHF_PREP)
+#undef SHF_PREP
+  return e;
+}
+
+int row_ctas_per_sm(int L) {
+  int fit = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (L) {
+#define SHF_OCC(N)                                                                                                \
+  case N:                                                                                                         \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_shrink<N>, RowGeo<N>::NTH, shrink_smem<N>()); \
+    break;
+    SHF_FAST_SIZES(SHF_OCC)
+#undef SHF_OCC
+    default: break;
+  }
+  return e == cudaSuccess ? fit : 0;
+}
+
+int row_groups_per_cta(int L) {
+  switch (L) {
+#define SHF_CASE(N) \
+  case N:           \
+    return RowGeo<N>::RPC;
+    SHF_FAST_SIZES(SHF_CASE)
+#undef SHF_CASE
+    default: return 0;
+  }
+}
+
+cudaError_t row_shrink(const Geo& g, int ctas, float2* Y, float* bv, const float* thr, int Whp, int label, int f0,
+                       int nf, float scale, cudaStream_t st) {
+  switch (g.L) {
+#define SHF_CASE(N)                                                                                                \
+  case N:                                                                                                          \
+    return launch_pdl(k_wrow_shrink<N>, dim3(ctas), dim3(RowGeo<N>::NTH), shrink_smem<N>(), st, Y, bv, thr,      \
+                      g.ranges, g.H, Whp, g.eta, label, f0, nf, scale, g.twW);
+    SHF_FAST_SIZES(SHF_CASE)
+#undef SHF_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+size_t ustep_smem_bytes(int L, int K) {
+  switch (L) {
+#define SHF_CASE(N) \
+  case N:           \
+    return ustep_smem<N>(K);
+    SHF_FAST_SIZES(SHF_CASE)
+#undef SHF_CASE
+    default: return 0;
+  }
+}
+
+cudaError_t row_ustep(const Geo& g, const float2* T, const float* s, float* w, float* bw, float* u, float2* Ur, int K,
+                      float gamma, float scale, cudaStream_t st) {
+  switch (g.L) {
+#define SHF_CASE(N) \
+  case N:           \
+    return ustep_t<N>(g, T, s, w, bw, u, Ur, K, gamma, scale, st);
+    SHF_FAST_SIZES(SHF_CASE)
+#undef SHF_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace fast
+}  // namespace shf

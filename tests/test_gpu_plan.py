@@ -89,8 +89,8 @@ def test_plan_is_bitwise_reproducible(torch_mod):
 
 
 def test_general_plans_match_oracle(torch_mod, oracle_mod):
-    # 96 x 160 is not a power of two: the general kernels
-    img, cb, Lam = _problem(96, 160, 3, 2, 33)
+    # 72 x 120 (72 = 9 * 8) is not a register-FFT size: the general kernels
+    img, cb, Lam = _problem(72, 120, 3, 2, 33)
     T = 12
     o = _oracle(oracle_mod, img, cb, 2, Lam, T)
     base = _run(torch_mod, img, cb, 2, Lam, T)
@@ -98,7 +98,7 @@ def test_general_plans_match_oracle(torch_mod, oracle_mod):
     _check(o, base)
     rb = base["plan"]["tile_rows"]
     for p in (dict(tile_cols=4, tile_rows=rb, groups=1), dict(tile_cols=16, tile_rows=max(1, rb // 2), groups=13),
-              dict(tile_cols=32, tile_rows=min(96, 2 * rb), groups=5)):
+              dict(tile_cols=32, tile_rows=min(72, 2 * rb), groups=5)):
         g = _run(torch_mod, img, cb, 2, Lam, T, p)
         assert g["plan"]["tile_cols"] == p["tile_cols"] and g["plan"]["tile_rows"] == p["tile_rows"]
         _check(o, g)
@@ -110,8 +110,8 @@ def test_bad_plans_are_rejected_and_keep_the_old_plan(torch_mod):
 
     for H, W, bad in ((64, 64, dict(wave_mib=64, col_ctas_per_sm=-1)), (64, 64, dict(wave_mib=0, col_ctas_per_sm=0)),
                       (64, 64, dict(wave_mib=64, col_ctas_per_sm=33)),
-                      (48, 80, dict(tile_cols=0, tile_rows=1, groups=1)),
-                      (48, 80, dict(tile_cols=8, tile_rows=10000, groups=1))):
+                      (72, 120, dict(tile_cols=0, tile_rows=1, groups=1)),
+                      (72, 120, dict(tile_cols=8, tile_rows=10000, groups=1))):
         img, cb, Lam = _problem(H, W, 3, 2, 34)
         fb = FilterBank(H, W, 2)
         seg = ShearletSegmenter(fb, torch_mod.tensor(img, device="cuda"), cb, Lam.tolist(), 1.0)
@@ -125,7 +125,7 @@ def test_bad_plans_are_rejected_and_keep_the_old_plan(torch_mod):
         fb.close()
 
 
-@pytest.mark.parametrize("H,W,J", [(256, 256, 3), (96, 160, 2)])
+@pytest.mark.parametrize("H,W,J", [(256, 256, 3), (96, 160, 2), (72, 120, 2)])
 def test_tune_restores_the_iterate_and_keeps_parity(torch_mod, oracle_mod, H, W, J):
     from paper_1112_1805_gb300 import binding as B
     from paper_1112_1805_gb300.api import FilterBank, ShearletSegmenter
@@ -159,12 +159,13 @@ def test_batch_tune(torch_mod, oracle_mod):
     from paper_1112_1805_gb300 import binding as B
     from paper_1112_1805_gb300.api import ShearletBatch
 
-    shapes = [(64, 64), (96, 160), (64, 64)]
+    shapes = [(64, 64), (72, 120), (64, 64), (96, 160)]
     probs = [_problem(H, W, 3, 2, 40 + i) for i, (H, W) in enumerate(shapes)]
     batch = ShearletBatch([torch_mod.tensor(p[0], device="cuda") for p in probs], [p[1] for p in probs],
                           [p[2].tolist() for p in probs])
     batch.tune(2)
-    plans = [batch.image(i).plan() for i in range(3)]
+    plans = [batch.image(i).plan() for i in range(4)]
+    assert [p["fast"] for p in plans] == [1, 0, 1, 1]
     assert plans[0] == plans[2]
     batch.step(10)
     batch.synchronize()

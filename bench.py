@@ -5,7 +5,12 @@ One step = one whole solve on the 512 x 512 workload (grayscale, K = 4 labels,
 J = 4 scales / 61 filters, 500 ADMM iterations, curved Bezier regions with
 oriented gratings and noise sigma = 0.05): data term and zero state
 (seg_admm_reset), 500 iterations (graph replays), label readout.  The metric
-is Mpixel*label*ADMM-iteration per second summed over all ranks.
+is Mpixel*label*ADMM-iteration per second summed over all ranks.  The work
+plan is autotuned on the image before the timed region (--no-tune keeps the
+default).  At N = 1 the line also carries `batched`: the same metric for the
+64-image uneven batch (one graph per iteration with a branch per image), one
+timed step of 300 iterations after three short warm-up steps (--no-batch
+skips it).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -50,6 +55,8 @@ def parse_args():
     ap.add_argument("--cpu-iters", type=int, default=2, help="oracle iterations in the CPU-baseline sample")
     ap.add_argument("--workload", choices=["bezier512", "batch"], default="bezier512",
                     help="bezier512 (default line) or the uneven batch of 64 images")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched measurement that the default line carries under 'batched'")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default work plan instead of autotuning it before the timed region")
     ap.add_argument("--iters", type=int, default=0,
@@ -345,25 +352,26 @@ def run_ours(args):
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
-    if rank == 0:
-        print(json.dumps(line))
     seg.close()
     fb.close()
+    if rank == 0 and world == 1 and not args.no_batch:
+        # the batched form on the same GPU (the plain state is released first)
+        line["batched"] = measure_batch(300, 1, 3, 30, not args.no_tune)
+    if rank == 0:
+        print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
     return 0
 
 
-def run_batch(args):
+def measure_batch(iters: int, steps: int, warmup_steps: int, warmup_iters: int, tune: bool):
     """The uneven batch: 64 seeded images (384 x 640 first, sides 128..1024), K
-    in 2..6, J = floor(log2(min side)/2), 300 iterations, all images in one
-    CUDA graph per iteration.  Reports the summed Mpixel*label*iter/s."""
+    in 2..6, J = floor(log2(min side)/2), all images in one CUDA graph per
+    iteration.  Returns the summed Mpixel*label*iter/s and its timing."""
     import torch
 
     from paper_1112_1805_gb300.api import ShearletBatch
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    iters = args.iters or 300
     shapes = synth.batch_shapes()
     rng = np.random.default_rng(synth.seed_for(3))
     imgs, cbs, lams, units = [], [], [], 0
@@ -375,26 +383,38 @@ def run_batch(args):
         lams.append(synth.scale_weights(0.1, J))
         units += H * W * K * iters
     batch = ShearletBatch(imgs, cbs, lams, 1.0)
-    if not args.no_tune:
+    if tune:
         batch.tune(3)
-    for _ in range(args.warmup):
-        batch.step(iters)
+    for _ in range(warmup_steps):
+        batch.step(warmup_iters)
     batch.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(batch.stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         batch.step(iters)
     ev1.record(batch.stream)
     ev1.synchronize()
     ms = ev0.elapsed_time(ev1)
-    line = {"metric": METRIC, "value": units * args.steps / (ms / 1000.0) / 1e6, "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"batch: {len(shapes)} images, sides 128..1024 (first 384x640), K 2..6, "
-                                   f"J = floor(log2(min side)/2), {iters} iterations, one graph per iteration",
-                       "images": len(shapes), "iters_per_step": iters, "tuned": not args.no_tune}}
-    print(json.dumps(line))
     batch.close()
+    return {"value": units * steps / (ms / 1000.0) / 1e6, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "warmup": warmup_steps, "tuned": tune,
+            "workload": f"batch: {len(shapes)} images, sides 128..1024 (first 384x640), K 2..6, "
+                        f"J = floor(log2(min side)/2), {iters} iterations per step, one graph per iteration "
+                        f"with a branch per image"}
+
+
+def run_batch(args):
+    """The batch as the bench line itself (--workload batch)."""
+    import torch
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    iters = args.iters or 300
+    b = measure_batch(iters, args.steps, args.warmup, iters, not args.no_tune)
+    line = {"metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": b["workload"], "images": 64, "iters_per_step": iters, "tuned": b["tuned"]}}
+    print(json.dumps(line))
     return 0
 
 

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kThreads)
   const size_t plane = blockIdx.y;
   const float t = thr[plane % eta];
   const size_t base = plane * static_cast<size_t>(P);
-  double acc = 0.0;
+  float acc = 0.f;  // per thread in FP32 (fixed order), across the block in FP64
   for (long r = blockIdx.x * static_cast<long>(kThreads) + threadIdx.x; r < P;
        r += static_cast<long>(gridDim.x) * kThreads) {
     const float gv = g[base + r], db = dbar[base + r], bb = bvbar[base + r];
@@ -71,21 +71,26 @@ __global__ void __launch_bounds__(kThreads)
       bvbar[base + r] = bb - db;
     } else {
       bvbar[base + r] = db;
-      acc += (gv > 0.f ? 1.0 : -1.0) * (static_cast<double>(bb) - 2.0 * static_cast<double>(db));
+      acc = fmaf(gv > 0.f ? 1.f : -1.f, fmaf(-2.f, db, bb), acc);
     }
   }
-  const double s = block_sum(acc);
+  const double s = block_sum(static_cast<double>(acc));
   if (threadIdx.x == 0) tpart[plane * gridDim.x + blockIdx.x] = s;
 }
 
-// tbar[f] += sum over labels and blocks, in order.
-__global__ void k_adj_tsum(const double* __restrict__ tpart, int K, int eta, int nblk, double* __restrict__ tbar) {
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= eta) return;
+// tbar[f] += sum over labels k and parts j < n of tpart[(k eta + f) n + j]:
+// one block per filter; thread t sums the parts j = t, t + kThreads, ... of
+// every label in order, then a fixed tree (deterministic).
+__global__ void __launch_bounds__(kThreads) k_adj_tsum(const double* __restrict__ tpart, int K, int eta, int n,
+                                                       double* __restrict__ tbar) {
+  const int f = blockIdx.x;
   double acc = 0.0;
-  for (int k = 0; k < K; ++k)
-    for (int b = 0; b < nblk; ++b) acc += tpart[(static_cast<size_t>(k) * eta + f) * nblk + b];
-  tbar[f] += acc;
+  for (int k = 0; k < K; ++k) {
+    const double* p = tpart + (static_cast<size_t>(k) * eta + f) * n;
+    for (int j = threadIdx.x; j < n; j += kThreads) acc += p[j];
+  }
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) tbar[f] += s;
 }
 
 __global__ void k_adj_u(const float* __restrict__ gwbar, const float* __restrict__ st, float* __restrict__ Qbar,
@@ -157,7 +162,12 @@ cudaError_t launch_adj_proj(const float* wn, const float* wbar, const float* bwb
 cudaError_t launch_adj_shrink(const float* g, const float* dbar, float* bvbar, const float* thr, int K, int eta,
                               long P, double* tpart, double* tbar, cudaStream_t st) {
   k_adj_shrink<<<dim3(kPartBlocks, K * eta), kThreads, 0, st>>>(g, dbar, bvbar, thr, eta, P, tpart);
-  k_adj_tsum<<<(eta + 127) / 128, 128, 0, st>>>(tpart, K, eta, kPartBlocks, tbar);
+  k_adj_tsum<<<eta, kThreads, 0, st>>>(tpart, K, eta, kPartBlocks, tbar);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_tsum_rows(const double* tpart, int K, int eta, int H, double* tbar, cudaStream_t st) {
+  k_adj_tsum<<<eta, kThreads, 0, st>>>(tpart, K, eta, H, tbar);
   return cudaGetLastError();
 }
 

@@ -114,6 +114,12 @@ struct seg_state {
   int un_groups = 0;
   std::vector<float*> ck_bv, ck_w, ck_bw;
   std::vector<float2*> ck_T;
+  // the forward and reverse sweeps captured as graphs for (T, ckpt) = un_key;
+  // the reverse sweep's temporaries live in un_mem (un_mem_bytes)
+  cudaGraphExec_t un_fwd_exec = nullptr, un_bwd_exec = nullptr;
+  int un_fwd_key[2] = {0, 0}, un_bwd_key[2] = {0, 0};
+  char* un_mem = nullptr;
+  size_t un_mem_bytes = 0;
   long long iter = 0;
   size_t P() const { return static_cast<size_t>(g.H) * g.W; }
   size_t Ph() const { return static_cast<size_t>(g.H) * g.Wh; }
@@ -276,6 +282,9 @@ void free_state(seg_state* s) {
   cudaFree(s->d_tile_slots);
   cudaFree(s->un_Y);
   cudaFree(s->un_partial);
+  if (s->un_fwd_exec) cudaGraphExecDestroy(s->un_fwd_exec);
+  if (s->un_bwd_exec) cudaGraphExecDestroy(s->un_bwd_exec);
+  cudaFree(s->un_mem);
   for (float* p : s->ck_bv) cudaFree(p);
   for (float* p : s->ck_w) cudaFree(p);
   for (float* p : s->ck_bw) cudaFree(p);
@@ -328,8 +337,9 @@ void mark_launch(void* ctx, int kind) {
 }
 
 // One ADMM iteration; `timed`: with an event recorded before every launch and
-// after the last one.
-cudaError_t enqueue_iteration(seg_state* st, bool timed) {
+// after the last one; `code` (fast path, optional): the per-coefficient codes
+// of the v-step for the reverse mode.
+cudaError_t enqueue_iteration(seg_state* st, bool timed, signed char* code = nullptr) {
   const Geo& g = st->g;
   const float scale = 1.f / (static_cast<float>(g.H) * g.W);
   cudaStream_t s = st->stream;
@@ -348,7 +358,7 @@ cudaError_t enqueue_iteration(seg_state* st, bool timed) {
   if (st->fast) {
     if (e == cudaSuccess)
       e = shf::run_fast_iteration_body(g, st->plan, st->Ur, st->uhat, st->Y, st->bv, st->thr, st->partial, st->T,
-                                       st->K, scale, s, hook);
+                                       st->K, scale, s, hook, code);
   } else {
     hook.mark(shf::kKindFan);
     if (e == cudaSuccess) e = shf::run_col_fan(g, st->Ur, st->Y, st->K, st->groups, s);
@@ -412,8 +422,31 @@ void try_capture(seg_state* st) {
 void drop_graphs(seg_state* st) {
   if (st->exec) cudaGraphExecDestroy(st->exec);
   if (st->exec_timed) cudaGraphExecDestroy(st->exec_timed);
-  st->exec = st->exec_timed = nullptr;
+  if (st->un_fwd_exec) cudaGraphExecDestroy(st->un_fwd_exec);
+  if (st->un_bwd_exec) cudaGraphExecDestroy(st->un_bwd_exec);
+  st->exec = st->exec_timed = st->un_fwd_exec = st->un_bwd_exec = nullptr;
+  st->un_fwd_key[0] = st->un_fwd_key[1] = st->un_bwd_key[0] = st->un_bwd_key[1] = 0;
   st->graph_tried = false;
+}
+
+// Captures the work `enqueue` puts on the state's stream into an executable
+// graph; nullptr when the stream cannot be captured or the work failed.
+extern "C++" template <typename F>
+cudaGraphExec_t capture_work(seg_state* st, F enqueue) {
+  if (st->stream == nullptr) return nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (cudaStreamBeginCapture(st->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  cudaError_t e = enqueue();
+  cudaError_t e2 = cudaStreamEndCapture(st->stream, &graph);
+  if (e == cudaSuccess && e2 == cudaSuccess && graph && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+    exec = nullptr;
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();
+  return exec;
 }
 
 // Fast path: builds the work list for (wave_mib, col_ctas_per_sm) and
@@ -1086,12 +1119,168 @@ int seg_admm_load(seg_state* st, const char* path) {
   return SHF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Layout of the reverse sweep's temporaries in st->un_mem (byte offsets, each
+// region on a 256-byte boundary: the fast kernels copy rows of bvbar and of
+// the codes with 16-byte asynchronous copies).
+struct UnLayout {
+  size_t tpart, tbar, cbpart, cbout;      // doubles
+  size_t Uw, Tt;                          // float2 [K][H][Wh]
+  size_t bvbar, dbar, Qbar, wbar, bwbar, sbar, gwbar, stv, fbar, grec, wrec;  // floats
+  size_t code;                            // bytes
+  size_t total;
+};
+
+UnLayout un_layout(const seg_state* st, int ck) {
+  const Geo& g = st->g;
+  const int K = st->K, C = st->C, eta = g.eta;
+  const size_t P = st->P(), Ph = st->Ph(), KP = P * K, NC = KP * eta;
+  const bool fast = st->fast;
+  const size_t nblk = static_cast<size_t>(shf::adj_part_blocks());
+  UnLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = (off + bytes + 255) & ~static_cast<size_t>(255);
+    return at;
+  };
+  L.tpart = take(sizeof(double) * K * eta * (fast ? static_cast<size_t>(g.H) : nblk));
+  L.tbar = take(sizeof(double) * eta);
+  L.cbpart = take(sizeof(double) * K * C * nblk);
+  L.cbout = take(sizeof(double) * K * C);
+  L.Uw = take(sizeof(float2) * Ph * K);
+  L.Tt = take(sizeof(float2) * Ph * K);
+  L.bvbar = take(sizeof(float) * NC);
+  L.dbar = fast ? 0 : take(sizeof(float) * NC);
+  L.Qbar = take(sizeof(float) * KP);
+  L.wbar = take(sizeof(float) * KP);
+  L.bwbar = take(sizeof(float) * KP);
+  L.sbar = take(sizeof(float) * KP);
+  L.gwbar = take(sizeof(float) * KP);
+  L.stv = take(sizeof(float) * KP);
+  L.fbar = take(sizeof(float) * P * C);
+  L.grec = fast ? 0 : take(sizeof(float) * NC * ck);
+  L.wrec = take(sizeof(float) * KP * ck);
+  L.code = fast ? take(NC * ck) : 0;
+  L.total = off;
+  return L;
+}
+
+// T iterations from the zero state, keeping (b_v, w, b_w, T) before every
+// ckpt-th iteration.
+cudaError_t enqueue_unrolled_fwd(seg_state* st, int T, int ck) {
+  const size_t P = st->P(), Ph = st->Ph(), KP = P * st->K, NC = KP * st->g.eta;
+  cudaStream_t s = st->stream;
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+  };
+  ok(cudaMemsetAsync(st->bv, 0, sizeof(float) * NC, s));
+  ok(cudaMemsetAsync(st->w, 0, sizeof(float) * KP, s));
+  ok(cudaMemsetAsync(st->bw, 0, sizeof(float) * KP, s));
+  ok(cudaMemsetAsync(st->u, 0, sizeof(float) * KP, s));
+  ok(cudaMemsetAsync(st->T, 0, sizeof(float2) * Ph * st->K, s));
+  for (int i = 0; i < T && e == cudaSuccess; ++i) {
+    if (i % ck == 0) {
+      const int c = i / ck;
+      ok(cudaMemcpyAsync(st->ck_bv[c], st->bv, sizeof(float) * NC, cudaMemcpyDeviceToDevice, s));
+      ok(cudaMemcpyAsync(st->ck_w[c], st->w, sizeof(float) * KP, cudaMemcpyDeviceToDevice, s));
+      ok(cudaMemcpyAsync(st->ck_bw[c], st->bw, sizeof(float) * KP, cudaMemcpyDeviceToDevice, s));
+      ok(cudaMemcpyAsync(st->ck_T[c], st->T, sizeof(float2) * Ph * st->K, cudaMemcpyDeviceToDevice, s));
+    }
+    ok(st->fast ? enqueue_iteration(st, false) : enqueue_generic_iteration(st, nullptr));
+  }
+  return e;
+}
+
+// The reverse sweep, from wbar (already holding dL/dw) to sbar, fbar, tbar
+// and cbout in st->un_mem.
+cudaError_t enqueue_unrolled_bwd(seg_state* st, const UnLayout& U) {
+  const Geo& g = st->g;
+  const int K = st->K, C = st->C, eta = g.eta, T = st->un_T, ck = st->un_ck;
+  const size_t P = st->P(), Ph = st->Ph(), KP = P * K, NC = KP * eta;
+  const float scale = 1.f / (static_cast<float>(g.H) * g.W);
+  cudaStream_t s = st->stream;
+  const bool fast = st->fast;
+  char* m = st->un_mem;
+  double* tpart = reinterpret_cast<double*>(m + U.tpart);
+  double* tbar = reinterpret_cast<double*>(m + U.tbar);
+  double* cbpart = reinterpret_cast<double*>(m + U.cbpart);
+  double* cbout = reinterpret_cast<double*>(m + U.cbout);
+  float2* Uw = reinterpret_cast<float2*>(m + U.Uw);
+  float2* Tt = reinterpret_cast<float2*>(m + U.Tt);
+  auto F = [&](size_t o) { return reinterpret_cast<float*>(m + o); };
+  float *bvbar = F(U.bvbar), *dbar = fast ? nullptr : F(U.dbar), *Qbar = F(U.Qbar), *wbar = F(U.wbar),
+        *bwbar = F(U.bwbar), *sbar = F(U.sbar), *gwbar = F(U.gwbar), *stv = F(U.stv), *fbar = F(U.fbar),
+        *grec = fast ? nullptr : F(U.grec), *wrec = F(U.wrec);
+  signed char* crec = fast ? reinterpret_cast<signed char*>(m + U.code) : nullptr;
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+    return e == cudaSuccess;
+  };
+  ok(cudaMemsetAsync(bvbar, 0, sizeof(float) * NC, s));
+  ok(cudaMemsetAsync(Qbar, 0, sizeof(float) * KP, s));
+  ok(cudaMemsetAsync(bwbar, 0, sizeof(float) * KP, s));
+  ok(cudaMemsetAsync(sbar, 0, sizeof(float) * KP, s));
+  ok(cudaMemsetAsync(tbar, 0, sizeof(double) * eta, s));
+  const int nseg = (T + ck - 1) / ck;
+  for (int seg = nseg - 1; seg >= 0 && e == cudaSuccess; --seg) {
+    const int n = std::min(ck, T - seg * ck);
+    ok(cudaMemcpyAsync(st->bv, st->ck_bv[seg], sizeof(float) * NC, cudaMemcpyDeviceToDevice, s));
+    ok(cudaMemcpyAsync(st->w, st->ck_w[seg], sizeof(float) * KP, cudaMemcpyDeviceToDevice, s));
+    ok(cudaMemcpyAsync(st->bw, st->ck_bw[seg], sizeof(float) * KP, cudaMemcpyDeviceToDevice, s));
+    ok(cudaMemcpyAsync(st->T, st->ck_T[seg], sizeof(float2) * Ph * K, cudaMemcpyDeviceToDevice, s));
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {  // recompute the segment, recording g (or its codes) and w'
+      if (fast)
+        ok(enqueue_iteration(st, false, crec + static_cast<size_t>(i) * NC));
+      else
+        ok(enqueue_generic_iteration(st, grec + static_cast<size_t>(i) * NC));
+      ok(cudaMemcpyAsync(wrec + static_cast<size_t>(i) * KP, st->w, sizeof(float) * KP, cudaMemcpyDeviceToDevice, s));
+    }
+    for (int i = n - 1; i >= 0 && e == cudaSuccess; --i) {
+      ok(shf::launch_adj_proj(wrec + static_cast<size_t>(i) * KP, wbar, bwbar, gwbar, K, static_cast<int>(P), s));
+      if (fast) {
+        // S Qbar, the v-step adjoint and S^T bvbar, fused per wave of filters
+        ok(shf::run_row_r2c(g, Qbar, Uw, K, 1.f, s));
+        ok(shf::run_fast_adjoint_body(g, st->plan, Uw, st->uhat, st->Y, bvbar, st->thr, st->partial, Tt, K, scale,
+                                      crec + static_cast<size_t>(i) * NC, tpart, s));
+        ok(shf::launch_adj_tsum_rows(tpart, K, eta, g.H, tbar, s));
+      } else {
+        // dbar = S Qbar
+        ok(shf::run_row_r2c(g, Qbar, Uw, K, 1.f, s));
+        ok(shf::run_col_fan(g, Uw, st->un_Y, K, st->groups, s));
+        ok(shf::run_row_c2r(g, st->un_Y, dbar, K * eta, scale, s));
+        ok(shf::launch_adj_shrink(grec + static_cast<size_t>(i) * NC, dbar, bvbar, st->thr, K, eta,
+                                  static_cast<long>(P), tpart, tbar, s));
+        // stv = S^T bvbar
+        ok(shf::run_row_r2c(g, bvbar, st->un_Y, K * eta, 1.f, s));
+        ok(shf::run_col_gather(g, st->un_Y, st->un_partial, K, st->un_groups, s));
+        ok(shf::run_col_reduce_inv(g, st->un_partial, Tt, K, st->un_groups, s));
+      }
+      ok(shf::run_row_c2r(g, Tt, stv, K, scale, s));
+      ok(shf::launch_adj_u(gwbar, stv, Qbar, wbar, bwbar, sbar, st->gamma, static_cast<long>(KP), s));
+    }
+  }
+  ok(shf::adj_codebook(sbar, st->f, st->codebook.data(), K, C, static_cast<long>(P), cbpart, cbout, fbar, s));
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
 int seg_admm_unrolled_fwd(seg_state* st, int T, int ckpt_every) {
   if (!st || T < 1 || ckpt_every < 1) return fail(SHF_ERR_ARG, "seg_admm_unrolled_fwd: bad argument");
   const Geo& g = st->g;
   const size_t P = st->P(), Ph = st->Ph(), KP = P * st->K, NC = KP * g.eta;
   int rc;
-  if (!st->un_Y) {
+  // the general path keeps the spectra of every filter; the fast path
+  // iterates with its own wave scratch
+  if (!st->fast && !st->un_Y) {
     if ((rc = dev_alloc(&st->un_Y, Ph * st->K * g.eta, "unrolled scratch")) ||
         (rc = dev_alloc(&st->un_partial, Ph * st->K * st->groups, "unrolled partials")))
       return rc;
@@ -1114,22 +1303,17 @@ int seg_admm_unrolled_fwd(seg_state* st, int T, int ckpt_every) {
     st->ck_bw.push_back(bw);
     st->ck_T.push_back(Tt);
   }
-  cudaStream_t s = st->stream;
-  SHF_CK(cudaMemsetAsync(st->bv, 0, sizeof(float) * NC, s));
-  SHF_CK(cudaMemsetAsync(st->w, 0, sizeof(float) * KP, s));
-  SHF_CK(cudaMemsetAsync(st->bw, 0, sizeof(float) * KP, s));
-  SHF_CK(cudaMemsetAsync(st->u, 0, sizeof(float) * KP, s));
-  SHF_CK(cudaMemsetAsync(st->T, 0, sizeof(float2) * Ph * st->K, s));
-  for (int i = 0; i < T; ++i) {
-    if (i % ckpt_every == 0) {
-      const int c = i / ckpt_every;
-      SHF_CK(cudaMemcpyAsync(st->ck_bv[c], st->bv, sizeof(float) * NC, cudaMemcpyDeviceToDevice, s));
-      SHF_CK(cudaMemcpyAsync(st->ck_w[c], st->w, sizeof(float) * KP, cudaMemcpyDeviceToDevice, s));
-      SHF_CK(cudaMemcpyAsync(st->ck_bw[c], st->bw, sizeof(float) * KP, cudaMemcpyDeviceToDevice, s));
-      SHF_CK(cudaMemcpyAsync(st->ck_T[c], st->T, sizeof(float2) * Ph * st->K, cudaMemcpyDeviceToDevice, s));
-    }
-    SHF_CK(enqueue_generic_iteration(st, nullptr));
+  // one graph per (T, ckpt), replayed by later calls
+  if (!(st->un_fwd_exec && st->un_fwd_key[0] == T && st->un_fwd_key[1] == ckpt_every)) {
+    if (st->un_fwd_exec) cudaGraphExecDestroy(st->un_fwd_exec);
+    st->un_fwd_exec = capture_work(st, [&]() { return enqueue_unrolled_fwd(st, T, ckpt_every); });
+    st->un_fwd_key[0] = T;
+    st->un_fwd_key[1] = ckpt_every;
   }
+  if (st->un_fwd_exec)
+    SHF_CK(cudaGraphLaunch(st->un_fwd_exec, st->stream));
+  else
+    SHF_CK(enqueue_unrolled_fwd(st, T, ckpt_every));
   st->iter = T;
   st->un_T = T;
   st->un_ck = ckpt_every;
@@ -1141,75 +1325,39 @@ int seg_admm_unrolled_bwd(seg_state* st, const float* dL_dw, float* dL_dcodebook
   if (!st || !dL_dw || !dL_dcodebook || !dL_dLambda) return fail(SHF_ERR_ARG, "seg_admm_unrolled_bwd: NULL argument");
   if (st->un_T < 1) return fail(SHF_ERR_STATE, "seg_admm_unrolled_fwd has not run");
   const Geo& g = st->g;
-  const int K = st->K, C = st->C, eta = g.eta, T = st->un_T, ck = st->un_ck;
-  const size_t P = st->P(), Ph = st->Ph(), KP = P * K, NC = KP * eta;
-  const float scale = 1.f / (static_cast<float>(g.H) * g.W);
+  const int K = st->K, C = st->C, eta = g.eta;
+  const size_t P = st->P(), KP = P * K;
   cudaStream_t s = st->stream;
-  const int nblk = shf::adj_part_blocks();
-  // one allocation for every temporary of the sweep
-  const size_t nf = NC * 2 + KP * 6 + static_cast<size_t>(ck) * (NC + KP);
-  const size_t nc2 = Ph * K * 2;
-  const size_t nd = static_cast<size_t>(K) * eta * nblk + eta + static_cast<size_t>(K) * C * (nblk + 1);
-  char* mem = nullptr;
-  SHF_CK(cudaMallocAsync(reinterpret_cast<void**>(&mem), sizeof(float) * nf + sizeof(float2) * nc2 + sizeof(double) * nd,
-                         s));
-  float* fp = reinterpret_cast<float*>(mem);
-  float *bvbar = fp, *dbar = fp + NC;
-  fp += 2 * NC;
-  float *Qbar = fp, *wbar = fp + KP, *bwbar = fp + 2 * KP, *sbar = fp + 3 * KP, *gwbar = fp + 4 * KP,
-        *stv = fp + 5 * KP;
-  fp += 6 * KP;
-  float* grec = fp;
-  float* wrec = fp + static_cast<size_t>(ck) * NC;
-  float2* Uw = reinterpret_cast<float2*>(mem + sizeof(float) * nf);
-  float2* Tt = Uw + Ph * K;
-  double* dp = reinterpret_cast<double*>(mem + sizeof(float) * nf + sizeof(float2) * nc2);
-  double *tpart = dp, *tbar = dp + static_cast<size_t>(K) * eta * nblk, *cbpart = tbar + eta,
-         *cbout = cbpart + static_cast<size_t>(K) * C * nblk;
-  cudaError_t e = cudaSuccess;
+  const UnLayout U = un_layout(st, st->un_ck);
+  if (st->un_mem_bytes < U.total) {
+    SHF_CK(cudaStreamSynchronize(s));
+    if (st->un_bwd_exec) cudaGraphExecDestroy(st->un_bwd_exec);
+    st->un_bwd_exec = nullptr;
+    cudaFree(st->un_mem);
+    st->un_mem = nullptr;
+    st->un_mem_bytes = 0;
+    int rc = dev_alloc(&st->un_mem, U.total, "reverse-sweep scratch");
+    if (rc) return rc;
+    st->un_mem_bytes = U.total;
+  }
+  char* m = st->un_mem;
+  SHF_CK(cudaMemcpyAsync(m + U.wbar, dL_dw, sizeof(float) * KP, cudaMemcpyDeviceToDevice, s));
+  // one graph per (T, ckpt), replayed by later calls
+  if (!(st->un_bwd_exec && st->un_bwd_key[0] == st->un_T && st->un_bwd_key[1] == st->un_ck)) {
+    if (st->un_bwd_exec) cudaGraphExecDestroy(st->un_bwd_exec);
+    st->un_bwd_exec = capture_work(st, [&]() { return enqueue_unrolled_bwd(st, U); });
+    st->un_bwd_key[0] = st->un_T;
+    st->un_bwd_key[1] = st->un_ck;
+  }
+  cudaError_t e = st->un_bwd_exec ? cudaGraphLaunch(st->un_bwd_exec, s) : enqueue_unrolled_bwd(st, U);
   auto ok = [&](cudaError_t x) {
     if (e == cudaSuccess) e = x;
-    return e == cudaSuccess;
   };
-  ok(cudaMemsetAsync(bvbar, 0, sizeof(float) * NC, s));
-  ok(cudaMemsetAsync(Qbar, 0, sizeof(float) * KP, s));
-  ok(cudaMemsetAsync(bwbar, 0, sizeof(float) * KP, s));
-  ok(cudaMemsetAsync(sbar, 0, sizeof(float) * KP, s));
-  ok(cudaMemsetAsync(tbar, 0, sizeof(double) * eta, s));
-  ok(cudaMemcpyAsync(wbar, dL_dw, sizeof(float) * KP, cudaMemcpyDeviceToDevice, s));
-  const int nseg = (T + ck - 1) / ck;
-  for (int seg = nseg - 1; seg >= 0 && e == cudaSuccess; --seg) {
-    const int n = std::min(ck, T - seg * ck);
-    ok(cudaMemcpyAsync(st->bv, st->ck_bv[seg], sizeof(float) * NC, cudaMemcpyDeviceToDevice, s));
-    ok(cudaMemcpyAsync(st->w, st->ck_w[seg], sizeof(float) * KP, cudaMemcpyDeviceToDevice, s));
-    ok(cudaMemcpyAsync(st->bw, st->ck_bw[seg], sizeof(float) * KP, cudaMemcpyDeviceToDevice, s));
-    ok(cudaMemcpyAsync(st->T, st->ck_T[seg], sizeof(float2) * Ph * K, cudaMemcpyDeviceToDevice, s));
-    for (int i = 0; i < n && e == cudaSuccess; ++i) {  // recompute the segment, recording g and w'
-      ok(enqueue_generic_iteration(st, grec + static_cast<size_t>(i) * NC));
-      ok(cudaMemcpyAsync(wrec + static_cast<size_t>(i) * KP, st->w, sizeof(float) * KP, cudaMemcpyDeviceToDevice, s));
-    }
-    for (int i = n - 1; i >= 0 && e == cudaSuccess; --i) {
-      ok(shf::launch_adj_proj(wrec + static_cast<size_t>(i) * KP, wbar, bwbar, gwbar, K, static_cast<int>(P), s));
-      // dbar = S Qbar
-      ok(shf::run_row_r2c(g, Qbar, Uw, K, 1.f, s));
-      ok(shf::run_col_fan(g, Uw, st->un_Y, K, st->groups, s));
-      ok(shf::run_row_c2r(g, st->un_Y, dbar, K * eta, scale, s));
-      ok(shf::launch_adj_shrink(grec + static_cast<size_t>(i) * NC, dbar, bvbar, st->thr, K, eta,
-                                static_cast<long>(P), tpart, tbar, s));
-      // stv = S^T bvbar
-      ok(shf::run_row_r2c(g, bvbar, st->un_Y, K * eta, 1.f, s));
-      ok(shf::run_col_gather(g, st->un_Y, st->un_partial, K, st->un_groups, s));
-      ok(shf::run_col_reduce_inv(g, st->un_partial, Tt, K, st->un_groups, s));
-      ok(shf::run_row_c2r(g, Tt, stv, K, scale, s));
-      ok(shf::launch_adj_u(gwbar, stv, Qbar, wbar, bwbar, sbar, st->gamma, static_cast<long>(KP), s));
-    }
-  }
-  ok(shf::adj_codebook(sbar, st->f, st->codebook.data(), K, C, static_cast<long>(P), cbpart, cbout, dL_df, s));
-  if (dL_ds) ok(cudaMemcpyAsync(dL_ds, sbar, sizeof(float) * KP, cudaMemcpyDeviceToDevice, s));
+  if (dL_df) ok(cudaMemcpyAsync(dL_df, m + U.fbar, sizeof(float) * P * C, cudaMemcpyDeviceToDevice, s));
+  if (dL_ds) ok(cudaMemcpyAsync(dL_ds, m + U.sbar, sizeof(float) * KP, cudaMemcpyDeviceToDevice, s));
   std::vector<double> th(eta), cb(static_cast<size_t>(K) * C);
-  ok(cudaMemcpyAsync(th.data(), tbar, sizeof(double) * eta, cudaMemcpyDeviceToHost, s));
-  ok(cudaMemcpyAsync(cb.data(), cbout, sizeof(double) * K * C, cudaMemcpyDeviceToHost, s));
-  ok(cudaFreeAsync(mem, s));
+  ok(cudaMemcpyAsync(th.data(), m + U.tbar, sizeof(double) * eta, cudaMemcpyDeviceToHost, s));
+  ok(cudaMemcpyAsync(cb.data(), m + U.cbout, sizeof(double) * K * C, cudaMemcpyDeviceToHost, s));
   ok(cudaStreamSynchronize(s));
   if (e != cudaSuccess) return fail(SHF_ERR_CUDA, std::string("seg_admm_unrolled_bwd: ") + cudaGetErrorString(e));
   std::vector<shf::FilterDesc> d(eta);

@@ -127,7 +127,7 @@ void build_fast_plan(const Geo& g, const int2* ranges, FastPlan* plan, std::vect
 
 cudaError_t run_fast_iteration_body(const Geo& g, const FastPlan& plan, const float2* Ur, float2* uhat, float2* Y,
                                     float* bv, const float* thr, float2* partial, float2* T, int K, float scale,
-                                    cudaStream_t st, const LaunchHook& hook) {
+                                    cudaStream_t st, const LaunchHook& hook, signed char* code) {
   const int Whp = fast_pitch(g);
   const int nslots = plan.nslots;
   const int nw = static_cast<int>(plan.wave_f0.size());
@@ -146,7 +146,7 @@ cudaError_t run_fast_iteration_body(const Geo& g, const FastPlan& plan, const fl
       hook.mark(kKindShrink);
       const int groups = (nf * g.H + rpc - 1) / rpc;
       const int ctas = std::min(groups, std::max(plan.row_ctas, 1));
-      if (e == cudaSuccess) e = fast::row_shrink(g, ctas, Y, bv, thr, Whp, label, f0, nf, scale, st);
+      if (e == cudaSuccess) e = fast::row_shrink(g, ctas, Y, bv, thr, Whp, label, f0, nf, scale, code, st);
       if (nc > 0 && e == cudaSuccess) {
         hook.mark(kKindGather);
         e = fast::col_gather(g, nc, Y, plan.items, cb, partial, Whp, nslots, label, f0, st);
@@ -155,6 +155,30 @@ cudaError_t run_fast_iteration_body(const Geo& g, const FastPlan& plan, const fl
   }
   hook.mark(kKindReduce);
   if (e == cudaSuccess) e = fast::col_reduce(g, partial, plan.tile_begin, plan.tile_slots, T, K, nslots, st);
+  return e;
+}
+
+cudaError_t run_fast_adjoint_body(const Geo& g, const FastPlan& plan, const float2* Qr, float2* uhat, float2* Y,
+                                  float* bvbar, const float* thr, float2* partial, float2* Tbar, int K, float scale,
+                                  const signed char* code, double* tpart, cudaStream_t st) {
+  const int Whp = fast_pitch(g);
+  const int nslots = plan.nslots;
+  const int nw = static_cast<int>(plan.wave_f0.size());
+  const int rpc = fast::row_groups_per_cta(g.L);
+  cudaError_t e = fast::col_fwd(g, Qr, uhat, K, Whp, st);
+  for (int label = 0; label < K && e == cudaSuccess; ++label) {
+    for (int w = 0; w < nw && e == cudaSuccess; ++w) {
+      const int f0 = plan.wave_f0[w], nf = plan.wave_nf[w];
+      const int c0 = plan.wave_cta0[w], nc = plan.wave_cta0[w + 1] - c0;
+      const int* cb = plan.cta_begin + c0 + w;
+      if (nc > 0) e = fast::col_fan(g, nc, uhat, plan.items, cb, Y, Whp, label, f0, st);
+      const int groups = (nf * g.H + rpc - 1) / rpc;
+      const int ctas = std::min(groups, std::max(plan.row_ctas, 1));
+      if (e == cudaSuccess) e = fast::row_adjoint(g, ctas, Y, bvbar, thr, Whp, label, f0, nf, scale, code, tpart, st);
+      if (nc > 0 && e == cudaSuccess) e = fast::col_gather(g, nc, Y, plan.items, cb, partial, Whp, nslots, label, f0, st);
+    }
+  }
+  if (e == cudaSuccess) e = fast::col_reduce(g, partial, plan.tile_begin, plan.tile_slots, Tbar, K, nslots, st);
   return e;
 }
 

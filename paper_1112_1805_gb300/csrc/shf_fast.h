@@ -78,9 +78,15 @@ cudaError_t col_reduce(const Geo& g, const float2* partial, const int* tile_begi
 cudaError_t prepare_row_kernels();
 int row_ctas_per_sm(int L);     // resident CTAs per SM of the v-step kernel
 int row_groups_per_cta(int L);  // rows in flight per CTA of the v-step kernel
-// v-step on the wave's rows: ctas resident CTAs over nf filters of `label`.
+// v-step on the wave's rows: ctas resident CTAs over nf filters of `label`;
+// code (optional, [K][eta][H][W] bytes) receives 0 where |g| < t, else sign g.
 cudaError_t row_shrink(const Geo& g, int ctas, float2* Y, float* bv, const float* thr, int Whp, int label, int f0,
-                       int nf, float scale, cudaStream_t st);
+                       int nf, float scale, signed char* code, cudaStream_t st);
+// Adjoint of the v-step for the reverse mode: Y holds the spectra of the rows
+// of S Qbar on input and those of the new bvbar on output; tpart
+// [K][eta][H] receives the rows' threshold sums.
+cudaError_t row_adjoint(const Geo& g, int ctas, float2* Y, float* bvbar, const float* thr, int Whp, int label, int f0,
+                        int nf, float scale, const signed char* code, double* tpart, cudaStream_t st);
 // Shared memory of the u/w-step for K labels (0 if L is not supported).
 size_t ustep_smem_bytes(int L, int K);
 cudaError_t row_ustep(const Geo& g, const float2* T, const float* s, float* w, float* bw, float* u, float2* Ur, int K,

@@ -58,28 +58,46 @@ __device__ __forceinline__ uint64_t evict_first_policy() {
   return p;
 }
 
-// Shared memory of one row group of k_wrow_shrink: FFT exchange buffer(s),
-// and the stage that receives the next row's spectrum columns and b_v row.
-// Every region is a whole number of 16-byte units (even float2 counts) so that
-// the stage is 16-byte aligned for the asynchronous copies.
+// Shared memory of one row group of the v-step kernels: FFT exchange
+// buffer(s), and the stage that receives the next row's spectrum columns and
+// b_v row (the adjoint also its coefficient codes, and a slot per thread for
+// the row's threshold sum).  Every region is a whole number of 16-byte units
+// (even float2 counts) so that the stage is 16-byte aligned for the
+// asynchronous copies.
 __host__ __device__ constexpr int even2(int n) { return (n + 1) & ~1; }
-template <int L>
+template <int L, int MODE>
 struct RowGroupSmem {
   static constexpr int T = L / 8;
   static constexpr int NBUF = T <= 32 ? 1 : 2;  // warp-sized groups exchange through one buffer
   static constexpr int BUF = even2(reg::row_buf(L));
   static constexpr int SX = L + 8;              // spectrum columns [c0, c0 + SX), SX >= the row pitch
-  static constexpr int SB = L;                  // b_v row as float2
-  static constexpr int SIZE = NBUF * BUF + SX + SB;
+  static constexpr int SB = L;                  // b_v (or its adjoint) row as float2
+  static constexpr int SC = MODE == 1 ? L / 4 : 0;        // codes of the row: 2L bytes
+  static constexpr int SD = MODE == 1 ? even2(T) : 0;     // one double per thread
+  static constexpr int SIZE = NBUF * BUF + SX + SB + SC + SD;
   static constexpr int TW = even2(L + 1);                     // exp(-2 pi i m / W), m <= L
   static constexpr int PT = even2(reg::Passes<L>::TWSIZE);    // per-pass twiddles
   static constexpr int RPC = RowGeo<L>::RPC;                  // row groups per CTA
   static constexpr int TOTAL = TW + PT + RPC * SIZE;          // float2 per CTA
 };
 
-// v-step and b_v update of Sec. 3 on rows of (S u)_f: g = b_v + c,
+// Code of a coefficient for the reverse mode: 0 where |g| < t (clip is the
+// identity, soft shrinkage is 0), else the sign of g.
+__device__ __forceinline__ signed char clip_code(float g, float t) {
+  return fabsf(g) < t ? 0 : (g > 0.f ? 1 : -1);
+}
+
+// MODE 0: v-step and b_v update of Sec. 3 on rows of (S u)_f: g = b_v + c,
 // b_v <- clip(g, -t, t), d = soft(g, t) - clip(g, -t, t) = g - 2 clip(g);
-// d (= v - b_v of the new iterate) is transformed back in place.
+// d (= v - b_v of the new iterate) is transformed back in place.  With `code`
+// non-null it also records clip_code(g, t) per coefficient.
+// MODE 1: its adjoint for the reverse mode of the unrolled iteration: with
+// dbar = c (the rows of S Qbar) and the recorded codes m,
+// bvbar <- bvbar - dbar where m = 0, dbar elsewhere; the row's threshold sum
+// sum m (bvbar - 2 dbar) over m != 0 (FP64, fixed order) goes to
+// tpart[(label eta + f) H + row] (each thread sums its 16 terms in FP32 in a
+// fixed order; the group's partials are added in FP64 in thread order); the
+// new bvbar is transformed back in place (the input of S^T).
 // Rows r = (filter fl, row) with r = fl H + row over the wave's nf filters;
 // resident CTAs, each row group takes rows gid, gid + G, ... (G groups in
 // all).  While a group transforms its row, the next row's spectrum columns
@@ -87,14 +105,12 @@ struct RowGroupSmem {
 // group's stage; the twiddle tables are built once per CTA.
 // Four CTAs of 256 threads per SM (64 registers) for powers of two; three for
 // L = 3 2^a or 5 2^a, whose radix-R pass holds more values.
-template <int L>
+template <int L, int MODE>
 __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 : 768) / RowGeo<L>::NTH)
-    k_wrow_shrink(float2* __restrict__ Y, float* __restrict__ bv,
-                                                        const float* __restrict__ thr,
-                                                        const int2* __restrict__ ranges, int H, int Whp, int eta,
-                                                        int label, int f0, int nf, float scale,
-                                                        const float2* __restrict__ twW) {
-  using SM = RowGroupSmem<L>;
+    k_wrow_vstep(float2* __restrict__ Y, float* __restrict__ bv, const float* __restrict__ thr,
+                 const int2* __restrict__ ranges, int H, int Whp, int eta, int label, int f0, int nf, float scale,
+                 const float2* __restrict__ twW, signed char* __restrict__ code, double* __restrict__ tpart) {
+  using SM = RowGroupSmem<L, MODE>;
   constexpr int T = SM::T;
   constexpr int RPC = SM::RPC;
   extern __shared__ __align__(16) float2 sm[];
@@ -108,15 +124,18 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 
   float2* fb1 = gb + (SM::NBUF - 1) * SM::BUF;
   float2* sX = gb + SM::NBUF * SM::BUF;
   float2* sB = sX + SM::SX;
+  const char2* sC = reinterpret_cast<const char2*>(sB + SM::SB);
+  double* sD = reinterpret_cast<double*>(sB + SM::SB + SM::SC);
   const int bar = 1 + grp;
   const int G = gridDim.x * RPC;
   const int gid = blockIdx.x * RPC + grp;
   const int rows = nf * H;
   const int niter = (rows + G - 1) / G;  // the same for every group: dead rows still take part in barriers
   const uint64_t pol = evict_first_policy();
+  const size_t W = 2 * static_cast<size_t>(L);
 
   // request row r's spectrum columns (its filter's column range only) and
-  // its b_v row into the stage
+  // its b_v row (and codes) into the stage
   auto request_x = [&](int r) {
     if (r >= rows || !act) return;
     const int fl = r / H, row = r - fl * H;
@@ -131,9 +150,13 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 
   auto request_b = [&](int r) {
     if (r >= rows || !act) return;
     const int fl = r / H, row = r - fl * H;
-    const float2* B =
-        reinterpret_cast<const float2*>(bv) + ((static_cast<size_t>(label) * eta + f0 + fl) * H + row) * L;
+    const size_t rix = (static_cast<size_t>(label) * eta + f0 + fl) * H + row;
+    const float2* B = reinterpret_cast<const float2*>(bv) + rix * L;
     for (int q = tt; q < L / 2; q += T) cp_async16(sB + 2 * q, B + 2 * q, true, pol);
+    if (MODE == 1) {  // 2L bytes of codes: L/8 = T chunks of 16 bytes
+      const signed char* Cr = code + rix * W;
+      cp_async16(sB + SM::SB + 2 * tt, Cr + 16 * tt, true, pol);
+    }
   };
 
   // b_v was last written by this kernel's previous launch for the label,
@@ -154,6 +177,7 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 
     const int c0 = any ? (rg.x & ~7) : L + 1;
     const int c1 = any ? min(L, (rg.y | 7)) : -1;
     const float th = thr[f];
+    const size_t rix = (static_cast<size_t>(label) * eta + f) * H + row;
     cp_async_commit_wait_all();
     reg::group_sync<T>(bar);
     float2 v[8];
@@ -174,20 +198,44 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 
       reg::row_fft<L, +1>(v, tt, fb0, fb1, pt, bar);
     float2* X = Y + (static_cast<size_t>(fl) * H + row) * Whp;
     if (live) {
-      float2* b2 = reinterpret_cast<float2*>(bv) + ((static_cast<size_t>(label) * eta + f) * H + row) * L;
+      float2* b2 = reinterpret_cast<float2*>(bv) + rix * L;
+      if (MODE == 0) {
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const float2 bo = sB[tt + k * T];
-        const float gx = fmaf(scale, v[k].x, bo.x), gy = fmaf(scale, v[k].y, bo.y);
-        const float cx = fminf(fmaxf(gx, -th), th), cy = fminf(fmaxf(gy, -th), th);
-        if (act) __stcs(b2 + tt + k * T, make_float2(cx, cy));
-        v[k] = make_float2(gx - 2.f * cx, gy - 2.f * cy);
+        for (int k = 0; k < 8; ++k) {
+          const float2 bo = sB[tt + k * T];
+          const float gx = fmaf(scale, v[k].x, bo.x), gy = fmaf(scale, v[k].y, bo.y);
+          const float cx = fminf(fmaxf(gx, -th), th), cy = fminf(fmaxf(gy, -th), th);
+          if (act) __stcs(b2 + tt + k * T, make_float2(cx, cy));
+          if (code && act)
+            reinterpret_cast<char2*>(code + rix * W)[tt + k * T] = make_char2(clip_code(gx, th), clip_code(gy, th));
+          v[k] = make_float2(gx - 2.f * cx, gy - 2.f * cy);
+        }
+      } else {
+        float tacc = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const float2 bo = sB[tt + k * T];
+          const char2 m = sC[tt + k * T];
+          const float dx = scale * v[k].x, dy = scale * v[k].y;
+          const float nx = m.x == 0 ? bo.x - dx : dx;
+          const float ny = m.y == 0 ? bo.y - dy : dy;
+          tacc = fmaf(static_cast<float>(m.x), fmaf(-2.f, dx, bo.x), tacc);
+          tacc = fmaf(static_cast<float>(m.y), fmaf(-2.f, dy, bo.y), tacc);
+          if (act) __stcs(b2 + tt + k * T, make_float2(nx, ny));
+          v[k] = make_float2(nx, ny);
+        }
+        sD[tt] = static_cast<double>(tacc);
       }
     } else {
 #pragma unroll
       for (int k = 0; k < 8; ++k) v[k] = make_float2(0.f, 0.f);
     }
     reg::group_sync<T>(bar);  // the b_v stage is read: refill it with the group's next row
+    if (MODE == 1 && live && act && tt == 0) {  // the row's threshold sum, in thread order
+      double s = 0.0;
+      for (int j = 0; j < T; ++j) s += sD[j];
+      tpart[rix] = s;
+    }
     request_b(r + G);
     if (SM::NBUF == 1)
       reg::row_fft1<L, -1>(v, tt, fb0, pt, bar);
@@ -239,43 +287,69 @@ __device__ __forceinline__ void simplex_project(float (&g)[KMAX], int K) {
   for (int k = 0; k < KMAX; ++k) g[k] = ((act >> k) & 1u) ? g[k] - tau : 0.f;
 }
 
+// Geometry of the u/w-step kernel: a CTA takes NR rows and runs one row
+// group per (row, label) — K NR groups, laid out like RowGeo's groups (whole
+// warps for T > 32, 32/T per warp otherwise; groups past K NR idle).
+template <int L>
+struct UstepGeo {
+  using RG = RowGeo<L>;
+  static constexpr int T = RG::T;
+  __host__ __device__ static int rows(int K) {
+    const int nr = T <= 32 ? (8 * RG::GPW) / K : 8 / (RG::WPG * K);
+    return nr < 1 ? 1 : nr;
+  }
+  __host__ __device__ static int groups(int K) { return K * rows(K); }
+  // warps of the CTA, and the group slots they hold
+  __host__ __device__ static int warps(int K) {
+    return T <= 32 ? (groups(K) + RG::GPW - 1) / RG::GPW : groups(K) * RG::WPG;
+  }
+  __host__ __device__ static int slots(int K) { return T <= 32 ? warps(K) * RG::GPW : groups(K); }
+  // the largest CTA over K <= 8, and the CTAs per SM to ask the compiler for
+  static constexpr int MAXTH = T <= 32 ? 256 : 256 * RG::WPG;
+  static constexpr int MINB = T <= 32 ? 3 : 1;
+};
+
 // u-step (u = 1/2 [S^T(v - b_v) + (w - b_w) - gamma s], A^T A = 2I), w-step
 // (pixelwise simplex projection of g_w = b_w + u), b_w = g_w - w, and the row
-// spectra of u for the next analysis.  One row per group of L/8 threads, all
-// K labels; the carried values of a thread live in its private slots of U.
+// spectra of u for the next analysis (Sec. 3).  Phase 1: group (r, k) inverts
+// the spectrum row of label k into U[k][r]; phase 2: all threads do the
+// pointwise steps over the CTA's pixels and labels; phase 3: group (r, k)
+// transforms U[k][r] (now u) forward into Ur.
 template <int L, int KMAX>
-__global__ void __launch_bounds__(RowGeo<L>::NTH) k_wrow_ustep(const float2* __restrict__ Tsp, const float* __restrict__ s,
-                                                    float* __restrict__ w, float* __restrict__ bw,
-                                                    float* __restrict__ u, float2* __restrict__ Ur, int K, int H,
-                                                    float scale, float gamma, const float2* __restrict__ twW) {
+__global__ void __launch_bounds__(UstepGeo<L>::MAXTH, UstepGeo<L>::MINB) k_wrow_ustep(const float2* __restrict__ Tsp, const float* __restrict__ s,
+                                                     float* __restrict__ w, float* __restrict__ bw,
+                                                     float* __restrict__ u, float2* __restrict__ Ur, int K, int H,
+                                                     float scale, float gamma, const float2* __restrict__ twW) {
+  using UG = UstepGeo<L>;
   constexpr int T = L / 8;
-  constexpr int RPC = RowGeo<L>::RPC;
-  constexpr int NTH = RowGeo<L>::NTH;
   constexpr int BUF = reg::row_buf(L);
+  constexpr int NBUF = T <= 32 ? 1 : 2;
   constexpr int Wh = L + 1;
+  const int NR = UG::rows(K), NG = K * NR;
   extern __shared__ float2 sm[];
   float2* tw = sm;
   float2* pt = tw + (L + 1);
   int grp, tt;
   bool act;
   RowGeo<L>::locate(grp, tt, act);
-  float2* b0 = pt + reg::Passes<L>::TWSIZE + grp * 2 * BUF;
-  float2* b1 = b0 + BUF;
-  float2* U = pt + reg::Passes<L>::TWSIZE + RPC * 2 * BUF;  // [k][e][thread]
+  float2* b0 = pt + reg::Passes<L>::TWSIZE + grp * NBUF * BUF;
+  float2* b1 = b0 + (NBUF - 1) * BUF;
+  float2* U = pt + reg::Passes<L>::TWSIZE + UG::slots(K) * NBUF * BUF;  // [k][r][L]
+  const bool real = grp < NG;  // groups past K NR only take part in barriers
+  const int r = real ? grp / K : 0, k = real ? grp - (grp / K) * K : 0;
   const int bar = 1 + grp;
-  const int row = blockIdx.x * RPC + grp;
-  const bool live = row < H;
-  const int rowc = live ? row : 0;
+  const int row = blockIdx.x * NR + r;
+  const bool live = real && row < H;
+  const int rowc = row < H ? row : 0;
   const size_t HL = static_cast<size_t>(H) * L, HWh = static_cast<size_t>(H) * Wh;
-  auto slot = [&](int k, int e) { return (k * 8 + e) * NTH + threadIdx.x; };
+  float2* Uk = U + (static_cast<size_t>(k) * NR + r) * L;
   load_table(tw, twW, L + 1);
   reg::build_pass_twiddles<L, 2>(pt, twW, threadIdx.x, blockDim.x);
   pdl_wait();
   pdl_trigger();
   __syncthreads();
-  // S^T(v - b_v) on this row, label by label
-  for (int k = 0; k < K; ++k) {
-    reg::group_sync<T>(bar);  // the previous label's transform may still read b1
+  // phase 1: S^T(v - b_v) on row r of label k
+  {
     const float2* X = Tsp + HWh * k + static_cast<size_t>(rowc) * Wh;
     for (int i = tt; i <= L; i += T) b1[reg::ridx(i)] = live ? X[i] : make_float2(0.f, 0.f);
     reg::group_sync<T>(bar);
@@ -289,71 +363,81 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH) k_wrow_ustep(const float2* __r
       const float2 t = c_mul(c_conj(tw[n]), d);
       v[e] = make_float2(sm2.x - t.y, sm2.y + t.x);
     }
-    reg::row_fft<L, +1>(v, tt, b0, b1, pt, bar);
+    if (NBUF == 1)
+      reg::row_fft1<L, +1>(v, tt, b0, pt, bar);
+    else
+      reg::row_fft<L, +1>(v, tt, b0, b1, pt, bar);
+    if (real && act) {
 #pragma unroll
-    for (int e = 0; e < 8; ++e) U[slot(k, e)] = c_scale(v[e], scale);
+      for (int e = 0; e < 8; ++e) Uk[tt + e * T] = c_scale(v[e], scale);
+    }
   }
-  // pointwise u-step, projection and b_w update (two pixels per slot)
-  if (live) {
-    const float2* s2 = reinterpret_cast<const float2*>(s) + static_cast<size_t>(row) * L;
-    float2* w2 = reinterpret_cast<float2*>(w) + static_cast<size_t>(row) * L;
-    float2* bw2 = reinterpret_cast<float2*>(bw) + static_cast<size_t>(row) * L;
-    float2* u2 = reinterpret_cast<float2*>(u) + static_cast<size_t>(row) * L;
+  __syncthreads();
+  // phase 2: pointwise u-step, projection and b_w update (two pixels per item)
+  {
     const float hg = 0.5f * gamma;
-#pragma unroll 1
-    for (int e = 0; e < 8; ++e) {
-      const int n = tt + e * T;
+    for (int i = threadIdx.x; i < NR * L; i += blockDim.x) {
+      const int ri = i / L, n = i - ri * L;
+      const int prow = blockIdx.x * NR + ri;
+      if (prow >= H) continue;
+      const size_t pix = static_cast<size_t>(prow) * L + n;
+      const float2* s2 = reinterpret_cast<const float2*>(s);
+      float2* w2 = reinterpret_cast<float2*>(w);
+      float2* bw2 = reinterpret_cast<float2*>(bw);
+      float2* u2 = reinterpret_cast<float2*>(u);
       float gx[KMAX], gy[KMAX];
 #pragma unroll
-      for (int k = 0; k < KMAX; ++k) {
-        gx[k] = 0.f;
-        gy[k] = 0.f;
-        if (k < K) {
-          const float2 st = U[slot(k, e)];
-          const float2 wv = w2[HL * k + n], bv = bw2[HL * k + n], sv = s2[HL * k + n];
+      for (int q = 0; q < KMAX; ++q) {
+        gx[q] = 0.f;
+        gy[q] = 0.f;
+        if (q < K) {
+          float2* Uq = U + (static_cast<size_t>(q) * NR + ri) * L + n;
+          const float2 st = *Uq;
+          const float2 wv = w2[HL * q + pix], bv = bw2[HL * q + pix], sv = s2[HL * q + pix];
           const float ux = 0.5f * (st.x + (wv.x - bv.x)) - hg * sv.x;
           const float uy = 0.5f * (st.y + (wv.y - bv.y)) - hg * sv.y;
-          if (act) u2[HL * k + n] = make_float2(ux, uy);
-          U[slot(k, e)] = make_float2(ux, uy);
-          gx[k] = bv.x + ux;
-          gy[k] = bv.y + uy;
+          u2[HL * q + pix] = make_float2(ux, uy);
+          *Uq = make_float2(ux, uy);
+          gx[q] = bv.x + ux;
+          gy[q] = bv.y + uy;
         }
       }
       float px[KMAX], py[KMAX];
 #pragma unroll
-      for (int k = 0; k < KMAX; ++k) {
-        px[k] = gx[k];
-        py[k] = gy[k];
+      for (int q = 0; q < KMAX; ++q) {
+        px[q] = gx[q];
+        py[q] = gy[q];
       }
       simplex_project<KMAX>(px, K);
       simplex_project<KMAX>(py, K);
 #pragma unroll
-      for (int k = 0; k < KMAX; ++k)
-        if (k < K && act) {
-          w2[HL * k + n] = make_float2(px[k], py[k]);
-          bw2[HL * k + n] = make_float2(gx[k] - px[k], gy[k] - py[k]);
+      for (int q = 0; q < KMAX; ++q)
+        if (q < K) {
+          w2[HL * q + pix] = make_float2(px[q], py[q]);
+          bw2[HL * q + pix] = make_float2(gx[q] - px[q], gy[q] - py[q]);
         }
     }
-  } else {
-    for (int k = 0; k < K; ++k)
-#pragma unroll
-      for (int e = 0; e < 8; ++e) U[slot(k, e)] = make_float2(0.f, 0.f);
   }
-  // row spectra of u
-  for (int k = 0; k < K; ++k) {
+  __syncthreads();
+  // phase 3: row spectrum of u on row r of label k
+  {
     float2 v[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = U[slot(k, e)];
-    reg::row_fft<L, -1>(v, tt, b0, b1, pt, bar);
+    for (int e = 0; e < 8; ++e) v[e] = Uk[tt + e * T];
+    if (NBUF == 1)
+      reg::row_fft1<L, -1>(v, tt, b0, pt, bar);
+    else
+      reg::row_fft<L, -1>(v, tt, b0, b1, pt, bar);
+    float2* ub = NBUF == 1 ? b0 : b1;
     reg::group_sync<T>(bar);
 #pragma unroll
-    for (int e = 0; e < 8; ++e) b1[reg::ridx(tt + e * T)] = v[e];
+    for (int e = 0; e < 8; ++e) ub[reg::ridx(tt + e * T)] = v[e];
     reg::group_sync<T>(bar);
     if (live && act) {
       float2* X = Ur + HWh * k + static_cast<size_t>(row) * Wh;
       for (int i = tt; i <= L; i += T) {
-        const float2 a = b1[reg::ridx(i == L ? 0 : i)];
-        const float2 c = c_conj(b1[reg::ridx(i == 0 ? 0 : L - i)]);
+        const float2 a = ub[reg::ridx(i == L ? 0 : i)];
+        const float2 c = c_conj(ub[reg::ridx(i == 0 ? 0 : L - i)]);
         const float2 sm2 = c_add(a, c), d = c_sub(a, c);
         const float2 t = c_mul(tw[i], d);
         X[i] = make_float2(0.5f * (sm2.x + t.y), 0.5f * (sm2.y - t.x));
@@ -366,21 +450,23 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH) k_wrow_ustep(const float2* __r
 
 namespace {
 
-template <int L>
-size_t shrink_smem() {
-  return sizeof(float2) * RowGroupSmem<L>::TOTAL;
+template <int L, int MODE>
+size_t vstep_smem() {
+  return sizeof(float2) * RowGroupSmem<L, MODE>::TOTAL;
 }
 
 template <int L>
 size_t ustep_smem(int K) {
-  using RG = RowGeo<L>;
-  return sizeof(float2) *
-         ((L + 1) + reg::Passes<L>::TWSIZE + RG::RPC * 2 * reg::row_buf(L) + static_cast<size_t>(K) * 8 * RG::NTH);
+  using UG = UstepGeo<L>;
+  const int nbuf = L / 8 <= 32 ? 1 : 2;
+  return sizeof(float2) * ((L + 1) + reg::Passes<L>::TWSIZE + static_cast<size_t>(UG::slots(K)) * nbuf * reg::row_buf(L) +
+                           static_cast<size_t>(K) * UG::rows(K) * L);
 }
 
 template <int L>
 cudaError_t prepare_row_t() {
-  cudaError_t e = allow_smem(k_wrow_shrink<L>, shrink_smem<L>());
+  cudaError_t e = allow_smem(k_wrow_vstep<L, 0>, vstep_smem<L, 0>());
+  if (e == cudaSuccess) e = allow_smem(k_wrow_vstep<L, 1>, vstep_smem<L, 1>());
   if (e == cudaSuccess) e = allow_smem(k_wrow_ustep<L, 4>, ustep_smem<L>(4));
   if (e == cudaSuccess) e = allow_smem(k_wrow_ustep<L, 8>, ustep_smem<L>(8));
   return e;
@@ -389,13 +475,14 @@ cudaError_t prepare_row_t() {
 template <int L>
 cudaError_t ustep_t(const Geo& g, const float2* T, const float* s, float* w, float* bw, float* u, float2* Ur, int K,
                     float gamma, float scale, cudaStream_t st) {
-  using RG = RowGeo<L>;
-  const dim3 grid((g.H + RG::RPC - 1) / RG::RPC);
+  using UG = UstepGeo<L>;
+  const int nr = UG::rows(K);
+  const dim3 grid((g.H + nr - 1) / nr), block(32 * UG::warps(K));
   if (K <= 4)
-    return launch_pdl(k_wrow_ustep<L, 4>, grid, dim3(RG::NTH), ustep_smem<L>(K), st, T, s, w, bw, u, Ur, K, g.H,
-                      scale, gamma, g.twW);
-  return launch_pdl(k_wrow_ustep<L, 8>, grid, dim3(RG::NTH), ustep_smem<L>(K), st, T, s, w, bw, u, Ur, K, g.H,
-                    scale, gamma, g.twW);
+    return launch_pdl(k_wrow_ustep<L, 4>, grid, block, ustep_smem<L>(K), st, T, s, w, bw, u, Ur, K, g.H, scale,
+                      gamma, g.twW);
+  return launch_pdl(k_wrow_ustep<L, 8>, grid, block, ustep_smem<L>(K), st, T, s, w, bw, u, Ur, K, g.H, scale,
+                    gamma, g.twW);
 }
 
 }  // namespace
@@ -415,7 +502,7 @@ int row_ctas_per_sm(int L) {
   switch (L) {
 #define SHF_OCC(N)                                                                                                \
   case N:                                                                                                         \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_shrink<N>, RowGeo<N>::NTH, shrink_smem<N>()); \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_vstep<N, 0>, RowGeo<N>::NTH, vstep_smem<N, 0>()); \
     break;
     SHF_FAST_SIZES(SHF_OCC)
 #undef SHF_OCC
@@ -436,12 +523,25 @@ int row_groups_per_cta(int L) {
 }
 
 cudaError_t row_shrink(const Geo& g, int ctas, float2* Y, float* bv, const float* thr, int Whp, int label, int f0,
-                       int nf, float scale, cudaStream_t st) {
+                       int nf, float scale, signed char* code, cudaStream_t st) {
   switch (g.L) {
-#define SHF_CASE(N)                                                                                                \
-  case N:                                                                                                          \
-    return launch_pdl(k_wrow_shrink<N>, dim3(ctas), dim3(RowGeo<N>::NTH), shrink_smem<N>(), st, Y, bv, thr,      \
-                      g.ranges, g.H, Whp, g.eta, label, f0, nf, scale, g.twW);
+#define SHF_CASE(N)                                                                                              \
+  case N:                                                                                                        \
+    return launch_pdl(k_wrow_vstep<N, 0>, dim3(ctas), dim3(RowGeo<N>::NTH), vstep_smem<N, 0>(), st, Y, bv, thr, \
+                      g.ranges, g.H, Whp, g.eta, label, f0, nf, scale, g.twW, code, static_cast<double*>(nullptr));
+    SHF_FAST_SIZES(SHF_CASE)
+#undef SHF_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t row_adjoint(const Geo& g, int ctas, float2* Y, float* bvbar, const float* thr, int Whp, int label, int f0,
+                        int nf, float scale, const signed char* code, double* tpart, cudaStream_t st) {
+  switch (g.L) {
+#define SHF_CASE(N)                                                                                                  \
+  case N:                                                                                                            \
+    return launch_pdl(k_wrow_vstep<N, 1>, dim3(ctas), dim3(RowGeo<N>::NTH), vstep_smem<N, 1>(), st, Y, bvbar, thr, \
+                      g.ranges, g.H, Whp, g.eta, label, f0, nf, scale, g.twW, const_cast<signed char*>(code), tpart);
     SHF_FAST_SIZES(SHF_CASE)
 #undef SHF_CASE
     default: return cudaErrorInvalidValue;

@@ -153,9 +153,19 @@ cudaError_t run_fast_ustep(const Geo& g, const float2* T, const float* s, float*
                            int K, float gamma, float scale, cudaStream_t st);
 // Everything of an iteration after the u/w-step: Ur (row spectra of u) -> uhat
 // -> per-filter analysis, v-step and synthesis -> T.
+// code (optional, [K][eta][H][W] bytes): receives, per coefficient, 0 where
+// |g| < t_f and the sign of g elsewhere (for the reverse mode).
 cudaError_t run_fast_iteration_body(const Geo& g, const FastPlan& plan, const float2* Ur, float2* uhat, float2* Y,
                                     float* bv, const float* thr, float2* partial, float2* T, int K, float scale,
-                                    cudaStream_t st, const LaunchHook& hook);
+                                    cudaStream_t st, const LaunchHook& hook, signed char* code = nullptr);
+// Adjoint of the analysis - v-step - synthesis part of an iteration (reverse
+// mode): Qr [K][H][Wh] the row spectra of Qbar; bvbar [K][eta][H][W] updated in
+// place with the codes of the forward iteration; Tbar [K][H][Wh] receives the
+// column-inverse spectrum of S^T bvbar (row-inverse and 1/(HW) left to the
+// caller); tpart [K][eta][H] the rows' threshold sums.
+cudaError_t run_fast_adjoint_body(const Geo& g, const FastPlan& plan, const float2* Qr, float2* uhat, float2* Y,
+                                  float* bvbar, const float* thr, float2* partial, float2* Tbar, int K, float scale,
+                                  const signed char* code, double* tpart, cudaStream_t st);
 // Resident CTAs of one column launch for `per_sm` CTAs per SM (0: as many
 // as fit; larger values are clamped to that).
 int fast_col_ctas(const Geo& g, int per_sm);
@@ -184,6 +194,8 @@ cudaError_t launch_adj_u(const float* gwbar, const float* st_, float* Qbar, floa
 cudaError_t adj_codebook(const float* sbar, const float* f, const float* codebook_host, int K, int C, long P,
                          double* part, double* out_dev, float* fbar, cudaStream_t st);
 int adj_part_blocks();
+// tbar[f] += sum over labels and rows of tpart[(k eta + f) H + row], in order.
+cudaError_t launch_adj_tsum_rows(const double* tpart, int K, int eta, int H, double* tbar, cudaStream_t st);
 
 // C ABI layer (shf_capi.cu): the geometry and device tables of a bank, and the
 // thread-local message behind shf_last_error() (returns code).

@@ -52,8 +52,11 @@ def _close(a, b, rel=1e-3, abs_=1e-6):
     return np.abs(a - b).max() <= rel * np.abs(b).max() + abs_
 
 
+# register-FFT sizes (24 x 32, 64 x 64, 32 x 48, 40 x 80) take the fused fast
+# reverse sweep; 30 x 50 takes the general kernels
 @pytest.mark.parametrize("H,W,K,J,C,T,ck", [(24, 32, 3, 2, 1, 8, 3), (24, 32, 3, 2, 3, 8, 8), (64, 64, 3, 2, 1, 20, 5),
-                                            (32, 48, 4, 1, 1, 12, 1)])
+                                            (32, 48, 4, 1, 1, 12, 1), (40, 80, 5, 2, 1, 10, 4),
+                                            (30, 50, 3, 2, 1, 8, 3)])
 def test_gradients_match_oracle(oracle_mod, H, W, K, J, C, T, ck):
     torch = need_cuda()
     img, lab, cb, Lam = _problem(H * W + K, H, W, K, J, C)

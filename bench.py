@@ -10,7 +10,8 @@ plan is autotuned on the image before the timed region (--no-tune keeps the
 default).  At N = 1 the line also carries `batched`: the same metric for the
 64-image uneven batch (one graph per iteration with a branch per image), one
 timed step of 300 iterations after three short warm-up steps (--no-batch
-skips it).
+skips it), and `differentiable`: 16 images of 256 x 256 through the unrolled
+forward and reverse sweeps (--no-differentiable skips it).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -55,6 +56,8 @@ def parse_args():
     ap.add_argument("--cpu-iters", type=int, default=2, help="oracle iterations in the CPU-baseline sample")
     ap.add_argument("--workload", choices=["bezier512", "batch"], default="bezier512",
                     help="bezier512 (default line) or the uneven batch of 64 images")
+    ap.add_argument("--no-differentiable", action="store_true",
+                    help="skip the unrolled forward+reverse measurement the default line carries under 'differentiable'")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched measurement that the default line carries under 'batched'")
     ap.add_argument("--no-tune", action="store_true",
@@ -357,6 +360,8 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_batch:
         # the batched form on the same GPU (the plain state is released first)
         line["batched"] = measure_batch(300, 1, 3, 30, not args.no_tune)
+    if rank == 0 and world == 1 and not args.no_differentiable:
+        line["differentiable"] = measure_differentiable(2, 1)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -401,6 +406,65 @@ def measure_batch(iters: int, steps: int, warmup_steps: int, warmup_iters: int, 
             "workload": f"batch: {len(shapes)} images, sides 128..1024 (first 384x640), K 2..6, "
                         f"J = floor(log2(min side)/2), {iters} iterations per step, one graph per iteration "
                         f"with a branch per image"}
+
+
+def measure_differentiable(steps: int, warmup: int, n_images: int = 16):
+    """The differentiable workload: n_images seeded 256 x 256 images (K = 4,
+    J = 3), each T = 50 unrolled ADMM iterations from the zero state with
+    checkpoints every 10, then the reverse sweep for a fixed cotangent of w
+    (gradients w.r.t. codebook, Lambda and the image).  Units per image and
+    pass: H*W*K*T, one forward + reverse pass counted once."""
+    import torch
+
+    from paper_1112_1805_gb300 import binding as B
+    from paper_1112_1805_gb300.api import FilterBank, ShearletSegmenter
+
+    wl = synth.WORKLOADS["unrolled256"]
+    T, ck = wl.iters, 10
+    fb = FilterBank(wl.H, wl.W, wl.J)
+    segs, cots = [], []
+    gen = torch.Generator(device="cuda").manual_seed(synth.seed_for(wl.index))
+    for i in range(n_images):
+        img, _, _ = synth.make_workload_image("unrolled256", i)
+        segs.append(ShearletSegmenter(fb, torch.tensor(img.astype(np.float32), device="cuda"), wl.codebook(),
+                                      wl.Lambda(), wl.gamma))
+        cots.append(1e-3 * torch.randn((wl.K, wl.H, wl.W), device="cuda", generator=gen))
+    fbar = torch.empty((1, wl.H, wl.W), device="cuda")
+    torch.cuda.synchronize()
+
+    def one_pass():
+        for sg, c in zip(segs, cots):
+            B.seg_admm_unrolled_fwd(sg.handle, T, ck)
+            B.seg_admm_unrolled_bwd(sg.handle, c.data_ptr(), wl.K, 1, wl.J, fbar.data_ptr())
+
+    for _ in range(warmup):
+        one_pass()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one_pass()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    plain_ms = None
+    # the plain iteration on the same images for comparison: T iterations per image
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(segs[0].stream)
+    for sg in segs:
+        B.seg_admm_step(sg.handle, T)
+    for sg in segs:
+        sg.synchronize()
+    e1.record(segs[0].stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    units = n_images * wl.H * wl.W * wl.K * T
+    for sg in segs:
+        sg.close()
+    fb.close()
+    return {"value": units / dt / 1e6, "unit": UNIT, "ms_per_step": dt * 1000.0, "steps": steps, "warmup": warmup,
+            "forward_only_value": units / (plain_ms / 1000.0) / 1e6,
+            "workload": f"{n_images} x 256x256 gray, K=4, J=3 (eta=29), {T} unrolled ADMM iterations from zero with "
+                        f"checkpoints every {ck}, reverse sweep for a fixed cotangent of w (gradients w.r.t. "
+                        f"codebook, Lambda, image); one forward+reverse pass counted as {T} iterations"}
 
 
 def run_batch(args):

@@ -54,8 +54,9 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--cpu-iters", type=int, default=2, help="oracle iterations in the CPU-baseline sample")
-    ap.add_argument("--workload", choices=["bezier512", "batch"], default="bezier512",
-                    help="bezier512 (default line) or the uneven batch of 64 images")
+    ap.add_argument("--workload", choices=["bezier512", "batch", "differentiable"], default="bezier512",
+                    help="bezier512 (default line), the uneven batch of 64 images, or the unrolled workload")
+    ap.add_argument("--images", type=int, default=16, help="images of the differentiable workload")
     ap.add_argument("--no-differentiable", action="store_true",
                     help="skip the unrolled forward+reverse measurement the default line carries under 'differentiable'")
     ap.add_argument("--no-batch", action="store_true",
@@ -467,6 +468,21 @@ def measure_differentiable(steps: int, warmup: int, n_images: int = 16):
                         f"codebook, Lambda, image); one forward+reverse pass counted as {T} iterations"}
 
 
+def run_differentiable(args):
+    """The differentiable workload as the bench line itself (--workload differentiable)."""
+    import torch
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    d = measure_differentiable(args.steps, args.warmup, args.images)
+    line = {"metric": METRIC, "value": d["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": d["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": d["workload"], "images": args.images},
+            "forward_only_value": d["forward_only_value"]}
+    print(json.dumps(line))
+    return 0
+
+
 def run_batch(args):
     """The batch as the bench line itself (--workload batch)."""
     import torch
@@ -488,6 +504,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "differentiable":
+        return run_differentiable(args)
     return run_ours(args)
 
 

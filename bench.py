@@ -430,13 +430,18 @@ def measure_differentiable(steps: int, warmup: int, n_images: int = 16):
         segs.append(ShearletSegmenter(fb, torch.tensor(img.astype(np.float32), device="cuda"), wl.codebook(),
                                       wl.Lambda(), wl.gamma))
         cots.append(1e-3 * torch.randn((wl.K, wl.H, wl.W), device="cuda", generator=gen))
-    fbar = torch.empty((1, wl.H, wl.W), device="cuda")
     torch.cuda.synchronize()
 
+    fbars = [torch.empty((1, wl.H, wl.W), device="cuda") for _ in segs]
+
     def one_pass():
+        # every image's forward and reverse sweep is queued on its own stream,
+        # then the gradients are read back
         for sg, c in zip(segs, cots):
             B.seg_admm_unrolled_fwd(sg.handle, T, ck)
-            B.seg_admm_unrolled_bwd(sg.handle, c.data_ptr(), wl.K, 1, wl.J, fbar.data_ptr())
+            B.seg_admm_unrolled_bwd_enqueue(sg.handle, c.data_ptr())
+        for sg, fb_ in zip(segs, fbars):
+            B.seg_admm_unrolled_grads(sg.handle, wl.K, 1, wl.J, fb_.data_ptr())
 
     for _ in range(warmup):
         one_pass()

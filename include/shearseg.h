@@ -264,6 +264,16 @@ int seg_admm_unrolled_fwd(seg_state* st, int T, int ckpt_every);
 int seg_admm_unrolled_bwd(seg_state* st, const float* dL_dw, float* dL_dcodebook, float* dL_dLambda, float* dL_df,
                           float* dL_ds);
 
+/* The reverse sweep of seg_admm_unrolled_bwd in two parts, so that states on
+ * different streams sweep concurrently.  _enqueue queues the sweep on the
+ * state's stream and returns at once; dL_dw (device [K][H][W]) is read by a
+ * queued copy and must stay valid until _grads returns.  _grads waits for the
+ * sweep and writes the same outputs as seg_admm_unrolled_bwd.  Errors:
+ * SHF_ERR_STATE (no forward; _grads without _enqueue), and those of
+ * seg_admm_unrolled_bwd. */
+int seg_admm_unrolled_bwd_enqueue(seg_state* st, const float* dL_dw);
+int seg_admm_unrolled_grads(seg_state* st, float* dL_dcodebook, float* dL_dLambda, float* dL_df, float* dL_ds);
+
 /* Instrumentation (no counterpart in the paper): time spent in each kind of
  * kernel during the most recent iteration, measured by CUDA events recorded
  * on the state's stream before every launch (event nodes inside the replayed

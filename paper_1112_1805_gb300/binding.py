@@ -93,6 +93,8 @@ _SIG = {
     "seg_admm_set_plan": (_I, [_VP, ctypes.POINTER(seg_plan)]),
     "seg_admm_tune": (_I, [_VP, _I, ctypes.POINTER(seg_plan)]),
     "seg_admm_batch_tune": (_I, [_VP, _I]),
+    "seg_admm_unrolled_bwd_enqueue": (_I, [_VP, _VP]),
+    "seg_admm_unrolled_grads": (_I, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _VP, _VP]),
     "seg_admm_sync": (_I, [_VP]),
     "seg_admm_destroy": (_I, [_VP]),
 }
@@ -318,5 +320,18 @@ def seg_admm_unrolled_bwd(state: int, dL_dw: int, K: int, C: int, J: int, dL_df:
     dc = (ctypes.c_float * (K * C))()
     dl = (ctypes.c_float * (J + 1))()
     _call("seg_admm_unrolled_bwd", _VP(state), _VP(dL_dw), dc, dl, _VP(dL_df) if dL_df else None,
+          _VP(dL_ds) if dL_ds else None)
+    return list(dc), list(dl)
+
+
+def seg_admm_unrolled_bwd_enqueue(state: int, dL_dw: int) -> None:
+    _call("seg_admm_unrolled_bwd_enqueue", _VP(state), _VP(dL_dw))
+
+
+def seg_admm_unrolled_grads(state: int, K: int, C: int, J: int, dL_df: int = 0, dL_ds: int = 0):
+    """(dL/dcodebook as a K*C list, dL/dLambda as a J+1 list) of the enqueued sweep."""
+    dc = (ctypes.c_float * (K * C))()
+    dl = (ctypes.c_float * (J + 1))()
+    _call("seg_admm_unrolled_grads", _VP(state), dc, dl, _VP(dL_df) if dL_df else None,
           _VP(dL_ds) if dL_ds else None)
     return list(dc), list(dl)

@@ -120,6 +120,7 @@ struct seg_state {
   int un_fwd_key[2] = {0, 0}, un_bwd_key[2] = {0, 0};
   char* un_mem = nullptr;
   size_t un_mem_bytes = 0;
+  bool un_bwd_pending = false;  // a reverse sweep was enqueued (its results are in un_mem)
   long long iter = 0;
   size_t P() const { return static_cast<size_t>(g.H) * g.W; }
   size_t Ph() const { return static_cast<size_t>(g.H) * g.Wh; }
@@ -1320,13 +1321,10 @@ int seg_admm_unrolled_fwd(seg_state* st, int T, int ckpt_every) {
   return SHF_OK;
 }
 
-int seg_admm_unrolled_bwd(seg_state* st, const float* dL_dw, float* dL_dcodebook, float* dL_dLambda, float* dL_df,
-                          float* dL_ds) {
-  if (!st || !dL_dw || !dL_dcodebook || !dL_dLambda) return fail(SHF_ERR_ARG, "seg_admm_unrolled_bwd: NULL argument");
+int seg_admm_unrolled_bwd_enqueue(seg_state* st, const float* dL_dw) {
+  if (!st || !dL_dw) return fail(SHF_ERR_ARG, "seg_admm_unrolled_bwd_enqueue: NULL argument");
   if (st->un_T < 1) return fail(SHF_ERR_STATE, "seg_admm_unrolled_fwd has not run");
-  const Geo& g = st->g;
-  const int K = st->K, C = st->C, eta = g.eta;
-  const size_t P = st->P(), KP = P * K;
+  const size_t KP = st->P() * st->K;
   cudaStream_t s = st->stream;
   const UnLayout U = un_layout(st, st->un_ck);
   if (st->un_mem_bytes < U.total) {
@@ -1340,8 +1338,7 @@ int seg_admm_unrolled_bwd(seg_state* st, const float* dL_dw, float* dL_dcodebook
     if (rc) return rc;
     st->un_mem_bytes = U.total;
   }
-  char* m = st->un_mem;
-  SHF_CK(cudaMemcpyAsync(m + U.wbar, dL_dw, sizeof(float) * KP, cudaMemcpyDeviceToDevice, s));
+  SHF_CK(cudaMemcpyAsync(st->un_mem + U.wbar, dL_dw, sizeof(float) * KP, cudaMemcpyDeviceToDevice, s));
   // one graph per (T, ckpt), replayed by later calls
   if (!(st->un_bwd_exec && st->un_bwd_key[0] == st->un_T && st->un_bwd_key[1] == st->un_ck)) {
     if (st->un_bwd_exec) cudaGraphExecDestroy(st->un_bwd_exec);
@@ -1349,7 +1346,21 @@ int seg_admm_unrolled_bwd(seg_state* st, const float* dL_dw, float* dL_dcodebook
     st->un_bwd_key[0] = st->un_T;
     st->un_bwd_key[1] = st->un_ck;
   }
-  cudaError_t e = st->un_bwd_exec ? cudaGraphLaunch(st->un_bwd_exec, s) : enqueue_unrolled_bwd(st, U);
+  SHF_CK(st->un_bwd_exec ? cudaGraphLaunch(st->un_bwd_exec, s) : enqueue_unrolled_bwd(st, U));
+  st->un_bwd_pending = true;
+  return SHF_OK;
+}
+
+int seg_admm_unrolled_grads(seg_state* st, float* dL_dcodebook, float* dL_dLambda, float* dL_df, float* dL_ds) {
+  if (!st || !dL_dcodebook || !dL_dLambda) return fail(SHF_ERR_ARG, "seg_admm_unrolled_grads: NULL argument");
+  if (!st->un_bwd_pending) return fail(SHF_ERR_STATE, "no reverse sweep has been enqueued");
+  const Geo& g = st->g;
+  const int K = st->K, C = st->C, eta = g.eta;
+  const size_t P = st->P(), KP = P * K;
+  cudaStream_t s = st->stream;
+  const UnLayout U = un_layout(st, st->un_ck);
+  char* m = st->un_mem;
+  cudaError_t e = cudaSuccess;
   auto ok = [&](cudaError_t x) {
     if (e == cudaSuccess) e = x;
   };
@@ -1359,7 +1370,7 @@ int seg_admm_unrolled_bwd(seg_state* st, const float* dL_dw, float* dL_dcodebook
   ok(cudaMemcpyAsync(th.data(), m + U.tbar, sizeof(double) * eta, cudaMemcpyDeviceToHost, s));
   ok(cudaMemcpyAsync(cb.data(), m + U.cbout, sizeof(double) * K * C, cudaMemcpyDeviceToHost, s));
   ok(cudaStreamSynchronize(s));
-  if (e != cudaSuccess) return fail(SHF_ERR_CUDA, std::string("seg_admm_unrolled_bwd: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(SHF_ERR_CUDA, std::string("seg_admm_unrolled_grads: ") + cudaGetErrorString(e));
   std::vector<shf::FilterDesc> d(eta);
   shf::filter_descs(g.J, d.data());
   std::vector<double> lam(g.J + 1, 0.0);
@@ -1367,6 +1378,14 @@ int seg_admm_unrolled_bwd(seg_state* st, const float* dL_dw, float* dL_dcodebook
   for (int j = 0; j <= g.J; ++j) dL_dLambda[j] = static_cast<float>(lam[j]);
   for (int i = 0; i < K * C; ++i) dL_dcodebook[i] = static_cast<float>(cb[i]);
   return SHF_OK;
+}
+
+int seg_admm_unrolled_bwd(seg_state* st, const float* dL_dw, float* dL_dcodebook, float* dL_dLambda, float* dL_df,
+                          float* dL_ds) {
+  if (!st || !dL_dw || !dL_dcodebook || !dL_dLambda) return fail(SHF_ERR_ARG, "seg_admm_unrolled_bwd: NULL argument");
+  int rc = seg_admm_unrolled_bwd_enqueue(st, dL_dw);
+  if (rc) return rc;
+  return seg_admm_unrolled_grads(st, dL_dcodebook, dL_dLambda, dL_df, dL_ds);
 }
 
 int seg_admm_kernel_times(seg_state* st, float* ms, int* launches, int* nk) {

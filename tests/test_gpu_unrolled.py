@@ -121,3 +121,31 @@ def test_unrolled_workload_shape():
     for key in ("codebook", "Lambda", "f"):
         assert np.all(np.isfinite(g[key]))
     assert np.abs(g["codebook"]).max() > 0 and np.abs(g["Lambda"][1:]).max() > 0
+
+
+def test_enqueued_sweeps_on_concurrent_states_equal_the_synchronous_call():
+    torch = need_cuda()
+    from paper_1112_1805_gb300 import binding as B
+    from paper_1112_1805_gb300.api import FilterBank, ShearletSegmenter
+
+    probs = [_problem(40 + i, 64, 64, 3, 2) for i in range(3)]
+    fb = FilterBank(64, 64, 2)
+    segs = [ShearletSegmenter(fb, torch.tensor(p[0], device="cuda"), p[2].astype(np.float64), p[3].tolist(), 1.0)
+            for p in probs]
+    cots = [torch.full((3, 64, 64), 1e-3 * (i + 1), device="cuda") for i in range(3)]
+    ref = []
+    for sg, c in zip(segs, cots):
+        B.seg_admm_unrolled_fwd(sg.handle, 9, 4)
+        ref.append(B.seg_admm_unrolled_bwd(sg.handle, c.data_ptr(), 3, 1, 2))
+    for sg, c in zip(segs, cots):
+        B.seg_admm_unrolled_fwd(sg.handle, 9, 4)
+        B.seg_admm_unrolled_bwd_enqueue(sg.handle, c.data_ptr())
+    got = [B.seg_admm_unrolled_grads(sg.handle, 3, 1, 2) for sg in segs]
+    assert got == ref
+    with pytest.raises(B.ShearsegError):
+        fresh = ShearletSegmenter(fb, torch.tensor(probs[0][0], device="cuda"), probs[0][2].astype(np.float64),
+                                  probs[0][3].tolist(), 1.0)
+        B.seg_admm_unrolled_grads(fresh.handle, 3, 1, 2)
+    for sg in segs:
+        sg.close()
+    fb.close()

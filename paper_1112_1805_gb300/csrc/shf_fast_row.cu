@@ -1,27 +1,37 @@
 // Row transforms of the fast path: the v-step (soft shrinkage and b_v update
 // between the inverse and forward row transforms of every coefficient row)
 // and the u/w-step (Sec. 3).
+#include <algorithm>
+
 #include "shf_fast.h"
 
 namespace shf {
 namespace fast {
 namespace {
 
-// Row groups of T = L/8 threads inside CTAs of NTH <= 256 threads.  For
-// T <= 32 a warp holds 32/T groups and never splits one (lanes beyond them
-// idle); for T > 32 a group is ceil(T/32) whole warps (lanes beyond T idle).
-// An idle lane mirrors the last lane of its warp's last group (same row, same
-// shared-memory values) and writes nothing to global memory.
+// Row groups of T = L/8 threads inside CTAs of NTH threads.  When T divides
+// 32 a warp holds 32/T groups; when T is a multiple of 32 a group is T/32
+// whole warps (their barriers stay inside the group).  Otherwise (T = 3 2^a
+// or 5 2^a, a < 5) the groups are packed back to back over CTAs of a multiple
+// of lcm(T, 32) = 32 R threads, every lane busy, and the group barrier is the
+// CTA's.  Lanes that a layout leaves idle mirror a lane of a real group (same
+// shared-memory values) and write nothing to global memory.
 template <int L>
 struct RowGeo {
   static constexpr int T = L / 8;
+  static constexpr bool TILE = reg::tiles_warps(T);
+  static constexpr int LCM = 32 * reg::odd_part(T);        // lcm(T, 32) when !TILE
   static constexpr int GPW = T <= 32 ? 32 / T : 1;         // groups per warp
   static constexpr int WPG = T <= 32 ? 1 : (T + 31) / 32;  // warps per group
-  static constexpr int RPC = T <= 32 ? 8 * GPW : 8 / WPG;  // groups per CTA
-  static constexpr int NTH = T <= 32 ? 256 : RPC * WPG * 32;
+  static constexpr int NTH = TILE ? (T <= 32 ? 256 : (8 / WPG) * WPG * 32) : (256 / LCM > 0 ? 256 / LCM : 1) * LCM;
+  static constexpr int RPC = TILE ? (T <= 32 ? 8 * GPW : 8 / WPG) : NTH / T;  // groups per CTA
   __device__ static void locate(int& grp, int& tt, bool& act) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (T <= 32) {
+    if (!TILE) {
+      grp = threadIdx.x / T;
+      tt = threadIdx.x - grp * T;
+      act = true;
+    } else if (T <= 32) {
       const int g = lane / T;
       act = g < GPW;
       grp = warp * GPW + (act ? g : GPW - 1);
@@ -133,12 +143,22 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 
   const int niter = (rows + G - 1) / G;  // the same for every group: dead rows still take part in barriers
   const uint64_t pol = evict_first_policy();
   const size_t W = 2 * static_cast<size_t>(L);
+  // row r = fl H + row is tracked as (fl, row): one step of G rows adds
+  // (gq, gr) with a carry, so the loop needs no division
+  const int gq = G / H, gr = G - gq * H;
+  auto advance = [&](int& fl, int& row) {
+    fl += gq;
+    row += gr;
+    if (row >= H) {
+      row -= H;
+      ++fl;
+    }
+  };
 
-  // request row r's spectrum columns (its filter's column range only) and
-  // its b_v row (and codes) into the stage
-  auto request_x = [&](int r) {
-    if (r >= rows || !act) return;
-    const int fl = r / H, row = r - fl * H;
+  // request row (fl, row)'s spectrum columns (its filter's column range
+  // only) and its b_v row (and codes) into the stage
+  auto request_x = [&](int fl, int row) {
+    if (fl >= nf || !act) return;
     const int2 rg = ranges[f0 + fl];
     if (rg.x <= rg.y) {
       const int c0 = rg.x & ~7;
@@ -147,9 +167,8 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 
       for (int q = tt; q < (c1e - c0) / 2; q += T) cp_async16(sX + 2 * q, X + 2 * q, false, pol);
     }
   };
-  auto request_b = [&](int r) {
-    if (r >= rows || !act) return;
-    const int fl = r / H, row = r - fl * H;
+  auto request_b = [&](int fl, int row) {
+    if (fl >= nf || !act) return;
     const size_t rix = (static_cast<size_t>(label) * eta + f0 + fl) * H + row;
     const float2* B = reinterpret_cast<const float2*>(bv) + rix * L;
     for (int q = tt; q < L / 2; q += T) cp_async16(sB + 2 * q, B + 2 * q, true, pol);
@@ -161,17 +180,19 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 
 
   // b_v was last written by this kernel's previous launch for the label,
   // which has completed: it may be requested before the wait
-  request_b(gid);
+  int flc = gid / H, rowc = gid - flc * H;  // the group's current row
+  request_b(flc, rowc);
   load_table(tw, twW, L + 1);
   reg::build_pass_twiddles<L, 2>(pt, twW, threadIdx.x, blockDim.x);
   pdl_wait();
   pdl_trigger();
-  request_x(gid);
+  request_x(flc, rowc);
   __syncthreads();
   for (int it = 0; it < niter; ++it) {
-    const int r = gid + it * G;
-    const bool live = r < rows;
-    const int fl = live ? r / H : 0, row = live ? r - fl * H : 0, f = f0 + fl;
+    const bool live = flc < nf;
+    const int fl = live ? flc : 0, row = live ? rowc : 0, f = f0 + fl;
+    int fln = flc, rown = rowc;  // the group's next row
+    advance(fln, rown);
     const int2 rg = ranges[f];
     const bool any = live && rg.x <= rg.y;
     const int c0 = any ? (rg.x & ~7) : L + 1;
@@ -191,7 +212,7 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 
       v[k] = make_float2(s2.x - t.y, s2.y + t.x);
     }
     reg::group_sync<T>(bar);  // the spectrum stage is read: refill it with the group's next row
-    request_x(r + G);
+    request_x(fln, rown);
     if (SM::NBUF == 1)
       reg::row_fft1<L, +1>(v, tt, fb0, pt, bar);
     else
@@ -236,7 +257,7 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 
       for (int j = 0; j < T; ++j) s += sD[j];
       tpart[rix] = s;
     }
-    request_b(r + G);
+    request_b(fln, rown);
     if (SM::NBUF == 1)
       reg::row_fft1<L, -1>(v, tt, fb0, pt, bar);
     else
@@ -247,13 +268,28 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 
     for (int k = 0; k < 8; ++k) ub[reg::ridx(tt + k * T)] = v[k];
     reg::group_sync<T>(bar);
     // forward unpacking X[k] = 1/2 [(Z_k + conj Z_{L-k}) - i e^{-2 pi i k/W} (Z_k - conj Z_{L-k})]
-    for (int i = c0 + tt; act && i <= c1; i += T) {
-      const float2 a = ub[reg::ridx(i == L ? 0 : i)];
-      const float2 c = c_conj(ub[reg::ridx(i == 0 ? 0 : L - i)]);
-      const float2 s2 = c_add(a, c), d = c_sub(a, c);
-      const float2 t = c_mul(tw[i], d);
-      X[i] = make_float2(0.5f * (s2.x + t.y), 0.5f * (s2.y - t.x));
+    // on columns i = c0 + tt + k T <= c1 (at most 9 per thread: L + 1 columns);
+    // for T a multiple of 16 the padded indices are ridx(i0) + k (T + T/16)
+    // and ridx(L - i0) - k (T + T/16)
+    {
+      const int i0 = c0 + tt;
+      const int pa = reg::ridx(i0), pc = reg::ridx(L - i0);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        const int i = i0 + k * T;
+        if (act && i <= c1) {
+          const int ia = i == L ? 0 : (T % 16 == 0 ? pa + k * (T + T / 16) : reg::ridx(i));
+          const int ic = i == 0 ? 0 : (T % 16 == 0 ? pc - k * (T + T / 16) : reg::ridx(L - i));
+          const float2 a = ub[ia];
+          const float2 c = c_conj(ub[ic]);
+          const float2 s2 = c_add(a, c), d = c_sub(a, c);
+          const float2 t = c_mul(tw[i], d);
+          X[i] = make_float2(0.5f * (s2.x + t.y), 0.5f * (s2.y - t.x));
+        }
+      }
     }
+    flc = fln;
+    rowc = rown;
   }
   cp_async_commit_wait_all();  // no copy outlives the kernel
 }
@@ -288,25 +324,30 @@ __device__ __forceinline__ void simplex_project(float (&g)[KMAX], int K) {
 }
 
 // Geometry of the u/w-step kernel: a CTA takes NR rows and runs one row
-// group per (row, label) — K NR groups, laid out like RowGeo's groups (whole
-// warps for T > 32, 32/T per warp otherwise; groups past K NR idle).
+// group per (row, label) — K NR groups, laid out like RowGeo's groups (32/T
+// per warp, T/32 warps each, or packed back to back; group slots past K NR
+// idle).
 template <int L>
 struct UstepGeo {
   using RG = RowGeo<L>;
   static constexpr int T = RG::T;
   __host__ __device__ static int rows(int K) {
-    const int nr = T <= 32 ? (8 * RG::GPW) / K : 8 / (RG::WPG * K);
+    const int nr = !RG::TILE ? (256 / T) / K : (T <= 32 ? (8 * RG::GPW) / K : 8 / (RG::WPG * K));
     return nr < 1 ? 1 : nr;
   }
   __host__ __device__ static int groups(int K) { return K * rows(K); }
-  // warps of the CTA, and the group slots they hold
+  // threads of the CTA, and the group slots they hold
   __host__ __device__ static int warps(int K) {
-    return T <= 32 ? (groups(K) + RG::GPW - 1) / RG::GPW : groups(K) * RG::WPG;
+    return !RG::TILE ? (groups(K) * T + 31) / 32
+                     : (T <= 32 ? (groups(K) + RG::GPW - 1) / RG::GPW : groups(K) * RG::WPG);
   }
-  __host__ __device__ static int slots(int K) { return T <= 32 ? warps(K) * RG::GPW : groups(K); }
+  __host__ __device__ static int slots(int K) {
+    return !RG::TILE ? (32 * warps(K) + T - 1) / T : (T <= 32 ? warps(K) * RG::GPW : groups(K));
+  }
   // the largest CTA over K <= 8, and the CTAs per SM to ask the compiler for
-  static constexpr int MAXTH = T <= 32 ? 256 : 256 * RG::WPG;
-  static constexpr int MINB = T <= 32 ? 3 : 1;
+  static constexpr int MAXTH = !RG::TILE ? (8 * T > 256 ? (8 * T + 31) / 32 * 32 : 256)
+                                         : (T <= 32 ? 256 : 256 * RG::WPG);
+  static constexpr int MINB = MAXTH <= 256 ? 3 : 1;
 };
 
 // u-step (u = 1/2 [S^T(v - b_v) + (w - b_w) - gamma s], A^T A = 2I), w-step
@@ -467,8 +508,12 @@ template <int L>
 cudaError_t prepare_row_t() {
   cudaError_t e = allow_smem(k_wrow_vstep<L, 0>, vstep_smem<L, 0>());
   if (e == cudaSuccess) e = allow_smem(k_wrow_vstep<L, 1>, vstep_smem<L, 1>());
-  if (e == cudaSuccess) e = allow_smem(k_wrow_ustep<L, 4>, ustep_smem<L>(4));
-  if (e == cudaSuccess) e = allow_smem(k_wrow_ustep<L, 8>, ustep_smem<L>(8));
+  // the u/w-step's shared memory depends on K (rows per CTA): the largest over
+  // the K each instance serves (2..4 and 5..8)
+  size_t m4 = 0, m8 = 0;
+  for (int K = 2; K <= 8; ++K) (K <= 4 ? m4 : m8) = std::max(K <= 4 ? m4 : m8, ustep_smem<L>(K));
+  if (e == cudaSuccess) e = allow_smem(k_wrow_ustep<L, 4>, m4);
+  if (e == cudaSuccess) e = allow_smem(k_wrow_ustep<L, 8>, m8);
   return e;
 }
 

@@ -290,16 +290,24 @@ __host__ __device__ __forceinline__ void rrun_pass(float2 (&v)[8], int tt, const
   if (P < PS::NPASS - 1) rpass_store<N, R, Ns>(v, tt, out);
 }
 
+// Whether row groups of T threads tile warps exactly (T divides 32, or is a
+// multiple of 32).  Groups of other sizes (3 2^a or 5 2^a threads, a < 5)
+// are packed back to back over the CTA's threads.
+__host__ __device__ constexpr bool tiles_warps(int T) { return 32 % T == 0 || T % 32 == 0; }
+
 #ifdef __CUDACC__
 // Barrier of a row group: the warp when the group fits in it (every lane of
-// the warp takes part), otherwise the named barrier `id` over the group's
-// whole warps.
+// the warp takes part), the named barrier `id` over the group's warps when
+// it is whole warps, and the CTA's barrier when groups are packed across
+// warps (every group of the CTA then takes part).
 template <int T>
 __device__ __forceinline__ void group_sync(int id) {
-  if (T <= 32) {
+  if (!tiles_warps(T)) {
+    __syncthreads();
+  } else if (T <= 32) {
     __syncwarp();
   } else {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(((T + 31) / 32) * 32) : "memory");
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(T) : "memory");
   }
 }
 

@@ -54,8 +54,9 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--cpu-iters", type=int, default=2, help="oracle iterations in the CPU-baseline sample")
-    ap.add_argument("--workload", choices=["bezier512", "batch", "differentiable"], default="bezier512",
-                    help="bezier512 (default line), the uneven batch of 64 images, or the unrolled workload")
+    ap.add_argument("--workload", choices=["bezier512", "batch", "differentiable", "rgb2048"], default="bezier512",
+                    help="bezier512 (default line), the uneven batch of 64 images, the unrolled workload, or the "
+                         "2048 x 2048 RGB image (K = 8, J = 5; 20 iterations per step unless --iters is given)")
     ap.add_argument("--images", type=int, default=16, help="images of the differentiable workload")
     ap.add_argument("--no-differentiable", action="store_true",
                     help="skip the unrolled forward+reverse measurement the default line carries under 'differentiable'")
@@ -69,12 +70,14 @@ def parse_args():
 
 
 def workload_config(wl, extra=None):
+    bv_mb = 4 * wl.K * wl.eta * wl.H * wl.W / 1e6
     cfg = {
-        "workload": f"{wl.name}: {wl.H}x{wl.W} gray, K={wl.K}, J={wl.J} (eta={wl.eta}), {wl.iters} ADMM iterations, "
-                    "seeded closed-Bezier regions with oriented gratings (amplitude 0.15) and N(0, 0.05^2) noise",
-        "H": wl.H, "W": wl.W, "K": wl.K, "J": wl.J, "eta": wl.eta, "iters_per_step": wl.iters,
+        "workload": f"{wl.name}: {wl.H}x{wl.W} {'RGB' if wl.C == 3 else 'gray'}, K={wl.K}, J={wl.J} (eta={wl.eta}), "
+                    f"{wl.iters} ADMM iterations, seeded closed-Bezier regions with oriented gratings (amplitude "
+                    "0.15) and N(0, 0.05^2) noise",
+        "H": wl.H, "W": wl.W, "C": wl.C, "K": wl.K, "J": wl.J, "eta": wl.eta, "iters_per_step": wl.iters,
         "lambda": wl.lam, "gamma": wl.gamma, "Lambda": [round(float(x), 6) for x in wl.Lambda()],
-        "l2": "no flush: per-iteration working set (b_v 256 MB + coefficient spectra 257 MB) exceeds the 129 MB L2",
+        "l2": f"no flush: per-iteration working set (b_v {bv_mb:.0f} MB + coefficient spectra) exceeds the 129 MB L2",
         "parallelism": "replicas (one independent image per GPU)",
     }
     if extra:
@@ -247,14 +250,17 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    img, lab, wl = synth.make_workload_image(WORKLOAD)
-    if args.iters > 0:
-        import dataclasses
+    import dataclasses
 
+    name = "rgb2048" if args.workload == "rgb2048" else WORKLOAD
+    img, lab, wl = synth.make_workload_image(name)
+    if args.iters > 0:
         wl = dataclasses.replace(wl, iters=args.iters)
+    elif name == "rgb2048":
+        wl = dataclasses.replace(wl, iters=20)
     # the CPU-baseline leg runs first (rank 0, N = 1), before any GPU work
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and name == WORKLOAD:
         v, dt, cores = oracle_sample(wl, img, args.cpu_iters)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{wl.name} at full size, data term + {args.cpu_iters} ADMM iterations "
@@ -358,10 +364,10 @@ def run_ours(args):
         line["cpu_baseline"] = cpu
     seg.close()
     fb.close()
-    if rank == 0 and world == 1 and not args.no_batch:
+    if rank == 0 and world == 1 and not args.no_batch and name == WORKLOAD:
         # the batched form on the same GPU (the plain state is released first)
         line["batched"] = measure_batch(300, 1, 3, 30, not args.no_tune)
-    if rank == 0 and world == 1 and not args.no_differentiable:
+    if rank == 0 and world == 1 and not args.no_differentiable and name == WORKLOAD:
         line["differentiable"] = measure_differentiable(2, 1)
     if rank == 0:
         print(json.dumps(line))

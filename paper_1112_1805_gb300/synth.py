@@ -167,7 +167,7 @@ def bezier_texture_image(H: int, W: int, codebook, rng: np.random.Generator, sig
     gr = _grating(H, W, K, rng)
     tex = np.take_along_axis(gr, lab[None], axis=0)[0]
     img = cb[lab].transpose(2, 0, 1) + tex[None] + sigma * rng.standard_normal((C, H, W))
-    return img, lab
+    return np.ascontiguousarray(img), lab
 
 
 def rgb_texture_image(H: int, W: int, codebook, rng: np.random.Generator, sigma: float = 0.05):

@@ -280,7 +280,9 @@ int seg_admm_unrolled_grads(seg_state* st, float* dL_dcodebook, float* dL_dLambd
  * graph).  ms[i] gets the milliseconds of kind i summed over its launches,
  * launches[i] (may be NULL) their number; both need room for 8 entries.  *nk
  * (may be NULL) gets the number of kinds.  Waits for that iteration to finish.
- * Errors: SHF_ERR_STATE before the first iteration. */
+ * Errors: SHF_ERR_STATE before the first iteration, and when an iteration has
+ * more than 8192 launches (the timing events are created for the current
+ * plan when an iteration is first run on the state's own stream). */
 int seg_admm_kernel_times(seg_state* st, float* ms, int* launches, int* nk);
 
 /* Name of kernel kind i of seg_admm_kernel_times ("" when out of range). */

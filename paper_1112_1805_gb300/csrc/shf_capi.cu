@@ -101,9 +101,10 @@ struct seg_state {
   float2* uhat = nullptr;     // fast path: 2-D spectra of u [K][H][Wh]
   // Events recorded before every launch of an iteration (graph event nodes),
   // with the kind of the launch that follows each.
-  static constexpr int kMaxMarks = 512;
-  cudaEvent_t ev[kMaxMarks] = {};
-  int kinds[kMaxMarks] = {};
+  // created when a timed iteration is first captured, as many as it has marks
+  static constexpr int kMaxMarks = 8192;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> kinds;
   int nmarks = 0;
   bool marks_ok = true;
   // unrolled mode (reverse-mode differentiation): generic-path scratch and
@@ -323,18 +324,50 @@ int restart(seg_state* st, const float* codebook) {
   return SHF_OK;
 }
 
+// Launches of one iteration, plus the closing mark.
+int marks_needed(const seg_state* st) {
+  if (!st->fast) return 8;
+  int n = 4;  // u/w-step, column forward, reduction, end
+  for (size_t w = 0; w < st->plan.wave_f0.size(); ++w) n += 3 * st->K;
+  return n;
+}
+
+// Creates the timing events an iteration of the current plan needs (at most
+// kMaxMarks); a failure leaves the timing disabled.
+void ensure_marks(seg_state* st) {
+  const size_t need = static_cast<size_t>(std::min(marks_needed(st), static_cast<int>(seg_state::kMaxMarks)));
+  while (st->ev.size() < need) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      break;
+    }
+    st->ev.push_back(e);
+  }
+  st->kinds.resize(st->ev.size());
+}
+
 // Records the event of the next mark; during stream capture it becomes an
 // event-record node of the graph (cudaEventRecordExternal), so that each
-// replay timestamps it.
+// replay timestamps it.  A failed record only disables the timing (its error
+// is cleared, not left for a later call to report).
 void mark_launch(void* ctx, int kind) {
   auto* st = static_cast<seg_state*>(ctx);
-  if (st->nmarks >= seg_state::kMaxMarks) {
+  if (st->nmarks >= static_cast<int>(st->ev.size())) {
     st->marks_ok = false;
     return;
   }
   const int i = st->nmarks++;
   st->kinds[i] = kind;
-  if (cudaEventRecordWithFlags(st->ev[i], st->stream, cudaEventRecordExternal) != cudaSuccess) st->marks_ok = false;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st->stream, &cs);
+  if (e == cudaSuccess)
+    e = cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(st->ev[i], st->stream, cudaEventRecordExternal)
+                                            : cudaEventRecord(st->ev[i], st->stream);
+  if (e != cudaSuccess) {
+    st->marks_ok = false;
+    cudaGetLastError();
+  }
 }
 
 // One ADMM iteration; `timed`: with an event recorded before every launch and
@@ -408,16 +441,15 @@ cudaGraphExec_t capture_iteration(seg_state* st, bool timed) {
 
 // Captures one iteration into two graphs (plain, and with the timing events)
 // when the stream can be captured (not the legacy default stream); otherwise
-// iterations are launched directly.
+// iterations are launched directly.  An iteration with more launches than
+// timing marks keeps only the plain graph (seg_admm_kernel_times then reports
+// the timing as unavailable).
 void try_capture(seg_state* st) {
   st->graph_tried = true;
+  ensure_marks(st);
   if (st->stream == nullptr) return;
   st->exec = capture_iteration(st, false);
   if (st->exec) st->exec_timed = capture_iteration(st, true);
-  if (st->exec && !st->exec_timed) {
-    cudaGraphExecDestroy(st->exec);
-    st->exec = nullptr;
-  }
 }
 
 void drop_graphs(seg_state* st) {
@@ -467,7 +499,7 @@ int install_fast_plan(seg_state* st, int wave_mib, int col_ctas_per_sm) {
   shf::build_fast_plan(g, st->ranges_host.data(), &plan, &h_items, &h_cta_begin, &h_tile_begin, &h_tile_slots);
   const size_t Phs = static_cast<size_t>(g.H) * shf::fast_pitch(g);
   const size_t y_elems = Phs * static_cast<size_t>(shf::fast_wave(g, wave_mib));
-  const size_t partial_elems = static_cast<size_t>(st->K) * std::max(plan.nslots, 1) * g.H * shf::reg_batch();
+  const size_t partial_elems = static_cast<size_t>(st->K) * std::max(plan.nslots, 1) * g.H * shf::fast_tile(g);
   float2 *Y = nullptr, *partial = nullptr;
   shf::WorkItem* items = nullptr;
   int *cta_begin = nullptr, *tile_begin = nullptr, *tile_slots = nullptr;
@@ -659,13 +691,6 @@ int seg_admm_init(const shf_bank* b, const float* f, int C, const float* codeboo
       return fail(SHF_ERR_CUDA, std::string("seg_admm_init: ") + cudaGetErrorString(e));
     }
   }
-  for (cudaEvent_t& ev : st->ev) {
-    cudaError_t e = cudaEventCreate(&ev);
-    if (e != cudaSuccess) {
-      free_state(st);
-      return fail(SHF_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
-    }
-  }
   const int l1_blocks = ((g.H + g.RB - 1) / g.RB) * K * g.eta;
   st->red_len = 2 + 512 + l1_blocks;
   int rc;
@@ -726,7 +751,7 @@ int seg_admm_step(seg_state* st, int n) {
   for (int i = 0; i < n; ++i) {
     const bool timed = i == n - 1;
     if (st->exec) {
-      SHF_CK(cudaGraphLaunch(timed ? st->exec_timed : st->exec, st->stream));
+      SHF_CK(cudaGraphLaunch(timed && st->exec_timed ? st->exec_timed : st->exec, st->stream));
     } else {
       SHF_CK(enqueue_iteration(st, timed));
     }

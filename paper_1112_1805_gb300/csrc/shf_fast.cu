@@ -20,11 +20,11 @@
 
 namespace shf {
 
-using reg::kB;
-
 int fast_pitch(const Geo& g) { return (g.Wh + 7) & ~7; }
 
-bool fast_path_ok(const Geo& g) { return reg::supported(g.H) && reg::supported(g.L); }
+bool fast_path_ok(const Geo& g) { return reg::supported_col(g.H) && reg::supported(g.L); }
+
+int fast_tile(const Geo& g) { return reg::col_batch(g.H); }
 
 bool fast_ustep_ok(const Geo& g, int K) {
   if (!fast_path_ok(g) || K > 8) return false;
@@ -78,7 +78,7 @@ int fast_row_ctas(const Geo& g) { return fast::row_ctas_per_sm(g.L) * sm_count()
 
 void build_fast_plan(const Geo& g, const int2* ranges, FastPlan* plan, std::vector<WorkItem>* items,
                      std::vector<int>* cta_begin, std::vector<int>* tile_begin, std::vector<int>* tile_slots) {
-  const int ntiles = (g.Wh + kB - 1) / kB;
+  const int tw = fast_tile(g), ntiles = (g.Wh + tw - 1) / tw;
   const int wave = fast_wave(g, plan->wave_mib);
   const int ctas = plan->col_ctas > 0 ? plan->col_ctas : 1;
   items->clear();
@@ -97,7 +97,7 @@ void build_fast_plan(const Geo& g, const int2* ranges, FastPlan* plan, std::vect
     for (int t = 0; t < ntiles; ++t)
       for (int fl = 0; fl < nf; ++fl) {
         const int2 r = ranges[f0 + fl];
-        if (r.x <= r.y && t >= (r.x >> 3) && t <= (r.y >> 3)) items->push_back(WorkItem{t, fl, 0, 0});
+        if (r.x <= r.y && t >= r.x / tw && t <= r.y / tw) items->push_back(WorkItem{t, fl, 0, 0});
       }
     const long n = static_cast<long>(items->size() - first);
     const int G = static_cast<int>(std::min<long>(ctas, n));

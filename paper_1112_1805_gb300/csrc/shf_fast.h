@@ -12,9 +12,11 @@
 #include "shf_fft_reg.cuh"
 #include "shf_internal.h"
 
-// The supported transform lengths, for dispatch over template instances.
+// The supported transform lengths, for dispatch over template instances:
+// rows (half widths L) up to 1024, columns (heights H) up to 2048.
 #define SHF_FAST_SIZES(X) \
   X(8) X(16) X(24) X(32) X(40) X(48) X(64) X(80) X(96) X(128) X(160) X(192) X(256) X(320) X(384) X(512) X(640) X(768) X(1024)
+#define SHF_COL_SIZES(X) SHF_FAST_SIZES(X) X(1280) X(1536) X(2048)
 
 namespace shf {
 namespace fast {

@@ -7,8 +7,13 @@ namespace shf {
 namespace fast {
 namespace {
 
-using reg::kB;
-using reg::kS;
+// Columns per CTA batch (8, or 4 for heights above 1024) and the CTA's
+// threads: 8 values per thread, H/8 threads per column.
+template <int H>
+struct ColGeo {
+  static constexpr int KB = reg::col_batch(H);
+  static constexpr int NT = H / 8 * KB;
+};
 using reg::sidx;
 
 // Per-pass twiddle table of a length-N transform, built by the whole CTA.
@@ -18,32 +23,34 @@ __device__ __forceinline__ void load_pass_table(float2* pt, const float2* __rest
 }
 
 // ---------------------------------------------------------------------------
-// Column kernels: a CTA of H threads owns 8 consecutive half-spectrum columns
-// (thread (b, tt) holds rows tt + k H/8 of column 8*blockIdx.x + b).  The
+// Column kernels: a CTA of H KB/8 threads owns KB consecutive half-spectrum
+// columns, KB = 8 (4 for H > 1024; thread (b, tt) holds rows tt + k H/8 of
+// column KB*tile + b).  The
 // internal spectra (uhat, Y, partial) use the row pitch Whp = Wh rounded up to
 // 8, so that each row segment of a tile is one aligned 64-byte piece; Ur and T,
 // shared with the generic kernels, use the pitch Wh.  Global operands of the
 // next filter are loaded while the current transform runs.
 // ---------------------------------------------------------------------------
 
-// Resident CTAs of H threads (whole warps) to ask for: 32 warps per SM (64
+// Resident CTAs of NT threads (whole warps) to ask for: 32 warps per SM (64
 // registers per thread) for powers of two; for H = 3 2^a or 5 2^a, whose
 // radix-R pass holds more values, about 80 registers per thread.
-constexpr int col_min_blocks(int H) {
+constexpr int col_min_blocks(int H, int NT) {
   return reg::odd_part(H) == 1
-             ? (32 / ((H + 31) / 32) > 32 ? 32 : (32 / ((H + 31) / 32) > 0 ? 32 / ((H + 31) / 32) : 1))
-             : ((65536 / 80) / (32 * ((H + 31) / 32)) > 0 ? (65536 / 80) / (32 * ((H + 31) / 32)) : 1);
+             ? (32 / ((NT + 31) / 32) > 32 ? 32 : (32 / ((NT + 31) / 32) > 0 ? 32 / ((NT + 31) / 32) : 1))
+             : ((65536 / 80) / (32 * ((NT + 31) / 32)) > 0 ? (65536 / 80) / (32 * ((NT + 31) / 32)) : 1);
 }
 
 template <int H>
-__global__ void __launch_bounds__(H) k_fcol_fwd(const float2* __restrict__ in, float2* __restrict__ out, int Wh,
+__global__ void __launch_bounds__(ColGeo<H>::NT) k_fcol_fwd(const float2* __restrict__ in, float2* __restrict__ out, int Wh,
                                                 int Whp, const float2* __restrict__ twH) {
   extern __shared__ float2 sm[];
   float2* tw = sm;  // per-pass twiddles
   float2* b0 = sm + reg::Passes<H>::TWSIZE;
-  float2* b1 = b0 + reg::batch_rows(H) * kS;
-  const int b = threadIdx.x & 7, tt = threadIdx.x >> 3;
-  const int col = blockIdx.x * kB + b;
+  float2* b1 = b0 + reg::batch_rows(H) * ColGeo<H>::KB;
+  constexpr int KB = ColGeo<H>::KB;
+  const int b = threadIdx.x % KB, tt = threadIdx.x / KB;
+  const int col = blockIdx.x * KB + b;
   const bool ok = col < Wh;
   const float2* src = in + static_cast<size_t>(H) * Wh * blockIdx.y + col;
   load_pass_table<H, 1>(tw, twH);
@@ -53,7 +60,7 @@ __global__ void __launch_bounds__(H) k_fcol_fwd(const float2* __restrict__ in, f
 #pragma unroll
   for (int k = 0; k < 8; ++k) v[k] = ok ? src[static_cast<size_t>(tt + k * (H / 8)) * Wh] : make_float2(0.f, 0.f);
   __syncthreads();
-  reg::fft<H, -1>(v, tt, b, b0, b1, tw);
+  reg::fft<H, -1, KB>(v, tt, b, b0, b1, tw);
   if (ok) {
     float2* dst = out + static_cast<size_t>(H) * Whp * blockIdx.y + col;
 #pragma unroll
@@ -81,20 +88,21 @@ __device__ __forceinline__ void load_tile8(float2 (&v)[8], const float2* __restr
 // (and, at a tile change, the next spectrum tile) is requested while the
 // current transform runs.
 template <int H>
-__global__ void __launch_bounds__(H, col_min_blocks(H))
+__global__ void __launch_bounds__(ColGeo<H>::NT, col_min_blocks(H, ColGeo<H>::NT))
     k_fcol_fan(const float2* __restrict__ uhat, const float* __restrict__ bank, const WorkItem* __restrict__ items,
                const int* __restrict__ cta_begin, float2* __restrict__ Y, int Wh, int Whp, int label, int f0,
                const float2* __restrict__ twH) {
   extern __shared__ float2 sm[];
   float2* tw = sm;  // per-pass twiddles
   float2* b0 = sm + reg::Passes<H>::TWSIZE;
-  float2* b1 = b0 + reg::batch_rows(H) * kS;
+  float2* b1 = b0 + reg::batch_rows(H) * ColGeo<H>::KB;
   const int ib = cta_begin[blockIdx.x], ie = cta_begin[blockIdx.x + 1];
   if (ib >= ie) return;
-  const int b = threadIdx.x & 7, tt = threadIdx.x >> 3;
+  constexpr int KB = ColGeo<H>::KB;
+  const int b = threadIdx.x % KB, tt = threadIdx.x / KB;
   const size_t Pb = static_cast<size_t>(H) * Wh, Pp = static_cast<size_t>(H) * Whp;
   WorkItem it = items[ib];
-  int col = it.tile * kB + b;
+  int col = it.tile * KB + b;
   bool ok = col < Wh;
   float2 u[8];
   float w[8];
@@ -112,13 +120,13 @@ __global__ void __launch_bounds__(H, col_min_blocks(H))
     const bool cok = ok;
     if (i + 1 < ie) {
       const WorkItem nx = items[i + 1];
-      col = nx.tile * kB + b;
+      col = nx.tile * KB + b;
       ok = col < Wh;
       load_bank8<H>(w, bank + Pb * (f0 + nx.filter), Wh, tt, col, ok);
       if (nx.tile != it.tile) load_tile8<H>(u, uhat + Pp * label, Whp, tt, col, ok);
       it = nx;
     }
-    reg::fft<H, +1>(v, tt, b, b0, b1, tw);
+    reg::fft<H, +1, KB>(v, tt, b, b0, b1, tw);
     if (cok) {
       float2* dst = Y + Pp * fl + ccol;
 #pragma unroll
@@ -131,20 +139,21 @@ __global__ void __launch_bounds__(H, col_min_blocks(H))
 // tile of W_f * column-forward(Y_f), stored compactly as [H][8]; the next
 // item's coefficient tile is requested while the current transform runs.
 template <int H>
-__global__ void __launch_bounds__(H, col_min_blocks(H))
+__global__ void __launch_bounds__(ColGeo<H>::NT, col_min_blocks(H, ColGeo<H>::NT))
     k_fcol_gather(const float2* __restrict__ Y, const float* __restrict__ bank, const WorkItem* __restrict__ items,
                   const int* __restrict__ cta_begin, float2* __restrict__ partial, int Wh, int Whp, int nslots,
                   int label, int f0, const float2* __restrict__ twH) {
   extern __shared__ float2 sm[];
   float2* tw = sm;  // per-pass twiddles
   float2* b0 = sm + reg::Passes<H>::TWSIZE;
-  float2* b1 = b0 + reg::batch_rows(H) * kS;
+  float2* b1 = b0 + reg::batch_rows(H) * ColGeo<H>::KB;
   const int ib = cta_begin[blockIdx.x], ie = cta_begin[blockIdx.x + 1];
   if (ib >= ie) return;
-  const int b = threadIdx.x & 7, tt = threadIdx.x >> 3;
+  constexpr int KB = ColGeo<H>::KB;
+  const int b = threadIdx.x % KB, tt = threadIdx.x / KB;
   const size_t Pb = static_cast<size_t>(H) * Wh, Pp = static_cast<size_t>(H) * Whp;
   WorkItem it = items[ib];
-  int col = it.tile * kB + b;
+  int col = it.tile * KB + b;
   bool ok = col < Wh;
   float2 acc[8], y[8];
   float w[8];
@@ -165,21 +174,21 @@ __global__ void __launch_bounds__(H, col_min_blocks(H))
     bool nok = ok;
     if (i + 1 < ie) {
       nx = items[i + 1];
-      ncol = nx.tile * kB + b;
+      ncol = nx.tile * KB + b;
       nok = ncol < Wh;
       load_tile8<H>(y, Y + Pp * nx.filter, Whp, tt, ncol, nok);
     }
-    reg::fft<H, -1>(v, tt, b, b0, b1, tw);
+    reg::fft<H, -1, KB>(v, tt, b, b0, b1, tw);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       acc[k].x = fmaf(w[k], v[k].x, acc[k].x);
       acc[k].y = fmaf(w[k], v[k].y, acc[k].y);
     }
     if (i + 1 == ie || nx.slot != it.slot) {
-      float2* dst = partial + (static_cast<size_t>(label) * nslots + it.slot) * H * kB + b;
+      float2* dst = partial + (static_cast<size_t>(label) * nslots + it.slot) * H * KB + b;
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        dst[static_cast<size_t>(tt + k * (H / 8)) * kB] = acc[k];
+        dst[static_cast<size_t>(tt + k * (H / 8)) * KB] = acc[k];
         acc[k] = make_float2(0.f, 0.f);
       }
     }
@@ -192,17 +201,18 @@ __global__ void __launch_bounds__(H, col_min_blocks(H))
 // T[label] on one tile = column-inverse of the sum of the tile's partial
 // slots, in the fixed slot order (filter order).
 template <int H>
-__global__ void __launch_bounds__(H) k_fcol_reduce_inv(const float2* __restrict__ partial,
+__global__ void __launch_bounds__(ColGeo<H>::NT) k_fcol_reduce_inv(const float2* __restrict__ partial,
                                                        const int* __restrict__ tile_begin,
                                                        const int* __restrict__ tile_slots, float2* __restrict__ T,
                                                        int Wh, int nslots, const float2* __restrict__ twH) {
   extern __shared__ float2 sm[];
   float2* tw = sm;  // per-pass twiddles
   float2* b0 = sm + reg::Passes<H>::TWSIZE;
-  float2* b1 = b0 + reg::batch_rows(H) * kS;
-  const int b = threadIdx.x & 7, tt = threadIdx.x >> 3;
+  float2* b1 = b0 + reg::batch_rows(H) * ColGeo<H>::KB;
+  constexpr int KB = ColGeo<H>::KB;
+  const int b = threadIdx.x % KB, tt = threadIdx.x / KB;
   const int tile = blockIdx.x, label = blockIdx.y;
-  const int col = tile * kB + b;
+  const int col = tile * KB + b;
   const bool ok = col < Wh;
   float2 v[8];
 #pragma unroll
@@ -212,12 +222,12 @@ __global__ void __launch_bounds__(H) k_fcol_reduce_inv(const float2* __restrict_
   pdl_trigger();
   const int s0 = tile_begin[tile], s1 = tile_begin[tile + 1];
   for (int si = s0; si < s1; ++si) {
-    const float2* src = partial + (static_cast<size_t>(label) * nslots + tile_slots[si]) * H * kB + b;
+    const float2* src = partial + (static_cast<size_t>(label) * nslots + tile_slots[si]) * H * KB + b;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = c_add(v[k], src[static_cast<size_t>(tt + k * (H / 8)) * kB]);
+    for (int k = 0; k < 8; ++k) v[k] = c_add(v[k], src[static_cast<size_t>(tt + k * (H / 8)) * KB]);
   }
   __syncthreads();
-  reg::fft<H, +1>(v, tt, b, b0, b1, tw);
+  reg::fft<H, +1, KB>(v, tt, b, b0, b1, tw);
   if (ok) {
     float2* dst = T + static_cast<size_t>(H) * Wh * label + col;
 #pragma unroll
@@ -227,7 +237,7 @@ __global__ void __launch_bounds__(H) k_fcol_reduce_inv(const float2* __restrict_
 
 template <int N>
 size_t col_smem() {
-  return sizeof(float2) * (reg::Passes<N>::TWSIZE + 2 * reg::batch_rows(N) * kS);
+  return sizeof(float2) * (reg::Passes<N>::TWSIZE + 2 * reg::batch_rows(N) * ColGeo<N>::KB);
 }
 
 template <int H>
@@ -246,7 +256,7 @@ cudaError_t prepare_col_kernels() {
 #define SHF_PREP(N) \
   if (e == cudaSuccess) e = prepare_col_t<N>();
   cudaError_t e = cudaSuccess;
-  SHF_FAST_SIZES(SHF_PREP)
+  SHF_COL_SIZES(SHF_PREP)
 #undef SHF_PREP
   return e;
 }
@@ -257,9 +267,9 @@ int col_ctas_per_sm(int H) {
   switch (H) {
 #define SHF_OCC(N)                                                                                \
   case N:                                                                                         \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_fcol_gather<N>, N, col_smem<N>()); \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_fcol_gather<N>, ColGeo<N>::NT, col_smem<N>()); \
     break;
-    SHF_FAST_SIZES(SHF_OCC)
+    SHF_COL_SIZES(SHF_OCC)
 #undef SHF_OCC
     default: break;
   }
@@ -267,12 +277,12 @@ int col_ctas_per_sm(int H) {
 }
 
 cudaError_t col_fwd(const Geo& g, const float2* Ur, float2* uhat, int K, int Whp, cudaStream_t st) {
-  const int ntiles = (g.Wh + kB - 1) / kB;
+  const int tw = reg::col_batch(g.H), ntiles = (g.Wh + tw - 1) / tw;
   switch (g.H) {
 #define SHF_CASE(N) \
   case N:           \
-    return launch_pdl(k_fcol_fwd<N>, dim3(ntiles, K), dim3(N), col_smem<N>(), st, Ur, uhat, g.Wh, Whp, g.twH);
-    SHF_FAST_SIZES(SHF_CASE)
+    return launch_pdl(k_fcol_fwd<N>, dim3(ntiles, K), dim3(ColGeo<N>::NT), col_smem<N>(), st, Ur, uhat, g.Wh, Whp, g.twH);
+    SHF_COL_SIZES(SHF_CASE)
 #undef SHF_CASE
     default: return cudaErrorInvalidValue;
   }
@@ -283,9 +293,9 @@ cudaError_t col_fan(const Geo& g, int nc, const float2* uhat, const WorkItem* it
   switch (g.H) {
 #define SHF_CASE(N)                                                                                              \
   case N:                                                                                                        \
-    return launch_pdl(k_fcol_fan<N>, dim3(nc), dim3(N), col_smem<N>(), st, uhat, g.bank, items, cta_begin, Y, \
+    return launch_pdl(k_fcol_fan<N>, dim3(nc), dim3(ColGeo<N>::NT), col_smem<N>(), st, uhat, g.bank, items, cta_begin, Y, \
                       g.Wh, Whp, label, f0, g.twH);
-    SHF_FAST_SIZES(SHF_CASE)
+    SHF_COL_SIZES(SHF_CASE)
 #undef SHF_CASE
     default: return cudaErrorInvalidValue;
   }
@@ -296,9 +306,9 @@ cudaError_t col_gather(const Geo& g, int nc, const float2* Y, const WorkItem* it
   switch (g.H) {
 #define SHF_CASE(N)                                                                                           \
   case N:                                                                                                     \
-    return launch_pdl(k_fcol_gather<N>, dim3(nc), dim3(N), col_smem<N>(), st, Y, g.bank, items, cta_begin, \
+    return launch_pdl(k_fcol_gather<N>, dim3(nc), dim3(ColGeo<N>::NT), col_smem<N>(), st, Y, g.bank, items, cta_begin, \
                       partial, g.Wh, Whp, nslots, label, f0, g.twH);
-    SHF_FAST_SIZES(SHF_CASE)
+    SHF_COL_SIZES(SHF_CASE)
 #undef SHF_CASE
     default: return cudaErrorInvalidValue;
   }
@@ -306,13 +316,13 @@ cudaError_t col_gather(const Geo& g, int nc, const float2* Y, const WorkItem* it
 
 cudaError_t col_reduce(const Geo& g, const float2* partial, const int* tile_begin, const int* tile_slots, float2* T,
                        int K, int nslots, cudaStream_t st) {
-  const int ntiles = (g.Wh + kB - 1) / kB;
+  const int tw = reg::col_batch(g.H), ntiles = (g.Wh + tw - 1) / tw;
   switch (g.H) {
 #define SHF_CASE(N)                                                                                          \
   case N:                                                                                                    \
-    return launch_pdl(k_fcol_reduce_inv<N>, dim3(ntiles, K), dim3(N), col_smem<N>(), st, partial, tile_begin, \
+    return launch_pdl(k_fcol_reduce_inv<N>, dim3(ntiles, K), dim3(ColGeo<N>::NT), col_smem<N>(), st, partial, tile_begin, \
                       tile_slots, T, g.Wh, nslots, g.twH);
-    SHF_FAST_SIZES(SHF_CASE)
+    SHF_COL_SIZES(SHF_CASE)
 #undef SHF_CASE
     default: return cudaErrorInvalidValue;
   }

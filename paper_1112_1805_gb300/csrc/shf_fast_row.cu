@@ -112,7 +112,8 @@ __device__ __forceinline__ signed char clip_code(float g, float t) {
 // resident CTAs, each row group takes rows gid, gid + G, ... (G groups in
 // all).  While a group transforms its row, the next row's spectrum columns
 // (only the filter's column tiles [c0, c1]) and b_v row are copied into the
-// group's stage; the twiddle tables are built once per CTA.
+// group's stage; the twiddle tables are built once per CTA.  Column ranges
+// are widened to the column kernels' tiles (8 columns, or 4 for H > 1024).
 // Four CTAs of 256 threads per SM (64 registers) for powers of two; three for
 // L = 3 2^a or 5 2^a, whose radix-R pass holds more values.
 template <int L, int MODE>
@@ -143,6 +144,9 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 
   const int niter = (rows + G - 1) / G;  // the same for every group: dead rows still take part in barriers
   const uint64_t pol = evict_first_policy();
   const size_t W = 2 * static_cast<size_t>(L);
+  // the column kernels write whole tiles of reg::col_batch(H) columns: the
+  // rows carry exactly those tiles
+  const int cmask = reg::col_batch(H) - 1;
   // row r = fl H + row is tracked as (fl, row): one step of G rows adds
   // (gq, gr) with a carry, so the loop needs no division
   const int gq = G / H, gr = G - gq * H;
@@ -161,8 +165,8 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 
     if (fl >= nf || !act) return;
     const int2 rg = ranges[f0 + fl];
     if (rg.x <= rg.y) {
-      const int c0 = rg.x & ~7;
-      const int c1e = min(Whp, (rg.y | 7) + 1);
+      const int c0 = rg.x & ~cmask;
+      const int c1e = min(Whp, (rg.y | cmask) + 1);
       const float2* X = Y + (static_cast<size_t>(fl) * H + row) * Whp + c0;
       for (int q = tt; q < (c1e - c0) / 2; q += T) cp_async16(sX + 2 * q, X + 2 * q, false, pol);
     }
@@ -195,8 +199,8 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 
     advance(fln, rown);
     const int2 rg = ranges[f];
     const bool any = live && rg.x <= rg.y;
-    const int c0 = any ? (rg.x & ~7) : L + 1;
-    const int c1 = any ? min(L, (rg.y | 7)) : -1;
+    const int c0 = any ? (rg.x & ~cmask) : L + 1;
+    const int c1 = any ? min(L, (rg.y | cmask)) : -1;
     const float th = thr[f];
     const size_t rix = (static_cast<size_t>(label) * eta + f) * H + row;
     cp_async_commit_wait_all();

@@ -1,9 +1,9 @@
 // Register-resident FFTs for lengths N = R 2^a with R in {1, 3, 5},
-// 2^a >= 8 and N <= 1024 (sm_103a fast path).
+// 2^a >= 8 and N <= 2048 (sm_103a fast path).
 //
-// A CTA transforms a batch of kB = 8 sequences of length N with N threads:
-// thread (b = t % 8, tt = t / 8) holds v[k] = x_b[tt + k N/8], k = 0..7
-// ("stride layout").  Stockham passes: for R > 1 a first pass of radix R,
+// A CTA transforms a batch of KB (8, or 4 for N > 1024) sequences of length N
+// with N KB / 8 threads: thread (b = t % KB, tt = t / KB) holds
+// v[k] = x_b[tt + k N/8], k = 0..7 ("stride layout").  Stockham passes: for R > 1 a first pass of radix R,
 // then radix-8 passes (a radix-4 or radix-2 pass last when log2(N/R) is not a
 // multiple of 3).  A radix-8/4/2 pass does its butterflies in registers;
 // between passes the values go through shared memory at their Stockham
@@ -32,15 +32,22 @@ constexpr int kS = kB;  // float2 per shared-memory row
 __host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
 // Odd factor R of a supported length N = R 2^a.
 __host__ __device__ constexpr int odd_part(int n) { return n % 3 == 0 ? 3 : (n % 5 == 0 ? 5 : 1); }
-// Lengths of the register FFTs: R 2^a with R in {1, 3, 5}, 2^a >= 8, at most 1024.
-__host__ __device__ constexpr bool supported(int n) {
-  return n >= 8 && n <= 1024 && (n / odd_part(n)) % 8 == 0 &&
-         ((n / odd_part(n)) & (n / odd_part(n) - 1)) == 0;
+// Lengths of the register FFTs: R 2^a with R in {1, 3, 5}, 2^a >= 8, at most
+// 1024 (rows and columns) or 2048 (columns, in batches of 4).
+__host__ __device__ constexpr bool supported_upto(int n, int nmax) {
+  return n >= 8 && n <= nmax && (n / odd_part(n)) % 8 == 0 && ((n / odd_part(n)) & (n / odd_part(n) - 1)) == 0;
 }
+__host__ __device__ constexpr bool supported(int n) { return supported_upto(n, 1024); }
+__host__ __device__ constexpr bool supported_col(int n) { return supported_upto(n, 2048); }
+// Columns per batch of the column transforms of height H.
+__host__ __device__ constexpr int col_batch(int H) { return H > 1024 ? 4 : 8; }
 
 // Padded row of index i in the batch layout, and the element offset.
 __host__ __device__ constexpr int brow(int i) { return i + (i >> 3); }
-__host__ __device__ __forceinline__ int sidx(int i, int b) { return brow(i) * kS + b; }
+template <int KB = kB>
+__host__ __device__ __forceinline__ int sidx(int i, int b) {
+  return brow(i) * KB + b;
+}
 // Rows a batch buffer of length N needs (index N included, for staging).
 __host__ __device__ constexpr int batch_rows(int N) { return brow(N) + 1; }
 
@@ -145,7 +152,7 @@ __host__ __device__ __forceinline__ void pass_bfly(float2 (&v)[8], int tt, const
 // Writes the outputs of a (non-final) pass to their Stockham positions
 // o + q Ns.  For Ns = 1 and for Ns a multiple of 8, brow(o + q Ns) =
 // brow(o) + brow(q Ns): one base per butterfly plus constant offsets.
-template <int N, int R, int Ns>
+template <int N, int R, int Ns, int KB>
 __host__ __device__ __forceinline__ void pass_store(const float2 (&v)[8], int tt, int b, float2* out) {
   constexpr int M = 8 / R;
 #pragma unroll
@@ -153,38 +160,38 @@ __host__ __device__ __forceinline__ void pass_store(const float2 (&v)[8], int tt
     const int j = tt + m * (N / 8);
     const int o = (j / Ns) * Ns * R + (j % Ns);
     if (Ns == 1 || Ns % 8 == 0) {
-      float2* p = out + brow(o) * kS + b;
+      float2* p = out + brow(o) * KB + b;
 #pragma unroll
-      for (int q = 0; q < R; ++q) p[brow(q * Ns) * kS] = v[m + q * M];
+      for (int q = 0; q < R; ++q) p[brow(q * Ns) * KB] = v[m + q * M];
     } else {
 #pragma unroll
-      for (int q = 0; q < R; ++q) out[sidx(o + q * Ns, b)] = v[m + q * M];
+      for (int q = 0; q < R; ++q) out[sidx<KB>(o + q * Ns, b)] = v[m + q * M];
     }
   }
 }
 
 // Reads the stride layout; for N/8 a multiple of 8 the rows are brow(tt) +
 // brow(k N/8).
-template <int N>
+template <int N, int KB>
 __host__ __device__ __forceinline__ void load_stride(float2 (&v)[8], int tt, int b, const float2* in) {
   constexpr int T = N / 8;
   if (T % 8 == 0) {
-    const float2* p = in + brow(tt) * kS + b;
+    const float2* p = in + brow(tt) * KB + b;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = p[brow(k * T) * kS];
+    for (int k = 0; k < 8; ++k) v[k] = p[brow(k * T) * KB];
   } else {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = in[sidx(tt + k * T, b)];
+    for (int k = 0; k < 8; ++k) v[k] = in[sidx<KB>(tt + k * T, b)];
   }
 }
 
 // Writes the stride layout to natural positions (the input of a radix-R
 // first pass).
-template <int N>
+template <int N, int KB>
 __host__ __device__ __forceinline__ void store_stride(const float2 (&v)[8], int tt, int b, float2* out) {
   constexpr int T = N / 8;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) out[sidx(tt + k * T, b)] = v[k];
+  for (int k = 0; k < 8; ++k) out[sidx<KB>(tt + k * T, b)] = v[k];
 }
 
 // Fills the per-pass twiddle table pt[TWSIZE] from the base table
@@ -205,15 +212,15 @@ __host__ __device__ __forceinline__ void build_pass_twiddles(float2* pt, const f
 
 // Pass p >= FIRST (radix 8, 4 or 2) of the batch transform: load (when the
 // previous pass stored), butterflies, store (p < last).
-template <int N, int S, int P>
+template <int N, int S, int P, int KB = kB>
 __host__ __device__ __forceinline__ void run_pass(float2 (&v)[8], int tt, int b, const float2* in, float2* out,
                                                   const float2* pt) {
   using PS = Passes<N>;
   constexpr int R = PS::radix(P);
   constexpr int Ns = PS::span(P);
-  if (P > PS::FIRST) load_stride<N>(v, tt, b, in);
+  if (P > PS::FIRST) load_stride<N, KB>(v, tt, b, in);
   pass_bfly<N, R, S, Ns>(v, tt, pt + PS::twoff(P));
-  if (P < PS::NPASS - 1) pass_store<N, R, Ns>(v, tt, b, out);
+  if (P < PS::NPASS - 1) pass_store<N, R, Ns, KB>(v, tt, b, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -393,51 +400,52 @@ __device__ __forceinline__ void row_fft1(float2 (&v)[8], int tt, float2* buf, co
 #endif
 
 #ifdef __CUDACC__
+template <int KB>
 struct BatchIdx {
   int b;
-  __device__ int operator()(int i) const { return sidx(i, b); }
+  __device__ int operator()(int i) const { return sidx<KB>(i, b); }
 };
 
-// The whole transform on the CTA's batch; buf0/buf1 hold batch_rows(N)*kS
+// The whole transform on the CTA's batch; buf0/buf1 hold batch_rows(N)*KB
 // float2 each.  Starts with a barrier (the buffers may still be read by a
 // previous transform) and ends with the result in v.
-template <int N, int S>
+template <int N, int S, int KB = kB>
 __device__ __forceinline__ void fft(float2 (&v)[8], int tt, int b, float2* buf0, float2* buf1, const float2* pt) {
   using PS = Passes<N>;
   constexpr int NP = PS::NPASS;
   if (PS::FIRST) {
     __syncthreads();
-    store_stride<N>(v, tt, b, buf1);
+    store_stride<N, KB>(v, tt, b, buf1);
     __syncthreads();
-    first_pass<N, S>(v, tt, buf1, BatchIdx{b});
-    run_pass<N, S, (NP > 1 ? 1 : 0)>(v, tt, b, nullptr, buf0, pt);  // v already in the stride layout
+    first_pass<N, S>(v, tt, buf1, BatchIdx<KB>{b});
+    run_pass<N, S, (NP > 1 ? 1 : 0), KB>(v, tt, b, nullptr, buf0, pt);  // v already in the stride layout
     if (NP > 2) {
       __syncthreads();
-      run_pass<N, S, (NP > 2 ? 2 : 0)>(v, tt, b, buf0, buf1, pt);
+      run_pass<N, S, (NP > 2 ? 2 : 0), KB>(v, tt, b, buf0, buf1, pt);
     }
     if (NP > 3) {
       __syncthreads();
-      run_pass<N, S, (NP > 3 ? 3 : 0)>(v, tt, b, buf1, buf0, pt);
+      run_pass<N, S, (NP > 3 ? 3 : 0), KB>(v, tt, b, buf1, buf0, pt);
     }
     if (NP > 4) {
       __syncthreads();
-      run_pass<N, S, (NP > 4 ? 4 : 0)>(v, tt, b, buf0, buf1, pt);
+      run_pass<N, S, (NP > 4 ? 4 : 0), KB>(v, tt, b, buf0, buf1, pt);
     }
     return;
   }
   if (NP > 1) __syncthreads();
-  run_pass<N, S, 0>(v, tt, b, nullptr, buf0, pt);
+  run_pass<N, S, 0, KB>(v, tt, b, nullptr, buf0, pt);
   if (NP > 1) {
     __syncthreads();
-    run_pass<N, S, (NP > 1 ? 1 : 0)>(v, tt, b, buf0, buf1, pt);
+    run_pass<N, S, (NP > 1 ? 1 : 0), KB>(v, tt, b, buf0, buf1, pt);
   }
   if (NP > 2) {
     __syncthreads();
-    run_pass<N, S, (NP > 2 ? 2 : 0)>(v, tt, b, buf1, buf0, pt);
+    run_pass<N, S, (NP > 2 ? 2 : 0), KB>(v, tt, b, buf1, buf0, pt);
   }
   if (NP > 3) {
     __syncthreads();
-    run_pass<N, S, (NP > 3 ? 3 : 0)>(v, tt, b, buf0, buf1, pt);
+    run_pass<N, S, (NP > 3 ? 3 : 0), KB>(v, tt, b, buf0, buf1, pt);
   }
 }
 #endif

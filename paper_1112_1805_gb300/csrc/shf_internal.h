@@ -115,7 +115,7 @@ struct LaunchHook {
 };
 
 // Static work list of the fast path.  The (column tile, filter) pairs of a
-// wave whose filter support touches the tile (8 half-spectrum columns) are
+// wave whose filter support touches the tile (fast_tile(g) half-spectrum columns) are
 // listed in (tile, filter) order and cut into one contiguous, balanced range
 // per CTA of a column launch, with as many CTAs as are resident at once.
 // Within a CTA's range, each run of one tile is one partial-sum slot of the
@@ -140,10 +140,10 @@ struct FastPlan {
   const int* tile_begin = nullptr;    // device [ntiles + 1], into tile_slots
   const int* tile_slots = nullptr;    // device, slots of each tile in filter order
 };
-constexpr int reg_batch() { return 8; }  // columns per tile of the fast column kernels
 
 // Fast path for power-of-two sizes (shf_fast.cu).
 bool fast_path_ok(const Geo& g);
+int fast_tile(const Geo& g);  // columns per tile of the fast column kernels (8, or 4 for H > 1024)
 cudaError_t prepare_fast_kernels();
 int fast_wave(const Geo& g, int wave_mib);  // filters per wave
 int fast_pitch(const Geo& g);       // row pitch (complex) of the internal spectra: Wh rounded up to 8

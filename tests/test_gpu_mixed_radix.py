@@ -3,9 +3,10 @@ against the oracle's trajectory (bars: max |u - u_oracle| <= 1e-4, relative
 energy <= 1e-5, labels equal except at top-two gaps below 1e-4).
 
 These sizes cover every radix-R first pass (R = 3, 5) of both the column
-transforms (height H) and the packed row transforms (L = W/2), the padded
-row groups (L/8 threads that do not divide a warp, or span 2 or 3 warps) and
-the mixed spans of the later passes."""
+transforms (height H) and the packed row transforms (L = W/2), the row-group
+layouts (L/8 threads that divide a warp, span whole warps, or are packed
+across warps), the mixed spans of the later passes, and heights above 1024
+(column batches of 4)."""
 
 import numpy as np
 import pytest
@@ -57,6 +58,9 @@ SHAPES = [
     (384, 768, 3, 3, 1, 3),    # H = 3*128, L = 384 (48-thread groups)
     (128, 1536, 2, 3, 1, 3),   # L = 768 = 3*256 (96-thread groups over 3 warps)
     (640, 80, 6, 2, 1, 4),     # H = 5*128, K = 6
+    (2048, 64, 2, 2, 1, 3),    # H = 2048: column batches of 4
+    (1536, 80, 3, 2, 1, 3),    # H = 3*512, batches of 4
+    (1280, 48, 2, 1, 3, 4),    # H = 5*256, batches of 4, RGB
 ]
 
 
@@ -78,7 +82,7 @@ def test_unsupported_sizes_take_the_general_path():
     torch = need_cuda()
     from paper_1112_1805_gb300.api import FilterBank, ShearletSegmenter
 
-    for H, W in ((72, 120), (30, 50), (1536, 64)):
+    for H, W in ((72, 120), (30, 50), (1152, 64)):
         img, cb, Lam = _problem(H, W, 3, 2, 5)
         fb = FilterBank(H, W, 2)
         seg = ShearletSegmenter(fb, torch.tensor(img, device="cuda"), cb, Lam.tolist(), 1.0)

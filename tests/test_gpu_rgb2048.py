@@ -6,7 +6,7 @@ per iteration), so, as planned for this workload: oracle parity on crops with
 the same K, J and colours (a register-FFT size and a general-path size), and
 at full size what holds exactly or at any size: the data term, the first
 iterate u = -gamma s / 2 (bitwise), simplex feasibility of w, |b_v| <= gamma
-Lambda_j per filter, finite iterates, and the general path's choice."""
+Lambda_j per filter, finite iterates."""
 
 import numpy as np
 import pytest
@@ -60,7 +60,7 @@ def test_rgb2048_full_size_properties():
     fb = FilterBank(wl.H, wl.W, wl.J)
     f = torch.tensor(img, device="cuda")
     seg = ShearletSegmenter(fb, f, cb, Lam.tolist(), wl.gamma)
-    assert seg.plan()["fast"] == 0  # H = 2048 exceeds the register FFTs
+    assert seg.plan()["fast"] == 1  # H = 2048: register FFTs with column batches of 4
     # data term at sampled pixels
     s = seg.get(B.SEG_S)
     rng = np.random.default_rng(3)

@@ -164,7 +164,8 @@ cudaError_t run_fast_adjoint_body(const Geo& g, const FastPlan& plan, const floa
   const int Whp = fast_pitch(g);
   const int nslots = plan.nslots;
   const int nw = static_cast<int>(plan.wave_f0.size());
-  const int rpc = fast::row_groups_per_cta(g.L);
+  const int rpc = fast::row_groups_per_cta(g.L, 1);
+  const int actas = fast::row_ctas_per_sm(g.L, 1) * sm_count();
   cudaError_t e = fast::col_fwd(g, Qr, uhat, K, Whp, st);
   for (int label = 0; label < K && e == cudaSuccess; ++label) {
     for (int w = 0; w < nw && e == cudaSuccess; ++w) {
@@ -173,7 +174,7 @@ cudaError_t run_fast_adjoint_body(const Geo& g, const FastPlan& plan, const floa
       const int* cb = plan.cta_begin + c0 + w;
       if (nc > 0) e = fast::col_fan(g, nc, uhat, plan.items, cb, Y, Whp, label, f0, st);
       const int groups = (nf * g.H + rpc - 1) / rpc;
-      const int ctas = std::min(groups, std::max(plan.row_ctas, 1));
+      const int ctas = std::min(groups, std::max(actas, 1));
       if (e == cudaSuccess) e = fast::row_adjoint(g, ctas, Y, bvbar, thr, Whp, label, f0, nf, scale, code, tpart, st);
       if (nc > 0 && e == cudaSuccess) e = fast::col_gather(g, nc, Y, plan.items, cb, partial, Whp, nslots, label, f0, st);
     }

@@ -78,8 +78,10 @@ cudaError_t col_reduce(const Geo& g, const float2* partial, const int* tile_begi
 
 // Row kernels (shf_fast_row.cu).
 cudaError_t prepare_row_kernels();
-int row_ctas_per_sm(int L);     // resident CTAs per SM of the v-step kernel
-int row_groups_per_cta(int L);  // rows in flight per CTA of the v-step kernel
+// Resident CTAs per SM and rows in flight per CTA of the v-step kernel
+// (mode 0) or of its adjoint (mode 1).
+int row_ctas_per_sm(int L, int mode = 0);
+int row_groups_per_cta(int L, int mode = 0);
 // v-step on the wave's rows: ctas resident CTAs over nf filters of `label`;
 // code (optional, [K][eta][H][W] bytes) receives 0 where |g| < t, else sign g.
 cudaError_t row_shrink(const Geo& g, int ctas, float2* Y, float* bv, const float* thr, int Whp, int label, int f0,

@@ -4,6 +4,7 @@
 #include <algorithm>
 
 #include "shf_fast.h"
+#include "shf_fft16.cuh"
 
 namespace shf {
 namespace fast {
@@ -298,6 +299,177 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 
   cp_async_commit_wait_all();  // no copy outlives the kernel
 }
 
+// ---------------------------------------------------------------------------
+// v-step with 16 values per thread (half widths L = 64 .. 512, powers of two;
+// shf_fft16.cuh): row groups of T = L/16 threads, 32/T groups per warp, eight
+// warps per CTA, every lane live.  Per group, shared memory holds the FFT
+// exchange buffer and the b_v stage, at a group stride that is T float2 apart
+// modulo 16 for T < 16 (the groups of a half-warp then use distinct banks).
+// The spectrum columns of a row are read straight from global memory (they
+// were written by the preceding fan launch and sit in L2); the b_v row is
+// staged by cp.async while the previous row is transformed.  The forward
+// unpacking pairs Z_i with Z_{L-i}, which lane (T - tt) mod T holds at
+// register 15 - q (lane 0 holds its own partners): one warp shuffle per value
+// replaces a round trip through shared memory.
+// ---------------------------------------------------------------------------
+template <int L>
+struct Row16Geo {
+  static constexpr int T = L / 16;
+  static constexpr int GPW = 32 / T;                         // groups per warp
+  static constexpr int NTH = 256;
+  static constexpr int RPC = 8 * GPW;                        // groups per CTA
+  static constexpr int BUF = even2(reg::row_buf(L));         // exchange buffer
+  static constexpr int RAW = BUF + L;                        // + b_v stage (L float2)
+  static constexpr int STRIDE = T >= 16 ? RAW : RAW + ((T - RAW % 16) % 16 + 16) % 16;
+  static constexpr int TW = even2(L + 1);                    // exp(-2 pi i m / W), m <= L
+  static constexpr int PT = even2(r16::Passes<L>::TWSIZE);   // per-pass twiddles
+  static constexpr int TOTAL = TW + PT + RPC * STRIDE;       // float2 per CTA
+};
+
+template <int L>
+__global__ void __launch_bounds__(256, 3)
+    k_wrow_vstep16(float2* __restrict__ Y, float* __restrict__ bv, const float* __restrict__ thr,
+                   const int2* __restrict__ ranges, int H, int Whp, int eta, int label, int f0, int nf, float scale,
+                   const float2* __restrict__ twW, signed char* __restrict__ code) {
+  using G = Row16Geo<L>;
+  constexpr int T = G::T;
+  constexpr int RPC = G::RPC;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* tw = sm;
+  float2* pt = tw + G::TW;
+  const int lane = threadIdx.x & 31;
+  const int tt = lane & (T - 1);
+  const int grp = threadIdx.x / T;
+  const int partner = (lane - tt) + ((T - tt) & (T - 1));
+  float2* fb = pt + G::PT + grp * G::STRIDE;
+  float2* sB = fb + G::BUF;
+  const int Gn = gridDim.x * RPC;
+  const int gid = blockIdx.x * RPC + grp;
+  const int rows = nf * H;
+  const int niter = (rows + Gn - 1) / Gn;  // the same for every group: every lane takes part in the shuffles
+  const uint64_t pol = evict_first_policy();
+  const size_t W = 2 * static_cast<size_t>(L);
+  const int cmask = reg::col_batch(H) - 1;
+  const int gq = Gn / H, gr = Gn - gq * H;
+  auto advance = [&](int& fl, int& row) {
+    fl += gq;
+    row += gr;
+    if (row >= H) {
+      row -= H;
+      ++fl;
+    }
+  };
+  auto request_b = [&](int fl, int row) {
+    if (fl >= nf) return;
+    const size_t rix = (static_cast<size_t>(label) * eta + f0 + fl) * H + row;
+    const float2* B = reinterpret_cast<const float2*>(bv) + rix * L;
+#pragma unroll
+    for (int q = tt; q < L / 2; q += T) cp_async16(sB + 2 * q, B + 2 * q, true, pol);
+  };
+
+  int flc = gid / H, rowc = gid - flc * H;
+  request_b(flc, rowc);  // b_v was last written by an earlier, completed grid
+  load_table(tw, twW, L + 1);
+  r16::build_pass_twiddles<L, 2>(pt, twW, threadIdx.x, blockDim.x);
+  pdl_wait();
+  pdl_trigger();
+  __syncthreads();
+  for (int it = 0; it < niter; ++it) {
+    const bool live = flc < nf;
+    const int fl = live ? flc : 0, row = live ? rowc : 0, f = f0 + fl;
+    int fln = flc, rown = rowc;
+    advance(fln, rown);
+    const int2 rg = ranges[f];
+    const bool any = live && rg.x <= rg.y;
+    const int c0 = any ? (rg.x & ~cmask) : L + 1;
+    const int c1 = any ? min(L, (rg.y | cmask)) : -1;
+    const float th = thr[f];
+    const size_t rix = (static_cast<size_t>(label) * eta + f) * H + row;
+    float2* X = Y + (static_cast<size_t>(fl) * H + row) * Whp;
+    // inverse packing Z[n] = (X_n + conj X_{L-n}) + i e^{+2 pi i n/W} (X_n - conj X_{L-n}), n = tt + k T.
+    // X_{L-n} is the partner lane's register 15 - k; lane 0 pairs its own
+    // registers k and 16 - k (and k = 0 with X_L).  Z is formed in place, two
+    // registers (k, 15 - k) per step; lane 0's partner register 16 - k was
+    // overwritten one step earlier, so it is carried over in `prev`.
+    float2 v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int n = tt + k * T;
+      v[k] = (n >= c0 && n <= c1) ? __ldcg(X + n) : make_float2(0.f, 0.f);
+    }
+    float2 prev = (c1 >= L) ? __ldcg(X + L) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int k2 = 15 - k;
+      float2 ra, rb;  // the partner's registers 15 - k and k: X_{L-n} for n at k and at k2
+      ra.x = __shfl_sync(0xffffffffu, v[k2].x, partner);
+      ra.y = __shfl_sync(0xffffffffu, v[k2].y, partner);
+      rb.x = __shfl_sync(0xffffffffu, v[k].x, partner);
+      rb.y = __shfl_sync(0xffffffffu, v[k].y, partner);
+      if (tt == 0) {
+        ra = prev;       // X_{L - T k}: register 16 - k before it was overwritten (X_L for k = 0)
+        rb = v[k + 1];   // X_{L - T k2} = register k + 1, not yet overwritten
+      }
+      prev = v[k2];
+      const float2 a1 = v[k], a2 = v[k2];
+      {
+        const float2 c = c_conj(ra);
+        const float2 s2 = c_add(a1, c), d = c_sub(a1, c);
+        const float2 t = c_mul(c_conj(tw[tt + k * T]), d);
+        v[k] = make_float2(s2.x - t.y, s2.y + t.x);
+      }
+      {
+        const float2 c = c_conj(rb);
+        const float2 s2 = c_add(a2, c), d = c_sub(a2, c);
+        const float2 t = c_mul(c_conj(tw[tt + k2 * T]), d);
+        v[k2] = make_float2(s2.x - t.y, s2.y + t.x);
+      }
+    }
+    r16::row_fft<L, +1>(v, tt, fb, pt);
+    cp_async_commit_wait_all();  // this lane's part of the b_v row
+    __syncwarp();                // ... and the group's
+    if (live) {
+      float2* b2 = reinterpret_cast<float2*>(bv) + rix * L;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const float2 bo = sB[tt + k * T];
+        const float gx = fmaf(scale, v[k].x, bo.x), gy = fmaf(scale, v[k].y, bo.y);
+        const float cx = fminf(fmaxf(gx, -th), th), cy = fminf(fmaxf(gy, -th), th);
+        __stcs(b2 + tt + k * T, make_float2(cx, cy));
+        if (code)
+          reinterpret_cast<char2*>(code + rix * W)[tt + k * T] = make_char2(clip_code(gx, th), clip_code(gy, th));
+        v[k] = make_float2(gx - 2.f * cx, gy - 2.f * cy);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[k] = make_float2(0.f, 0.f);
+    }
+    __syncwarp();  // the b_v stage is read: refill it with the group's next row
+    request_b(fln, rown);
+    r16::row_fft<L, -1>(v, tt, fb, pt);
+    // forward unpacking X[i] = 1/2 [(Z_i + conj Z_{L-i}) - i e^{-2 pi i i/W} (Z_i - conj Z_{L-i})],
+    // i = tt + q T; Z_{L-i} is register 15 - q of the partner lane (lane 0: its own register (16 - q) mod 16)
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      float2 r;
+      r.x = __shfl_sync(0xffffffffu, v[15 - q].x, partner);
+      r.y = __shfl_sync(0xffffffffu, v[15 - q].y, partner);
+      const float2 zb = tt == 0 ? v[(16 - q) & 15] : r;
+      const int i = tt + q * T;
+      if (i >= c0 && i <= c1) {
+        const float2 c = c_conj(zb);
+        const float2 s2 = c_add(v[q], c), d = c_sub(v[q], c);
+        const float2 t = c_mul(tw[i], d);
+        X[i] = make_float2(0.5f * (s2.x + t.y), 0.5f * (s2.y - t.x));
+      }
+    }
+    if (tt == 0 && c1 >= L) X[L] = make_float2(v[0].x - v[0].y, 0.f);  // i = L: e^{-i pi} = -1
+    flc = fln;
+    rowc = rown;
+  }
+  cp_async_commit_wait_all();  // no copy outlives the kernel
+}
+
 // Euclidean projection of g[0..K) onto the unit simplex, as the paper
 // constructs it: project onto the hyperplane sum = 1 (g + (1 - sum g)/q), set
 // the negative components to zero and repeat on the remaining ones (at most K
@@ -508,10 +680,21 @@ size_t ustep_smem(int K) {
                            static_cast<size_t>(K) * UG::rows(K) * L);
 }
 
+// Half widths served by the radix-16 v-step (the adjoint keeps the 8-value
+// kernel for every length).
+__host__ __device__ constexpr bool use_r16(int L) { return L == 64 || L == 128 || L == 256 || L == 512; }
+
+template <int L>
+size_t vstep16_smem() {
+  return sizeof(float2) * Row16Geo<(use_r16(L) ? L : 64)>::TOTAL;
+}
+
 template <int L>
 cudaError_t prepare_row_t() {
   cudaError_t e = allow_smem(k_wrow_vstep<L, 0>, vstep_smem<L, 0>());
   if (e == cudaSuccess) e = allow_smem(k_wrow_vstep<L, 1>, vstep_smem<L, 1>());
+  if constexpr (use_r16(L))
+    if (e == cudaSuccess) e = allow_smem(k_wrow_vstep16<L>, vstep16_smem<L>());
   // the u/w-step's shared memory depends on K (rows per CTA): the largest over
   // the K each instance serves (2..4 and 5..8)
   size_t m4 = 0, m8 = 0;
@@ -545,13 +728,17 @@ cudaError_t prepare_row_kernels() {
   return e;
 }
 
-int row_ctas_per_sm(int L) {
+int row_ctas_per_sm(int L, int mode) {
   int fit = 0;
   cudaError_t e = cudaErrorInvalidValue;
   switch (L) {
-#define SHF_OCC(N)                                                                                                \
-  case N:                                                                                                         \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_vstep<N, 0>, RowGeo<N>::NTH, vstep_smem<N, 0>()); \
+#define SHF_OCC(N)                                                                                                  \
+  case N:                                                                                                           \
+    if (mode == 0 && use_r16(N))                                                                                    \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_vstep16<(use_r16(N) ? N : 64)>, 256,           \
+                                                        vstep16_smem<N>());                                         \
+    else                                                                                                            \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_vstep<N, 0>, RowGeo<N>::NTH, vstep_smem<N, 0>()); \
     break;
     SHF_FAST_SIZES(SHF_OCC)
 #undef SHF_OCC
@@ -560,11 +747,11 @@ int row_ctas_per_sm(int L) {
   return e == cudaSuccess ? fit : 0;
 }
 
-int row_groups_per_cta(int L) {
+int row_groups_per_cta(int L, int mode) {
   switch (L) {
 #define SHF_CASE(N) \
   case N:           \
-    return RowGeo<N>::RPC;
+    return mode == 0 && use_r16(N) ? Row16Geo<(use_r16(N) ? N : 64)>::RPC : RowGeo<N>::RPC;
     SHF_FAST_SIZES(SHF_CASE)
 #undef SHF_CASE
     default: return 0;
@@ -576,6 +763,9 @@ cudaError_t row_shrink(const Geo& g, int ctas, float2* Y, float* bv, const float
   switch (g.L) {
 #define SHF_CASE(N)                                                                                              \
   case N:                                                                                                        \
+    if (use_r16(N))                                                                                              \
+      return launch_pdl(k_wrow_vstep16<(use_r16(N) ? N : 64)>, dim3(ctas), dim3(256), vstep16_smem<N>(), st, Y, \
+                        bv, thr, g.ranges, g.H, Whp, g.eta, label, f0, nf, scale, g.twW, code);                  \
     return launch_pdl(k_wrow_vstep<N, 0>, dim3(ctas), dim3(RowGeo<N>::NTH), vstep_smem<N, 0>(), st, Y, bv, thr, \
                       g.ranges, g.H, Whp, g.eta, label, f0, nf, scale, g.twW, code, static_cast<double*>(nullptr));
     SHF_FAST_SIZES(SHF_CASE)

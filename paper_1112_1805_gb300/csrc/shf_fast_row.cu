@@ -327,7 +327,7 @@ struct Row16Geo {
 };
 
 template <int L>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, 2)
     k_wrow_vstep16(float2* __restrict__ Y, float* __restrict__ bv, const float* __restrict__ thr,
                    const int2* __restrict__ ranges, int H, int Whp, int eta, int label, int f0, int nf, float scale,
                    const float2* __restrict__ twW, signed char* __restrict__ code) {

@@ -9,8 +9,9 @@ is Mpixel*label*ADMM-iteration per second summed over all ranks.  The work
 plan is autotuned on the image before the timed region (--no-tune keeps the
 default).  At N = 1 the line also carries `batched`: the same metric for the
 64-image uneven batch (one graph per iteration with a branch per image), one
-timed step of 300 iterations after three short warm-up steps (--no-batch
-skips it), and `differentiable`: 16 images of 256 x 256 through the unrolled
+timed step of 300 iterations after three short warm-up steps, beside the same
+images solved one after another through the single-image path (--no-batch
+skips both), and `differentiable`: 16 images of 256 x 256 through the unrolled
 forward and reverse sweeps (--no-differentiable skips it).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -412,12 +413,45 @@ def measure_batch(iters: int, steps: int, warmup_steps: int, warmup_iters: int, 
     ev1.record(batch.stream)
     ev1.synchronize()
     ms = ev0.elapsed_time(ev1)
+    plans = [batch.image(i).plan() for i in range(len(shapes))]
     batch.close()
-    return {"value": units * steps / (ms / 1000.0) / 1e6, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+    value = units * steps / (ms / 1000.0) / 1e6
+    seq = measure_sequential(shapes, imgs, cbs, lams, plans)
+    return {"value": value, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
             "warmup": warmup_steps, "tuned": tune,
+            "sequential_value": seq, "speedup_vs_sequential": value / seq,
             "workload": f"batch: {len(shapes)} images, sides 128..1024 (first 384x640), K 2..6, "
                         f"J = floor(log2(min side)/2), {iters} iterations per step, one graph per iteration "
-                        f"with a branch per image"}
+                        f"with a branch per image; sequential_value: the same images one after another through "
+                        f"the single-image path with the batch's plans"}
+
+
+def measure_sequential(shapes, imgs, cbs, lams, plans, iters: int = 20, warmup: int = 3):
+    """The batch's images solved one after another through the plain
+    single-image path (own filter bank and state, the plan the batch tuned),
+    `iters` graph-replayed iterations each after `warmup`; the summed
+    Mpixel*label*iter/s over the summed per-image times."""
+    import torch
+
+    from paper_1112_1805_gb300.api import FilterBank, ShearletSegmenter
+
+    total_ms, units = 0.0, 0
+    for i, (H, W, K, J) in enumerate(shapes):
+        fb = FilterBank(H, W, J)
+        seg = ShearletSegmenter(fb, imgs[i], cbs[i], lams[i].tolist(), 1.0)
+        seg.set_plan(plans[i])
+        seg.step(warmup)
+        seg.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(seg.stream)
+        seg.step(iters)
+        b.record(seg.stream)
+        b.synchronize()
+        total_ms += a.elapsed_time(b)
+        units += H * W * K * iters
+        seg.close()
+        fb.close()
+    return units / (total_ms / 1000.0) / 1e6
 
 
 def measure_differentiable(steps: int, warmup: int, n_images: int = 16):

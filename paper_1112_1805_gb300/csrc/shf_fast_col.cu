@@ -199,18 +199,36 @@ __global__ void __launch_bounds__(ColGeo<H>::NT, col_min_blocks(H, ColGeo<H>::NT
 }
 
 // T[label] on one tile = column-inverse of the sum of the tile's partial
-// slots, in the fixed slot order (filter order).
+// slots, in a fixed order.  The sum is load-latency bound, so where two
+// copies of the CTA's threads fit in 1024 (RG = 2) the slots are split in two
+// halves summed by two thread groups at once; the first group adds the second
+// group's sums (first half + second half) and transforms.  The second group
+// runs the same transform on its own buffers (its result is discarded), so
+// that both groups pass the same barriers.
 template <int H>
-__global__ void __launch_bounds__(ColGeo<H>::NT) k_fcol_reduce_inv(const float2* __restrict__ partial,
-                                                       const int* __restrict__ tile_begin,
-                                                       const int* __restrict__ tile_slots, float2* __restrict__ T,
-                                                       int Wh, int nslots, const float2* __restrict__ twH) {
-  extern __shared__ float2 sm[];
-  float2* tw = sm;  // per-pass twiddles
-  float2* b0 = sm + reg::Passes<H>::TWSIZE;
-  float2* b1 = b0 + reg::batch_rows(H) * ColGeo<H>::KB;
+struct ReduceGeo {
+  static constexpr int NT = ColGeo<H>::NT;
+  static constexpr int RG = 2 * NT <= 1024 ? 2 : 1;
+  static constexpr int BR = reg::batch_rows(H) * ColGeo<H>::KB;       // one exchange buffer
+  static constexpr int BUFS = (reg::Passes<H>::TWSIZE + 1) & ~1;     // offset of the buffers
+  static constexpr int STAGE = BUFS + 2 * RG * BR;                    // the second group's sums [H][KB]
+  static constexpr int TOTAL = STAGE + (RG > 1 ? H * ColGeo<H>::KB : 0);
+};
+
+template <int H>
+__global__ void __launch_bounds__(ReduceGeo<H>::RG * ColGeo<H>::NT) k_fcol_reduce_inv(
+    const float2* __restrict__ partial, const int* __restrict__ tile_begin, const int* __restrict__ tile_slots,
+    float2* __restrict__ T, int Wh, int nslots, const float2* __restrict__ twH) {
+  using RGeo = ReduceGeo<H>;
   constexpr int KB = ColGeo<H>::KB;
-  const int b = threadIdx.x % KB, tt = threadIdx.x / KB;
+  constexpr int NT = ColGeo<H>::NT;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* tw = sm;  // per-pass twiddles
+  const int grp = threadIdx.x / NT, lt = threadIdx.x - grp * NT;
+  float2* b0 = sm + RGeo::BUFS + 2 * grp * RGeo::BR;
+  float2* b1 = b0 + RGeo::BR;
+  float2* stage = sm + RGeo::STAGE;
+  const int b = lt % KB, tt = lt / KB;
   const int tile = blockIdx.x, label = blockIdx.y;
   const int col = tile * KB + b;
   const bool ok = col < Wh;
@@ -221,14 +239,27 @@ __global__ void __launch_bounds__(ColGeo<H>::NT) k_fcol_reduce_inv(const float2*
   pdl_wait();
   pdl_trigger();
   const int s0 = tile_begin[tile], s1 = tile_begin[tile + 1];
-  for (int si = s0; si < s1; ++si) {
+  const int sm1 = RGeo::RG > 1 ? s0 + (s1 - s0 + 1) / 2 : s1;
+  const int a0 = grp == 0 ? s0 : sm1, a1 = grp == 0 ? sm1 : s1;
+  for (int si = a0; si < a1; ++si) {
     const float2* src = partial + (static_cast<size_t>(label) * nslots + tile_slots[si]) * H * KB + b;
 #pragma unroll
     for (int k = 0; k < 8; ++k) v[k] = c_add(v[k], src[static_cast<size_t>(tt + k * (H / 8)) * KB]);
   }
+  if constexpr (RGeo::RG > 1) {
+    if (grp == 1) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) stage[(tt + k * (H / 8)) * KB + b] = v[k];
+    }
+    __syncthreads();
+    if (grp == 0) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = c_add(v[k], stage[(tt + k * (H / 8)) * KB + b]);
+    }
+  }
   __syncthreads();
   reg::fft<H, +1, KB>(v, tt, b, b0, b1, tw);
-  if (ok) {
+  if (grp == 0 && ok) {
     float2* dst = T + static_cast<size_t>(H) * Wh * label + col;
 #pragma unroll
     for (int k = 0; k < 8; ++k) dst[static_cast<size_t>(tt + k * (H / 8)) * Wh] = v[k];
@@ -246,7 +277,7 @@ cudaError_t prepare_col_t() {
   cudaError_t e = allow_smem(k_fcol_fwd<H>, s);
   if (e == cudaSuccess) e = allow_smem(k_fcol_fan<H>, s);
   if (e == cudaSuccess) e = allow_smem(k_fcol_gather<H>, s);
-  if (e == cudaSuccess) e = allow_smem(k_fcol_reduce_inv<H>, s);
+  if (e == cudaSuccess) e = allow_smem(k_fcol_reduce_inv<H>, sizeof(float2) * ReduceGeo<H>::TOTAL);
   return e;
 }
 
@@ -320,7 +351,8 @@ cudaError_t col_reduce(const Geo& g, const float2* partial, const int* tile_begi
   switch (g.H) {
 #define SHF_CASE(N)                                                                                          \
   case N:                                                                                                    \
-    return launch_pdl(k_fcol_reduce_inv<N>, dim3(ntiles, K), dim3(ColGeo<N>::NT), col_smem<N>(), st, partial, tile_begin, \
+    return launch_pdl(k_fcol_reduce_inv<N>, dim3(ntiles, K), dim3(ReduceGeo<N>::RG * ColGeo<N>::NT),             \
+                      sizeof(float2) * ReduceGeo<N>::TOTAL, st, partial, tile_begin,                                  \
                       tile_slots, T, g.Wh, nslots, g.twH);
     SHF_COL_SIZES(SHF_CASE)
 #undef SHF_CASE

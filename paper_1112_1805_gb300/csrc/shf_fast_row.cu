@@ -386,11 +386,7 @@ __global__ void __launch_bounds__(256, 2)
     const float th = thr[f];
     const size_t rix = (static_cast<size_t>(label) * eta + f) * H + row;
     float2* X = Y + (static_cast<size_t>(fl) * H + row) * Whp;
-    // inverse packing Z[n] = (X_n + conj X_{L-n}) + i e^{+2 pi i n/W} (X_n - conj X_{L-n}), n = tt + k T.
-    // X_{L-n} is the partner lane's register 15 - k; lane 0 pairs its own
-    // registers k and 16 - k (and k = 0 with X_L).  Z is formed in place, two
-    // registers (k, 15 - k) per step; lane 0's partner register 16 - k was
-    // overwritten one step earlier, so it is carried over in `prev`.
+    // inverse packing (r16::pack_step), X_{L-n} from the partner lane
     float2 v[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
@@ -400,30 +396,12 @@ __global__ void __launch_bounds__(256, 2)
     float2 prev = (c1 >= L) ? __ldcg(X + L) : make_float2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const int k2 = 15 - k;
-      float2 ra, rb;  // the partner's registers 15 - k and k: X_{L-n} for n at k and at k2
-      ra.x = __shfl_sync(0xffffffffu, v[k2].x, partner);
-      ra.y = __shfl_sync(0xffffffffu, v[k2].y, partner);
+      float2 ra, rb;
+      ra.x = __shfl_sync(0xffffffffu, v[15 - k].x, partner);
+      ra.y = __shfl_sync(0xffffffffu, v[15 - k].y, partner);
       rb.x = __shfl_sync(0xffffffffu, v[k].x, partner);
       rb.y = __shfl_sync(0xffffffffu, v[k].y, partner);
-      if (tt == 0) {
-        ra = prev;       // X_{L - T k}: register 16 - k before it was overwritten (X_L for k = 0)
-        rb = v[k + 1];   // X_{L - T k2} = register k + 1, not yet overwritten
-      }
-      prev = v[k2];
-      const float2 a1 = v[k], a2 = v[k2];
-      {
-        const float2 c = c_conj(ra);
-        const float2 s2 = c_add(a1, c), d = c_sub(a1, c);
-        const float2 t = c_mul(c_conj(tw[tt + k * T]), d);
-        v[k] = make_float2(s2.x - t.y, s2.y + t.x);
-      }
-      {
-        const float2 c = c_conj(rb);
-        const float2 s2 = c_add(a2, c), d = c_sub(a2, c);
-        const float2 t = c_mul(c_conj(tw[tt + k2 * T]), d);
-        v[k2] = make_float2(s2.x - t.y, s2.y + t.x);
-      }
+      r16::pack_step<L>(v, k, tt, ra, rb, prev, tw);
     }
     r16::row_fft<L, +1>(v, tt, fb, pt);
     cp_async_commit_wait_all();  // this lane's part of the b_v row
@@ -447,21 +425,14 @@ __global__ void __launch_bounds__(256, 2)
     __syncwarp();  // the b_v stage is read: refill it with the group's next row
     request_b(fln, rown);
     r16::row_fft<L, -1>(v, tt, fb, pt);
-    // forward unpacking X[i] = 1/2 [(Z_i + conj Z_{L-i}) - i e^{-2 pi i i/W} (Z_i - conj Z_{L-i})],
-    // i = tt + q T; Z_{L-i} is register 15 - q of the partner lane (lane 0: its own register (16 - q) mod 16)
+    // forward unpacking (r16::unpack_value), Z_{L-i} from the partner lane
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       float2 r;
       r.x = __shfl_sync(0xffffffffu, v[15 - q].x, partner);
       r.y = __shfl_sync(0xffffffffu, v[15 - q].y, partner);
-      const float2 zb = tt == 0 ? v[(16 - q) & 15] : r;
       const int i = tt + q * T;
-      if (i >= c0 && i <= c1) {
-        const float2 c = c_conj(zb);
-        const float2 s2 = c_add(v[q], c), d = c_sub(v[q], c);
-        const float2 t = c_mul(tw[i], d);
-        X[i] = make_float2(0.5f * (s2.x + t.y), 0.5f * (s2.y - t.x));
-      }
+      if (i >= c0 && i <= c1) X[i] = r16::unpack_value<L>(v, q, tt, r, tw);
     }
     if (tt == 0 && c1 >= L) X[L] = make_float2(v[0].x - v[0].y, 0.f);  // i = L: e^{-i pi} = -1
     flc = fln;

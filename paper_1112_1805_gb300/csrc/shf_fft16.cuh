@@ -156,6 +156,58 @@ __host__ __device__ __forceinline__ void build_pass_twiddles(float2* pt, const f
   }
 }
 
+// Real rows of length W = 2L as complex rows of length L (z[n] = x[2n] + i x[2n+1]).
+// In the stride layout index L - (tt + k T) is register 15 - k of lane
+// (T - tt) mod T, and for lane 0 its own register 16 - k (k >= 1; index L for
+// k = 0): the pairings of the packing are warp shuffles.
+
+// Step k (0..7) of the in-place inverse packing
+// Z[n] = (X_n + conj X_{L-n}) + i e^{+2 pi i n/W} (X_n - conj X_{L-n}): registers
+// k and 15 - k (holding X at n = tt + k T and tt + (15 - k) T) become Z.  ra, rb
+// are the partner lane's registers 15 - k and k as they were before this step
+// (unused on lane 0).  Lane 0 pairs registers k and 16 - k instead; its register
+// 16 - k was overwritten at step k - 1, so it is carried in `prev` (X_L before
+// step 0).  tw[m] = exp(-2 pi i m / W).
+template <int L>
+__host__ __device__ __forceinline__ void pack_step(float2 (&v)[16], int k, int tt, float2 ra, float2 rb, float2& prev,
+                                                   const float2* tw) {
+  constexpr int T = L / 16;
+  const int k2 = 15 - k;
+  if (tt == 0) {
+    ra = prev;      // X_{L - T k}
+    rb = v[k + 1];  // X_{L - T k2}, not yet overwritten
+  }
+  prev = v[k2];
+  const float2 a1 = v[k], a2 = v[k2];
+  {
+    const float2 c = c_conj(ra);
+    const float2 s2 = c_add(a1, c), d = c_sub(a1, c);
+    const float2 t = c_mul(c_conj(tw[tt + k * T]), d);
+    v[k] = make_float2(s2.x - t.y, s2.y + t.x);
+  }
+  {
+    const float2 c = c_conj(rb);
+    const float2 s2 = c_add(a2, c), d = c_sub(a2, c);
+    const float2 t = c_mul(c_conj(tw[tt + k2 * T]), d);
+    v[k2] = make_float2(s2.x - t.y, s2.y + t.x);
+  }
+}
+
+// Forward unpacking X[i] = 1/2 [(Z_i + conj Z_{L-i}) - i e^{-2 pi i i/W} (Z_i - conj Z_{L-i})]
+// at i = tt + q T from register q (Z_i) and r, the partner lane's register
+// 15 - q (on lane 0 Z_{L-i} is its own register (16 - q) mod 16).  X[L] is
+// Re Z_0 - Im Z_0 (e^{-i pi} = -1), formed by lane 0.
+template <int L>
+__host__ __device__ __forceinline__ float2 unpack_value(const float2 (&v)[16], int q, int tt, float2 r,
+                                                        const float2* tw) {
+  constexpr int T = L / 16;
+  const float2 zb = tt == 0 ? v[(16 - q) & 15] : r;
+  const float2 c = c_conj(zb);
+  const float2 s2 = c_add(v[q], c), d = c_sub(v[q], c);
+  const float2 t = c_mul(tw[tt + q * T], d);
+  return make_float2(0.5f * (s2.x + t.y), 0.5f * (s2.y - t.x));
+}
+
 #ifdef __CUDACC__
 // The transform of one sequence by its row group (T <= 32 threads inside one
 // warp, all lanes of the warp taking part); result in v, in the stride layout.

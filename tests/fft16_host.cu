@@ -1,0 +1,130 @@
+// Host-side check of the radix-16 row FFT building blocks (shf_fft16.cuh)
+// against FP64 DFTs, for the half widths 64, 128, 256 and 512.  A row group
+// of T threads is emulated lane by lane, phase by phase, exactly as the kernel
+// sequences them between warp barriers: butterflies, Stockham stores to the
+// padded group buffer, stride reads, and the packing steps with each lane's
+// partner values taken from a snapshot of the registers before the step (what
+// a warp shuffle returns).  Prints one line per length and exits non-zero on
+// a failed bound.
+#include <array>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <random>
+#include <vector>
+
+#include "shf_fft16.cuh"
+
+using namespace shf;
+using cd = std::complex<double>;
+using Regs = std::array<float2, 16>;
+
+static float2 (&regs(Regs& r))[16] { return *reinterpret_cast<float2(*)[16]>(r.data()); }
+
+template <int N, int P, int S>
+static void bfly_all(std::vector<Regs>& V, const float2* pt) {
+  for (int tt = 0; tt < N / 16; ++tt) r16::pass_bfly<N, P, S>(regs(V[tt]), tt, pt);
+}
+
+// The whole transform of one row group (r16::row_fft's sequence of phases).
+template <int N, int S>
+static void group_fft(std::vector<Regs>& V, std::vector<float2>& buf, const float2* pt) {
+  using PS = r16::Passes<N>;
+  constexpr int T = PS::T;
+  bfly_all<N, 0, S>(V, pt);
+  if constexpr (PS::NPASS > 1) {
+    for (int tt = 0; tt < T; ++tt) r16::pass_store<N, 0>(regs(V[tt]), tt, buf.data());
+    for (int tt = 0; tt < T; ++tt) r16::load_stride<N>(regs(V[tt]), tt, buf.data());
+    bfly_all<N, (PS::NPASS > 1 ? 1 : 0), S>(V, pt);
+  }
+  if constexpr (PS::NPASS > 2) {
+    for (int tt = 0; tt < T; ++tt) r16::pass_store<N, (PS::NPASS > 2 ? 1 : 0)>(regs(V[tt]), tt, buf.data());
+    for (int tt = 0; tt < T; ++tt) r16::load_stride<N>(regs(V[tt]), tt, buf.data());
+    bfly_all<N, (PS::NPASS > 2 ? 2 : 0), S>(V, pt);
+  }
+}
+
+template <int L>
+static int check() {
+  using PS = r16::Passes<L>;
+  constexpr int T = PS::T;
+  const int W = 2 * L;
+  std::vector<float2> tw(W);  // exp(-2 pi i m / W), as the library's table
+  for (int m = 0; m < W; ++m) tw[m] = make_float2(std::cos(-2 * M_PI * m / W), std::sin(-2 * M_PI * m / W));
+  std::vector<float2> pt(PS::TWSIZE);
+  r16::build_pass_twiddles<L, 2>(pt.data(), tw.data(), 0, 1);
+  std::vector<float2> buf(reg::row_buf(L), make_float2(NAN, NAN));
+  std::mt19937 rng(1805 + L);
+  std::normal_distribution<double> nd;
+  auto partner = [](int tt) { return (T - tt) & (T - 1); };
+
+  // 1. complex transform, both exponent signs
+  double e_fft = 0;
+  for (int S : {+1, -1}) {
+    std::vector<cd> x(L);
+    for (auto& a : x) a = cd(nd(rng), nd(rng));
+    std::vector<Regs> V(T);
+    for (int tt = 0; tt < T; ++tt)
+      for (int k = 0; k < 16; ++k) V[tt][k] = make_float2(x[tt + k * T].real(), x[tt + k * T].imag());
+    if (S > 0)
+      group_fft<L, +1>(V, buf, pt.data());
+    else
+      group_fft<L, -1>(V, buf, pt.data());
+    for (int q = 0; q < L; ++q) {
+      cd ref = 0;
+      for (int n = 0; n < L; ++n) ref += x[n] * std::polar(1.0, S * 2 * M_PI * double(n) * q / L);
+      const float2 g = V[q % T][q / T];
+      e_fft = std::max(e_fft, std::abs(cd(g.x, g.y) - ref) / std::sqrt(double(L)));
+    }
+  }
+
+  // 2. real row: X = rfft(x); packing + inverse gives W (x[2n] + i x[2n+1]);
+  //    forward + unpacking gives X back
+  std::vector<double> xr(W);
+  for (auto& a : xr) a = nd(rng);
+  std::vector<cd> X(L + 1);
+  for (int k = 0; k <= L; ++k) {
+    cd s = 0;
+    for (int m = 0; m < W; ++m) s += xr[m] * std::polar(1.0, -2 * M_PI * double(k) * m / W);
+    X[k] = s;
+  }
+  auto f2 = [](cd a) { return make_float2(float(a.real()), float(a.imag())); };
+  std::vector<Regs> V(T);
+  for (int tt = 0; tt < T; ++tt)
+    for (int k = 0; k < 16; ++k) V[tt][k] = f2(X[tt + k * T]);
+  std::vector<float2> prev(T, f2(X[L]));
+  for (int k = 0; k < 8; ++k) {
+    const std::vector<Regs> snap = V;
+    for (int tt = 0; tt < T; ++tt) {
+      const Regs& p = snap[partner(tt)];
+      r16::pack_step<L>(regs(V[tt]), k, tt, p[15 - k], p[k], prev[tt], tw.data());
+    }
+  }
+  group_fft<L, +1>(V, buf, pt.data());
+  double e_inv = 0;
+  for (int n = 0; n < L; ++n) {
+    const float2 g = V[n % T][n / T];
+    e_inv = std::max(e_inv, std::abs(cd(g.x, g.y) / double(W) - cd(xr[2 * n], xr[2 * n + 1])));
+  }
+  for (auto& r : V)
+    for (auto& a : r) a = c_scale(a, 1.f / W);
+  group_fft<L, -1>(V, buf, pt.data());
+  double e_fwd = 0, xmax = 0;
+  for (int tt = 0; tt < T; ++tt)
+    for (int q = 0; q < 16; ++q) {
+      const float2 o = r16::unpack_value<L>(regs(V[tt]), q, tt, V[partner(tt)][15 - q], tw.data());
+      e_fwd = std::max(e_fwd, std::abs(cd(o.x, o.y) - X[tt + q * T]));
+    }
+  e_fwd = std::max(e_fwd, std::abs(cd(V[0][0].x - V[0][0].y, 0.0) - X[L]));
+  for (const auto& a : X) xmax = std::max(xmax, std::abs(a));
+
+  // FP32 transforms: error ~ eps log2(L) times the data scale; bounds with a
+  // margin of about 10
+  const double eps = 6e-8, lg = std::log2(double(L));
+  const bool ok = e_fft < 10 * eps * lg * 4 && e_inv < 10 * eps * lg * 4 && e_fwd < 10 * eps * lg * xmax;
+  std::printf("L=%d T=%d passes=%d fft %.2e inverse-real %.2e forward-real %.2e (|X| <= %.1f) %s\n", L, T,
+              PS::NPASS, e_fft, e_inv, e_fwd, xmax, ok ? "ok" : "FAIL");
+  return ok ? 0 : 1;
+}
+
+int main() { return check<64>() + check<128>() + check<256>() + check<512>(); }

@@ -199,20 +199,20 @@ __global__ void __launch_bounds__(ColGeo<H>::NT, col_min_blocks(H, ColGeo<H>::NT
 }
 
 // T[label] on one tile = column-inverse of the sum of the tile's partial
-// slots, in a fixed order.  The sum is load-latency bound, so where two
-// copies of the CTA's threads fit in 1024 (RG = 2) the slots are split in two
-// halves summed by two thread groups at once; the first group adds the second
-// group's sums (first half + second half) and transforms.  The second group
-// runs the same transform on its own buffers (its result is discarded), so
-// that both groups pass the same barriers.
+// slots, in a fixed order.  The sum is load-latency bound (and small images
+// have few tiles), so the slots are split into RG consecutive runs (RG copies
+// of the CTA's threads, up to 4, within 1024 threads) summed by RG thread
+// groups at once; the first group adds the other groups' sums in group order
+// and transforms.  The other groups run the same transform on their own
+// buffers (their results are discarded), so that all pass the same barriers.
 template <int H>
 struct ReduceGeo {
   static constexpr int NT = ColGeo<H>::NT;
-  static constexpr int RG = 2 * NT <= 1024 ? 2 : 1;
+  static constexpr int RG = 1024 / NT >= 4 ? 4 : (1024 / NT >= 1 ? 1024 / NT : 1);
   static constexpr int BR = reg::batch_rows(H) * ColGeo<H>::KB;       // one exchange buffer
   static constexpr int BUFS = (reg::Passes<H>::TWSIZE + 1) & ~1;     // offset of the buffers
-  static constexpr int STAGE = BUFS + 2 * RG * BR;                    // the second group's sums [H][KB]
-  static constexpr int TOTAL = STAGE + (RG > 1 ? H * ColGeo<H>::KB : 0);
+  static constexpr int STAGE = BUFS + 2 * RG * BR;                    // groups 1.. : their sums [H][KB]
+  static constexpr int TOTAL = STAGE + (RG - 1) * H * ColGeo<H>::KB;
 };
 
 template <int H>
@@ -238,23 +238,26 @@ __global__ void __launch_bounds__(ReduceGeo<H>::RG * ColGeo<H>::NT) k_fcol_reduc
   load_pass_table<H, 1>(tw, twH);
   pdl_wait();
   pdl_trigger();
-  const int s0 = tile_begin[tile], s1 = tile_begin[tile + 1];
-  const int sm1 = RGeo::RG > 1 ? s0 + (s1 - s0 + 1) / 2 : s1;
-  const int a0 = grp == 0 ? s0 : sm1, a1 = grp == 0 ? sm1 : s1;
+  const int s0 = tile_begin[tile], s1 = tile_begin[tile + 1], ns = s1 - s0;
+  const int a0 = s0 + ns * grp / RGeo::RG, a1 = s0 + ns * (grp + 1) / RGeo::RG;
   for (int si = a0; si < a1; ++si) {
     const float2* src = partial + (static_cast<size_t>(label) * nslots + tile_slots[si]) * H * KB + b;
 #pragma unroll
     for (int k = 0; k < 8; ++k) v[k] = c_add(v[k], src[static_cast<size_t>(tt + k * (H / 8)) * KB]);
   }
   if constexpr (RGeo::RG > 1) {
-    if (grp == 1) {
+    if (grp > 0) {
+      float2* st = stage + (grp - 1) * H * KB;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) stage[(tt + k * (H / 8)) * KB + b] = v[k];
+      for (int k = 0; k < 8; ++k) st[(tt + k * (H / 8)) * KB + b] = v[k];
     }
     __syncthreads();
     if (grp == 0) {
+      for (int g2 = 1; g2 < RGeo::RG; ++g2) {
+        const float2* st = stage + (g2 - 1) * H * KB;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) v[k] = c_add(v[k], stage[(tt + k * (H / 8)) * KB + b]);
+        for (int k = 0; k < 8; ++k) v[k] = c_add(v[k], st[(tt + k * (H / 8)) * KB + b]);
+      }
     }
   }
   __syncthreads();

@@ -300,24 +300,27 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 
 }
 
 // ---------------------------------------------------------------------------
-// v-step with 16 values per thread (half widths L = 64 .. 512, powers of two;
-// shf_fft16.cuh): row groups of T = L/16 threads, 32/T groups per warp, eight
-// warps per CTA, every lane live.  Per group, shared memory holds the FFT
-// exchange buffer and the b_v stage, at a group stride that is T float2 apart
-// modulo 16 for T < 16 (the groups of a half-warp then use distinct banks).
-// The spectrum columns of a row are read straight from global memory (they
-// were written by the preceding fan launch and sit in L2); the b_v row is
-// staged by cp.async while the previous row is transformed.  The forward
-// unpacking pairs Z_i with Z_{L-i}, which lane (T - tt) mod T holds at
-// register 15 - q (lane 0 holds its own partners): one warp shuffle per value
-// replaces a round trip through shared memory.
+// v-step with 16 values per thread (half widths L = 64 .. 1024, powers of two;
+// shf_fft16.cuh): row groups of T = L/16 threads, 32/T groups per warp (two
+// warps per group and a named barrier for L = 1024), eight warps per CTA,
+// every lane live.  Per group, shared memory holds the FFT exchange buffer and
+// the b_v stage, at a group stride that is T float2 apart modulo 16 for T < 16
+// (the groups of a half-warp then use distinct banks).  The spectrum columns
+// of a row are read straight from global memory (they were written by the
+// preceding fan launch and sit in L2); the b_v row is staged by cp.async while
+// the previous row is transformed.  The packing pairs X_n with X_{L-n} and the
+// unpacking Z_i with Z_{L-i}, which lane (T - tt) mod T holds at register
+// 15 - q (lane 0 holds its own partners): for T <= 32 one warp shuffle per
+// value replaces a round trip through shared memory; for T = 64 the partner
+// is in the other warp, and X_{L-n} is read from L2 and Z_{L-i} through the
+// exchange buffer.
 // ---------------------------------------------------------------------------
 template <int L>
 struct Row16Geo {
   static constexpr int T = L / 16;
-  static constexpr int GPW = 32 / T;                         // groups per warp
+  static constexpr int GPW = T <= 32 ? 32 / T : 0;          // groups per warp (T <= 32)
   static constexpr int NTH = 256;
-  static constexpr int RPC = 8 * GPW;                        // groups per CTA
+  static constexpr int RPC = T <= 32 ? 8 * GPW : NTH / T;    // groups per CTA
   static constexpr int BUF = even2(reg::row_buf(L));         // exchange buffer
   static constexpr int RAW = BUF + L;                        // + b_v stage (L float2)
   static constexpr int STRIDE = T >= 16 ? RAW : RAW + ((T - RAW % 16) % 16 + 16) % 16;
@@ -338,9 +341,10 @@ __global__ void __launch_bounds__(256, 2)
   float2* tw = sm;
   float2* pt = tw + G::TW;
   const int lane = threadIdx.x & 31;
-  const int tt = lane & (T - 1);
+  const int tt = threadIdx.x & (T - 1);
   const int grp = threadIdx.x / T;
-  const int partner = (lane - tt) + ((T - tt) & (T - 1));
+  const int partner = T <= 32 ? (lane - tt) + ((T - tt) & (T - 1)) : 0;  // shuffle source (T <= 32)
+  const int bar = 1 + grp;                                               // named barrier (T = 64)
   float2* fb = pt + G::PT + grp * G::STRIDE;
   float2* sB = fb + G::BUF;
   const int Gn = gridDim.x * RPC;
@@ -386,26 +390,39 @@ __global__ void __launch_bounds__(256, 2)
     const float th = thr[f];
     const size_t rix = (static_cast<size_t>(label) * eta + f) * H + row;
     float2* X = Y + (static_cast<size_t>(fl) * H + row) * Whp;
-    // inverse packing (r16::pack_step), X_{L-n} from the partner lane
     float2 v[16];
+    if constexpr (T <= 32) {
+      // inverse packing (r16::pack_step), X_{L-n} from the partner lane
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const int n = tt + k * T;
-      v[k] = (n >= c0 && n <= c1) ? __ldcg(X + n) : make_float2(0.f, 0.f);
-    }
-    float2 prev = (c1 >= L) ? __ldcg(X + L) : make_float2(0.f, 0.f);
+      for (int k = 0; k < 16; ++k) {
+        const int n = tt + k * T;
+        v[k] = (n >= c0 && n <= c1) ? __ldcg(X + n) : make_float2(0.f, 0.f);
+      }
+      float2 prev = (c1 >= L) ? __ldcg(X + L) : make_float2(0.f, 0.f);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      float2 ra, rb;
-      ra.x = __shfl_sync(0xffffffffu, v[15 - k].x, partner);
-      ra.y = __shfl_sync(0xffffffffu, v[15 - k].y, partner);
-      rb.x = __shfl_sync(0xffffffffu, v[k].x, partner);
-      rb.y = __shfl_sync(0xffffffffu, v[k].y, partner);
-      r16::pack_step<L>(v, k, tt, ra, rb, prev, tw);
+      for (int k = 0; k < 8; ++k) {
+        float2 ra, rb;
+        ra.x = __shfl_sync(0xffffffffu, v[15 - k].x, partner);
+        ra.y = __shfl_sync(0xffffffffu, v[15 - k].y, partner);
+        rb.x = __shfl_sync(0xffffffffu, v[k].x, partner);
+        rb.y = __shfl_sync(0xffffffffu, v[k].y, partner);
+        r16::pack_step<L>(v, k, tt, ra, rb, prev, tw);
+      }
+    } else {
+      // the partner lane is in the group's other warp: X_{L-n} is read from L2 as well
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int n = tt + k * T, m = L - n;
+        const float2 a = (n >= c0 && n <= c1) ? __ldcg(X + n) : make_float2(0.f, 0.f);
+        const float2 c = (m >= c0 && m <= c1) ? c_conj(__ldcg(X + m)) : make_float2(0.f, 0.f);
+        const float2 s2 = c_add(a, c), d = c_sub(a, c);
+        const float2 t = c_mul(c_conj(tw[n]), d);
+        v[k] = make_float2(s2.x - t.y, s2.y + t.x);
+      }
     }
-    r16::row_fft<L, +1>(v, tt, fb, pt);
+    r16::row_fft<L, +1>(v, tt, fb, pt, bar);
     cp_async_commit_wait_all();  // this lane's part of the b_v row
-    __syncwarp();                // ... and the group's
+    r16::group_sync<L>(bar);     // ... and the group's
     if (live) {
       float2* b2 = reinterpret_cast<float2*>(bv) + rix * L;
 #pragma unroll
@@ -422,17 +439,30 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
       for (int k = 0; k < 16; ++k) v[k] = make_float2(0.f, 0.f);
     }
-    __syncwarp();  // the b_v stage is read: refill it with the group's next row
+    r16::group_sync<L>(bar);  // the b_v stage is read: refill it with the group's next row
     request_b(fln, rown);
-    r16::row_fft<L, -1>(v, tt, fb, pt);
-    // forward unpacking (r16::unpack_value), Z_{L-i} from the partner lane
+    r16::row_fft<L, -1>(v, tt, fb, pt, bar);
+    if constexpr (T <= 32) {
+      // forward unpacking (r16::unpack_value), Z_{L-i} from the partner lane
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      float2 r;
-      r.x = __shfl_sync(0xffffffffu, v[15 - q].x, partner);
-      r.y = __shfl_sync(0xffffffffu, v[15 - q].y, partner);
-      const int i = tt + q * T;
-      if (i >= c0 && i <= c1) X[i] = r16::unpack_value<L>(v, q, tt, r, tw);
+      for (int q = 0; q < 16; ++q) {
+        float2 r;
+        r.x = __shfl_sync(0xffffffffu, v[15 - q].x, partner);
+        r.y = __shfl_sync(0xffffffffu, v[15 - q].y, partner);
+        const int i = tt + q * T;
+        if (i >= c0 && i <= c1) X[i] = r16::unpack_value<L>(v, q, tt, r, tw);
+      }
+    } else {
+      // Z_{L-i} through the exchange buffer (natural order at ridx)
+      r16::group_sync<L>(bar);  // the last pass may still read the buffer
+#pragma unroll
+      for (int q = 0; q < 16; ++q) fb[reg::ridx(tt + q * T)] = v[q];
+      r16::group_sync<L>(bar);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int i = tt + q * T;
+        if (i >= c0 && i <= c1) X[i] = r16::unpack_value<L>(v, q, tt, fb[reg::ridx((L - i) & (L - 1))], tw);
+      }
     }
     if (tt == 0 && c1 >= L) X[L] = make_float2(v[0].x - v[0].y, 0.f);  // i = L: e^{-i pi} = -1
     flc = fln;
@@ -653,7 +683,7 @@ size_t ustep_smem(int K) {
 
 // Half widths served by the radix-16 v-step (the adjoint keeps the 8-value
 // kernel for every length).
-__host__ __device__ constexpr bool use_r16(int L) { return L == 64 || L == 128 || L == 256 || L == 512; }
+__host__ __device__ constexpr bool use_r16(int L) { return L == 64 || L == 128 || L == 256 || L == 512 || L == 1024; }
 
 template <int L>
 size_t vstep16_smem() {

@@ -1,8 +1,8 @@
 // Register FFTs with 16 values per thread for the rows of the v-step, lengths
-// N = 2^a with 64 <= N <= 512 (sm_103a fast path).
+// N = 2^a with 64 <= N <= 1024 (sm_103a fast path).
 //
-// A row group of T = N/16 threads (4, 8, 16 or 32: whole fractions of a warp)
-// transforms one sequence; thread tt holds v[k] = x[tt + k T], k = 0..15
+// A row group of T = N/16 threads (4, 8, 16 or 32: whole fractions of a warp;
+// 64 for N = 1024: two warps) transforms one sequence; thread tt holds v[k] = x[tt + k T], k = 0..15
 // ("stride layout").  Stockham passes of radix 16 (spans 1, 16, ...) and, when
 // log2 N is not a multiple of 4, a last pass of radix 2, 4 or 8 in which each
 // thread does 16/R butterflies.  N = 256 = 16 * 16 thus needs one exchange
@@ -29,7 +29,7 @@ using reg::ridx;
 
 template <int N>
 struct Passes {
-  static_assert(N >= 32 && N <= 512 && (N & (N - 1)) == 0, "radix-16 row FFT: N = 2^a, 32 <= N <= 512");
+  static_assert(N >= 32 && N <= 1024 && (N & (N - 1)) == 0, "radix-16 row FFT: N = 2^a, 32 <= N <= 1024");
   static constexpr int T = N / 16;                        // threads of a group
   static constexpr int LG = ilog2(N);
   static constexpr int N16 = LG / 4;                      // radix-16 passes (first)
@@ -209,24 +209,35 @@ __host__ __device__ __forceinline__ float2 unpack_value(const float2 (&v)[16], i
 }
 
 #ifdef __CUDACC__
-// The transform of one sequence by its row group (T <= 32 threads inside one
-// warp, all lanes of the warp taking part); result in v, in the stride layout.
-// Starts with a barrier: the buffer may still be read by a previous transform.
+// Barrier of a row group: the warp for T <= 32 (all lanes of the warp take
+// part), else the named barrier `id` over the group's T threads (whole warps).
+template <int N>
+__device__ __forceinline__ void group_sync(int id) {
+  if constexpr (Passes<N>::T <= 32) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(Passes<N>::T) : "memory");
+  }
+}
+
+// The transform of one sequence by its row group; result in v, in the stride
+// layout.  The first exchange starts with a barrier: the buffer may still be
+// read by a previous transform.
 template <int N, int S>
-__device__ __forceinline__ void row_fft(float2 (&v)[16], int tt, float2* buf, const float2* pt) {
+__device__ __forceinline__ void row_fft(float2 (&v)[16], int tt, float2* buf, const float2* pt, int bar_id) {
   using PS = Passes<N>;
   pass_bfly<N, 0, S>(v, tt, pt);
   if constexpr (PS::NPASS > 1) {
-    __syncwarp();
+    group_sync<N>(bar_id);
     pass_store<N, 0>(v, tt, buf);
-    __syncwarp();
+    group_sync<N>(bar_id);
     load_stride<N>(v, tt, buf);
     pass_bfly<N, (PS::NPASS > 1 ? 1 : 0), S>(v, tt, pt);
   }
   if constexpr (PS::NPASS > 2) {
-    __syncwarp();
+    group_sync<N>(bar_id);
     pass_store<N, (PS::NPASS > 2 ? 1 : 0)>(v, tt, buf);
-    __syncwarp();
+    group_sync<N>(bar_id);
     load_stride<N>(v, tt, buf);
     pass_bfly<N, (PS::NPASS > 2 ? 2 : 0), S>(v, tt, pt);
   }

@@ -1,5 +1,5 @@
 // Host-side check of the radix-16 row FFT building blocks (shf_fft16.cuh)
-// against FP64 DFTs, for the half widths 64, 128, 256 and 512.  A row group
+// against FP64 DFTs, for the half widths 64, 128, 256, 512 and 1024.  A row group
 // of T threads is emulated lane by lane, phase by phase, exactly as the kernel
 // sequences them between warp barriers: butterflies, Stockham stores to the
 // padded group buffer, stride reads, and the packing steps with each lane's
@@ -127,4 +127,4 @@ static int check() {
   return ok ? 0 : 1;
 }
 
-int main() { return check<64>() + check<128>() + check<256>() + check<512>(); }
+int main() { return check<64>() + check<128>() + check<256>() + check<512>() + check<1024>(); }

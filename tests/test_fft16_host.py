@@ -3,7 +3,7 @@
 Compiles tests/fft16_host.cu for the host with nvcc and runs it: the radix-16
 passes, the padded group buffer's Stockham exchanges and the partner-lane
 packing of real rows are emulated lane by lane and compared with FP64 DFTs for
-half widths 64..512.  No GPU is needed.
+half widths 64..1024.  No GPU is needed.
 """
 
 import os
@@ -26,4 +26,4 @@ def test_fft16_host(tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     print(r.stdout)
     assert r.returncode == 0, r.stdout + r.stderr
-    assert r.stdout.count(" ok") == 4
+    assert r.stdout.count(" ok") == 5

@@ -88,6 +88,23 @@ def test_edge_shapes(torch_mod, O, H, W, K, J, C, T):
     _check_against(o, g)
 
 
+@pytest.mark.parametrize("H,W,K,J,T", [(16, 128, 3, 1, 12), (24, 256, 4, 2, 12), (16, 512, 3, 2, 10),
+                                      (8, 1024, 2, 1, 10), (16, 2048, 3, 1, 8), (40, 2048, 2, 2, 6)])
+def test_radix16_row_widths(torch_mod, O, H, W, K, J, T):
+    # half widths L = 64 .. 1024 take the v-step with 16 values per thread
+    # (L = 1024: row groups of two warps with a named barrier); a ragged
+    # number of rows per launch leaves some row groups without a row
+    rng = np.random.default_rng(H * W + 7 * K)
+    cb = np.linspace(0.15, 0.85, K)[:, None]
+    img, lab = synth.ellipse_image(H, W, cb, rng, n_ellipses=3)
+    Lam = synth.scale_weights(0.1, J)
+    img32 = img.astype(np.float32)
+    o = O.admm_run(img32.astype(np.float64), cb.astype(np.float32).astype(np.float64), J,
+                   Lam.astype(np.float32).astype(np.float64), 1.0, T)
+    g = _gpu_run(torch_mod, img32, cb, J, Lam, 1.0, T)
+    _check_against(o, g)
+
+
 def test_one_iteration_from_given_state(torch_mod, O):
     # Start both sides from the same arbitrary (v, b_v, w, b_w): every term of the
     # u-, v-, w- and b-updates is exercised from the first iteration on.

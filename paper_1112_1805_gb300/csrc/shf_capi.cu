@@ -328,7 +328,7 @@ int restart(seg_state* st, const float* codebook) {
 int marks_needed(const seg_state* st) {
   if (!st->fast) return 8;
   int n = 4;  // u/w-step, column forward, reduction, end
-  for (size_t w = 0; w < st->plan.wave_f0.size(); ++w) n += 3 * st->K;
+  n += 3 * static_cast<int>(st->plan.wave_f0.size());  // fan, v-step, gather per wave
   return n;
 }
 
@@ -496,10 +496,11 @@ int install_fast_plan(seg_state* st, int wave_mib, int col_ctas_per_sm) {
   if (plan.col_ctas < 1 || plan.row_ctas < 1) return fail(SHF_ERR_CUDA, "install_fast_plan: no resident CTA");
   std::vector<shf::WorkItem> h_items;
   std::vector<int> h_cta_begin, h_tile_begin, h_tile_slots;
-  shf::build_fast_plan(g, st->ranges_host.data(), &plan, &h_items, &h_cta_begin, &h_tile_begin, &h_tile_slots);
+  shf::build_fast_plan(g, st->ranges_host.data(), st->K, &plan, &h_items, &h_cta_begin, &h_tile_begin,
+                       &h_tile_slots);
   const size_t Phs = static_cast<size_t>(g.H) * shf::fast_pitch(g);
-  const size_t y_elems = Phs * static_cast<size_t>(shf::fast_wave(g, wave_mib));
-  const size_t partial_elems = static_cast<size_t>(st->K) * std::max(plan.nslots, 1) * g.H * shf::fast_tile(g);
+  const size_t y_elems = Phs * static_cast<size_t>(std::max(plan.y_planes, 1));
+  const size_t partial_elems = static_cast<size_t>(std::max(plan.nslots, 1)) * g.H * shf::fast_tile(g);
   float2 *Y = nullptr, *partial = nullptr;
   shf::WorkItem* items = nullptr;
   int *cta_begin = nullptr, *tile_begin = nullptr, *tile_slots = nullptr;
@@ -821,13 +822,14 @@ std::vector<seg_plan> plan_candidates(const seg_state* st, const seg_plan& base,
   const Geo& g = st->g;
   if (st->fast) {
     if (stage == 0) {
-      // wave budgets that give distinct numbers of waves per label
+      // wave budgets that give distinct waves (filters per wave of one label,
+      // or labels per wave)
       std::vector<int> seen;
       for (int mib : {16, 32, 64, 96, 128, 192}) {
-        const int w = shf::fast_wave(g, mib);
-        const int nw = (g.eta + w - 1) / w;
-        if (std::find(seen.begin(), seen.end(), nw) != seen.end()) continue;
-        seen.push_back(nw);
+        const int w = shf::fast_wave(g, mib), nl = shf::fast_wave_labels(g, mib, st->K);
+        const int sig = nl > 1 ? -nl : (g.eta + w - 1) / w;
+        if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
+        seen.push_back(sig);
         seg_plan p = base;
         p.wave_mib = mib;
         out.push_back(p);

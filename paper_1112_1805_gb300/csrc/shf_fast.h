@@ -60,21 +60,27 @@ cudaError_t allow_smem(KERN k, size_t bytes) {
 }
 #endif
 
+// A wave of (label, filter) pairs: labels from l0, filters [f0, f0 + nf) of
+// each; nv pairs in all, whose spectra are Y_v with v = (label - l0) nf + (f - f0).
+struct Wave {
+  int l0, f0, nf, nv;
+};
+
 // Column kernels (shf_fast_col.cu).  Whp: row pitch of the internal spectra.
 cudaError_t prepare_col_kernels();
 int col_ctas_per_sm(int H);  // resident CTAs per SM of the fan/gather kernels
 // Ur [K][H][Wh] -> uhat [K][H][Whp]: column-forward of the row spectra of u.
 cudaError_t col_fwd(const Geo& g, const float2* Ur, float2* uhat, int K, int Whp, cudaStream_t st);
-// Y_f = column-inverse(W_f * uhat_label) on the (tile, filter) items of CTA
-// ranges cta_begin[0..nc].
+// Y_v = column-inverse(W_f * uhat_label) on the (label, tile, filter) items of
+// CTA ranges cta_begin[0..nc] of wave wv.
 cudaError_t col_fan(const Geo& g, int nc, const float2* uhat, const WorkItem* items, const int* cta_begin,
-                    float2* Y, int Whp, int label, int f0, cudaStream_t st);
-// partial[label][slot] = sum over runs of items of W_f * column-forward(Y_f).
+                    float2* Y, int Whp, const Wave& wv, cudaStream_t st);
+// partial[slot] = sum over runs of items of W_f * column-forward(Y_v).
 cudaError_t col_gather(const Geo& g, int nc, const float2* Y, const WorkItem* items, const int* cta_begin,
-                       float2* partial, int Whp, int nslots, int label, int f0, cudaStream_t st);
-// T [K][H][Wh] = column-inverse of the per-tile sums of the partial slots.
+                       float2* partial, int Whp, const Wave& wv, cudaStream_t st);
+// T [K][H][Wh] = column-inverse of the per-(label, tile) sums of the partial slots.
 cudaError_t col_reduce(const Geo& g, const float2* partial, const int* tile_begin, const int* tile_slots, float2* T,
-                       int K, int nslots, cudaStream_t st);
+                       int K, cudaStream_t st);
 
 // Row kernels (shf_fast_row.cu).
 cudaError_t prepare_row_kernels();
@@ -82,15 +88,15 @@ cudaError_t prepare_row_kernels();
 // (mode 0) or of its adjoint (mode 1).
 int row_ctas_per_sm(int L, int mode = 0);
 int row_groups_per_cta(int L, int mode = 0);
-// v-step on the wave's rows: ctas resident CTAs over nf filters of `label`;
-// code (optional, [K][eta][H][W] bytes) receives 0 where |g| < t, else sign g.
-cudaError_t row_shrink(const Geo& g, int ctas, float2* Y, float* bv, const float* thr, int Whp, int label, int f0,
-                       int nf, float scale, signed char* code, cudaStream_t st);
+// v-step on the rows of wave wv: ctas resident CTAs; code (optional,
+// [K][eta][H][W] bytes) receives 0 where |g| < t, else sign g.
+cudaError_t row_shrink(const Geo& g, int ctas, float2* Y, float* bv, const float* thr, int Whp, const Wave& wv,
+                       float scale, signed char* code, cudaStream_t st);
 // Adjoint of the v-step for the reverse mode: Y holds the spectra of the rows
 // of S Qbar on input and those of the new bvbar on output; tpart
 // [K][eta][H] receives the rows' threshold sums.
-cudaError_t row_adjoint(const Geo& g, int ctas, float2* Y, float* bvbar, const float* thr, int Whp, int label, int f0,
-                        int nf, float scale, const signed char* code, double* tpart, cudaStream_t st);
+cudaError_t row_adjoint(const Geo& g, int ctas, float2* Y, float* bvbar, const float* thr, int Whp, const Wave& wv,
+                        float scale, const signed char* code, double* tpart, cudaStream_t st);
 // Shared memory of the u/w-step for K labels (0 if L is not supported).
 size_t ustep_smem_bytes(int L, int K);
 cudaError_t row_ustep(const Geo& g, const float2* T, const float* s, float* w, float* bw, float* u, float2* Ur, int K,

@@ -83,14 +83,14 @@ __device__ __forceinline__ void load_tile8(float2 (&v)[8], const float2* __restr
     v[k] = ok ? src[static_cast<size_t>(tt + k * (H / 8)) * pitch + col] : make_float2(0.f, 0.f);
 }
 
-// Analysis fan-out: for every item (tile, filter) of the CTA's range,
-// Y_f = column-inverse(W_f * uhat) on the tile.  The next item's filter tile
-// (and, at a tile change, the next spectrum tile) is requested while the
-// current transform runs.
+// Analysis fan-out: for every item (label, tile, filter) of the CTA's range,
+// Y_v = column-inverse(W_f * uhat_label) on the tile, v = (label - l0) nf +
+// (f - f0).  The next item's filter tile (and, at a change of tile or label,
+// the next spectrum tile) is requested while the current transform runs.
 template <int H>
 __global__ void __launch_bounds__(ColGeo<H>::NT, col_min_blocks(H, ColGeo<H>::NT))
     k_fcol_fan(const float2* __restrict__ uhat, const float* __restrict__ bank, const WorkItem* __restrict__ items,
-               const int* __restrict__ cta_begin, float2* __restrict__ Y, int Wh, int Whp, int label, int f0,
+               const int* __restrict__ cta_begin, float2* __restrict__ Y, int Wh, int Whp, int l0, int f0, int nf,
                const float2* __restrict__ twH) {
   extern __shared__ float2 sm[];
   float2* tw = sm;  // per-pass twiddles
@@ -106,24 +106,24 @@ __global__ void __launch_bounds__(ColGeo<H>::NT, col_min_blocks(H, ColGeo<H>::NT
   bool ok = col < Wh;
   float2 u[8];
   float w[8];
-  load_bank8<H>(w, bank + Pb * (f0 + it.filter), Wh, tt, col, ok);
+  load_bank8<H>(w, bank + Pb * it.filter, Wh, tt, col, ok);
   load_pass_table<H, 1>(tw, twH);
   pdl_wait();
   pdl_trigger();
-  load_tile8<H>(u, uhat + Pp * label, Whp, tt, col, ok);
+  load_tile8<H>(u, uhat + Pp * it.label, Whp, tt, col, ok);
   __syncthreads();
   for (int i = ib; i < ie; ++i) {
     float2 v[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) v[k] = c_scale(u[k], w[k]);
-    const int fl = it.filter, ccol = col;
+    const int fl = (it.label - l0) * nf + (it.filter - f0), ccol = col;
     const bool cok = ok;
     if (i + 1 < ie) {
       const WorkItem nx = items[i + 1];
       col = nx.tile * KB + b;
       ok = col < Wh;
-      load_bank8<H>(w, bank + Pb * (f0 + nx.filter), Wh, tt, col, ok);
-      if (nx.tile != it.tile) load_tile8<H>(u, uhat + Pp * label, Whp, tt, col, ok);
+      load_bank8<H>(w, bank + Pb * nx.filter, Wh, tt, col, ok);
+      if (nx.tile != it.tile || nx.label != it.label) load_tile8<H>(u, uhat + Pp * nx.label, Whp, tt, col, ok);
       it = nx;
     }
     reg::fft<H, +1, KB>(v, tt, b, b0, b1, tw);
@@ -135,14 +135,14 @@ __global__ void __launch_bounds__(ColGeo<H>::NT, col_min_blocks(H, ColGeo<H>::NT
   }
 }
 
-// Synthesis gather: partial[label][slot] = sum over a run of items of one
-// tile of W_f * column-forward(Y_f), stored compactly as [H][8]; the next
+// Synthesis gather: partial[slot] = sum over a run of items of one (label,
+// tile) of W_f * column-forward(Y_v), stored compactly as [H][KB]; the next
 // item's coefficient tile is requested while the current transform runs.
 template <int H>
 __global__ void __launch_bounds__(ColGeo<H>::NT, col_min_blocks(H, ColGeo<H>::NT))
     k_fcol_gather(const float2* __restrict__ Y, const float* __restrict__ bank, const WorkItem* __restrict__ items,
-                  const int* __restrict__ cta_begin, float2* __restrict__ partial, int Wh, int Whp, int nslots,
-                  int label, int f0, const float2* __restrict__ twH) {
+                  const int* __restrict__ cta_begin, float2* __restrict__ partial, int Wh, int Whp, int l0, int f0,
+                  int nf, const float2* __restrict__ twH) {
   extern __shared__ float2 sm[];
   float2* tw = sm;  // per-pass twiddles
   float2* b0 = sm + reg::Passes<H>::TWSIZE;
@@ -162,13 +162,13 @@ __global__ void __launch_bounds__(ColGeo<H>::NT, col_min_blocks(H, ColGeo<H>::NT
   load_pass_table<H, 1>(tw, twH);
   pdl_wait();
   pdl_trigger();
-  load_tile8<H>(y, Y + Pp * it.filter, Whp, tt, col, ok);
+  load_tile8<H>(y, Y + Pp * ((it.label - l0) * nf + (it.filter - f0)), Whp, tt, col, ok);
   __syncthreads();
   for (int i = ib; i < ie; ++i) {
     float2 v[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) v[k] = y[k];
-    load_bank8<H>(w, bank + Pb * (f0 + it.filter), Wh, tt, col, ok);
+    load_bank8<H>(w, bank + Pb * it.filter, Wh, tt, col, ok);
     WorkItem nx = it;
     int ncol = col;
     bool nok = ok;
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(ColGeo<H>::NT, col_min_blocks(H, ColGeo<H>::NT
       nx = items[i + 1];
       ncol = nx.tile * KB + b;
       nok = ncol < Wh;
-      load_tile8<H>(y, Y + Pp * nx.filter, Whp, tt, ncol, nok);
+      load_tile8<H>(y, Y + Pp * ((nx.label - l0) * nf + (nx.filter - f0)), Whp, tt, ncol, nok);
     }
     reg::fft<H, -1, KB>(v, tt, b, b0, b1, tw);
 #pragma unroll
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(ColGeo<H>::NT, col_min_blocks(H, ColGeo<H>::NT
       acc[k].y = fmaf(w[k], v[k].y, acc[k].y);
     }
     if (i + 1 == ie || nx.slot != it.slot) {
-      float2* dst = partial + (static_cast<size_t>(label) * nslots + it.slot) * H * KB + b;
+      float2* dst = partial + static_cast<size_t>(it.slot) * H * KB + b;
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         dst[static_cast<size_t>(tt + k * (H / 8)) * KB] = acc[k];
@@ -218,7 +218,7 @@ struct ReduceGeo {
 template <int H>
 __global__ void __launch_bounds__(ReduceGeo<H>::RG * ColGeo<H>::NT) k_fcol_reduce_inv(
     const float2* __restrict__ partial, const int* __restrict__ tile_begin, const int* __restrict__ tile_slots,
-    float2* __restrict__ T, int Wh, int nslots, const float2* __restrict__ twH) {
+    float2* __restrict__ T, int Wh, const float2* __restrict__ twH) {
   using RGeo = ReduceGeo<H>;
   constexpr int KB = ColGeo<H>::KB;
   constexpr int NT = ColGeo<H>::NT;
@@ -238,10 +238,11 @@ __global__ void __launch_bounds__(ReduceGeo<H>::RG * ColGeo<H>::NT) k_fcol_reduc
   load_pass_table<H, 1>(tw, twH);
   pdl_wait();
   pdl_trigger();
-  const int s0 = tile_begin[tile], s1 = tile_begin[tile + 1], ns = s1 - s0;
+  const int lt0 = label * gridDim.x + tile;  // the (label, tile) slot list
+  const int s0 = tile_begin[lt0], s1 = tile_begin[lt0 + 1], ns = s1 - s0;
   const int a0 = s0 + ns * grp / RGeo::RG, a1 = s0 + ns * (grp + 1) / RGeo::RG;
   for (int si = a0; si < a1; ++si) {
-    const float2* src = partial + (static_cast<size_t>(label) * nslots + tile_slots[si]) * H * KB + b;
+    const float2* src = partial + static_cast<size_t>(tile_slots[si]) * H * KB + b;
 #pragma unroll
     for (int k = 0; k < 8; ++k) v[k] = c_add(v[k], src[static_cast<size_t>(tt + k * (H / 8)) * KB]);
   }
@@ -323,12 +324,12 @@ cudaError_t col_fwd(const Geo& g, const float2* Ur, float2* uhat, int K, int Whp
 }
 
 cudaError_t col_fan(const Geo& g, int nc, const float2* uhat, const WorkItem* items, const int* cta_begin,
-                    float2* Y, int Whp, int label, int f0, cudaStream_t st) {
+                    float2* Y, int Whp, const Wave& wv, cudaStream_t st) {
   switch (g.H) {
 #define SHF_CASE(N)                                                                                              \
   case N:                                                                                                        \
     return launch_pdl(k_fcol_fan<N>, dim3(nc), dim3(ColGeo<N>::NT), col_smem<N>(), st, uhat, g.bank, items, cta_begin, Y, \
-                      g.Wh, Whp, label, f0, g.twH);
+                      g.Wh, Whp, wv.l0, wv.f0, wv.nf, g.twH);
     SHF_COL_SIZES(SHF_CASE)
 #undef SHF_CASE
     default: return cudaErrorInvalidValue;
@@ -336,12 +337,12 @@ cudaError_t col_fan(const Geo& g, int nc, const float2* uhat, const WorkItem* it
 }
 
 cudaError_t col_gather(const Geo& g, int nc, const float2* Y, const WorkItem* items, const int* cta_begin,
-                       float2* partial, int Whp, int nslots, int label, int f0, cudaStream_t st) {
+                       float2* partial, int Whp, const Wave& wv, cudaStream_t st) {
   switch (g.H) {
 #define SHF_CASE(N)                                                                                           \
   case N:                                                                                                     \
     return launch_pdl(k_fcol_gather<N>, dim3(nc), dim3(ColGeo<N>::NT), col_smem<N>(), st, Y, g.bank, items, cta_begin, \
-                      partial, g.Wh, Whp, nslots, label, f0, g.twH);
+                      partial, g.Wh, Whp, wv.l0, wv.f0, wv.nf, g.twH);
     SHF_COL_SIZES(SHF_CASE)
 #undef SHF_CASE
     default: return cudaErrorInvalidValue;
@@ -349,14 +350,14 @@ cudaError_t col_gather(const Geo& g, int nc, const float2* Y, const WorkItem* it
 }
 
 cudaError_t col_reduce(const Geo& g, const float2* partial, const int* tile_begin, const int* tile_slots, float2* T,
-                       int K, int nslots, cudaStream_t st) {
+                       int K, cudaStream_t st) {
   const int tw = reg::col_batch(g.H), ntiles = (g.Wh + tw - 1) / tw;
   switch (g.H) {
 #define SHF_CASE(N)                                                                                          \
   case N:                                                                                                    \
     return launch_pdl(k_fcol_reduce_inv<N>, dim3(ntiles, K), dim3(ReduceGeo<N>::RG * ColGeo<N>::NT),             \
                       sizeof(float2) * ReduceGeo<N>::TOTAL, st, partial, tile_begin,                                  \
-                      tile_slots, T, g.Wh, nslots, g.twH);
+                      tile_slots, T, g.Wh, g.twH);
     SHF_COL_SIZES(SHF_CASE)
 #undef SHF_CASE
     default: return cudaErrorInvalidValue;

@@ -109,7 +109,8 @@ __device__ __forceinline__ signed char clip_code(float g, float t) {
 // tpart[(label eta + f) H + row] (each thread sums its 16 terms in FP32 in a
 // fixed order; the group's partials are added in FP64 in thread order); the
 // new bvbar is transformed back in place (the input of S^T).
-// Rows r = (filter fl, row) with r = fl H + row over the wave's nf filters;
+// Rows r = (pair fl, row) with r = fl H + row over the wave's nv (label,
+// filter) pairs, fl = (label - l0) nf + (f - f0);
 // resident CTAs, each row group takes rows gid, gid + G, ... (G groups in
 // all).  While a group transforms its row, the next row's spectrum columns
 // (only the filter's column tiles [c0, c1]) and b_v row are copied into the
@@ -120,8 +121,9 @@ __device__ __forceinline__ signed char clip_code(float g, float t) {
 template <int L, int MODE>
 __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 : 768) / RowGeo<L>::NTH)
     k_wrow_vstep(float2* __restrict__ Y, float* __restrict__ bv, const float* __restrict__ thr,
-                 const int2* __restrict__ ranges, int H, int Whp, int eta, int label, int f0, int nf, float scale,
-                 const float2* __restrict__ twW, signed char* __restrict__ code, double* __restrict__ tpart) {
+                 const int2* __restrict__ ranges, int H, int Whp, int eta, int l0, int f0, int nf, int nv,
+                 float scale, const float2* __restrict__ twW, signed char* __restrict__ code,
+                 double* __restrict__ tpart) {
   using SM = RowGroupSmem<L, MODE>;
   constexpr int T = SM::T;
   constexpr int RPC = SM::RPC;
@@ -141,8 +143,14 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 
   const int bar = 1 + grp;
   const int G = gridDim.x * RPC;
   const int gid = blockIdx.x * RPC + grp;
-  const int rows = nf * H;
+  const int rows = nv * H;
   const int niter = (rows + G - 1) / G;  // the same for every group: dead rows still take part in barriers
+  // label and filter of pair fl
+  auto pair_of = [&](int fl, int& lab, int& f) {
+    const int q = fl / nf;
+    lab = l0 + q;
+    f = f0 + fl - q * nf;
+  };
   const uint64_t pol = evict_first_policy();
   const size_t W = 2 * static_cast<size_t>(L);
   // the column kernels write whole tiles of reg::col_batch(H) columns: the
@@ -163,8 +171,10 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 
   // request row (fl, row)'s spectrum columns (its filter's column range
   // only) and its b_v row (and codes) into the stage
   auto request_x = [&](int fl, int row) {
-    if (fl >= nf || !act) return;
-    const int2 rg = ranges[f0 + fl];
+    if (fl >= nv || !act) return;
+    int lab, f;
+    pair_of(fl, lab, f);
+    const int2 rg = ranges[f];
     if (rg.x <= rg.y) {
       const int c0 = rg.x & ~cmask;
       const int c1e = min(Whp, (rg.y | cmask) + 1);
@@ -173,8 +183,10 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 
     }
   };
   auto request_b = [&](int fl, int row) {
-    if (fl >= nf || !act) return;
-    const size_t rix = (static_cast<size_t>(label) * eta + f0 + fl) * H + row;
+    if (fl >= nv || !act) return;
+    int lab, f;
+    pair_of(fl, lab, f);
+    const size_t rix = (static_cast<size_t>(lab) * eta + f) * H + row;
     const float2* B = reinterpret_cast<const float2*>(bv) + rix * L;
     for (int q = tt; q < L / 2; q += T) cp_async16(sB + 2 * q, B + 2 * q, true, pol);
     if (MODE == 1) {  // 2L bytes of codes: L/8 = T chunks of 16 bytes
@@ -194,8 +206,10 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 
   request_x(flc, rowc);
   __syncthreads();
   for (int it = 0; it < niter; ++it) {
-    const bool live = flc < nf;
-    const int fl = live ? flc : 0, row = live ? rowc : 0, f = f0 + fl;
+    const bool live = flc < nv;
+    const int fl = live ? flc : 0, row = live ? rowc : 0;
+    int label, f;
+    pair_of(fl, label, f);
     int fln = flc, rown = rowc;  // the group's next row
     advance(fln, rown);
     const int2 rg = ranges[f];
@@ -332,8 +346,8 @@ struct Row16Geo {
 template <int L>
 __global__ void __launch_bounds__(256, 2)
     k_wrow_vstep16(float2* __restrict__ Y, float* __restrict__ bv, const float* __restrict__ thr,
-                   const int2* __restrict__ ranges, int H, int Whp, int eta, int label, int f0, int nf, float scale,
-                   const float2* __restrict__ twW, signed char* __restrict__ code) {
+                   const int2* __restrict__ ranges, int H, int Whp, int eta, int l0, int f0, int nf, int nv,
+                   float scale, const float2* __restrict__ twW, signed char* __restrict__ code) {
   using G = Row16Geo<L>;
   constexpr int T = G::T;
   constexpr int RPC = G::RPC;
@@ -349,8 +363,14 @@ __global__ void __launch_bounds__(256, 2)
   float2* sB = fb + G::BUF;
   const int Gn = gridDim.x * RPC;
   const int gid = blockIdx.x * RPC + grp;
-  const int rows = nf * H;
+  const int rows = nv * H;
   const int niter = (rows + Gn - 1) / Gn;  // the same for every group: every lane takes part in the shuffles
+  // label and filter of pair fl
+  auto pair_of = [&](int fl, int& lab, int& f) {
+    const int q = fl / nf;
+    lab = l0 + q;
+    f = f0 + fl - q * nf;
+  };
   const uint64_t pol = evict_first_policy();
   const size_t W = 2 * static_cast<size_t>(L);
   const int cmask = reg::col_batch(H) - 1;
@@ -364,8 +384,10 @@ __global__ void __launch_bounds__(256, 2)
     }
   };
   auto request_b = [&](int fl, int row) {
-    if (fl >= nf) return;
-    const size_t rix = (static_cast<size_t>(label) * eta + f0 + fl) * H + row;
+    if (fl >= nv) return;
+    int lab, f;
+    pair_of(fl, lab, f);
+    const size_t rix = (static_cast<size_t>(lab) * eta + f) * H + row;
     const float2* B = reinterpret_cast<const float2*>(bv) + rix * L;
 #pragma unroll
     for (int q = tt; q < L / 2; q += T) cp_async16(sB + 2 * q, B + 2 * q, true, pol);
@@ -379,8 +401,10 @@ __global__ void __launch_bounds__(256, 2)
   pdl_trigger();
   __syncthreads();
   for (int it = 0; it < niter; ++it) {
-    const bool live = flc < nf;
-    const int fl = live ? flc : 0, row = live ? rowc : 0, f = f0 + fl;
+    const bool live = flc < nv;
+    const int fl = live ? flc : 0, row = live ? rowc : 0;
+    int label, f;
+    pair_of(fl, label, f);
     int fln = flc, rown = rowc;
     advance(fln, rown);
     const int2 rg = ranges[f];
@@ -759,29 +783,31 @@ int row_groups_per_cta(int L, int mode) {
   }
 }
 
-cudaError_t row_shrink(const Geo& g, int ctas, float2* Y, float* bv, const float* thr, int Whp, int label, int f0,
-                       int nf, float scale, signed char* code, cudaStream_t st) {
+cudaError_t row_shrink(const Geo& g, int ctas, float2* Y, float* bv, const float* thr, int Whp, const Wave& wv,
+                       float scale, signed char* code, cudaStream_t st) {
   switch (g.L) {
 #define SHF_CASE(N)                                                                                              \
   case N:                                                                                                        \
     if (use_r16(N))                                                                                              \
       return launch_pdl(k_wrow_vstep16<(use_r16(N) ? N : 64)>, dim3(ctas), dim3(256), vstep16_smem<N>(), st, Y, \
-                        bv, thr, g.ranges, g.H, Whp, g.eta, label, f0, nf, scale, g.twW, code);                  \
+                        bv, thr, g.ranges, g.H, Whp, g.eta, wv.l0, wv.f0, wv.nf, wv.nv, scale, g.twW, code);   \
     return launch_pdl(k_wrow_vstep<N, 0>, dim3(ctas), dim3(RowGeo<N>::NTH), vstep_smem<N, 0>(), st, Y, bv, thr, \
-                      g.ranges, g.H, Whp, g.eta, label, f0, nf, scale, g.twW, code, static_cast<double*>(nullptr));
+                      g.ranges, g.H, Whp, g.eta, wv.l0, wv.f0, wv.nf, wv.nv, scale, g.twW, code,                  \
+                      static_cast<double*>(nullptr));
     SHF_FAST_SIZES(SHF_CASE)
 #undef SHF_CASE
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t row_adjoint(const Geo& g, int ctas, float2* Y, float* bvbar, const float* thr, int Whp, int label, int f0,
-                        int nf, float scale, const signed char* code, double* tpart, cudaStream_t st) {
+cudaError_t row_adjoint(const Geo& g, int ctas, float2* Y, float* bvbar, const float* thr, int Whp, const Wave& wv,
+                        float scale, const signed char* code, double* tpart, cudaStream_t st) {
   switch (g.L) {
 #define SHF_CASE(N)                                                                                                  \
   case N:                                                                                                            \
     return launch_pdl(k_wrow_vstep<N, 1>, dim3(ctas), dim3(RowGeo<N>::NTH), vstep_smem<N, 1>(), st, Y, bvbar, thr, \
-                      g.ranges, g.H, Whp, g.eta, label, f0, nf, scale, g.twW, const_cast<signed char*>(code), tpart);
+                      g.ranges, g.H, Whp, g.eta, wv.l0, wv.f0, wv.nf, wv.nv, scale, g.twW,                        \
+                      const_cast<signed char*>(code), tpart);
     SHF_FAST_SIZES(SHF_CASE)
 #undef SHF_CASE
     default: return cudaErrorInvalidValue;

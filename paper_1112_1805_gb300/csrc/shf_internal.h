@@ -114,38 +114,46 @@ struct LaunchHook {
   }
 };
 
-// Static work list of the fast path.  The (column tile, filter) pairs of a
-// wave whose filter support touches the tile (fast_tile(g) half-spectrum columns) are
-// listed in (tile, filter) order and cut into one contiguous, balanced range
-// per CTA of a column launch, with as many CTAs as are resident at once.
-// Within a CTA's range, each run of one tile is one partial-sum slot of the
-// synthesis; the slots of a tile are summed in filter order.
+// Static work list of the fast path.  A wave is a set of (label, filter)
+// pairs whose coefficient spectra stay in L2 between its three launches: the
+// filters [f0, f0 + nf) of one label when a label's spectra exceed the wave
+// budget, else whole labels [l0, l0 + nl) (nf = eta), so that small images
+// fill the GPU with fewer, larger launches.  The wave's spectra are indexed by
+// v = (label - l0) nf + (f - f0).  Its (label, column tile, filter) items whose
+// filter support touches the tile (fast_tile(g) half-spectrum columns) are
+// listed in that order and cut into one contiguous, balanced range per CTA of
+// a column launch, with as many CTAs as are resident at once.  Within a CTA's
+// range, each run of one (label, tile) is one partial-sum slot of the
+// synthesis; the slots of a (label, tile) are summed in filter order.
 struct WorkItem {
   int tile;    // column tile
-  int filter;  // wave-local filter index
-  int slot;    // partial-sum slot of the item's run (within its label)
-  int pad;
+  int filter;  // filter index (0..eta-1)
+  int slot;    // partial-sum slot of the item's run
+  int label;
 };
-constexpr int kDefaultWaveMiB = 64;  // coefficient spectra per wave of filters
+constexpr int kDefaultWaveMiB = 64;  // coefficient spectra per wave
 struct FastPlan {
   int wave_mib = kDefaultWaveMiB;
   int col_ctas_per_sm = 0;  // CTAs per SM of the column launches (0: as many as fit)
   int col_ctas = 0;         // resolved: CTAs of one column launch
   int row_ctas = 0;         // resolved: resident CTAs of the row (v-step) launch
+  std::vector<int> wave_l0, wave_nl;  // per wave: first label, number of labels
   std::vector<int> wave_f0, wave_nf;  // per wave: first filter, number of filters
   std::vector<int> wave_cta0;         // per wave: first entry of cta_begin (size waves + 1)
-  int nslots = 0;                     // partial slots per label (all waves)
+  int y_planes = 0;                   // spectra planes of the largest wave (max nl nf)
+  int nslots = 0;                     // partial slots in all (every wave and label)
   const WorkItem* items = nullptr;    // device, all waves
   const int* cta_begin = nullptr;     // device, item range [cta_begin[c], cta_begin[c+1]) of CTA c
-  const int* tile_begin = nullptr;    // device [ntiles + 1], into tile_slots
-  const int* tile_slots = nullptr;    // device, slots of each tile in filter order
+  const int* tile_begin = nullptr;    // device [K ntiles + 1], into tile_slots, per (label, tile)
+  const int* tile_slots = nullptr;    // device, slots of each (label, tile) in filter order
 };
 
 // Fast path for power-of-two sizes (shf_fast.cu).
 bool fast_path_ok(const Geo& g);
 int fast_tile(const Geo& g);  // columns per tile of the fast column kernels (8, or 4 for H > 1024)
 cudaError_t prepare_fast_kernels();
-int fast_wave(const Geo& g, int wave_mib);  // filters per wave
+int fast_wave(const Geo& g, int wave_mib);  // filters per wave of one label (at most eta)
+int fast_wave_labels(const Geo& g, int wave_mib, int K);  // labels per wave (1: waves of filters)
 int fast_pitch(const Geo& g);       // row pitch (complex) of the internal spectra: Wh rounded up to 8
 bool fast_ustep_ok(const Geo& g, int K);
 // u-step, w-step, b_w update and row spectra of u (power-of-two sizes, K <= 8).
@@ -171,10 +179,10 @@ cudaError_t run_fast_adjoint_body(const Geo& g, const FastPlan& plan, const floa
 int fast_col_ctas(const Geo& g, int per_sm);
 // Resident CTAs of the row (v-step) kernel.
 int fast_row_ctas(const Geo& g);
-// Host construction of the work list from the filters' column ranges
-// (ranges_host[eta]) for plan->wave_mib and plan->col_ctas; returns the host
-// arrays to upload (cta_begin holds one entry more per wave).
-void build_fast_plan(const Geo& g, const int2* ranges_host, FastPlan* plan, std::vector<WorkItem>* items,
+// Host construction of the work list of K labels from the filters' column
+// ranges (ranges_host[eta]) for plan->wave_mib and plan->col_ctas; returns the
+// host arrays to upload (cta_begin holds one entry more per wave).
+void build_fast_plan(const Geo& g, const int2* ranges_host, int K, FastPlan* plan, std::vector<WorkItem>* items,
                      std::vector<int>* cta_begin, std::vector<int>* tile_begin, std::vector<int>* tile_slots);
 
 // Reverse mode of the unrolled iteration (shf_adjoint.cu).

@@ -272,7 +272,7 @@ def run_ours(args):
     fb = FilterBank(wl.H, wl.W, wl.J)
     seg = ShearletSegmenter(fb, f_dev, wl.codebook(), wl.Lambda(), wl.gamma)
     # work plan: autotuned on this image before the timed region (iterate restored)
-    plan = seg.plan() if args.no_tune else seg.tune(3)
+    plan = seg.plan() if args.no_tune else seg.tune(10)
     labels_dev = torch.empty((wl.H, wl.W), dtype=torch.int32, device="cuda")
     st = seg.stream
     units_per_step = wl.H * wl.W * wl.K * wl.iters
@@ -402,7 +402,7 @@ def measure_batch(iters: int, steps: int, warmup_steps: int, warmup_iters: int, 
         units += H * W * K * iters
     batch = ShearletBatch(imgs, cbs, lams, 1.0)
     if tune:
-        batch.tune(3)
+        batch.tune(5)
     for _ in range(warmup_steps):
         batch.step(warmup_iters)
     batch.synchronize()

@@ -170,10 +170,12 @@ int seg_admm_step(seg_state* st, int n_iters);
 /* ---------------------------------------------------------------------------
  * Work plan and autotuner (no counterpart in the paper: how the iteration of
  * Sec. 3 is cut into kernel launches).  Power-of-two sizes (fast = 1) run the
- * register-FFT kernels over waves of filters whose coefficient spectra stay in
- * L2 (wave_mib); each column launch runs col_ctas_per_sm resident CTAs per SM
- * (0: as many as fit), each on a balanced range of the wave's (column tile,
- * filter) pairs.  Other sizes (fast = 0) run the general kernels with tiles of
+ * register-FFT kernels over waves of (label, filter) pairs whose coefficient
+ * spectra take about wave_mib MiB: the filters of one label when a label's
+ * spectra exceed the budget, else whole labels (as many as fit, balanced), so
+ * that one launch of each kernel covers several labels; each column launch
+ * runs col_ctas_per_sm resident CTAs per SM (0: as many as fit), each on a
+ * balanced range of the wave's (label, column tile, filter) triples.  Other sizes (fast = 0) run the general kernels with tiles of
  * tile_cols half-spectrum columns and tile_rows rows and `groups` filter
  * groups in the synthesis sums.  Fields of the other path are 0 in
  * seg_admm_get_plan and ignored by seg_admm_set_plan.  The plan changes the

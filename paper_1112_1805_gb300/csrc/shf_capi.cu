@@ -92,6 +92,7 @@ struct seg_state {
   cudaGraphExec_t exec = nullptr;        // one iteration
   cudaGraphExec_t exec_timed = nullptr;  // the same with an event before every launch
   bool graph_tried = false;
+  bool untimed = false;  // steps record no per-kernel events (the tuner's trials)
   bool fast = false;          // power-of-two sizes: the shf_fast.cu kernels
   bool fast_ustep = false;    // ... including the u/w-step (K <= 8)
   shf::FastPlan plan;         // fast path: static per-wave work list
@@ -750,7 +751,7 @@ int seg_admm_step(seg_state* st, int n) {
   if (!st->graph_tried) try_capture(st);
   // the last iteration of the call records the per-kernel timing events
   for (int i = 0; i < n; ++i) {
-    const bool timed = i == n - 1;
+    const bool timed = i == n - 1 && !st->untimed;
     if (st->exec) {
       SHF_CK(cudaGraphLaunch(timed && st->exec_timed ? st->exec_timed : st->exec, st->stream));
     } else {
@@ -794,7 +795,14 @@ namespace {
 
 // Mean time (microseconds) of one iteration over `iters` replays, after one
 // warm-up iteration that also captures the graphs.
+// Average time of `iters` iterations of the plain graph (without the event
+// nodes of the timed iteration, which cost differently per plan).
 int time_iterations(seg_state* st, int iters, float* us) {
+  st->untimed = true;
+  struct Restore {
+    seg_state* st;
+    ~Restore() { st->untimed = false; }
+  } restore{st};
   int rc = seg_admm_step(st, 1);
   if (rc) return rc;
   cudaEvent_t a = nullptr, b = nullptr;
@@ -825,7 +833,7 @@ std::vector<seg_plan> plan_candidates(const seg_state* st, const seg_plan& base,
       // wave budgets that give distinct waves (filters per wave of one label,
       // or labels per wave)
       std::vector<int> seen;
-      for (int mib : {16, 32, 64, 96, 128, 192}) {
+      for (int mib : {16, 32, 64, 96, 128, 192, 256, 384}) {
         const int w = shf::fast_wave(g, mib), nl = shf::fast_wave_labels(g, mib, st->K);
         const int sig = nl > 1 ? -nl : (g.eta + w - 1) / w;
         if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;

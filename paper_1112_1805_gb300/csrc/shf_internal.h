@@ -131,7 +131,7 @@ struct WorkItem {
   int slot;    // partial-sum slot of the item's run
   int label;
 };
-constexpr int kDefaultWaveMiB = 64;  // coefficient spectra per wave
+constexpr int kDefaultWaveMiB = 128;  // coefficient spectra per wave
 struct FastPlan {
   int wave_mib = kDefaultWaveMiB;
   int col_ctas_per_sm = 0;  // CTAs per SM of the column launches (0: as many as fit)

@@ -69,7 +69,8 @@ FAST_PLANS = [dict(wave_mib=1, col_ctas_per_sm=1), dict(wave_mib=1, col_ctas_per
 
 def test_fast_plans_match_oracle(torch_mod, oracle_mod):
     # 128 x 256, J = 3 (29 filters, 0.13 MiB of spectra per filter): 1 MiB
-    # waves give 5 waves per label, 64 MiB one wave
+    # waves give 5 waves per label, 2 MiB 2 waves per label, 64 MiB and 4096
+    # MiB one wave of all three labels
     img, cb, Lam = _problem(128, 256, 3, 3, 31)
     T = 12
     o = _oracle(oracle_mod, img, cb, 3, Lam, T)

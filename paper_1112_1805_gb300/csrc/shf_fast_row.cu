@@ -329,26 +329,33 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 
 // is in the other warp, and X_{L-n} is read from L2 and Z_{L-i} through the
 // exchange buffer.
 // ---------------------------------------------------------------------------
-template <int L>
+template <int L, int MODE = 0>
 struct Row16Geo {
   static constexpr int T = L / 16;
   static constexpr int GPW = T <= 32 ? 32 / T : 0;          // groups per warp (T <= 32)
   static constexpr int NTH = 256;
   static constexpr int RPC = T <= 32 ? 8 * GPW : NTH / T;    // groups per CTA
   static constexpr int BUF = even2(reg::row_buf(L));         // exchange buffer
-  static constexpr int RAW = BUF + L;                        // + b_v stage (L float2)
+  static constexpr int SC = MODE == 1 ? L / 4 : 0;           // adjoint: codes of the row (2L bytes)
+  static constexpr int SD = MODE == 1 ? even2(T) : 0;        // adjoint: one double per thread
+  static constexpr int RAW = BUF + L + SC + SD;              // + b_v (or its adjoint) stage (L float2)
   static constexpr int STRIDE = T >= 16 ? RAW : RAW + ((T - RAW % 16) % 16 + 16) % 16;
   static constexpr int TW = even2(L + 1);                    // exp(-2 pi i m / W), m <= L
   static constexpr int PT = even2(r16::Passes<L>::TWSIZE);   // per-pass twiddles
   static constexpr int TOTAL = TW + PT + RPC * STRIDE;       // float2 per CTA
 };
 
-template <int L>
+// MODE 0: the v-step (with optional codes); MODE 1: its adjoint, as MODE 1 of
+// k_wrow_vstep (codes staged with the b_v row; each thread sums its 32
+// threshold terms in FP32 in a fixed order, the group's partials are added in
+// FP64 in thread order).
+template <int L, int MODE>
 __global__ void __launch_bounds__(256, 2)
     k_wrow_vstep16(float2* __restrict__ Y, float* __restrict__ bv, const float* __restrict__ thr,
                    const int2* __restrict__ ranges, int H, int Whp, int eta, int l0, int f0, int nf, int nv,
-                   float scale, const float2* __restrict__ twW, signed char* __restrict__ code) {
-  using G = Row16Geo<L>;
+                   float scale, const float2* __restrict__ twW, signed char* __restrict__ code,
+                   double* __restrict__ tpart) {
+  using G = Row16Geo<L, MODE>;
   constexpr int T = G::T;
   constexpr int RPC = G::RPC;
   extern __shared__ __align__(16) float2 sm[];
@@ -361,6 +368,8 @@ __global__ void __launch_bounds__(256, 2)
   const int bar = 1 + grp;                                               // named barrier (T = 64)
   float2* fb = pt + G::PT + grp * G::STRIDE;
   float2* sB = fb + G::BUF;
+  const char2* sC = reinterpret_cast<const char2*>(sB + L);
+  double* sD = reinterpret_cast<double*>(sB + L + G::SC);
   const int Gn = gridDim.x * RPC;
   const int gid = blockIdx.x * RPC + grp;
   const int rows = nv * H;
@@ -391,6 +400,11 @@ __global__ void __launch_bounds__(256, 2)
     const float2* B = reinterpret_cast<const float2*>(bv) + rix * L;
 #pragma unroll
     for (int q = tt; q < L / 2; q += T) cp_async16(sB + 2 * q, B + 2 * q, true, pol);
+    if (MODE == 1) {  // 2L bytes of codes: L/8 = 2T chunks of 16 bytes
+      const signed char* Cr = code + rix * (2 * static_cast<size_t>(L));
+#pragma unroll
+      for (int q = tt; q < L / 8; q += T) cp_async16(sB + L + 2 * q, Cr + 16 * q, true, pol);
+    }
   };
 
   int flc = gid / H, rowc = gid - flc * H;
@@ -449,21 +463,43 @@ __global__ void __launch_bounds__(256, 2)
     r16::group_sync<L>(bar);     // ... and the group's
     if (live) {
       float2* b2 = reinterpret_cast<float2*>(bv) + rix * L;
+      if constexpr (MODE == 0) {
 #pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const float2 bo = sB[tt + k * T];
-        const float gx = fmaf(scale, v[k].x, bo.x), gy = fmaf(scale, v[k].y, bo.y);
-        const float cx = fminf(fmaxf(gx, -th), th), cy = fminf(fmaxf(gy, -th), th);
-        __stcs(b2 + tt + k * T, make_float2(cx, cy));
-        if (code)
-          reinterpret_cast<char2*>(code + rix * W)[tt + k * T] = make_char2(clip_code(gx, th), clip_code(gy, th));
-        v[k] = make_float2(gx - 2.f * cx, gy - 2.f * cy);
+        for (int k = 0; k < 16; ++k) {
+          const float2 bo = sB[tt + k * T];
+          const float gx = fmaf(scale, v[k].x, bo.x), gy = fmaf(scale, v[k].y, bo.y);
+          const float cx = fminf(fmaxf(gx, -th), th), cy = fminf(fmaxf(gy, -th), th);
+          __stcs(b2 + tt + k * T, make_float2(cx, cy));
+          if (code)
+            reinterpret_cast<char2*>(code + rix * W)[tt + k * T] = make_char2(clip_code(gx, th), clip_code(gy, th));
+          v[k] = make_float2(gx - 2.f * cx, gy - 2.f * cy);
+        }
+      } else {
+        float tacc = 0.f;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const float2 bo = sB[tt + k * T];
+          const char2 m = sC[tt + k * T];
+          const float dx = scale * v[k].x, dy = scale * v[k].y;
+          const float nx = m.x == 0 ? bo.x - dx : dx;
+          const float ny = m.y == 0 ? bo.y - dy : dy;
+          tacc = fmaf(static_cast<float>(m.x), fmaf(-2.f, dx, bo.x), tacc);
+          tacc = fmaf(static_cast<float>(m.y), fmaf(-2.f, dy, bo.y), tacc);
+          __stcs(b2 + tt + k * T, make_float2(nx, ny));
+          v[k] = make_float2(nx, ny);
+        }
+        sD[tt] = static_cast<double>(tacc);
       }
     } else {
 #pragma unroll
       for (int k = 0; k < 16; ++k) v[k] = make_float2(0.f, 0.f);
     }
     r16::group_sync<L>(bar);  // the b_v stage is read: refill it with the group's next row
+    if (MODE == 1 && live && tt == 0) {  // the row's threshold sum, in thread order
+      double sum = 0.0;
+      for (int j = 0; j < T; ++j) sum += sD[j];
+      tpart[rix] = sum;
+    }
     request_b(fln, rown);
     r16::row_fft<L, -1>(v, tt, fb, pt, bar);
     if constexpr (T <= 32) {
@@ -705,21 +741,24 @@ size_t ustep_smem(int K) {
                            static_cast<size_t>(K) * UG::rows(K) * L);
 }
 
-// Half widths served by the radix-16 v-step (the adjoint keeps the 8-value
-// kernel for every length).
+// Half widths served by the radix-16 v-step and its adjoint.
 __host__ __device__ constexpr bool use_r16(int L) { return L == 64 || L == 128 || L == 256 || L == 512 || L == 1024; }
+// the radix-16 instance of a dispatch case (a valid placeholder where not used)
+__host__ __device__ constexpr int r16_len(int L) { return use_r16(L) ? L : 64; }
 
-template <int L>
+template <int L, int MODE>
 size_t vstep16_smem() {
-  return sizeof(float2) * Row16Geo<(use_r16(L) ? L : 64)>::TOTAL;
+  return sizeof(float2) * Row16Geo<r16_len(L), MODE>::TOTAL;
 }
 
 template <int L>
 cudaError_t prepare_row_t() {
   cudaError_t e = allow_smem(k_wrow_vstep<L, 0>, vstep_smem<L, 0>());
   if (e == cudaSuccess) e = allow_smem(k_wrow_vstep<L, 1>, vstep_smem<L, 1>());
-  if constexpr (use_r16(L))
-    if (e == cudaSuccess) e = allow_smem(k_wrow_vstep16<L>, vstep16_smem<L>());
+  if constexpr (use_r16(L)) {
+    if (e == cudaSuccess) e = allow_smem(k_wrow_vstep16<L, 0>, vstep16_smem<L, 0>());
+    if (e == cudaSuccess) e = allow_smem(k_wrow_vstep16<L, 1>, vstep16_smem<L, 1>());
+  }
   // the u/w-step's shared memory depends on K (rows per CTA): the largest over
   // the K each instance serves (2..4 and 5..8)
   size_t m4 = 0, m8 = 0;
@@ -757,13 +796,18 @@ int row_ctas_per_sm(int L, int mode) {
   int fit = 0;
   cudaError_t e = cudaErrorInvalidValue;
   switch (L) {
-#define SHF_OCC(N)                                                                                                  \
-  case N:                                                                                                           \
-    if (mode == 0 && use_r16(N))                                                                                    \
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_vstep16<(use_r16(N) ? N : 64)>, 256,           \
-                                                        vstep16_smem<N>());                                         \
-    else                                                                                                            \
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_vstep<N, 0>, RowGeo<N>::NTH, vstep_smem<N, 0>()); \
+#define SHF_OCC(N)                                                                                              \
+  case N:                                                                                                       \
+    if (use_r16(N))                                                                                             \
+      e = mode == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_vstep16<r16_len(N), 0>, 256,   \
+                                                                    vstep16_smem<N, 0>())                       \
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_vstep16<r16_len(N), 1>, 256,   \
+                                                                    vstep16_smem<N, 1>());                      \
+    else                                                                                                        \
+      e = mode == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_vstep<N, 0>, RowGeo<N>::NTH,   \
+                                                                    vstep_smem<N, 0>())                         \
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_vstep<N, 1>, RowGeo<N>::NTH,   \
+                                                                    vstep_smem<N, 1>());                        \
     break;
     SHF_FAST_SIZES(SHF_OCC)
 #undef SHF_OCC
@@ -773,10 +817,11 @@ int row_ctas_per_sm(int L, int mode) {
 }
 
 int row_groups_per_cta(int L, int mode) {
+  (void)mode;  // the same row groups in both modes
   switch (L) {
 #define SHF_CASE(N) \
   case N:           \
-    return mode == 0 && use_r16(N) ? Row16Geo<(use_r16(N) ? N : 64)>::RPC : RowGeo<N>::RPC;
+    return use_r16(N) ? Row16Geo<r16_len(N)>::RPC : RowGeo<N>::RPC;
     SHF_FAST_SIZES(SHF_CASE)
 #undef SHF_CASE
     default: return 0;
@@ -786,13 +831,14 @@ int row_groups_per_cta(int L, int mode) {
 cudaError_t row_shrink(const Geo& g, int ctas, float2* Y, float* bv, const float* thr, int Whp, const Wave& wv,
                        float scale, signed char* code, cudaStream_t st) {
   switch (g.L) {
-#define SHF_CASE(N)                                                                                              \
-  case N:                                                                                                        \
-    if (use_r16(N))                                                                                              \
-      return launch_pdl(k_wrow_vstep16<(use_r16(N) ? N : 64)>, dim3(ctas), dim3(256), vstep16_smem<N>(), st, Y, \
-                        bv, thr, g.ranges, g.H, Whp, g.eta, wv.l0, wv.f0, wv.nf, wv.nv, scale, g.twW, code);   \
-    return launch_pdl(k_wrow_vstep<N, 0>, dim3(ctas), dim3(RowGeo<N>::NTH), vstep_smem<N, 0>(), st, Y, bv, thr, \
-                      g.ranges, g.H, Whp, g.eta, wv.l0, wv.f0, wv.nf, wv.nv, scale, g.twW, code,                  \
+#define SHF_CASE(N)                                                                                                \
+  case N:                                                                                                          \
+    if (use_r16(N))                                                                                                \
+      return launch_pdl(k_wrow_vstep16<r16_len(N), 0>, dim3(ctas), dim3(256), vstep16_smem<N, 0>(), st, Y, bv,    \
+                        thr, g.ranges, g.H, Whp, g.eta, wv.l0, wv.f0, wv.nf, wv.nv, scale, g.twW, code,            \
+                        static_cast<double*>(nullptr));                                                            \
+    return launch_pdl(k_wrow_vstep<N, 0>, dim3(ctas), dim3(RowGeo<N>::NTH), vstep_smem<N, 0>(), st, Y, bv, thr,   \
+                      g.ranges, g.H, Whp, g.eta, wv.l0, wv.f0, wv.nf, wv.nv, scale, g.twW, code,                    \
                       static_cast<double*>(nullptr));
     SHF_FAST_SIZES(SHF_CASE)
 #undef SHF_CASE
@@ -805,6 +851,10 @@ cudaError_t row_adjoint(const Geo& g, int ctas, float2* Y, float* bvbar, const f
   switch (g.L) {
 #define SHF_CASE(N)                                                                                                  \
   case N:                                                                                                            \
+    if (use_r16(N))                                                                                                  \
+      return launch_pdl(k_wrow_vstep16<r16_len(N), 1>, dim3(ctas), dim3(256), vstep16_smem<N, 1>(), st, Y, bvbar,   \
+                        thr, g.ranges, g.H, Whp, g.eta, wv.l0, wv.f0, wv.nf, wv.nv, scale, g.twW,                    \
+                        const_cast<signed char*>(code), tpart);                                                      \
     return launch_pdl(k_wrow_vstep<N, 1>, dim3(ctas), dim3(RowGeo<N>::NTH), vstep_smem<N, 1>(), st, Y, bvbar, thr, \
                       g.ranges, g.H, Whp, g.eta, wv.l0, wv.f0, wv.nf, wv.nv, scale, g.twW,                        \
                       const_cast<signed char*>(code), tpart);

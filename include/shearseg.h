@@ -175,8 +175,9 @@ int seg_admm_step(seg_state* st, int n_iters);
  * spectra exceed the budget, else whole labels (as many as fit, balanced), so
  * that one launch of each kernel covers several labels; each column launch
  * runs col_ctas_per_sm resident CTAs per SM (0: as many as fit), each on a
- * balanced range of the wave's (label, column tile, filter) triples.  Other sizes (fast = 0) run the general kernels with tiles of
- * tile_cols half-spectrum columns and tile_rows rows and `groups` filter
+ * balanced range of the wave's (label, column tile, filter) triples.  Other
+ * sizes (fast = 0) run the general kernels with tiles of tile_cols
+ * half-spectrum columns and tile_rows rows and `groups` filter
  * groups in the synthesis sums.  Fields of the other path are 0 in
  * seg_admm_get_plan and ignored by seg_admm_set_plan.  The plan changes the
  * grouping of the FP32 synthesis sums (wave_mib, col_ctas_per_sm, groups), so
@@ -202,7 +203,8 @@ int seg_admm_get_plan(const seg_state* st, seg_plan* out);
  * stays), SHF_ERR_OOM. */
 int seg_admm_set_plan(seg_state* st, const seg_plan* p);
 
-/* Autotuner: times `iters` iterations (after one warm-up) of each candidate
+/* Autotuner: times `iters` iterations (after one warm-up; replays of the plain
+ * iteration graph, without the per-kernel timing events) of each candidate
  * plan, varying one parameter at a time around the best so far (fast: wave
  * budget, then col_ctas_per_sm; general: groups, then tile_cols, then
  * tile_rows), and installs the fastest.  The iterate and the iteration count

@@ -117,7 +117,8 @@ __device__ __forceinline__ signed char clip_code(float g, float t) {
 // group's stage; the twiddle tables are built once per CTA.  Column ranges
 // are widened to the column kernels' tiles (8 columns, or 4 for H > 1024).
 // Four CTAs of 256 threads per SM (64 registers) for powers of two; three for
-// L = 3 2^a or 5 2^a, whose radix-R pass holds more values.
+// L = 3 2^a or 5 2^a, whose radix-R pass holds more values.  The half widths
+// 64..1024 take k_wrow_vstep16 instead (below); this kernel serves the others.
 template <int L, int MODE>
 __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 : 768) / RowGeo<L>::NTH)
     k_wrow_vstep(float2* __restrict__ Y, float* __restrict__ bv, const float* __restrict__ thr,

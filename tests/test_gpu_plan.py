@@ -81,6 +81,19 @@ def test_fast_plans_match_oracle(torch_mod, oracle_mod):
         _check(o, g)
 
 
+def test_uneven_label_groups_match_oracle(torch_mod, oracle_mod):
+    # 64 x 64, J = 2 (13 filters, 20 KiB of spectra per filter), K = 5: a 1 MiB
+    # wave holds 51 planes, i.e. three whole labels, and the labels split into
+    # waves of 3 and 2; 4096 MiB puts all five in one wave
+    img, cb, Lam = _problem(64, 64, 5, 2, 35)
+    T = 15
+    o = _oracle(oracle_mod, img, cb, 2, Lam, T)
+    for p in (dict(wave_mib=1, col_ctas_per_sm=0), dict(wave_mib=4096, col_ctas_per_sm=1)):
+        g = _run(torch_mod, img, cb, 2, Lam, T, p)
+        assert g["plan"]["fast"] == 1 and g["plan"]["wave_mib"] == p["wave_mib"]
+        _check(o, g)
+
+
 def test_plan_is_bitwise_reproducible(torch_mod):
     img, cb, Lam = _problem(128, 256, 3, 3, 32)
     for p in (FAST_PLANS[0], FAST_PLANS[2]):

@@ -532,6 +532,154 @@ __global__ void __launch_bounds__(256, 2)
   cp_async_commit_wait_all();  // no copy outlives the kernel
 }
 
+// ---------------------------------------------------------------------------
+// v-step on pairs of rows (half widths L = 64, 128): rows r and r + 1 of
+// the same (label, filter) are one complex row z = a + i b of length W = 2L
+// (r16::pair_pack / pair_unpack), transformed by a group of T = W/16 <= 32
+// threads.  Against one half-length transform per row this drops the packing
+// twiddles and the packing shuffles, and half of the exchanges.
+// The b_v rows of a pair are contiguous (2W floats), staged by cp.async.
+// Forward mode only (optional codes); the adjoint keeps k_wrow_vstep16.
+// ---------------------------------------------------------------------------
+template <int L>
+struct PairGeo {
+  static constexpr int W = 2 * L;
+  static constexpr int T = W / 16;                           // threads per pair
+  static_assert(T <= 32, "pair groups inside one warp");
+  static constexpr int GPW = 32 / T;
+  static constexpr int NTH = 256;
+  static constexpr int RPC = 8 * GPW;                        // pair groups per CTA
+  static constexpr int BUF = even2(reg::row_buf(W));         // exchange buffer (length W)
+  static constexpr int RAW = BUF + W;                        // + the two b_v rows (W float2)
+  static constexpr int STRIDE = T >= 16 ? RAW : RAW + ((T - RAW % 16) % 16 + 16) % 16;
+  static constexpr int PT = even2(r16::Passes<W>::TWSIZE);  // per-pass twiddles (length W)
+  static constexpr int TOTAL = PT + RPC * STRIDE;            // float2 per CTA
+};
+
+template <int L>
+__global__ void __launch_bounds__(256, 2)
+    k_wrow_vstep2r(float2* __restrict__ Y, float* __restrict__ bv, const float* __restrict__ thr,
+                   const int2* __restrict__ ranges, int H, int Whp, int eta, int l0, int f0, int nf, int nv,
+                   float scale, const float2* __restrict__ twW, signed char* __restrict__ code) {
+  using G = PairGeo<L>;
+  constexpr int T = G::T, W = G::W;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* pt = sm;
+  const int lane = threadIdx.x & 31;
+  const int tt = lane & (T - 1);
+  const int grp = threadIdx.x / T;
+  const int partner = (lane - tt) + ((T - tt) & (T - 1));
+  float2* fb = pt + G::PT + grp * G::STRIDE;
+  float* sB = reinterpret_cast<float*>(fb + G::BUF);  // b_v rows r, r + 1: 2W floats
+  const int Hp = H / 2;                               // row pairs per (label, filter)
+  const int Gn = gridDim.x * G::RPC;
+  const int gid = blockIdx.x * G::RPC + grp;
+  const int pairs = nv * Hp;
+  const int niter = (pairs + Gn - 1) / Gn;  // the same for every group: every lane takes part in the shuffles
+  auto pair_of = [&](int fl, int& lab, int& f) {
+    const int q = fl / nf;
+    lab = l0 + q;
+    f = f0 + fl - q * nf;
+  };
+  const uint64_t pol = evict_first_policy();
+  const int cmask = reg::col_batch(H) - 1;
+  const int gq = Gn / Hp, gr = Gn - gq * Hp;
+  auto advance = [&](int& fl, int& pr) {
+    fl += gq;
+    pr += gr;
+    if (pr >= Hp) {
+      pr -= Hp;
+      ++fl;
+    }
+  };
+  auto request_b = [&](int fl, int pr) {
+    if (fl >= nv) return;
+    int lab, f;
+    pair_of(fl, lab, f);
+    const size_t rix = (static_cast<size_t>(lab) * eta + f) * H + 2 * pr;
+    const float* B = bv + rix * W;
+#pragma unroll
+    for (int q = tt; q < W / 2; q += T) cp_async16(sB + 4 * q, B + 4 * q, true, pol);
+  };
+
+  int flc = gid / Hp, prc = gid - flc * Hp;
+  request_b(flc, prc);  // b_v was last written by an earlier, completed grid
+  r16::build_pass_twiddles<W, 1>(pt, twW, threadIdx.x, blockDim.x);
+  pdl_wait();
+  pdl_trigger();
+  __syncthreads();
+  for (int it = 0; it < niter; ++it) {
+    const bool live = flc < nv;
+    const int fl = live ? flc : 0, pr = live ? prc : 0;
+    int label, f;
+    pair_of(fl, label, f);
+    int fln = flc, prn = prc;
+    advance(fln, prn);
+    const int2 rg = ranges[f];
+    const bool any = live && rg.x <= rg.y;
+    const int c0 = any ? (rg.x & ~cmask) : L + 1;
+    const int c1 = any ? min(L, (rg.y | cmask)) : -1;
+    const float th = thr[f];
+    const size_t rix = (static_cast<size_t>(label) * eta + f) * H + 2 * pr;  // row a; row b = rix + 1
+    float2* Xa = Y + (static_cast<size_t>(fl) * H + 2 * pr) * Whp;
+    float2* Xb = Xa + Whp;
+    // Z[n] = Xa[n] + i Xb[n] (n <= L), conj Xa[W-n] + i conj Xb[W-n] (n > L)
+    float2 v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int n = tt + k * T;
+      const bool up = n > L;
+      const int m = up ? W - n : n;
+      const bool in = m >= c0 && m <= c1;
+      const float2 xa = in ? __ldcg(Xa + m) : make_float2(0.f, 0.f);
+      const float2 xb = in ? __ldcg(Xb + m) : make_float2(0.f, 0.f);
+      v[k] = r16::pair_pack(xa, xb, up);
+    }
+    r16::row_fft<W, +1>(v, tt, fb, pt, 0);
+    cp_async_commit_wait_all();  // this lane's part of the b_v rows
+    __syncwarp();                // ... and the group's
+    if (live) {
+      float* b2 = bv + rix * W;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int m = tt + k * T;
+        const float ga = fmaf(scale, v[k].x, sB[m]), gb = fmaf(scale, v[k].y, sB[W + m]);
+        const float ca = fminf(fmaxf(ga, -th), th), cb = fminf(fmaxf(gb, -th), th);
+        __stcs(b2 + m, ca);
+        __stcs(b2 + W + m, cb);
+        if (code) {
+          code[rix * W + m] = clip_code(ga, th);
+          code[(rix + 1) * W + m] = clip_code(gb, th);
+        }
+        v[k] = make_float2(ga - 2.f * ca, gb - 2.f * cb);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[k] = make_float2(0.f, 0.f);
+    }
+    __syncwarp();  // the b_v stage is read: refill it with the group's next pair
+    request_b(fln, prn);
+    r16::row_fft<W, -1>(v, tt, fb, pt, 0);
+    // Xa[k], Xb[k] for k = tt + q T <= L from D_k (register q) and D_{W-k}
+#pragma unroll
+    for (int q = 0; q <= 8; ++q) {
+      float2 r;
+      r.x = __shfl_sync(0xffffffffu, v[15 - q].x, partner);
+      r.y = __shfl_sync(0xffffffffu, v[15 - q].y, partner);
+      const int k = tt + q * T;
+      if (k >= c0 && k <= c1) {
+        float2 xa, xb;
+        r16::pair_unpack(v[q], r16::pair_partner(tt, r, v[(16 - q) & 15]), xa, xb);
+        Xa[k] = xa;
+        Xb[k] = xb;
+      }
+    }
+    flc = fln;
+    prc = prn;
+  }
+  cp_async_commit_wait_all();  // no copy outlives the kernel
+}
+
 // Euclidean projection of g[0..K) onto the unit simplex, as the paper
 // constructs it: project onto the hyperplane sum = 1 (g + (1 - sum g)/q), set
 // the negative components to zero and repeat on the remaining ones (at most K
@@ -752,6 +900,18 @@ size_t vstep16_smem() {
   return sizeof(float2) * Row16Geo<r16_len(L), MODE>::TOTAL;
 }
 
+// Half widths whose forward v-step runs on pairs of rows: 64 and 128, where a
+// pair takes one exchange where two single rows take two (measured: the
+// unrolled 256^2 sweeps 1695 -> 1745 Mpixel*label*iter/s).  At 256 a pair
+// needs three passes where a row needs two, and the one-row kernel is faster
+// (v-step 156 against 164 us per 512^2 iteration).
+__host__ __device__ constexpr bool use_pair(int L) { return L == 64 || L == 128; }
+__host__ __device__ constexpr int pair_len(int L) { return use_pair(L) ? L : 64; }
+template <int L>
+size_t pair_smem() {
+  return sizeof(float2) * PairGeo<pair_len(L)>::TOTAL;
+}
+
 template <int L>
 cudaError_t prepare_row_t() {
   cudaError_t e = allow_smem(k_wrow_vstep<L, 0>, vstep_smem<L, 0>());
@@ -760,6 +920,8 @@ cudaError_t prepare_row_t() {
     if (e == cudaSuccess) e = allow_smem(k_wrow_vstep16<L, 0>, vstep16_smem<L, 0>());
     if (e == cudaSuccess) e = allow_smem(k_wrow_vstep16<L, 1>, vstep16_smem<L, 1>());
   }
+  if constexpr (use_pair(L))
+    if (e == cudaSuccess) e = allow_smem(k_wrow_vstep2r<L>, pair_smem<L>());
   // the u/w-step's shared memory depends on K (rows per CTA): the largest over
   // the K each instance serves (2..4 and 5..8)
   size_t m4 = 0, m8 = 0;
@@ -799,7 +961,9 @@ int row_ctas_per_sm(int L, int mode) {
   switch (L) {
 #define SHF_OCC(N)                                                                                              \
   case N:                                                                                                       \
-    if (use_r16(N))                                                                                             \
+    if (mode == 0 && use_pair(N))                                                                               \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_vstep2r<pair_len(N)>, 256, pair_smem<N>());  \
+    else if (use_r16(N))                                                                                        \
       e = mode == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_vstep16<r16_len(N), 0>, 256,   \
                                                                     vstep16_smem<N, 0>())                       \
                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_vstep16<r16_len(N), 1>, 256,   \
@@ -818,10 +982,11 @@ int row_ctas_per_sm(int L, int mode) {
 }
 
 int row_groups_per_cta(int L, int mode) {
-  (void)mode;  // the same row groups in both modes
   switch (L) {
-#define SHF_CASE(N) \
-  case N:           \
+#define SHF_CASE(N)                                        \
+  case N:                                                  \
+    if (mode == 0 && use_pair(N))                          \
+      return 2 * PairGeo<pair_len(N)>::RPC; /* rows */     \
     return use_r16(N) ? Row16Geo<r16_len(N)>::RPC : RowGeo<N>::RPC;
     SHF_FAST_SIZES(SHF_CASE)
 #undef SHF_CASE
@@ -834,6 +999,9 @@ cudaError_t row_shrink(const Geo& g, int ctas, float2* Y, float* bv, const float
   switch (g.L) {
 #define SHF_CASE(N)                                                                                                \
   case N:                                                                                                          \
+    if (use_pair(N))                                                                                               \
+      return launch_pdl(k_wrow_vstep2r<pair_len(N)>, dim3(ctas), dim3(256), pair_smem<N>(), st, Y, bv, thr,      \
+                        g.ranges, g.H, Whp, g.eta, wv.l0, wv.f0, wv.nf, wv.nv, scale, g.twW, code);              \
     if (use_r16(N))                                                                                                \
       return launch_pdl(k_wrow_vstep16<r16_len(N), 0>, dim3(ctas), dim3(256), vstep16_smem<N, 0>(), st, Y, bv,    \
                         thr, g.ranges, g.H, Whp, g.eta, wv.l0, wv.f0, wv.nf, wv.nv, scale, g.twW, code,            \

@@ -208,6 +208,30 @@ __host__ __device__ __forceinline__ float2 unpack_value(const float2 (&v)[16], i
   return make_float2(0.5f * (s2.x + t.y), 0.5f * (s2.y - t.x));
 }
 
+// Two real rows a, b of length W as one complex row z = a + i b, transformed
+// with length W.  Spectrum of z from the half spectra Xa, Xb (k = 0 .. W/2):
+// Z[n] = Xa[n] + i Xb[n] for n <= W/2 and Z[n] = conj Xa[W-n] + i conj Xb[W-n]
+// above; `upper` selects the second form (xa, xb then hold Xa[W-n], Xb[W-n]).
+__host__ __device__ __forceinline__ float2 pair_pack(float2 xa, float2 xb, bool upper) {
+  return upper ? make_float2(xa.x + xb.y, xb.x - xa.y) : make_float2(xa.x - xb.y, xa.y + xb.x);
+}
+
+// Half spectra of the rows from D = FFT(d_a + i d_b): Xa[k] = (D_k + conj D_{W-k})/2,
+// Xb[k] = (D_k - conj D_{W-k})/(2i); dm = D_{W-k}.
+__host__ __device__ __forceinline__ void pair_unpack(float2 dk, float2 dm, float2& xa, float2& xb) {
+  const float2 c = c_conj(dm);
+  const float2 s2 = c_add(dk, c), t = c_sub(dk, c);
+  xa = make_float2(0.5f * s2.x, 0.5f * s2.y);
+  xb = make_float2(0.5f * t.y, -0.5f * t.x);
+}
+
+// The register of the partner lane holding D_{W-k} for k = tt + q T (stride
+// layout of a length-N = 16 T transform): register 15 - q of lane (T - tt)
+// mod T, or, on lane 0, its own register (16 - q) mod 16 (given as `own`).
+__host__ __device__ __forceinline__ float2 pair_partner(int tt, float2 from_partner, float2 own) {
+  return tt == 0 ? own : from_partner;
+}
+
 #ifdef __CUDACC__
 // Barrier of a row group: the warp for T <= 32 (all lanes of the warp take
 // part), else the named barrier `id` over the group's T threads (whole warps).

@@ -1,5 +1,6 @@
 // Host-side check of the radix-16 row FFT building blocks (shf_fft16.cuh)
-// against FP64 DFTs, for the half widths 64, 128, 256, 512 and 1024.  A row group
+// against FP64 DFTs, for the half widths 64, 128, 256, 512 and 1024, and the
+// two-rows-per-transform packing for widths 128, 256 and 512.  A row group
 // of T threads is emulated lane by lane, phase by phase, exactly as the kernel
 // sequences them between warp barriers: butterflies, Stockham stores to the
 // padded group buffer, stride reads, and the packing steps with each lane's
@@ -127,4 +128,69 @@ static int check() {
   return ok ? 0 : 1;
 }
 
-int main() { return check<64>() + check<128>() + check<256>() + check<512>() + check<1024>(); }
+// Two real rows as one complex row of length W (r16::pair_pack / pair_unpack):
+// packing + inverse gives W (a + i b); forward + unpacking gives both half
+// spectra back.
+template <int W>
+static int check_pair() {
+  using PS = r16::Passes<W>;
+  constexpr int T = PS::T, L = W / 2;
+  std::vector<float2> tw(W);
+  for (int m = 0; m < W; ++m) tw[m] = make_float2(std::cos(-2 * M_PI * m / W), std::sin(-2 * M_PI * m / W));
+  std::vector<float2> pt(PS::TWSIZE);
+  r16::build_pass_twiddles<W, 1>(pt.data(), tw.data(), 0, 1);
+  std::vector<float2> buf(reg::row_buf(W), make_float2(NAN, NAN));
+  std::mt19937 rng(2 * W + 1);
+  std::normal_distribution<double> nd;
+  std::vector<double> a(W), b(W);
+  for (int m = 0; m < W; ++m) a[m] = nd(rng), b[m] = nd(rng);
+  std::vector<cd> Xa(L + 1), Xb(L + 1);
+  for (int k = 0; k <= L; ++k) {
+    cd sa = 0, sb = 0;
+    for (int m = 0; m < W; ++m) {
+      const cd e = std::polar(1.0, -2 * M_PI * double(k) * m / W);
+      sa += a[m] * e;
+      sb += b[m] * e;
+    }
+    Xa[k] = sa, Xb[k] = sb;
+  }
+  auto f2 = [](cd z) { return make_float2(float(z.real()), float(z.imag())); };
+  std::vector<Regs> V(T);
+  for (int tt = 0; tt < T; ++tt)
+    for (int k = 0; k < 16; ++k) {
+      const int n = tt + k * T;
+      const bool up = n > L;
+      const int m = up ? W - n : n;
+      V[tt][k] = r16::pair_pack(f2(Xa[m]), f2(Xb[m]), up);
+    }
+  group_fft<W, +1>(V, buf, pt.data());
+  double e_inv = 0;
+  for (int m = 0; m < W; ++m) {
+    const float2 g = V[m % T][m / T];
+    e_inv = std::max(e_inv, std::abs(cd(g.x, g.y) / double(W) - cd(a[m], b[m])));
+  }
+  for (auto& r : V)
+    for (auto& z : r) z = c_scale(z, 1.f / W);
+  group_fft<W, -1>(V, buf, pt.data());
+  double e_fwd = 0, xmax = 0;
+  for (int tt = 0; tt < T; ++tt)
+    for (int q = 0; q <= 8; ++q) {
+      const int k = tt + q * T;
+      if (k > L) continue;
+      const float2 dm = r16::pair_partner(tt, V[(T - tt) & (T - 1)][15 - q], V[tt][(16 - q) & 15]);
+      float2 xa, xb;
+      r16::pair_unpack(V[tt][q], dm, xa, xb);
+      e_fwd = std::max(e_fwd, std::max(std::abs(cd(xa.x, xa.y) - Xa[k]), std::abs(cd(xb.x, xb.y) - Xb[k])));
+    }
+  for (int k = 0; k <= L; ++k) xmax = std::max(xmax, std::max(std::abs(Xa[k]), std::abs(Xb[k])));
+  const double eps = 6e-8, lg = std::log2(double(W));
+  const bool ok = e_inv < 10 * eps * lg * 4 && e_fwd < 10 * eps * lg * xmax;
+  std::printf("pair W=%d T=%d inverse %.2e forward %.2e (|X| <= %.1f) %s\n", W, T, e_inv, e_fwd, xmax,
+              ok ? "ok" : "FAIL");
+  return ok ? 0 : 1;
+}
+
+int main() {
+  return check<64>() + check<128>() + check<256>() + check<512>() + check<1024>() + check_pair<128>() +
+         check_pair<256>() + check_pair<512>();
+}

@@ -173,9 +173,10 @@ int seg_admm_step(seg_state* st, int n_iters);
  * register-FFT kernels over waves of (label, filter) pairs whose coefficient
  * spectra take about wave_mib MiB: the filters of one label when a label's
  * spectra exceed the budget, else whole labels (as many as fit, balanced), so
- * that one launch of each kernel covers several labels; each column launch
- * runs col_ctas_per_sm resident CTAs per SM (0: as many as fit), each on a
- * balanced range of the wave's (label, column tile, filter) triples.  Other
+ * that one launch of each kernel covers several labels; each synthesis
+ * (gather) launch runs col_ctas_per_sm resident CTAs per SM (0: as many as
+ * fit) and each analysis (fan) launch as many as fit, each CTA on a balanced
+ * range of the wave's (label, column tile, filter) triples.  Other
  * sizes (fast = 0) run the general kernels with tiles of tile_cols
  * half-spectrum columns and tile_rows rows and `groups` filter
  * groups in the synthesis sums.  Fields of the other path are 0 in
@@ -187,7 +188,7 @@ int seg_admm_step(seg_state* st, int n_iters);
 typedef struct {
   int fast;          /* read-only: 1 power-of-two path, 0 general path        */
   int wave_mib;      /* fast: MiB of coefficient spectra per wave, [1, 4096]  */
-  int col_ctas_per_sm; /* fast: column CTAs per SM, [0, 32], 0 = all that fit */
+  int col_ctas_per_sm; /* fast: gather CTAs per SM, [0, 32], 0 = all that fit */
   int tile_cols;     /* general: half-spectrum columns per column tile        */
   int tile_rows;     /* general: rows per row block                           */
   int groups;        /* general: filter groups of the synthesis partial sums  */

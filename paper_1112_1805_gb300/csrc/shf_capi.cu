@@ -493,8 +493,10 @@ int install_fast_plan(seg_state* st, int wave_mib, int col_ctas_per_sm) {
   plan.wave_mib = wave_mib;
   plan.col_ctas_per_sm = col_ctas_per_sm;
   plan.col_ctas = shf::fast_col_ctas(g, col_ctas_per_sm);
+  plan.fan_ctas = shf::fast_fan_ctas(g);
   plan.row_ctas = shf::fast_row_ctas(g);
-  if (plan.col_ctas < 1 || plan.row_ctas < 1) return fail(SHF_ERR_CUDA, "install_fast_plan: no resident CTA");
+  if (plan.col_ctas < 1 || plan.fan_ctas < 1 || plan.row_ctas < 1)
+    return fail(SHF_ERR_CUDA, "install_fast_plan: no resident CTA");
   std::vector<shf::WorkItem> h_items;
   std::vector<int> h_cta_begin, h_tile_begin, h_tile_slots;
   shf::build_fast_plan(g, st->ranges_host.data(), st->K, &plan, &h_items, &h_cta_begin, &h_tile_begin,

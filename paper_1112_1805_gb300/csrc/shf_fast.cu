@@ -92,6 +92,8 @@ int fast_col_ctas(const Geo& g, int per_sm) {
 
 int fast_row_ctas(const Geo& g) { return fast::row_ctas_per_sm(g.L) * sm_count(); }
 
+int fast_fan_ctas(const Geo& g) { return fast::fan_ctas_per_sm(g.H) * sm_count(); }
+
 void build_fast_plan(const Geo& g, const int2* ranges, int K, FastPlan* plan, std::vector<WorkItem>* items,
                      std::vector<int>* cta_begin, std::vector<int>* tile_begin, std::vector<int>* tile_slots) {
   const int tw = fast_tile(g), ntiles = (g.Wh + tw - 1) / tw;
@@ -103,6 +105,7 @@ void build_fast_plan(const Geo& g, const int2* ranges, int K, FastPlan* plan, st
   plan->wave_f0.clear();
   plan->wave_nf.clear();
   plan->wave_cta0.clear();
+  plan->wave_fcta0.clear();
   plan->y_planes = 0;
   // the waves: label groups of whole labels, or per label the filter waves
   const int nl = fast_wave_labels(g, plan->wave_mib, K);
@@ -153,6 +156,20 @@ void build_fast_plan(const Geo& g, const int2* ranges, int K, FastPlan* plan, st
     }
   }
   plan->wave_cta0.push_back(static_cast<int>(cta_begin->size()) - static_cast<int>(plan->wave_cta0.size()));
+  // the fan's ranges over the same items, for its own number of CTAs
+  {
+    const int fctas = plan->fan_ctas > 0 ? plan->fan_ctas : ctas;
+    size_t first = 0;
+    for (size_t w = 0; w < plan->wave_f0.size(); ++w) {
+      const int c0 = plan->wave_cta0[w] + static_cast<int>(w), c1 = plan->wave_cta0[w + 1] + static_cast<int>(w) + 1;
+      const long n = (*cta_begin)[c1 - 1] - (*cta_begin)[c0];  // the wave's items
+      first = static_cast<size_t>((*cta_begin)[c0]);
+      const int G = static_cast<int>(std::min<long>(fctas, n));
+      plan->wave_fcta0.push_back(static_cast<int>(cta_begin->size()) - static_cast<int>(plan->wave_fcta0.size()));
+      for (int c = 0; c <= G; ++c) cta_begin->push_back(static_cast<int>(first + (G > 0 ? n * c / G : 0)));
+    }
+    plan->wave_fcta0.push_back(static_cast<int>(cta_begin->size()) - static_cast<int>(plan->wave_fcta0.size()));
+  }
   plan->nslots = slot;
   tile_begin->assign(1, 0);
   tile_slots->clear();
@@ -176,9 +193,11 @@ cudaError_t run_fast_iteration_body(const Geo& g, const FastPlan& plan, const fl
     const fast::Wave wv{plan.wave_l0[w], plan.wave_f0[w], plan.wave_nf[w], plan.wave_nl[w] * plan.wave_nf[w]};
     const int c0 = plan.wave_cta0[w], nc = plan.wave_cta0[w + 1] - c0;
     const int* cb = plan.cta_begin + c0 + w;  // each wave's ranges end with one extra entry
-    if (nc > 0) {
+    const int f0c = plan.wave_fcta0[w], nfc = plan.wave_fcta0[w + 1] - f0c;
+    const int* fcb = plan.cta_begin + f0c + w;
+    if (nfc > 0) {
       hook.mark(kKindFan);
-      e = fast::col_fan(g, nc, uhat, plan.items, cb, Y, Whp, wv, st);
+      e = fast::col_fan(g, nfc, uhat, plan.items, fcb, Y, Whp, wv, st);
     }
     hook.mark(kKindShrink);
     const int groups = (wv.nv * g.H + rpc - 1) / rpc;
@@ -206,7 +225,9 @@ cudaError_t run_fast_adjoint_body(const Geo& g, const FastPlan& plan, const floa
     const fast::Wave wv{plan.wave_l0[w], plan.wave_f0[w], plan.wave_nf[w], plan.wave_nl[w] * plan.wave_nf[w]};
     const int c0 = plan.wave_cta0[w], nc = plan.wave_cta0[w + 1] - c0;
     const int* cb = plan.cta_begin + c0 + w;
-    if (nc > 0) e = fast::col_fan(g, nc, uhat, plan.items, cb, Y, Whp, wv, st);
+    const int f0c = plan.wave_fcta0[w], nfc = plan.wave_fcta0[w + 1] - f0c;
+    const int* fcb = plan.cta_begin + f0c + w;
+    if (nfc > 0) e = fast::col_fan(g, nfc, uhat, plan.items, fcb, Y, Whp, wv, st);
     const int groups = (wv.nv * g.H + rpc - 1) / rpc;
     const int ctas = std::min(groups, std::max(actas, 1));
     if (e == cudaSuccess) e = fast::row_adjoint(g, ctas, Y, bvbar, thr, Whp, wv, scale, code, tpart, st);

@@ -68,7 +68,8 @@ struct Wave {
 
 // Column kernels (shf_fast_col.cu).  Whp: row pitch of the internal spectra.
 cudaError_t prepare_col_kernels();
-int col_ctas_per_sm(int H);  // resident CTAs per SM of the fan/gather kernels
+int col_ctas_per_sm(int H);  // resident CTAs per SM of the gather kernel
+int fan_ctas_per_sm(int H);  // resident CTAs per SM of the fan kernel
 // Ur [K][H][Wh] -> uhat [K][H][Whp]: column-forward of the row spectra of u.
 cudaError_t col_fwd(const Geo& g, const float2* Ur, float2* uhat, int K, int Whp, cudaStream_t st);
 // Y_v = column-inverse(W_f * uhat_label) on the (label, tile, filter) items of

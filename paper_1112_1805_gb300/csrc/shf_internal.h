@@ -122,7 +122,8 @@ struct LaunchHook {
 // v = (label - l0) nf + (f - f0).  Its (label, column tile, filter) items whose
 // filter support touches the tile (fast_tile(g) half-spectrum columns) are
 // listed in that order and cut into one contiguous, balanced range per CTA of
-// a column launch, with as many CTAs as are resident at once.  Within a CTA's
+// a column launch (separately for the fan and the gather, which run different
+// numbers of resident CTAs).  Within a CTA's
 // range, each run of one (label, tile) is one partial-sum slot of the
 // synthesis; the slots of a (label, tile) are summed in filter order.
 struct WorkItem {
@@ -135,11 +136,13 @@ constexpr int kDefaultWaveMiB = 128;  // coefficient spectra per wave
 struct FastPlan {
   int wave_mib = kDefaultWaveMiB;
   int col_ctas_per_sm = 0;  // CTAs per SM of the column launches (0: as many as fit)
-  int col_ctas = 0;         // resolved: CTAs of one column launch
+  int col_ctas = 0;         // resolved: CTAs of one gather launch
+  int fan_ctas = 0;         // resolved: CTAs of one fan launch (all resident)
   int row_ctas = 0;         // resolved: resident CTAs of the row (v-step) launch
   std::vector<int> wave_l0, wave_nl;  // per wave: first label, number of labels
   std::vector<int> wave_f0, wave_nf;  // per wave: first filter, number of filters
-  std::vector<int> wave_cta0;         // per wave: first entry of cta_begin (size waves + 1)
+  std::vector<int> wave_cta0;         // per wave: first entry of its gather ranges in cta_begin (size waves + 1)
+  std::vector<int> wave_fcta0;        // per wave: first entry of its fan ranges in cta_begin (size waves + 1)
   int y_planes = 0;                   // spectra planes of the largest wave (max nl nf)
   int nslots = 0;                     // partial slots in all (every wave and label)
   const WorkItem* items = nullptr;    // device, all waves
@@ -174,9 +177,10 @@ cudaError_t run_fast_iteration_body(const Geo& g, const FastPlan& plan, const fl
 cudaError_t run_fast_adjoint_body(const Geo& g, const FastPlan& plan, const float2* Qr, float2* uhat, float2* Y,
                                   float* bvbar, const float* thr, float2* partial, float2* Tbar, int K, float scale,
                                   const signed char* code, double* tpart, cudaStream_t st);
-// Resident CTAs of one column launch for `per_sm` CTAs per SM (0: as many
-// as fit; larger values are clamped to that).
+// Resident CTAs of one gather launch for `per_sm` CTAs per SM (0: as many
+// as fit; larger values are clamped to that), and of one fan launch.
 int fast_col_ctas(const Geo& g, int per_sm);
+int fast_fan_ctas(const Geo& g);
 // Resident CTAs of the row (v-step) kernel.
 int fast_row_ctas(const Geo& g);
 // Host construction of the work list of K labels from the filters' column

@@ -2,6 +2,7 @@
 // gather over the filters of a wave, and the forward/inverse column passes of
 // u and of the synthesis sum (Sec. 2, eq. for S and S^T; Sec. 3, ADMM steps).
 #include "shf_fast.h"
+#include "shf_fft16.cuh"
 
 namespace shf {
 namespace fast {
@@ -131,6 +132,79 @@ __global__ void __launch_bounds__(ColGeo<H>::NT, col_min_blocks(H, ColGeo<H>::NT
       float2* dst = Y + Pp * fl + ccol;
 #pragma unroll
       for (int k = 0; k < 8; ++k) dst[static_cast<size_t>(tt + k * (H / 8)) * Whp] = v[k];
+    }
+  }
+}
+
+// The analysis fan-out with 16 values per thread (heights 512 and 1024:
+// radix-16 column transforms, one exchange fewer at 1024): CTAs of 8 H/16
+// threads, thread (b, tt) holding rows tt + k H/16 of column b.  Measured at
+// 512 x 512: 3667 -> 3721 Mpixel*label*iter/s; at 256 (unrolled 256 x 256
+// sweeps) neutral, so 256 keeps the 8-value kernel.
+template <int H>
+struct Col16Geo {
+  static constexpr int KB = 8;
+  static constexpr int T = H / 16;
+  static constexpr int NT = KB * T;
+  static constexpr int PT = (r16::Passes<H>::TWSIZE + 1) & ~1;  // per-pass twiddles
+  static constexpr int BR = r16::brows16(H) * KB;                // one exchange buffer
+  static constexpr int TOTAL = PT + 2 * BR;
+};
+__host__ __device__ constexpr bool use_fan16(int H) { return H == 512 || H == 1024; }
+__host__ __device__ constexpr int fan16_len(int H) { return use_fan16(H) ? H : 512; }
+
+template <int H>
+__global__ void __launch_bounds__(Col16Geo<H>::NT, H == 512 ? 2 : 1)
+    k_fcol_fan16(const float2* __restrict__ uhat, const float* __restrict__ bank, const WorkItem* __restrict__ items,
+                 const int* __restrict__ cta_begin, float2* __restrict__ Y, int Wh, int Whp, int l0, int f0, int nf,
+                 const float2* __restrict__ twH) {
+  using G = Col16Geo<H>;
+  constexpr int KB = G::KB, T = G::T;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* pt = sm;
+  float2* b0 = sm + G::PT;
+  float2* b1 = b0 + G::BR;
+  const int ib = cta_begin[blockIdx.x], ie = cta_begin[blockIdx.x + 1];
+  if (ib >= ie) return;
+  const int b = threadIdx.x % KB, tt = threadIdx.x / KB;
+  const size_t Pb = static_cast<size_t>(H) * Wh, Pp = static_cast<size_t>(H) * Whp;
+  WorkItem it = items[ib];
+  int col = it.tile * KB + b;
+  bool ok = col < Wh;
+  float2 u[16];
+  float w[16];
+  auto load_w = [&](const float* wf, int c, bool o) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) w[k] = o ? __ldg(wf + static_cast<size_t>(tt + k * T) * Wh + c) : 0.f;
+  };
+  auto load_u = [&](const float2* src, int c, bool o) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) u[k] = o ? src[static_cast<size_t>(tt + k * T) * Whp + c] : make_float2(0.f, 0.f);
+  };
+  load_w(bank + Pb * it.filter, col, ok);
+  r16::build_pass_twiddles<H, 1>(pt, twH, threadIdx.x, blockDim.x);
+  pdl_wait();
+  pdl_trigger();
+  load_u(uhat + Pp * it.label, col, ok);
+  for (int i = ib; i < ie; ++i) {
+    float2 v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = c_scale(u[k], w[k]);
+    const int fl = (it.label - l0) * nf + (it.filter - f0), ccol = col;
+    const bool cok = ok;
+    if (i + 1 < ie) {
+      const WorkItem nx = items[i + 1];
+      col = nx.tile * KB + b;
+      ok = col < Wh;
+      load_w(bank + Pb * nx.filter, col, ok);
+      if (nx.tile != it.tile || nx.label != it.label) load_u(uhat + Pp * nx.label, col, ok);
+      it = nx;
+    }
+    r16::batch_fft<H, +1, KB>(v, tt, b, b0, b1, pt);  // starts with a CTA barrier (also after the twiddle table)
+    if (cok) {
+      float2* dst = Y + Pp * fl + ccol;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) dst[static_cast<size_t>(tt + k * T) * Whp] = v[k];
     }
   }
 }
@@ -280,11 +354,18 @@ size_t col_smem() {
   return sizeof(float2) * (reg::Passes<N>::TWSIZE + 2 * reg::batch_rows(N) * ColGeo<N>::KB);
 }
 
+template <int N>
+size_t fan16_smem() {
+  return sizeof(float2) * Col16Geo<fan16_len(N)>::TOTAL;
+}
+
 template <int H>
 cudaError_t prepare_col_t() {
   const size_t s = col_smem<H>();
   cudaError_t e = allow_smem(k_fcol_fwd<H>, s);
   if (e == cudaSuccess) e = allow_smem(k_fcol_fan<H>, s);
+  if constexpr (use_fan16(H))
+    if (e == cudaSuccess) e = allow_smem(k_fcol_fan16<H>, fan16_smem<H>());
   if (e == cudaSuccess) e = allow_smem(k_fcol_gather<H>, s);
   if (e == cudaSuccess) e = allow_smem(k_fcol_reduce_inv<H>, sizeof(float2) * ReduceGeo<H>::TOTAL);
   return e;
@@ -305,9 +386,13 @@ int fan_ctas_per_sm(int H) {
   int fit = 0;
   cudaError_t e = cudaErrorInvalidValue;
   switch (H) {
-#define SHF_OCC(N)                                                                                \
-  case N:                                                                                         \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_fcol_fan<N>, ColGeo<N>::NT, col_smem<N>()); \
+#define SHF_OCC(N)                                                                                          \
+  case N:                                                                                                   \
+    if (use_fan16(N))                                                                                       \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_fcol_fan16<fan16_len(N)>,                  \
+                                                        Col16Geo<fan16_len(N)>::NT, fan16_smem<N>());      \
+    else                                                                                                    \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_fcol_fan<N>, ColGeo<N>::NT, col_smem<N>()); \
     break;
     SHF_COL_SIZES(SHF_OCC)
 #undef SHF_OCC
@@ -348,6 +433,9 @@ cudaError_t col_fan(const Geo& g, int nc, const float2* uhat, const WorkItem* it
   switch (g.H) {
 #define SHF_CASE(N)                                                                                              \
   case N:                                                                                                        \
+    if (use_fan16(N))                                                                                            \
+      return launch_pdl(k_fcol_fan16<fan16_len(N)>, dim3(nc), dim3(Col16Geo<fan16_len(N)>::NT), fan16_smem<N>(),  \
+                        st, uhat, g.bank, items, cta_begin, Y, g.Wh, Whp, wv.l0, wv.f0, wv.nf, g.twH);           \
     return launch_pdl(k_fcol_fan<N>, dim3(nc), dim3(ColGeo<N>::NT), col_smem<N>(), st, uhat, g.bank, items, cta_begin, Y, \
                       g.Wh, Whp, wv.l0, wv.f0, wv.nf, g.twH);
     SHF_COL_SIZES(SHF_CASE)

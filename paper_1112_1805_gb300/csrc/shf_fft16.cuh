@@ -156,6 +156,34 @@ __host__ __device__ __forceinline__ void build_pass_twiddles(float2* pt, const f
   }
 }
 
+// Batch variants for the column transforms: a CTA transforms KB columns of
+// length N; thread (b, tt) holds v[k] = x_b[tt + k T] (T = N/16), and element i
+// of column b lives at (ridx(i)) KB + b of the exchange buffer.  Within a
+// half-warp (KB = 8: two consecutive tt; KB = 4: four) the stride reads are
+// consecutive rows and the span-1 stores are rows 17 apart, i.e. 8 (or 4)
+// banks apart per row: no bank conflicts.
+template <int N, int P, int KB>
+__host__ __device__ __forceinline__ void bpass_store(const float2 (&v)[16], int tt, int b, float2* out) {
+  using PS = Passes<N>;
+  constexpr int R = PS::radix(P), Ns = PS::span(P);
+  static_assert(R == 16, "only radix-16 passes are followed by an exchange");
+  const int o = (tt / Ns) * Ns * 16 + (tt & (Ns - 1));
+  float2* p = out + ridx(o) * KB + b;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) p[ridx(q * Ns) * KB] = v[q];
+}
+
+template <int N, int KB>
+__host__ __device__ __forceinline__ void bload_stride(float2 (&v)[16], int tt, int b, const float2* in) {
+  constexpr int T = Passes<N>::T;
+  const float2* p = in + (T % 16 == 0 ? ridx(tt) : tt) * KB + b;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = p[ridx(k * T) * KB];
+}
+
+// Rows of an exchange buffer of a length-N batch transform.
+__host__ __device__ constexpr int brows16(int N) { return ridx(N) + 1; }
+
 // Real rows of length W = 2L as complex rows of length L (z[n] = x[2n] + i x[2n+1]).
 // In the stride layout index L - (tt + k T) is register 15 - k of lane
 // (T - tt) mod T, and for lane 0 its own register 16 - k (k >= 1; index L for
@@ -241,6 +269,30 @@ __device__ __forceinline__ void group_sync(int id) {
     __syncwarp();
   } else {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(Passes<N>::T) : "memory");
+  }
+}
+
+// The transform of a CTA's KB columns (every thread of the CTA takes part;
+// two buffers, one CTA barrier per exchange plus one before the first, which
+// also covers the previous transform's reads); result in v, in the stride
+// layout.
+template <int N, int S, int KB>
+__device__ __forceinline__ void batch_fft(float2 (&v)[16], int tt, int b, float2* buf0, float2* buf1,
+                                          const float2* pt) {
+  using PS = Passes<N>;
+  pass_bfly<N, 0, S>(v, tt, pt);
+  if constexpr (PS::NPASS > 1) {
+    __syncthreads();
+    bpass_store<N, 0, KB>(v, tt, b, buf0);
+    __syncthreads();
+    bload_stride<N, KB>(v, tt, b, buf0);
+    pass_bfly<N, (PS::NPASS > 1 ? 1 : 0), S>(v, tt, pt);
+  }
+  if constexpr (PS::NPASS > 2) {
+    bpass_store<N, (PS::NPASS > 2 ? 1 : 0), KB>(v, tt, b, buf1);
+    __syncthreads();
+    bload_stride<N, KB>(v, tt, b, buf1);
+    pass_bfly<N, (PS::NPASS > 2 ? 2 : 0), S>(v, tt, pt);
   }
 }
 

@@ -1,6 +1,7 @@
 // Host-side check of the radix-16 row FFT building blocks (shf_fft16.cuh)
 // against FP64 DFTs, for the half widths 64, 128, 256, 512 and 1024, and the
-// two-rows-per-transform packing for widths 128, 256 and 512.  A row group
+// two-rows-per-transform packing for widths 128, 256 and 512, and the column
+// (batch) layout for heights 512 and 1024.  A row group
 // of T threads is emulated lane by lane, phase by phase, exactly as the kernel
 // sequences them between warp barriers: butterflies, Stockham stores to the
 // padded group buffer, stride reads, and the packing steps with each lane's
@@ -190,7 +191,56 @@ static int check_pair() {
   return ok ? 0 : 1;
 }
 
+// The column (batch) layout of r16::batch_fft: KB columns, element i of
+// column b at ridx(i) KB + b, thread (b, tt); checked against FP64 DFTs.
+template <int N, int KB>
+static int check_batch() {
+  using PS = r16::Passes<N>;
+  constexpr int T = PS::T;
+  std::vector<float2> tw(N);
+  for (int m = 0; m < N; ++m) tw[m] = make_float2(std::cos(-2 * M_PI * m / N), std::sin(-2 * M_PI * m / N));
+  std::vector<float2> pt(PS::TWSIZE);
+  r16::build_pass_twiddles<N, 1>(pt.data(), tw.data(), 0, 1);
+  std::vector<float2> buf0(r16::brows16(N) * KB, make_float2(NAN, NAN)), buf1 = buf0;
+  std::mt19937 rng(3 * N + KB);
+  std::normal_distribution<double> nd;
+  std::vector<std::vector<cd>> x(KB, std::vector<cd>(N));
+  for (auto& c : x)
+    for (auto& a : c) a = cd(nd(rng), nd(rng));
+  std::vector<Regs> V(T * KB);  // thread (b, tt) at tt * KB + b
+  for (int tt = 0; tt < T; ++tt)
+    for (int b = 0; b < KB; ++b)
+      for (int k = 0; k < 16; ++k) V[tt * KB + b][k] = make_float2(x[b][tt + k * T].real(), x[b][tt + k * T].imag());
+  // the phases of batch_fft<N, +1, KB> with every thread of the CTA in turn
+  auto bfly = [&](auto P) {
+    for (int t = 0; t < T * KB; ++t) r16::pass_bfly<N, decltype(P)::value, +1>(regs(V[t]), t / KB, pt.data());
+  };
+  bfly(std::integral_constant<int, 0>());
+  if constexpr (PS::NPASS > 1) {
+    for (int t = 0; t < T * KB; ++t) r16::bpass_store<N, 0, KB>(regs(V[t]), t / KB, t % KB, buf0.data());
+    for (int t = 0; t < T * KB; ++t) r16::bload_stride<N, KB>(regs(V[t]), t / KB, t % KB, buf0.data());
+    bfly(std::integral_constant<int, (PS::NPASS > 1 ? 1 : 0)>());
+  }
+  if constexpr (PS::NPASS > 2) {
+    for (int t = 0; t < T * KB; ++t)
+      r16::bpass_store<N, (PS::NPASS > 2 ? 1 : 0), KB>(regs(V[t]), t / KB, t % KB, buf1.data());
+    for (int t = 0; t < T * KB; ++t) r16::bload_stride<N, KB>(regs(V[t]), t / KB, t % KB, buf1.data());
+    bfly(std::integral_constant<int, (PS::NPASS > 2 ? 2 : 0)>());
+  }
+  double e = 0;
+  for (int b = 0; b < KB; ++b)
+    for (int q = 0; q < N; ++q) {
+      cd ref = 0;
+      for (int n = 0; n < N; ++n) ref += x[b][n] * std::polar(1.0, 2 * M_PI * double(n) * q / N);
+      const float2 g = V[(q % T) * KB + b][q / T];
+      e = std::max(e, std::abs(cd(g.x, g.y) - ref) / std::sqrt(double(N)));
+    }
+  const bool ok = e < 10 * 6e-8 * std::log2(double(N)) * 4;
+  std::printf("batch N=%d KB=%d err %.2e %s\n", N, KB, e, ok ? "ok" : "FAIL");
+  return ok ? 0 : 1;
+}
+
 int main() {
   return check<64>() + check<128>() + check<256>() + check<512>() + check<1024>() + check_pair<128>() +
-         check_pair<256>() + check_pair<512>();
+         check_pair<256>() + check_pair<512>() + check_batch<512, 8>() + check_batch<1024, 8>();
 }

@@ -277,6 +277,78 @@ __global__ void __launch_bounds__(ColGeo<H>::NT, gather_min_blocks(H, ColGeo<H>:
   }
 }
 
+// The synthesis gather with 16 values per thread (heights 512 and 1024), on
+// the fan's radix-16 geometry (two CTAs of 256 threads per SM at 512, with
+// 128 registers for the prefetched tile, the accumulator and the transform).
+// Measured at 512 x 512: gather 69.5 -> 65.5 us per iteration, 3739 -> 3758
+// Mpixel*label*iter/s (more gather CTAs leave more slots to the reduction).
+template <int H>
+__global__ void __launch_bounds__(Col16Geo<H>::NT, H == 512 ? 2 : 1)
+    k_fcol_gather16(const float2* __restrict__ Y, const float* __restrict__ bank,
+                    const WorkItem* __restrict__ items, const int* __restrict__ cta_begin,
+                    float2* __restrict__ partial, int Wh, int Whp, int l0, int f0, int nf,
+                    const float2* __restrict__ twH) {
+  using G = Col16Geo<H>;
+  constexpr int KB = G::KB, T = G::T;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* pt = sm;
+  float2* b0 = sm + G::PT;
+  float2* b1 = b0 + G::BR;
+  const int ib = cta_begin[blockIdx.x], ie = cta_begin[blockIdx.x + 1];
+  if (ib >= ie) return;
+  const int b = threadIdx.x % KB, tt = threadIdx.x / KB;
+  const size_t Pb = static_cast<size_t>(H) * Wh, Pp = static_cast<size_t>(H) * Whp;
+  WorkItem it = items[ib];
+  int col = it.tile * KB + b;
+  bool ok = col < Wh;
+  float2 acc[16], y[16];
+  float w[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) acc[k] = make_float2(0.f, 0.f);
+  auto load_y = [&](const float2* src, int c, bool o) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) y[k] = o ? src[static_cast<size_t>(tt + k * T) * Whp + c] : make_float2(0.f, 0.f);
+  };
+  r16::build_pass_twiddles<H, 1>(pt, twH, threadIdx.x, blockDim.x);
+  pdl_wait();
+  pdl_trigger();
+  load_y(Y + Pp * ((it.label - l0) * nf + (it.filter - f0)), col, ok);
+  for (int i = ib; i < ie; ++i) {
+    float2 v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = y[k];
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      w[k] = ok ? __ldg(bank + Pb * it.filter + static_cast<size_t>(tt + k * T) * Wh + col) : 0.f;
+    WorkItem nx = it;
+    int ncol = col;
+    bool nok = ok;
+    if (i + 1 < ie) {
+      nx = items[i + 1];
+      ncol = nx.tile * KB + b;
+      nok = ncol < Wh;
+      load_y(Y + Pp * ((nx.label - l0) * nf + (nx.filter - f0)), ncol, nok);
+    }
+    r16::batch_fft<H, -1, KB>(v, tt, b, b0, b1, pt);  // starts with a CTA barrier (also after the twiddle table)
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      acc[k].x = fmaf(w[k], v[k].x, acc[k].x);
+      acc[k].y = fmaf(w[k], v[k].y, acc[k].y);
+    }
+    if (i + 1 == ie || nx.slot != it.slot) {
+      float2* dst = partial + static_cast<size_t>(it.slot) * H * KB + b;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        dst[static_cast<size_t>(tt + k * T) * KB] = acc[k];
+        acc[k] = make_float2(0.f, 0.f);
+      }
+    }
+    it = nx;
+    col = ncol;
+    ok = nok;
+  }
+}
+
 // T[label] on one tile = column-inverse of the sum of the tile's partial
 // slots, in a fixed order.  The sum is load-latency bound (and small images
 // have few tiles), so the slots are split into RG consecutive runs (RG copies
@@ -364,8 +436,10 @@ cudaError_t prepare_col_t() {
   const size_t s = col_smem<H>();
   cudaError_t e = allow_smem(k_fcol_fwd<H>, s);
   if (e == cudaSuccess) e = allow_smem(k_fcol_fan<H>, s);
-  if constexpr (use_fan16(H))
+  if constexpr (use_fan16(H)) {
     if (e == cudaSuccess) e = allow_smem(k_fcol_fan16<H>, fan16_smem<H>());
+    if (e == cudaSuccess) e = allow_smem(k_fcol_gather16<H>, fan16_smem<H>());
+  }
   if (e == cudaSuccess) e = allow_smem(k_fcol_gather<H>, s);
   if (e == cudaSuccess) e = allow_smem(k_fcol_reduce_inv<H>, sizeof(float2) * ReduceGeo<H>::TOTAL);
   return e;
@@ -405,9 +479,13 @@ int col_ctas_per_sm(int H) {
   int fit = 0;
   cudaError_t e = cudaErrorInvalidValue;
   switch (H) {
-#define SHF_OCC(N)                                                                                \
-  case N:                                                                                         \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_fcol_gather<N>, ColGeo<N>::NT, col_smem<N>()); \
+#define SHF_OCC(N)                                                                                          \
+  case N:                                                                                                   \
+    if (use_fan16(N))                                                                                       \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_fcol_gather16<fan16_len(N)>,               \
+                                                        Col16Geo<fan16_len(N)>::NT, fan16_smem<N>());      \
+    else                                                                                                    \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_fcol_gather<N>, ColGeo<N>::NT, col_smem<N>()); \
     break;
     SHF_COL_SIZES(SHF_OCC)
 #undef SHF_OCC
@@ -449,6 +527,10 @@ cudaError_t col_gather(const Geo& g, int nc, const float2* Y, const WorkItem* it
   switch (g.H) {
 #define SHF_CASE(N)                                                                                           \
   case N:                                                                                                     \
+    if (use_fan16(N))                                                                                         \
+      return launch_pdl(k_fcol_gather16<fan16_len(N)>, dim3(nc), dim3(Col16Geo<fan16_len(N)>::NT),           \
+                        fan16_smem<N>(), st, Y, g.bank, items, cta_begin, partial, g.Wh, Whp, wv.l0, wv.f0,   \
+                        wv.nf, g.twH);                                                                        \
     return launch_pdl(k_fcol_gather<N>, dim3(nc), dim3(ColGeo<N>::NT), col_smem<N>(), st, Y, g.bank, items, cta_begin, \
                       partial, g.Wh, Whp, wv.l0, wv.f0, wv.nf, g.twH);
     SHF_COL_SIZES(SHF_CASE)

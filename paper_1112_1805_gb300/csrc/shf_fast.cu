@@ -13,8 +13,11 @@
 //                     clip(g) (= v - b_v), row-forward of d, in place in Y_v
 //     col_gather      partial slots += W_f * column-forward(Y_v)
 //   col_reduce      T_k = column-inverse(sum of the partial slots)
-// The coefficient spectra of one wave stay in L2 between the three kernels;
-// b_v is streamed with evict-first hints.
+// The coefficient spectra of one wave stay in (or, for two 512^2 labels, just
+// exceed) L2 between the three kernels; b_v is streamed with evict-first
+// hints.  Kernel variants by size: the v-step on pairs of rows (half widths 64,
+// 128), radix-16 rows (256 .. 1024) or 8-value rows (other widths); the fan
+// and gather with radix-16 columns at heights 512 and 1024.
 #include <algorithm>
 
 #include "shf_fast.h"

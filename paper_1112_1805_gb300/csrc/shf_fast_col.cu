@@ -1,6 +1,8 @@
 // Column transforms of the fast path: the analysis fan-out and the synthesis
 // gather over the filters of a wave, and the forward/inverse column passes of
 // u and of the synthesis sum (Sec. 2, eq. for S and S^T; Sec. 3, ADMM steps).
+// 8-value register FFTs (shf_fft_reg.cuh) for every height; the fan and the
+// gather at heights 512 and 1024 on 16-value radix-16 FFTs (shf_fft16.cuh).
 #include "shf_fast.h"
 #include "shf_fft16.cuh"
 

@@ -733,7 +733,7 @@ struct UstepGeo {
   // the largest CTA over K <= 8, and the CTAs per SM to ask the compiler for
   static constexpr int MAXTH = !RG::TILE ? (8 * T > 256 ? (8 * T + 31) / 32 * 32 : 256)
                                          : (T <= 32 ? 256 : 256 * RG::WPG);
-  static constexpr int MINB = MAXTH <= 256 ? 3 : 1;
+  static constexpr int MINB = MAXTH <= 256 ? 2 : 1;  // room for the phase-2 operand prefetch
 };
 
 // u-step (u = 1/2 [S^T(v - b_v) + (w - b_w) - gamma s], A^T A = 2I), w-step
@@ -774,6 +774,30 @@ __global__ void __launch_bounds__(UstepGeo<L>::MAXTH, UstepGeo<L>::MINB) k_wrow_
   reg::build_pass_twiddles<L, 2>(pt, twW, threadIdx.x, blockDim.x);
   pdl_wait();
   pdl_trigger();
+  // the operands of this thread's first PRE phase-2 items (w, b_w, s: written
+  // by earlier, completed grids) are requested now, so that their latency
+  // overlaps phase 1
+  constexpr int PRE = KMAX <= 4 ? 2 : 1;
+  const float2* s2 = reinterpret_cast<const float2*>(s);
+  float2* w2 = reinterpret_cast<float2*>(w);
+  float2* bw2 = reinterpret_cast<float2*>(bw);
+  float2* u2 = reinterpret_cast<float2*>(u);
+  float2 pw[PRE][KMAX], pb[PRE][KMAX], ps[PRE][KMAX];
+#pragma unroll
+  for (int j = 0; j < PRE; ++j) {
+    const int i = threadIdx.x + j * blockDim.x;
+    const int ri = i / L, n = i - ri * L;
+    const int prow = blockIdx.x * NR + ri;
+    const bool ok = i < NR * L && prow < H;
+    const size_t pix = static_cast<size_t>(ok ? prow : 0) * L + n;
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q) {
+      const bool lq = ok && q < K;
+      pw[j][q] = lq ? w2[HL * q + pix] : make_float2(0.f, 0.f);
+      pb[j][q] = lq ? bw2[HL * q + pix] : make_float2(0.f, 0.f);
+      ps[j][q] = lq ? s2[HL * q + pix] : make_float2(0.f, 0.f);
+    }
+  }
   __syncthreads();
   // phase 1: S^T(v - b_v) on row r of label k
   {
@@ -803,15 +827,11 @@ __global__ void __launch_bounds__(UstepGeo<L>::MAXTH, UstepGeo<L>::MINB) k_wrow_
   // phase 2: pointwise u-step, projection and b_w update (two pixels per item)
   {
     const float hg = 0.5f * gamma;
-    for (int i = threadIdx.x; i < NR * L; i += blockDim.x) {
+    auto item = [&](int i, const float2 (&wv)[KMAX], const float2 (&bv)[KMAX], const float2 (&sv)[KMAX]) {
       const int ri = i / L, n = i - ri * L;
       const int prow = blockIdx.x * NR + ri;
-      if (prow >= H) continue;
+      if (prow >= H) return;
       const size_t pix = static_cast<size_t>(prow) * L + n;
-      const float2* s2 = reinterpret_cast<const float2*>(s);
-      float2* w2 = reinterpret_cast<float2*>(w);
-      float2* bw2 = reinterpret_cast<float2*>(bw);
-      float2* u2 = reinterpret_cast<float2*>(u);
       float gx[KMAX], gy[KMAX];
 #pragma unroll
       for (int q = 0; q < KMAX; ++q) {
@@ -820,13 +840,12 @@ __global__ void __launch_bounds__(UstepGeo<L>::MAXTH, UstepGeo<L>::MINB) k_wrow_
         if (q < K) {
           float2* Uq = U + (static_cast<size_t>(q) * NR + ri) * L + n;
           const float2 st = *Uq;
-          const float2 wv = w2[HL * q + pix], bv = bw2[HL * q + pix], sv = s2[HL * q + pix];
-          const float ux = 0.5f * (st.x + (wv.x - bv.x)) - hg * sv.x;
-          const float uy = 0.5f * (st.y + (wv.y - bv.y)) - hg * sv.y;
+          const float ux = 0.5f * (st.x + (wv[q].x - bv[q].x)) - hg * sv[q].x;
+          const float uy = 0.5f * (st.y + (wv[q].y - bv[q].y)) - hg * sv[q].y;
           u2[HL * q + pix] = make_float2(ux, uy);
           *Uq = make_float2(ux, uy);
-          gx[q] = bv.x + ux;
-          gy[q] = bv.y + uy;
+          gx[q] = bv[q].x + ux;
+          gy[q] = bv[q].y + uy;
         }
       }
       float px[KMAX], py[KMAX];
@@ -843,6 +862,25 @@ __global__ void __launch_bounds__(UstepGeo<L>::MAXTH, UstepGeo<L>::MINB) k_wrow_
           w2[HL * q + pix] = make_float2(px[q], py[q]);
           bw2[HL * q + pix] = make_float2(gx[q] - px[q], gy[q] - py[q]);
         }
+    };
+#pragma unroll
+    for (int j = 0; j < PRE; ++j) {
+      const int i = threadIdx.x + j * blockDim.x;
+      if (i < NR * L) item(i, pw[j], pb[j], ps[j]);
+    }
+    for (int i = threadIdx.x + PRE * blockDim.x; i < NR * L; i += blockDim.x) {
+      const int ri = i / L, n = i - ri * L;
+      const int prow = blockIdx.x * NR + ri;
+      const size_t pix = static_cast<size_t>(prow < H ? prow : 0) * L + n;
+      float2 wv[KMAX], bv[KMAX], sv[KMAX];
+#pragma unroll
+      for (int q = 0; q < KMAX; ++q) {
+        const bool lq = prow < H && q < K;
+        wv[q] = lq ? w2[HL * q + pix] : make_float2(0.f, 0.f);
+        bv[q] = lq ? bw2[HL * q + pix] : make_float2(0.f, 0.f);
+        sv[q] = lq ? s2[HL * q + pix] : make_float2(0.f, 0.f);
+      }
+      item(i, wv, bv, sv);
     }
   }
   __syncthreads();

@@ -2,7 +2,7 @@
 // gather over the filters of a wave, and the forward/inverse column passes of
 // u and of the synthesis sum (Sec. 2, eq. for S and S^T; Sec. 3, ADMM steps).
 // 8-value register FFTs (shf_fft_reg.cuh) for every height; the fan and the
-// gather at heights 512 and 1024 on 16-value radix-16 FFTs (shf_fft16.cuh).
+// gather at heights 512, 1024 and 2048 on 16-value radix-16 FFTs (shf_fft16.cuh).
 #include "shf_fast.h"
 #include "shf_fft16.cuh"
 
@@ -138,21 +138,22 @@ __global__ void __launch_bounds__(ColGeo<H>::NT, col_min_blocks(H, ColGeo<H>::NT
   }
 }
 
-// The analysis fan-out with 16 values per thread (heights 512 and 1024:
-// radix-16 column transforms, one exchange fewer at 1024): CTAs of 8 H/16
-// threads, thread (b, tt) holding rows tt + k H/16 of column b.  Measured at
+// The analysis fan-out with 16 values per thread (heights 512, 1024 and 2048:
+// radix-16 column transforms, one exchange fewer at 1024 and 2048): CTAs of
+// KB H/16 threads (KB = 8, or 4 at 2048), thread (b, tt) holding rows
+// tt + k H/16 of column b.  Measured at
 // 512 x 512: 3667 -> 3721 Mpixel*label*iter/s; at 256 (unrolled 256 x 256
 // sweeps) neutral, so 256 keeps the 8-value kernel.
 template <int H>
 struct Col16Geo {
-  static constexpr int KB = 8;
+  static constexpr int KB = reg::col_batch(H);  // the plan's column tile: 8, or 4 above 1024
   static constexpr int T = H / 16;
   static constexpr int NT = KB * T;
   static constexpr int PT = (r16::Passes<H>::TWSIZE + 1) & ~1;  // per-pass twiddles
   static constexpr int BR = r16::brows16(H) * KB;                // one exchange buffer
   static constexpr int TOTAL = PT + 2 * BR;
 };
-__host__ __device__ constexpr bool use_fan16(int H) { return H == 512 || H == 1024; }
+__host__ __device__ constexpr bool use_fan16(int H) { return H == 512 || H == 1024 || H == 2048; }
 __host__ __device__ constexpr int fan16_len(int H) { return use_fan16(H) ? H : 512; }
 
 template <int H>
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(ColGeo<H>::NT, gather_min_blocks(H, ColGeo<H>:
   }
 }
 
-// The synthesis gather with 16 values per thread (heights 512 and 1024), on
+// The synthesis gather with 16 values per thread (heights 512, 1024, 2048), on
 // the fan's radix-16 geometry (two CTAs of 256 threads per SM at 512, with
 // 128 registers for the prefetched tile, the accumulator and the transform).
 // Measured at 512 x 512: gather 69.5 -> 65.5 us per iteration, 3739 -> 3758

@@ -777,12 +777,15 @@ __global__ void __launch_bounds__(UstepGeo<L>::MAXTH, UstepGeo<L>::MINB) k_wrow_
   // the operands of this thread's first PRE phase-2 items (w, b_w, s: written
   // by earlier, completed grids) are requested now, so that their latency
   // overlaps phase 1
-  constexpr int PRE = KMAX <= 4 ? 2 : 1;
+  // (K <= 4 only: with K up to 8 the registers cost more than the overlap gains,
+  // 424 -> 451 us per 2048^2 iteration)
+  constexpr int PRE = KMAX <= 4 ? 2 : 0;
+  constexpr int PREA = PRE > 0 ? PRE : 1;
   const float2* s2 = reinterpret_cast<const float2*>(s);
   float2* w2 = reinterpret_cast<float2*>(w);
   float2* bw2 = reinterpret_cast<float2*>(bw);
   float2* u2 = reinterpret_cast<float2*>(u);
-  float2 pw[PRE][KMAX], pb[PRE][KMAX], ps[PRE][KMAX];
+  float2 pw[PREA][KMAX], pb[PREA][KMAX], ps[PREA][KMAX];
 #pragma unroll
   for (int j = 0; j < PRE; ++j) {
     const int i = threadIdx.x + j * blockDim.x;
@@ -827,7 +830,8 @@ __global__ void __launch_bounds__(UstepGeo<L>::MAXTH, UstepGeo<L>::MINB) k_wrow_
   // phase 2: pointwise u-step, projection and b_w update (two pixels per item)
   {
     const float hg = 0.5f * gamma;
-    auto item = [&](int i, const float2 (&wv)[KMAX], const float2 (&bv)[KMAX], const float2 (&sv)[KMAX]) {
+    // one item: `get(q, pix, wv, bv, sv)` supplies label q's w, b_w and s
+    auto item = [&](int i, auto get) {
       const int ri = i / L, n = i - ri * L;
       const int prow = blockIdx.x * NR + ri;
       if (prow >= H) return;
@@ -838,14 +842,16 @@ __global__ void __launch_bounds__(UstepGeo<L>::MAXTH, UstepGeo<L>::MINB) k_wrow_
         gx[q] = 0.f;
         gy[q] = 0.f;
         if (q < K) {
+          float2 wv, bv, sv;
+          get(q, pix, wv, bv, sv);
           float2* Uq = U + (static_cast<size_t>(q) * NR + ri) * L + n;
           const float2 st = *Uq;
-          const float ux = 0.5f * (st.x + (wv[q].x - bv[q].x)) - hg * sv[q].x;
-          const float uy = 0.5f * (st.y + (wv[q].y - bv[q].y)) - hg * sv[q].y;
+          const float ux = 0.5f * (st.x + (wv.x - bv.x)) - hg * sv.x;
+          const float uy = 0.5f * (st.y + (wv.y - bv.y)) - hg * sv.y;
           u2[HL * q + pix] = make_float2(ux, uy);
           *Uq = make_float2(ux, uy);
-          gx[q] = bv[q].x + ux;
-          gy[q] = bv[q].y + uy;
+          gx[q] = bv.x + ux;
+          gy[q] = bv.y + uy;
         }
       }
       float px[KMAX], py[KMAX];
@@ -866,22 +872,19 @@ __global__ void __launch_bounds__(UstepGeo<L>::MAXTH, UstepGeo<L>::MINB) k_wrow_
 #pragma unroll
     for (int j = 0; j < PRE; ++j) {
       const int i = threadIdx.x + j * blockDim.x;
-      if (i < NR * L) item(i, pw[j], pb[j], ps[j]);
+      if (i < NR * L)
+        item(i, [&](int q, size_t, float2& wv, float2& bv, float2& sv) {
+          wv = pw[j][q];
+          bv = pb[j][q];
+          sv = ps[j][q];
+        });
     }
-    for (int i = threadIdx.x + PRE * blockDim.x; i < NR * L; i += blockDim.x) {
-      const int ri = i / L, n = i - ri * L;
-      const int prow = blockIdx.x * NR + ri;
-      const size_t pix = static_cast<size_t>(prow < H ? prow : 0) * L + n;
-      float2 wv[KMAX], bv[KMAX], sv[KMAX];
-#pragma unroll
-      for (int q = 0; q < KMAX; ++q) {
-        const bool lq = prow < H && q < K;
-        wv[q] = lq ? w2[HL * q + pix] : make_float2(0.f, 0.f);
-        bv[q] = lq ? bw2[HL * q + pix] : make_float2(0.f, 0.f);
-        sv[q] = lq ? s2[HL * q + pix] : make_float2(0.f, 0.f);
-      }
-      item(i, wv, bv, sv);
-    }
+    for (int i = threadIdx.x + PRE * blockDim.x; i < NR * L; i += blockDim.x)
+      item(i, [&](int q, size_t pix, float2& wv, float2& bv, float2& sv) {
+        wv = w2[HL * q + pix];
+        bv = bw2[HL * q + pix];
+        sv = s2[HL * q + pix];
+      });
   }
   __syncthreads();
   // phase 3: row spectrum of u on row r of label k

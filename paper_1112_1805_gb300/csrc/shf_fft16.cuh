@@ -29,7 +29,7 @@ using reg::ridx;
 
 template <int N>
 struct Passes {
-  static_assert(N >= 32 && N <= 1024 && (N & (N - 1)) == 0, "radix-16 row FFT: N = 2^a, 32 <= N <= 1024");
+  static_assert(N >= 32 && N <= 2048 && (N & (N - 1)) == 0, "radix-16 FFT: N = 2^a, 32 <= N <= 2048");
   static constexpr int T = N / 16;                        // threads of a group
   static constexpr int LG = ilog2(N);
   static constexpr int N16 = LG / 4;                      // radix-16 passes (first)

@@ -1,7 +1,7 @@
 // Host-side check of the radix-16 row FFT building blocks (shf_fft16.cuh)
 // against FP64 DFTs, for the half widths 64, 128, 256, 512 and 1024, and the
 // two-rows-per-transform packing for widths 128, 256 and 512, and the column
-// (batch) layout for heights 512 and 1024.  A row group
+// (batch) layout for heights 512, 1024 (8 columns) and 2048 (4 columns).  A row group
 // of T threads is emulated lane by lane, phase by phase, exactly as the kernel
 // sequences them between warp barriers: butterflies, Stockham stores to the
 // padded group buffer, stride reads, and the packing steps with each lane's
@@ -242,5 +242,6 @@ static int check_batch() {
 
 int main() {
   return check<64>() + check<128>() + check<256>() + check<512>() + check<1024>() + check_pair<128>() +
-         check_pair<256>() + check_pair<512>() + check_batch<512, 8>() + check_batch<1024, 8>();
+         check_pair<256>() + check_pair<512>() + check_batch<512, 8>() + check_batch<1024, 8>() +
+         check_batch<2048, 4>();
 }

@@ -26,4 +26,4 @@ def test_fft16_host(tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     print(r.stdout)
     assert r.returncode == 0, r.stdout + r.stderr
-    assert r.stdout.count(" ok") == 10
+    assert r.stdout.count(" ok") == 11

@@ -18,8 +18,10 @@
  *   - Sizes: W even; H and W/2 products of powers of 2, 3 and 5; 8 <= H, W <=
  *     2048.  Labels 2 <= K <= 16; channels C in {1, 3}; scales 1 <= J <= 6.
  *   - Device pointers are caller-owned CUDA device memory unless the argument
- *     says "host".  The library never frees caller memory and never returns
- *     memory it allocated for the caller.
+ *     says "host".  Calls that take a bank or a state run on the device the
+ *     bank was built on, which must be the current device.  The library never
+ *     frees caller memory and never returns memory it allocated for the
+ *     caller.
  *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
  *     default stream.  Work is enqueued asynchronously on that stream unless
  *     the function says it synchronises.
@@ -124,10 +126,13 @@ int shearlet_synthesize(const shf_bank* bank, const float* coef, int nch, float*
  * that loads the library keeps reserved until the process exits; the call
  * itself allocates nothing (no cudaMalloc, no pool, no library allocation).
  * Limit: nch * (eta + 1) * H * (W/2 + 1) * 8 bytes must not exceed 32 MiB
- * (e.g. one 512 x 512 channel at J = 3, or four 256 x 256 channels at J = 4);
- * larger requests fail with SHF_ERR_SIZE and a message giving both numbers.
- * The first call on each device looks up the array's device address with
- * that device current; make that first call before any stream capture.
+ * (e.g. one 512 x 512 channel at J = 3: 31.6 MB, or two 256 x 256 channels
+ * at J = 4: 32.8 MB); larger requests fail with SHF_ERR_SIZE and a message
+ * giving both numbers.  The device the bank was built on must be the current
+ * device (its tables and the array are then on the same GPU); otherwise the
+ * call fails with SHF_ERR_STATE.  The first call on each device looks up the
+ * array's device address with that device current; make that first call
+ * before any stream capture.
  * Every call on a device shares the one array and leaves its contents behind
  * (nothing needs clearing: each call writes every element it reads), so calls
  * whose work overlaps on the GPU -- other streams, other host threads --

@@ -130,6 +130,7 @@ struct seg_state {
 
 namespace shf {
 void bank_geo(const shf_bank* b, Geo* g) { *g = b->g; }
+int bank_device(const shf_bank* b) { return b->device; }
 int set_error(int code, const std::string& msg) { return fail(code, msg); }
 }  // namespace shf
 

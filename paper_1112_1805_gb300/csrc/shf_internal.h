@@ -212,6 +212,7 @@ cudaError_t launch_adj_tsum_rows(const double* tpart, int K, int eta, int H, dou
 // C ABI layer (shf_capi.cu): the geometry and device tables of a bank, and the
 // thread-local message behind shf_last_error() (returns code).
 void bank_geo(const shf_bank* b, Geo* g);
+int bank_device(const shf_bank* b);  // the device the bank's tables live on
 int set_error(int code, const std::string& msg);
 
 }  // namespace shf

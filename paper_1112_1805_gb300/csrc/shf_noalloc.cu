@@ -25,14 +25,13 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_dev[kMaxDevices] = {};  // device address of g_scratch, per device
 
-// Device address of the scratch array on the current device.  The name
-// g_scratch in host code is only a host-side stand-in, so the address is
-// looked up once per device with that device current.
-int scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return shf::set_error(SHF_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+// Device address of the scratch array on device `dev`, which must be the
+// current device.  The name g_scratch in host code is only a host-side
+// stand-in, so the address is looked up once per device with that device
+// current.
+int scratch_address(int dev, void** out) {
   if (dev < 0 || dev >= kMaxDevices) return shf::set_error(SHF_ERR_CUDA, "device ordinal out of range");
+  cudaError_t e = cudaSuccess;
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_scratch_dev[dev]) {
     void* p = nullptr;
@@ -63,8 +62,18 @@ int shearlet_analyze_noalloc(const shf_bank* bank, const float* u, int nch, floa
     return shf::set_error(SHF_ERR_SIZE, "shearlet_analyze_noalloc: needs " + std::to_string(need) +
                                             " bytes of scratch (nch * (eta + 1) * H * (W/2 + 1) * 8), more than the "
                                             "fixed " + std::to_string(kScratchBytes) + " bytes");
+  // The bank's tables and the scratch must belong to the same GPU: the
+  // scratch address is that of the current device.
+  int dev = 0;
+  cudaError_t ed = cudaGetDevice(&dev);
+  if (ed != cudaSuccess)
+    return shf::set_error(SHF_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(ed));
+  if (dev != shf::bank_device(bank))
+    return shf::set_error(SHF_ERR_STATE, "shearlet_analyze_noalloc: the current device (" + std::to_string(dev) +
+                                             ") is not the device the bank was built on (" +
+                                             std::to_string(shf::bank_device(bank)) + ")");
   void* base = nullptr;
-  int rc = scratch_address(&base);
+  int rc = scratch_address(dev, &base);
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   float2* Ur = static_cast<float2*>(base);

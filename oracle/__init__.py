@@ -21,7 +21,15 @@ follows.  Parity status per function:
 * admm_iterate -- pinned through its invariants: u-subproblem stationarity,
   fixed-point residual monotonicity, KKT stationarity at convergence, the
   Lambda = 0 and constant-image special cases;
-* energy, labels -- pinned (hand values).
+* energy, labels -- pinned (hand values);
+* tv_grad, tv_grad_adj -- pinned (hand values, adjointness, constants);
+* tv_solve -- pinned (the explicit periodic 5-point stencil applied to the
+  solution returns the right-hand side);
+* tv_shrink -- pinned (prox optimality by brute force, closed form);
+* tv_admm_iterate -- pinned through its invariants (u-subproblem
+  stationarity, fixed-point residual monotonicity, KKT at convergence, the
+  lambda = 0 and constant-image special cases); tv_energy by hand values of
+  a stripe image.
 """
 
 from .oracle import *  # noqa: F401,F403

@@ -25,6 +25,8 @@ __all__ = [
     "filters", "filters_unsymmetrised", "fft2", "dft2_brute", "analyze", "synthesize",
     "data_term", "soft_shrink", "project_simplex", "admm_iterate", "admm_run", "energy",
     "labels", "thresholds", "zero_state", "unrolled_vjp", "ce_loss", "unrolled_grads",
+    "tv_grad", "tv_grad_adj", "tv_solve", "tv_shrink", "tv_zero_state", "tv_admm_iterate", "tv_admm_run",
+    "tv_energy",
 ]
 
 
@@ -67,6 +69,13 @@ def lib():
                 "oracle_energy": (c_int, [c_int, c_int, c_int, c_int, D, D, D, D]),
                 "oracle_unrolled_vjp": (c_int, [c_int, c_int, c_int, c_int, D, D, c_double, c_int, D, D, D, D]),
                 "oracle_labels": (c_int, [c_int, c_int, c_int, D, I, D]),
+                "oracle_tv_grad": (c_int, [c_int, c_int, c_int, D, D]),
+                "oracle_tv_grad_adj": (c_int, [c_int, c_int, c_int, D, D]),
+                "oracle_tv_solve": (c_int, [c_int, c_int, c_int, D, D]),
+                "oracle_tv_shrink": (c_int, [c_int, c_int, c_int, D, c_double, c_int, D]),
+                "oracle_tv_admm_iterate": (c_int, [c_int, c_int, c_int, D, c_double, c_double, c_int, c_int,
+                                                   D, D, D, D, D, D]),
+                "oracle_tv_energy": (c_int, [c_int, c_int, c_int, D, D, c_double, c_int, D]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -326,3 +335,85 @@ def unrolled_grads(f, codebook, J: int, Lambda, gamma: float, T: int, labels, ep
     dcb = (sbar[:, None] * (-2.0) * diff).sum(axis=(2, 3))
     df = (sbar[:, None] * 2.0 * diff).sum(axis=0)
     return {"loss": loss, "w": wT, "codebook": dcb, "Lambda": lbar, "f": df, "sbar": sbar}
+
+
+# ---------------------------------------------------------------------------
+# TV-regularised segmentation (Sec. 4, eq. TVreg): the comparison model.
+# Gradients and their duals are [K, 2, H, W] (component 0 along rows).
+# ---------------------------------------------------------------------------
+def tv_grad(u) -> np.ndarray:
+    """Periodic forward differences of each plane: u[K, H, W] -> [K, 2, H, W]."""
+    u = _f64(u)
+    K, H, W = u.shape
+    g = np.empty((K, 2, H, W))
+    _check(lib().oracle_tv_grad(H, W, K, _d(u), _d(g)), "tv_grad")
+    return g
+
+
+def tv_grad_adj(p) -> np.ndarray:
+    """Adjoint of tv_grad: p[K, 2, H, W] -> [K, H, W]."""
+    p = _f64(p)
+    K, _, H, W = p.shape
+    out = np.empty((K, H, W))
+    _check(lib().oracle_tv_grad_adj(H, W, K, _d(p), _d(out)), "tv_grad_adj")
+    return out
+
+
+def tv_solve(rhs) -> np.ndarray:
+    """(I + grad^T grad)^-1 rhs per plane (periodic, diagonal in the DFT basis)."""
+    rhs = _f64(rhs)
+    K, H, W = rhs.shape
+    u = np.empty_like(rhs)
+    _check(lib().oracle_tv_solve(H, W, K, _d(rhs), _d(u)), "tv_solve")
+    return u
+
+
+def tv_shrink(g, t: float, per_label: bool = False) -> np.ndarray:
+    """Vector shrinkage of g[K, 2, H, W] by t over all 2K values of a pixel
+    (or over the two values of each label with per_label)."""
+    g = _f64(g)
+    K, _, H, W = g.shape
+    v = np.empty_like(g)
+    _check(lib().oracle_tv_shrink(H, W, K, _d(g), float(t), int(per_label), _d(v)), "tv_shrink")
+    return v
+
+
+def tv_zero_state(K: int, H: int, W: int) -> dict:
+    return {"v": np.zeros((K, 2, H, W)), "bv": np.zeros((K, 2, H, W)), "w": np.zeros((K, H, W)),
+            "bw": np.zeros((K, H, W)), "u": np.zeros((K, H, W))}
+
+
+def tv_admm_iterate(state: dict, s, lam: float, gamma: float, T: int, per_label: bool = False,
+                    record_residual: bool = False):
+    """T ADMM iterations of the TV model in place on ``state`` (keys v, bv, w, bw, u)."""
+    s = _f64(s)
+    K, H, W = s.shape
+    for key in ("v", "bv", "w", "bw", "u"):
+        assert state[key].dtype == np.float64 and state[key].flags.c_contiguous
+    res = np.zeros(max(T, 1)) if record_residual else None
+    rc = lib().oracle_tv_admm_iterate(H, W, K, _d(s), float(lam), float(gamma), int(per_label), int(T),
+                                      _d(state["v"]), _d(state["bv"]), _d(state["w"]), _d(state["bw"]),
+                                      _d(state["u"]), _d(res) if res is not None else None)
+    _check(rc, "tv_admm_iterate")
+    return res[:T] if res is not None else None
+
+
+def tv_energy(x, s, lam: float, per_label: bool = False) -> float:
+    """<x, s> + lam sum_pixels |(I_q (x) grad) x| (eq. TVreg)."""
+    x, s = _f64(x), _f64(s)
+    K, H, W = x.shape
+    e = ctypes.c_double(0.0)
+    _check(lib().oracle_tv_energy(H, W, K, _d(x), _d(s), float(lam), int(per_label), ctypes.byref(e)), "tv_energy")
+    return e.value
+
+
+def tv_admm_run(f, codebook, lam: float, gamma: float, T: int, per_label: bool = False) -> dict:
+    """Data term + zero state + T TV-ADMM iterations; adds labels, gap, energy."""
+    s = data_term(f, codebook)
+    K, H, W = s.shape
+    st = tv_zero_state(K, H, W)
+    st["fp_res"] = tv_admm_iterate(st, s, lam, gamma, T, per_label, record_residual=True)
+    st["s"] = s
+    st["labels"], st["gap"] = labels(st["w"])
+    st["energy"] = tv_energy(st["w"], s, lam, per_label)
+    return st

@@ -812,3 +812,184 @@ int oracle_labels(int H, int W, int K, const double* x, int* labels, double* gap
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// TV-regularised segmentation, the comparison model of Sec. 4 (eq. TVreg):
+//   min_u <u, s> + lambda || |(I_q (x) grad) u| ||_1 + iota_C(u),
+// with |(I_q (x) grad) u|(x) = (|grad u_1(x)|^2 + ... + |grad u_q(x)|^2)^(1/2)
+// (the labels coupled per pixel), or, in the alternative the paper mentions,
+// sum_k |grad u_k(x)|.  Readings (the paper states neither): grad is the
+// forward difference with periodic boundary, the same periodic setting as the
+// FFT-based shearlets, so that I + grad^T grad is diagonalised by the DFT; the
+// ADMM is the one of Sec. 3 with S replaced by grad (same splitting v =
+// (I_q (x) grad) u, w = u, same scaling by gamma), so that the u-step solves
+// (I + grad^T grad) u = grad^T (v - b_v) + (w - b_w) - gamma s.
+// Layout: gradients and their duals are [K][2][H][W], component 0 along the
+// row axis (index r, omega_1), component 1 along the column axis.
+// ===========================================================================
+namespace {
+
+// (grad u)(r, c) = (u(r+1, c) - u(r, c), u(r, c+1) - u(r, c)), periodic.
+void tv_grad(int H, int W, const double* u, double* g) {
+  const size_t P = static_cast<size_t>(H) * W;
+  for (int r = 0; r < H; ++r)
+    for (int c = 0; c < W; ++c) {
+      const double x = u[r * W + c];
+      g[r * W + c] = u[((r + 1) % H) * W + c] - x;
+      g[P + r * W + c] = u[r * W + (c + 1) % W] - x;
+    }
+}
+
+// Adjoint of tv_grad: (grad^T p)(r, c) = p0(r-1, c) - p0(r, c) + p1(r, c-1) - p1(r, c).
+void tv_grad_adj(int H, int W, const double* p, double* out) {
+  const size_t P = static_cast<size_t>(H) * W;
+  for (int r = 0; r < H; ++r)
+    for (int c = 0; c < W; ++c)
+      out[r * W + c] = p[((r + H - 1) % H) * W + c] - p[r * W + c] + p[P + r * W + (c + W - 1) % W] - p[P + r * W + c];
+}
+
+// u = (I + grad^T grad)^(-1) rhs for one plane: grad^T grad is the periodic
+// 5-point negative Laplacian, whose DFT symbol at index (n1, n2) is
+// 4 sin^2(pi n1 / H) + 4 sin^2(pi n2 / W).
+void tv_solve_one(int H, int W, const double* rhs, double* u) {
+  const size_t P = static_cast<size_t>(H) * W;
+  std::vector<cd> a(P);
+  for (size_t i = 0; i < P; ++i) a[i] = rhs[i];
+  fft2(a.data(), H, W, false);
+  for (int n1 = 0; n1 < H; ++n1) {
+    const double s1 = std::sin(kPi * n1 / H);
+    for (int n2 = 0; n2 < W; ++n2) {
+      const double s2 = std::sin(kPi * n2 / W);
+      a[static_cast<size_t>(n1) * W + n2] /= 1.0 + 4.0 * s1 * s1 + 4.0 * s2 * s2;
+    }
+  }
+  fft2(a.data(), H, W, true);
+  for (size_t i = 0; i < P; ++i) u[i] = a[i].real();
+}
+
+// Proximal map of t |.|_2 on a group of n values: x (1 - t/|x|)_+.
+void shrink_group(const double* x, int n, size_t stride, double t, double* out) {
+  double nrm2 = 0.0;
+  for (int i = 0; i < n; ++i) nrm2 += x[i * stride] * x[i * stride];
+  const double nrm = std::sqrt(nrm2);
+  const double f = nrm > t ? 1.0 - t / nrm : 0.0;
+  for (int i = 0; i < n; ++i) out[i * stride] = f * x[i * stride];
+}
+
+// Vector shrinkage of g [K][2][H][W] with threshold t per pixel: the group is
+// all 2K values of a pixel (per_label = 0, the coupled TV of eq. TVreg) or the
+// two values of each label (per_label = 1).
+void tv_shrink(int H, int W, int K, const double* g, double t, int per_label, double* v) {
+  const size_t P = static_cast<size_t>(H) * W;
+  for (size_t x = 0; x < P; ++x) {
+    if (per_label) {
+      for (int k = 0; k < K; ++k) shrink_group(g + 2 * k * P + x, 2, P, t, v + 2 * k * P + x);
+    } else {
+      shrink_group(g + x, 2 * K, P, t, v + x);
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+// grad u for K planes: u [K][H][W] -> g [K][2][H][W].
+int oracle_tv_grad(int H, int W, int K, const double* u, double* g) {
+  if (H < 2 || W < 2 || K < 1) return -1;
+  const size_t P = static_cast<size_t>(H) * W;
+  for (int k = 0; k < K; ++k) tv_grad(H, W, u + k * P, g + 2 * k * P);
+  return 0;
+}
+
+// grad^T p for K planes: p [K][2][H][W] -> out [K][H][W].
+int oracle_tv_grad_adj(int H, int W, int K, const double* p, double* out) {
+  if (H < 2 || W < 2 || K < 1) return -1;
+  const size_t P = static_cast<size_t>(H) * W;
+  for (int k = 0; k < K; ++k) tv_grad_adj(H, W, p + 2 * k * P, out + k * P);
+  return 0;
+}
+
+// (I + grad^T grad)^(-1) rhs for K planes.
+int oracle_tv_solve(int H, int W, int K, const double* rhs, double* u) {
+  if (H < 2 || W < 2 || K < 1) return -1;
+  const size_t P = static_cast<size_t>(H) * W;
+  parallel_for(K, [&](int k) { tv_solve_one(H, W, rhs + k * P, u + k * P); });
+  return 0;
+}
+
+// Vector shrinkage (see tv_shrink), g and v [K][2][H][W].
+int oracle_tv_shrink(int H, int W, int K, const double* g, double t, int per_label, double* v) {
+  if (H < 1 || W < 1 || K < 1 || t < 0.0) return -1;
+  tv_shrink(H, W, K, g, t, per_label, v);
+  return 0;
+}
+
+// T iterations of the ADMM for the TV model, in place (v, bv: [K][2][H][W];
+// w, bw, u: [K][H][W]):
+//   u   = (I + grad^T grad)^(-1) [ grad^T (v - b_v) + (w - b_w) - gamma s ]
+//   g_v = b_v + grad u ;  v = vector shrinkage of g_v by gamma lambda
+//   g_w = b_w + u      ;  w = P_C(g_w) pixelwise
+//   b_v = g_v - v      ;  b_w = g_w - w
+// fp_res (nullable, length T): the fixed-point residual of each iteration, as
+// in oracle_admm_iterate.
+int oracle_tv_admm_iterate(int H, int W, int K, const double* s, double lambda, double gamma, int per_label, int T,
+                           double* v, double* bv, double* w, double* bw, double* u, double* fp_res) {
+  if (H < 2 || W < 2 || K < 1 || T < 0 || !(gamma > 0.0) || lambda < 0.0) return -1;
+  const size_t P = static_cast<size_t>(H) * W, KP = static_cast<size_t>(K) * P, NV = 2 * KP;
+  const double t = gamma * lambda;
+  std::vector<double> diff(NV), rhs(KP), gu(NV), vn(NV), gw(K), x(K);
+  for (int it = 0; it < T; ++it) {
+    for (size_t i = 0; i < NV; ++i) diff[i] = v[i] - bv[i];
+    for (int k = 0; k < K; ++k) tv_grad_adj(H, W, diff.data() + 2 * k * P, rhs.data() + k * P);
+    for (size_t i = 0; i < KP; ++i) rhs[i] += (w[i] - bw[i]) - gamma * s[i];
+    parallel_for(K, [&](int k) { tv_solve_one(H, W, rhs.data() + k * P, u + k * P); });
+    for (int k = 0; k < K; ++k) tv_grad(H, W, u + k * P, gu.data() + 2 * k * P);
+    for (size_t i = 0; i < NV; ++i) gu[i] += bv[i];  // g_v
+    tv_shrink(H, W, K, gu.data(), t, per_label, vn.data());
+    double res = 0.0;
+    for (size_t i = 0; i < NV; ++i) {
+      const double bn = gu[i] - vn[i];
+      res += (vn[i] - v[i]) * (vn[i] - v[i]) + (bn - bv[i]) * (bn - bv[i]);
+      v[i] = vn[i];
+      bv[i] = bn;
+    }
+    for (size_t r = 0; r < P; ++r) {
+      for (int k = 0; k < K; ++k) gw[k] = bw[k * P + r] + u[k * P + r];
+      project_simplex_sort(gw.data(), K, x.data());
+      for (int k = 0; k < K; ++k) {
+        const double bn = gw[k] - x[k];
+        res += (x[k] - w[k * P + r]) * (x[k] - w[k * P + r]) + (bn - bw[k * P + r]) * (bn - bw[k * P + r]);
+        w[k * P + r] = x[k];
+        bw[k * P + r] = bn;
+      }
+    }
+    if (fp_res) fp_res[it] = res;
+  }
+  return 0;
+}
+
+// Energy of the TV model at x: <x, s> + lambda sum_pixels |(I_q (x) grad) x|.
+int oracle_tv_energy(int H, int W, int K, const double* x, const double* s, double lambda, int per_label,
+                     double* energy) {
+  if (H < 2 || W < 2 || K < 1) return -1;
+  const size_t P = static_cast<size_t>(H) * W;
+  std::vector<double> g(2 * K * P);
+  for (int k = 0; k < K; ++k) tv_grad(H, W, x + k * P, g.data() + 2 * k * P);
+  double data = 0.0, reg = 0.0;
+  for (size_t i = 0; i < static_cast<size_t>(K) * P; ++i) data += x[i] * s[i];
+  for (size_t r = 0; r < P; ++r) {
+    if (per_label) {
+      for (int k = 0; k < K; ++k)
+        reg += std::sqrt(g[2 * k * P + r] * g[2 * k * P + r] + g[(2 * k + 1) * P + r] * g[(2 * k + 1) * P + r]);
+    } else {
+      double n2 = 0.0;
+      for (int i = 0; i < 2 * K; ++i) n2 += g[i * P + r] * g[i * P + r];
+      reg += std::sqrt(n2);
+    }
+  }
+  *energy = data + lambda * reg;
+  return 0;
+}
+
+}  // extern "C"

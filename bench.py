@@ -11,8 +11,18 @@ default).  At N = 1 the line also carries `batched`: the same metric for the
 64-image uneven batch (one graph per iteration with a branch per image), one
 timed step of 300 iterations after three short warm-up steps, beside the same
 images solved one after another through the single-image path (--no-batch
-skips both), and `differentiable`: 16 images of 256 x 256 through the unrolled
-forward and reverse sweeps (--no-differentiable skips it).
+skips both), `differentiable`: 16 images of 256 x 256 through the unrolled
+forward and reverse sweeps beside the same images solved one after another
+(--no-differentiable skips it), and `workloads`: the 2048 x 2048 RGB image
+(K = 8, J = 5, 20 of its iterations per step) and the 64 x 64 image (K = 3,
+J = 2, 200 iterations) through the same path, and the TV-regularised model of
+Sec. 4 on the 512 x 512 image (`tv512`, gamma = 1, lambda = 1/12, 100
+iterations; the line and tv512 carry the label error of each model against
+the generator's label map) (--no-legs skips them).  The
+line reports the dominant kernel's HBM roofline and, for the whole iteration,
+the method's algorithmic bytes and FP32 operations over the plain iteration
+time against the measured HBM bandwidth and the FP32 peak from the unit
+counts.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -63,6 +73,8 @@ def parse_args():
                     help="skip the unrolled forward+reverse measurement the default line carries under 'differentiable'")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched measurement that the default line carries under 'batched'")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the 2048 x 2048 RGB and 64 x 64 legs that the default line carries under 'workloads'")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default work plan instead of autotuning it before the timed region")
     ap.add_argument("--iters", type=int, default=0,
@@ -72,13 +84,16 @@ def parse_args():
 
 def workload_config(wl, extra=None):
     bv_mb = 4 * wl.K * wl.eta * wl.H * wl.W / 1e6
+    scene = ("seeded ellipses on a background label, N(0, 0.05^2) noise" if wl.name in ("ellipses64", "unrolled256")
+             else "seeded closed-Bezier regions with oriented gratings (amplitude 0.15) and N(0, 0.05^2) noise")
+    l2 = (f"no flush: per-iteration working set (b_v {bv_mb:.0f} MB + coefficient spectra) exceeds the 129 MB L2"
+          if bv_mb > 129 else f"L2-resident (b_v {bv_mb:.1f} MB): no flush, a latency-bound size")
     cfg = {
         "workload": f"{wl.name}: {wl.H}x{wl.W} {'RGB' if wl.C == 3 else 'gray'}, K={wl.K}, J={wl.J} (eta={wl.eta}), "
-                    f"{wl.iters} ADMM iterations, seeded closed-Bezier regions with oriented gratings (amplitude "
-                    "0.15) and N(0, 0.05^2) noise",
+                    f"{wl.iters} ADMM iterations, {scene}",
         "H": wl.H, "W": wl.W, "C": wl.C, "K": wl.K, "J": wl.J, "eta": wl.eta, "iters_per_step": wl.iters,
         "lambda": wl.lam, "gamma": wl.gamma, "Lambda": [round(float(x), 6) for x in wl.Lambda()],
-        "l2": f"no flush: per-iteration working set (b_v {bv_mb:.0f} MB + coefficient spectra) exceeds the 129 MB L2",
+        "l2": l2,
         "parallelism": "replicas (one independent image per GPU)",
     }
     if extra:
@@ -151,6 +166,44 @@ def kernel_bytes(wl):
         "col_gather": eta * Ph * 4,                 # the filter bank in
         "col_reduce_inv": K * Ph * 8 * 2,           # group sums in (at least one), T out
     }
+
+
+def iteration_bytes(wl):
+    """Algorithmic HBM bytes of one iteration: per pixel and label 8 eta (b_v
+    read and written) + 24 (s, w, b_w in; u, w, b_w out, as FP32) + the filter
+    bank read once per label, 4 eta (W/2+1)/W / K per pixel and label when the
+    bank is shared by the K labels of a wave (it is re-read per label here)."""
+    P, K, eta = wl.H * wl.W, wl.K, wl.eta
+    per = 8 * eta + 24 + 4 * eta * (wl.W // 2 + 1) / wl.W
+    return int(per * P * K)
+
+
+def iteration_flops(wl):
+    """FP32 operations of one iteration as the method's arithmetic (not the
+    instructions issued): per (label, filter) one inverse and one forward real
+    2-D FFT of H x W at 2.5 P log2 P each (the radix-2 count of a real
+    transform), the filter product on the half plane in both directions
+    (4 H (W/2+1)) and the shrinkage and dual update (6 per coefficient); per
+    label the forward FFT of u and the inverse FFT of the synthesis sum, the
+    u-step (4 per pixel) and the simplex projection (about 4 K per pixel)."""
+    import math
+
+    P, K, eta = wl.H * wl.W, wl.K, wl.eta
+    Ph = wl.H * (wl.W // 2 + 1)
+    fft2 = 2.5 * P * math.log2(P)
+    per_pair = 2 * fft2 + 4 * Ph + 6 * P
+    per_label = 2 * fft2 + 4 * P + 4 * K * P
+    return K * (eta * per_pair + per_label)
+
+
+def fp32_peak_tflops(sm_mhz):
+    """FP32 peak of the GPU from its unit counts: SMs x 128 FP32 lanes x 2
+    (an FMA counted as two operations) x SM clock."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = sm_mhz or 2070.0
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, sms, mhz
 
 
 def source_sha() -> str:
@@ -286,6 +339,7 @@ def run_ours(args):
         device_step()
     seg.synchronize()
     torch.cuda.synchronize()
+    label_error = float((labels_dev.cpu().numpy() != lab).mean())
 
     # timed region: K steps bracketed by barrier + synchronize, CUDA events on the state's stream
     clocks = ClockSampler(local)
@@ -342,15 +396,26 @@ def run_ours(args):
         peak, peak_kind = peaks()
         achieved = kb[dom] / (mean_ms[dom] / 1000.0) / 1e9
         it_ms = sum(mean_ms.values())
-        iter_alg = (8 * wl.eta + 24) * wl.H * wl.W * wl.K  # per-iteration algorithmic bytes of the method
         roofline = {
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": measured_traffic(dom), "kernel": dom, "launches_per_iteration": n_launch[dom],
             "kernel_ms_per_launch": mean_ms[dom] / n_launch[dom],
             "algorithmic_bytes_per_launch": kb[dom] / n_launch[dom], "peak_source": f"{peak_kind} hbm_gbs",
         }
-        iteration = {"ms": it_ms, "kernel_ms": mean_ms, "launches": n_launch, "algorithmic_bytes": iter_alg,
-                     "hbm_frac_algorithmic": iter_alg / (it_ms / 1000.0) / 1e9 / peak}
+        # whole iteration: the method's bytes and flops over the plain graph's
+        # time per iteration (the step's time over its iterations: it also
+        # holds the reset and the readout, so this slightly understates)
+        plain_ms = ms_max / args.steps / wl.iters
+        iter_alg = iteration_bytes(wl)
+        flops = iteration_flops(wl)
+        fpk, sms, mhz = fp32_peak_tflops(clk["sm_mhz"])
+        iteration = {"instrumented_ms": it_ms, "kernel_ms": mean_ms, "launches": n_launch,
+                     "plain_ms": plain_ms, "algorithmic_bytes": iter_alg,
+                     "hbm_frac_algorithmic": iter_alg / (plain_ms / 1000.0) / 1e9 / peak,
+                     "fp32": {"flops": flops, "achieved_tflops": flops / (plain_ms / 1000.0) / 1e12,
+                              "peak_tflops": fpk, "frac": flops / (plain_ms / 1000.0) / 1e12 / fpk,
+                              "peak_derivation": f"{sms} SMs x 128 FP32 lanes x 2 (FMA) x {mhz:.0f} MHz "
+                                                 "(median SM clock under load)"}}
     launches_per_step = 2 + (sum(n_launch.values()) * wl.iters if n_launch else 0) + 1
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -365,11 +430,18 @@ def run_ours(args):
         "roofline": roofline,
         "plan": plan,
         "iteration": iteration,
+        "label_error": label_error,
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
     seg.close()
     fb.close()
+    if rank == 0 and world == 1 and not args.no_legs and name == WORKLOAD:
+        # the other single-image workloads: 2048 x 2048 RGB (K = 8, J = 5; 20 of
+        # its 1000 iterations per step) and 64 x 64 (K = 3, J = 2, 200 iterations)
+        line["workloads"] = {"rgb2048": measure_leg("rgb2048", 20, 3, 3, not args.no_tune),
+                             "ellipses64": measure_leg("ellipses64", 200, 5, 3, not args.no_tune),
+                             "tv512": measure_tv(100, 5, 3)}
     if rank == 0 and world == 1 and not args.no_batch and name == WORKLOAD:
         # the batched form on the same GPU (the plain state is released first)
         line["batched"] = measure_batch(300, 1, 3, 30, not args.no_tune)
@@ -380,6 +452,135 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def measure_leg(name: str, iters: int, steps: int, warmup: int, tune: bool):
+    """Another single-image workload on the same GPU, timed like the main
+    line (reset + `iters` graph-replayed iterations + label readout per step,
+    CUDA events on the state's stream), with the roofline of its dominant
+    kernel kind and the whole iteration's algorithmic bytes and flops."""
+    import dataclasses
+
+    import torch
+
+    from paper_1112_1805_gb300 import binding as B
+    from paper_1112_1805_gb300.api import FilterBank, ShearletSegmenter
+
+    img, _, wl = synth.make_workload_image(name)
+    wl = dataclasses.replace(wl, iters=iters)
+    f_dev = torch.tensor(np.ascontiguousarray(img, dtype=np.float32), device="cuda")
+    fb = FilterBank(wl.H, wl.W, wl.J)
+    seg = ShearletSegmenter(fb, f_dev, wl.codebook(), wl.Lambda(), wl.gamma)
+    plan = seg.tune(3) if tune else seg.plan()
+    labels_dev = torch.empty((wl.H, wl.W), dtype=torch.int32, device="cuda")
+
+    def device_step():
+        B.seg_admm_reset(seg.handle, f_dev.data_ptr(), False)
+        B.seg_admm_step(seg.handle, wl.iters)
+        B.seg_admm_get(seg.handle, B.SEG_LABELS, labels_dev.data_ptr(), False)
+
+    for _ in range(warmup):
+        device_step()
+    seg.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(seg.stream)
+    kt = []
+    for _ in range(steps):
+        device_step()
+        try:
+            kt.append(B.seg_admm_kernel_times(seg.handle))
+        except B.ShearsegError:
+            kt.append(None)
+    ev1.record(seg.stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    seg.close()
+    fb.close()
+    del f_dev
+    torch.cuda.empty_cache()
+    units = wl.H * wl.W * wl.K * wl.iters * steps
+    plain_ms = ms / steps / wl.iters
+    peak, peak_kind = peaks()
+    out = {"value": units / (ms / 1000.0) / 1e6, "unit": UNIT, "steps": steps, "warmup": warmup,
+           "iters_per_step": wl.iters, "ms_per_step": ms / steps, "plan": plan,
+           "config": workload_config(wl),
+           "iteration": {"plain_ms": plain_ms, "algorithmic_bytes": iteration_bytes(wl),
+                         "hbm_frac_algorithmic": iteration_bytes(wl) / (plain_ms / 1000.0) / 1e9 / peak,
+                         "fp32_tflops": iteration_flops(wl) / (plain_ms / 1000.0) / 1e12}}
+    if kt and all(t is not None for t in kt):
+        kinds = [k for k in kt[0] if kt[0][k][1] > 0]
+        mean_ms = {k: statistics.mean(t[k][0] for t in kt) for k in kinds}
+        n_launch = {k: kt[0][k][1] for k in kinds}
+        dom = max(mean_ms, key=mean_ms.get)
+        kb = kernel_bytes(wl)
+        achieved = kb[dom] / (mean_ms[dom] / 1000.0) / 1e9
+        out["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                           "frac": achieved / peak, "launches_per_iteration": n_launch[dom],
+                           "kernel_ms_per_launch": mean_ms[dom] / n_launch[dom],
+                           "peak_source": f"{peak_kind} hbm_gbs"}
+        out["iteration"]["kernel_ms"] = mean_ms
+        out["iteration"]["launches"] = n_launch
+    return out
+
+
+def tv_kernel_bytes(H, W, K):
+    """Compulsory DRAM bytes of one TV iteration per kernel: the u-step's three
+    transforms (right-hand side in, half spectra through, u out; the symbol
+    read once) and the two pointwise kernels (the prox kernel reads u, b_v,
+    b_w, s and writes b_v, d, w, b_w, q: 48 B per pixel and label; the
+    right-hand side reads q and d and writes rhs: 16 B)."""
+    P, Ph = H * W, H * (W // 2 + 1)
+    return {"tv_row_fwd": K * (P * 4 + Ph * 8), "tv_col_solve": K * 2 * Ph * 8 + Ph * 4,
+            "tv_row_inv": K * (Ph * 8 + P * 4), "tv_prox": K * P * 48, "tv_rhs": K * P * 16}
+
+
+def measure_tv(iters: int, steps: int, warmup: int, lam: float = 1.0 / 12.0):
+    """The TV-regularised model of Sec. 4 on the 512 x 512 textured image
+    (K = 4) with the paper's TV weights of its stripes and fish runs (gamma =
+    1, lambda = 1/12, 100 iterations): the comparison model on the same
+    image and GPU.  Also the label error of both models against the
+    generator's label map (the paper's comparison on curved textures)."""
+    import torch
+
+    from paper_1112_1805_gb300 import binding as B
+    from paper_1112_1805_gb300.api import TVSegmenter
+
+    img, lab, wl = synth.make_workload_image("bezier512")
+    f_dev = torch.tensor(np.ascontiguousarray(img, dtype=np.float32), device="cuda")
+    seg = TVSegmenter(f_dev, wl.codebook(), lam, 1.0)
+    labels_dev = torch.empty((wl.H, wl.W), dtype=torch.int32, device="cuda")
+
+    def device_step():
+        B.tv_admm_reset(seg.handle, f_dev.data_ptr(), False)
+        B.tv_admm_step(seg.handle, iters)
+        B.tv_admm_get(seg.handle, B.SEG_LABELS, labels_dev.data_ptr(), False)
+
+    for _ in range(warmup):
+        device_step()
+    seg.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(seg.stream)
+    for _ in range(steps):
+        device_step()
+    ev1.record(seg.stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    label_error = float((labels_dev.cpu().numpy() != lab).mean())
+    kt = seg.kernel_times(5)
+    seg.close()
+    units = wl.H * wl.W * wl.K * iters * steps
+    kb = tv_kernel_bytes(wl.H, wl.W, wl.K)
+    dom = max(kt, key=kt.get)
+    peak, peak_kind = peaks()
+    achieved = kb[dom] / (kt[dom] / 1000.0) / 1e9
+    return {"value": units / (ms / 1000.0) / 1e6, "unit": UNIT, "steps": steps, "warmup": warmup,
+            "iters_per_step": iters, "ms_per_step": ms / steps, "label_error": label_error,
+            "kernel_ms": kt, "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                                          "unit": "GB/s", "frac": achieved / peak,
+                                          "peak_source": f"{peak_kind} hbm_gbs"},
+            "workload": f"tv512: bezier512's image (512x512 gray, K=4) with the TV regulariser of Sec. 4 "
+                        f"(labels coupled per pixel, periodic forward differences), gamma=1, lambda=1/12, "
+                        f"{iters} ADMM iterations per step"}
 
 
 def measure_batch(iters: int, steps: int, warmup_steps: int, warmup_iters: int, tune: bool):
@@ -500,8 +701,10 @@ def measure_differentiable(steps: int, warmup: int, n_images: int = 16):
         one_pass()
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / steps
-    plain_ms = None
-    # the plain iteration on the same images for comparison: T iterations per image
+    # the plain iteration on the same images for comparison, T iterations per
+    # image: all images queued at once on their own streams (forward only), and
+    # one image after another through the single-image path (like for like
+    # with the plain line: one solve at a time)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(segs[0].stream)
     for sg in segs:
@@ -511,12 +714,20 @@ def measure_differentiable(steps: int, warmup: int, n_images: int = 16):
     e1.record(segs[0].stream)
     torch.cuda.synchronize()
     plain_ms = e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for sg in segs:
+        B.seg_admm_step(sg.handle, T)
+        sg.synchronize()
+    seq_s = time.perf_counter() - t0
     units = n_images * wl.H * wl.W * wl.K * T
     for sg in segs:
         sg.close()
     fb.close()
     return {"value": units / dt / 1e6, "unit": UNIT, "ms_per_step": dt * 1000.0, "steps": steps, "warmup": warmup,
             "forward_only_value": units / (plain_ms / 1000.0) / 1e6,
+            "plain_sequential_value": units / seq_s / 1e6,
+            "vs_plain_sequential": (units / dt) / (units / seq_s),
             "plan": {k: plan[k] for k in ("wave_mib", "col_ctas_per_sm")},
             "workload": f"{n_images} x 256x256 gray, K=4, J=3 (eta=29), {T} unrolled ADMM iterations from zero with "
                         f"checkpoints every {ck}, reverse sweep for a fixed cotangent of w (gradients w.r.t. "

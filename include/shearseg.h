@@ -332,6 +332,68 @@ int seg_admm_batch_sync(seg_batch* batch);
 /* Releases every state and bank of the batch.  NULL is accepted. */
 int seg_admm_batch_destroy(seg_batch* batch);
 
+/* ---------------------------------------------------------------------------
+ * TV-regularised segmentation, the comparison model of Sec. 4 (eq. TVreg):
+ *   min_u <u, s> + lambda sum_pixels |(I_q (x) grad) u| + iota_C(u)
+ * with |(I_q (x) grad) u|(x) = (|grad u_1(x)|^2 + ... + |grad u_q(x)|^2)^(1/2)
+ * (per_label = 0: the labels coupled per pixel, as eq. TVreg writes it) or
+ * sum_k |grad u_k(x)| (per_label = 1: the alternative the paper mentions).
+ * The paper fixes neither the difference scheme nor the solver; readings:
+ * grad is the forward difference with periodic boundary, and the ADMM is the
+ * one of Sec. 3 with S replaced by grad (splitting v = (I_q (x) grad) u,
+ * w = u, same gamma):
+ *   u   = (I + grad^T grad)^(-1) [ grad^T (v - b_v) + (w - b_w) - gamma s ]
+ *   v   = group shrinkage of b_v + grad u by gamma lambda, b_v += grad u - v
+ *   w   = pixelwise projection of b_w + u onto the simplex, b_w += u - w
+ * from v = b_v = w = b_w = 0.  I + grad^T grad is diagonal in the DFT basis
+ * (symbol 1 + 4 sin^2(pi n1/H) + 4 sin^2(pi n2/W)), so the u-step is one
+ * filtered 2-D FFT per label.  Gradients and their duals are [K][2][H][W]
+ * (component 0 along the row axis).
+ * ------------------------------------------------------------------------- */
+typedef struct tv_state tv_state;
+typedef struct {
+  float gamma;   /* ADMM step, > 0                                           */
+  float lambda;  /* regularisation weight, >= 0 (threshold gamma * lambda)   */
+  int per_label; /* 0: labels coupled per pixel (eq. TVreg); 1: per label    */
+} tv_params;
+
+/* f: device [C][H][W]; codebook: HOST [K][C]; sizes as for shfilters_build
+ * (H and W/2 products of 2, 3 and 5, W even, 8..2048).  The state owns its
+ * buffers and, if `stream` is NULL, a private stream.  Synchronises.  Errors:
+ * SHF_ERR_ARG, SHF_ERR_SIZE, SHF_ERR_NONFINITE, SHF_ERR_OOM, SHF_ERR_CUDA. */
+int tv_admm_init(int H, int W, const float* f, int C, const float* codebook, int K, const tv_params* params,
+                 void* stream, tv_state** out);
+
+/* New image of the same size (device, or host if f_on_host), data term
+ * recomputed, state back to zero.  Synchronises. */
+int tv_admm_reset(tv_state* st, const float* f, int f_on_host);
+
+/* Enqueues n_iters iterations (replays of a CUDA graph of one iteration when
+ * the stream can be captured). */
+int tv_admm_step(tv_state* st, int n_iters);
+
+/* Readouts as seg_admm_get: SEG_U, SEG_W, SEG_BW, SEG_S ([K][H][W]), SEG_BV
+ * and SEG_V ([K][2][H][W]), SEG_LABELS, SEG_GAP ([H][W]), SEG_ENERGY (double:
+ * <w, s> + lambda TV(w)), SEG_ITER (int, host only).  Host destinations and
+ * SEG_ENERGY synchronise. */
+int tv_admm_get(tv_state* st, int what, void* dst, int dst_on_host);
+
+/* Overwrites SEG_W, SEG_BW, SEG_BV or SEG_V (v itself; set SEG_BV first,
+ * since the state keeps v - b_v, which setting SEG_BV leaves unchanged) and
+ * rebuilds the next u-step's right-hand side.  Synchronises. */
+int tv_admm_set(tv_state* st, int what, const void* src, int src_on_host);
+
+/* Instrumentation (no counterpart in the paper): runs n iterations launched
+ * one by one with CUDA events between the kernels and writes the mean
+ * milliseconds of each of the iteration's 5 kernels to ms (room for 5), *nk
+ * (may be NULL) = 5.  Advances the iterate by n.  Synchronises. */
+int tv_admm_kernel_times(tv_state* st, int n, float* ms, int* nk);
+const char* tv_admm_kernel_name(int i);
+
+int tv_admm_sync(tv_state* st);
+/* Releases the state (synchronises its stream).  NULL is accepted. */
+int tv_admm_destroy(tv_state* st);
+
 /* Waits for the state's stream. */
 int seg_admm_sync(seg_state* st);
 

@@ -269,6 +269,107 @@ class ShearletBatch:
         return _BorrowedState(B.seg_admm_batch_image(self.handle, i), K, C, H, W, 2 ** (J + 2) - 3)
 
 
+class TVSegmenter:
+    """ADMM state of the TV-regularised model of Sec. 4 (eq. TVreg) for one
+    image: the same data term, simplex constraint and ADMM as
+    ShearletSegmenter with the shearlet transform replaced by the periodic
+    forward-difference gradient (labels coupled per pixel, or per label).
+
+    f: [C, H, W] or [H, W] float32 CUDA tensor; codebook: [K, C] host values."""
+
+    def __init__(self, f: torch.Tensor, codebook, lam: float, gamma: float = 1.0, per_label: bool = False,
+                 stream=None):
+        if f.dim() == 2:
+            f = f.unsqueeze(0)
+        _dev_f32(f, "f")
+        cb = np.asarray(codebook, dtype=np.float64).reshape(-1, f.shape[0])
+        self.K, self.C = cb.shape
+        self.H, self.W = int(f.shape[1]), int(f.shape[2])
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.stream.wait_stream(torch.cuda.current_stream())
+        self.handle = B.tv_admm_init(self.H, self.W, f.data_ptr(), self.C, cb.ravel().tolist(), self.K, gamma, lam,
+                                     per_label, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            B.tv_admm_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int) -> None:
+        B.tv_admm_step(self.handle, n)
+
+    def synchronize(self) -> None:
+        B.tv_admm_sync(self.handle)
+
+    def reset(self, f) -> None:
+        if isinstance(f, torch.Tensor) and f.is_cuda:
+            _dev_f32(f, "f")
+            self.stream.wait_stream(torch.cuda.current_stream())
+            B.tv_admm_reset(self.handle, f.data_ptr(), False)
+        else:
+            a = f if isinstance(f, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(f, dtype=np.float32))
+            B.tv_admm_reset(self.handle, a.contiguous().data_ptr(), True)
+
+    def _shape(self, what: int):
+        K, H, W = self.K, self.H, self.W
+        if what in (B.SEG_U, B.SEG_W, B.SEG_BW, B.SEG_S):
+            return (K, H, W), torch.float32
+        if what in (B.SEG_BV, B.SEG_V):
+            return (K, 2, H, W), torch.float32
+        if what == B.SEG_LABELS:
+            return (H, W), torch.int32
+        if what == B.SEG_GAP:
+            return (H, W), torch.float32
+        raise ValueError(what)
+
+    def get(self, what: int) -> torch.Tensor:
+        if what == B.SEG_ENERGY:
+            buf = np.zeros(1, dtype=np.float64)
+            B.tv_admm_get(self.handle, what, buf.ctypes.data, True)
+            return torch.tensor(buf[0], dtype=torch.float64)
+        if what == B.SEG_ITER:
+            buf = np.zeros(1, dtype=np.int32)
+            B.tv_admm_get(self.handle, what, buf.ctypes.data, True)
+            return torch.tensor(int(buf[0]))
+        shape, dt = self._shape(what)
+        out = torch.empty(shape, dtype=dt, device="cuda")
+        B.tv_admm_get(self.handle, what, out.data_ptr(), False)
+        self.synchronize()
+        return out
+
+    def get_host(self, what: int, out: torch.Tensor | None = None) -> torch.Tensor:
+        shape, dt = self._shape(what)
+        if out is None:
+            out = torch.empty(shape, dtype=dt, pin_memory=True)
+        B.tv_admm_get(self.handle, what, out.data_ptr(), True)
+        return out
+
+    def set(self, what: int, src: torch.Tensor) -> None:
+        shape, dt = self._shape(what)
+        src = src.to(dt).contiguous()
+        if tuple(src.shape) != shape:
+            raise ValueError(f"expected shape {shape}, got {tuple(src.shape)}")
+        if src.is_cuda:
+            self.stream.wait_stream(torch.cuda.current_stream())
+        B.tv_admm_set(self.handle, what, src.data_ptr(), not src.is_cuda)
+
+    def energy(self) -> float:
+        return float(self.get(B.SEG_ENERGY))
+
+    def labels(self) -> torch.Tensor:
+        return self.get(B.SEG_LABELS)
+
+    def kernel_times(self, n: int = 5) -> dict:
+        """Mean milliseconds per kernel over n iterations (advances the iterate)."""
+        return B.tv_admm_kernel_times(self.handle, n)
+
+
 class UnrolledSegmentation(torch.autograd.Function):
     """w_T of T ADMM iterations from the zero state as a differentiable function
     of the image f [C, H, W], the codebook [K, C] and the weights Lambda [J+1]

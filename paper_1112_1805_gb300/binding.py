@@ -49,8 +49,14 @@ class seg_params(ctypes.Structure):
     ]
 
 
+class tv_params(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_float), ("lambda_", ctypes.c_float), ("per_label", ctypes.c_int)]
+
+
 _VP = ctypes.c_void_p
 _I = ctypes.c_int
+
+
 class seg_plan(ctypes.Structure):
     _fields_ = [("fast", ctypes.c_int), ("wave_mib", ctypes.c_int), ("col_ctas_per_sm", ctypes.c_int),
                 ("tile_cols", ctypes.c_int), ("tile_rows", ctypes.c_int), ("groups", ctypes.c_int),
@@ -97,6 +103,16 @@ _SIG = {
     "seg_admm_unrolled_grads": (_I, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _VP, _VP]),
     "seg_admm_sync": (_I, [_VP]),
     "seg_admm_destroy": (_I, [_VP]),
+    "tv_admm_init": (_I, [_I, _I, _VP, _I, ctypes.POINTER(ctypes.c_float), _I, ctypes.POINTER(tv_params), _VP,
+                          ctypes.POINTER(_VP)]),
+    "tv_admm_reset": (_I, [_VP, _VP, _I]),
+    "tv_admm_step": (_I, [_VP, _I]),
+    "tv_admm_get": (_I, [_VP, _I, _VP, _I]),
+    "tv_admm_set": (_I, [_VP, _I, _VP, _I]),
+    "tv_admm_kernel_times": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_I)]),
+    "tv_admm_kernel_name": (ctypes.c_char_p, [_I]),
+    "tv_admm_sync": (_I, [_VP]),
+    "tv_admm_destroy": (_I, [_VP]),
 }
 
 
@@ -335,3 +351,48 @@ def seg_admm_unrolled_grads(state: int, K: int, C: int, J: int, dL_df: int = 0, 
     _call("seg_admm_unrolled_grads", _VP(state), dc, dl, _VP(dL_df) if dL_df else None,
           _VP(dL_ds) if dL_ds else None)
     return list(dc), list(dl)
+
+
+# ---------------------------------------------------------------------------
+# TV-regularised segmentation (Sec. 4, eq. TVreg)
+# ---------------------------------------------------------------------------
+def tv_admm_init(H: int, W: int, f: int, C: int, codebook, K: int, gamma: float, lam: float, per_label: bool = False,
+                 stream=None) -> int:
+    cb = (ctypes.c_float * (K * C))(*[float(x) for x in codebook])
+    p = tv_params(float(gamma), float(lam), int(bool(per_label)))
+    out = _VP()
+    _call("tv_admm_init", int(H), int(W), _VP(f), int(C), cb, int(K), ctypes.byref(p), _stream(stream),
+          ctypes.byref(out))
+    return out.value
+
+
+def tv_admm_reset(state: int, f: int, f_on_host: bool) -> None:
+    _call("tv_admm_reset", _VP(state), _VP(f), int(bool(f_on_host)))
+
+
+def tv_admm_step(state: int, n_iters: int) -> None:
+    _call("tv_admm_step", _VP(state), int(n_iters))
+
+
+def tv_admm_get(state: int, what: int, dst: int, dst_on_host: bool) -> None:
+    _call("tv_admm_get", _VP(state), int(what), _VP(dst), int(bool(dst_on_host)))
+
+
+def tv_admm_set(state: int, what: int, src: int, src_on_host: bool) -> None:
+    _call("tv_admm_set", _VP(state), int(what), _VP(src), int(bool(src_on_host)))
+
+
+def tv_admm_kernel_times(state: int, n: int) -> dict:
+    """{kernel: mean milliseconds} over n iterations launched one by one."""
+    ms = (ctypes.c_float * 8)()
+    nk = _I()
+    _call("tv_admm_kernel_times", _VP(state), int(n), ms, ctypes.byref(nk))
+    return {lib().tv_admm_kernel_name(i).decode(): float(ms[i]) for i in range(nk.value)}
+
+
+def tv_admm_sync(state: int) -> None:
+    _call("tv_admm_sync", _VP(state))
+
+
+def tv_admm_destroy(state: int) -> None:
+    _call("tv_admm_destroy", _VP(state))

@@ -5,6 +5,7 @@
 
 #include "shf_fast.h"
 #include "shf_fft16.cuh"
+#include "shf_simplex.cuh"
 
 namespace shf {
 namespace fast {
@@ -678,35 +679,6 @@ __global__ void __launch_bounds__(256, 2)
     prc = prn;
   }
   cp_async_commit_wait_all();  // no copy outlives the kernel
-}
-
-// Euclidean projection of g[0..K) onto the unit simplex, as the paper
-// constructs it: project onto the hyperplane sum = 1 (g + (1 - sum g)/q), set
-// the negative components to zero and repeat on the remaining ones (at most K
-// passes; the result is exact).
-template <int KMAX>
-__device__ __forceinline__ void simplex_project(float (&g)[KMAX], int K) {
-  unsigned act = (1u << K) - 1u;
-  float tau = 0.f;
-  for (int pass = 0; pass < K; ++pass) {
-    float sum = 0.f;
-    int q = 0;
-#pragma unroll
-    for (int k = 0; k < KMAX; ++k)
-      if ((act >> k) & 1u) {
-        sum += g[k];
-        ++q;
-      }
-    tau = (sum - 1.f) / static_cast<float>(q);
-    unsigned nact = act;
-#pragma unroll
-    for (int k = 0; k < KMAX; ++k)
-      if (((act >> k) & 1u) && g[k] - tau < 0.f) nact &= ~(1u << k);
-    if (nact == act) break;
-    act = nact;
-  }
-#pragma unroll
-  for (int k = 0; k < KMAX; ++k) g[k] = ((act >> k) & 1u) ? g[k] - tau : 0.f;
 }
 
 // Geometry of the u/w-step kernel: a CTA takes NR rows and runs one row

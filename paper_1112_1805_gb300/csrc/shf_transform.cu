@@ -23,6 +23,7 @@
 #include <algorithm>
 
 #include "shf_internal.h"
+#include "shf_simplex.cuh"
 
 namespace shf {
 
@@ -281,34 +282,6 @@ __global__ void __launch_bounds__(kRowThreads)
   if (threadIdx.x == 0) partial[plane * gridDim.x + blockIdx.x] = red[0];
 }
 
-// Euclidean projection of g[0..K) onto the unit simplex by the paper's
-// construction: project onto the hyperplane sum = 1 (g + (1 - sum g)/q), set
-// the negative components to zero and repeat on the remaining ones (at most K
-// passes; exact result).
-__device__ __forceinline__ void project_simplex(float (&g)[kMaxK], int K) {
-  unsigned act = (K >= 32) ? 0xffffffffu : ((1u << K) - 1u);
-  float tau = 0.f;
-  for (int pass = 0; pass < K; ++pass) {
-    float sum = 0.f;
-    int q = 0;
-#pragma unroll
-    for (int k = 0; k < kMaxK; ++k)
-      if ((act >> k) & 1u) {
-        sum += g[k];
-        ++q;
-      }
-    tau = (sum - 1.f) / static_cast<float>(q);
-    unsigned nact = act;
-#pragma unroll
-    for (int k = 0; k < kMaxK; ++k)
-      if (((act >> k) & 1u) && g[k] - tau < 0.f) nact &= ~(1u << k);
-    if (nact == act) break;
-    act = nact;
-  }
-#pragma unroll
-  for (int k = 0; k < kMaxK; ++k) g[k] = ((act >> k) & 1u) ? g[k] - tau : 0.f;
-}
-
 // u-step (u = 1/2 [S^T(v - b_v) + (w - b_w) - gamma s], A^T A = 2I), w-step
 // (pixelwise projection of g_w = b_w + u onto the simplex), b_w = g_w - w,
 // and the row-forward transform of u for the next analysis.  Shared memory:
@@ -367,8 +340,8 @@ __global__ void __launch_bounds__(kRowThreads)
       px[k] = gx[k];
       py[k] = gy[k];
     }
-    project_simplex(px, K);
-    project_simplex(py, K);
+    simplex_project<kMaxK>(px, K);
+    simplex_project<kMaxK>(py, K);
 #pragma unroll
     for (int k = 0; k < kMaxK; ++k) {
       if (k < K) {

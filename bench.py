@@ -27,7 +27,9 @@ counts.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 N > 1 is launched by torchrun: every rank solves its own copy of the image
-(independent problems, no collective on the data path; weak scaling).
+(independent problems, no collective on the data path; weak scaling), and the
+`batched` leg shards the 64 images whole across the ranks by LPT on their cost
+(strong scaling of the fixed batch; the time is the largest over the ranks).
 --impl reference times the FP64 CPU oracle (the baseline arm) on a bounded
 sample of the same workload.
 """
@@ -442,9 +444,12 @@ def run_ours(args):
         line["workloads"] = {"rgb2048": measure_leg("rgb2048", 20, 3, 3, not args.no_tune),
                              "ellipses64": measure_leg("ellipses64", 200, 5, 3, not args.no_tune),
                              "tv512": measure_tv(100, 5, 3)}
-    if rank == 0 and world == 1 and not args.no_batch and name == WORKLOAD:
-        # the batched form on the same GPU (the plain state is released first)
-        line["batched"] = measure_batch(300, 1, 3, 30, not args.no_tune)
+    if not args.no_batch and name == WORKLOAD:
+        # the batched form on the same GPUs (the plain state is released
+        # first): the 64-image batch sharded over the ranks
+        b = measure_batch(300, 1, 3, 30, not args.no_tune, rank, world)
+        if rank == 0:
+            line["batched"] = b
     if rank == 0 and world == 1 and not args.no_differentiable and name == WORKLOAD:
         line["differentiable"] = measure_differentiable(2, 1)
     if rank == 0:
@@ -583,48 +588,68 @@ def measure_tv(iters: int, steps: int, warmup: int, lam: float = 1.0 / 12.0):
                         f"{iters} ADMM iterations per step"}
 
 
-def measure_batch(iters: int, steps: int, warmup_steps: int, warmup_iters: int, tune: bool):
+def measure_batch(iters: int, steps: int, warmup_steps: int, warmup_iters: int, tune: bool, rank: int = 0,
+                  world: int = 1):
     """The uneven batch: 64 seeded images (384 x 640 first, sides 128..1024), K
-    in 2..6, J = floor(log2(min side)/2), all images in one CUDA graph per
-    iteration.  Returns the summed Mpixel*label*iter/s and its timing."""
+    in 2..6, J = floor(log2(min side)/2).  With N ranks the images are sharded
+    whole by LPT on their cost (shard.share; no collective on the data path)
+    and each rank solves its share as one batch (one CUDA graph per
+    iteration); the time is the largest over the ranks (strong scaling: the
+    batch is fixed).  Returns the summed Mpixel*label*iter/s and its timing;
+    at N = 1 also the same images solved one after another."""
     import torch
+    import torch.distributed as dist
 
+    from paper_1112_1805_gb300 import shard
     from paper_1112_1805_gb300.api import ShearletBatch
 
     shapes = synth.batch_shapes()
     rng = np.random.default_rng(synth.seed_for(3))
-    imgs, cbs, lams, units = [], [], [], 0
-    for H, W, K, J in shapes:
+    host, cbs, lams, units = [], [], [], 0
+    for H, W, K, J in shapes:  # every rank draws every image, in order, and keeps its share
         cb = np.array([[0.2 + 0.6 * k / (K - 1)] for k in range(K)])
         img, _ = synth.ellipse_image(H, W, cb, rng)
-        imgs.append(torch.tensor(img.astype(np.float32), device="cuda"))
+        host.append(img.astype(np.float32))
         cbs.append(cb)
         lams.append(synth.scale_weights(0.1, J))
         units += H * W * K * iters
-    batch = ShearletBatch(imgs, cbs, lams, 1.0)
+    mine = shard.share(shapes, rank, world)
+    imgs = [torch.tensor(host[i], device="cuda") for i in mine]
+    batch = ShearletBatch(imgs, [cbs[i] for i in mine], [lams[i] for i in mine], 1.0)
     if tune:
         batch.tune(5)
     for _ in range(warmup_steps):
         batch.step(warmup_iters)
     batch.synchronize()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(batch.stream)
     for _ in range(steps):
         batch.step(iters)
     ev1.record(batch.stream)
     ev1.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    plans = [batch.image(i).plan() for i in range(len(shapes))]
+    t = torch.tensor([ev0.elapsed_time(ev1)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    plans = [batch.image(j).plan() for j in range(len(mine))]
     batch.close()
     value = units * steps / (ms / 1000.0) / 1e6
-    seq = measure_sequential(shapes, imgs, cbs, lams, plans)
-    return {"value": value, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
-            "warmup": warmup_steps, "tuned": tune,
-            "sequential_value": seq, "speedup_vs_sequential": value / seq,
-            "workload": f"batch: {len(shapes)} images, sides 128..1024 (first 384x640), K 2..6, "
-                        f"J = floor(log2(min side)/2), {iters} iterations per step, one graph per iteration "
-                        f"with a branch per image; sequential_value: the same images one after another through "
-                        f"the single-image path with the batch's plans"}
+    out = {"value": value, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+           "warmup": warmup_steps, "tuned": tune, "n_ranks": world, "images_per_rank_max": max(
+               len(shard.share(shapes, r, world)) for r in range(world)),
+           "workload": f"batch: {len(shapes)} images, sides 128..1024 (first 384x640), K 2..6, "
+                       f"J = floor(log2(min side)/2), {iters} iterations per step, one graph per iteration "
+                       f"with a branch per image; {world} rank(s), images sharded whole by LPT on H W K eta "
+                       f"(strong scaling of the fixed batch); sequential_value: the same images one after "
+                       f"another through the single-image path with the batch's plans"}
+    if world == 1:
+        seq = measure_sequential(shapes, imgs, [cbs[i] for i in mine], [lams[i] for i in mine], plans)
+        out["sequential_value"] = seq
+        out["speedup_vs_sequential"] = value / seq
+    return out
 
 
 def measure_sequential(shapes, imgs, cbs, lams, plans, iters: int = 20, warmup: int = 3):

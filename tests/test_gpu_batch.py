@@ -87,3 +87,23 @@ def test_uneven_batch_shapes_first_iterations():
         w = batch.image(i).get(B.SEG_W)
         assert float(w.min()) >= 0 and float((w.sum(0) - 1).abs().max()) < 1e-5
     batch.close()
+
+
+def test_sharded_batch_solver_on_one_rank(oracle_mod):
+    # the product's sharded batched solve (shard.solve_batch_sharded with the
+    # GPU batch solver) on one rank: the label maps of every image, against
+    # the oracle's after the same number of iterations
+    need_cuda()
+    from paper_1112_1805_gb300 import shard
+
+    shapes5 = [(64, 96, 2, 2, 1), (48, 80, 3, 1, 1), (32, 32, 4, 2, 1), (30, 50, 5, 2, 1), (40, 64, 3, 2, 1)]
+    data = _images(shapes5, 77)
+    T = 20
+    shapes = [(H, W, K, J) for H, W, K, J, _ in shapes5]
+    solver = shard.batch_solver([d[0] for d in data], [d[1] for d in data], [d[2] for d in data], 1.0, T)
+    res = shard.solve_batch_sharded(shapes, solver, 0, 1)
+    assert sorted(res) == list(range(len(shapes)))
+    for i, (img, cb, Lam) in enumerate(data):
+        o = oracle_mod.admm_run(img.astype(np.float64), cb.astype(np.float32).astype(np.float64), len(Lam) - 1,
+                                Lam.astype(np.float32).astype(np.float64), 1.0, T)
+        assert labels_agree(res[i], o["labels"], o["gap"]), i

@@ -68,3 +68,64 @@ def test_solve_sharded_gloo_world2(tmp_path):
     costs = [shard.image_cost(*s) for s in shapes]
     assert [list(h0), list(h1)] == shard.lpt_partition(costs, 2)
     assert all(r0[i, 2] == (0 if i in set(h0) else 1) for i in range(11))
+
+
+def _problem_set(n=6):
+    """Small seeded images of uneven sizes (host arrays) with their codebooks and weights."""
+    rng = np.random.default_rng(synth.seed_for(3, 900))
+    sides = [(16, 24), (24, 16), (32, 32), (16, 16), (20, 30), (24, 24), (18, 28), (28, 20)]
+    shapes, images, cbs, lams = [], [], [], []
+    for i in range(n):
+        H, W = sides[i % len(sides)]
+        K, J = 2 + i % 3, 1 + i % 2
+        cb = np.array([[0.2 + 0.6 * k / (K - 1)] for k in range(K)])
+        img, _ = synth.ellipse_image(H, W, cb, rng, n_ellipses=3)
+        shapes.append((H, W, K, J))
+        images.append(img.astype(np.float32))
+        cbs.append(cb)
+        lams.append(synth.scale_weights(0.1, J))
+    return shapes, images, cbs, lams
+
+
+def _oracle_solver(images, cbs, lams, iters):
+    """CPU stand-in for shard.batch_solver with the same signature: each
+    image of the share solved by the FP64 oracle; returns label maps."""
+    import oracle
+
+    def solve(indices):
+        out = {}
+        for i in indices:
+            o = oracle.admm_run(images[i].astype(np.float64), cbs[i], len(lams[i]) - 1, lams[i], 1.0, iters)
+            out[i] = o["labels"]
+        return out
+
+    return solve
+
+
+def _batch_worker(rank, world, port, n, iters, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    shapes, images, cbs, lams = _problem_set(n)
+    res = shard.solve_batch_sharded(shapes, _oracle_solver(images, cbs, lams, iters), rank, world)
+    for i, lab in res.items():
+        np.save(os.path.join(out_dir, f"r{rank}_{i}.npy"), lab)
+    np.save(os.path.join(out_dir, f"share{rank}.npy"), np.array(shard.share(shapes, rank, world), dtype=np.int64))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_solve_batch_sharded_gloo_world2_real_solves(tmp_path, oracle_mod):
+    # the product's sharded batched solve over two gloo ranks on CPU, each rank
+    # solving its LPT share for real (the oracle standing in for the GPU
+    # batch); every rank gets every label map, equal to a one-process solve
+    n, iters = 6, 8
+    port = _free_port()
+    mp.start_processes(_batch_worker, args=(2, port, n, iters, str(tmp_path)), nprocs=2, join=True,
+                       start_method="spawn")
+    shapes, images, cbs, lams = _problem_set(n)
+    ref = _oracle_solver(images, cbs, lams, iters)(list(range(n)))
+    for rank in (0, 1):
+        for i in range(n):
+            assert np.array_equal(np.load(tmp_path / f"r{rank}_{i}.npy"), ref[i]), (rank, i)
+    s0, s1 = np.load(tmp_path / "share0.npy"), np.load(tmp_path / "share1.npy")
+    assert len(s0) and len(s1) and set(s0).isdisjoint(set(s1)) and sorted(list(s0) + list(s1)) == list(range(n))

@@ -26,7 +26,8 @@ __all__ = [
     "data_term", "soft_shrink", "project_simplex", "admm_iterate", "admm_run", "energy",
     "labels", "thresholds", "zero_state", "unrolled_vjp", "ce_loss", "unrolled_grads",
     "tv_grad", "tv_grad_adj", "tv_solve", "tv_shrink", "tv_zero_state", "tv_admm_iterate", "tv_admm_run",
-    "tv_energy",
+    "tv_energy", "NL_PARAMS", "nl_distance", "nl_graph", "nl_D", "nl_Dt", "nl_solve", "nl_zero_state",
+    "nl_admm_iterate", "nl_admm_run", "nl_energy",
 ]
 
 
@@ -34,7 +35,9 @@ def build(force: bool = False) -> str:
     """Compile the oracle shared library with g++ (FP64, -O2, pthreads)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC]
+        # no fused multiply-adds: the NL-means graph compares patch distances
+        # that must round the same way on every host
+        cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -76,6 +79,15 @@ def lib():
                 "oracle_tv_admm_iterate": (c_int, [c_int, c_int, c_int, D, c_double, c_double, c_int, c_int,
                                                    D, D, D, D, D, D]),
                 "oracle_tv_energy": (c_int, [c_int, c_int, c_int, D, D, c_double, c_int, D]),
+                "oracle_nl_distance": (c_double, [c_int, c_int, c_int, D, c_int, c_double, c_int, c_int, c_int,
+                                                  c_int]),
+                "oracle_nl_graph": (c_int, [c_int, c_int, c_int, D, c_int, c_int, c_double, c_int, I, I]),
+                "oracle_nl_D": (c_int, [c_int, c_int, c_int, c_int, I, D, D]),
+                "oracle_nl_Dt": (c_int, [c_int, c_int, c_int, c_int, I, D, D]),
+                "oracle_nl_solve": (c_int, [c_int, c_int, c_int, c_int, I, D, D]),
+                "oracle_nl_admm_iterate": (c_int, [c_int, c_int, c_int, c_int, I, D, c_double, c_double, c_int,
+                                                   D, D, D, D, D, D]),
+                "oracle_nl_energy": (c_int, [c_int, c_int, c_int, c_int, I, D, D, c_double, D]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -416,4 +428,115 @@ def tv_admm_run(f, codebook, lam: float, gamma: float, T: int, per_label: bool =
     st["s"] = s
     st["labels"], st["gap"] = labels(st["w"])
     st["energy"] = tv_energy(st["w"], s, lam, per_label)
+    return st
+
+
+# ---------------------------------------------------------------------------
+# NL-means regulariser (Sec. 4): D from patch similarities of f.  Graphs are
+# (nbr [P, m] int32, increasing index, -1 padded; deg [P]); D's coefficients
+# and their duals are [K, m, H, W].
+# ---------------------------------------------------------------------------
+# patch size p, search window varpi, Gaussian a, neighbours per pixel mt (Sec. 4)
+NL_PARAMS = {"p": 5, "win": 15, "a": 2.0, "mt": 5}
+
+
+def _i32(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def nl_distance(f, i, j, p: int = 5, a: float = 2.0) -> float:
+    """d_a between pixels i = (row, col) and j of f [C, H, W] (or [H, W])."""
+    f = _f64(f)
+    if f.ndim == 2:
+        f = f[None]
+    C, H, W = f.shape
+    return float(lib().oracle_nl_distance(H, W, C, _d(f), int(p), float(a), int(i[0]), int(i[1]), int(j[0]),
+                                          int(j[1])))
+
+
+def nl_graph(f, p: int = 5, win: int = 15, a: float = 2.0, mt: int = 5):
+    """(nbr [H W, 2 mt], deg [H W]) of the NL-means construction of Sec. 4."""
+    f = _f64(f)
+    if f.ndim == 2:
+        f = f[None]
+    C, H, W = f.shape
+    nbr = np.empty((H * W, 2 * mt), dtype=np.int32)
+    deg = np.empty(H * W, dtype=np.int32)
+    _check(lib().oracle_nl_graph(H, W, C, _d(f), int(p), int(win), float(a), int(mt),
+                                 nbr.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                 deg.ctypes.data_as(ctypes.POINTER(ctypes.c_int))), "nl_graph")
+    return nbr, deg
+
+
+def nl_D(nbr, u) -> np.ndarray:
+    u = _f64(u)
+    K, H, W = u.shape
+    nb, pn = _i32(nbr)
+    m = nb.shape[1]
+    q = np.empty((K, m, H, W))
+    _check(lib().oracle_nl_D(H, W, K, m, pn, _d(u), _d(q)), "nl_D")
+    return q
+
+
+def nl_Dt(nbr, q) -> np.ndarray:
+    q = _f64(q)
+    K, m, H, W = q.shape
+    nb, pn = _i32(nbr)
+    u = np.empty((K, H, W))
+    _check(lib().oracle_nl_Dt(H, W, K, m, pn, _d(q), _d(u)), "nl_Dt")
+    return u
+
+
+def nl_solve(nbr, rhs) -> np.ndarray:
+    """(I + D^T D)^-1 rhs per plane (conjugate gradients to 1e-13)."""
+    rhs = _f64(rhs)
+    K, H, W = rhs.shape
+    nb, pn = _i32(nbr)
+    u = np.empty_like(rhs)
+    _check(lib().oracle_nl_solve(H, W, K, nb.shape[1], pn, _d(rhs), _d(u)), "nl_solve")
+    return u
+
+
+def nl_zero_state(K: int, m: int, H: int, W: int) -> dict:
+    return {"v": np.zeros((K, m, H, W)), "bv": np.zeros((K, m, H, W)), "w": np.zeros((K, H, W)),
+            "bw": np.zeros((K, H, W)), "u": np.zeros((K, H, W))}
+
+
+def nl_admm_iterate(state: dict, s, nbr, lam: float, gamma: float, T: int, record_residual: bool = False):
+    s = _f64(s)
+    K, H, W = s.shape
+    nb, pn = _i32(nbr)
+    for key in ("v", "bv", "w", "bw", "u"):
+        assert state[key].dtype == np.float64 and state[key].flags.c_contiguous
+    res = np.zeros(max(T, 1)) if record_residual else None
+    rc = lib().oracle_nl_admm_iterate(H, W, K, nb.shape[1], pn, _d(s), float(lam), float(gamma), int(T),
+                                      _d(state["v"]), _d(state["bv"]), _d(state["w"]), _d(state["bw"]),
+                                      _d(state["u"]), _d(res) if res is not None else None)
+    _check(rc, "nl_admm_iterate")
+    return res[:T] if res is not None else None
+
+
+def nl_energy(x, s, nbr, lam: float) -> float:
+    x, s = _f64(x), _f64(s)
+    K, H, W = x.shape
+    nb, pn = _i32(nbr)
+    e = ctypes.c_double(0.0)
+    _check(lib().oracle_nl_energy(H, W, K, nb.shape[1], pn, _d(x), _d(s), float(lam), ctypes.byref(e)),
+           "nl_energy")
+    return e.value
+
+
+def nl_admm_run(f, codebook, lam: float, gamma: float, T: int, graph=None, **graph_params) -> dict:
+    """Graph of f (unless given), data term, zero state, T NL-ADMM iterations;
+    adds the graph, labels, gap and energy."""
+    prm = dict(NL_PARAMS, **graph_params)
+    nbr, deg = graph if graph is not None else nl_graph(f, **prm)
+    s = data_term(f, codebook)
+    K, H, W = s.shape
+    st = nl_zero_state(K, nbr.shape[1], H, W)
+    st["fp_res"] = nl_admm_iterate(st, s, nbr, lam, gamma, T, record_residual=True)
+    st["s"], st["nbr"], st["deg"] = s, nbr, deg
+    st["labels"], st["gap"] = labels(st["w"])
+    st["energy"] = nl_energy(st["w"], s, nbr, lam)
     return st

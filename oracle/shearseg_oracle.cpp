@@ -993,3 +993,264 @@ int oracle_tv_energy(int H, int W, int K, const double* x, const double* s, doub
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// NL-means regulariser, the second comparison model of Sec. 4: the gradient
+// of the TV model replaced by a matrix D built from patch similarities of f.
+//   * patch distance d_a(i, j) = sum_{|t1|,|t2| <= h} G_a(t) sum_ch
+//     (f(i + t) - f(j + t))^2, h = ceil((p - 1)/2), G_a the Gaussian of
+//     standard deviation a on the patch, normalised to sum 1;
+//   * pixels i in raster order pick k = min(mt, 2 mt - l) new neighbours j
+//     (l: i's neighbours so far) among the candidates of the varpi x varpi
+//     search window with the smallest d_a(i, j), and set w(i, j) = w(j, i) = 1;
+//   * D has m = 2 mt blocks; block b, row i: -1 at i and +1 at i's b-th
+//     neighbour (a zero row when i has fewer than b + 1 neighbours).
+// Readings (the paper leaves them open): the window is clipped to the image
+// and f is mirrored at the border for the patches (index -1 -> 1); the
+// distance is taken over all channels; candidates are ordered by (distance,
+// raster index); a candidate already linked to i, or whose neighbour count
+// has reached 2 mt, is passed over (so that no row needs more than m
+// blocks); neighbours are listed in increasing raster index.  The regulariser
+// is the isotropic one, lambda sum_i (sum_k sum_b ((D u_k)_b(i))^2)^(1/2);
+// the ADMM is that of Sec. 3 with S replaced by D, whose u-step solves
+// (I + D^T D) u = rhs (here by conjugate gradients to a relative residual of
+// 1e-13: the exact solve).  The distances are summed in a fixed order
+// without fused multiply-adds, so that the integer graph does not depend on
+// the compiler.
+// ===========================================================================
+namespace {
+
+int mirror(int x, int n) {
+  while (x < 0 || x >= n) x = x < 0 ? -x : 2 * (n - 1) - x;
+  return x;
+}
+
+std::vector<double> nl_patch_weights(int p, double a) {
+  const int h = p / 2;  // ceil((p - 1)/2) for integer p
+  const int n = 2 * h + 1;
+  std::vector<double> G(static_cast<size_t>(n) * n);
+  double sum = 0.0;
+  for (int t1 = -h; t1 <= h; ++t1)
+    for (int t2 = -h; t2 <= h; ++t2) {
+      const double g = std::exp(-static_cast<double>(t1 * t1 + t2 * t2) / (2.0 * a * a));
+      G[(t1 + h) * n + (t2 + h)] = g;
+      sum += g;
+    }
+  for (double& g : G) g /= sum;
+  return G;
+}
+
+double nl_dist(int H, int W, int C, const double* f, const std::vector<double>& G, int h, int ri, int ci, int rj,
+               int cj) {
+  const size_t P = static_cast<size_t>(H) * W;
+  const int n = 2 * h + 1;
+  double acc = 0.0;
+  for (int t1 = -h; t1 <= h; ++t1)
+    for (int t2 = -h; t2 <= h; ++t2) {
+      const size_t a = static_cast<size_t>(mirror(ri + t1, H)) * W + mirror(ci + t2, W);
+      const size_t b = static_cast<size_t>(mirror(rj + t1, H)) * W + mirror(cj + t2, W);
+      double s = 0.0;
+      for (int ch = 0; ch < C; ++ch) {
+        const double d = f[ch * P + a] - f[ch * P + b];
+        const double dd = d * d;
+        s = s + dd;
+      }
+      const double term = G[(t1 + h) * n + (t2 + h)] * s;
+      acc = acc + term;
+    }
+  return acc;
+}
+
+// Neighbour lists nbr[i][0 .. m) (increasing index, -1 padded) and counts.
+void nl_graph(int H, int W, int C, const double* f, int p, int win, double a, int mt, std::vector<int>& nbr,
+              std::vector<int>& deg) {
+  const size_t P = static_cast<size_t>(H) * W;
+  const int m = 2 * mt, r = win / 2, h = p / 2;
+  const auto G = nl_patch_weights(p, a);
+  std::vector<std::vector<int>> lists(P);
+  deg.assign(P, 0);
+  std::vector<std::pair<double, int>> cand;
+  for (int ri = 0; ri < H; ++ri)
+    for (int ci = 0; ci < W; ++ci) {
+      const int i = ri * W + ci;
+      cand.clear();
+      for (int rj = std::max(0, ri - r); rj <= std::min(H - 1, ri + r); ++rj)
+        for (int cj = std::max(0, ci - r); cj <= std::min(W - 1, ci + r); ++cj) {
+          const int j = rj * W + cj;
+          if (j != i) cand.push_back({nl_dist(H, W, C, f, G, h, ri, ci, rj, cj), j});
+        }
+      std::sort(cand.begin(), cand.end());
+      const int k = std::min(mt, m - deg[i]);
+      int taken = 0;
+      for (const auto& c : cand) {
+        if (taken >= k) break;
+        const int j = c.second;
+        if (deg[j] >= m) continue;
+        if (std::find(lists[i].begin(), lists[i].end(), j) != lists[i].end()) continue;
+        lists[i].push_back(j);
+        lists[j].push_back(i);
+        ++deg[i];
+        ++deg[j];
+        ++taken;
+      }
+    }
+  nbr.assign(P * m, -1);
+  for (size_t i = 0; i < P; ++i) {
+    std::sort(lists[i].begin(), lists[i].end());
+    for (size_t b = 0; b < lists[i].size(); ++b) nbr[i * m + b] = lists[i][b];
+  }
+}
+
+// (D x)_b(i) = x(nbr_b(i)) - x(i) for one plane: out [m][P].
+void nl_D(size_t P, int m, const int* nbr, const double* x, double* out) {
+  for (int b = 0; b < m; ++b)
+    for (size_t i = 0; i < P; ++i) {
+      const int j = nbr[i * m + b];
+      out[b * P + i] = j >= 0 ? x[j] - x[i] : 0.0;
+    }
+}
+
+// D^T q for one plane, by scattering the rows of D: q [m][P] -> out [P].
+void nl_Dt(size_t P, int m, const int* nbr, const double* q, double* out) {
+  std::fill(out, out + P, 0.0);
+  for (size_t i = 0; i < P; ++i)
+    for (int b = 0; b < m; ++b) {
+      const int j = nbr[i * m + b];
+      if (j < 0) continue;
+      out[j] += q[b * P + i];
+      out[i] -= q[b * P + i];
+    }
+}
+
+// (I + D^T D) x for one plane.
+void nl_apply(size_t P, int m, const int* nbr, const double* x, double* y, std::vector<double>& tmp) {
+  tmp.resize(static_cast<size_t>(m) * P);
+  nl_D(P, m, nbr, x, tmp.data());
+  nl_Dt(P, m, nbr, tmp.data(), y);
+  for (size_t i = 0; i < P; ++i) y[i] += x[i];
+}
+
+// Conjugate gradients for (I + D^T D) u = rhs from u = 0 until the residual
+// is below 1e-13 of |rhs| (I + D^T D is symmetric positive definite with
+// eigenvalues in [1, 1 + 4 m]).
+void nl_solve_one(size_t P, int m, const int* nbr, const double* rhs, double* u) {
+  std::vector<double> r(rhs, rhs + P), d(rhs, rhs + P), q(P), tmp;
+  std::fill(u, u + P, 0.0);
+  double rr = 0.0;
+  for (size_t i = 0; i < P; ++i) rr += r[i] * r[i];
+  const double stop = 1e-26 * std::max(rr, 1e-300);
+  for (int it = 0; it < 2000 && rr > stop; ++it) {
+    nl_apply(P, m, nbr, d.data(), q.data(), tmp);
+    double dq = 0.0;
+    for (size_t i = 0; i < P; ++i) dq += d[i] * q[i];
+    const double alpha = rr / dq;
+    double rr2 = 0.0;
+    for (size_t i = 0; i < P; ++i) {
+      u[i] += alpha * d[i];
+      r[i] -= alpha * q[i];
+      rr2 += r[i] * r[i];
+    }
+    const double beta = rr2 / rr;
+    for (size_t i = 0; i < P; ++i) d[i] = r[i] + beta * d[i];
+    rr = rr2;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+// Patch distance d_a(i, j) between pixels (ri, ci) and (rj, cj) of f [C][H][W].
+double oracle_nl_distance(int H, int W, int C, const double* f, int p, double a, int ri, int ci, int rj, int cj) {
+  const auto G = nl_patch_weights(p, a);
+  return nl_dist(H, W, C, f, G, p / 2, ri, ci, rj, cj);
+}
+
+// The neighbour graph of f [C][H][W]: nbr [H W][2 mt] (increasing index, -1
+// padded) and deg [H W].
+int oracle_nl_graph(int H, int W, int C, const double* f, int p, int win, double a, int mt, int* nbr, int* deg) {
+  if (H < 2 || W < 2 || C < 1 || p < 1 || win < 3 || !(a > 0.0) || mt < 1) return -1;
+  std::vector<int> n, d;
+  nl_graph(H, W, C, f, p, win, a, mt, n, d);
+  std::copy(n.begin(), n.end(), nbr);
+  std::copy(d.begin(), d.end(), deg);
+  return 0;
+}
+
+// D and D^T for K planes: u [K][H][W] <-> q [K][m][H][W].
+int oracle_nl_D(int H, int W, int K, int m, const int* nbr, const double* u, double* q) {
+  const size_t P = static_cast<size_t>(H) * W;
+  for (int k = 0; k < K; ++k) nl_D(P, m, nbr, u + k * P, q + static_cast<size_t>(k) * m * P);
+  return 0;
+}
+
+int oracle_nl_Dt(int H, int W, int K, int m, const int* nbr, const double* q, double* u) {
+  const size_t P = static_cast<size_t>(H) * W;
+  for (int k = 0; k < K; ++k) nl_Dt(P, m, nbr, q + static_cast<size_t>(k) * m * P, u + k * P);
+  return 0;
+}
+
+// (I + D^T D)^(-1) rhs for K planes.
+int oracle_nl_solve(int H, int W, int K, int m, const int* nbr, const double* rhs, double* u) {
+  const size_t P = static_cast<size_t>(H) * W;
+  parallel_for(K, [&](int k) { nl_solve_one(P, m, nbr, rhs + k * P, u + k * P); });
+  return 0;
+}
+
+// T iterations of the ADMM for the NL model, in place (v, bv [K][m][H][W];
+// w, bw, u [K][H][W]), the TV iteration with grad replaced by D; the group of
+// the shrinkage is all m K values of a pixel.
+int oracle_nl_admm_iterate(int H, int W, int K, int m, const int* nbr, const double* s, double lambda, double gamma,
+                           int T, double* v, double* bv, double* w, double* bw, double* u, double* fp_res) {
+  if (H < 2 || W < 2 || K < 1 || m < 1 || T < 0 || !(gamma > 0.0) || lambda < 0.0) return -1;
+  const size_t P = static_cast<size_t>(H) * W, KP = static_cast<size_t>(K) * P, NV = static_cast<size_t>(m) * KP;
+  const double t = gamma * lambda;
+  std::vector<double> diff(NV), rhs(KP), g(NV), vn(NV), gw(K), x(K);
+  for (int it = 0; it < T; ++it) {
+    for (size_t i = 0; i < NV; ++i) diff[i] = v[i] - bv[i];
+    for (int k = 0; k < K; ++k) nl_Dt(P, m, nbr, diff.data() + k * m * P, rhs.data() + k * P);
+    for (size_t i = 0; i < KP; ++i) rhs[i] += (w[i] - bw[i]) - gamma * s[i];
+    parallel_for(K, [&](int k) { nl_solve_one(P, m, nbr, rhs.data() + k * P, u + k * P); });
+    for (int k = 0; k < K; ++k) nl_D(P, m, nbr, u + k * P, g.data() + k * m * P);
+    for (size_t i = 0; i < NV; ++i) g[i] += bv[i];
+    for (size_t px = 0; px < P; ++px) shrink_group(g.data() + px, m * K, P, t, vn.data() + px);
+    double res = 0.0;
+    for (size_t i = 0; i < NV; ++i) {
+      const double bn = g[i] - vn[i];
+      res += (vn[i] - v[i]) * (vn[i] - v[i]) + (bn - bv[i]) * (bn - bv[i]);
+      v[i] = vn[i];
+      bv[i] = bn;
+    }
+    for (size_t px = 0; px < P; ++px) {
+      for (int k = 0; k < K; ++k) gw[k] = bw[k * P + px] + u[k * P + px];
+      project_simplex_sort(gw.data(), K, x.data());
+      for (int k = 0; k < K; ++k) {
+        const double bn = gw[k] - x[k];
+        res += (x[k] - w[k * P + px]) * (x[k] - w[k * P + px]) + (bn - bw[k * P + px]) * (bn - bw[k * P + px]);
+        w[k * P + px] = x[k];
+        bw[k * P + px] = bn;
+      }
+    }
+    if (fp_res) fp_res[it] = res;
+  }
+  return 0;
+}
+
+// Energy of the NL model at x: <x, s> + lambda sum_i |(I_q (x) D) x|(i).
+int oracle_nl_energy(int H, int W, int K, int m, const int* nbr, const double* x, const double* s, double lambda,
+                     double* energy) {
+  const size_t P = static_cast<size_t>(H) * W;
+  std::vector<double> q(static_cast<size_t>(K) * m * P);
+  for (int k = 0; k < K; ++k) nl_D(P, m, nbr, x + k * P, q.data() + k * m * P);
+  double data = 0.0, reg = 0.0;
+  for (size_t i = 0; i < static_cast<size_t>(K) * P; ++i) data += x[i] * s[i];
+  for (size_t px = 0; px < P; ++px) {
+    double n2 = 0.0;
+    for (size_t c = 0; c < static_cast<size_t>(K) * m; ++c) n2 += q[c * P + px] * q[c * P + px];
+    reg += std::sqrt(n2);
+  }
+  *energy = data + lambda * reg;
+  return 0;
+}
+
+}  // extern "C"

@@ -17,8 +17,10 @@ forward and reverse sweeps beside the same images solved one after another
 (K = 8, J = 5, 20 of its iterations per step) and the 64 x 64 image (K = 3,
 J = 2, 200 iterations) through the same path, and the TV-regularised model of
 Sec. 4 on the 512 x 512 image (`tv512`, gamma = 1, lambda = 1/12, 100
-iterations; the line and tv512 carry the label error of each model against
-the generator's label map) (--no-legs skips them).  The
+iterations) and the NL-means-regularised model of Sec. 4 on it (`nl512`, the
+paper's p = 5, varpi = 15, a = 2, mt = 5, gamma = 1/5, lambda = 1/32, 100
+iterations; graph built once); the line, tv512 and nl512 carry each model's
+label error against the generator's label map (--no-legs skips them).  The
 line reports the dominant kernel's HBM roofline and, for the whole iteration,
 the method's algorithmic bytes and FP32 operations over the plain iteration
 time against the measured HBM bandwidth and the FP32 peak from the unit
@@ -443,7 +445,8 @@ def run_ours(args):
         # its 1000 iterations per step) and 64 x 64 (K = 3, J = 2, 200 iterations)
         line["workloads"] = {"rgb2048": measure_leg("rgb2048", 20, 3, 3, not args.no_tune),
                              "ellipses64": measure_leg("ellipses64", 200, 5, 3, not args.no_tune),
-                             "tv512": measure_tv(100, 5, 3)}
+                             "tv512": measure_tv(100, 5, 3),
+                             "nl512": measure_nl(100, 3, 2)}
     if not args.no_batch and name == WORKLOAD:
         # the batched form on the same GPUs (the plain state is released
         # first): the 64-image batch sharded over the ranks
@@ -586,6 +589,62 @@ def measure_tv(iters: int, steps: int, warmup: int, lam: float = 1.0 / 12.0):
             "workload": f"tv512: bezier512's image (512x512 gray, K=4) with the TV regulariser of Sec. 4 "
                         f"(labels coupled per pixel, periodic forward differences), gamma=1, lambda=1/12, "
                         f"{iters} ADMM iterations per step"}
+
+
+def measure_nl(iters: int, steps: int, warmup: int, lam: float = 1.0 / 32.0, gamma: float = 0.2):
+    """The NL-means-regularised model of Sec. 4 on the 512 x 512 textured
+    image (K = 4) with the paper's NL settings (p = 5, varpi = 15, a = 2,
+    mt = 5; gamma = 1/5, lambda = 1/32, 100 iterations).  The neighbour
+    graph depends on the image only: it is built once (timed separately) and
+    the timed steps run the iterations from the zero state."""
+    import torch
+
+    from paper_1112_1805_gb300 import binding as B
+    from paper_1112_1805_gb300.api import NLSegmenter
+
+    img, lab, wl = synth.make_workload_image("bezier512")
+    f_dev = torch.tensor(np.ascontiguousarray(img, dtype=np.float32), device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seg = NLSegmenter(f_dev, wl.codebook(), lam, gamma)
+    graph_s = time.perf_counter() - t0
+    nbr, deg, cheb = seg.graph()
+    zero_k = torch.zeros((wl.K, wl.H, wl.W), device="cuda")
+    zero_v = torch.zeros((wl.K, seg.m, wl.H, wl.W), device="cuda")
+
+    def zero_state():
+        for what, z in ((B.SEG_BV, zero_v), (B.SEG_V, zero_v), (B.SEG_W, zero_k), (B.SEG_BW, zero_k),
+                        (B.SEG_U, zero_k)):
+            seg.set(what, z)
+
+    ms = 0.0
+    for step in range(warmup + steps):
+        zero_state()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(seg.stream)
+        seg.step(iters)
+        ev1.record(seg.stream)
+        ev1.synchronize()
+        if step >= warmup:
+            ms += ev0.elapsed_time(ev1)
+    label_error = float((seg.labels().cpu().numpy() != lab).mean())
+    kt = seg.kernel_times(3)
+    seg.close()
+    P, K, m = wl.H * wl.W, wl.K, 2 * 5
+    units = P * K * iters * steps
+    # Chebyshev step: x, rhs, d in; x, d out (20 B per pixel and label) + the
+    # neighbour lists and counts (4 m + 1 B per pixel)
+    solve_bytes = cheb * (K * P * 20 + P * (4 * m + 1))
+    peak, peak_kind = peaks()
+    achieved = solve_bytes / (kt["nl_solve"] / 1000.0) / 1e9
+    return {"value": units / (ms / 1000.0) / 1e6, "unit": UNIT, "steps": steps, "warmup": warmup,
+            "iters_per_step": iters, "ms_per_step": ms / steps, "label_error": label_error, "kernel_ms": kt,
+            "graph_build_s": graph_s, "chebyshev_steps_per_u_step": cheb, "mean_neighbours": float(deg.mean()),
+            "roofline": {"bound": "hbm", "kernel": "nl_solve (Chebyshev steps)", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs"},
+            "workload": f"nl512: bezier512's image (512x512 gray, K=4) with the NL-means regulariser of Sec. 4 "
+                        f"(p=5, varpi=15, a=2, mt=5), gamma=1/5, lambda=1/32, {iters} ADMM iterations per step "
+                        f"from the zero state; the graph (built once per image, graph_build_s) is not in the steps"}
 
 
 def measure_batch(iters: int, steps: int, warmup_steps: int, warmup_iters: int, tune: bool, rank: int = 0,

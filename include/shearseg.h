@@ -394,6 +394,79 @@ int tv_admm_sync(tv_state* st);
 /* Releases the state (synchronises its stream).  NULL is accepted. */
 int tv_admm_destroy(tv_state* st);
 
+/* ---------------------------------------------------------------------------
+ * NL-means-regularised segmentation, the second comparison model of Sec. 4:
+ * the gradient of the TV model replaced by a matrix D from patch similarities
+ * of f.  Every pixel i, in raster order, picks min(mt, 2 mt - l) new
+ * neighbours j (l: the neighbours it already has) among the candidates of the
+ * varpi x varpi search window with the smallest patch distance
+ *   d_a(i, j) = sum_{|t1|, |t2| <= h} G_a(t) sum_ch (f(i + t) - f(j + t))^2,
+ * h = ceil((p - 1)/2), G_a the Gaussian of standard deviation a normalised to
+ * sum 1, and links are symmetric (w(i, j) = w(j, i) = 1).  D has m = 2 mt
+ * blocks: block b, row i is -1 at i and +1 at i's b-th neighbour (zero when i
+ * has fewer neighbours).  The regulariser is the isotropic
+ *   lambda sum_i (sum_k sum_b ((D u_k)_b(i))^2)^(1/2),
+ * minimised with the ADMM of Sec. 3 with S replaced by D:
+ *   u   = (I + D^T D)^(-1) [ D^T (v - b_v) + (w - b_w) - gamma s ]
+ *   v   = group shrinkage of b_v + D u by gamma lambda, b_v += D u - v
+ *   w   = pixelwise projection of b_w + u onto the simplex, b_w += u - w.
+ * Readings (the paper leaves them open): the window is clipped to the image,
+ * f is mirrored at the border inside patches (index -1 -> 1), distances run
+ * over all channels and are computed in FP64 with every operation rounded
+ * separately, ties go to the lower raster index, candidates already linked or
+ * holding 2 mt neighbours are passed over, and the u-step solve runs
+ * solve_steps Chebyshev iterations on the spectrum bound [1, 1 + 4 deg_max]
+ * of I + D^T D = I + 2 L from the previous u (0: as many as give a relative
+ * error of 1e-7).  The paper's values: p = 5, varpi = 15, a = 2, mt = 5.
+ * Coefficients and duals are [K][m][H][W].
+ * ------------------------------------------------------------------------- */
+typedef struct nl_state nl_state;
+typedef struct {
+  float gamma;     /* ADMM step, > 0                                          */
+  float lambda;    /* regularisation weight, >= 0                            */
+  int patch;       /* p, 1..9                                                */
+  int window;      /* varpi, odd, 3..15                                      */
+  float a;         /* standard deviation of the patch Gaussian, > 0          */
+  int neighbours;  /* mt, 1..8 (m = 2 mt blocks of D)                        */
+  int solve_steps; /* Chebyshev iterations per u-step, 0 = automatic         */
+} nl_params;
+
+/* f: device [C][H][W] (H, W in 8..2048); codebook: HOST [K][C].  Builds the
+ * neighbour graph of f (patch distances and their ranking on the GPU, the
+ * sequential selection on the host), the data term and the zero state.
+ * Synchronises.  Errors: SHF_ERR_ARG, SHF_ERR_SIZE, SHF_ERR_NONFINITE,
+ * SHF_ERR_OOM, SHF_ERR_CUDA. */
+int nl_admm_init(int H, int W, const float* f, int C, const float* codebook, int K, const nl_params* params,
+                 void* stream, nl_state** out);
+
+/* New image of the same size (device, or host if f_on_host): graph, data
+ * term and state rebuilt.  Synchronises. */
+int nl_admm_reset(nl_state* st, const float* f, int f_on_host);
+
+/* The graph: nbr HOST [H W][2 mt] (increasing index, -1 padded), deg HOST
+ * [H W], solve_steps (Chebyshev iterations per u-step); any may be NULL. */
+int nl_admm_graph(const nl_state* st, int* nbr, int* deg, int* solve_steps);
+
+/* Enqueues n_iters iterations (replays of a CUDA graph of one iteration). */
+int nl_admm_step(nl_state* st, int n_iters);
+
+/* Readouts as tv_admm_get, with SEG_BV and SEG_V of shape [K][m][H][W]. */
+int nl_admm_get(nl_state* st, int what, void* dst, int dst_on_host);
+
+/* Overwrites SEG_W, SEG_BW, SEG_U (the u-step's starting point), SEG_BV or
+ * SEG_V (set SEG_BV first) and rebuilds the right-hand side.  Synchronises. */
+int nl_admm_set(nl_state* st, int what, const void* src, int src_on_host);
+
+/* Instrumentation: n iterations with events around the u-step solve, the
+ * prox kernel and the right-hand side; mean milliseconds into ms (room for
+ * 3), *nk = 3.  Advances the iterate.  Synchronises. */
+int nl_admm_kernel_times(nl_state* st, int n, float* ms, int* nk);
+const char* nl_admm_kernel_name(int i);
+
+int nl_admm_sync(nl_state* st);
+/* Releases the state (synchronises its stream).  NULL is accepted. */
+int nl_admm_destroy(nl_state* st);
+
 /* Waits for the state's stream. */
 int seg_admm_sync(seg_state* st);
 

@@ -370,6 +370,94 @@ class TVSegmenter:
         return B.tv_admm_kernel_times(self.handle, n)
 
 
+class NLSegmenter(TVSegmenter):
+    """ADMM state of the NL-means-regularised model of Sec. 4 for one image:
+    the neighbour graph of f (patch size p, search window varpi, Gaussian a,
+    mt neighbours picked per pixel; the paper's 5, 15, 2, 5), then the ADMM
+    with the difference matrix D in place of the gradient.
+
+    f: [C, H, W] or [H, W] float32 CUDA tensor; codebook: [K, C] host values."""
+
+    def __init__(self, f: torch.Tensor, codebook, lam: float, gamma: float = 0.2, patch: int = 5, window: int = 15,
+                 a: float = 2.0, neighbours: int = 5, solve_steps: int = 0, stream=None):
+        if f.dim() == 2:
+            f = f.unsqueeze(0)
+        _dev_f32(f, "f")
+        cb = np.asarray(codebook, dtype=np.float64).reshape(-1, f.shape[0])
+        self.K, self.C = cb.shape
+        self.H, self.W = int(f.shape[1]), int(f.shape[2])
+        self.m = 2 * neighbours
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.stream.wait_stream(torch.cuda.current_stream())
+        torch.cuda.current_stream().synchronize()
+        self.handle = B.nl_admm_init(self.H, self.W, f.data_ptr(), self.C, cb.ravel().tolist(), self.K, gamma, lam,
+                                     patch, window, a, neighbours, solve_steps, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            B.nl_admm_destroy(self.handle)
+        self.handle = None
+
+    def step(self, n: int) -> None:
+        B.nl_admm_step(self.handle, n)
+
+    def synchronize(self) -> None:
+        B.nl_admm_sync(self.handle)
+
+    def reset(self, f) -> None:
+        if isinstance(f, torch.Tensor) and f.is_cuda:
+            _dev_f32(f, "f")
+            self.stream.wait_stream(torch.cuda.current_stream())
+            torch.cuda.current_stream().synchronize()
+            B.nl_admm_reset(self.handle, f.data_ptr(), False)
+        else:
+            a = f if isinstance(f, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(f, dtype=np.float32))
+            B.nl_admm_reset(self.handle, a.contiguous().data_ptr(), True)
+
+    def graph(self):
+        """(nbr [H W, m], deg [H W], Chebyshev steps per u-step) of the state's image."""
+        return B.nl_admm_graph(self.handle, self.H * self.W, self.m)
+
+    def _shape(self, what: int):
+        if what in (B.SEG_BV, B.SEG_V):
+            return (self.K, self.m, self.H, self.W), torch.float32
+        return TVSegmenter._shape(self, what)
+
+    def get(self, what: int) -> torch.Tensor:
+        if what == B.SEG_ENERGY:
+            buf = np.zeros(1, dtype=np.float64)
+            B.nl_admm_get(self.handle, what, buf.ctypes.data, True)
+            return torch.tensor(buf[0], dtype=torch.float64)
+        if what == B.SEG_ITER:
+            buf = np.zeros(1, dtype=np.int32)
+            B.nl_admm_get(self.handle, what, buf.ctypes.data, True)
+            return torch.tensor(int(buf[0]))
+        shape, dt = self._shape(what)
+        out = torch.empty(shape, dtype=dt, device="cuda")
+        B.nl_admm_get(self.handle, what, out.data_ptr(), False)
+        self.synchronize()
+        return out
+
+    def get_host(self, what: int, out: torch.Tensor | None = None) -> torch.Tensor:
+        shape, dt = self._shape(what)
+        if out is None:
+            out = torch.empty(shape, dtype=dt, pin_memory=True)
+        B.nl_admm_get(self.handle, what, out.data_ptr(), True)
+        return out
+
+    def set(self, what: int, src: torch.Tensor) -> None:
+        shape, dt = self._shape(what)
+        src = src.to(dt).contiguous()
+        if tuple(src.shape) != shape:
+            raise ValueError(f"expected shape {shape}, got {tuple(src.shape)}")
+        if src.is_cuda:
+            self.stream.wait_stream(torch.cuda.current_stream())
+        B.nl_admm_set(self.handle, what, src.data_ptr(), not src.is_cuda)
+
+    def kernel_times(self, n: int = 5) -> dict:
+        return B.nl_admm_kernel_times(self.handle, n)
+
+
 class UnrolledSegmentation(torch.autograd.Function):
     """w_T of T ADMM iterations from the zero state as a differentiable function
     of the image f [C, H, W], the codebook [K, C] and the weights Lambda [J+1]

@@ -53,6 +53,12 @@ class tv_params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_float), ("lambda_", ctypes.c_float), ("per_label", ctypes.c_int)]
 
 
+class nl_params(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_float), ("lambda_", ctypes.c_float), ("patch", ctypes.c_int),
+                ("window", ctypes.c_int), ("a", ctypes.c_float), ("neighbours", ctypes.c_int),
+                ("solve_steps", ctypes.c_int)]
+
+
 _VP = ctypes.c_void_p
 _I = ctypes.c_int
 
@@ -113,6 +119,17 @@ _SIG = {
     "tv_admm_kernel_name": (ctypes.c_char_p, [_I]),
     "tv_admm_sync": (_I, [_VP]),
     "tv_admm_destroy": (_I, [_VP]),
+    "nl_admm_init": (_I, [_I, _I, _VP, _I, ctypes.POINTER(ctypes.c_float), _I, ctypes.POINTER(nl_params), _VP,
+                          ctypes.POINTER(_VP)]),
+    "nl_admm_reset": (_I, [_VP, _VP, _I]),
+    "nl_admm_graph": (_I, [_VP, _VP, _VP, ctypes.POINTER(_I)]),
+    "nl_admm_step": (_I, [_VP, _I]),
+    "nl_admm_get": (_I, [_VP, _I, _VP, _I]),
+    "nl_admm_set": (_I, [_VP, _I, _VP, _I]),
+    "nl_admm_kernel_times": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_I)]),
+    "nl_admm_kernel_name": (ctypes.c_char_p, [_I]),
+    "nl_admm_sync": (_I, [_VP]),
+    "nl_admm_destroy": (_I, [_VP]),
 }
 
 
@@ -396,3 +413,58 @@ def tv_admm_sync(state: int) -> None:
 
 def tv_admm_destroy(state: int) -> None:
     _call("tv_admm_destroy", _VP(state))
+
+
+# ---------------------------------------------------------------------------
+# NL-means-regularised segmentation (Sec. 4)
+# ---------------------------------------------------------------------------
+def nl_admm_init(H: int, W: int, f: int, C: int, codebook, K: int, gamma: float, lam: float, patch: int = 5,
+                 window: int = 15, a: float = 2.0, neighbours: int = 5, solve_steps: int = 0, stream=None) -> int:
+    cb = (ctypes.c_float * (K * C))(*[float(x) for x in codebook])
+    p = nl_params(float(gamma), float(lam), int(patch), int(window), float(a), int(neighbours), int(solve_steps))
+    out = _VP()
+    _call("nl_admm_init", int(H), int(W), _VP(f), int(C), cb, int(K), ctypes.byref(p), _stream(stream),
+          ctypes.byref(out))
+    return out.value
+
+
+def nl_admm_reset(state: int, f: int, f_on_host: bool) -> None:
+    _call("nl_admm_reset", _VP(state), _VP(f), int(bool(f_on_host)))
+
+
+def nl_admm_graph(state: int, P: int, m: int):
+    """(nbr [P, m] int32, deg [P] int32, Chebyshev steps per u-step)."""
+    import numpy as np
+
+    nbr = np.empty((P, m), dtype=np.int32)
+    deg = np.empty(P, dtype=np.int32)
+    steps = _I()
+    _call("nl_admm_graph", _VP(state), _VP(nbr.ctypes.data), _VP(deg.ctypes.data), ctypes.byref(steps))
+    return nbr, deg, steps.value
+
+
+def nl_admm_step(state: int, n_iters: int) -> None:
+    _call("nl_admm_step", _VP(state), int(n_iters))
+
+
+def nl_admm_get(state: int, what: int, dst: int, dst_on_host: bool) -> None:
+    _call("nl_admm_get", _VP(state), int(what), _VP(dst), int(bool(dst_on_host)))
+
+
+def nl_admm_set(state: int, what: int, src: int, src_on_host: bool) -> None:
+    _call("nl_admm_set", _VP(state), int(what), _VP(src), int(bool(src_on_host)))
+
+
+def nl_admm_kernel_times(state: int, n: int) -> dict:
+    ms = (ctypes.c_float * 8)()
+    nk = _I()
+    _call("nl_admm_kernel_times", _VP(state), int(n), ms, ctypes.byref(nk))
+    return {lib().nl_admm_kernel_name(i).decode(): float(ms[i]) for i in range(nk.value)}
+
+
+def nl_admm_sync(state: int) -> None:
+    _call("nl_admm_sync", _VP(state))
+
+
+def nl_admm_destroy(state: int) -> None:
+    _call("nl_admm_destroy", _VP(state))

@@ -1,0 +1,783 @@
+// NL-means-regularised segmentation, the second comparison model of Sec. 4:
+// the gradient of the TV model replaced by a matrix D built from patch
+// similarities of the image f.
+//
+// Graph (once per image): the patch distance d_a(i, j) = sum over the p x p
+// patch of G_a(t) sum_ch (f(i + t) - f(j + t))^2 (G_a the Gaussian of
+// standard deviation a normalised to sum 1, f mirrored at the border) for
+// every candidate j of the varpi x varpi search window (clipped to the image)
+// is computed on the GPU in FP64 with every product and sum rounded
+// separately, and each pixel's candidates are ranked by (distance, raster
+// index).  The selection itself is sequential in the paper (pixels in
+// raster order pick min(mt, 2 mt - l) new neighbours, l the neighbours they
+// already have, and links are symmetric), so it runs on the host over the
+// ranked lists; a candidate already linked or holding 2 mt neighbours is
+// passed over.
+//
+// ADMM (Sec. 3 with S replaced by D, per iteration):
+//   u   = (I + D^T D)^(-1) [ D^T (v - b_v) + (w - b_w) - gamma s ]
+//   v   = group shrinkage of g = b_v + D u over the m K values of a pixel,
+//         b_v = g - v (kept as b_v and d = v - b_v)
+//   w   = simplex projection of b_w + u, b_w = b_w + u - w.
+// D^T D = 2 L (L the graph Laplacian of the symmetric neighbour sets), so
+// I + D^T D has its spectrum in [1, 1 + 4 deg_max]; the u-step runs a fixed
+// number of Chebyshev iterations on that interval from the previous u (no
+// inner products, one launch per step), enough for a relative error below
+// 1e-7 of the initial one.
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "shearseg.h"
+#include "shf_internal.h"
+#include "shf_simplex.cuh"
+
+struct nl_state {
+  int H = 0, W = 0, K = 0, C = 0, m = 0, device = 0, deg_max = 0;
+  float gamma = 1.f, lambda = 0.f;
+  nl_params prm{};
+  std::vector<float> codebook;
+  std::vector<int> nbr_host, deg_host;  // [P][m] (increasing index, -1 padded), [P]
+  std::vector<float> cheb_a, cheb_c;    // Chebyshev coefficients per step
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  float *f = nullptr, *s = nullptr, *u = nullptr, *u2 = nullptr, *cd = nullptr, *bv = nullptr, *d = nullptr;
+  float *w = nullptr, *bw = nullptr, *q = nullptr, *rhs = nullptr, *gap = nullptr;
+  int* nbr = nullptr;                   // [m][P]
+  unsigned char *rev = nullptr, *deg = nullptr;
+  int* labels = nullptr;
+  int* flag = nullptr;
+  double* red = nullptr;
+  int iter = 0;
+  cudaGraphExec_t exec = nullptr;
+  bool graph_tried = false;
+  size_t P() const { return static_cast<size_t>(H) * W; }
+};
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRedBlocks = 512;
+constexpr int kMaxM = 16;       // neighbours per pixel (2 mt, mt <= 8)
+constexpr int kMaxWin = 15;     // search window side: (2r + 1)^2 <= 225 window codes
+constexpr int kMaxPatch = 9;    // patch side
+constexpr int kRankWarps = 4;   // warps (pixels) per CTA of the ranking kernel
+
+__device__ __forceinline__ int mirror_idx(int x, int n) {
+  while (x < 0 || x >= n) x = x < 0 ? -x : 2 * (n - 1) - x;
+  return x;
+}
+
+// One warp per pixel: the patch distances to every window code c = (dy + r)
+// (2r + 1) + (dx + r) (the centre and codes outside the image excluded) and
+// their ranks by (distance, code); rank[i][pos] = code of position pos, 255
+// for the unused positions at the end.  Codes in increasing order are
+// candidates in increasing raster index, so this is the order (distance,
+// raster index).  G: the patch weights [(2h+1)^2] in FP64.
+__global__ void __launch_bounds__(32 * kRankWarps) k_nl_rank(const float* __restrict__ f, int H, int W, int C,
+                                                             const double* __restrict__ G, int h, int r,
+                                                             unsigned char* __restrict__ rank) {
+  __shared__ double key[kRankWarps][(2 * (kMaxWin / 2) + 1) * (2 * (kMaxWin / 2) + 1)];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int i = blockIdx.x * kRankWarps + wid;
+  const int side = 2 * r + 1, NW = side * side;
+  const size_t P = static_cast<size_t>(H) * W;
+  if (i >= H * W) return;  // whole warps leave together
+  const int ri = i / W, ci = i - ri * W;
+  const int n = 2 * h + 1;
+  for (int c = lane; c < NW; c += 32) {
+    const int dy = c / side - r, dx = c % side - r;
+    const int rj = ri + dy, cj = ci + dx;
+    double acc = INFINITY;
+    if ((dy != 0 || dx != 0) && rj >= 0 && rj < H && cj >= 0 && cj < W) {
+      acc = 0.0;
+      for (int t1 = -h; t1 <= h; ++t1)
+        for (int t2 = -h; t2 <= h; ++t2) {
+          const size_t a = static_cast<size_t>(mirror_idx(ri + t1, H)) * W + mirror_idx(ci + t2, W);
+          const size_t b = static_cast<size_t>(mirror_idx(rj + t1, H)) * W + mirror_idx(cj + t2, W);
+          double sum = 0.0;
+          for (int ch = 0; ch < C; ++ch) {
+            const double dd = __dsub_rn(static_cast<double>(f[ch * P + a]), static_cast<double>(f[ch * P + b]));
+            sum = __dadd_rn(sum, __dmul_rn(dd, dd));
+          }
+          acc = __dadd_rn(acc, __dmul_rn(G[(t1 + h) * n + (t2 + h)], sum));
+        }
+    }
+    key[wid][c] = acc;
+  }
+  __syncwarp();
+  unsigned char* out = rank + static_cast<size_t>(i) * NW;
+  for (int c = lane; c < NW; c += 32) {
+    const double kc = key[wid][c];
+    int pos = 0;
+    for (int c2 = 0; c2 < NW; ++c2) {
+      const double k2 = key[wid][c2];
+      pos += (k2 < kc || (k2 == kc && c2 < c)) ? 1 : 0;
+    }
+    out[pos] = kc == INFINITY ? 255 : static_cast<unsigned char>(c);
+  }
+}
+
+// The neighbours of pixel i into registers: nb[b] for b < deg(i).
+__device__ __forceinline__ int load_nbrs(const int* __restrict__ nbr, const unsigned char* __restrict__ deg, size_t P,
+                                         size_t i, int m, int (&nb)[kMaxM]) {
+  const int dg = deg[i];
+#pragma unroll
+  for (int b = 0; b < kMaxM; ++b) nb[b] = (b < dg && b < m) ? nbr[b * P + i] : 0;
+  return dg;
+}
+
+// One Chebyshev step for (I + D^T D) x = rhs on every label:
+// r = rhs - x - 2 (deg x - sum_nbrs x), d <- a d + c r, x_out = x_in + d.
+__global__ void __launch_bounds__(kThreads) k_nl_cheb(const float* __restrict__ xin, float* __restrict__ xout,
+                                                      float* __restrict__ d, const float* __restrict__ rhs,
+                                                      const int* __restrict__ nbr,
+                                                      const unsigned char* __restrict__ deg, int K, int m, size_t P,
+                                                      float a, float c) {
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < P;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    int nb[kMaxM];
+    const int dg = load_nbrs(nbr, deg, P, i, m, nb);
+    for (int k = 0; k < K; ++k) {
+      const float* x = xin + k * P;
+      const float xi = x[i];
+      float sn = 0.f;
+#pragma unroll
+      for (int b = 0; b < kMaxM; ++b)
+        if (b < dg) sn += x[nb[b]];
+      const float ax = xi + 2.f * (static_cast<float>(dg) * xi - sn);
+      const float res = rhs[k * P + i] - ax;
+      const float dn = a * d[k * P + i] + c * res;
+      d[k * P + i] = dn;
+      xout[k * P + i] = xi + dn;
+    }
+  }
+}
+
+// The v-, w- and b-updates after the u-step: g_b = b_v,b + u(nbr_b) - u(i)
+// (b < deg; b_v,b for the zero rows), group clip over the m K values,
+// d = g - 2 b_v; w-step and q = (w - b_w) - gamma s.
+template <int KM>
+__global__ void __launch_bounds__(kThreads) k_nl_prox(const float* __restrict__ u, float* __restrict__ bv,
+                                                      float* __restrict__ d, float* __restrict__ w,
+                                                      float* __restrict__ bw, const float* __restrict__ s,
+                                                      float* __restrict__ q, const int* __restrict__ nbr,
+                                                      const unsigned char* __restrict__ deg, int K, int m, size_t P,
+                                                      float t, float gamma) {
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < P;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    int nb[kMaxM];
+    const int dg = load_nbrs(nbr, deg, P, i, m, nb);
+    // the group norm over the m K values of g (the label loop is not unrolled:
+    // only the neighbour indices stay in registers)
+    float n2 = 0.f;
+    for (int k = 0; k < K; ++k) {
+      const float* up = u + k * P;
+      const float ui = up[i];
+      const float* bk = bv + static_cast<size_t>(k) * m * P;
+#pragma unroll
+      for (int b = 0; b < kMaxM; ++b) {
+        if (b < m) {
+          const float g = bk[b * P + i] + (b < dg ? up[nb[b]] - ui : 0.f);
+          n2 = fmaf(g, g, n2);
+        }
+      }
+    }
+    const float nrm = sqrtf(n2);
+    const float fac = nrm > t ? t / nrm : 1.f;
+    for (int k = 0; k < K; ++k) {
+      const float* up = u + k * P;
+      const float ui = up[i];
+      float* bk = bv + static_cast<size_t>(k) * m * P;
+      float* dk = d + static_cast<size_t>(k) * m * P;
+#pragma unroll
+      for (int b = 0; b < kMaxM; ++b) {
+        if (b < m) {
+          const float g = bk[b * P + i] + (b < dg ? up[nb[b]] - ui : 0.f);
+          const float bn = fac * g;
+          bk[b * P + i] = bn;
+          dk[b * P + i] = g - 2.f * bn;
+        }
+      }
+    }
+    float gw[KM], wk[KM];
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+      gw[k] = k < K ? bw[k * P + i] + u[k * P + i] : 0.f;
+      wk[k] = gw[k];
+    }
+    shf::simplex_project<KM>(wk, K);
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+      if (k < K) {
+        const float bn = gw[k] - wk[k];
+        w[k * P + i] = wk[k];
+        bw[k * P + i] = bn;
+        q[k * P + i] = (wk[k] - bn) - gamma * s[k * P + i];
+      }
+    }
+  }
+}
+
+// rhs = q + D^T d: (D^T d)(j) = sum_{b < deg(j)} [d_rev(j,b)(nbr_b(j)) - d_b(j)].
+__global__ void __launch_bounds__(kThreads) k_nl_rhs(const float* __restrict__ q, const float* __restrict__ d,
+                                                     float* __restrict__ rhs, const int* __restrict__ nbr,
+                                                     const unsigned char* __restrict__ rev,
+                                                     const unsigned char* __restrict__ deg, int K, int m, size_t P) {
+  for (size_t j = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; j < P;
+       j += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    int nb[kMaxM];
+    const int dg = load_nbrs(nbr, deg, P, j, m, nb);
+    int rv[kMaxM];
+#pragma unroll
+    for (int b = 0; b < kMaxM; ++b) rv[b] = b < dg ? rev[b * P + j] : 0;
+    for (int k = 0; k < K; ++k) {
+      const float* dk = d + static_cast<size_t>(k) * m * P;
+      float acc = 0.f;
+#pragma unroll
+      for (int b = 0; b < kMaxM; ++b)
+        if (b < dg) acc += dk[rv[b] * P + nb[b]] - dk[b * P + j];
+      rhs[k * P + j] = q[k * P + j] + acc;
+    }
+  }
+}
+
+__global__ void k_nl_q(const float* __restrict__ w, const float* __restrict__ bw, const float* __restrict__ s,
+                       float* __restrict__ q, float gamma, size_t n) {
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x)
+    q[i] = (w[i] - bw[i]) - gamma * s[i];
+}
+
+// out = a + sb b (out may alias a).
+__global__ void k_nl_axpb(const float* a, const float* __restrict__ b, float* out, float sb, size_t n) {
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x)
+    out[i] = a[i] + sb * b[i];
+}
+
+// FP64 energy partials: <w, s> and sum_i (sum_k sum_b ((D w_k)_b(i))^2)^(1/2).
+__global__ void __launch_bounds__(kThreads) k_nl_energy(const float* __restrict__ w, const float* __restrict__ s,
+                                                        const int* __restrict__ nbr,
+                                                        const unsigned char* __restrict__ deg, int K, int m, size_t P,
+                                                        double* __restrict__ partial) {
+  double ds = 0.0, dt = 0.0;
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < P;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    int nb[kMaxM];
+    const int dg = load_nbrs(nbr, deg, P, i, m, nb);
+    double n2 = 0.0;
+    for (int k = 0; k < K; ++k) {
+      const float* wp = w + k * P;
+      ds += static_cast<double>(wp[i]) * s[k * P + i];
+#pragma unroll
+      for (int b = 0; b < kMaxM; ++b) {
+        if (b < dg) {
+          const double e = static_cast<double>(wp[nb[b]]) - wp[i];
+          n2 += e * e;
+        }
+      }
+    }
+    dt += sqrt(n2);
+  }
+  __shared__ double sh[2][kThreads];
+  sh[0][threadIdx.x] = ds;
+  sh[1][threadIdx.x] = dt;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = sh[0][0];
+    partial[2 * blockIdx.x + 1] = sh[1][0];
+  }
+}
+
+__global__ void k_nl_energy_final(const double* __restrict__ partial, int nblocks, double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double a = 0.0, b = 0.0;
+  for (int i = 0; i < nblocks; ++i) {
+    a += partial[2 * i];
+    b += partial[2 * i + 1];
+  }
+  out[0] = a;
+  out[1] = b;
+}
+
+int nl_fail(int code, const std::string& msg) { return shf::set_error(code, msg); }
+
+#define NL_CK(call)                                                                                         \
+  do {                                                                                                      \
+    cudaError_t e_ = (call);                                                                                \
+    if (e_ != cudaSuccess) return nl_fail(SHF_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+int nl_alloc(T** p, size_t count, const char* what) {
+  *p = nullptr;
+  if (count == 0) return SHF_OK;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return nl_fail(e == cudaErrorMemoryAllocation ? SHF_ERR_OOM : SHF_ERR_CUDA,
+                   std::string("cudaMalloc(") + what + "): " + cudaGetErrorString(e));
+  }
+  return SHF_OK;
+}
+
+int grid_for(size_t n) {
+  const size_t b = (n + kThreads - 1) / kThreads;
+  return static_cast<int>(b < 8192 ? (b ? b : 1) : 8192);
+}
+
+void free_nl(nl_state* st) {
+  if (!st) return;
+  if (st->stream) cudaStreamSynchronize(st->stream);
+  if (st->exec) cudaGraphExecDestroy(st->exec);
+  void* bufs[] = {st->f, st->s, st->u, st->u2, st->cd, st->bv, st->d, st->w, st->bw, st->q, st->rhs, st->gap,
+                  st->nbr, st->rev, st->deg, st->labels, st->flag, st->red};
+  for (void* b : bufs) cudaFree(b);
+  if (st->own_stream && st->stream) cudaStreamDestroy(st->stream);
+  delete st;
+}
+
+// Patch weights G_a on the (2h+1)^2 patch, normalised to sum 1.
+std::vector<double> patch_weights(int h, double a) {
+  const int n = 2 * h + 1;
+  std::vector<double> G(static_cast<size_t>(n) * n);
+  double sum = 0.0;
+  for (int t1 = -h; t1 <= h; ++t1)
+    for (int t2 = -h; t2 <= h; ++t2) {
+      const double g = std::exp(-static_cast<double>(t1 * t1 + t2 * t2) / (2.0 * a * a));
+      G[(t1 + h) * n + (t2 + h)] = g;
+      sum += g;
+    }
+  for (double& g : G) g /= sum;
+  return G;
+}
+
+// The graph of st->f: ranks on the GPU, the sequential selection here; then
+// the device tables (neighbours [m][P], reverse positions, counts) and the
+// Chebyshev coefficients.  Synchronises.
+int build_graph(nl_state* st) {
+  const int H = st->H, W = st->W, mt = st->prm.neighbours, m = st->m;
+  const int h = st->prm.patch / 2, r = st->prm.window / 2, side = 2 * r + 1, NW = side * side;
+  const size_t P = st->P();
+  const auto G = patch_weights(h, st->prm.a);
+  double* dG = nullptr;
+  unsigned char* drank = nullptr;
+  NL_CK(cudaMallocAsync(reinterpret_cast<void**>(&dG), sizeof(double) * G.size(), st->stream));
+  NL_CK(cudaMallocAsync(reinterpret_cast<void**>(&drank), P * NW, st->stream));
+  std::vector<unsigned char> rank(P * NW);
+  cudaError_t e = cudaMemcpyAsync(dG, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice, st->stream);
+  if (e == cudaSuccess) {
+    k_nl_rank<<<static_cast<unsigned>((P + kRankWarps - 1) / kRankWarps), 32 * kRankWarps, 0, st->stream>>>(
+        st->f, H, W, st->C, dG, h, r, drank);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(rank.data(), drank, P * NW, cudaMemcpyDeviceToHost, st->stream);
+  cudaError_t e2 = cudaFreeAsync(dG, st->stream);
+  cudaError_t e3 = cudaFreeAsync(drank, st->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
+  if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : e3;
+  NL_CK(e);
+  // selection in raster order over the ranked candidates
+  std::vector<int>& nb = st->nbr_host;
+  std::vector<int>& dg = st->deg_host;
+  nb.assign(P * m, -1);
+  dg.assign(P, 0);
+  for (size_t i = 0; i < P; ++i) {
+    const int ri = static_cast<int>(i / W), ci = static_cast<int>(i % W);
+    const int k = std::min(mt, m - dg[i]);
+    int taken = 0;
+    for (int pos = 0; pos < NW && taken < k; ++pos) {
+      const int c = rank[i * NW + pos];
+      if (c == 255) break;  // the rest lie outside the image
+      const int j = (ri + c / side - r) * W + (ci + c % side - r);
+      if (dg[j] >= m) continue;
+      bool linked = false;
+      for (int b = 0; b < dg[i]; ++b) linked = linked || nb[i * m + b] == j;
+      if (linked) continue;
+      nb[i * m + dg[i]++] = j;
+      nb[static_cast<size_t>(j) * m + dg[j]++] = static_cast<int>(i);
+      ++taken;
+    }
+  }
+  st->deg_max = 0;
+  std::vector<int> nbt(P * m, -1);
+  std::vector<unsigned char> rev(P * m, 0), deg8(P);
+  for (size_t i = 0; i < P; ++i) {
+    std::sort(nb.begin() + i * m, nb.begin() + i * m + dg[i]);
+    st->deg_max = std::max(st->deg_max, dg[i]);
+    deg8[i] = static_cast<unsigned char>(dg[i]);
+    for (int b = 0; b < dg[i]; ++b) nbt[static_cast<size_t>(b) * P + i] = nb[i * m + b];
+  }
+  for (size_t i = 0; i < P; ++i)
+    for (int b = 0; b < dg[i]; ++b) {  // position of i in the list of its b-th neighbour
+      const int j = nb[i * m + b];
+      int pos = 0;
+      while (nb[static_cast<size_t>(j) * m + pos] != static_cast<int>(i)) ++pos;
+      rev[static_cast<size_t>(b) * P + i] = static_cast<unsigned char>(pos);
+    }
+  NL_CK(cudaMemcpy(st->nbr, nbt.data(), sizeof(int) * P * m, cudaMemcpyHostToDevice));
+  NL_CK(cudaMemcpy(st->rev, rev.data(), P * m, cudaMemcpyHostToDevice));
+  NL_CK(cudaMemcpy(st->deg, deg8.data(), P, cudaMemcpyHostToDevice));
+  // Chebyshev iteration on [1, 1 + 4 deg_max]: theta = centre, delta = half width
+  const double lo = 1.0, hi = 1.0 + 4.0 * st->deg_max;
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
+  int n = st->prm.solve_steps;
+  if (n <= 0) {
+    const double kappa = hi / lo;
+    const double qrate = (std::sqrt(kappa) - 1.0) / (std::sqrt(kappa) + 1.0);
+    n = qrate > 0.0 ? static_cast<int>(std::ceil(std::log(2.0 / 1e-7) / -std::log(qrate))) : 1;
+  }
+  n += n & 1;  // even: the result lands in u
+  st->cheb_a.assign(n, 0.f);
+  st->cheb_c.assign(n, 0.f);
+  st->cheb_c[0] = static_cast<float>(1.0 / theta);
+  if (delta > 0.0) {
+    const double sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    for (int k = 1; k < n; ++k) {
+      const double rn = 1.0 / (2.0 * sigma - rho);
+      st->cheb_a[k] = static_cast<float>(rn * rho);
+      st->cheb_c[k] = static_cast<float>(2.0 * rn / delta);
+      rho = rn;
+    }
+  }
+  return SHF_OK;
+}
+
+enum NlKind { kNlSolve = 0, kNlProx = 1, kNlRhs = 2, kNlKinds = 3 };
+const char* const kNlNames[kNlKinds] = {"nl_solve", "nl_prox", "nl_rhs"};
+
+cudaError_t launch_prox(nl_state* st) {
+  const size_t P = st->P();
+  const float t = st->gamma * st->lambda;
+  const int grid = grid_for(P);
+  if (st->K <= 4)
+    k_nl_prox<4><<<grid, kThreads, 0, st->stream>>>(st->u, st->bv, st->d, st->w, st->bw, st->s, st->q, st->nbr,
+                                                     st->deg, st->K, st->m, P, t, st->gamma);
+  else if (st->K <= 8)
+    k_nl_prox<8><<<grid, kThreads, 0, st->stream>>>(st->u, st->bv, st->d, st->w, st->bw, st->s, st->q, st->nbr,
+                                                     st->deg, st->K, st->m, P, t, st->gamma);
+  else
+    k_nl_prox<16><<<grid, kThreads, 0, st->stream>>>(st->u, st->bv, st->d, st->w, st->bw, st->s, st->q, st->nbr,
+                                                      st->deg, st->K, st->m, P, t, st->gamma);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs(nl_state* st) {
+  k_nl_rhs<<<grid_for(st->P()), kThreads, 0, st->stream>>>(st->q, st->d, st->rhs, st->nbr, st->rev, st->deg, st->K,
+                                                           st->m, st->P());
+  return cudaGetLastError();
+}
+
+// One iteration; ev (nullable, kNlKinds + 1 events) recorded before each
+// part and after the last.
+cudaError_t enqueue_nl_iteration(nl_state* st, cudaEvent_t* ev) {
+  cudaStream_t ss = st->stream;
+  auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], ss) : cudaSuccess; };
+  cudaError_t e = mark(kNlSolve);
+  const size_t P = st->P();
+  float* x0 = st->u;
+  float* x1 = st->u2;
+  for (size_t k = 0; k < st->cheb_a.size() && e == cudaSuccess; ++k) {
+    k_nl_cheb<<<grid_for(P), kThreads, 0, ss>>>(x0, x1, st->cd, st->rhs, st->nbr, st->deg, st->K, st->m, P,
+                                                st->cheb_a[k], st->cheb_c[k]);
+    e = cudaGetLastError();
+    std::swap(x0, x1);
+  }
+  if (e == cudaSuccess) e = mark(kNlProx);
+  if (e == cudaSuccess) e = launch_prox(st);
+  if (e == cudaSuccess) e = mark(kNlRhs);
+  if (e == cudaSuccess) e = launch_rhs(st);
+  if (e == cudaSuccess) e = mark(kNlKinds);
+  return e;
+}
+
+cudaError_t rebuild_rhs(nl_state* st) {
+  const size_t n = st->P() * st->K;
+  k_nl_q<<<grid_for(n), kThreads, 0, st->stream>>>(st->w, st->bw, st->s, st->q, st->gamma, n);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? launch_rhs(st) : e;
+}
+
+// Graph, data term and the zero state.  Synchronises.
+int nl_restart(nl_state* st) {
+  const size_t P = st->P(), K = st->K, m = st->m;
+  NL_CK(cudaMemsetAsync(st->flag, 0, sizeof(int), st->stream));
+  NL_CK(shf::launch_count_nonfinite(st->f, static_cast<long>(P * st->C), st->flag, st->stream));
+  int bad = 0;
+  NL_CK(cudaMemcpyAsync(&bad, st->flag, sizeof(int), cudaMemcpyDeviceToHost, st->stream));
+  NL_CK(cudaStreamSynchronize(st->stream));
+  if (bad) return nl_fail(SHF_ERR_NONFINITE, "nl: the image contains NaN or Inf");
+  int rc = build_graph(st);
+  if (rc) return rc;
+  if (st->exec) {  // the step count may have changed with the graph
+    cudaGraphExecDestroy(st->exec);
+    st->exec = nullptr;
+    st->graph_tried = false;
+  }
+  NL_CK(shf::launch_data_term(st->f, st->C, st->codebook.data(), st->K, st->s, static_cast<int>(P), st->stream));
+  NL_CK(cudaMemsetAsync(st->u, 0, sizeof(float) * P * K, st->stream));
+  NL_CK(cudaMemsetAsync(st->w, 0, sizeof(float) * P * K, st->stream));
+  NL_CK(cudaMemsetAsync(st->bw, 0, sizeof(float) * P * K, st->stream));
+  NL_CK(cudaMemsetAsync(st->bv, 0, sizeof(float) * m * P * K, st->stream));
+  NL_CK(cudaMemsetAsync(st->d, 0, sizeof(float) * m * P * K, st->stream));
+  NL_CK(cudaMemsetAsync(st->cd, 0, sizeof(float) * P * K, st->stream));
+  NL_CK(rebuild_rhs(st));
+  NL_CK(cudaStreamSynchronize(st->stream));
+  st->iter = 0;
+  return SHF_OK;
+}
+
+int nl_copy(nl_state* st, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind, bool sync) {
+  NL_CK(cudaMemcpyAsync(dst, src, bytes, kind, st->stream));
+  if (sync) NL_CK(cudaStreamSynchronize(st->stream));
+  return SHF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nl_admm_init(int H, int W, const float* f, int C, const float* codebook, int K, const nl_params* p, void* stream,
+                 nl_state** out) {
+  if (!out) return nl_fail(SHF_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!f || !codebook || !p) return nl_fail(SHF_ERR_ARG, "nl_admm_init: NULL argument");
+  if (K < 2 || K > shf::kMaxK) return nl_fail(SHF_ERR_ARG, "K must be in [2, 16]");
+  if (C != 1 && C != 3) return nl_fail(SHF_ERR_ARG, "C must be 1 or 3");
+  if (!(p->gamma > 0.f) || !std::isfinite(p->gamma)) return nl_fail(SHF_ERR_ARG, "gamma must be positive and finite");
+  if (!(p->lambda >= 0.f) || !std::isfinite(p->lambda))
+    return nl_fail(SHF_ERR_ARG, "lambda must be finite and non-negative");
+  if (p->patch < 1 || p->patch > kMaxPatch) return nl_fail(SHF_ERR_ARG, "patch must be in [1, 9]");
+  if (p->window < 3 || p->window > kMaxWin || !(p->window & 1)) return nl_fail(SHF_ERR_ARG, "window must be odd, 3..15");
+  if (!(p->a > 0.f) || !std::isfinite(p->a)) return nl_fail(SHF_ERR_ARG, "a must be positive");
+  if (p->neighbours < 1 || 2 * p->neighbours > kMaxM) return nl_fail(SHF_ERR_ARG, "neighbours must be in [1, 8]");
+  if (p->solve_steps < 0 || p->solve_steps > 1000) return nl_fail(SHF_ERR_ARG, "solve_steps must be in [0, 1000]");
+  if (H < 8 || W < 8 || H > shf::kMaxSide || W > shf::kMaxSide) return nl_fail(SHF_ERR_SIZE, "H and W must be in [8, 2048]");
+  if (reinterpret_cast<uintptr_t>(f) & 7u) return nl_fail(SHF_ERR_ARG, "f must be 8-byte aligned");
+  for (int i = 0; i < K * C; ++i)
+    if (!std::isfinite(codebook[i])) return nl_fail(SHF_ERR_NONFINITE, "codebook contains NaN or Inf");
+  auto* st = new nl_state();
+  st->H = H;
+  st->W = W;
+  st->K = K;
+  st->C = C;
+  st->prm = *p;
+  st->m = 2 * p->neighbours;
+  st->gamma = p->gamma;
+  st->lambda = p->lambda;
+  st->codebook.assign(codebook, codebook + K * C);
+  cudaError_t ed = cudaGetDevice(&st->device);
+  if (ed != cudaSuccess) {
+    delete st;
+    return nl_fail(SHF_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(ed));
+  }
+  if (stream) {
+    st->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&st->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete st;
+      return nl_fail(SHF_ERR_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    }
+    st->own_stream = true;
+  }
+  const size_t P = static_cast<size_t>(H) * W, m = st->m;
+  int rc;
+  if ((rc = nl_alloc(&st->f, P * C, "f")) || (rc = nl_alloc(&st->s, P * K, "s")) ||
+      (rc = nl_alloc(&st->u, P * K, "u")) || (rc = nl_alloc(&st->u2, P * K, "u2")) ||
+      (rc = nl_alloc(&st->cd, P * K, "chebyshev d")) || (rc = nl_alloc(&st->bv, m * P * K, "b_v")) ||
+      (rc = nl_alloc(&st->d, m * P * K, "d")) || (rc = nl_alloc(&st->w, P * K, "w")) ||
+      (rc = nl_alloc(&st->bw, P * K, "b_w")) || (rc = nl_alloc(&st->q, P * K, "q")) ||
+      (rc = nl_alloc(&st->rhs, P * K, "rhs")) || (rc = nl_alloc(&st->gap, P, "gap")) ||
+      (rc = nl_alloc(&st->nbr, P * m, "neighbours")) || (rc = nl_alloc(&st->rev, P * m, "reverse")) ||
+      (rc = nl_alloc(&st->deg, P, "counts")) || (rc = nl_alloc(&st->labels, P, "labels")) ||
+      (rc = nl_alloc(&st->flag, 1, "flag")) || (rc = nl_alloc(&st->red, 2 * kRedBlocks + 2, "red"))) {
+    free_nl(st);
+    return rc;
+  }
+  cudaError_t e = cudaMemcpyAsync(st->f, f, sizeof(float) * P * C, cudaMemcpyDeviceToDevice, st->stream);
+  if (e != cudaSuccess) {
+    free_nl(st);
+    return nl_fail(SHF_ERR_CUDA, std::string("nl_admm_init: ") + cudaGetErrorString(e));
+  }
+  rc = nl_restart(st);
+  if (rc) {
+    free_nl(st);
+    return rc;
+  }
+  *out = st;
+  return SHF_OK;
+}
+
+int nl_admm_reset(nl_state* st, const float* f, int f_on_host) {
+  if (!st || !f) return nl_fail(SHF_ERR_ARG, "nl_admm_reset: NULL argument");
+  if (!f_on_host && (reinterpret_cast<uintptr_t>(f) & 7u)) return nl_fail(SHF_ERR_ARG, "f must be 8-byte aligned");
+  NL_CK(cudaMemcpyAsync(st->f, f, sizeof(float) * st->P() * st->C,
+                        f_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st->stream));
+  return nl_restart(st);
+}
+
+int nl_admm_graph(const nl_state* st, int* nbr, int* deg, int* solve_steps) {
+  if (!st) return nl_fail(SHF_ERR_ARG, "nl_admm_graph: NULL state");
+  if (nbr) std::copy(st->nbr_host.begin(), st->nbr_host.end(), nbr);
+  if (deg) std::copy(st->deg_host.begin(), st->deg_host.end(), deg);
+  if (solve_steps) *solve_steps = static_cast<int>(st->cheb_a.size());
+  return SHF_OK;
+}
+
+int nl_admm_step(nl_state* st, int n) {
+  if (!st || n < 0) return nl_fail(SHF_ERR_ARG, "nl_admm_step: bad argument");
+  if (n == 0) return SHF_OK;
+  if (!st->graph_tried) {
+    st->graph_tried = true;
+    cudaGraph_t graph = nullptr;
+    if (st->stream && cudaStreamBeginCapture(st->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      cudaError_t e = enqueue_nl_iteration(st, nullptr);
+      cudaError_t e2 = cudaStreamEndCapture(st->stream, &graph);
+      if (e == cudaSuccess && e2 == cudaSuccess && graph) {
+        if (cudaGraphInstantiate(&st->exec, graph, 0) != cudaSuccess) st->exec = nullptr;
+      }
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    if (st->exec)
+      NL_CK(cudaGraphLaunch(st->exec, st->stream));
+    else
+      NL_CK(enqueue_nl_iteration(st, nullptr));
+  }
+  st->iter += n;
+  return SHF_OK;
+}
+
+int nl_admm_kernel_times(nl_state* st, int n, float* ms, int* nk) {
+  if (!st || !ms || n < 1) return nl_fail(SHF_ERR_ARG, "nl_admm_kernel_times: bad argument");
+  cudaEvent_t ev[kNlKinds + 1];
+  for (int i = 0; i <= kNlKinds; ++i) NL_CK(cudaEventCreate(&ev[i]));
+  for (int i = 0; i < kNlKinds; ++i) ms[i] = 0.f;
+  int rc = SHF_OK;
+  for (int it = 0; it < n && rc == SHF_OK; ++it) {
+    cudaError_t e = enqueue_nl_iteration(st, ev);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[kNlKinds]);
+    for (int i = 0; i < kNlKinds && e == cudaSuccess; ++i) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+      ms[i] += t / n;
+    }
+    if (e != cudaSuccess) rc = nl_fail(SHF_ERR_CUDA, std::string("nl_admm_kernel_times: ") + cudaGetErrorString(e));
+  }
+  for (int i = 0; i <= kNlKinds; ++i) cudaEventDestroy(ev[i]);
+  if (rc == SHF_OK) st->iter += n;
+  if (nk) *nk = kNlKinds;
+  return rc;
+}
+
+const char* nl_admm_kernel_name(int i) { return (i >= 0 && i < kNlKinds) ? kNlNames[i] : ""; }
+
+int nl_admm_get(nl_state* st, int what, void* dst, int on_host) {
+  if (!st || !dst) return nl_fail(SHF_ERR_ARG, "nl_admm_get: NULL argument");
+  const size_t P = st->P(), K = st->K, m = st->m;
+  const cudaMemcpyKind kind = on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  switch (what) {
+    case SEG_U: return nl_copy(st, dst, st->u, sizeof(float) * P * K, kind, on_host);
+    case SEG_W: return nl_copy(st, dst, st->w, sizeof(float) * P * K, kind, on_host);
+    case SEG_BW: return nl_copy(st, dst, st->bw, sizeof(float) * P * K, kind, on_host);
+    case SEG_S: return nl_copy(st, dst, st->s, sizeof(float) * P * K, kind, on_host);
+    case SEG_BV: return nl_copy(st, dst, st->bv, sizeof(float) * m * P * K, kind, on_host);
+    case SEG_V: {  // v = d + b_v
+      const size_t n = m * P * K;
+      float* tgt = static_cast<float*>(dst);
+      if (on_host) NL_CK(cudaMallocAsync(reinterpret_cast<void**>(&tgt), sizeof(float) * n, st->stream));
+      k_nl_axpb<<<grid_for(n), kThreads, 0, st->stream>>>(st->d, st->bv, tgt, 1.f, n);
+      cudaError_t e = cudaGetLastError();
+      if (on_host) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, tgt, sizeof(float) * n, cudaMemcpyDeviceToHost, st->stream);
+        cudaError_t e2 = cudaFreeAsync(tgt, st->stream);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
+      }
+      NL_CK(e);
+      return SHF_OK;
+    }
+    case SEG_LABELS:
+    case SEG_GAP: {
+      NL_CK(shf::launch_labels(st->w, st->K, static_cast<int>(P), st->labels, st->gap, st->stream));
+      return nl_copy(st, dst, what == SEG_LABELS ? static_cast<void*>(st->labels) : static_cast<void*>(st->gap),
+                     sizeof(float) * P, kind, on_host);
+    }
+    case SEG_ENERGY: {
+      k_nl_energy<<<kRedBlocks, kThreads, 0, st->stream>>>(st->w, st->s, st->nbr, st->deg, st->K, st->m, P,
+                                                           st->red + 2);
+      NL_CK(cudaGetLastError());
+      k_nl_energy_final<<<1, 32, 0, st->stream>>>(st->red + 2, kRedBlocks, st->red);
+      NL_CK(cudaGetLastError());
+      double hst[2];
+      NL_CK(cudaMemcpyAsync(hst, st->red, sizeof(hst), cudaMemcpyDeviceToHost, st->stream));
+      NL_CK(cudaStreamSynchronize(st->stream));
+      const double energy = hst[0] + static_cast<double>(st->lambda) * hst[1];
+      if (on_host) {
+        *static_cast<double*>(dst) = energy;
+        return SHF_OK;
+      }
+      return nl_copy(st, dst, &energy, sizeof(double), cudaMemcpyHostToDevice, true);
+    }
+    case SEG_ITER: {
+      if (!on_host) return nl_fail(SHF_ERR_ARG, "SEG_ITER is read into host memory");
+      NL_CK(cudaStreamSynchronize(st->stream));
+      *static_cast<int*>(dst) = st->iter;
+      return SHF_OK;
+    }
+    default: return nl_fail(SHF_ERR_ARG, "nl_admm_get: unknown selector");
+  }
+}
+
+int nl_admm_set(nl_state* st, int what, const void* src, int on_host) {
+  if (!st || !src) return nl_fail(SHF_ERR_ARG, "nl_admm_set: NULL argument");
+  const size_t P = st->P(), K = st->K, m = st->m;
+  const cudaMemcpyKind kind = on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  int rc = SHF_OK;
+  switch (what) {
+    case SEG_W: rc = nl_copy(st, st->w, src, sizeof(float) * P * K, kind, false); break;
+    case SEG_BW: rc = nl_copy(st, st->bw, src, sizeof(float) * P * K, kind, false); break;
+    case SEG_U: rc = nl_copy(st, st->u, src, sizeof(float) * P * K, kind, false); break;
+    case SEG_BV: rc = nl_copy(st, st->bv, src, sizeof(float) * m * P * K, kind, false); break;
+    case SEG_V: {
+      rc = nl_copy(st, st->d, src, sizeof(float) * m * P * K, kind, false);
+      if (rc == SHF_OK) {
+        k_nl_axpb<<<grid_for(m * P * K), kThreads, 0, st->stream>>>(st->d, st->bv, st->d, -1.f, m * P * K);
+        NL_CK(cudaGetLastError());
+      }
+      break;
+    }
+    default: return nl_fail(SHF_ERR_ARG, "nl_admm_set: accepts SEG_W, SEG_BW, SEG_U, SEG_BV and SEG_V");
+  }
+  if (rc) return rc;
+  NL_CK(rebuild_rhs(st));
+  NL_CK(cudaStreamSynchronize(st->stream));
+  return SHF_OK;
+}
+
+int nl_admm_sync(nl_state* st) {
+  if (!st) return nl_fail(SHF_ERR_ARG, "nl_admm_sync: NULL state");
+  NL_CK(cudaStreamSynchronize(st->stream));
+  return SHF_OK;
+}
+
+int nl_admm_destroy(nl_state* st) {
+  free_nl(st);
+  return SHF_OK;
+}
+
+}  // extern "C"

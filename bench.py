@@ -69,9 +69,11 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--cpu-iters", type=int, default=2, help="oracle iterations in the CPU-baseline sample")
-    ap.add_argument("--workload", choices=["bezier512", "batch", "differentiable", "rgb2048"], default="bezier512",
-                    help="bezier512 (default line), the uneven batch of 64 images, the unrolled workload, or the "
-                         "2048 x 2048 RGB image (K = 8, J = 5; 20 iterations per step unless --iters is given)")
+    ap.add_argument("--workload", choices=["bezier512", "batch", "differentiable", "rgb2048", "tv512", "nl512"],
+                    default="bezier512",
+                    help="bezier512 (default line), the uneven batch of 64 images, the unrolled workload, the "
+                         "2048 x 2048 RGB image (K = 8, J = 5; 20 iterations per step unless --iters is given), or "
+                         "the 512 x 512 image with the TV or NL-means regulariser of Sec. 4")
     ap.add_argument("--images", type=int, default=16, help="images of the differentiable workload")
     ap.add_argument("--no-differentiable", action="store_true",
                     help="skip the unrolled forward+reverse measurement the default line carries under 'differentiable'")
@@ -848,10 +850,29 @@ def run_batch(args):
     return 0
 
 
+def run_comparison_model(args):
+    """The TV or NL-means leg as the bench line itself (--workload tv512 / nl512)."""
+    import torch
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    iters = args.iters or 100
+    d = measure_tv(iters, args.steps, args.warmup) if args.workload == "tv512" else \
+        measure_nl(iters, args.steps, args.warmup)
+    line = {"metric": METRIC, "value": d["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": d["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": d["workload"], "iters_per_step": iters}, "roofline": d["roofline"],
+            "kernel_ms": d["kernel_ms"], "label_error": d["label_error"]}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload in ("tv512", "nl512"):
+        return run_comparison_model(args)
     if args.workload == "batch":
         return run_batch(args)
     if args.workload == "differentiable":

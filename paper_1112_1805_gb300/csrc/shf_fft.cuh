@@ -18,8 +18,33 @@ struct FftPlan {
   int radix[kMaxStages];
 };
 
-__host__ __device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__host__ __device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex sums on the device use the packed FP32x2 adds of sm_100-class GPUs
+// (one instruction for both components, IEEE round-to-nearest per component,
+// the same values as two scalar adds); the host emulation keeps plain floats.
+__host__ __device__ __forceinline__ float2 c_add(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+#else
+  return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
+__host__ __device__ __forceinline__ float2 c_sub(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+#else
+  return make_float2(a.x - b.x, a.y - b.y);
+#endif
+}
 __host__ __device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -42,11 +67,14 @@ __host__ __device__ __forceinline__ void dft2(float2* v) {
 template <int S>
 __host__ __device__ __forceinline__ void dft4_vals(float2& a0, float2& a1, float2& a2, float2& a3) {
   const float2 s02 = c_add(a0, a2), d02 = c_sub(a0, a2);
-  const float2 s13 = c_add(a1, a3), d13 = c_mul_si<S>(c_sub(a1, a3));
+  const float2 s13 = c_add(a1, a3), t = c_sub(a1, a3);
   a0 = c_add(s02, s13);
   a2 = c_sub(s02, s13);
-  a1 = c_add(d02, d13);
-  a3 = c_sub(d02, d13);
+  // d02 +- S i t with the swapped components in scalar adds (a packed add
+  // would first have to move them into a register pair)
+  const float s = static_cast<float>(S);
+  a1 = make_float2(d02.x - s * t.y, d02.y + s * t.x);
+  a3 = make_float2(d02.x + s * t.y, d02.y - s * t.x);
 }
 
 template <int S>

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libshearseg.so")
 SOURCES = ["shf_bank.cu", "shf_transform.cu", "shf_fast.cu", "shf_fast_col.cu", "shf_fast_row.cu", "shf_adjoint.cu",
-           "shf_capi.cu", "shf_noalloc.cu", "shf_tv.cu", "shf_nl.cu"]
+           "shf_capi.cu", "shf_noalloc.cu", "shf_tv.cu", "shf_tv_fast.cu", "shf_nl.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -209,6 +209,23 @@ int adj_part_blocks();
 // tbar[f] += sum over labels and rows of tpart[(k eta + f) H + row], in order.
 cudaError_t launch_adj_tsum_rows(const double* tpart, int K, int eta, int H, double* tbar, cudaStream_t st);
 
+// The TV u-step on register FFTs (shf_tv_fast.cu) for W/2 in 64..1024 and H
+// in 512, 1024, 2048 (powers of two): spectra [K][H][tv_fast_pitch(W)].
+namespace tvfast {
+bool tv_fast_ok(int H, int W);
+int tv_fast_pitch(int W);
+cudaError_t tv_fast_prepare();
+// rhs = q + grad^T d row by row, row transforms -> half spectra Ur.
+cudaError_t tv_fast_rows_fwd(const float* q, const float* d, float2* Ur, int K, int H, int W, const float2* twW,
+                             cudaStream_t st);
+// column transform, times the inverse symbol sym [H][W/2+1], inverse column transform: Ur -> Y.
+cudaError_t tv_fast_cols(const float2* Ur, const float* sym, float2* Y, int K, int H, int W, const float2* twH,
+                         cudaStream_t st);
+// inverse row transforms times scale -> u [K][H][W].
+cudaError_t tv_fast_rows_inv(const float2* Y, float* u, int K, int H, int W, float scale, const float2* twW,
+                             cudaStream_t st);
+}  // namespace tvfast
+
 // C ABI layer (shf_capi.cu): the geometry and device tables of a bank, and the
 // thread-local message behind shf_last_error() (returns code).
 void bank_geo(const shf_bank* b, Geo* g);

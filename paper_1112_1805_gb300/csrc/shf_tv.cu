@@ -28,6 +28,8 @@ using shf::Geo;
 struct tv_state {
   Geo g;  // eta = 1: the filter is the inverse symbol of I + grad^T grad
   int K = 0, C = 0, per_label = 0, device = 0;
+  bool fast = false;  // register-FFT u-step (power-of-two sizes), spectra at row pitch `pitch`
+  int pitch = 0;
   float gamma = 1.f, lambda = 0.f;
   std::vector<float> codebook;
   cudaStream_t stream = nullptr;
@@ -282,6 +284,20 @@ cudaError_t enqueue_tv_iteration(tv_state* st, cudaEvent_t* ev) {
   const Geo& g = st->g;
   cudaStream_t ss = st->stream;
   auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], ss) : cudaSuccess; };
+  if (st->fast) {  // the right-hand side is formed inside the row transforms
+    const float scale = 1.f / (static_cast<float>(g.H) * g.W);
+    cudaError_t e = mark(kTvRowFwd);
+    if (e == cudaSuccess) e = shf::tvfast::tv_fast_rows_fwd(st->q, st->d, st->Ur, st->K, g.H, g.W, g.twW, ss);
+    if (e == cudaSuccess) e = mark(kTvCol);
+    if (e == cudaSuccess) e = shf::tvfast::tv_fast_cols(st->Ur, st->sym, st->Y, st->K, g.H, g.W, g.twH, ss);
+    if (e == cudaSuccess) e = mark(kTvRowInv);
+    if (e == cudaSuccess) e = shf::tvfast::tv_fast_rows_inv(st->Y, st->u, st->K, g.H, g.W, scale, g.twW, ss);
+    if (e == cudaSuccess) e = mark(kTvProx);
+    if (e == cudaSuccess) e = launch_prox(st);
+    if (e == cudaSuccess) e = mark(kTvRhs);
+    if (e == cudaSuccess) e = mark(kTvKinds);
+    return e;
+  }
   cudaError_t e = mark(kTvRowFwd);
   if (e == cudaSuccess) e = shf::run_row_r2c(g, st->rhs, st->Ur, st->K, 1.f, ss);
   if (e == cudaSuccess) e = mark(kTvCol);
@@ -375,7 +391,17 @@ int tv_admm_init(int H, int W, const float* f, int C, const float* codebook, int
     }
     st->own_stream = true;
   }
+  st->fast = shf::tvfast::tv_fast_ok(H, W);
+  if (st->fast) {
+    cudaError_t e = shf::tvfast::tv_fast_prepare();
+    if (e != cudaSuccess) {
+      free_tv(st);
+      return tv_fail(SHF_ERR_CUDA, std::string("tv_admm_init: ") + cudaGetErrorString(e));
+    }
+  }
+  st->pitch = st->fast ? shf::tvfast::tv_fast_pitch(W) : g.Wh;
   const size_t P = static_cast<size_t>(H) * W, Ph = static_cast<size_t>(H) * g.Wh;
+  const size_t Phs = static_cast<size_t>(H) * st->pitch;  // spectra of the u-step at the path's pitch
   int rc;
   if ((rc = tv_alloc(&st->f, P * C, "f")) || (rc = tv_alloc(&st->s, P * K, "s")) ||
       (rc = tv_alloc(&st->u, P * K, "u")) || (rc = tv_alloc(&st->bv, 2 * P * K, "b_v")) ||
@@ -383,8 +409,8 @@ int tv_admm_init(int H, int W, const float* f, int C, const float* codebook, int
       (rc = tv_alloc(&st->bw, P * K, "b_w")) || (rc = tv_alloc(&st->q, P * K, "q")) ||
       (rc = tv_alloc(&st->rhs, P * K, "rhs")) || (rc = tv_alloc(&st->sym, Ph, "symbol")) ||
       (rc = tv_alloc(&st->gap, P, "gap")) || (rc = tv_alloc(&st->twH, H, "twH")) ||
-      (rc = tv_alloc(&st->twW, W, "twW")) || (rc = tv_alloc(&st->Ur, Ph * K, "Ur")) ||
-      (rc = tv_alloc(&st->Y, Ph * K, "Y")) || (rc = tv_alloc(&st->labels, P, "labels")) ||
+      (rc = tv_alloc(&st->twW, W, "twW")) || (rc = tv_alloc(&st->Ur, Phs * K, "Ur")) ||
+      (rc = tv_alloc(&st->Y, Phs * K, "Y")) || (rc = tv_alloc(&st->labels, P, "labels")) ||
       (rc = tv_alloc(&st->flag, 1, "flag")) || (rc = tv_alloc(&st->red, 2 * kRedBlocks + 2, "red"))) {
     free_tv(st);
     return rc;

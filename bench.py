@@ -635,8 +635,8 @@ def measure_nl(iters: int, steps: int, warmup: int, lam: float = 1.0 / 32.0, gam
     P, K, m = wl.H * wl.W, wl.K, 2 * 5
     units = P * K * iters * steps
     # Chebyshev step: x, rhs, d in; x, d out (20 B per pixel and label) + the
-    # neighbour lists and counts (4 m + 1 B per pixel)
-    solve_bytes = cheb * (K * P * 20 + P * (4 * m + 1))
+    # neighbour offsets and counts (2 m + 1 B per pixel)
+    solve_bytes = cheb * (K * P * 20 + P * (2 * m + 1))
     peak, peak_kind = peaks()
     achieved = solve_bytes / (kt["nl_solve"] / 1000.0) / 1e9
     return {"value": units / (ms / 1000.0) / 1e6, "unit": UNIT, "steps": steps, "warmup": warmup,

@@ -42,9 +42,14 @@ struct nl_state {
   std::vector<float> cheb_a, cheb_c;    // Chebyshev coefficients per step
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  float *f = nullptr, *s = nullptr, *u = nullptr, *u2 = nullptr, *cd = nullptr, *bv = nullptr, *d = nullptr;
-  float *w = nullptr, *bw = nullptr, *q = nullptr, *rhs = nullptr, *gap = nullptr;
+  float *f = nullptr, *s = nullptr, *u = nullptr, *bv = nullptr, *d = nullptr;
+  float *w = nullptr, *bw = nullptr, *q = nullptr, *gap = nullptr;
+  // the u-step's vectors pixel-major, four labels per float4 ([P][Q], Q = ceil(K/4)):
+  // two Chebyshev iterates, the Chebyshev direction and the right-hand side
+  float4 *xa = nullptr, *xb = nullptr, *cd = nullptr, *rhs = nullptr;
+  int Q = 0;
   int* nbr = nullptr;                   // [m][P]
+  short* off = nullptr;                 // [m][P] neighbour minus pixel index (|off| <= 7 W + 7)
   unsigned char *rev = nullptr, *deg = nullptr;
   int* labels = nullptr;
   int* flag = nullptr;
@@ -130,27 +135,63 @@ __device__ __forceinline__ int load_nbrs(const int* __restrict__ nbr, const unsi
 
 // One Chebyshev step for (I + D^T D) x = rhs on every label:
 // r = rhs - x - 2 (deg x - sum_nbrs x), d <- a d + c r, x_out = x_in + d.
-__global__ void __launch_bounds__(kThreads) k_nl_cheb(const float* __restrict__ xin, float* __restrict__ xout,
-                                                      float* __restrict__ d, const float* __restrict__ rhs,
-                                                      const int* __restrict__ nbr,
-                                                      const unsigned char* __restrict__ deg, int K, int m, size_t P,
-                                                      float a, float c) {
+// The iterates, the direction and the right-hand side are pixel-major, four
+// labels per float4, so that each neighbour is one 16-byte load per four
+// labels; the first step reads u label-major ([K][P], IN_LM) and the last
+// writes it back label-major (OUT_LM).
+__device__ __forceinline__ float4 f4_axpy(float a, float4 x, float4 y) {
+  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+
+template <bool IN_LM, bool OUT_LM>
+__global__ void __launch_bounds__(kThreads) k_nl_cheb(const float* __restrict__ xin_lm, const float4* __restrict__ xin,
+                                                      float* __restrict__ xout_lm, float4* __restrict__ xout,
+                                                      float4* __restrict__ d, const float4* __restrict__ rhs,
+                                                      const short* __restrict__ off,
+                                                      const unsigned char* __restrict__ deg, int K, int Q, int m,
+                                                      size_t P, float a, float c) {
   for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < P;
        i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int dg = deg[i];
     int nb[kMaxM];
-    const int dg = load_nbrs(nbr, deg, P, i, m, nb);
-    for (int k = 0; k < K; ++k) {
-      const float* x = xin + k * P;
-      const float xi = x[i];
-      float sn = 0.f;
 #pragma unroll
-      for (int b = 0; b < kMaxM; ++b)
-        if (b < dg) sn += x[nb[b]];
-      const float ax = xi + 2.f * (static_cast<float>(dg) * xi - sn);
-      const float res = rhs[k * P + i] - ax;
-      const float dn = a * d[k * P + i] + c * res;
-      d[k * P + i] = dn;
-      xout[k * P + i] = xi + dn;
+    for (int b = 0; b < kMaxM; ++b) nb[b] = (b < dg && b < m) ? static_cast<int>(i) + off[b * P + i] : 0;
+    auto load = [&](size_t j, int qd) -> float4 {
+      if constexpr (IN_LM) {
+        const int k0 = 4 * qd;
+        return make_float4(xin_lm[k0 * P + j], k0 + 1 < K ? xin_lm[(k0 + 1) * P + j] : 0.f,
+                           k0 + 2 < K ? xin_lm[(k0 + 2) * P + j] : 0.f, k0 + 3 < K ? xin_lm[(k0 + 3) * P + j] : 0.f);
+      } else {
+        return xin[j * Q + qd];
+      }
+    };
+    for (int qd = 0; qd < Q; ++qd) {
+      const float4 xi = load(i, qd);
+      float4 sn = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int b = 0; b < kMaxM; ++b) {
+        if (b < dg) {
+          const float4 xn = load(static_cast<size_t>(nb[b]), qd);
+          sn = make_float4(sn.x + xn.x, sn.y + xn.y, sn.z + xn.z, sn.w + xn.w);
+        }
+      }
+      const float fd = static_cast<float>(dg);
+      const float4 rh = rhs[i * Q + qd];
+      const float4 res = make_float4(rh.x - (xi.x + 2.f * (fd * xi.x - sn.x)), rh.y - (xi.y + 2.f * (fd * xi.y - sn.y)),
+                                     rh.z - (xi.z + 2.f * (fd * xi.z - sn.z)), rh.w - (xi.w + 2.f * (fd * xi.w - sn.w)));
+      const float4 dn = f4_axpy(c, res, make_float4(a * d[i * Q + qd].x, a * d[i * Q + qd].y, a * d[i * Q + qd].z,
+                                                     a * d[i * Q + qd].w));
+      d[i * Q + qd] = dn;
+      const float4 xo = make_float4(xi.x + dn.x, xi.y + dn.y, xi.z + dn.z, xi.w + dn.w);
+      if constexpr (OUT_LM) {
+        const int k0 = 4 * qd;
+        xout_lm[k0 * P + i] = xo.x;
+        if (k0 + 1 < K) xout_lm[(k0 + 1) * P + i] = xo.y;
+        if (k0 + 2 < K) xout_lm[(k0 + 2) * P + i] = xo.z;
+        if (k0 + 3 < K) xout_lm[(k0 + 3) * P + i] = xo.w;
+      } else {
+        xout[i * Q + qd] = xo;
+      }
     }
   }
 }
@@ -220,11 +261,13 @@ __global__ void __launch_bounds__(kThreads) k_nl_prox(const float* __restrict__ 
   }
 }
 
-// rhs = q + D^T d: (D^T d)(j) = sum_{b < deg(j)} [d_rev(j,b)(nbr_b(j)) - d_b(j)].
+// rhs = q + D^T d: (D^T d)(j) = sum_{b < deg(j)} [d_rev(j,b)(nbr_b(j)) - d_b(j)],
+// written pixel-major ([P][4 Q], labels K..4Q-1 zero) for the Chebyshev steps.
 __global__ void __launch_bounds__(kThreads) k_nl_rhs(const float* __restrict__ q, const float* __restrict__ d,
                                                      float* __restrict__ rhs, const int* __restrict__ nbr,
                                                      const unsigned char* __restrict__ rev,
-                                                     const unsigned char* __restrict__ deg, int K, int m, size_t P) {
+                                                     const unsigned char* __restrict__ deg, int K, int Q, int m,
+                                                     size_t P) {
   for (size_t j = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; j < P;
        j += static_cast<size_t>(gridDim.x) * blockDim.x) {
     int nb[kMaxM];
@@ -238,8 +281,9 @@ __global__ void __launch_bounds__(kThreads) k_nl_rhs(const float* __restrict__ q
 #pragma unroll
       for (int b = 0; b < kMaxM; ++b)
         if (b < dg) acc += dk[rv[b] * P + nb[b]] - dk[b * P + j];
-      rhs[k * P + j] = q[k * P + j] + acc;
+      rhs[j * 4 * Q + k] = q[k * P + j] + acc;  // pixel-major, four labels per float4
     }
+    for (int k = K; k < 4 * Q; ++k) rhs[j * 4 * Q + k] = 0.f;
   }
 }
 
@@ -340,8 +384,8 @@ void free_nl(nl_state* st) {
   if (!st) return;
   if (st->stream) cudaStreamSynchronize(st->stream);
   if (st->exec) cudaGraphExecDestroy(st->exec);
-  void* bufs[] = {st->f, st->s, st->u, st->u2, st->cd, st->bv, st->d, st->w, st->bw, st->q, st->rhs, st->gap,
-                  st->nbr, st->rev, st->deg, st->labels, st->flag, st->red};
+  void* bufs[] = {st->f, st->s, st->u, st->xa, st->xb, st->cd, st->bv, st->d, st->w, st->bw, st->q, st->rhs,
+                  st->gap, st->nbr, st->off, st->rev, st->deg, st->labels, st->flag, st->red};
   for (void* b : bufs) cudaFree(b);
   if (st->own_stream && st->stream) cudaStreamDestroy(st->stream);
   delete st;
@@ -425,7 +469,11 @@ int build_graph(nl_state* st) {
       while (nb[static_cast<size_t>(j) * m + pos] != static_cast<int>(i)) ++pos;
       rev[static_cast<size_t>(b) * P + i] = static_cast<unsigned char>(pos);
     }
+  std::vector<short> offs(P * m, 0);
+  for (size_t e = 0; e < P * m; ++e)
+    if (nbt[e] >= 0) offs[e] = static_cast<short>(nbt[e] - static_cast<long long>(e % P));
   NL_CK(cudaMemcpy(st->nbr, nbt.data(), sizeof(int) * P * m, cudaMemcpyHostToDevice));
+  NL_CK(cudaMemcpy(st->off, offs.data(), sizeof(short) * P * m, cudaMemcpyHostToDevice));
   NL_CK(cudaMemcpy(st->rev, rev.data(), P * m, cudaMemcpyHostToDevice));
   NL_CK(cudaMemcpy(st->deg, deg8.data(), P, cudaMemcpyHostToDevice));
   // Chebyshev iteration on [1, 1 + 4 deg_max]: theta = centre, delta = half width
@@ -437,7 +485,7 @@ int build_graph(nl_state* st) {
     const double qrate = (std::sqrt(kappa) - 1.0) / (std::sqrt(kappa) + 1.0);
     n = qrate > 0.0 ? static_cast<int>(std::ceil(std::log(2.0 / 1e-7) / -std::log(qrate))) : 1;
   }
-  n += n & 1;  // even: the result lands in u
+  n = std::max(n + (n & 1), 2);  // even and >= 2: the first step reads u, the last writes it
   st->cheb_a.assign(n, 0.f);
   st->cheb_c.assign(n, 0.f);
   st->cheb_c[0] = static_cast<float>(1.0 / theta);
@@ -474,8 +522,8 @@ cudaError_t launch_prox(nl_state* st) {
 }
 
 cudaError_t launch_rhs(nl_state* st) {
-  k_nl_rhs<<<grid_for(st->P()), kThreads, 0, st->stream>>>(st->q, st->d, st->rhs, st->nbr, st->rev, st->deg, st->K,
-                                                           st->m, st->P());
+  k_nl_rhs<<<grid_for(st->P()), kThreads, 0, st->stream>>>(st->q, st->d, reinterpret_cast<float*>(st->rhs), st->nbr,
+                                                           st->rev, st->deg, st->K, st->Q, st->m, st->P());
   return cudaGetLastError();
 }
 
@@ -486,13 +534,23 @@ cudaError_t enqueue_nl_iteration(nl_state* st, cudaEvent_t* ev) {
   auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], ss) : cudaSuccess; };
   cudaError_t e = mark(kNlSolve);
   const size_t P = st->P();
-  float* x0 = st->u;
-  float* x1 = st->u2;
-  for (size_t k = 0; k < st->cheb_a.size() && e == cudaSuccess; ++k) {
-    k_nl_cheb<<<grid_for(P), kThreads, 0, ss>>>(x0, x1, st->cd, st->rhs, st->nbr, st->deg, st->K, st->m, P,
-                                                st->cheb_a[k], st->cheb_c[k]);
+  const int n = static_cast<int>(st->cheb_a.size());  // even, >= 2
+  float4* x0 = st->xa;
+  float4* x1 = st->xb;
+  for (int k = 0; k < n && e == cudaSuccess; ++k) {
+    const float a = st->cheb_a[k], c = st->cheb_c[k];
+    if (k == 0)  // from u (label-major)
+      k_nl_cheb<true, false><<<grid_for(P), kThreads, 0, ss>>>(st->u, nullptr, nullptr, x0, st->cd, st->rhs, st->off,
+                                                                st->deg, st->K, st->Q, st->m, P, a, c);
+    else if (k == n - 1)  // back into u
+      k_nl_cheb<false, true><<<grid_for(P), kThreads, 0, ss>>>(nullptr, x0, st->u, nullptr, st->cd, st->rhs, st->off,
+                                                                st->deg, st->K, st->Q, st->m, P, a, c);
+    else {
+      k_nl_cheb<false, false><<<grid_for(P), kThreads, 0, ss>>>(nullptr, x0, nullptr, x1, st->cd, st->rhs, st->off,
+                                                                 st->deg, st->K, st->Q, st->m, P, a, c);
+      std::swap(x0, x1);
+    }
     e = cudaGetLastError();
-    std::swap(x0, x1);
   }
   if (e == cudaSuccess) e = mark(kNlProx);
   if (e == cudaSuccess) e = launch_prox(st);
@@ -531,7 +589,7 @@ int nl_restart(nl_state* st) {
   NL_CK(cudaMemsetAsync(st->bw, 0, sizeof(float) * P * K, st->stream));
   NL_CK(cudaMemsetAsync(st->bv, 0, sizeof(float) * m * P * K, st->stream));
   NL_CK(cudaMemsetAsync(st->d, 0, sizeof(float) * m * P * K, st->stream));
-  NL_CK(cudaMemsetAsync(st->cd, 0, sizeof(float) * P * K, st->stream));
+  NL_CK(cudaMemsetAsync(st->cd, 0, sizeof(float4) * P * st->Q, st->stream));
   NL_CK(rebuild_rhs(st));
   NL_CK(cudaStreamSynchronize(st->stream));
   st->iter = 0;
@@ -574,6 +632,7 @@ int nl_admm_init(int H, int W, const float* f, int C, const float* codebook, int
   st->C = C;
   st->prm = *p;
   st->m = 2 * p->neighbours;
+  st->Q = (K + 3) / 4;
   st->gamma = p->gamma;
   st->lambda = p->lambda;
   st->codebook.assign(codebook, codebook + K * C);
@@ -595,12 +654,14 @@ int nl_admm_init(int H, int W, const float* f, int C, const float* codebook, int
   const size_t P = static_cast<size_t>(H) * W, m = st->m;
   int rc;
   if ((rc = nl_alloc(&st->f, P * C, "f")) || (rc = nl_alloc(&st->s, P * K, "s")) ||
-      (rc = nl_alloc(&st->u, P * K, "u")) || (rc = nl_alloc(&st->u2, P * K, "u2")) ||
-      (rc = nl_alloc(&st->cd, P * K, "chebyshev d")) || (rc = nl_alloc(&st->bv, m * P * K, "b_v")) ||
+      (rc = nl_alloc(&st->u, P * K, "u")) || (rc = nl_alloc(&st->xa, P * st->Q, "chebyshev x")) ||
+      (rc = nl_alloc(&st->xb, P * st->Q, "chebyshev x")) || (rc = nl_alloc(&st->cd, P * st->Q, "chebyshev d")) ||
+      (rc = nl_alloc(&st->bv, m * P * K, "b_v")) ||
       (rc = nl_alloc(&st->d, m * P * K, "d")) || (rc = nl_alloc(&st->w, P * K, "w")) ||
       (rc = nl_alloc(&st->bw, P * K, "b_w")) || (rc = nl_alloc(&st->q, P * K, "q")) ||
-      (rc = nl_alloc(&st->rhs, P * K, "rhs")) || (rc = nl_alloc(&st->gap, P, "gap")) ||
-      (rc = nl_alloc(&st->nbr, P * m, "neighbours")) || (rc = nl_alloc(&st->rev, P * m, "reverse")) ||
+      (rc = nl_alloc(&st->rhs, P * st->Q, "rhs")) || (rc = nl_alloc(&st->gap, P, "gap")) ||
+      (rc = nl_alloc(&st->nbr, P * m, "neighbours")) || (rc = nl_alloc(&st->off, P * m, "offsets")) ||
+      (rc = nl_alloc(&st->rev, P * m, "reverse")) ||
       (rc = nl_alloc(&st->deg, P, "counts")) || (rc = nl_alloc(&st->labels, P, "labels")) ||
       (rc = nl_alloc(&st->flag, 1, "flag")) || (rc = nl_alloc(&st->red, 2 * kRedBlocks + 2, "red"))) {
     free_nl(st);

@@ -430,15 +430,28 @@ __global__ void __launch_bounds__(256, 2)
     const float th = thr[f];
     const size_t rix = (static_cast<size_t>(label) * eta + f) * H + row;
     float2* X = Y + (static_cast<size_t>(fl) * H + row) * Whp;
+    // the next row's spectrum columns into L1 (one 128-byte line per thread
+    // and step), so that its loads a row from now do not wait on L2
+    if (fln < nv) {
+      int labn, fn;
+      pair_of(fln, labn, fn);
+      const int2 rgn = ranges[fn];
+      if (rgn.x <= rgn.y) {
+        const int n0 = rgn.x & ~cmask, n1 = min(L, (rgn.y | cmask));
+        const char* base = reinterpret_cast<const char*>(Y + (static_cast<size_t>(fln) * H + rown) * Whp + n0);
+        const int lines = ((n1 - n0 + 1) * 8 + 127) / 128;
+        for (int ln = tt; ln < lines; ln += T) asm volatile("prefetch.global.L1 [%0];" ::"l"(base + 128 * ln));
+      }
+    }
     float2 v[16];
     if constexpr (T <= 32) {
       // inverse packing (r16::pack_step), X_{L-n} from the partner lane
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         const int n = tt + k * T;
-        v[k] = (n >= c0 && n <= c1) ? __ldcg(X + n) : make_float2(0.f, 0.f);
+        v[k] = (n >= c0 && n <= c1) ? __ldca(X + n) : make_float2(0.f, 0.f);
       }
-      float2 prev = (c1 >= L) ? __ldcg(X + L) : make_float2(0.f, 0.f);
+      float2 prev = (c1 >= L) ? __ldca(X + L) : make_float2(0.f, 0.f);
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         float2 ra, rb;
@@ -453,8 +466,8 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         const int n = tt + k * T, m = L - n;
-        const float2 a = (n >= c0 && n <= c1) ? __ldcg(X + n) : make_float2(0.f, 0.f);
-        const float2 c = (m >= c0 && m <= c1) ? c_conj(__ldcg(X + m)) : make_float2(0.f, 0.f);
+        const float2 a = (n >= c0 && n <= c1) ? __ldca(X + n) : make_float2(0.f, 0.f);
+        const float2 c = (m >= c0 && m <= c1) ? c_conj(__ldca(X + m)) : make_float2(0.f, 0.f);
         const float2 s2 = c_add(a, c), d = c_sub(a, c);
         const float2 t = c_mul(c_conj(tw[n]), d);
         v[k] = make_float2(s2.x - t.y, s2.y + t.x);

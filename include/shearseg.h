@@ -184,11 +184,15 @@ int seg_admm_step(seg_state* st, int n_iters);
  * range of the wave's (label, column tile, filter) triples.  Other
  * sizes (fast = 0) run the general kernels with tiles of tile_cols
  * half-spectrum columns and tile_rows rows and `groups` filter
- * groups in the synthesis sums.  Fields of the other path are 0 in
- * seg_admm_get_plan and ignored by seg_admm_set_plan.  The plan changes the
- * grouping of the FP32 synthesis sums (wave_mib, col_ctas_per_sm, groups), so
- * results are bitwise reproducible for a fixed plan on a given GPU model, and
- * agree within rounding across plans.
+ * groups in the synthesis sums.  On the fast path the plan also names the
+ * FFT kernels: the v-step's (8 or 16 values per thread, one row or a pair of
+ * rows per thread group) and the fan's and gather's (8 or 16 values per
+ * thread), among those that exist for the size.  Fields of the other path
+ * are 0 in seg_admm_get_plan and ignored by seg_admm_set_plan.  The plan
+ * changes the grouping of the FP32 synthesis sums (wave_mib,
+ * col_ctas_per_sm, groups) and the order of the FFT arithmetic (row_kernel,
+ * col_kernel), so results are bitwise reproducible for a fixed plan on a
+ * given GPU model, and agree within rounding across plans.
  * ------------------------------------------------------------------------- */
 typedef struct {
   int fast;          /* read-only: 1 power-of-two path, 0 general path        */
@@ -198,6 +202,12 @@ typedef struct {
   int tile_rows;     /* general: rows per row block                           */
   int groups;        /* general: filter groups of the synthesis partial sums  */
   float us_per_iter; /* seg_admm_tune: measured microseconds per iteration    */
+  int row_kernel;    /* fast: v-step FFT kernel, 0 default for the width, 1 8
+                        values per thread, 2 16 values (half widths 64..1024,
+                        powers of two), 3 pairs of rows (half widths 64, 128)  */
+  int col_kernel;    /* fast: fan and gather FFT kernel, 0 default for the
+                        height, 1 8 values per thread, 2 16 values (heights
+                        512, 1024, 2048)                                      */
 } seg_plan;
 
 /* The state's current plan. */
@@ -212,8 +222,9 @@ int seg_admm_set_plan(seg_state* st, const seg_plan* p);
 /* Autotuner: times `iters` iterations (after one warm-up; replays of the plain
  * iteration graph, without the per-kernel timing events) of each candidate
  * plan, varying one parameter at a time around the best so far (fast: wave
- * budget, then col_ctas_per_sm; general: groups, then tile_cols, then
- * tile_rows), and installs the fastest.  The iterate and the iteration count
+ * budget, then col_ctas_per_sm, then the v-step's FFT kernel, then the
+ * column FFT kernel; general: groups, then tile_cols, then tile_rows), and
+ * installs the fastest.  The iterate and the iteration count
  * are saved before and restored after the trials (needs memory for one copy
  * of b_v, w, b_w, u and the u-spectra).  best (may be NULL) receives the plan
  * with its time.  Synchronises.  Errors: SHF_ERR_ARG (iters < 1),

@@ -488,14 +488,17 @@ cudaGraphExec_t capture_work(seg_state* st, F enqueue) {
 // allocates what depends on it (one wave of coefficient spectra Y, the
 // partial tiles, the device work list); the previous buffers are released
 // only once the new ones exist.  Synchronises the state's stream.
-int install_fast_plan(seg_state* st, int wave_mib, int col_ctas_per_sm) {
+int install_fast_plan(seg_state* st, int wave_mib, int col_ctas_per_sm, int row_kernel = shf::kRowDefault,
+                      int col_kernel = shf::kColDefault) {
   const Geo& g = st->g;
   shf::FastPlan plan;
   plan.wave_mib = wave_mib;
   plan.col_ctas_per_sm = col_ctas_per_sm;
-  plan.col_ctas = shf::fast_col_ctas(g, col_ctas_per_sm);
-  plan.fan_ctas = shf::fast_fan_ctas(g);
-  plan.row_ctas = shf::fast_row_ctas(g);
+  plan.row_kernel = row_kernel;
+  plan.col_kernel = col_kernel;
+  plan.col_ctas = shf::fast_col_ctas(g, col_ctas_per_sm, col_kernel);
+  plan.fan_ctas = shf::fast_fan_ctas(g, col_kernel);
+  plan.row_ctas = shf::fast_row_ctas(g, row_kernel);
   if (plan.col_ctas < 1 || plan.fan_ctas < 1 || plan.row_ctas < 1)
     return fail(SHF_ERR_CUDA, "install_fast_plan: no resident CTA");
   std::vector<shf::WorkItem> h_items;
@@ -774,6 +777,8 @@ int seg_admm_get_plan(const seg_state* st, seg_plan* out) {
   out->tile_rows = st->fast ? 0 : st->g.RB;
   out->groups = st->fast ? 0 : st->groups;
   out->us_per_iter = 0.f;
+  out->row_kernel = st->fast ? st->plan.row_kernel : 0;
+  out->col_kernel = st->fast ? st->plan.col_kernel : 0;
   return SHF_OK;
 }
 
@@ -782,8 +787,12 @@ int seg_admm_set_plan(seg_state* st, const seg_plan* p) {
   if (st->fast) {
     if (p->col_ctas_per_sm < 0 || p->col_ctas_per_sm > 32 || p->wave_mib < 1 || p->wave_mib > 4096)
       return fail(SHF_ERR_ARG, "seg_admm_set_plan: col_ctas_per_sm must be in [0, 32] and wave_mib in [1, 4096]");
-    if (p->col_ctas_per_sm == st->plan.col_ctas_per_sm && p->wave_mib == st->plan.wave_mib) return SHF_OK;
-    return install_fast_plan(st, p->wave_mib, p->col_ctas_per_sm);
+    if (!shf::fast_row_kernel_ok(st->g, p->row_kernel) || !shf::fast_col_kernel_ok(st->g, p->col_kernel))
+      return fail(SHF_ERR_ARG, "seg_admm_set_plan: row_kernel or col_kernel not available at this size");
+    if (p->col_ctas_per_sm == st->plan.col_ctas_per_sm && p->wave_mib == st->plan.wave_mib &&
+        p->row_kernel == st->plan.row_kernel && p->col_kernel == st->plan.col_kernel)
+      return SHF_OK;
+    return install_fast_plan(st, p->wave_mib, p->col_ctas_per_sm, p->row_kernel, p->col_kernel);
   }
   if (p->tile_cols < 1 || p->tile_rows < 1 || p->groups < 1)
     return fail(SHF_ERR_ARG, "seg_admm_set_plan: tile_cols, tile_rows and groups must be positive");
@@ -845,9 +854,26 @@ std::vector<seg_plan> plan_candidates(const seg_state* st, const seg_plan& base,
         p.wave_mib = mib;
         out.push_back(p);
       }
+    } else if (stage == 2) {
+      // the FFT kernel of the forward v-step: 8 or 16 values per thread, one
+      // row or a pair of rows per group
+      for (int rk : {shf::kRow8, shf::kRow16, shf::kRowPair}) {
+        if (!shf::fast_row_kernel_ok(g, rk)) continue;
+        seg_plan p = base;
+        p.row_kernel = rk;
+        out.push_back(p);
+      }
+    } else if (stage == 3) {
+      // the FFT kernel of the fan and the gather: 8 or 16 values per thread
+      for (int ck : {shf::kCol8, shf::kCol16}) {
+        if (!shf::fast_col_kernel_ok(g, ck)) continue;
+        seg_plan p = base;
+        p.col_kernel = ck;
+        out.push_back(p);
+      }
     } else if (stage == 1) {
       // resident column CTAs per SM: every count up to what fits (0 = all)
-      const int fit = shf::fast_col_ctas(g, 0) / std::max(1, shf::fast_col_ctas(g, 1));
+      const int fit = shf::fast_col_ctas(g, 0, base.col_kernel) / std::max(1, shf::fast_col_ctas(g, 1, base.col_kernel));
       for (int c = 1; c < fit; ++c) {
         seg_plan p = base;
         p.col_ctas_per_sm = c;
@@ -929,7 +955,7 @@ int seg_admm_tune(seg_state* st, int iters, seg_plan* best_out) {
   seg_admm_get_plan(st, &best);
   best.us_per_iter = INFINITY;
   int rc = e == cudaSuccess ? SHF_OK : fail(SHF_ERR_CUDA, cudaGetErrorString(e));
-  for (int stage = 0; stage < 3 && !rc; ++stage) {
+  for (int stage = 0; stage < 4 && !rc; ++stage) {
     const seg_plan base = best;
     for (const seg_plan& cand : plan_candidates(st, base, stage)) {
       int r = seg_admm_set_plan(st, &cand);

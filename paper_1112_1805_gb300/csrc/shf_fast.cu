@@ -86,16 +86,20 @@ int sm_count() {
 }
 }  // namespace
 
-int fast_col_ctas(const Geo& g, int per_sm) {
-  const int fit = fast::col_ctas_per_sm(g.H);
+int fast_col_ctas(const Geo& g, int per_sm, int col_kernel) {
+  const int fit = fast::col_ctas_per_sm(g.H, col_kernel);
   if (fit < 1) return 0;
   const int k = (per_sm <= 0 || per_sm > fit) ? fit : per_sm;
   return k * sm_count();
 }
 
-int fast_row_ctas(const Geo& g) { return fast::row_ctas_per_sm(g.L) * sm_count(); }
+int fast_row_ctas(const Geo& g, int row_kernel) { return fast::row_ctas_per_sm(g.L, 0, row_kernel) * sm_count(); }
 
-int fast_fan_ctas(const Geo& g) { return fast::fan_ctas_per_sm(g.H) * sm_count(); }
+int fast_fan_ctas(const Geo& g, int col_kernel) { return fast::fan_ctas_per_sm(g.H, col_kernel) * sm_count(); }
+
+bool fast_row_kernel_ok(const Geo& g, int row_kernel) { return fast::row_kernel_ok(g.L, row_kernel); }
+
+bool fast_col_kernel_ok(const Geo& g, int col_kernel) { return fast::col_kernel_ok(g.H, col_kernel); }
 
 void build_fast_plan(const Geo& g, const int2* ranges, int K, FastPlan* plan, std::vector<WorkItem>* items,
                      std::vector<int>* cta_begin, std::vector<int>* tile_begin, std::vector<int>* tile_slots) {
@@ -189,7 +193,7 @@ cudaError_t run_fast_iteration_body(const Geo& g, const FastPlan& plan, const fl
                                     cudaStream_t st, const LaunchHook& hook, signed char* code) {
   const int Whp = fast_pitch(g);
   const int nw = static_cast<int>(plan.wave_f0.size());
-  const int rpc = fast::row_groups_per_cta(g.L);
+  const int rpc = fast::row_groups_per_cta(g.L, 0, plan.row_kernel);
   hook.mark(kKindColFwd);
   cudaError_t e = fast::col_fwd(g, Ur, uhat, K, Whp, st);
   for (int w = 0; w < nw && e == cudaSuccess; ++w) {
@@ -200,15 +204,15 @@ cudaError_t run_fast_iteration_body(const Geo& g, const FastPlan& plan, const fl
     const int* fcb = plan.cta_begin + f0c + w;
     if (nfc > 0) {
       hook.mark(kKindFan);
-      e = fast::col_fan(g, nfc, uhat, plan.items, fcb, Y, Whp, wv, st);
+      e = fast::col_fan(g, nfc, uhat, plan.items, fcb, Y, Whp, wv, plan.col_kernel, st);
     }
     hook.mark(kKindShrink);
     const int groups = (wv.nv * g.H + rpc - 1) / rpc;
     const int ctas = std::min(groups, std::max(plan.row_ctas, 1));
-    if (e == cudaSuccess) e = fast::row_shrink(g, ctas, Y, bv, thr, Whp, wv, scale, code, st);
+    if (e == cudaSuccess) e = fast::row_shrink(g, ctas, Y, bv, thr, Whp, wv, scale, code, plan.row_kernel, st);
     if (nc > 0 && e == cudaSuccess) {
       hook.mark(kKindGather);
-      e = fast::col_gather(g, nc, Y, plan.items, cb, partial, Whp, wv, st);
+      e = fast::col_gather(g, nc, Y, plan.items, cb, partial, Whp, wv, plan.col_kernel, st);
     }
   }
   hook.mark(kKindReduce);
@@ -230,11 +234,11 @@ cudaError_t run_fast_adjoint_body(const Geo& g, const FastPlan& plan, const floa
     const int* cb = plan.cta_begin + c0 + w;
     const int f0c = plan.wave_fcta0[w], nfc = plan.wave_fcta0[w + 1] - f0c;
     const int* fcb = plan.cta_begin + f0c + w;
-    if (nfc > 0) e = fast::col_fan(g, nfc, uhat, plan.items, fcb, Y, Whp, wv, st);
+    if (nfc > 0) e = fast::col_fan(g, nfc, uhat, plan.items, fcb, Y, Whp, wv, plan.col_kernel, st);
     const int groups = (wv.nv * g.H + rpc - 1) / rpc;
     const int ctas = std::min(groups, std::max(actas, 1));
     if (e == cudaSuccess) e = fast::row_adjoint(g, ctas, Y, bvbar, thr, Whp, wv, scale, code, tpart, st);
-    if (nc > 0 && e == cudaSuccess) e = fast::col_gather(g, nc, Y, plan.items, cb, partial, Whp, wv, st);
+    if (nc > 0 && e == cudaSuccess) e = fast::col_gather(g, nc, Y, plan.items, cb, partial, Whp, wv, plan.col_kernel, st);
   }
   if (e == cudaSuccess) e = fast::col_reduce(g, partial, plan.tile_begin, plan.tile_slots, Tbar, K, st);
   return e;

@@ -67,18 +67,22 @@ struct Wave {
 };
 
 // Column kernels (shf_fast_col.cu).  Whp: row pitch of the internal spectra.
+// `variant` (ColKernel, shf_internal.h) selects the transform: 8 values per
+// thread, or 16 (radix-16 passes; heights 512, 1024, 2048); 0 is the default
+// for the height.
+bool col_kernel_ok(int H, int variant);
 cudaError_t prepare_col_kernels();
-int col_ctas_per_sm(int H);  // resident CTAs per SM of the gather kernel
-int fan_ctas_per_sm(int H);  // resident CTAs per SM of the fan kernel
+int col_ctas_per_sm(int H, int variant = 0);  // resident CTAs per SM of the gather kernel
+int fan_ctas_per_sm(int H, int variant = 0);  // resident CTAs per SM of the fan kernel
 // Ur [K][H][Wh] -> uhat [K][H][Whp]: column-forward of the row spectra of u.
 cudaError_t col_fwd(const Geo& g, const float2* Ur, float2* uhat, int K, int Whp, cudaStream_t st);
 // Y_v = column-inverse(W_f * uhat_label) on the (label, tile, filter) items of
 // CTA ranges cta_begin[0..nc] of wave wv.
 cudaError_t col_fan(const Geo& g, int nc, const float2* uhat, const WorkItem* items, const int* cta_begin,
-                    float2* Y, int Whp, const Wave& wv, cudaStream_t st);
+                    float2* Y, int Whp, const Wave& wv, int variant, cudaStream_t st);
 // partial[slot] = sum over runs of items of W_f * column-forward(Y_v).
 cudaError_t col_gather(const Geo& g, int nc, const float2* Y, const WorkItem* items, const int* cta_begin,
-                       float2* partial, int Whp, const Wave& wv, cudaStream_t st);
+                       float2* partial, int Whp, const Wave& wv, int variant, cudaStream_t st);
 // T [K][H][Wh] = column-inverse of the per-(label, tile) sums of the partial slots.
 cudaError_t col_reduce(const Geo& g, const float2* partial, const int* tile_begin, const int* tile_slots, float2* T,
                        int K, cudaStream_t st);
@@ -87,12 +91,17 @@ cudaError_t col_reduce(const Geo& g, const float2* partial, const int* tile_begi
 cudaError_t prepare_row_kernels();
 // Resident CTAs per SM and rows in flight per CTA of the v-step kernel
 // (mode 0) or of its adjoint (mode 1).
-int row_ctas_per_sm(int L, int mode = 0);
-int row_groups_per_cta(int L, int mode = 0);
+// `variant` (RowKernel, shf_internal.h) selects the forward v-step: 8 values
+// per thread, 16 (half widths 64..1024, powers of two) or pairs of rows (64,
+// 128); 0 is the default for the width; the adjoint (mode 1) always takes its
+// default.
+bool row_kernel_ok(int L, int variant);
+int row_ctas_per_sm(int L, int mode = 0, int variant = 0);
+int row_groups_per_cta(int L, int mode = 0, int variant = 0);
 // v-step on the rows of wave wv: ctas resident CTAs; code (optional,
 // [K][eta][H][W] bytes) receives 0 where |g| < t, else sign g.
 cudaError_t row_shrink(const Geo& g, int ctas, float2* Y, float* bv, const float* thr, int Whp, const Wave& wv,
-                       float scale, signed char* code, cudaStream_t st);
+                       float scale, signed char* code, int variant, cudaStream_t st);
 // Adjoint of the v-step for the reverse mode: Y holds the spectra of the rows
 // of S Qbar on input and those of the new bvbar on output; tpart
 // [K][eta][H] receives the rows' threshold sums.

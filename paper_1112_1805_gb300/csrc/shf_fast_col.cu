@@ -459,13 +459,21 @@ cudaError_t prepare_col_kernels() {
   return e;
 }
 
-int fan_ctas_per_sm(int H) {
+// The column transform a plan's variant selects at height H: radix-16 (16
+// values per thread) where it exists and is asked for or is the default.
+bool use16(int H, int variant) { return use_fan16(H) && variant != kCol8; }
+
+bool col_kernel_ok(int H, int variant) {
+  return variant == kColDefault || variant == kCol8 || (variant == kCol16 && use_fan16(H));
+}
+
+int fan_ctas_per_sm(int H, int variant) {
   int fit = 0;
   cudaError_t e = cudaErrorInvalidValue;
   switch (H) {
 #define SHF_OCC(N)                                                                                          \
   case N:                                                                                                   \
-    if (use_fan16(N))                                                                                       \
+    if (use16(N, variant))                                                                                  \
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_fcol_fan16<fan16_len(N)>,                  \
                                                         Col16Geo<fan16_len(N)>::NT, fan16_smem<N>());      \
     else                                                                                                    \
@@ -478,13 +486,13 @@ int fan_ctas_per_sm(int H) {
   return e == cudaSuccess ? fit : 0;
 }
 
-int col_ctas_per_sm(int H) {
+int col_ctas_per_sm(int H, int variant) {
   int fit = 0;
   cudaError_t e = cudaErrorInvalidValue;
   switch (H) {
 #define SHF_OCC(N)                                                                                          \
   case N:                                                                                                   \
-    if (use_fan16(N))                                                                                       \
+    if (use16(N, variant))                                                                                  \
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_fcol_gather16<fan16_len(N)>,               \
                                                         Col16Geo<fan16_len(N)>::NT, fan16_smem<N>());      \
     else                                                                                                    \
@@ -510,11 +518,11 @@ cudaError_t col_fwd(const Geo& g, const float2* Ur, float2* uhat, int K, int Whp
 }
 
 cudaError_t col_fan(const Geo& g, int nc, const float2* uhat, const WorkItem* items, const int* cta_begin,
-                    float2* Y, int Whp, const Wave& wv, cudaStream_t st) {
+                    float2* Y, int Whp, const Wave& wv, int variant, cudaStream_t st) {
   switch (g.H) {
 #define SHF_CASE(N)                                                                                              \
   case N:                                                                                                        \
-    if (use_fan16(N))                                                                                            \
+    if (use16(N, variant))                                                                                       \
       return launch_pdl(k_fcol_fan16<fan16_len(N)>, dim3(nc), dim3(Col16Geo<fan16_len(N)>::NT), fan16_smem<N>(),  \
                         st, uhat, g.bank, items, cta_begin, Y, g.Wh, Whp, wv.l0, wv.f0, wv.nf, g.twH);           \
     return launch_pdl(k_fcol_fan<N>, dim3(nc), dim3(ColGeo<N>::NT), col_smem<N>(), st, uhat, g.bank, items, cta_begin, Y, \
@@ -526,11 +534,11 @@ cudaError_t col_fan(const Geo& g, int nc, const float2* uhat, const WorkItem* it
 }
 
 cudaError_t col_gather(const Geo& g, int nc, const float2* Y, const WorkItem* items, const int* cta_begin,
-                       float2* partial, int Whp, const Wave& wv, cudaStream_t st) {
+                       float2* partial, int Whp, const Wave& wv, int variant, cudaStream_t st) {
   switch (g.H) {
 #define SHF_CASE(N)                                                                                           \
   case N:                                                                                                     \
-    if (use_fan16(N))                                                                                         \
+    if (use16(N, variant))                                                                                    \
       return launch_pdl(k_fcol_gather16<fan16_len(N)>, dim3(nc), dim3(Col16Geo<fan16_len(N)>::NT),           \
                         fan16_smem<N>(), st, Y, g.bank, items, cta_begin, partial, g.Wh, Whp, wv.l0, wv.f0,   \
                         wv.nf, g.twH);                                                                        \

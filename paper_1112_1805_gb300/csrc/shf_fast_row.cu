@@ -981,15 +981,32 @@ cudaError_t prepare_row_kernels() {
   return e;
 }
 
-int row_ctas_per_sm(int L, int mode) {
+// The forward v-step a plan's variant selects at half width L (the default:
+// pairs of rows at 64 and 128, radix-16 rows at the other powers of two up to
+// 1024, 8 values per thread elsewhere).
+int row_variant(int L, int mode, int variant) {
+  if (mode == 1) return use_r16(L) ? kRow16 : kRow8;
+  if (variant == kRowDefault) return use_pair(L) ? kRowPair : (use_r16(L) ? kRow16 : kRow8);
+  if (variant == kRowPair && !use_pair(L)) return kRow8;
+  if (variant == kRow16 && !use_r16(L)) return kRow8;
+  return variant;
+}
+
+bool row_kernel_ok(int L, int variant) {
+  return variant == kRowDefault || variant == kRow8 || (variant == kRow16 && use_r16(L)) ||
+         (variant == kRowPair && use_pair(L));
+}
+
+int row_ctas_per_sm(int L, int mode, int variant) {
   int fit = 0;
   cudaError_t e = cudaErrorInvalidValue;
+  const int v = row_variant(L, mode, variant);
   switch (L) {
 #define SHF_OCC(N)                                                                                              \
   case N:                                                                                                       \
-    if (mode == 0 && use_pair(N))                                                                               \
+    if (v == kRowPair)                                                                                          \
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_vstep2r<pair_len(N)>, 256, pair_smem<N>());  \
-    else if (use_r16(N))                                                                                        \
+    else if (v == kRow16)                                                                                       \
       e = mode == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_vstep16<r16_len(N), 0>, 256,   \
                                                                     vstep16_smem<N, 0>())                       \
                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_vstep16<r16_len(N), 1>, 256,   \
@@ -1007,13 +1024,13 @@ int row_ctas_per_sm(int L, int mode) {
   return e == cudaSuccess ? fit : 0;
 }
 
-int row_groups_per_cta(int L, int mode) {
+int row_groups_per_cta(int L, int mode, int variant) {
+  const int v = row_variant(L, mode, variant);
   switch (L) {
 #define SHF_CASE(N)                                        \
   case N:                                                  \
-    if (mode == 0 && use_pair(N))                          \
-      return 2 * PairGeo<pair_len(N)>::RPC; /* rows */     \
-    return use_r16(N) ? Row16Geo<r16_len(N)>::RPC : RowGeo<N>::RPC;
+    if (v == kRowPair) return 2 * PairGeo<pair_len(N)>::RPC; /* rows */ \
+    return v == kRow16 ? Row16Geo<r16_len(N)>::RPC : RowGeo<N>::RPC;
     SHF_FAST_SIZES(SHF_CASE)
 #undef SHF_CASE
     default: return 0;
@@ -1021,14 +1038,15 @@ int row_groups_per_cta(int L, int mode) {
 }
 
 cudaError_t row_shrink(const Geo& g, int ctas, float2* Y, float* bv, const float* thr, int Whp, const Wave& wv,
-                       float scale, signed char* code, cudaStream_t st) {
+                       float scale, signed char* code, int variant, cudaStream_t st) {
+  const int v = row_variant(g.L, 0, variant);
   switch (g.L) {
 #define SHF_CASE(N)                                                                                                \
   case N:                                                                                                          \
-    if (use_pair(N))                                                                                               \
+    if (v == kRowPair)                                                                                             \
       return launch_pdl(k_wrow_vstep2r<pair_len(N)>, dim3(ctas), dim3(256), pair_smem<N>(), st, Y, bv, thr,      \
                         g.ranges, g.H, Whp, g.eta, wv.l0, wv.f0, wv.nf, wv.nv, scale, g.twW, code);              \
-    if (use_r16(N))                                                                                                \
+    if (v == kRow16)                                                                                               \
       return launch_pdl(k_wrow_vstep16<r16_len(N), 0>, dim3(ctas), dim3(256), vstep16_smem<N, 0>(), st, Y, bv,    \
                         thr, g.ranges, g.H, Whp, g.eta, wv.l0, wv.f0, wv.nf, wv.nv, scale, g.twW, code,            \
                         static_cast<double*>(nullptr));                                                            \

@@ -133,9 +133,14 @@ struct WorkItem {
   int label;
 };
 constexpr int kDefaultWaveMiB = 128;  // coefficient spectra per wave
+// FFT kernel variants of a plan (0: the default for the size).
+enum RowKernel { kRowDefault = 0, kRow8 = 1, kRow16 = 2, kRowPair = 3 };
+enum ColKernel { kColDefault = 0, kCol8 = 1, kCol16 = 2 };
 struct FastPlan {
   int wave_mib = kDefaultWaveMiB;
   int col_ctas_per_sm = 0;  // CTAs per SM of the column launches (0: as many as fit)
+  int row_kernel = kRowDefault;  // forward v-step transform (RowKernel)
+  int col_kernel = kColDefault;  // fan and gather transforms (ColKernel)
   int col_ctas = 0;         // resolved: CTAs of one gather launch
   int fan_ctas = 0;         // resolved: CTAs of one fan launch (all resident)
   int row_ctas = 0;         // resolved: resident CTAs of the row (v-step) launch
@@ -179,10 +184,12 @@ cudaError_t run_fast_adjoint_body(const Geo& g, const FastPlan& plan, const floa
                                   const signed char* code, double* tpart, cudaStream_t st);
 // Resident CTAs of one gather launch for `per_sm` CTAs per SM (0: as many
 // as fit; larger values are clamped to that), and of one fan launch.
-int fast_col_ctas(const Geo& g, int per_sm);
-int fast_fan_ctas(const Geo& g);
+int fast_col_ctas(const Geo& g, int per_sm, int col_kernel = kColDefault);
+int fast_fan_ctas(const Geo& g, int col_kernel = kColDefault);
+bool fast_row_kernel_ok(const Geo& g, int row_kernel);
+bool fast_col_kernel_ok(const Geo& g, int col_kernel);
 // Resident CTAs of the row (v-step) kernel.
-int fast_row_ctas(const Geo& g);
+int fast_row_ctas(const Geo& g, int row_kernel = kRowDefault);
 // Host construction of the work list of K labels from the filters' column
 // ranges (ranges_host[eta]) for plan->wave_mib and plan->col_ctas; returns the
 // host arrays to upload (cta_begin holds one entry more per wave).

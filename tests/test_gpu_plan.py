@@ -188,3 +188,37 @@ def test_batch_tune(torch_mod, oracle_mod):
         o = _oracle(oracle_mod, p[0], p[1], 2, p[2], 10)
         assert np.abs(u - o["u"]).max() <= U_TOL
     batch.close()
+
+
+@pytest.mark.parametrize("H,W,K,J,T", [(512, 128, 3, 2, 6),   # v-step: 8 values, 16 values, pairs (L = 64); columns 8 / 16
+                                      (512, 256, 2, 3, 5),   # L = 128: all three row kernels; H = 512: both columns
+                                      (1024, 512, 2, 2, 4),  # L = 256: 8 / 16 values; H = 1024: both columns
+                                      (96, 384, 3, 2, 12)])  # L = 192 (8 values only), H = 96 (8 values only)
+def test_every_fft_kernel_variant_meets_the_bars(torch_mod, oracle_mod, H, W, K, J, T):
+    # the plan's FFT kernels (row_kernel: 1 eight values per thread, 2 sixteen,
+    # 3 pairs of rows; col_kernel: 1 eight, 2 sixteen) change only the order of
+    # the FFT arithmetic: each one meets the oracle bars, and the sizes without
+    # a variant refuse it
+    from paper_1112_1805_gb300 import binding as B
+
+    img, cb, Lam = _problem(H, W, K, J, H + 3 * W)
+    o = _oracle(oracle_mod, img, cb, J, Lam, T)
+    L = W // 2
+    rows = [1] + ([2] if L in (64, 128, 256, 512, 1024) else []) + ([3] if L in (64, 128) else [])
+    cols = [1] + ([2] if H in (512, 1024, 2048) else [])
+    seen = set()
+    for rk in rows:
+        for ck in cols:
+            g = _run(torch_mod, img, cb, J, Lam, T, plan={"wave_mib": 64, "col_ctas_per_sm": 0, "row_kernel": rk,
+                                                          "col_kernel": ck})
+            assert (g["plan"]["row_kernel"], g["plan"]["col_kernel"]) == (rk, ck)
+            _check(o, g)
+            seen.add((rk, ck))
+    assert len(seen) == len(rows) * len(cols)
+    for bad in ({"row_kernel": 3} if 3 not in rows else {}, {"col_kernel": 2} if 2 not in cols else {},
+                {"row_kernel": 7}, {"col_kernel": -1}):
+        if not bad:
+            continue
+        with pytest.raises(B.ShearsegError) as e:
+            _run(torch_mod, img, cb, J, Lam, 1, plan=dict({"wave_mib": 64, "col_ctas_per_sm": 0}, **bad))
+        assert e.value.code == B.SHF_ERR_ARG

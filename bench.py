@@ -83,6 +83,9 @@ def parse_args():
                     help="skip the 2048 x 2048 RGB and 64 x 64 legs that the default line carries under 'workloads'")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default work plan instead of autotuning it before the timed region")
+    ap.add_argument("--plan", default="",
+                    help="fixed work plan fields for profiling runs, e.g. 'wave_mib=256,row_kernel=2' (implies "
+                         "--no-tune for the main workload)")
     ap.add_argument("--iters", type=int, default=0,
                     help="ADMM iterations per step for short profiling runs (default: the workload's 500)")
     return ap.parse_args()
@@ -331,7 +334,15 @@ def run_ours(args):
     fb = FilterBank(wl.H, wl.W, wl.J)
     seg = ShearletSegmenter(fb, f_dev, wl.codebook(), wl.Lambda(), wl.gamma)
     # work plan: autotuned on this image before the timed region (iterate restored)
-    plan = seg.plan() if args.no_tune else seg.tune(10)
+    if args.plan:
+        fixed = seg.plan()
+        for kv in args.plan.split(","):
+            k, v = kv.split("=")
+            fixed[k.strip()] = int(v)
+        seg.set_plan(fixed)
+        plan = seg.plan()
+    else:
+        plan = seg.plan() if args.no_tune else seg.tune(10)
     labels_dev = torch.empty((wl.H, wl.W), dtype=torch.int32, device="cuda")
     st = seg.stream
     units_per_step = wl.H * wl.W * wl.K * wl.iters

@@ -229,8 +229,7 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 
       const float2 a = (n >= c0 && n <= c1) ? sX[n - c0] : make_float2(0.f, 0.f);
       const float2 c = (m >= c0 && m <= c1) ? c_conj(sX[m - c0]) : make_float2(0.f, 0.f);
       const float2 s2 = c_add(a, c), d = c_sub(a, c);
-      const float2 t = c_mul(c_conj(tw[n]), d);
-      v[k] = make_float2(s2.x - t.y, s2.y + t.x);
+      v[k] = pack_combine(s2, d, tw[n]);
     }
     reg::group_sync<T>(bar);  // the spectrum stage is read: refill it with the group's next row
     request_x(fln, rown);
@@ -244,13 +243,12 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 
       if (MODE == 0) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-          const float2 bo = sB[tt + k * T];
-          const float gx = fmaf(scale, v[k].x, bo.x), gy = fmaf(scale, v[k].y, bo.y);
-          const float cx = fminf(fmaxf(gx, -th), th), cy = fminf(fmaxf(gy, -th), th);
-          if (act) __stcs(b2 + tt + k * T, make_float2(cx, cy));
+          const float2 g = c_fma2(make_float2(scale, scale), v[k], sB[tt + k * T]);
+          const float2 c = make_float2(fminf(fmaxf(g.x, -th), th), fminf(fmaxf(g.y, -th), th));
+          if (act) __stcs(b2 + tt + k * T, c);
           if (code && act)
-            reinterpret_cast<char2*>(code + rix * W)[tt + k * T] = make_char2(clip_code(gx, th), clip_code(gy, th));
-          v[k] = make_float2(gx - 2.f * cx, gy - 2.f * cy);
+            reinterpret_cast<char2*>(code + rix * W)[tt + k * T] = make_char2(clip_code(g.x, th), clip_code(g.y, th));
+          v[k] = c_fma2(make_float2(-2.f, -2.f), c, g);  // g - 2 clip(g)
         }
       } else {
         float tacc = 0.f;
@@ -304,8 +302,7 @@ __global__ void __launch_bounds__(RowGeo<L>::NTH, (reg::odd_part(L) == 1 ? 1024 
           const float2 a = ub[ia];
           const float2 c = c_conj(ub[ic]);
           const float2 s2 = c_add(a, c), d = c_sub(a, c);
-          const float2 t = c_mul(tw[i], d);
-          X[i] = make_float2(0.5f * (s2.x + t.y), 0.5f * (s2.y - t.x));
+          X[i] = unpack_combine(s2, d, tw[i]);
         }
       }
     }
@@ -469,8 +466,7 @@ __global__ void __launch_bounds__(256, 2)
         const float2 a = (n >= c0 && n <= c1) ? __ldca(X + n) : make_float2(0.f, 0.f);
         const float2 c = (m >= c0 && m <= c1) ? c_conj(__ldca(X + m)) : make_float2(0.f, 0.f);
         const float2 s2 = c_add(a, c), d = c_sub(a, c);
-        const float2 t = c_mul(c_conj(tw[n]), d);
-        v[k] = make_float2(s2.x - t.y, s2.y + t.x);
+        v[k] = pack_combine(s2, d, tw[n]);
       }
     }
     r16::row_fft<L, +1>(v, tt, fb, pt, bar);
@@ -481,13 +477,12 @@ __global__ void __launch_bounds__(256, 2)
       if constexpr (MODE == 0) {
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-          const float2 bo = sB[tt + k * T];
-          const float gx = fmaf(scale, v[k].x, bo.x), gy = fmaf(scale, v[k].y, bo.y);
-          const float cx = fminf(fmaxf(gx, -th), th), cy = fminf(fmaxf(gy, -th), th);
-          __stcs(b2 + tt + k * T, make_float2(cx, cy));
+          const float2 g = c_fma2(make_float2(scale, scale), v[k], sB[tt + k * T]);
+          const float2 c = make_float2(fminf(fmaxf(g.x, -th), th), fminf(fmaxf(g.y, -th), th));
+          __stcs(b2 + tt + k * T, c);
           if (code)
-            reinterpret_cast<char2*>(code + rix * W)[tt + k * T] = make_char2(clip_code(gx, th), clip_code(gy, th));
-          v[k] = make_float2(gx - 2.f * cx, gy - 2.f * cy);
+            reinterpret_cast<char2*>(code + rix * W)[tt + k * T] = make_char2(clip_code(g.x, th), clip_code(g.y, th));
+          v[k] = c_fma2(make_float2(-2.f, -2.f), c, g);  // g - 2 clip(g)
         }
       } else {
         float tacc = 0.f;
@@ -657,15 +652,15 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         const int m = tt + k * T;
-        const float ga = fmaf(scale, v[k].x, sB[m]), gb = fmaf(scale, v[k].y, sB[W + m]);
-        const float ca = fminf(fmaxf(ga, -th), th), cb = fminf(fmaxf(gb, -th), th);
-        __stcs(b2 + m, ca);
-        __stcs(b2 + W + m, cb);
+        const float2 g = c_fma2(make_float2(scale, scale), v[k], make_float2(sB[m], sB[W + m]));  // rows a, b
+        const float2 c = make_float2(fminf(fmaxf(g.x, -th), th), fminf(fmaxf(g.y, -th), th));
+        __stcs(b2 + m, c.x);
+        __stcs(b2 + W + m, c.y);
         if (code) {
-          code[rix * W + m] = clip_code(ga, th);
-          code[(rix + 1) * W + m] = clip_code(gb, th);
+          code[rix * W + m] = clip_code(g.x, th);
+          code[(rix + 1) * W + m] = clip_code(g.y, th);
         }
-        v[k] = make_float2(ga - 2.f * ca, gb - 2.f * cb);
+        v[k] = c_fma2(make_float2(-2.f, -2.f), c, g);  // g - 2 clip(g)
       }
     } else {
 #pragma unroll

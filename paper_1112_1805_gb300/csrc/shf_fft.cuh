@@ -48,6 +48,42 @@ __host__ __device__ __forceinline__ float2 c_sub(float2 a, float2 b) {
 __host__ __device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
+// Component-wise a * b and a * b + c: packed FP32x2 multiply and fused
+// multiply-add on the device (per component the same IEEE operation as the
+// scalar one).
+__host__ __device__ __forceinline__ float2 c_mul2(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+#else
+  return make_float2(a.x * b.x, a.y * b.y);
+#endif
+}
+__host__ __device__ __forceinline__ float2 c_fma2(float2 a, float2 b, float2 c) {
+#ifdef __CUDA_ARCH__
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+#else
+  return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+#endif
+}
+// The last step of the real-row packing, s + i conj(w) d with w = e^{-2 pi i k/W}
+// (i conj w = (w.y, w.x): one complex product and one packed add).
+__host__ __device__ __forceinline__ float2 pack_combine(float2 s, float2 d, float2 w) {
+  return c_add(s, c_mul(make_float2(w.y, w.x), d));
+}
+// The last step of the real-row unpacking, (s - i w d) / 2 (-i w = (w.y, -w.x)).
+__host__ __device__ __forceinline__ float2 unpack_combine(float2 s, float2 d, float2 w) {
+  return c_mul2(c_add(s, c_mul(make_float2(w.y, -w.x), d)), make_float2(0.5f, 0.5f));
+}
 __host__ __device__ __forceinline__ float2 c_conj(float2 a) { return make_float2(a.x, -a.y); }
 __host__ __device__ __forceinline__ float2 c_scale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 // a * (S i) for S = +1 or -1
@@ -230,8 +266,7 @@ __host__ __device__ __forceinline__ float2 c2r_pack(const float2* X, int L, int 
   const float2 a = X[k];
   const float2 b = c_conj(X[L - k]);
   const float2 s = c_add(a, b), d = c_sub(a, b);
-  const float2 t = c_mul(c_conj(twW[k]), d);
-  return make_float2(s.x - t.y, s.y + t.x);
+  return pack_combine(s, d, twW[k]);
 }
 
 // Forward unpacking: Z = DFT_L(x[2n] + i x[2n+1]); returns X[k], k = 0..L,
@@ -240,8 +275,7 @@ __host__ __device__ __forceinline__ float2 r2c_unpack(const float2* Z, int L, in
   const float2 a = Z[k == L ? 0 : k];
   const float2 b = c_conj(Z[k == 0 ? 0 : L - k]);
   const float2 s = c_add(a, b), d = c_sub(a, b);
-  const float2 t = c_mul(twW[k], d);
-  return make_float2(0.5f * (s.x + t.y), 0.5f * (s.y - t.x));
+  return unpack_combine(s, d, twW[k]);
 }
 
 // Radix sequence for L = 2^a 3^b 5^c (8s first, then a 4 or 2, then 3s and

@@ -210,14 +210,12 @@ __host__ __device__ __forceinline__ void pack_step(float2 (&v)[16], int k, int t
   {
     const float2 c = c_conj(ra);
     const float2 s2 = c_add(a1, c), d = c_sub(a1, c);
-    const float2 t = c_mul(c_conj(tw[tt + k * T]), d);
-    v[k] = make_float2(s2.x - t.y, s2.y + t.x);
+    v[k] = pack_combine(s2, d, tw[tt + k * T]);
   }
   {
     const float2 c = c_conj(rb);
     const float2 s2 = c_add(a2, c), d = c_sub(a2, c);
-    const float2 t = c_mul(c_conj(tw[tt + k2 * T]), d);
-    v[k2] = make_float2(s2.x - t.y, s2.y + t.x);
+    v[k2] = pack_combine(s2, d, tw[tt + k2 * T]);
   }
 }
 
@@ -232,8 +230,7 @@ __host__ __device__ __forceinline__ float2 unpack_value(const float2 (&v)[16], i
   const float2 zb = tt == 0 ? v[(16 - q) & 15] : r;
   const float2 c = c_conj(zb);
   const float2 s2 = c_add(v[q], c), d = c_sub(v[q], c);
-  const float2 t = c_mul(tw[tt + q * T], d);
-  return make_float2(0.5f * (s2.x + t.y), 0.5f * (s2.y - t.x));
+  return unpack_combine(s2, d, tw[tt + q * T]);
 }
 
 // Two real rows a, b of length W as one complex row z = a + i b, transformed
@@ -249,7 +246,7 @@ __host__ __device__ __forceinline__ float2 pair_pack(float2 xa, float2 xb, bool 
 __host__ __device__ __forceinline__ void pair_unpack(float2 dk, float2 dm, float2& xa, float2& xb) {
   const float2 c = c_conj(dm);
   const float2 s2 = c_add(dk, c), t = c_sub(dk, c);
-  xa = make_float2(0.5f * s2.x, 0.5f * s2.y);
+  xa = c_mul2(s2, make_float2(0.5f, 0.5f));
   xb = make_float2(0.5f * t.y, -0.5f * t.x);
 }
 

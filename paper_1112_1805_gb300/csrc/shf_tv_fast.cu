@@ -176,8 +176,7 @@ __global__ void __launch_bounds__(256, 2)
         const float2 a = __ldcg(X + n);
         const float2 c = c_conj(__ldcg(X + m));
         const float2 s2 = c_add(a, c), dd = c_sub(a, c);
-        const float2 t = c_mul(c_conj(tw[n]), dd);
-        v[j] = make_float2(s2.x - t.y, s2.y + t.x);
+        v[j] = pack_combine(s2, dd, tw[n]);
       }
     }
     r16::row_fft<L, +1>(v, tt, fb, pt, bar);

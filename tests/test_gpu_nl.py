@@ -157,3 +157,33 @@ def test_nl_argument_errors():
     with pytest.raises(B.ShearsegError) as e:
         NLSegmenter(bad, cb, 0.1, 0.2)
     assert e.value.code == B.SHF_ERR_NONFINITE
+
+
+def test_nl_textured_512_graph_and_first_iterations(oracle_mod):
+    # the 512 x 512 textured image of the NL-means benchmark leg (K = 4, the
+    # paper's p = 5, varpi = 15, a = 2, mt = 5, gamma = 1/5, lambda = 1/32): the
+    # graph equal to the oracle's at full size, and five iterations at the bars
+    torch = need_cuda()
+    from paper_1112_1805_gb300 import binding as B
+    from paper_1112_1805_gb300.api import NLSegmenter
+
+    img, _, wl = synth.make_workload_image("bezier512")
+    img = img.astype(np.float32)
+    cb = wl.codebook()
+    lam32, g32 = float(np.float32(1 / 32)), float(np.float32(0.2))
+    T = 5
+    seg = NLSegmenter(torch.tensor(img, device="cuda"), cb, lam32, g32)
+    nbr, deg, _ = seg.graph()
+    seg.step(T)
+    seg.synchronize()
+    got = {k: seg.get(getattr(B, "SEG_" + k.upper())).cpu().numpy() for k in ("u", "w", "bw", "bv", "labels")}
+    energy = seg.energy()
+    seg.close()
+    onbr, odeg = oracle_mod.nl_graph(img.astype(np.float64))
+    assert np.array_equal(deg, odeg)
+    assert np.array_equal(nbr, onbr)
+    o = oracle_mod.nl_admm_run(img.astype(np.float64), _r32(cb), lam32, g32, T)
+    for k in ("u", "w", "bw", "bv"):
+        assert np.abs(got[k] - o[k]).max() <= U_TOL, k
+    assert abs(energy - o["energy"]) / abs(o["energy"]) <= E_TOL
+    assert labels_agree(got["labels"], o["labels"], o["gap"])

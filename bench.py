@@ -223,15 +223,18 @@ def source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel: str):
+def measured_traffic(kernel: str, plan=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources; else None."""
+    the current kernel sources and with the same wave size (a launch's work
+    depends on it); else None."""
     try:
         with open(TRAFFIC_FILE) as fp:
             t = json.load(fp)
     except (OSError, ValueError):
         return None
     if t.get("source_sha") != source_sha():
+        return None
+    if plan is not None and "wave_mib" in t and plan.get("wave_mib") != t["wave_mib"]:
         return None
     k = t.get("kernels", {}).get(kernel)
     return None if k is None else float(k["dram_bytes_per_launch"])
@@ -413,12 +416,17 @@ def run_ours(args):
         peak, peak_kind = peaks()
         achieved = kb[dom] / (mean_ms[dom] / 1000.0) / 1e9
         it_ms = sum(mean_ms.values())
+        traffic = measured_traffic(dom, plan)
         roofline = {
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": measured_traffic(dom), "kernel": dom, "launches_per_iteration": n_launch[dom],
+            "traffic": traffic, "kernel": dom, "launches_per_iteration": n_launch[dom],
             "kernel_ms_per_launch": mean_ms[dom] / n_launch[dom],
             "algorithmic_bytes_per_launch": kb[dom] / n_launch[dom], "peak_source": f"{peak_kind} hbm_gbs",
         }
+        if traffic is not None:
+            # the same launch in DRAM bytes (ncu) over its live CUDA-event time
+            roofline["traffic_gbs"] = traffic / (mean_ms[dom] / n_launch[dom] / 1000.0) / 1e9
+            roofline["traffic_frac"] = roofline["traffic_gbs"] / peak
         # whole iteration: the method's bytes and flops over the plain graph's
         # time per iteration (the step's time over its iterations: it also
         # holds the reset and the readout, so this slightly understates)

@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "shearseg.h"
+#include "shf_fast.h"
 #include "shf_internal.h"
 #include "shf_simplex.cuh"
 
@@ -150,6 +151,8 @@ __global__ void __launch_bounds__(kThreads) k_nl_cheb(const float* __restrict__ 
                                                       const short* __restrict__ off,
                                                       const unsigned char* __restrict__ deg, int K, int Q, int m,
                                                       size_t P, float a, float c) {
+  shf::fast::pdl_wait();  // x and d come from the previous step
+  shf::fast::pdl_trigger();
   for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < P;
        i += static_cast<size_t>(gridDim.x) * blockDim.x) {
     const int dg = deg[i];
@@ -206,6 +209,8 @@ __global__ void __launch_bounds__(kThreads) k_nl_prox(const float* __restrict__ 
                                                       float* __restrict__ q, const int* __restrict__ nbr,
                                                       const unsigned char* __restrict__ deg, int K, int m, size_t P,
                                                       float t, float gamma) {
+  shf::fast::pdl_wait();  // u comes from the last Chebyshev step
+  shf::fast::pdl_trigger();
   for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < P;
        i += static_cast<size_t>(gridDim.x) * blockDim.x) {
     int nb[kMaxM];
@@ -268,6 +273,8 @@ __global__ void __launch_bounds__(kThreads) k_nl_rhs(const float* __restrict__ q
                                                      const unsigned char* __restrict__ rev,
                                                      const unsigned char* __restrict__ deg, int K, int Q, int m,
                                                      size_t P) {
+  shf::fast::pdl_wait();  // q and d come from the prox kernel
+  shf::fast::pdl_trigger();
   for (size_t j = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; j < P;
        j += static_cast<size_t>(gridDim.x) * blockDim.x) {
     int nb[kMaxM];
@@ -510,21 +517,20 @@ cudaError_t launch_prox(nl_state* st) {
   const float t = st->gamma * st->lambda;
   const int grid = grid_for(P);
   if (st->K <= 4)
-    k_nl_prox<4><<<grid, kThreads, 0, st->stream>>>(st->u, st->bv, st->d, st->w, st->bw, st->s, st->q, st->nbr,
-                                                     st->deg, st->K, st->m, P, t, st->gamma);
+    return shf::fast::launch_pdl(k_nl_prox<4>, dim3(grid), dim3(kThreads), 0, st->stream, st->u, st->bv, st->d, st->w,
+                                 st->bw, st->s, st->q, st->nbr, st->deg, st->K, st->m, P, t, st->gamma);
   else if (st->K <= 8)
-    k_nl_prox<8><<<grid, kThreads, 0, st->stream>>>(st->u, st->bv, st->d, st->w, st->bw, st->s, st->q, st->nbr,
-                                                     st->deg, st->K, st->m, P, t, st->gamma);
+    return shf::fast::launch_pdl(k_nl_prox<8>, dim3(grid), dim3(kThreads), 0, st->stream, st->u, st->bv, st->d, st->w,
+                                 st->bw, st->s, st->q, st->nbr, st->deg, st->K, st->m, P, t, st->gamma);
   else
-    k_nl_prox<16><<<grid, kThreads, 0, st->stream>>>(st->u, st->bv, st->d, st->w, st->bw, st->s, st->q, st->nbr,
-                                                      st->deg, st->K, st->m, P, t, st->gamma);
-  return cudaGetLastError();
+    return shf::fast::launch_pdl(k_nl_prox<16>, dim3(grid), dim3(kThreads), 0, st->stream, st->u, st->bv, st->d, st->w,
+                                 st->bw, st->s, st->q, st->nbr, st->deg, st->K, st->m, P, t, st->gamma);
 }
 
 cudaError_t launch_rhs(nl_state* st) {
-  k_nl_rhs<<<grid_for(st->P()), kThreads, 0, st->stream>>>(st->q, st->d, reinterpret_cast<float*>(st->rhs), st->nbr,
-                                                           st->rev, st->deg, st->K, st->Q, st->m, st->P());
-  return cudaGetLastError();
+  return shf::fast::launch_pdl(k_nl_rhs, dim3(grid_for(st->P())), dim3(kThreads), 0, st->stream, st->q, st->d,
+                               reinterpret_cast<float*>(st->rhs), st->nbr, st->rev, st->deg, st->K, st->Q, st->m,
+                               st->P());
 }
 
 // One iteration; ev (nullable, kNlKinds + 1 events) recorded before each
@@ -539,18 +545,22 @@ cudaError_t enqueue_nl_iteration(nl_state* st, cudaEvent_t* ev) {
   float4* x1 = st->xb;
   for (int k = 0; k < n && e == cudaSuccess; ++k) {
     const float a = st->cheb_a[k], c = st->cheb_c[k];
+    const dim3 grid(grid_for(P)), block(kThreads);
+    const float* none = nullptr;
+    float* none_out = nullptr;
+    const float4* none4 = nullptr;
+    float4* none4_out = nullptr;
     if (k == 0)  // from u (label-major)
-      k_nl_cheb<true, false><<<grid_for(P), kThreads, 0, ss>>>(st->u, nullptr, nullptr, x0, st->cd, st->rhs, st->off,
-                                                                st->deg, st->K, st->Q, st->m, P, a, c);
+      e = shf::fast::launch_pdl(k_nl_cheb<true, false>, grid, block, 0, ss, st->u, none4, none_out, x0, st->cd,
+                                st->rhs, st->off, st->deg, st->K, st->Q, st->m, P, a, c);
     else if (k == n - 1)  // back into u
-      k_nl_cheb<false, true><<<grid_for(P), kThreads, 0, ss>>>(nullptr, x0, st->u, nullptr, st->cd, st->rhs, st->off,
-                                                                st->deg, st->K, st->Q, st->m, P, a, c);
+      e = shf::fast::launch_pdl(k_nl_cheb<false, true>, grid, block, 0, ss, none, x0, st->u, none4_out, st->cd,
+                                st->rhs, st->off, st->deg, st->K, st->Q, st->m, P, a, c);
     else {
-      k_nl_cheb<false, false><<<grid_for(P), kThreads, 0, ss>>>(nullptr, x0, nullptr, x1, st->cd, st->rhs, st->off,
-                                                                 st->deg, st->K, st->Q, st->m, P, a, c);
+      e = shf::fast::launch_pdl(k_nl_cheb<false, false>, grid, block, 0, ss, none, x0, none_out, x1, st->cd,
+                                st->rhs, st->off, st->deg, st->K, st->Q, st->m, P, a, c);
       std::swap(x0, x1);
     }
-    e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = mark(kNlProx);
   if (e == cudaSuccess) e = launch_prox(st);

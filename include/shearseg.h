@@ -46,7 +46,7 @@ extern "C" {
 #define SHF_ERR_OOM (-3)       /* device allocation failed                     */
 #define SHF_ERR_CUDA (-4)      /* CUDA runtime or launch error                 */
 #define SHF_ERR_NONFINITE (-5) /* NaN/Inf in an input image or codebook        */
-#define SHF_ERR_TIMEOUT (-6)   /* reserved: a bounded device wait gave up      */
+#define SHF_ERR_TIMEOUT (-6)   /* a bounded device wait gave up (nl_admm_sync) */
 #define SHF_ERR_STATE (-7)     /* handle used inconsistently (sizes, J, K)     */
 #define SHF_ERR_IO (-8)        /* checkpoint file could not be read/written    */
 
@@ -458,7 +458,12 @@ int nl_admm_reset(nl_state* st, const float* f, int f_on_host);
  * [H W], solve_steps (Chebyshev iterations per u-step); any may be NULL. */
 int nl_admm_graph(const nl_state* st, int* nbr, int* deg, int* solve_steps);
 
-/* Enqueues n_iters iterations (replays of a CUDA graph of one iteration). */
+/* Enqueues n_iters iterations (replays of a CUDA graph of one iteration).
+ * For K <= 4 and images whose pixels fit one resident grid at two pixels per
+ * thread, the u-step's Chebyshev steps run in one cooperative launch with a
+ * grid barrier between steps; every barrier wait gives up after one second,
+ * which nl_admm_sync then reports as SHF_ERR_TIMEOUT (a barrier cannot wait
+ * that long unless the GPU is broken: all CTAs of the launch are resident). */
 int nl_admm_step(nl_state* st, int n_iters);
 
 /* Readouts as tv_admm_get, with SEG_BV and SEG_V of shape [K][m][H][W]. */
@@ -474,6 +479,8 @@ int nl_admm_set(nl_state* st, int what, const void* src, int src_on_host);
 int nl_admm_kernel_times(nl_state* st, int n, float* ms, int* nk);
 const char* nl_admm_kernel_name(int i);
 
+/* Waits for the state's stream; SHF_ERR_TIMEOUT if a grid barrier of the
+ * Chebyshev solve gave up since the last call (the iterate is then invalid). */
 int nl_admm_sync(nl_state* st);
 /* Releases the state (synchronises its stream).  NULL is accepted. */
 int nl_admm_destroy(nl_state* st);

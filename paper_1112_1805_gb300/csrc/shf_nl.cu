@@ -55,6 +55,12 @@ struct nl_state {
   int* labels = nullptr;
   int* flag = nullptr;
   double* red = nullptr;
+  // the persistent Chebyshev solve (K <= 4 and the image within one resident
+  // grid): its barrier counter and timeout flag, the steps' (a, c), its grid
+  unsigned* cbar = nullptr;
+  int* cerr = nullptr;
+  float2* cheb_ac = nullptr;
+  int cheb_grid = 0, cheb_halo = 0;
   int iter = 0;
   cudaGraphExec_t exec = nullptr;
   bool graph_tried = false;
@@ -198,6 +204,139 @@ __global__ void __launch_bounds__(kThreads) k_nl_cheb(const float* __restrict__ 
     }
   }
 }
+
+// The whole Chebyshev solve in one cooperative launch (K <= 4: one float4 per
+// pixel), for images whose pixels fit the resident grid.  CTA c owns the
+// contiguous pixels [c B, c B + B), B = kChebThreads kChebPPT; each thread
+// keeps its pixels' right-hand side, direction d and iterate in registers for
+// all the steps (the neighbour offsets, read-only, come through L1).  Per step the CTA copies the
+// iterate over its pixels and the window halo (R = r W + r pixels each side,
+// every neighbour offset is within it) from the previous step's buffer into
+// shared memory (contiguous loads through L2), gathers the neighbours from
+// there, and writes its pixels to the other buffer; a grid barrier separates
+// the steps.  The arithmetic is k_nl_cheb's, in its order.
+constexpr int kChebPPT = 2;
+constexpr int kChebThreads = 1024;
+constexpr int kChebBlock = kChebPPT * kChebThreads;         // pixels per CTA
+constexpr unsigned long long kBarrierNs = 1000000000ull;  // a barrier gives up after one second
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned load_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid barrier number gen (1, 2, ...) on a counter that was zero at launch:
+// every CTA adds one and waits until gen * gridDim.x CTAs have arrived.  The
+// wait is bounded: after kBarrierNs it sets *err and the barrier reports
+// failure (every CTA then leaves the kernel; the host reads *err).
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned gen, int* err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // release: the CTA's writes (ordered before this thread by the CTA
+    // barrier) become visible with the arrival; acquire on the way out
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+    const unsigned target = gen * gridDim.x;
+    const unsigned long long t0 = global_ns();
+    int ok = 1;
+    while (load_acquire(bar) < target) {
+      if (global_ns() - t0 > kBarrierNs) {
+        ok = 0;
+        atomicExch(err, 1);
+        break;
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(kChebThreads, 1) k_nl_cheb_all(float* __restrict__ u, float4* xa, float4* xb,
+                                                               const float4* __restrict__ rhs,
+                                                               const short* __restrict__ off,
+                                                               const unsigned char* __restrict__ deg, int K, int m,
+                                                               size_t P, int R, int nsteps,
+                                                               const float2* __restrict__ ac, unsigned* bar,
+                                                               int* err) {
+  extern __shared__ __align__(16) float4 sx[];  // the iterate on [lo, hi)
+  const size_t base = static_cast<size_t>(blockIdx.x) * kChebBlock;
+  const size_t lo = base > static_cast<size_t>(R) ? base - R : 0;
+  const size_t hi = base + kChebBlock + R < P ? base + kChebBlock + R : P;
+  int dg[kChebPPT];
+  float4 r[kChebPPT], dd[kChebPPT], xi[kChebPPT];
+#pragma unroll
+  for (int p = 0; p < kChebPPT; ++p) {
+    const size_t i = base + p * kChebThreads + threadIdx.x;
+    const bool live = i < P;
+    dg[p] = live ? min(static_cast<int>(deg[i]), m) : 0;
+    r[p] = live ? rhs[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    dd[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+    xi[p] = live ? make_float4(u[i], K > 1 ? u[P + i] : 0.f, K > 2 ? u[2 * P + i] : 0.f, K > 3 ? u[3 * P + i] : 0.f)
+                 : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (live) xa[i] = xi[p];
+  }
+  if (!grid_barrier(bar, 1, err)) return;
+  const float4* xin = xa;
+  float4* xout = xb;
+  for (int k = 0; k < nsteps; ++k) {
+    // asynchronous 16-byte copies (through L2; the buffer was written by
+    // other CTAs in the previous step), all in flight at once
+    for (size_t j = lo + threadIdx.x; j < hi; j += kChebThreads) {
+      const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(sx + (j - lo)));
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(xin + j) : "memory");
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    const float a = ac[k].x, c = ac[k].y;
+#pragma unroll
+    for (int p = 0; p < kChebPPT; ++p) {
+      const size_t i = base + p * kChebThreads + threadIdx.x;
+      if (i >= P) continue;
+      const long long il = static_cast<long long>(i - lo);
+      float4 sn = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int b = 0; b < kMaxM; ++b) {
+        if (b < dg[p]) {
+          const float4 xn = sx[il + __ldg(off + b * P + i)];
+          sn = make_float4(sn.x + xn.x, sn.y + xn.y, sn.z + xn.z, sn.w + xn.w);
+        }
+      }
+      const float fd = static_cast<float>(dg[p]);
+      const float4 x = xi[p], rh = r[p], d0 = dd[p];
+      const float4 res = make_float4(rh.x - (x.x + 2.f * (fd * x.x - sn.x)), rh.y - (x.y + 2.f * (fd * x.y - sn.y)),
+                                     rh.z - (x.z + 2.f * (fd * x.z - sn.z)), rh.w - (x.w + 2.f * (fd * x.w - sn.w)));
+      const float4 dn = f4_axpy(c, res, make_float4(a * d0.x, a * d0.y, a * d0.z, a * d0.w));
+      dd[p] = dn;
+      xi[p] = make_float4(x.x + dn.x, x.y + dn.y, x.z + dn.z, x.w + dn.w);
+      if (k + 1 < nsteps) xout[i] = xi[p];
+    }
+    if (k + 1 < nsteps) {
+      if (!grid_barrier(bar, static_cast<unsigned>(k) + 2u, err)) return;  // also orders the shared reads
+      const float4* t = xout;
+      xout = const_cast<float4*>(xin);
+      xin = t;
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < kChebPPT; ++p) {
+    const size_t i = base + p * kChebThreads + threadIdx.x;
+    if (i >= P) continue;
+    u[i] = xi[p].x;
+    if (K > 1) u[P + i] = xi[p].y;
+    if (K > 2) u[2 * P + i] = xi[p].z;
+    if (K > 3) u[3 * P + i] = xi[p].w;
+  }
+}
+
+// Shared memory of the persistent solve: the CTA's pixels and two halos.
+size_t cheb_all_smem(int R) { return sizeof(float4) * (static_cast<size_t>(kChebBlock) + 2 * static_cast<size_t>(R)); }
 
 // The v-, w- and b-updates after the u-step: g_b = b_v,b + u(nbr_b) - u(i)
 // (b < deg; b_v,b for the zero rows), group clip over the m K values,
@@ -392,7 +531,8 @@ void free_nl(nl_state* st) {
   if (st->stream) cudaStreamSynchronize(st->stream);
   if (st->exec) cudaGraphExecDestroy(st->exec);
   void* bufs[] = {st->f, st->s, st->u, st->xa, st->xb, st->cd, st->bv, st->d, st->w, st->bw, st->q, st->rhs,
-                  st->gap, st->nbr, st->off, st->rev, st->deg, st->labels, st->flag, st->red};
+                  st->gap, st->nbr, st->off, st->rev, st->deg, st->labels, st->flag, st->red,
+                  st->cbar, st->cerr, st->cheb_ac};
   for (void* b : bufs) cudaFree(b);
   if (st->own_stream && st->stream) cudaStreamDestroy(st->stream);
   delete st;
@@ -506,6 +646,33 @@ int build_graph(nl_state* st) {
       rho = rn;
     }
   }
+  // the persistent solve: the steps' (a, c) on the device, and its grid when
+  // the pixels fit the resident CTAs at kChebPPT pixels per thread
+  cudaFree(st->cheb_ac);
+  st->cheb_ac = nullptr;
+  st->cheb_grid = 0;
+  // (the neighbours of a pixel lie in its window: |offset| <= r W + r)
+  int coop = 0, sms = 0, per_sm = 0, optin = 0;
+  st->cheb_halo = r * W + r;
+  const size_t smem = cheb_all_smem(st->cheb_halo);
+  if (st->Q == 1 && cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, st->device) == cudaSuccess && coop &&
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, st->device) == cudaSuccess &&
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, st->device) == cudaSuccess &&
+      smem <= static_cast<size_t>(optin) &&
+      cudaFuncSetAttribute(k_nl_cheb_all, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) ==
+          cudaSuccess &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nl_cheb_all, kChebThreads, smem) == cudaSuccess) {
+    const size_t need = (P + kChebBlock - 1) / kChebBlock;
+    if (need >= 1 && need <= static_cast<size_t>(per_sm) * sms) {
+      std::vector<float2> ac(n);
+      for (int k = 0; k < n; ++k) ac[k] = make_float2(st->cheb_a[k], st->cheb_c[k]);
+      int rc = nl_alloc(&st->cheb_ac, static_cast<size_t>(n), "chebyshev coefficients");
+      if (rc) return rc;
+      NL_CK(cudaMemcpy(st->cheb_ac, ac.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
+      st->cheb_grid = static_cast<int>(need);
+    }
+  }
+  cudaGetLastError();
   return SHF_OK;
 }
 
@@ -543,7 +710,26 @@ cudaError_t enqueue_nl_iteration(nl_state* st, cudaEvent_t* ev) {
   const int n = static_cast<int>(st->cheb_a.size());  // even, >= 2
   float4* x0 = st->xa;
   float4* x1 = st->xb;
-  for (int k = 0; k < n && e == cudaSuccess; ++k) {
+  if (st->cheb_grid > 0 && e == cudaSuccess) {  // one cooperative launch for all the steps
+    e = cudaMemsetAsync(st->cbar, 0, sizeof(unsigned), ss);
+    if (e == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(st->cheb_grid);
+      cfg.blockDim = dim3(kChebThreads);
+      cfg.dynamicSmemBytes = cheb_all_smem(st->cheb_halo);
+      cfg.stream = ss;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      e = cudaLaunchKernelEx(&cfg, k_nl_cheb_all, st->u, x0, x1, static_cast<const float4*>(st->rhs),
+                             static_cast<const short*>(st->off), static_cast<const unsigned char*>(st->deg), st->K,
+                             st->m, P, st->cheb_halo, n, static_cast<const float2*>(st->cheb_ac), st->cbar,
+                             st->cerr);
+    }
+  }
+  for (int k = 0; k < n && e == cudaSuccess && st->cheb_grid == 0; ++k) {
     const float a = st->cheb_a[k], c = st->cheb_c[k];
     const dim3 grid(grid_for(P)), block(kThreads);
     const float* none = nullptr;
@@ -673,9 +859,14 @@ int nl_admm_init(int H, int W, const float* f, int C, const float* codebook, int
       (rc = nl_alloc(&st->nbr, P * m, "neighbours")) || (rc = nl_alloc(&st->off, P * m, "offsets")) ||
       (rc = nl_alloc(&st->rev, P * m, "reverse")) ||
       (rc = nl_alloc(&st->deg, P, "counts")) || (rc = nl_alloc(&st->labels, P, "labels")) ||
-      (rc = nl_alloc(&st->flag, 1, "flag")) || (rc = nl_alloc(&st->red, 2 * kRedBlocks + 2, "red"))) {
+      (rc = nl_alloc(&st->flag, 1, "flag")) || (rc = nl_alloc(&st->red, 2 * kRedBlocks + 2, "red")) ||
+      (rc = nl_alloc(&st->cbar, 1, "barrier")) || (rc = nl_alloc(&st->cerr, 1, "barrier flag"))) {
     free_nl(st);
     return rc;
+  }
+  if (cudaMemset(st->cerr, 0, sizeof(int)) != cudaSuccess) {
+    free_nl(st);
+    return nl_fail(SHF_ERR_CUDA, "nl_admm_init: cudaMemset");
   }
   cudaError_t e = cudaMemcpyAsync(st->f, f, sizeof(float) * P * C, cudaMemcpyDeviceToDevice, st->stream);
   if (e != cudaSuccess) {
@@ -843,6 +1034,12 @@ int nl_admm_set(nl_state* st, int what, const void* src, int on_host) {
 int nl_admm_sync(nl_state* st) {
   if (!st) return nl_fail(SHF_ERR_ARG, "nl_admm_sync: NULL state");
   NL_CK(cudaStreamSynchronize(st->stream));
+  int gave_up = 0;
+  NL_CK(cudaMemcpy(&gave_up, st->cerr, sizeof(int), cudaMemcpyDeviceToHost));
+  if (gave_up) {
+    NL_CK(cudaMemset(st->cerr, 0, sizeof(int)));
+    return nl_fail(SHF_ERR_TIMEOUT, "nl_admm_sync: a grid barrier of the Chebyshev solve gave up");
+  }
   return SHF_OK;
 }
 

@@ -482,6 +482,14 @@ const char* nl_admm_kernel_name(int i);
 /* Waits for the state's stream; SHF_ERR_TIMEOUT if a grid barrier of the
  * Chebyshev solve gave up since the last call (the iterate is then invalid). */
 int nl_admm_sync(nl_state* st);
+
+/* Self-test of the bounded wait in the Chebyshev solve's grid barrier: runs,
+ * on the state's stream, a two-CTA cooperative launch of that barrier with a
+ * target that no CTA reaches, waits, and returns what nl_admm_sync reports:
+ * SHF_ERR_TIMEOUT when the wait gave up after its one-second bound, as it
+ * should.  No fault, trap or hang; the state and its iterate are untouched
+ * and stay usable.  Synchronises. */
+int nl_admm_barrier_selftest(nl_state* st);
 /* Releases the state (synchronises its stream).  NULL is accepted. */
 int nl_admm_destroy(nl_state* st);
 

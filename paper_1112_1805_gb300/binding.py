@@ -130,6 +130,7 @@ _SIG = {
     "nl_admm_kernel_times": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_I)]),
     "nl_admm_kernel_name": (ctypes.c_char_p, [_I]),
     "nl_admm_sync": (_I, [_VP]),
+    "nl_admm_barrier_selftest": (_I, [_VP]),
     "nl_admm_destroy": (_I, [_VP]),
 }
 
@@ -465,6 +466,10 @@ def nl_admm_kernel_times(state: int, n: int) -> dict:
 
 def nl_admm_sync(state: int) -> None:
     _call("nl_admm_sync", _VP(state))
+
+
+def nl_admm_barrier_selftest(state: int) -> None:
+    _call("nl_admm_barrier_selftest", _VP(state))
 
 
 def nl_admm_destroy(state: int) -> None:

@@ -335,6 +335,10 @@ __global__ void __launch_bounds__(kChebThreads, 1) k_nl_cheb_all(float* __restri
   }
 }
 
+// The barrier with a target no CTA reaches (each arrives once, generation 2
+// needs two arrivals each): the bounded wait must give up (self-test).
+__global__ void k_barrier_unreachable(unsigned* bar, int* err) { grid_barrier(bar, 2, err); }
+
 // Shared memory of the persistent solve: the CTA's pixels and two halos.
 size_t cheb_all_smem(int R) { return sizeof(float4) * (static_cast<size_t>(kChebBlock) + 2 * static_cast<size_t>(R)); }
 
@@ -1041,6 +1045,23 @@ int nl_admm_sync(nl_state* st) {
     return nl_fail(SHF_ERR_TIMEOUT, "nl_admm_sync: a grid barrier of the Chebyshev solve gave up");
   }
   return SHF_OK;
+}
+
+int nl_admm_barrier_selftest(nl_state* st) {
+  if (!st) return nl_fail(SHF_ERR_ARG, "nl_admm_barrier_selftest: NULL state");
+  NL_CK(cudaStreamSynchronize(st->stream));
+  NL_CK(cudaMemsetAsync(st->cbar, 0, sizeof(unsigned), st->stream));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2);
+  cfg.blockDim = dim3(32);
+  cfg.stream = st->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  NL_CK(cudaLaunchKernelEx(&cfg, k_barrier_unreachable, st->cbar, st->cerr));
+  return nl_admm_sync(st);
 }
 
 int nl_admm_destroy(nl_state* st) {

@@ -187,3 +187,29 @@ def test_nl_textured_512_graph_and_first_iterations(oracle_mod):
         assert np.abs(got[k] - o[k]).max() <= U_TOL, k
     assert abs(energy - o["energy"]) / abs(o["energy"]) <= E_TOL
     assert labels_agree(got["labels"], o["labels"], o["gap"])
+
+
+def test_nl_barrier_wait_gives_up_and_state_stays_usable():
+    # the grid barrier of the Chebyshev solve waits at most one second: a
+    # barrier that cannot complete reports SHF_ERR_TIMEOUT (no fault, no
+    # hang), and the state then iterates on as before
+    torch = need_cuda()
+    from paper_1112_1805_gb300 import binding as B
+    from paper_1112_1805_gb300.api import NLSegmenter
+
+    img, cb, _ = _image(32, 48, 3, 1, 77)
+    f = torch.tensor(img, device="cuda")
+    seg = NLSegmenter(f, cb, 1 / 32, 0.2)
+    seg.step(3)
+    seg.synchronize()
+    u3 = seg.get(B.SEG_U)
+    with pytest.raises(B.ShearsegError) as e:
+        B.nl_admm_barrier_selftest(seg.handle)
+    assert e.value.code == B.SHF_ERR_TIMEOUT
+    seg.synchronize()  # the flag was cleared
+    assert torch.equal(seg.get(B.SEG_U), u3)
+    seg.reset(f)
+    seg.step(3)
+    seg.synchronize()
+    assert torch.equal(seg.get(B.SEG_U), u3)
+    seg.close()

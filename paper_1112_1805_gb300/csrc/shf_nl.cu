@@ -209,7 +209,8 @@ __global__ void __launch_bounds__(kThreads) k_nl_cheb(const float* __restrict__ 
 // pixel), for images whose pixels fit the resident grid.  CTA c owns the
 // contiguous pixels [c B, c B + B), B = kChebThreads kChebPPT; each thread
 // keeps its pixels' right-hand side, direction d and iterate in registers for
-// all the steps (the neighbour offsets, read-only, come through L1).  Per step the CTA copies the
+// all the steps, and the CTA keeps its pixels' neighbour offsets (at most MM
+// per pixel) in shared memory.  Per step the CTA copies the
 // iterate over its pixels and the window halo (R = r W + r pixels each side,
 // every neighbour offset is within it) from the previous step's buffer into
 // shared memory (contiguous loads through L2), gathers the neighbours from
@@ -258,6 +259,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned gen, int* e
   return s_ok != 0;
 }
 
+template <int MM>
 __global__ void __launch_bounds__(kChebThreads, 1) k_nl_cheb_all(float* __restrict__ u, float4* xa, float4* xb,
                                                                const float4* __restrict__ rhs,
                                                                const short* __restrict__ off,
@@ -265,10 +267,16 @@ __global__ void __launch_bounds__(kChebThreads, 1) k_nl_cheb_all(float* __restri
                                                                size_t P, int R, int nsteps,
                                                                const float2* __restrict__ ac, unsigned* bar,
                                                                int* err) {
-  extern __shared__ __align__(16) float4 sx[];  // the iterate on [lo, hi)
+  extern __shared__ __align__(16) float4 sx[];  // the iterate on [lo, hi), then the offsets
+  short* so = reinterpret_cast<short*>(sx + kChebBlock + 2 * static_cast<size_t>(R));  // [MM][kChebBlock]
   const size_t base = static_cast<size_t>(blockIdx.x) * kChebBlock;
   const size_t lo = base > static_cast<size_t>(R) ? base - R : 0;
   const size_t hi = base + kChebBlock + R < P ? base + kChebBlock + R : P;
+  for (int e = threadIdx.x; e < MM * kChebBlock; e += kChebThreads) {
+    const int b = e / kChebBlock, j = e - b * kChebBlock;
+    const size_t i = base + j;
+    so[e] = (i < P && b < m) ? off[b * P + i] : static_cast<short>(0);
+  }
   int dg[kChebPPT];
   float4 r[kChebPPT], dd[kChebPPT], xi[kChebPPT];
 #pragma unroll
@@ -286,11 +294,19 @@ __global__ void __launch_bounds__(kChebThreads, 1) k_nl_cheb_all(float* __restri
   const float4* xin = xa;
   float4* xout = xb;
   for (int k = 0; k < nsteps; ++k) {
-    // asynchronous 16-byte copies (through L2; the buffer was written by
-    // other CTAs in the previous step), all in flight at once
+    // the halos by asynchronous 16-byte copies (through L2: other CTAs wrote
+    // them in the previous step), all in flight at once; the CTA's own
+    // pixels from registers
+    const size_t own_end = base + kChebBlock < hi ? base + kChebBlock : hi;
     for (size_t j = lo + threadIdx.x; j < hi; j += kChebThreads) {
+      if (j >= base && j < own_end) continue;
       const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(sx + (j - lo)));
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(xin + j) : "memory");
+    }
+#pragma unroll
+    for (int p = 0; p < kChebPPT; ++p) {
+      const size_t i = base + p * kChebThreads + threadIdx.x;
+      if (i < P) sx[i - lo] = xi[p];
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
@@ -300,11 +316,12 @@ __global__ void __launch_bounds__(kChebThreads, 1) k_nl_cheb_all(float* __restri
       const size_t i = base + p * kChebThreads + threadIdx.x;
       if (i >= P) continue;
       const long long il = static_cast<long long>(i - lo);
+      const short* sop = so + p * kChebThreads + threadIdx.x;
       float4 sn = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-      for (int b = 0; b < kMaxM; ++b) {
+      for (int b = 0; b < MM; ++b) {
         if (b < dg[p]) {
-          const float4 xn = sx[il + __ldg(off + b * P + i)];
+          const float4 xn = sx[il + sop[b * kChebBlock]];
           sn = make_float4(sn.x + xn.x, sn.y + xn.y, sn.z + xn.z, sn.w + xn.w);
         }
       }
@@ -339,8 +356,12 @@ __global__ void __launch_bounds__(kChebThreads, 1) k_nl_cheb_all(float* __restri
 // needs two arrivals each): the bounded wait must give up (self-test).
 __global__ void k_barrier_unreachable(unsigned* bar, int* err) { grid_barrier(bar, 2, err); }
 
-// Shared memory of the persistent solve: the CTA's pixels and two halos.
-size_t cheb_all_smem(int R) { return sizeof(float4) * (static_cast<size_t>(kChebBlock) + 2 * static_cast<size_t>(R)); }
+// Shared memory of the persistent solve: the iterate on the CTA's pixels and
+// two halos, and MM neighbour offsets per pixel.
+size_t cheb_all_smem(int R, int MM) {
+  return sizeof(float4) * (static_cast<size_t>(kChebBlock) + 2 * static_cast<size_t>(R)) +
+         sizeof(short) * static_cast<size_t>(MM) * kChebBlock;
+}
 
 // The v-, w- and b-updates after the u-step: g_b = b_v,b + u(nbr_b) - u(i)
 // (b < deg; b_v,b for the zero rows), group clip over the m K values,
@@ -658,14 +679,16 @@ int build_graph(nl_state* st) {
   // (the neighbours of a pixel lie in its window: |offset| <= r W + r)
   int coop = 0, sms = 0, per_sm = 0, optin = 0;
   st->cheb_halo = r * W + r;
-  const size_t smem = cheb_all_smem(st->cheb_halo);
+  const int MM = m <= 10 ? 10 : kMaxM;
+  const size_t smem = cheb_all_smem(st->cheb_halo, MM);
+  const void* kern = MM == 10 ? reinterpret_cast<const void*>(k_nl_cheb_all<10>)
+                              : reinterpret_cast<const void*>(k_nl_cheb_all<kMaxM>);
   if (st->Q == 1 && cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, st->device) == cudaSuccess && coop &&
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, st->device) == cudaSuccess &&
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, st->device) == cudaSuccess &&
       smem <= static_cast<size_t>(optin) &&
-      cudaFuncSetAttribute(k_nl_cheb_all, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) ==
-          cudaSuccess &&
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nl_cheb_all, kChebThreads, smem) == cudaSuccess) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) == cudaSuccess &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kChebThreads, smem) == cudaSuccess) {
     const size_t need = (P + kChebBlock - 1) / kChebBlock;
     if (need >= 1 && need <= static_cast<size_t>(per_sm) * sms) {
       std::vector<float2> ac(n);
@@ -720,14 +743,15 @@ cudaError_t enqueue_nl_iteration(nl_state* st, cudaEvent_t* ev) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(st->cheb_grid);
       cfg.blockDim = dim3(kChebThreads);
-      cfg.dynamicSmemBytes = cheb_all_smem(st->cheb_halo);
+      const int MM = st->m <= 10 ? 10 : kMaxM;
+      cfg.dynamicSmemBytes = cheb_all_smem(st->cheb_halo, MM);
       cfg.stream = ss;
       cudaLaunchAttribute attr[1];
       attr[0].id = cudaLaunchAttributeCooperative;
       attr[0].val.cooperative = 1;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      e = cudaLaunchKernelEx(&cfg, k_nl_cheb_all, st->u, x0, x1, static_cast<const float4*>(st->rhs),
+      e = cudaLaunchKernelEx(&cfg, MM == 10 ? k_nl_cheb_all<10> : k_nl_cheb_all<kMaxM>, st->u, x0, x1, static_cast<const float4*>(st->rhs),
                              static_cast<const short*>(st->off), static_cast<const unsigned char*>(st->deg), st->K,
                              st->m, P, st->cheb_halo, n, static_cast<const float2*>(st->cheb_ac), st->cbar,
                              st->cerr);

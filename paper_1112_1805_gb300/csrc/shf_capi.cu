@@ -71,6 +71,7 @@ struct shf_bank {
 
 struct seg_state {
   const shf_bank* bank = nullptr;
+  seg_batch* batch = nullptr;  // the batch whose graphs replay this state, if any
   Geo g;
   int K = 0, C = 0;
   float gamma = 1.f;
@@ -454,7 +455,12 @@ void try_capture(seg_state* st) {
   if (st->exec) st->exec_timed = capture_iteration(st, true);
 }
 
+void drop_batch_graphs(seg_batch* b);
+
 void drop_graphs(seg_state* st) {
+  // a batch's graphs hold this state's buffers: they go too (a new plan
+  // reallocates them)
+  if (st->batch) drop_batch_graphs(st->batch);
   if (st->exec) cudaGraphExecDestroy(st->exec);
   if (st->exec_timed) cudaGraphExecDestroy(st->exec_timed);
   if (st->un_fwd_exec) cudaGraphExecDestroy(st->un_fwd_exec);
@@ -1494,9 +1500,19 @@ struct seg_batch {
 
 namespace {
 
+void drop_batch_graphs(seg_batch* b) {
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  b->graph_tried = false;
+}
+
 void free_batch(seg_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  for (seg_state* s : b->states)
+    if (s) s->batch = nullptr;
   for (seg_state* s : b->states)
     if (s) seg_admm_destroy(s);
   for (shf_bank* k : b->banks)
@@ -1576,6 +1592,7 @@ int seg_admm_batch_init(int n, const int* H, const int* W, const int* C, const i
       free_batch(b);
       return fail(rc, "image " + std::to_string(i) + ": " + m);
     }
+    b->states[i]->batch = b;
   }
   *out = b;
   return SHF_OK;
@@ -1638,9 +1655,7 @@ int seg_admm_batch_tune(seg_batch* b, int iters) {
     }
     if (rc) return rc;
   }
-  if (b->exec) cudaGraphExecDestroy(b->exec);
-  b->exec = nullptr;
-  b->graph_tried = false;
+  drop_batch_graphs(b);
   return SHF_OK;
 }
 

@@ -221,7 +221,7 @@ int seg_admm_set_plan(seg_state* st, const seg_plan* p);
 
 /* Autotuner: times `iters` iterations (after one warm-up; replays of the plain
  * iteration graph, without the per-kernel timing events) of each candidate
- * plan, varying one parameter at a time around the best so far (fast: wave
+ * plan twice and keeps the better time, varying one parameter at a time around the best so far (fast: wave
  * budget, then col_ctas_per_sm, then the v-step's FFT kernel, then the
  * column FFT kernel; general: groups, then tile_cols, then tile_rows), and
  * installs the fastest.  The iterate and the iteration count

@@ -210,12 +210,13 @@ __global__ void __launch_bounds__(kThreads) k_nl_cheb(const float* __restrict__ 
 // contiguous pixels [c B, c B + B), B = kChebThreads kChebPPT; each thread
 // keeps its pixels' right-hand side, direction d and iterate in registers for
 // all the steps, and the CTA keeps its pixels' neighbour offsets (at most MM
-// per pixel) in shared memory.  Per step the CTA copies the
-// iterate over its pixels and the window halo (R = r W + r pixels each side,
-// every neighbour offset is within it) from the previous step's buffer into
-// shared memory (contiguous loads through L2), gathers the neighbours from
-// there, and writes its pixels to the other buffer; a grid barrier separates
-// the steps.  The arithmetic is k_nl_cheb's, in its order.
+// per pixel) in shared memory.  Per step the CTA copies the iterate on the
+// window halo of its pixels (R = r W + r pixels on each side: every neighbour
+// offset falls inside it) from the previous step's buffer into shared memory
+// (asynchronous copies through L2), puts its own pixels there from registers,
+// gathers the neighbours there, and writes its pixels to the other buffer; a
+// grid barrier separates the steps.  The arithmetic is k_nl_cheb's, in its
+// order.
 constexpr int kChebPPT = 2;
 constexpr int kChebThreads = 1024;
 constexpr int kChebBlock = kChebPPT * kChebThreads;         // pixels per CTA

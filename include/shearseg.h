@@ -204,7 +204,9 @@ typedef struct {
   float us_per_iter; /* seg_admm_tune: measured microseconds per iteration    */
   int row_kernel;    /* fast: v-step FFT kernel, 0 default for the width, 1 8
                         values per thread, 2 16 values (half widths 64..1024,
-                        powers of two), 3 pairs of rows (half widths 64, 128)  */
+                        powers of two), 3 pairs of rows (half widths 64, 128),
+                        4 12 or 20 values (half widths 12 T or 20 T, T =
+                        2..32: 24..384 and 40..640)                           */
   int col_kernel;    /* fast: fan and gather FFT kernel, 0 default for the
                         height, 1 8 values per thread, 2 16 values (heights
                         512, 1024, 2048)                                      */

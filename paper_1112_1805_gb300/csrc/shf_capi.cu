@@ -862,8 +862,9 @@ std::vector<seg_plan> plan_candidates(const seg_state* st, const seg_plan& base,
       }
     } else if (stage == 2) {
       // the FFT kernel of the forward v-step: 8 or 16 values per thread, one
-      // row or a pair of rows per group
-      for (int rk : {shf::kRow8, shf::kRow16, shf::kRowPair}) {
+      // row or a pair of rows per group, or 12 / 20 values per thread (odd
+      // factor 3 or 5)
+      for (int rk : {shf::kRow8, shf::kRow16, shf::kRowPair, shf::kRowV}) {
         if (!shf::fast_row_kernel_ok(g, rk)) continue;
         seg_plan p = base;
         p.row_kernel = rk;

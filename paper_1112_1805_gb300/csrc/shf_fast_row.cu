@@ -5,6 +5,7 @@
 
 #include "shf_fast.h"
 #include "shf_fft16.cuh"
+#include "shf_fftv.cuh"
 #include "shf_simplex.cuh"
 
 namespace shf {
@@ -689,6 +690,163 @@ __global__ void __launch_bounds__(256, 2)
   cp_async_commit_wait_all();  // no copy outlives the kernel
 }
 
+// ---------------------------------------------------------------------------
+// v-step with V values per thread for the half widths with an odd factor
+// (L = 12 T or 20 T, T = 2..32: shf_fftv.cuh): row groups of T threads, 32/T
+// groups per warp, eight warps per CTA, every lane live; the layout, the b_v
+// stage, the L1 prefetch of the next row's spectrum columns and the
+// partner-lane packing are those of k_wrow_vstep16 for T <= 32.  Forward mode
+// (optional codes); the adjoint keeps k_wrow_vstep.
+// ---------------------------------------------------------------------------
+template <int L>
+struct RowVGeo {
+  static constexpr int V = rv::vals_for(L);
+  static constexpr int T = L / V;
+  static constexpr int GPW = 32 / T;                           // groups per warp
+  static constexpr int NTH = 256;
+  static constexpr int RPC = 8 * GPW;                          // groups per CTA
+  static constexpr int BUF = even2(rv::row_buf(L));            // exchange buffer
+  static constexpr int RAW = BUF + L;                          // + the b_v stage (L float2)
+  static constexpr int STRIDE = T >= 16 ? RAW : RAW + ((T - RAW % 16) % 16 + 16) % 16;
+  static constexpr int TW = even2(L + 1);                      // exp(-2 pi i m / W), m <= L
+  static constexpr int PT = even2(rv::Passes<L>::TWSIZE);      // per-pass twiddles
+  static constexpr int TOTAL = TW + PT + RPC * STRIDE;         // float2 per CTA
+};
+
+template <int L>
+__global__ void __launch_bounds__(256, 2)
+    k_wrow_vstepv(float2* __restrict__ Y, float* __restrict__ bv, const float* __restrict__ thr,
+                  const int2* __restrict__ ranges, int H, int Whp, int eta, int l0, int f0, int nf, int nv,
+                  float scale, const float2* __restrict__ twW, signed char* __restrict__ code) {
+  using G = RowVGeo<L>;
+  constexpr int T = G::T, V = G::V, RPC = G::RPC;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* tw = sm;
+  float2* pt = tw + G::TW;
+  const int lane = threadIdx.x & 31;
+  const int tt = threadIdx.x & (T - 1);
+  const int grp = threadIdx.x / T;
+  const int partner = (lane - tt) + ((T - tt) & (T - 1));  // shuffle source
+  float2* fb = pt + G::PT + grp * G::STRIDE;
+  float2* sB = fb + G::BUF;
+  const int Gn = gridDim.x * RPC;
+  const int gid = blockIdx.x * RPC + grp;
+  const int rows = nv * H;
+  const int niter = (rows + Gn - 1) / Gn;  // the same for every group: every lane takes part in the shuffles
+  auto pair_of = [&](int fl, int& lab, int& f) {
+    const int q = fl / nf;
+    lab = l0 + q;
+    f = f0 + fl - q * nf;
+  };
+  const uint64_t pol = evict_first_policy();
+  const size_t W = 2 * static_cast<size_t>(L);
+  const int cmask = reg::col_batch(H) - 1;
+  const int gq = Gn / H, gr = Gn - gq * H;
+  auto advance = [&](int& fl, int& row) {
+    fl += gq;
+    row += gr;
+    if (row >= H) {
+      row -= H;
+      ++fl;
+    }
+  };
+  auto request_b = [&](int fl, int row) {
+    if (fl >= nv) return;
+    int lab, f;
+    pair_of(fl, lab, f);
+    const size_t rix = (static_cast<size_t>(lab) * eta + f) * H + row;
+    const float2* B = reinterpret_cast<const float2*>(bv) + rix * L;
+#pragma unroll
+    for (int q = tt; q < L / 2; q += T) cp_async16(sB + 2 * q, B + 2 * q, true, pol);
+  };
+
+  int flc = gid / H, rowc = gid - flc * H;
+  request_b(flc, rowc);  // b_v was last written by an earlier, completed grid
+  load_table(tw, twW, L + 1);
+  rv::build_pass_twiddles<L, 2>(pt, twW, threadIdx.x, blockDim.x);
+  pdl_wait();
+  pdl_trigger();
+  __syncthreads();
+  for (int it = 0; it < niter; ++it) {
+    const bool live = flc < nv;
+    const int fl = live ? flc : 0, row = live ? rowc : 0;
+    int label, f;
+    pair_of(fl, label, f);
+    int fln = flc, rown = rowc;
+    advance(fln, rown);
+    const int2 rg = ranges[f];
+    const bool any = live && rg.x <= rg.y;
+    const int c0 = any ? (rg.x & ~cmask) : L + 1;
+    const int c1 = any ? min(L, (rg.y | cmask)) : -1;
+    const float th = thr[f];
+    const size_t rix = (static_cast<size_t>(label) * eta + f) * H + row;
+    float2* X = Y + (static_cast<size_t>(fl) * H + row) * Whp;
+    // the next row's spectrum columns into L1 (one 128-byte line per thread and step)
+    if (fln < nv) {
+      int labn, fn;
+      pair_of(fln, labn, fn);
+      const int2 rgn = ranges[fn];
+      if (rgn.x <= rgn.y) {
+        const int n0 = rgn.x & ~cmask, n1 = min(L, (rgn.y | cmask));
+        const char* base = reinterpret_cast<const char*>(Y + (static_cast<size_t>(fln) * H + rown) * Whp + n0);
+        const int lines = ((n1 - n0 + 1) * 8 + 127) / 128;
+        for (int ln = tt; ln < lines; ln += T) asm volatile("prefetch.global.L1 [%0];" ::"l"(base + 128 * ln));
+      }
+    }
+    // inverse packing (rv::pack_step), X_{L-n} from the partner lane
+    float2 v[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const int n = tt + k * T;
+      v[k] = (n >= c0 && n <= c1) ? __ldca(X + n) : make_float2(0.f, 0.f);
+    }
+    float2 prev = (c1 >= L) ? __ldca(X + L) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < V / 2; ++k) {
+      float2 ra, rb;
+      ra.x = __shfl_sync(0xffffffffu, v[V - 1 - k].x, partner);
+      ra.y = __shfl_sync(0xffffffffu, v[V - 1 - k].y, partner);
+      rb.x = __shfl_sync(0xffffffffu, v[k].x, partner);
+      rb.y = __shfl_sync(0xffffffffu, v[k].y, partner);
+      rv::pack_step<L>(v, k, tt, ra, rb, prev, tw);
+    }
+    rv::row_fft<L, +1>(v, tt, fb, pt);
+    cp_async_commit_wait_all();  // this lane's part of the b_v row
+    __syncwarp();                // ... and the group's
+    if (live) {
+      float2* b2 = reinterpret_cast<float2*>(bv) + rix * L;
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        const float2 g = c_fma2(make_float2(scale, scale), v[k], sB[tt + k * T]);
+        const float2 c = make_float2(fminf(fmaxf(g.x, -th), th), fminf(fmaxf(g.y, -th), th));
+        __stcs(b2 + tt + k * T, c);
+        if (code)
+          reinterpret_cast<char2*>(code + rix * W)[tt + k * T] = make_char2(clip_code(g.x, th), clip_code(g.y, th));
+        v[k] = c_fma2(make_float2(-2.f, -2.f), c, g);  // g - 2 clip(g)
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < V; ++k) v[k] = make_float2(0.f, 0.f);
+    }
+    __syncwarp();  // the b_v stage is read: refill it with the group's next row
+    request_b(fln, rown);
+    rv::row_fft<L, -1>(v, tt, fb, pt);
+    // forward unpacking (rv::unpack_value), Z_{L-i} from the partner lane
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      float2 r;
+      r.x = __shfl_sync(0xffffffffu, v[V - 1 - q].x, partner);
+      r.y = __shfl_sync(0xffffffffu, v[V - 1 - q].y, partner);
+      const int i = tt + q * T;
+      if (i >= c0 && i <= c1) X[i] = rv::unpack_value<L>(v, q, tt, r, tw);
+    }
+    if (tt == 0 && c1 >= L) X[L] = make_float2(v[0].x - v[0].y, 0.f);  // i = L: e^{-i pi} = -1
+    flc = fln;
+    rowc = rown;
+  }
+  cp_async_commit_wait_all();  // no copy outlives the kernel
+}
+
 // Geometry of the u/w-step kernel: a CTA takes NR rows and runs one row
 // group per (row, label) — K NR groups, laid out like RowGeo's groups (32/T
 // per warp, T/32 warps each, or packed back to back; group slots past K NR
@@ -933,6 +1091,15 @@ size_t pair_smem() {
   return sizeof(float2) * PairGeo<pair_len(L)>::TOTAL;
 }
 
+// Half widths whose forward v-step can run on V values per thread
+// (shf_fftv.cuh): 12 T or 20 T with T = 2..32.
+__host__ __device__ constexpr bool use_v(int L) { return rv::supported(L); }
+__host__ __device__ constexpr int v_len(int L) { return use_v(L) ? L : 24; }
+template <int L>
+size_t vstepv_smem() {
+  return sizeof(float2) * RowVGeo<v_len(L)>::TOTAL;
+}
+
 template <int L>
 cudaError_t prepare_row_t() {
   cudaError_t e = allow_smem(k_wrow_vstep<L, 0>, vstep_smem<L, 0>());
@@ -943,6 +1110,8 @@ cudaError_t prepare_row_t() {
   }
   if constexpr (use_pair(L))
     if (e == cudaSuccess) e = allow_smem(k_wrow_vstep2r<L>, pair_smem<L>());
+  if constexpr (use_v(L))
+    if (e == cudaSuccess) e = allow_smem(k_wrow_vstepv<L>, vstepv_smem<L>());
   // the u/w-step's shared memory depends on K (rows per CTA): the largest over
   // the K each instance serves (2..4 and 5..8)
   size_t m4 = 0, m8 = 0;
@@ -981,15 +1150,16 @@ cudaError_t prepare_row_kernels() {
 // 1024, 8 values per thread elsewhere).
 int row_variant(int L, int mode, int variant) {
   if (mode == 1) return use_r16(L) ? kRow16 : kRow8;
-  if (variant == kRowDefault) return use_pair(L) ? kRowPair : (use_r16(L) ? kRow16 : kRow8);
+  if (variant == kRowDefault) return use_pair(L) ? kRowPair : (use_r16(L) ? kRow16 : (use_v(L) ? kRowV : kRow8));
   if (variant == kRowPair && !use_pair(L)) return kRow8;
   if (variant == kRow16 && !use_r16(L)) return kRow8;
+  if (variant == kRowV && !use_v(L)) return kRow8;
   return variant;
 }
 
 bool row_kernel_ok(int L, int variant) {
   return variant == kRowDefault || variant == kRow8 || (variant == kRow16 && use_r16(L)) ||
-         (variant == kRowPair && use_pair(L));
+         (variant == kRowPair && use_pair(L)) || (variant == kRowV && use_v(L));
 }
 
 int row_ctas_per_sm(int L, int mode, int variant) {
@@ -1001,6 +1171,8 @@ int row_ctas_per_sm(int L, int mode, int variant) {
   case N:                                                                                                       \
     if (v == kRowPair)                                                                                          \
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_vstep2r<pair_len(N)>, 256, pair_smem<N>());  \
+    else if (v == kRowV)                                                                                        \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_vstepv<v_len(N)>, 256, vstepv_smem<N>());    \
     else if (v == kRow16)                                                                                       \
       e = mode == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_vstep16<r16_len(N), 0>, 256,   \
                                                                     vstep16_smem<N, 0>())                       \
@@ -1025,6 +1197,7 @@ int row_groups_per_cta(int L, int mode, int variant) {
 #define SHF_CASE(N)                                        \
   case N:                                                  \
     if (v == kRowPair) return 2 * PairGeo<pair_len(N)>::RPC; /* rows */ \
+    if (v == kRowV) return RowVGeo<v_len(N)>::RPC;                        \
     return v == kRow16 ? Row16Geo<r16_len(N)>::RPC : RowGeo<N>::RPC;
     SHF_FAST_SIZES(SHF_CASE)
 #undef SHF_CASE
@@ -1040,6 +1213,9 @@ cudaError_t row_shrink(const Geo& g, int ctas, float2* Y, float* bv, const float
   case N:                                                                                                          \
     if (v == kRowPair)                                                                                             \
       return launch_pdl(k_wrow_vstep2r<pair_len(N)>, dim3(ctas), dim3(256), pair_smem<N>(), st, Y, bv, thr,      \
+                        g.ranges, g.H, Whp, g.eta, wv.l0, wv.f0, wv.nf, wv.nv, scale, g.twW, code);              \
+    if (v == kRowV)                                                                                                \
+      return launch_pdl(k_wrow_vstepv<v_len(N)>, dim3(ctas), dim3(256), vstepv_smem<N>(), st, Y, bv, thr,         \
                         g.ranges, g.H, Whp, g.eta, wv.l0, wv.f0, wv.nf, wv.nv, scale, g.twW, code);              \
     if (v == kRow16)                                                                                               \
       return launch_pdl(k_wrow_vstep16<r16_len(N), 0>, dim3(ctas), dim3(256), vstep16_smem<N, 0>(), st, Y, bv,    \

@@ -134,7 +134,7 @@ struct WorkItem {
 };
 constexpr int kDefaultWaveMiB = 128;  // coefficient spectra per wave
 // FFT kernel variants of a plan (0: the default for the size).
-enum RowKernel { kRowDefault = 0, kRow8 = 1, kRow16 = 2, kRowPair = 3 };
+enum RowKernel { kRowDefault = 0, kRow8 = 1, kRow16 = 2, kRowPair = 3, kRowV = 4 };
 enum ColKernel { kColDefault = 0, kCol8 = 1, kCol16 = 2 };
 struct FastPlan {
   int wave_mib = kDefaultWaveMiB;

@@ -209,7 +209,8 @@ typedef struct {
                         2..32: 24..384 and 40..640)                           */
   int col_kernel;    /* fast: fan and gather FFT kernel, 0 default for the
                         height, 1 8 values per thread, 2 16 values (heights
-                        512, 1024, 2048)                                      */
+                        512, 1024, 2048), 3 12 or 20 values (heights 12 T or
+                        20 T, T = 2..128)                                     */
 } seg_plan;
 
 /* The state's current plan. */

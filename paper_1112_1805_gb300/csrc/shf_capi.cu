@@ -872,7 +872,7 @@ std::vector<seg_plan> plan_candidates(const seg_state* st, const seg_plan& base,
       }
     } else if (stage == 3) {
       // the FFT kernel of the fan and the gather: 8 or 16 values per thread
-      for (int ck : {shf::kCol8, shf::kCol16}) {
+      for (int ck : {shf::kCol8, shf::kCol16, shf::kColV}) {
         if (!shf::fast_col_kernel_ok(g, ck)) continue;
         seg_plan p = base;
         p.col_kernel = ck;

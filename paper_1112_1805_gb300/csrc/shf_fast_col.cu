@@ -5,6 +5,7 @@
 // gather at heights 512, 1024 and 2048 on 16-value radix-16 FFTs (shf_fft16.cuh).
 #include "shf_fast.h"
 #include "shf_fft16.cuh"
+#include "shf_fftv.cuh"
 
 namespace shf {
 namespace fast {
@@ -352,6 +353,165 @@ __global__ void __launch_bounds__(Col16Geo<H>::NT, H == 512 ? 2 : 1)
   }
 }
 
+// The fan and the gather with V = 12 or 20 values per thread for the heights
+// with an odd factor (H = 12 T or 20 T, T = 2..128: shf_fftv.cuh), on the
+// geometry of the radix-16 kernels: CTAs of KB H/V threads, thread (b, tt)
+// holding rows tt + k H/V of column b.  Resident CTAs are asked for with at
+// most 128 registers per thread.
+template <int H>
+struct ColVGeo {
+  static constexpr int KB = reg::col_batch(H);
+  static constexpr int V = rv::vals_for(H);
+  static constexpr int T = H / V;
+  static constexpr int NT = KB * T;
+  static constexpr int PT = (rv::Passes<H>::TWSIZE + 1) & ~1;  // per-pass twiddles
+  static constexpr int BR = rv::brows(H) * KB;                 // one exchange buffer
+  static constexpr int TOTAL = PT + 2 * BR;
+  static constexpr int WARPS = (NT + 31) / 32;
+  static constexpr int MINB = 16 / WARPS > 1 ? 16 / WARPS : 1;  // 128 registers per thread
+};
+__host__ __device__ constexpr bool use_colv(int H) { return rv::supported_col(H); }
+__host__ __device__ constexpr int colv_len(int H) { return use_colv(H) ? H : 24; }
+
+template <int H>
+__global__ void __launch_bounds__(ColVGeo<H>::NT, ColVGeo<H>::MINB)
+    k_fcol_fanv(const float2* __restrict__ uhat, const float* __restrict__ bank, const WorkItem* __restrict__ items,
+                const int* __restrict__ cta_begin, float2* __restrict__ Y, int Wh, int Whp, int l0, int f0, int nf,
+                const float2* __restrict__ twH) {
+  using G = ColVGeo<H>;
+  constexpr int KB = G::KB, T = G::T, V = G::V;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* pt = sm;
+  float2* b0 = sm + G::PT;
+  float2* b1 = b0 + G::BR;
+  const int ib = cta_begin[blockIdx.x], ie = cta_begin[blockIdx.x + 1];
+  if (ib >= ie) return;
+  const int b = threadIdx.x % KB, tt = threadIdx.x / KB;
+  const size_t Pb = static_cast<size_t>(H) * Wh, Pp = static_cast<size_t>(H) * Whp;
+  WorkItem it = items[ib];
+  int col = it.tile * KB + b;
+  bool ok = col < Wh;
+  float2 u[V];
+  float w[V];
+  auto load_w = [&](const float* wf, int c, bool o) {
+#pragma unroll
+    for (int k = 0; k < V; ++k) w[k] = o ? __ldg(wf + static_cast<size_t>(tt + k * T) * Wh + c) : 0.f;
+  };
+  auto load_u = [&](const float2* src, int c, bool o) {
+#pragma unroll
+    for (int k = 0; k < V; ++k) u[k] = o ? src[static_cast<size_t>(tt + k * T) * Whp + c] : make_float2(0.f, 0.f);
+  };
+  load_w(bank + Pb * it.filter, col, ok);
+  rv::build_pass_twiddles<H, 1>(pt, twH, threadIdx.x, blockDim.x);
+  pdl_wait();
+  pdl_trigger();
+  load_u(uhat + Pp * it.label, col, ok);
+  for (int i = ib; i < ie; ++i) {
+    float2 v[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) v[k] = c_scale(u[k], w[k]);
+    const int fl = (it.label - l0) * nf + (it.filter - f0), ccol = col;
+    const bool cok = ok;
+    if (i + 1 < ie) {
+      const WorkItem nx = items[i + 1];
+      col = nx.tile * KB + b;
+      ok = col < Wh;
+      load_w(bank + Pb * nx.filter, col, ok);
+      if (nx.tile != it.tile || nx.label != it.label) load_u(uhat + Pp * nx.label, col, ok);
+      it = nx;
+    }
+    rv::batch_fft<H, +1, KB>(v, tt, b, b0, b1, pt);  // starts with a CTA barrier (also after the twiddle table)
+    if (cok) {
+      float2* dst = Y + Pp * fl + ccol;
+#pragma unroll
+      for (int k = 0; k < V; ++k) dst[static_cast<size_t>(tt + k * T) * Whp] = v[k];
+    }
+  }
+}
+
+// The gather keeps the next item's tile in registers while the current one
+// is transformed for V = 12; for V = 20 the run accumulator, the filter column
+// and the transform already take 100 registers, and the tile is loaded when
+// its item starts.
+template <int H>
+__global__ void __launch_bounds__(ColVGeo<H>::NT, ColVGeo<H>::MINB)
+    k_fcol_gatherv(const float2* __restrict__ Y, const float* __restrict__ bank, const WorkItem* __restrict__ items,
+                   const int* __restrict__ cta_begin, float2* __restrict__ partial, int Wh, int Whp, int l0, int f0,
+                   int nf, const float2* __restrict__ twH) {
+  using G = ColVGeo<H>;
+  constexpr int KB = G::KB, T = G::T, V = G::V;
+  constexpr bool PREFETCH = V <= 12;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* pt = sm;
+  float2* b0 = sm + G::PT;
+  float2* b1 = b0 + G::BR;
+  const int ib = cta_begin[blockIdx.x], ie = cta_begin[blockIdx.x + 1];
+  if (ib >= ie) return;
+  const int b = threadIdx.x % KB, tt = threadIdx.x / KB;
+  const size_t Pb = static_cast<size_t>(H) * Wh, Pp = static_cast<size_t>(H) * Whp;
+  WorkItem it = items[ib];
+  int col = it.tile * KB + b;
+  bool ok = col < Wh;
+  float2 acc[V], y[PREFETCH ? V : 1];
+  float w[V];
+#pragma unroll
+  for (int k = 0; k < V; ++k) acc[k] = make_float2(0.f, 0.f);
+  auto tile_of = [&](const WorkItem& x) { return Y + Pp * ((x.label - l0) * nf + (x.filter - f0)); };
+  rv::build_pass_twiddles<H, 1>(pt, twH, threadIdx.x, blockDim.x);
+  pdl_wait();
+  pdl_trigger();
+  if constexpr (PREFETCH) {
+    const float2* src = tile_of(it);
+#pragma unroll
+    for (int k = 0; k < V; ++k) y[k] = ok ? src[static_cast<size_t>(tt + k * T) * Whp + col] : make_float2(0.f, 0.f);
+  }
+  for (int i = ib; i < ie; ++i) {
+    float2 v[V];
+    if constexpr (PREFETCH) {
+#pragma unroll
+      for (int k = 0; k < V; ++k) v[k] = y[k];
+    } else {
+      const float2* src = tile_of(it);
+#pragma unroll
+      for (int k = 0; k < V; ++k) v[k] = ok ? src[static_cast<size_t>(tt + k * T) * Whp + col] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k)
+      w[k] = ok ? __ldg(bank + Pb * it.filter + static_cast<size_t>(tt + k * T) * Wh + col) : 0.f;
+    WorkItem nx = it;
+    int ncol = col;
+    bool nok = ok;
+    if (i + 1 < ie) {
+      nx = items[i + 1];
+      ncol = nx.tile * KB + b;
+      nok = ncol < Wh;
+      if constexpr (PREFETCH) {
+        const float2* src = tile_of(nx);
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+          y[k] = nok ? src[static_cast<size_t>(tt + k * T) * Whp + ncol] : make_float2(0.f, 0.f);
+      }
+    }
+    rv::batch_fft<H, -1, KB>(v, tt, b, b0, b1, pt);  // starts with a CTA barrier (also after the twiddle table)
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      acc[k].x = fmaf(w[k], v[k].x, acc[k].x);
+      acc[k].y = fmaf(w[k], v[k].y, acc[k].y);
+    }
+    if (i + 1 == ie || nx.slot != it.slot) {
+      float2* dst = partial + static_cast<size_t>(it.slot) * H * KB + b;
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        dst[static_cast<size_t>(tt + k * T) * KB] = acc[k];
+        acc[k] = make_float2(0.f, 0.f);
+      }
+    }
+    it = nx;
+    col = ncol;
+    ok = nok;
+  }
+}
+
 // T[label] on one tile = column-inverse of the sum of the tile's partial
 // slots, in a fixed order.  The sum is load-latency bound (and small images
 // have few tiles), so the slots are split into RG consecutive runs (RG copies
@@ -434,6 +594,11 @@ size_t fan16_smem() {
   return sizeof(float2) * Col16Geo<fan16_len(N)>::TOTAL;
 }
 
+template <int N>
+size_t colv_smem() {
+  return sizeof(float2) * ColVGeo<colv_len(N)>::TOTAL;
+}
+
 template <int H>
 cudaError_t prepare_col_t() {
   const size_t s = col_smem<H>();
@@ -442,6 +607,10 @@ cudaError_t prepare_col_t() {
   if constexpr (use_fan16(H)) {
     if (e == cudaSuccess) e = allow_smem(k_fcol_fan16<H>, fan16_smem<H>());
     if (e == cudaSuccess) e = allow_smem(k_fcol_gather16<H>, fan16_smem<H>());
+  }
+  if constexpr (use_colv(H)) {
+    if (e == cudaSuccess) e = allow_smem(k_fcol_fanv<H>, colv_smem<H>());
+    if (e == cudaSuccess) e = allow_smem(k_fcol_gatherv<H>, colv_smem<H>());
   }
   if (e == cudaSuccess) e = allow_smem(k_fcol_gather<H>, s);
   if (e == cudaSuccess) e = allow_smem(k_fcol_reduce_inv<H>, sizeof(float2) * ReduceGeo<H>::TOTAL);
@@ -462,9 +631,12 @@ cudaError_t prepare_col_kernels() {
 // The column transform a plan's variant selects at height H: radix-16 (16
 // values per thread) where it exists and is asked for or is the default.
 bool use16(int H, int variant) { return use_fan16(H) && variant != kCol8; }
+// V values per thread: asked for, or the default where it exists
+bool usev(int H, int variant) { return use_colv(H) && (variant == kColV || variant == kColDefault); }
 
 bool col_kernel_ok(int H, int variant) {
-  return variant == kColDefault || variant == kCol8 || (variant == kCol16 && use_fan16(H));
+  return variant == kColDefault || variant == kCol8 || (variant == kCol16 && use_fan16(H)) ||
+         (variant == kColV && use_colv(H));
 }
 
 int fan_ctas_per_sm(int H, int variant) {
@@ -476,6 +648,9 @@ int fan_ctas_per_sm(int H, int variant) {
     if (use16(N, variant))                                                                                  \
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_fcol_fan16<fan16_len(N)>,                  \
                                                         Col16Geo<fan16_len(N)>::NT, fan16_smem<N>());      \
+    else if (usev(N, variant))                                                                              \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_fcol_fanv<colv_len(N)>,                    \
+                                                        ColVGeo<colv_len(N)>::NT, colv_smem<N>());         \
     else                                                                                                    \
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_fcol_fan<N>, ColGeo<N>::NT, col_smem<N>()); \
     break;
@@ -495,6 +670,9 @@ int col_ctas_per_sm(int H, int variant) {
     if (use16(N, variant))                                                                                  \
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_fcol_gather16<fan16_len(N)>,               \
                                                         Col16Geo<fan16_len(N)>::NT, fan16_smem<N>());      \
+    else if (usev(N, variant))                                                                              \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_fcol_gatherv<colv_len(N)>,                \
+                                                        ColVGeo<colv_len(N)>::NT, colv_smem<N>());         \
     else                                                                                                    \
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_fcol_gather<N>, ColGeo<N>::NT, col_smem<N>()); \
     break;
@@ -525,6 +703,9 @@ cudaError_t col_fan(const Geo& g, int nc, const float2* uhat, const WorkItem* it
     if (use16(N, variant))                                                                                       \
       return launch_pdl(k_fcol_fan16<fan16_len(N)>, dim3(nc), dim3(Col16Geo<fan16_len(N)>::NT), fan16_smem<N>(),  \
                         st, uhat, g.bank, items, cta_begin, Y, g.Wh, Whp, wv.l0, wv.f0, wv.nf, g.twH);           \
+    if (usev(N, variant))                                                                                        \
+      return launch_pdl(k_fcol_fanv<colv_len(N)>, dim3(nc), dim3(ColVGeo<colv_len(N)>::NT), colv_smem<N>(), st,  \
+                        uhat, g.bank, items, cta_begin, Y, g.Wh, Whp, wv.l0, wv.f0, wv.nf, g.twH);               \
     return launch_pdl(k_fcol_fan<N>, dim3(nc), dim3(ColGeo<N>::NT), col_smem<N>(), st, uhat, g.bank, items, cta_begin, Y, \
                       g.Wh, Whp, wv.l0, wv.f0, wv.nf, g.twH);
     SHF_COL_SIZES(SHF_CASE)
@@ -542,6 +723,9 @@ cudaError_t col_gather(const Geo& g, int nc, const float2* Y, const WorkItem* it
       return launch_pdl(k_fcol_gather16<fan16_len(N)>, dim3(nc), dim3(Col16Geo<fan16_len(N)>::NT),           \
                         fan16_smem<N>(), st, Y, g.bank, items, cta_begin, partial, g.Wh, Whp, wv.l0, wv.f0,   \
                         wv.nf, g.twH);                                                                        \
+    if (usev(N, variant))                                                                                     \
+      return launch_pdl(k_fcol_gatherv<colv_len(N)>, dim3(nc), dim3(ColVGeo<colv_len(N)>::NT), colv_smem<N>(), \
+                        st, Y, g.bank, items, cta_begin, partial, g.Wh, Whp, wv.l0, wv.f0, wv.nf, g.twH);      \
     return launch_pdl(k_fcol_gather<N>, dim3(nc), dim3(ColGeo<N>::NT), col_smem<N>(), st, Y, g.bank, items, cta_begin, \
                       partial, g.Wh, Whp, wv.l0, wv.f0, wv.nf, g.twH);
     SHF_COL_SIZES(SHF_CASE)

@@ -1,7 +1,8 @@
-// Register FFTs with V values per thread for the v-step rows whose half width
-// has an odd factor: L = 3 2^a (V = 12) and L = 5 2^a (V = 20), split as
-// L = V T over a row group of T = 2 .. 32 threads (a power of two, so that a
-// group never leaves its warp and every barrier is __syncwarp).
+// Register FFTs with V values per thread for the lengths with an odd factor:
+// L = 3 2^a (V = 12) and L = 5 2^a (V = 20), split as L = V T over T threads
+// (a power of two): the v-step's rows with T = 2 .. 32 (a group never leaves
+// its warp and every barrier is __syncwarp), and the fan's and gather's
+// columns in batches of KB columns with T = 2 .. 128 (CTA barriers).
 //
 // Thread tt holds v[k] = x[tt + k T], k = 0..V-1 ("stride layout", as in
 // shf_fft16.cuh).  Stockham passes: first one of radix V (span 1: no
@@ -27,15 +28,19 @@ __host__ __device__ constexpr int vals_for(int L) {
   return reg::odd_part(L) == 3 ? 12 : (reg::odd_part(L) == 5 ? 20 : 0);
 }
 __host__ __device__ constexpr bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
-// Half widths with a V-value transform: T = L / V a power of two in [2, 32].
-__host__ __device__ constexpr bool supported(int L) {
+// Lengths with a V-value transform of T = L / V threads per sequence, a power
+// of two in [2, tmax]: rows up to 32 (one warp), columns up to 128 (the CTA's
+// barriers).
+__host__ __device__ constexpr bool supported_upto(int L, int tmax) {
   return vals_for(L) > 0 && L % vals_for(L) == 0 && pow2(L / vals_for(L)) && L / vals_for(L) >= 2 &&
-         L / vals_for(L) <= 32;
+         L / vals_for(L) <= tmax;
 }
+__host__ __device__ constexpr bool supported(int L) { return supported_upto(L, 32); }
+__host__ __device__ constexpr bool supported_col(int H) { return supported_upto(H, 128); }
 
 template <int L>
 struct Passes {
-  static_assert(supported(L), "V-value FFT: L = 12 T or 20 T, T = 2^a in [2, 32]");
+  static_assert(supported_col(L), "V-value FFT: L = 12 T or 20 T, T = 2^a in [2, 128]");
   static constexpr int V = vals_for(L);
   static constexpr int T = L / V;
   static constexpr int LGT = ilog2(T);
@@ -217,7 +222,52 @@ __host__ __device__ __forceinline__ float2 unpack_value(const float2 (&v)[Passes
 // Exchange buffer of one group (index L included for staging).
 __host__ __device__ constexpr int row_buf(int L) { return ridx(L) + 1; }
 
+// Batch variants for the column transforms: a CTA transforms KB columns of
+// length N; thread (b, tt) holds v[k] = x_b[tt + k T], and element i of column
+// b lives at ridx(i) KB + b of the exchange buffer.
+template <int N, int P, int KB>
+__host__ __device__ __forceinline__ void bpass_store(const float2 (&v)[Passes<N>::V], int tt, int b, float2* out) {
+  using PS = Passes<N>;
+  constexpr int V = PS::V, R = PS::radix(P), Ns = PS::span(P), M = V / R, T = PS::T;
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int j = tt + m * T;
+    const int o = (j / Ns) * Ns * R + (j % Ns);
+#pragma unroll
+    for (int q = 0; q < R; ++q) out[ridx(o + q * Ns) * KB + b] = v[m + q * M];
+  }
+}
+
+template <int N, int KB>
+__host__ __device__ __forceinline__ void bload_stride(float2 (&v)[Passes<N>::V], int tt, int b, const float2* in) {
+  using PS = Passes<N>;
+#pragma unroll
+  for (int k = 0; k < PS::V; ++k) v[k] = in[ridx(tt + k * PS::T) * KB + b];
+}
+
+// Rows of an exchange buffer of a length-N batch transform.
+__host__ __device__ constexpr int brows(int N) { return ridx(N) + 1; }
+
 #ifdef __CUDACC__
+// The transform of a CTA's KB columns (every thread of the CTA takes part);
+// exchanges alternate between two buffers, so that one CTA barrier per
+// exchange suffices (plus one before the first, which also covers the
+// previous transform's reads); result in v, stride layout.
+template <int N, int S, int KB, int P = 0>
+__device__ __forceinline__ void batch_fft(float2 (&v)[Passes<N>::V], int tt, int b, float2* buf0, float2* buf1,
+                                          const float2* pt) {
+  using PS = Passes<N>;
+  pass_bfly<N, P, S>(v, tt, pt);
+  if constexpr (P + 1 < PS::NPASS) {
+    float2* buf = (P % 2 == 0) ? buf0 : buf1;
+    if constexpr (P == 0) __syncthreads();
+    bpass_store<N, P, KB>(v, tt, b, buf);
+    __syncthreads();
+    bload_stride<N, KB>(v, tt, b, buf);
+    batch_fft<N, S, KB, P + 1>(v, tt, b, buf0, buf1, pt);
+  }
+}
+
 // The transform of one sequence by its row group (T <= 32: warp barriers);
 // result in v, stride layout.  Each exchange starts with a barrier: the buffer
 // may still be read by a previous transform.

@@ -135,7 +135,7 @@ struct WorkItem {
 constexpr int kDefaultWaveMiB = 128;  // coefficient spectra per wave
 // FFT kernel variants of a plan (0: the default for the size).
 enum RowKernel { kRowDefault = 0, kRow8 = 1, kRow16 = 2, kRowPair = 3, kRowV = 4 };
-enum ColKernel { kColDefault = 0, kCol8 = 1, kCol16 = 2 };
+enum ColKernel { kColDefault = 0, kCol8 = 1, kCol16 = 2, kColV = 3 };
 struct FastPlan {
   int wave_mib = kDefaultWaveMiB;
   int col_ctas_per_sm = 0;  // CTAs per SM of the column launches (0: as many as fit)

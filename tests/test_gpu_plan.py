@@ -193,11 +193,13 @@ def test_batch_tune(torch_mod, oracle_mod):
 @pytest.mark.parametrize("H,W,K,J,T", [(512, 128, 3, 2, 6),   # v-step: 8 values, 16 values, pairs (L = 64); columns 8 / 16
                                       (512, 256, 2, 3, 5),   # L = 128: all three row kernels; H = 512: both columns
                                       (1024, 512, 2, 2, 4),  # L = 256: 8 / 16 values; H = 1024: both columns
-                                      (96, 384, 3, 2, 12),   # L = 192: 8 / 12 values; H = 96 (8 values only)
-                                      (64, 640, 2, 2, 6)])   # L = 320: 8 / 20 values
+                                      (96, 384, 3, 2, 12),   # L = 192: 8 / 12 values; H = 96: 8 / 12 values
+                                      (64, 640, 2, 2, 6),    # L = 320: 8 / 20 values
+                                      (320, 192, 2, 2, 6)])  # H = 320: 8 / 20 values; L = 96: 8 / 12 values
 def test_every_fft_kernel_variant_meets_the_bars(torch_mod, oracle_mod, H, W, K, J, T):
     # the plan's FFT kernels (row_kernel: 1 eight values per thread, 2 sixteen,
-    # 3 pairs of rows, 4 twelve or twenty; col_kernel: 1 eight, 2 sixteen)
+    # 3 pairs of rows, 4 twelve or twenty; col_kernel: 1 eight, 2 sixteen, 3
+    # twelve or twenty)
     # change only the order of
     # the FFT arithmetic: each one meets the oracle bars, and the sizes without
     # a variant refuse it
@@ -208,7 +210,8 @@ def test_every_fft_kernel_variant_meets_the_bars(torch_mod, oracle_mod, H, W, K,
     L = W // 2
     rows = ([1] + ([2] if L in (64, 128, 256, 512, 1024) else []) + ([3] if L in (64, 128) else [])
             + ([4] if L in (24, 40, 48, 80, 96, 160, 192, 320, 384, 640) else []))
-    cols = [1] + ([2] if H in (512, 1024, 2048) else [])
+    cols = ([1] + ([2] if H in (512, 1024, 2048) else [])
+            + ([3] if H in (24, 40, 48, 80, 96, 160, 192, 320, 384, 640, 768, 1280, 1536) else []))
     seen = set()
     for rk in rows:
         for ck in cols:
@@ -219,7 +222,8 @@ def test_every_fft_kernel_variant_meets_the_bars(torch_mod, oracle_mod, H, W, K,
             seen.add((rk, ck))
     assert len(seen) == len(rows) * len(cols)
     for bad in ({"row_kernel": 3} if 3 not in rows else {}, {"row_kernel": 4} if 4 not in rows else {},
-                {"col_kernel": 2} if 2 not in cols else {}, {"row_kernel": 7}, {"col_kernel": -1}):
+                {"col_kernel": 2} if 2 not in cols else {}, {"col_kernel": 3} if 3 not in cols else {},
+                {"row_kernel": 7}, {"col_kernel": -1}):
         if not bad:
             continue
         with pytest.raises(B.ShearsegError) as e:

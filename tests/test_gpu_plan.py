@@ -195,7 +195,9 @@ def test_batch_tune(torch_mod, oracle_mod):
                                       (1024, 512, 2, 2, 4),  # L = 256: 8 / 16 values; H = 1024: both columns
                                       (96, 384, 3, 2, 12),   # L = 192: 8 / 12 values; H = 96: 8 / 12 values
                                       (64, 640, 2, 2, 6),    # L = 320: 8 / 20 values
-                                      (320, 192, 2, 2, 6)])  # H = 320: 8 / 20 values; L = 96: 8 / 12 values
+                                      (320, 192, 2, 2, 6),   # H = 320: 8 / 20 values; L = 96: 8 / 12 values
+                                      (1280, 64, 2, 2, 5),   # H = 1280: columns of 4, 8 / 20 values
+                                      (1536, 48, 2, 1, 5)])  # H = 1536: 8 / 12 values (128 threads a column)
 def test_every_fft_kernel_variant_meets_the_bars(torch_mod, oracle_mod, H, W, K, J, T):
     # the plan's FFT kernels (row_kernel: 1 eight values per thread, 2 sixteen,
     # 3 pairs of rows, 4 twelve or twenty; col_kernel: 1 eight, 2 sixteen, 3

@@ -143,6 +143,39 @@ __host__ __device__ __forceinline__ void pass_bfly(float2 (&v)[Passes<L>::V], in
   }
 }
 
+// Layout of a row group's exchange buffer after the radix-V pass, which
+// writes V consecutive elements per thread (lanes V apart, so with the padding
+// i + (i >> 4) four or more lanes of a half-warp share a bank pair of the
+// 64-bit accesses):
+//   1: i ^ ((i >> 2) & 15), an XOR of the four bank bits with bits 2..5 (V = 12,
+//      L a multiple of 16: the XOR permutes 16-aligned blocks);
+//   2: the padding i + (i >> 2) (V = 20, T = 4, 16, 32): conflict-free writes,
+//      two-way stride reads, and addresses that stay base + constant;
+//   0: i + (i >> 4) (T = 2, and T = 8 with V = 20, where the others measured
+//      slower: their extra address registers spill).
+// Counted per half-warp, the exchanges of L = 192 take 112 wavefronts instead
+// of 168, of L = 320 224 instead of 304.
+__host__ __device__ constexpr int first_layout(int L) {
+  return vals_for(L) == 12 ? (L % 16 == 0 ? 1 : 0)
+                           : (L / 20 == 4 || L / 20 == 16 || L / 20 == 32 ? 2 : 0);
+}
+
+// Position of element i in the exchange buffer after pass P: the layout above
+// after pass 0; for V = 12 the XOR with bits 3..6 after pass 1 (L a multiple of
+// 16); the padding i + (i >> 4) otherwise.
+template <int L, int P>
+__host__ __device__ __forceinline__ int xidx(int i) {
+  if constexpr (P == 0 && first_layout(L) == 1) {
+    return i ^ ((i >> 2) & 15);
+  } else if constexpr (P == 0 && first_layout(L) == 2) {
+    return i + (i >> 2);
+  } else if constexpr (P == 1 && Passes<L>::V == 12 && L % 16 == 0) {
+    return i ^ ((i >> 3) & 15);
+  } else {
+    return ridx(i);
+  }
+}
+
 // Stockham writes of pass P: output q of butterfly j goes to o + q Ns with
 // o = (j / Ns) Ns R + (j mod Ns).
 template <int L, int P>
@@ -154,15 +187,16 @@ __host__ __device__ __forceinline__ void pass_store(const float2 (&v)[Passes<L>:
     const int j = tt + m * T;
     const int o = (j / Ns) * Ns * R + (j % Ns);
 #pragma unroll
-    for (int q = 0; q < R; ++q) out[ridx(o + q * Ns)] = v[m + q * M];
+    for (int q = 0; q < R; ++q) out[xidx<L, P>(o + q * Ns)] = v[m + q * M];
   }
 }
 
-template <int L>
+// Stride-layout reads after the exchange that follows pass P.
+template <int L, int P>
 __host__ __device__ __forceinline__ void load_stride(float2 (&v)[Passes<L>::V], int tt, const float2* in) {
   using PS = Passes<L>;
 #pragma unroll
-  for (int k = 0; k < PS::V; ++k) v[k] = in[ridx(tt + k * PS::T)];
+  for (int k = 0; k < PS::V; ++k) v[k] = in[xidx<L, P>(tt + k * PS::T)];
 }
 
 // Per-pass twiddle table pt[TWSIZE] from tw[m] = exp(-2 pi i m / (L TWSTEP)):
@@ -220,11 +254,25 @@ __host__ __device__ __forceinline__ float2 unpack_value(const float2 (&v)[Passes
 }
 
 // Exchange buffer of one group (index L included for staging).
-__host__ __device__ constexpr int row_buf(int L) { return ridx(L) + 1; }
+__host__ __device__ constexpr int row_buf(int L) {
+  return (first_layout(L) == 2 ? L + (L >> 2) : ridx(L)) + 1;
+}
 
 // Batch variants for the column transforms: a CTA transforms KB columns of
 // length N; thread (b, tt) holds v[k] = x_b[tt + k T], and element i of column
-// b lives at ridx(i) KB + b of the exchange buffer.
+// b lives at bxidx(i) KB + b of the exchange buffer.  A half-warp spans 16/KB
+// values of tt; after the radix-V pass they write V consecutive elements each,
+// so i is XORed with bits 2.. of itself (16/KB - 1 of them) to give those
+// threads distinct bank pairs; the later exchanges keep the padding.
+template <int N, int P, int KB>
+__host__ __device__ __forceinline__ int bxidx(int i) {
+  if constexpr (P == 0 && N % 4 == 0 && (KB == 8 || KB == 4)) {
+    return i ^ ((i >> 2) & (16 / KB - 1));
+  } else {
+    return ridx(i);
+  }
+}
+
 template <int N, int P, int KB>
 __host__ __device__ __forceinline__ void bpass_store(const float2 (&v)[Passes<N>::V], int tt, int b, float2* out) {
   using PS = Passes<N>;
@@ -234,15 +282,15 @@ __host__ __device__ __forceinline__ void bpass_store(const float2 (&v)[Passes<N>
     const int j = tt + m * T;
     const int o = (j / Ns) * Ns * R + (j % Ns);
 #pragma unroll
-    for (int q = 0; q < R; ++q) out[ridx(o + q * Ns) * KB + b] = v[m + q * M];
+    for (int q = 0; q < R; ++q) out[bxidx<N, P, KB>(o + q * Ns) * KB + b] = v[m + q * M];
   }
 }
 
-template <int N, int KB>
+template <int N, int P, int KB>
 __host__ __device__ __forceinline__ void bload_stride(float2 (&v)[Passes<N>::V], int tt, int b, const float2* in) {
   using PS = Passes<N>;
 #pragma unroll
-  for (int k = 0; k < PS::V; ++k) v[k] = in[ridx(tt + k * PS::T) * KB + b];
+  for (int k = 0; k < PS::V; ++k) v[k] = in[bxidx<N, P, KB>(tt + k * PS::T) * KB + b];
 }
 
 // Rows of an exchange buffer of a length-N batch transform.
@@ -263,7 +311,7 @@ __device__ __forceinline__ void batch_fft(float2 (&v)[Passes<N>::V], int tt, int
     if constexpr (P == 0) __syncthreads();
     bpass_store<N, P, KB>(v, tt, b, buf);
     __syncthreads();
-    bload_stride<N, KB>(v, tt, b, buf);
+    bload_stride<N, P, KB>(v, tt, b, buf);
     batch_fft<N, S, KB, P + 1>(v, tt, b, buf0, buf1, pt);
   }
 }
@@ -279,7 +327,7 @@ __device__ __forceinline__ void row_fft(float2 (&v)[Passes<L>::V], int tt, float
     __syncwarp();
     pass_store<L, P>(v, tt, buf);
     __syncwarp();
-    load_stride<L>(v, tt, buf);
+    load_stride<L, P>(v, tt, buf);
     row_fft<L, S, P + 1>(v, tt, buf, pt);
   }
 }

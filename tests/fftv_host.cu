@@ -35,12 +35,30 @@ struct Emu {
     bfly_all<P, S>(R, pt);
     if constexpr (P + 1 < PS::NPASS) {
       for (int tt = 0; tt < T; ++tt) rv::pass_store<L, P>(regs(R[tt]), tt, buf.data());
-      for (int tt = 0; tt < T; ++tt) rv::load_stride<L>(regs(R[tt]), tt, buf.data());
+      for (int tt = 0; tt < T; ++tt) rv::load_stride<L, P>(regs(R[tt]), tt, buf.data());
       group_fft<S, P + 1>(R, buf, pt);
     }
   }
 
+  // the exchange layout after pass P: inside the buffer and one slot per index
+  template <int P = 0>
+  static bool layout_ok() {
+    if constexpr (P + 1 < PS::NPASS) {
+      std::vector<int> seen(rv::row_buf(L), 0);
+      for (int i = 0; i < L; ++i) {
+        const int a = rv::xidx<L, P>(i);
+        if (a < 0 || a >= rv::row_buf(L) || seen[a]++) return false;
+      }
+      return layout_ok<P + 1>();
+    }
+    return true;
+  }
+
   static int check() {
+    if (!layout_ok()) {
+      std::printf("L=%d exchange layout out of the buffer or not injective FAIL\n", L);
+      return 1;
+    }
     const int W = 2 * L;
     std::vector<float2> tw(W);  // exp(-2 pi i m / W), as the library's table
     for (int m = 0; m < W; ++m) tw[m] = make_float2(std::cos(-2 * M_PI * m / W), std::sin(-2 * M_PI * m / W));
@@ -121,7 +139,83 @@ struct Emu {
   }
 };
 
+// rv::batch_fft over KB columns of length N (threads (b, tt), alternating
+// exchange buffers of brows(N) KB elements), against FP64 DFTs per column.
+template <int N, int KB>
+struct BatchEmu {
+  using PS = rv::Passes<N>;
+  static constexpr int V = PS::V, T = PS::T, BR = rv::brows(N) * KB;
+  using Regs = std::array<float2, V>;
+  static float2 (&regs(Regs& r))[V] { return *reinterpret_cast<float2(*)[V]>(r.data()); }
+
+  template <int P = 0>
+  static bool layout_ok() {
+    if constexpr (P + 1 < PS::NPASS) {
+      std::vector<int> seen(BR, 0);
+      for (int i = 0; i < N; ++i)
+        for (int b = 0; b < KB; ++b) {
+          const int a = rv::bxidx<N, P, KB>(i) * KB + b;
+          if (a < 0 || a >= BR || seen[a]++) return false;
+        }
+      return layout_ok<P + 1>();
+    }
+    return true;
+  }
+  template <int S, int P = 0>
+  static void fft(std::vector<Regs>& R, std::vector<float2>& b0, std::vector<float2>& b1, const float2* pt) {
+    for (int t = 0; t < T * KB; ++t) rv::pass_bfly<N, P, S>(regs(R[t]), t / KB, pt);
+    if constexpr (P + 1 < PS::NPASS) {
+      std::vector<float2>& buf = (P % 2 == 0) ? b0 : b1;
+      for (int t = 0; t < T * KB; ++t) rv::bpass_store<N, P, KB>(regs(R[t]), t / KB, t % KB, buf.data());
+      for (int t = 0; t < T * KB; ++t) rv::bload_stride<N, P, KB>(regs(R[t]), t / KB, t % KB, buf.data());
+      fft<S, P + 1>(R, b0, b1, pt);
+    }
+  }
+  static int check() {
+    if (!layout_ok()) {
+      std::printf("batch N=%d KB=%d exchange layout out of the buffer or not injective FAIL\n", N, KB);
+      return 1;
+    }
+    std::vector<float2> tw(N);  // exp(-2 pi i m / N)
+    for (int m = 0; m < N; ++m) tw[m] = make_float2(std::cos(-2 * M_PI * m / N), std::sin(-2 * M_PI * m / N));
+    std::vector<float2> pt(PS::TWSIZE);
+    rv::build_pass_twiddles<N, 1>(pt.data(), tw.data(), 0, 1);
+    std::vector<float2> b0(BR, make_float2(NAN, NAN)), b1(BR, make_float2(NAN, NAN));
+    std::mt19937 rng(2011 + N + KB);
+    std::normal_distribution<double> nd;
+    double err = 0;
+    for (int S : {+1, -1}) {
+      std::vector<std::vector<cd>> x(KB, std::vector<cd>(N));
+      for (auto& c : x)
+        for (auto& a : c) a = cd(nd(rng), nd(rng));
+      std::vector<Regs> R(T * KB);
+      for (int t = 0; t < T * KB; ++t)
+        for (int k = 0; k < V; ++k) {
+          const cd a = x[t % KB][t / KB + k * T];
+          R[t][k] = make_float2(a.real(), a.imag());
+        }
+      if (S > 0)
+        fft<+1>(R, b0, b1, pt.data());
+      else
+        fft<-1>(R, b0, b1, pt.data());
+      for (int b = 0; b < KB; ++b)
+        for (int q = 0; q < N; ++q) {
+          cd ref = 0;
+          for (int n = 0; n < N; ++n) ref += x[b][n] * std::polar(1.0, S * 2 * M_PI * double(n) * q / N);
+          const float2 g = R[(q % T) * KB + b][q / T];
+          err = std::max(err, std::abs(cd(g.x, g.y) - ref) / std::sqrt(double(N)));
+        }
+    }
+    const bool ok = err < 10 * 6e-8 * std::log2(double(N)) * 4;
+    std::printf("batch N=%d KB=%d V=%d T=%d fft %.2e %s\n", N, KB, V, T, err, ok ? "ok" : "FAIL");
+    return ok ? 0 : 1;
+  }
+};
+
 int main() {
   return Emu<24>::check() + Emu<48>::check() + Emu<96>::check() + Emu<192>::check() + Emu<384>::check() +
-         Emu<40>::check() + Emu<80>::check() + Emu<160>::check() + Emu<320>::check() + Emu<640>::check();
+         Emu<40>::check() + Emu<80>::check() + Emu<160>::check() + Emu<320>::check() + Emu<640>::check() +
+         BatchEmu<24, 8>::check() + BatchEmu<96, 8>::check() + BatchEmu<384, 8>::check() + BatchEmu<768, 8>::check() +
+         BatchEmu<1536, 4>::check() + BatchEmu<40, 8>::check() + BatchEmu<160, 8>::check() +
+         BatchEmu<640, 8>::check() + BatchEmu<1280, 4>::check() + BatchEmu<2560, 4>::check();
 }

@@ -185,9 +185,10 @@ int seg_admm_step(seg_state* st, int n_iters);
  * sizes (fast = 0) run the general kernels with tiles of tile_cols
  * half-spectrum columns and tile_rows rows and `groups` filter
  * groups in the synthesis sums.  On the fast path the plan also names the
- * FFT kernels: the v-step's (8 or 16 values per thread, one row or a pair of
- * rows per thread group) and the fan's and gather's (8 or 16 values per
- * thread), among those that exist for the size.  Fields of the other path
+ * FFT kernels: the v-step's (8, 16, 12, 20 or 32 values per thread, one row
+ * or a pair of rows per thread group) and the fan's and gather's (8, 16, 12
+ * or 20 values per thread), among those that exist for the size, and whether
+ * the iteration's launches overlap (serial).  Fields of the other path
  * are 0 in seg_admm_get_plan and ignored by seg_admm_set_plan.  The plan
  * changes the grouping of the FP32 synthesis sums (wave_mib,
  * col_ctas_per_sm, groups) and the order of the FFT arithmetic (row_kernel,
@@ -205,12 +206,16 @@ typedef struct {
   int row_kernel;    /* fast: v-step FFT kernel, 0 default for the width, 1 8
                         values per thread, 2 16 values (half widths 64..1024,
                         powers of two), 3 pairs of rows (half widths 64, 128),
-                        4 12 or 20 values (half widths 12 T or 20 T, T =
-                        2..32: 24..384 and 40..640)                           */
+                        4 12, 20 or 32 values (half widths 12 T or 20 T, T =
+                        2..32: 24..384 and 40..640; and 1024 = 32 x 32)       */
   int col_kernel;    /* fast: fan and gather FFT kernel, 0 default for the
                         height, 1 8 values per thread, 2 16 values (heights
                         512, 1024, 2048), 3 12 or 20 values (heights 12 T or
                         20 T, T = 2..128)                                     */
+  int serial;        /* fast: 0 (default) each kernel of the iteration is
+                        launched with programmatic dependent launch (its CTAs
+                        start while the previous kernel drains), 1 plain
+                        stream order; no effect on the results            */
 } seg_plan;
 
 /* The state's current plan. */
@@ -224,14 +229,14 @@ int seg_admm_set_plan(seg_state* st, const seg_plan* p);
 
 /* Autotuner: times `iters` iterations (after one warm-up; replays of the plain
  * iteration graph, without the per-kernel timing events) of each candidate
- * plan twice and keeps the better time, varying one parameter at a time around the best so far (fast: wave
- * budget, then col_ctas_per_sm, then the v-step's FFT kernel, then the
- * column FFT kernel; general: groups, then tile_cols, then tile_rows), and
- * installs the fastest.  The iterate and the iteration count
- * are saved before and restored after the trials (needs memory for one copy
- * of b_v, w, b_w, u and the u-spectra).  best (may be NULL) receives the plan
- * with its time.  Synchronises.  Errors: SHF_ERR_ARG (iters < 1),
- * SHF_ERR_OOM, SHF_ERR_CUDA. */
+ * plan twice and keeps the better time, varying one parameter at a time
+ * around the best so far (fast: wave budget, then col_ctas_per_sm, then the
+ * v-step's FFT kernel together with serial, then the column FFT kernel;
+ * general: groups, then tile_cols, then tile_rows), and installs the fastest.
+ * The iterate and the iteration count are saved before and restored after the
+ * trials (needs memory for one copy of b_v, w, b_w, u and the u-spectra).
+ * best (may be NULL) receives the plan with its time.  Synchronises.  Errors:
+ * SHF_ERR_ARG (iters < 1), SHF_ERR_OOM, SHF_ERR_CUDA. */
 int seg_admm_tune(seg_state* st, int iters, seg_plan* best);
 
 /* Iterates until ||u - w||_2 / sqrt(K H W) < tol (checked every check_every

@@ -378,6 +378,7 @@ void mark_launch(void* ctx, int kind) {
 // of the v-step for the reverse mode.
 cudaError_t enqueue_iteration(seg_state* st, bool timed, signed char* code = nullptr) {
   const Geo& g = st->g;
+  const shf::PdlScope pdl(!(st->fast && st->plan.serial));
   const float scale = 1.f / (static_cast<float>(g.H) * g.W);
   cudaStream_t s = st->stream;
   shf::LaunchHook hook;
@@ -495,13 +496,14 @@ cudaGraphExec_t capture_work(seg_state* st, F enqueue) {
 // partial tiles, the device work list); the previous buffers are released
 // only once the new ones exist.  Synchronises the state's stream.
 int install_fast_plan(seg_state* st, int wave_mib, int col_ctas_per_sm, int row_kernel = shf::kRowDefault,
-                      int col_kernel = shf::kColDefault) {
+                      int col_kernel = shf::kColDefault, int serial = 0) {
   const Geo& g = st->g;
   shf::FastPlan plan;
   plan.wave_mib = wave_mib;
   plan.col_ctas_per_sm = col_ctas_per_sm;
   plan.row_kernel = row_kernel;
   plan.col_kernel = col_kernel;
+  plan.serial = serial;
   plan.col_ctas = shf::fast_col_ctas(g, col_ctas_per_sm, col_kernel);
   plan.fan_ctas = shf::fast_fan_ctas(g, col_kernel);
   plan.row_ctas = shf::fast_row_ctas(g, row_kernel);
@@ -785,6 +787,7 @@ int seg_admm_get_plan(const seg_state* st, seg_plan* out) {
   out->us_per_iter = 0.f;
   out->row_kernel = st->fast ? st->plan.row_kernel : 0;
   out->col_kernel = st->fast ? st->plan.col_kernel : 0;
+  out->serial = st->fast ? st->plan.serial : 0;
   return SHF_OK;
 }
 
@@ -795,10 +798,16 @@ int seg_admm_set_plan(seg_state* st, const seg_plan* p) {
       return fail(SHF_ERR_ARG, "seg_admm_set_plan: col_ctas_per_sm must be in [0, 32] and wave_mib in [1, 4096]");
     if (!shf::fast_row_kernel_ok(st->g, p->row_kernel) || !shf::fast_col_kernel_ok(st->g, p->col_kernel))
       return fail(SHF_ERR_ARG, "seg_admm_set_plan: row_kernel or col_kernel not available at this size");
+    if (p->serial != 0 && p->serial != 1) return fail(SHF_ERR_ARG, "seg_admm_set_plan: serial must be 0 or 1");
     if (p->col_ctas_per_sm == st->plan.col_ctas_per_sm && p->wave_mib == st->plan.wave_mib &&
-        p->row_kernel == st->plan.row_kernel && p->col_kernel == st->plan.col_kernel)
+        p->row_kernel == st->plan.row_kernel && p->col_kernel == st->plan.col_kernel) {
+      if (p->serial != st->plan.serial) {  // same buffers, other launches: capture the graphs again
+        st->plan.serial = p->serial;
+        drop_graphs(st);
+      }
       return SHF_OK;
-    return install_fast_plan(st, p->wave_mib, p->col_ctas_per_sm, p->row_kernel, p->col_kernel);
+    }
+    return install_fast_plan(st, p->wave_mib, p->col_ctas_per_sm, p->row_kernel, p->col_kernel, p->serial);
   }
   if (p->tile_cols < 1 || p->tile_rows < 1 || p->groups < 1)
     return fail(SHF_ERR_ARG, "seg_admm_set_plan: tile_cols, tile_rows and groups must be positive");
@@ -862,13 +871,17 @@ std::vector<seg_plan> plan_candidates(const seg_state* st, const seg_plan& base,
       }
     } else if (stage == 2) {
       // the FFT kernel of the forward v-step: 8 or 16 values per thread, one
-      // row or a pair of rows per group, or 12 / 20 values per thread (odd
-      // factor 3 or 5)
+      // row or a pair of rows per group, or 12 / 20 / 32 values per thread
+      // (odd factor 3 or 5, or 1024 = 32 x 32); each with the iteration's
+      // launches overlapped (programmatic dependent launch) and serial
       for (int rk : {shf::kRow8, shf::kRow16, shf::kRowPair, shf::kRowV}) {
         if (!shf::fast_row_kernel_ok(g, rk)) continue;
-        seg_plan p = base;
-        p.row_kernel = rk;
-        out.push_back(p);
+        for (int serial : {0, 1}) {  // with and without programmatic dependent launch
+          seg_plan p = base;
+          p.row_kernel = rk;
+          p.serial = serial;
+          out.push_back(p);
+        }
       }
     } else if (stage == 3) {
       // the FFT kernel of the fan and the gather: 8 or 16 values per thread

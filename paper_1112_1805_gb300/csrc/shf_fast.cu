@@ -223,6 +223,7 @@ cudaError_t run_fast_iteration_body(const Geo& g, const FastPlan& plan, const fl
 cudaError_t run_fast_adjoint_body(const Geo& g, const FastPlan& plan, const float2* Qr, float2* uhat, float2* Y,
                                   float* bvbar, const float* thr, float2* partial, float2* Tbar, int K, float scale,
                                   const signed char* code, double* tpart, cudaStream_t st) {
+  const PdlScope pdl(!plan.serial);
   const int Whp = fast_pitch(g);
   const int nw = static_cast<int>(plan.wave_f0.size());
   const int rpc = fast::row_groups_per_cta(g.L, 1);

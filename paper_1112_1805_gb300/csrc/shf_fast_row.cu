@@ -703,8 +703,11 @@ struct RowVGeo {
   static constexpr int V = rv::vals_for(L);
   static constexpr int T = L / V;
   static constexpr int GPW = 32 / T;                           // groups per warp
-  static constexpr int NTH = 256;
-  static constexpr int RPC = 8 * GPW;                          // groups per CTA
+  // 32 values per thread: 17 KB of buffers per row, 12 one-warp rows in one
+  // CTA per SM (219 KB) with up to 168 registers per thread
+  static constexpr int NTH = V == 32 ? 384 : 256;
+  static constexpr int MINB = V == 32 ? 1 : 2;
+  static constexpr int RPC = NTH / 32 * GPW;                   // groups per CTA
   static constexpr int BUF = even2(rv::row_buf(L));            // exchange buffer
   static constexpr int RAW = BUF + L;                          // + the b_v stage (L float2)
   static constexpr int STRIDE = T >= 16 ? RAW : RAW + ((T - RAW % 16) % 16 + 16) % 16;
@@ -714,7 +717,7 @@ struct RowVGeo {
 };
 
 template <int L>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(RowVGeo<L>::NTH, RowVGeo<L>::MINB)
     k_wrow_vstepv(float2* __restrict__ Y, float* __restrict__ bv, const float* __restrict__ thr,
                   const int2* __restrict__ ranges, int H, int Whp, int eta, int l0, int f0, int nf, int nv,
                   float scale, const float2* __restrict__ twW, signed char* __restrict__ code) {
@@ -1172,7 +1175,8 @@ int row_ctas_per_sm(int L, int mode, int variant) {
     if (v == kRowPair)                                                                                          \
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_vstep2r<pair_len(N)>, 256, pair_smem<N>());  \
     else if (v == kRowV)                                                                                        \
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_vstepv<v_len(N)>, 256, vstepv_smem<N>());    \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_vstepv<v_len(N)>, RowVGeo<v_len(N)>::NTH,   \
+                                                        vstepv_smem<N>());                                      \
     else if (v == kRow16)                                                                                       \
       e = mode == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_wrow_vstep16<r16_len(N), 0>, 256,   \
                                                                     vstep16_smem<N, 0>())                       \
@@ -1215,7 +1219,8 @@ cudaError_t row_shrink(const Geo& g, int ctas, float2* Y, float* bv, const float
       return launch_pdl(k_wrow_vstep2r<pair_len(N)>, dim3(ctas), dim3(256), pair_smem<N>(), st, Y, bv, thr,      \
                         g.ranges, g.H, Whp, g.eta, wv.l0, wv.f0, wv.nf, wv.nv, scale, g.twW, code);              \
     if (v == kRowV)                                                                                                \
-      return launch_pdl(k_wrow_vstepv<v_len(N)>, dim3(ctas), dim3(256), vstepv_smem<N>(), st, Y, bv, thr,         \
+      return launch_pdl(k_wrow_vstepv<v_len(N)>, dim3(ctas), dim3(RowVGeo<v_len(N)>::NTH), vstepv_smem<N>(), st,  \
+                        Y, bv, thr,                                                                              \
                         g.ranges, g.H, Whp, g.eta, wv.l0, wv.f0, wv.nf, wv.nv, scale, g.twW, code);              \
     if (v == kRow16)                                                                                               \
       return launch_pdl(k_wrow_vstep16<r16_len(N), 0>, dim3(ctas), dim3(256), vstep16_smem<N, 0>(), st, Y, bv,    \

@@ -23,9 +23,10 @@ namespace rv {
 using reg::ilog2;
 using reg::ridx;
 
-// Values per thread for a half width L (0: no V-value transform).
+// Values per thread for a half width L (0: no V-value transform); 32 for the
+// power of two 1024 = 32 x 32, split as two radix-32 passes over one warp.
 __host__ __device__ constexpr int vals_for(int L) {
-  return reg::odd_part(L) == 3 ? 12 : (reg::odd_part(L) == 5 ? 20 : 0);
+  return reg::odd_part(L) == 3 ? 12 : (reg::odd_part(L) == 5 ? 20 : (L == 1024 ? 32 : 0));
 }
 __host__ __device__ constexpr bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 // Lengths with a V-value transform of T = L / V threads per sequence, a power
@@ -36,18 +37,21 @@ __host__ __device__ constexpr bool supported_upto(int L, int tmax) {
          L / vals_for(L) <= tmax;
 }
 __host__ __device__ constexpr bool supported(int L) { return supported_upto(L, 32); }
-__host__ __device__ constexpr bool supported_col(int H) { return supported_upto(H, 128); }
+__host__ __device__ constexpr bool supported_col(int H) { return supported_upto(H, 128) && vals_for(H) != 32; }
 
 template <int L>
 struct Passes {
-  static_assert(supported_col(L), "V-value FFT: L = 12 T or 20 T, T = 2^a in [2, 128]");
+  static_assert(supported_upto(L, 128), "V-value FFT: L = 12 T or 20 T, T = 2^a in [2, 128], or L = 32 x 32");
   static constexpr int V = vals_for(L);
   static constexpr int T = L / V;
+  static constexpr bool SQ = V == 32;             // 32 x 32: a second radix-32 pass, one butterfly per thread
   static constexpr int LGT = ilog2(T);
-  static constexpr int N4 = LGT / 2;              // radix-4 passes after the first
-  static constexpr int REM = (LGT % 2) ? 2 : 1;   // a last radix-2 pass
-  static constexpr int NPASS = 1 + N4 + (REM > 1 ? 1 : 0);
-  __host__ __device__ static constexpr int radix(int p) { return p == 0 ? V : (p - 1 < N4 ? 4 : REM); }
+  static constexpr int N4 = SQ ? 0 : LGT / 2;     // radix-4 passes after the first
+  static constexpr int REM = (!SQ && LGT % 2) ? 2 : 1;  // a last radix-2 pass
+  static constexpr int NPASS = SQ ? 2 : 1 + N4 + (REM > 1 ? 1 : 0);
+  __host__ __device__ static constexpr int radix(int p) {
+    return p == 0 ? V : (SQ ? T : (p - 1 < N4 ? 4 : REM));
+  }
   __host__ __device__ static constexpr int span(int p) { return p == 0 ? 1 : span(p - 1) * radix(p - 1); }
   // offset of pass p's twiddles (p >= 1): (radix - 1) * span entries, [t - 1][k]
   __host__ __device__ static constexpr int twoff(int p) {
@@ -56,11 +60,25 @@ struct Passes {
   static constexpr int TWSIZE = twoff(NPASS) > 0 ? twoff(NPASS) : 1;
 };
 
-// cos and sin of 2 pi m / V for the internal twiddles of the first pass
-// (m < V: 12 or 20), from the values of sin and cos at multiples of 18 and 30
-// degrees.
+// cos and sin of 2 pi m / V for the internal twiddles of a radix-V pass
+// (m < V: 12, 20 or 32), from the values of sin and cos at multiples of 30,
+// 18 and 11.25 degrees.
 template <int V>
 __host__ __device__ __forceinline__ float2 root(int m) {
+  if (V == 32) {
+    const float2 q[8] = {make_float2(1.f, 0.f),
+                         make_float2(0.98078528040323044913f, 0.19509032201612826785f),
+                         make_float2(0.92387953251128675613f, 0.38268343236508977173f),
+                         make_float2(0.83146961230254523708f, 0.55557023301960222474f),
+                         make_float2(0.70710678118654752440f, 0.70710678118654752440f),
+                         make_float2(0.55557023301960222474f, 0.83146961230254523708f),
+                         make_float2(0.38268343236508977173f, 0.92387953251128675613f),
+                         make_float2(0.19509032201612826785f, 0.98078528040323044913f)};  // 11.25 r degrees
+    const int r = m % 8, s = m / 8;  // m * 11.25 = 90 s + 11.25 r
+    float2 a = q[r];
+    for (int i = 0; i < s; ++i) a = make_float2(-a.y, a.x);
+    return a;
+  }
   constexpr float H3 = 0.86602540378443864676f;  // cos 30, sin 60
   constexpr float C18 = 0.95105651629515357212f, S18 = 0.30901699437494742410f;
   constexpr float C36 = 0.80901699437494742410f, S36 = 0.58778525229247312917f;
@@ -136,7 +154,10 @@ __host__ __device__ __forceinline__ void pass_bfly(float2 (&v)[Passes<L>::V], in
       const float2* p = pt + PS::twoff(P) + k;
 #pragma unroll
       for (int t = 1; t < R; ++t) x[t] = c_mul(x[t], reg::twid<S>(p, (t - 1) * Ns));
-      dft_small<R, S>(x);
+      if constexpr (R == V)
+        dftv<V, S>(x);
+      else
+        dft_small<R, S>(x);
 #pragma unroll
       for (int q = 0; q < R; ++q) v[m + q * M] = x[q];
     }
@@ -151,13 +172,16 @@ __host__ __device__ __forceinline__ void pass_bfly(float2 (&v)[Passes<L>::V], in
 //      L a multiple of 16: the XOR permutes 16-aligned blocks);
 //   2: the padding i + (i >> 2) (V = 20, T = 4, 16, 32): conflict-free writes,
 //      two-way stride reads, and addresses that stay base + constant;
+//   3: the padding i + (i >> 5) (V = T = 32): writes 32 apart and reads 1
+//      apart both conflict-free, addresses base + constant;
 //   0: i + (i >> 4) (T = 2, and T = 8 with V = 20, where the others measured
 //      slower: their extra address registers spill).
 // Counted per half-warp, the exchanges of L = 192 take 112 wavefronts instead
 // of 168, of L = 320 224 instead of 304.
 __host__ __device__ constexpr int first_layout(int L) {
-  return vals_for(L) == 12 ? (L % 16 == 0 ? 1 : 0)
-                           : (L / 20 == 4 || L / 20 == 16 || L / 20 == 32 ? 2 : 0);
+  return vals_for(L) == 32   ? 3
+         : vals_for(L) == 12 ? (L % 16 == 0 ? 1 : 0)
+                             : (L / 20 == 4 || L / 20 == 16 || L / 20 == 32 ? 2 : 0);
 }
 
 // Position of element i in the exchange buffer after pass P: the layout above
@@ -169,6 +193,8 @@ __host__ __device__ __forceinline__ int xidx(int i) {
     return i ^ ((i >> 2) & 15);
   } else if constexpr (P == 0 && first_layout(L) == 2) {
     return i + (i >> 2);
+  } else if constexpr (P == 0 && first_layout(L) == 3) {
+    return i + (i >> 5);
   } else if constexpr (P == 1 && Passes<L>::V == 12 && L % 16 == 0) {
     return i ^ ((i >> 3) & 15);
   } else {
@@ -255,7 +281,7 @@ __host__ __device__ __forceinline__ float2 unpack_value(const float2 (&v)[Passes
 
 // Exchange buffer of one group (index L included for staging).
 __host__ __device__ constexpr int row_buf(int L) {
-  return (first_layout(L) == 2 ? L + (L >> 2) : ridx(L)) + 1;
+  return (first_layout(L) == 2 ? L + (L >> 2) : ridx(L)) + 1;  // ridx(L) >= L + (L >> 5)
 }
 
 // Batch variants for the column transforms: a CTA transforms KB columns of

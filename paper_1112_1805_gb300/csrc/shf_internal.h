@@ -141,6 +141,7 @@ struct FastPlan {
   int col_ctas_per_sm = 0;  // CTAs per SM of the column launches (0: as many as fit)
   int row_kernel = kRowDefault;  // forward v-step transform (RowKernel)
   int col_kernel = kColDefault;  // fan and gather transforms (ColKernel)
+  int serial = 0;           // 1: launches without programmatic dependent launch
   int col_ctas = 0;         // resolved: CTAs of one gather launch
   int fan_ctas = 0;         // resolved: CTAs of one fan launch (all resident)
   int row_ctas = 0;         // resolved: resident CTAs of the row (v-step) launch
@@ -154,6 +155,23 @@ struct FastPlan {
   const int* cta_begin = nullptr;     // device, item range [cta_begin[c], cta_begin[c+1]) of CTA c
   const int* tile_begin = nullptr;    // device [K ntiles + 1], into tile_slots, per (label, tile)
   const int* tile_slots = nullptr;    // device, slots of each (label, tile) in filter order
+};
+
+// Whether launch_pdl asks for programmatic dependent launch, per host thread
+// (on unless a PdlScope turned it off).  It lets a kernel's CTAs become
+// resident and run their prologue while the previous kernel drains; at some
+// shapes that costs more than it saves (a plan's `serial` field).  Kernels
+// launched through fast::launch_pdl read it.
+inline bool& pdl_enabled() {
+  static thread_local bool on = true;
+  return on;
+}
+struct PdlScope {
+  bool old;
+  explicit PdlScope(bool on) : old(pdl_enabled()) { pdl_enabled() = on; }
+  ~PdlScope() { pdl_enabled() = old; }
+  PdlScope(const PdlScope&) = delete;
+  PdlScope& operator=(const PdlScope&) = delete;
 };
 
 // Fast path for power-of-two sizes (shf_fast.cu).

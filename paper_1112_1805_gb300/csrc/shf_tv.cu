@@ -284,6 +284,9 @@ cudaError_t enqueue_tv_iteration(tv_state* st, cudaEvent_t* ev) {
   const Geo& g = st->g;
   cudaStream_t ss = st->stream;
   auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], ss) : cudaSuccess; };
+  // plain stream order: with programmatic dependent launch the 512 x 512
+  // iteration measured 3.8% slower
+  const shf::PdlScope pdl(false);
   if (st->fast) {  // the right-hand side is formed inside the row transforms
     const float scale = 1.f / (static_cast<float>(g.H) * g.W);
     cudaError_t e = mark(kTvRowFwd);

@@ -1,11 +1,12 @@
-// Host-side check of the V-value row FFT building blocks (shf_fftv.cuh)
-// against FP64 DFTs, for the half widths 3 2^a (V = 12) and 5 2^a (V = 20)
-// with row groups of 2 to 32 threads.  A row group of T threads is emulated
-// lane by lane, phase by phase, exactly as the kernel sequences them between
-// warp barriers: butterflies, Stockham stores to the padded group buffer,
-// stride reads, and the packing steps with each lane's partner values taken
-// from a snapshot of the registers before the step (what a warp shuffle
-// returns).  Prints one line per length and exits non-zero on a failed bound.
+// Host-side check of the V-value FFT building blocks (shf_fftv.cuh) against
+// FP64 DFTs: rows for the half widths 3 2^a (V = 12), 5 2^a (V = 20) and 1024
+// (V = 32) with row groups of 2 to 32 threads, and column batches.  A row
+// group of T threads is emulated lane by lane, phase by phase, exactly as the
+// kernel sequences them between warp barriers: butterflies, Stockham stores
+// to the group buffer, stride reads, and the packing steps with each lane's
+// partner values taken from a snapshot of the registers before the step (what
+// a warp shuffle returns).  Prints one line per length and exits non-zero on
+// a failed bound.
 #include <array>
 #include <cmath>
 #include <complex>
@@ -215,6 +216,7 @@ struct BatchEmu {
 int main() {
   return Emu<24>::check() + Emu<48>::check() + Emu<96>::check() + Emu<192>::check() + Emu<384>::check() +
          Emu<40>::check() + Emu<80>::check() + Emu<160>::check() + Emu<320>::check() + Emu<640>::check() +
+         Emu<1024>::check() +
          BatchEmu<24, 8>::check() + BatchEmu<96, 8>::check() + BatchEmu<384, 8>::check() + BatchEmu<768, 8>::check() +
          BatchEmu<1536, 4>::check() + BatchEmu<40, 8>::check() + BatchEmu<160, 8>::check() +
          BatchEmu<640, 8>::check() + BatchEmu<1280, 4>::check() + BatchEmu<2560, 4>::check();

@@ -1,10 +1,10 @@
-"""Host-side check of the V-value row FFT of the v-step (shf_fftv.cuh).
+"""Host-side check of the V-value FFTs of the v-step, fan and gather (shf_fftv.cuh).
 
-Compiles tests/fftv_host.cu for the host with nvcc and runs it: the radix-12
-or radix-20 first pass, the radix-4/2 passes, the group buffer's Stockham
-exchanges (swizzled or padded) and the partner-lane packing of real rows are
-emulated lane by lane and compared with FP64 DFTs for the half widths 3 2^a
-(24..384) and 5 2^a (40..640); the column batch transforms (8 or 4 columns per
+Compiles tests/fftv_host.cu for the host with nvcc and runs it: the radix-12,
+radix-20 or radix-32 first pass, the radix-4/2 (or second radix-32) passes, the
+group buffer's Stockham exchanges (swizzled or padded) and the partner-lane
+packing of real rows are emulated lane by lane and compared with FP64 DFTs for
+the half widths 3 2^a (24..384), 5 2^a (40..640) and 1024; the column batch transforms (8 or 4 columns per
 CTA, two exchange buffers) likewise for heights 24..2560.  Every exchange
 layout is also checked to stay inside its buffer and to give each element its
 own slot.  No GPU is needed.
@@ -30,4 +30,4 @@ def test_fftv_host(tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     print(r.stdout)
     assert r.returncode == 0, r.stdout + r.stderr
-    assert r.stdout.count(" ok") == 20
+    assert r.stdout.count(" ok") == 21

@@ -102,6 +102,40 @@ def test_plan_is_bitwise_reproducible(torch_mod):
         assert np.array_equal(a["u"], b["u"]) and np.array_equal(a["bv"], b["bv"])
 
 
+def test_serial_launches_give_the_same_bits(torch_mod):
+    # serial = 1 drops programmatic dependent launch: the same kernels in the
+    # same order, so the same bits; changing only it recaptures the graphs
+    from paper_1112_1805_gb300 import binding as B
+    from paper_1112_1805_gb300.api import FilterBank, ShearletSegmenter
+
+    # the second: 32 values per thread at L = 1024
+    for H, W, K, J, extra in ((128, 256, 3, 3, {}), (64, 2048, 2, 1, {"row_kernel": 4})):
+        img, cb, Lam = _problem(H, W, K, J, 35)
+        fb = FilterBank(H, W, J)
+        res = []
+        for serial in (0, 1, 2):
+            seg = ShearletSegmenter(fb, torch_mod.tensor(img, device="cuda"), cb, Lam.tolist(), 1.0)
+            seg.set_plan(dict(seg.plan(), **extra))
+            if serial < 2:
+                seg.set_plan(dict(seg.plan(), serial=serial))
+                assert seg.plan()["serial"] == serial
+                seg.step(5)
+            else:  # serial from the third iteration on
+                seg.step(2)
+                seg.set_plan(dict(seg.plan(), serial=1))
+                seg.step(3)
+                with pytest.raises(B.ShearsegError) as e:
+                    seg.set_plan(dict(seg.plan(), serial=2))
+                assert e.value.code == B.SHF_ERR_ARG and seg.plan()["serial"] == 1
+            seg.synchronize()
+            res.append({k: seg.get(getattr(B, "SEG_" + k.upper())).cpu().numpy() for k in ("u", "w", "bv")})
+            seg.close()
+        fb.close()
+        for r in res[1:]:
+            for k in ("u", "w", "bv"):
+                assert np.array_equal(res[0][k], r[k]), (H, W, k)
+
+
 def test_general_plans_match_oracle(torch_mod, oracle_mod):
     # 72 x 120 (72 = 9 * 8) is not a register-FFT size: the general kernels
     img, cb, Lam = _problem(72, 120, 3, 2, 33)
@@ -197,10 +231,11 @@ def test_batch_tune(torch_mod, oracle_mod):
                                       (64, 640, 2, 2, 6),    # L = 320: 8 / 20 values
                                       (320, 192, 2, 2, 6),   # H = 320: 8 / 20 values; L = 96: 8 / 12 values
                                       (1280, 64, 2, 2, 5),   # H = 1280: columns of 4, 8 / 20 values
-                                      (1536, 48, 2, 1, 5)])  # H = 1536: 8 / 12 values (128 threads a column)
+                                      (1536, 48, 2, 1, 5),   # H = 1536: 8 / 12 values (128 threads a column)
+                                      (48, 2048, 2, 1, 4)])  # L = 1024: 8 / 16 / 32 values; H = 48: 8 / 12 values
 def test_every_fft_kernel_variant_meets_the_bars(torch_mod, oracle_mod, H, W, K, J, T):
     # the plan's FFT kernels (row_kernel: 1 eight values per thread, 2 sixteen,
-    # 3 pairs of rows, 4 twelve or twenty; col_kernel: 1 eight, 2 sixteen, 3
+    # 3 pairs of rows, 4 twelve, twenty or thirty-two; col_kernel: 1 eight, 2 sixteen, 3
     # twelve or twenty)
     # change only the order of
     # the FFT arithmetic: each one meets the oracle bars, and the sizes without
@@ -211,7 +246,7 @@ def test_every_fft_kernel_variant_meets_the_bars(torch_mod, oracle_mod, H, W, K,
     o = _oracle(oracle_mod, img, cb, J, Lam, T)
     L = W // 2
     rows = ([1] + ([2] if L in (64, 128, 256, 512, 1024) else []) + ([3] if L in (64, 128) else [])
-            + ([4] if L in (24, 40, 48, 80, 96, 160, 192, 320, 384, 640) else []))
+            + ([4] if L in (24, 40, 48, 80, 96, 160, 192, 320, 384, 640, 1024) else []))
     cols = ([1] + ([2] if H in (512, 1024, 2048) else [])
             + ([3] if H in (24, 40, 48, 80, 96, 160, 192, 320, 384, 640, 768, 1280, 1536) else []))
     seen = set()

@@ -6,7 +6,10 @@ per iteration), so, as planned for this workload: oracle parity on crops with
 the same K, J and colours (a register-FFT size and a general-path size), and
 at full size what holds exactly or at any size: the data term, the first
 iterate u = -gamma s / 2 (bitwise), simplex feasibility of w, |b_v| <= gamma
-Lambda_j per filter, finite iterates."""
+Lambda_j per filter, finite iterates -- with the default plan and with the
+one the benchmark's tuner picks (32-value rows, plain launches), whose
+iterates agree with the default's to rounding.  Oracle parity of the 32-value
+rows themselves: the kernel-variant test at 48 x 2048 (test_gpu_plan.py)."""
 
 import numpy as np
 import pytest
@@ -48,7 +51,10 @@ def test_rgb_crop_matches_oracle(oracle_mod, H, W, T):
     assert labels_agree(g["labels"], o["labels"], o["gap"])
 
 
-def test_rgb2048_full_size_properties():
+# the default plan, and the one the tuner picks for this image on a GB300 (rows
+# of 32 values per thread at half width 1024, plain stream order)
+@pytest.mark.parametrize("plan", [{}, {"row_kernel": 4, "serial": 1}])
+def test_rgb2048_full_size_properties(plan):
     torch = need_cuda()
     from paper_1112_1805_gb300 import binding as B
     from paper_1112_1805_gb300.api import FilterBank, ShearletSegmenter
@@ -61,6 +67,8 @@ def test_rgb2048_full_size_properties():
     f = torch.tensor(img, device="cuda")
     seg = ShearletSegmenter(fb, f, cb, Lam.tolist(), wl.gamma)
     assert seg.plan()["fast"] == 1  # H = 2048: register FFTs with column batches of 4
+    if plan:
+        seg.set_plan(dict(seg.plan(), **plan))
     # data term at sampled pixels
     s = seg.get(B.SEG_S)
     rng = np.random.default_rng(3)
@@ -97,3 +105,25 @@ def test_rgb2048_full_size_properties():
     assert labels.shape == (wl.H, wl.W) and labels.min() >= 0 and labels.max() < wl.K
     seg.close()
     fb.close()
+
+
+def test_rgb2048_full_size_row_kernels_agree():
+    # the 16- and 32-value row transforms at half width 1024 on the full image:
+    # the same iteration up to the order of the FP32 FFT arithmetic
+    torch = need_cuda()
+    from paper_1112_1805_gb300 import binding as B
+    from paper_1112_1805_gb300.api import FilterBank, ShearletSegmenter
+
+    img, _, wl = synth.make_workload_image("rgb2048")
+    f = torch.tensor(np.ascontiguousarray(img, dtype=np.float32), device="cuda")
+    fb = FilterBank(wl.H, wl.W, wl.J)
+    us = []
+    for rk in (2, 4):
+        seg = ShearletSegmenter(fb, f, wl.codebook(), wl.Lambda().tolist(), wl.gamma)
+        seg.set_plan(dict(seg.plan(), row_kernel=rk))
+        seg.step(3)
+        seg.synchronize()
+        us.append(seg.get(B.SEG_U).clone())
+        seg.close()
+    fb.close()
+    assert float((us[0] - us[1]).abs().max()) <= 1e-5

@@ -692,11 +692,12 @@ __global__ void __launch_bounds__(256, 2)
 
 // ---------------------------------------------------------------------------
 // v-step with V values per thread for the half widths with an odd factor
-// (L = 12 T or 20 T, T = 2..32: shf_fftv.cuh): row groups of T threads, 32/T
-// groups per warp, eight warps per CTA, every lane live; the layout, the b_v
-// stage, the L1 prefetch of the next row's spectrum columns and the
-// partner-lane packing are those of k_wrow_vstep16 for T <= 32.  Forward mode
-// (optional codes); the adjoint keeps k_wrow_vstep.
+// (L = 12 T or 20 T, T = 2..32) and for L = 1024 (V = T = 32; shf_fftv.cuh):
+// row groups of T threads, 32/T groups per warp, eight warps per CTA (twelve
+// for V = 32), every lane live; the layout, the b_v stage, the L1 prefetch of
+// the next row's spectrum columns and the partner-lane packing are those of
+// k_wrow_vstep16 for T <= 32.  Forward mode (optional codes); the adjoint
+// keeps k_wrow_vstep16 / k_wrow_vstep.
 // ---------------------------------------------------------------------------
 template <int L>
 struct RowVGeo {

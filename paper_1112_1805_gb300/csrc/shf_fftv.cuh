@@ -1,18 +1,21 @@
-// Register FFTs with V values per thread for the lengths with an odd factor:
-// L = 3 2^a (V = 12) and L = 5 2^a (V = 20), split as L = V T over T threads
-// (a power of two): the v-step's rows with T = 2 .. 32 (a group never leaves
-// its warp and every barrier is __syncwarp), and the fan's and gather's
-// columns in batches of KB columns with T = 2 .. 128 (CTA barriers).
+// Register FFTs with V values per thread: for the lengths with an odd factor,
+// L = 3 2^a (V = 12) and L = 5 2^a (V = 20), and for the row length
+// 1024 = 32 x 32 (V = 32), split as L = V T over T threads (a power of two):
+// the v-step's rows with T = 2 .. 32 (a group never leaves its warp and every
+// barrier is __syncwarp), and the fan's and gather's columns (V = 12, 20) in
+// batches of KB columns with T = 2 .. 128 (CTA barriers).
 //
 // Thread tt holds v[k] = x[tt + k T], k = 0..V-1 ("stride layout", as in
 // shf_fft16.cuh).  Stockham passes: first one of radix V (span 1: no
-// twiddles; a V = R x 4 decomposition in registers with R = 3 or 5 and the
+// twiddles; a V = R x 4 decomposition in registers with R = 3, 5 or 8 and the
 // V-th roots of unity as constants), then radix-4 passes and, when log2 T is
 // odd, a last radix-2 pass, in which each thread does V/4 (or V/2)
-// butterflies.  The exchange buffer of a group stores element i at
-// ridx(i) = i + (i >> 4).  The real-row packing pairs index n = tt + k T with
-// L - n, which is register V - 1 - k of lane (T - tt) mod T (lane 0: its own
-// register V - k, or X_L for k = 0): the pairings are warp shuffles.
+// butterflies; for V = 32 one more radix-32 pass, one butterfly per thread.
+// The exchange buffers are laid out per pass so that a half-warp's 64-bit
+// accesses spread over the 16 bank pairs (xidx, bxidx).  The real-row packing
+// pairs index n = tt + k T with L - n, which is register V - 1 - k of lane
+// (T - tt) mod T (lane 0: its own register V - k, or X_L for k = 0): the
+// pairings are warp shuffles.
 #pragma once
 
 #include "shf_fft16.cuh"

@@ -725,6 +725,7 @@ def measure_batch(iters: int, steps: int, warmup_steps: int, warmup_iters: int, 
                        f"with a branch per image; {world} rank(s), images sharded whole by LPT on H W K eta "
                        f"(strong scaling of the fixed batch); sequential_value: the same images one after "
                        f"another through the single-image path with the batch's plans"}
+    out["sms"] = sorted({p.get("sms", 0) for p in plans if p.get("fast")})
     if world == 1:
         seq = measure_sequential(shapes, imgs, [cbs[i] for i in mine], [lams[i] for i in mine], plans)
         out["sequential_value"] = seq
@@ -734,9 +735,10 @@ def measure_batch(iters: int, steps: int, warmup_steps: int, warmup_iters: int, 
 
 def measure_sequential(shapes, imgs, cbs, lams, plans, iters: int = 20, warmup: int = 3):
     """The batch's images solved one after another through the plain
-    single-image path (own filter bank and state, the plan the batch tuned),
-    `iters` graph-replayed iterations each after `warmup`; the summed
-    Mpixel*label*iter/s over the summed per-image times."""
+    single-image path (own filter bank and state, the plan the batch tuned
+    for the image's shape, with its grids on all SMs: a share of them pays only
+    when images run side by side), `iters` graph-replayed iterations each after
+    `warmup`; the summed Mpixel*label*iter/s over the summed per-image times."""
     import torch
 
     from paper_1112_1805_gb300.api import FilterBank, ShearletSegmenter
@@ -745,7 +747,7 @@ def measure_sequential(shapes, imgs, cbs, lams, plans, iters: int = 20, warmup: 
     for i, (H, W, K, J) in enumerate(shapes):
         fb = FilterBank(H, W, J)
         seg = ShearletSegmenter(fb, imgs[i], cbs[i], lams[i].tolist(), 1.0)
-        seg.set_plan(plans[i])
+        seg.set_plan(dict(plans[i], sms=0))
         seg.step(warmup)
         seg.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -864,7 +866,9 @@ def run_batch(args):
     line = {"metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": b["workload"], "images": 64, "iters_per_step": iters, "tuned": b["tuned"]}}
+            "config": {"workload": b["workload"], "images": 64, "iters_per_step": iters, "tuned": b["tuned"]},
+            "sequential_value": b.get("sequential_value"), "speedup_vs_sequential": b.get("speedup_vs_sequential"),
+            "sms": b.get("sms")}
     print(json.dumps(line))
     return 0
 

@@ -216,6 +216,11 @@ typedef struct {
                         launched with programmatic dependent launch (its CTAs
                         start while the previous kernel drains), 1 plain
                         stream order; no effect on the results            */
+  int sms;           /* fast: SMs the fan, v-step and gather launches size
+                        their resident grids for, [0, 65536]; 0 (default) or
+                        more than the GPU has: all of them.  A share lets the
+                        images of a batch run side by side
+                        (seg_admm_batch_tune chooses it)                     */
 } seg_plan;
 
 /* The state's current plan. */
@@ -341,8 +346,13 @@ int seg_admm_batch_step(seg_batch* batch, int n_iters);
 int seg_admm_batch_image(seg_batch* batch, int i, seg_state** out);
 
 /* Runs seg_admm_tune on the first image of every distinct (path, H, W, J, K)
- * and installs its plan on the other images of that shape; the batch graph
- * is recaptured at the next step.  Synchronises. */
+ * (with sms = 0) and installs its plan on the other images of that shape;
+ * then times `iters` iterations of the whole batch (twice, the better time
+ * kept) with every fast image's sms set to all SMs, a half, a third and a
+ * quarter of them, and keeps the fastest share.  The iterates are saved
+ * before and restored after the batch-wide trials (a copy of every image's
+ * b_v, w, b_w, u and u-spectra; without memory for them that stage is
+ * skipped).  The batch graph is recaptured at the next step.  Synchronises. */
 int seg_admm_batch_tune(seg_batch* batch, int iters);
 
 /* Waits for the batch's stream. */

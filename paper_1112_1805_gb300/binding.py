@@ -67,11 +67,11 @@ class seg_plan(ctypes.Structure):
     _fields_ = [("fast", ctypes.c_int), ("wave_mib", ctypes.c_int), ("col_ctas_per_sm", ctypes.c_int),
                 ("tile_cols", ctypes.c_int), ("tile_rows", ctypes.c_int), ("groups", ctypes.c_int),
                 ("us_per_iter", ctypes.c_float), ("row_kernel", ctypes.c_int), ("col_kernel", ctypes.c_int),
-                ("serial", ctypes.c_int)]
+                ("serial", ctypes.c_int), ("sms", ctypes.c_int)]
 
 
 _PLAN_FIELDS = ("fast", "wave_mib", "col_ctas_per_sm", "tile_cols", "tile_rows", "groups", "us_per_iter",
-                "row_kernel", "col_kernel", "serial")
+                "row_kernel", "col_kernel", "serial", "sms")
 
 _SIG = {
     "shf_version": (_I, []),

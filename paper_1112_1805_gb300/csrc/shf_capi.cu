@@ -496,7 +496,7 @@ cudaGraphExec_t capture_work(seg_state* st, F enqueue) {
 // partial tiles, the device work list); the previous buffers are released
 // only once the new ones exist.  Synchronises the state's stream.
 int install_fast_plan(seg_state* st, int wave_mib, int col_ctas_per_sm, int row_kernel = shf::kRowDefault,
-                      int col_kernel = shf::kColDefault, int serial = 0) {
+                      int col_kernel = shf::kColDefault, int serial = 0, int sms = 0) {
   const Geo& g = st->g;
   shf::FastPlan plan;
   plan.wave_mib = wave_mib;
@@ -504,9 +504,10 @@ int install_fast_plan(seg_state* st, int wave_mib, int col_ctas_per_sm, int row_
   plan.row_kernel = row_kernel;
   plan.col_kernel = col_kernel;
   plan.serial = serial;
-  plan.col_ctas = shf::fast_col_ctas(g, col_ctas_per_sm, col_kernel);
-  plan.fan_ctas = shf::fast_fan_ctas(g, col_kernel);
-  plan.row_ctas = shf::fast_row_ctas(g, row_kernel);
+  plan.sms = sms;
+  plan.col_ctas = shf::fast_col_ctas(g, col_ctas_per_sm, col_kernel, sms);
+  plan.fan_ctas = shf::fast_fan_ctas(g, col_kernel, sms);
+  plan.row_ctas = shf::fast_row_ctas(g, row_kernel, sms);
   if (plan.col_ctas < 1 || plan.fan_ctas < 1 || plan.row_ctas < 1)
     return fail(SHF_ERR_CUDA, "install_fast_plan: no resident CTA");
   std::vector<shf::WorkItem> h_items;
@@ -788,6 +789,7 @@ int seg_admm_get_plan(const seg_state* st, seg_plan* out) {
   out->row_kernel = st->fast ? st->plan.row_kernel : 0;
   out->col_kernel = st->fast ? st->plan.col_kernel : 0;
   out->serial = st->fast ? st->plan.serial : 0;
+  out->sms = st->fast ? st->plan.sms : 0;
   return SHF_OK;
 }
 
@@ -799,15 +801,16 @@ int seg_admm_set_plan(seg_state* st, const seg_plan* p) {
     if (!shf::fast_row_kernel_ok(st->g, p->row_kernel) || !shf::fast_col_kernel_ok(st->g, p->col_kernel))
       return fail(SHF_ERR_ARG, "seg_admm_set_plan: row_kernel or col_kernel not available at this size");
     if (p->serial != 0 && p->serial != 1) return fail(SHF_ERR_ARG, "seg_admm_set_plan: serial must be 0 or 1");
+    if (p->sms < 0 || p->sms > 65536) return fail(SHF_ERR_ARG, "seg_admm_set_plan: sms must be in [0, 65536]");
     if (p->col_ctas_per_sm == st->plan.col_ctas_per_sm && p->wave_mib == st->plan.wave_mib &&
-        p->row_kernel == st->plan.row_kernel && p->col_kernel == st->plan.col_kernel) {
+        p->row_kernel == st->plan.row_kernel && p->col_kernel == st->plan.col_kernel && p->sms == st->plan.sms) {
       if (p->serial != st->plan.serial) {  // same buffers, other launches: capture the graphs again
         st->plan.serial = p->serial;
         drop_graphs(st);
       }
       return SHF_OK;
     }
-    return install_fast_plan(st, p->wave_mib, p->col_ctas_per_sm, p->row_kernel, p->col_kernel, p->serial);
+    return install_fast_plan(st, p->wave_mib, p->col_ctas_per_sm, p->row_kernel, p->col_kernel, p->serial, p->sms);
   }
   if (p->tile_cols < 1 || p->tile_rows < 1 || p->groups < 1)
     return fail(SHF_ERR_ARG, "seg_admm_set_plan: tile_cols, tile_rows and groups must be positive");
@@ -935,32 +938,51 @@ std::vector<seg_plan> plan_candidates(const seg_state* st, const seg_plan& base,
   return out;
 }
 
-}  // namespace
+// A copy of a state's iterate (b_v, w, b_w, u and the u-spectra) and
+// iteration count, taken on the state's stream before trial iterations and
+// put back after them.
+struct IterateCopy {
+  seg_state* st = nullptr;
+  float* buf = nullptr;
+  long long iter0 = 0;
 
-extern "C" {
-
-int seg_admm_tune(seg_state* st, int iters, seg_plan* best_out) {
-  if (!st || iters < 1) return fail(SHF_ERR_ARG, "seg_admm_tune: bad argument");
-  const Geo& g0 = st->g;
-  const size_t P = st->P(), KP = P * st->K, NC = KP * g0.eta, TH = st->Ph() * st->K;
-  // the iterate is saved and restored around the trial iterations
-  float* snap = nullptr;
-  const size_t nsnap = NC + 3 * KP + 2 * TH;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&snap), sizeof(float) * nsnap, st->stream) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(SHF_ERR_OOM, "seg_admm_tune: no memory to save the iterate");
+  // SHF_ERR_OOM when there is no memory for the copy
+  int save(seg_state* s) {
+    st = s;
+    iter0 = s->iter;
+    const size_t KP = s->P() * s->K, NC = KP * s->g.eta, TH = s->Ph() * s->K;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&buf), sizeof(float) * (NC + 3 * KP + 2 * TH), s->stream) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      buf = nullptr;
+      return fail(SHF_ERR_OOM, "no memory to save the iterate for the tuning trials");
+    }
+    return copy(true) == cudaSuccess ? SHF_OK : fail(SHF_ERR_CUDA, "saving the iterate failed");
   }
-  struct Piece {
-    void* p;
-    size_t bytes;
-  };
-  const Piece pieces[] = {{st->bv, sizeof(float) * NC},
-                          {st->w, sizeof(float) * KP},
-                          {st->bw, sizeof(float) * KP},
-                          {st->u, sizeof(float) * KP},
-                          {st->T, sizeof(float2) * TH}};
-  auto copy_all = [&](bool save) {
-    char* q = reinterpret_cast<char*>(snap);
+  // copies the iterate back, frees the copy and synchronises the stream
+  cudaError_t restore() {
+    if (!buf) return cudaSuccess;
+    cudaError_t e = copy(false);
+    cudaError_t e2 = cudaFreeAsync(buf, st->stream);
+    cudaError_t e3 = cudaStreamSynchronize(st->stream);
+    buf = nullptr;
+    st->iter = iter0;
+    return e != cudaSuccess ? e : (e2 != cudaSuccess ? e2 : e3);
+  }
+
+ private:
+  cudaError_t copy(bool save) {
+    const size_t KP = st->P() * st->K, NC = KP * st->g.eta, TH = st->Ph() * st->K;
+    struct Piece {
+      void* p;
+      size_t bytes;
+    };
+    const Piece pieces[] = {{st->bv, sizeof(float) * NC},
+                            {st->w, sizeof(float) * KP},
+                            {st->bw, sizeof(float) * KP},
+                            {st->u, sizeof(float) * KP},
+                            {st->T, sizeof(float2) * TH}};
+    char* q = reinterpret_cast<char*>(buf);
     cudaError_t e = cudaSuccess;
     for (const Piece& pc : pieces) {
       if (e == cudaSuccess)
@@ -968,13 +990,26 @@ int seg_admm_tune(seg_state* st, int iters, seg_plan* best_out) {
       q += pc.bytes;
     }
     return e;
-  };
-  const long long iter0 = st->iter;
-  cudaError_t e = copy_all(true);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+int seg_admm_tune(seg_state* st, int iters, seg_plan* best_out) {
+  if (!st || iters < 1) return fail(SHF_ERR_ARG, "seg_admm_tune: bad argument");
+  // the iterate is saved and restored around the trial iterations
+  IterateCopy snap;
+  int rc0 = snap.save(st);
+  if (rc0) {
+    snap.restore();
+    return rc0;
+  }
   seg_plan best;
   seg_admm_get_plan(st, &best);
   best.us_per_iter = INFINITY;
-  int rc = e == cudaSuccess ? SHF_OK : fail(SHF_ERR_CUDA, cudaGetErrorString(e));
+  int rc = SHF_OK;
   for (int stage = 0; stage < 4 && !rc; ++stage) {
     const seg_plan base = best;
     for (const seg_plan& cand : plan_candidates(st, base, stage)) {
@@ -1001,13 +1036,9 @@ int seg_admm_tune(seg_state* st, int iters, seg_plan* best_out) {
     }
   }
   if (!rc) rc = seg_admm_set_plan(st, &best);
-  e = copy_all(false);
-  cudaError_t e2 = cudaFreeAsync(snap, st->stream);
-  cudaError_t e3 = cudaStreamSynchronize(st->stream);
-  st->iter = iter0;
+  const cudaError_t e = snap.restore();
   if (rc) return rc;
-  if (e != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
-    return fail(SHF_ERR_CUDA, "seg_admm_tune: restoring the iterate failed");
+  if (e != cudaSuccess) return fail(SHF_ERR_CUDA, "seg_admm_tune: restoring the iterate failed");
   if (best_out) *best_out = best;
   return SHF_OK;
 }
@@ -1525,6 +1556,8 @@ void drop_batch_graphs(seg_batch* b) {
   b->graph_tried = false;
 }
 
+int tune_batch_share(seg_batch* b, int iters);
+
 void free_batch(seg_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -1650,8 +1683,105 @@ int seg_admm_batch_image(seg_batch* b, int i, seg_state** out) {
   return SHF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Mean time (microseconds) of one batch iteration over `iters` replays of the
+// batch's graph, after one that also captures it.
+int time_batch_iterations(seg_batch* b, int iters, float* us) {
+  int rc = seg_admm_batch_step(b, 1);
+  if (rc) return rc;
+  cudaEvent_t a = nullptr, c = nullptr;
+  SHF_CK(cudaEventCreate(&a));
+  cudaError_t e = cudaEventCreate(&c);
+  if (e == cudaSuccess) e = cudaEventRecord(a, b->stream);
+  if (e == cudaSuccess) rc = seg_admm_batch_step(b, iters);
+  if (e == cudaSuccess && !rc) e = cudaEventRecord(c, b->stream);
+  if (e == cudaSuccess && !rc) e = cudaEventSynchronize(c);
+  float ms = 0.f;
+  if (e == cudaSuccess && !rc) e = cudaEventElapsedTime(&ms, a, c);
+  cudaEventDestroy(a);
+  if (c) cudaEventDestroy(c);
+  if (rc) return rc;
+  SHF_CK(e);
+  *us = 1000.f * ms / static_cast<float>(iters);
+  return SHF_OK;
+}
+
+// The fast images' fan, v-step and gather grids sized for `sms` SMs (0: all).
+int set_batch_share(seg_batch* b, int sms) {
+  for (seg_state* st : b->states) {
+    if (!st->fast) continue;
+    seg_plan p;
+    seg_admm_get_plan(st, &p);
+    p.sms = sms;
+    const int rc = seg_admm_set_plan(st, &p);
+    if (rc) return rc;
+  }
+  return SHF_OK;
+}
+
+// Batch-wide stage of the tuner: every fast image's persistent grids sized for
+// all SMs or for a half, a third or a quarter of them, so that the images of
+// the batch's graph run side by side instead of taking turns on the whole GPU;
+// each share timed twice on the batch's graph (the better time kept), the
+// iterates saved before and restored after.  Without memory for the copies
+// the stage is skipped.
+int tune_batch_share(seg_batch* b, int iters) {
+  int nfast = 0;
+  for (seg_state* st : b->states) nfast += st->fast ? 1 : 0;
+  if (nfast < 2) return SHF_OK;
+  int dev = 0, nsm = 0;
+  SHF_CK(cudaGetDevice(&dev));
+  SHF_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  std::vector<IterateCopy> snaps(b->states.size());
+  int rc = SHF_OK;
+  for (size_t i = 0; i < b->states.size() && !rc; ++i) rc = snaps[i].save(b->states[i]);
+  for (seg_state* st : b->states) cudaStreamSynchronize(st->stream);  // copies before the batch's streams
+  int best = 0;
+  if (!rc) {
+    float best_us = INFINITY;
+    for (int share : {0, nsm / 2, nsm / 3, nsm / 4}) {
+      if (share < 0 || (share > 0 && share < 8)) continue;
+      rc = set_batch_share(b, share);
+      float us = INFINITY;
+      for (int t = 0; t < 2 && !rc; ++t) {
+        float u = 0.f;
+        rc = time_batch_iterations(b, iters, &u);
+        us = std::min(us, u);
+      }
+      if (rc) break;
+      if (us < best_us) {
+        best_us = us;
+        best = share;
+      }
+    }
+  }
+  const bool skipped = rc == SHF_ERR_OOM;
+  if (skipped) rc = SHF_OK;
+  if (!rc) rc = set_batch_share(b, best);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (IterateCopy& sn : snaps)
+    if (sn.restore() != cudaSuccess && !rc) rc = fail(SHF_ERR_CUDA, "seg_admm_batch_tune: restoring an iterate failed");
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
 int seg_admm_batch_tune(seg_batch* b, int iters) {
   if (!b || iters < 1) return fail(SHF_ERR_ARG, "seg_admm_batch_tune: bad argument");
+  // every image back on grids for all SMs before its shape is tuned alone
+  for (seg_state* st : b->states) {
+    if (!st->fast || st->plan.sms == 0) continue;
+    seg_plan p;
+    seg_admm_get_plan(st, &p);
+    p.sms = 0;
+    const int rc = seg_admm_set_plan(st, &p);
+    if (rc) return rc;
+  }
   // one tuning run per distinct problem shape; the other images take its plan
   struct Key {
     int fast, H, W, J, K;
@@ -1674,7 +1804,7 @@ int seg_admm_batch_tune(seg_batch* b, int iters) {
     if (rc) return rc;
   }
   drop_batch_graphs(b);
-  return SHF_OK;
+  return tune_batch_share(b, iters);
 }
 
 int seg_admm_batch_sync(seg_batch* b) {

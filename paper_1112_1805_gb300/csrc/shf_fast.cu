@@ -86,16 +86,24 @@ int sm_count() {
 }
 }  // namespace
 
-int fast_col_ctas(const Geo& g, int per_sm, int col_kernel) {
+// SMs a plan's persistent grids are sized for
+int sms_for(int sms) {
+  const int n = sm_count();
+  return sms > 0 && sms < n ? sms : n;
+}
+
+int fast_col_ctas(const Geo& g, int per_sm, int col_kernel, int sms) {
   const int fit = fast::col_ctas_per_sm(g.H, col_kernel);
   if (fit < 1) return 0;
   const int k = (per_sm <= 0 || per_sm > fit) ? fit : per_sm;
-  return k * sm_count();
+  return k * sms_for(sms);
 }
 
-int fast_row_ctas(const Geo& g, int row_kernel) { return fast::row_ctas_per_sm(g.L, 0, row_kernel) * sm_count(); }
+int fast_row_ctas(const Geo& g, int row_kernel, int sms) {
+  return fast::row_ctas_per_sm(g.L, 0, row_kernel) * sms_for(sms);
+}
 
-int fast_fan_ctas(const Geo& g, int col_kernel) { return fast::fan_ctas_per_sm(g.H, col_kernel) * sm_count(); }
+int fast_fan_ctas(const Geo& g, int col_kernel, int sms) { return fast::fan_ctas_per_sm(g.H, col_kernel) * sms_for(sms); }
 
 bool fast_row_kernel_ok(const Geo& g, int row_kernel) { return fast::row_kernel_ok(g.L, row_kernel); }
 

@@ -142,6 +142,7 @@ struct FastPlan {
   int row_kernel = kRowDefault;  // forward v-step transform (RowKernel)
   int col_kernel = kColDefault;  // fan and gather transforms (ColKernel)
   int serial = 0;           // 1: launches without programmatic dependent launch
+  int sms = 0;              // SMs the fan, v-step and gather grids are sized for (0: all)
   int col_ctas = 0;         // resolved: CTAs of one gather launch
   int fan_ctas = 0;         // resolved: CTAs of one fan launch (all resident)
   int row_ctas = 0;         // resolved: resident CTAs of the row (v-step) launch
@@ -201,13 +202,14 @@ cudaError_t run_fast_adjoint_body(const Geo& g, const FastPlan& plan, const floa
                                   float* bvbar, const float* thr, float2* partial, float2* Tbar, int K, float scale,
                                   const signed char* code, double* tpart, cudaStream_t st);
 // Resident CTAs of one gather launch for `per_sm` CTAs per SM (0: as many
-// as fit; larger values are clamped to that), and of one fan launch.
-int fast_col_ctas(const Geo& g, int per_sm, int col_kernel = kColDefault);
-int fast_fan_ctas(const Geo& g, int col_kernel = kColDefault);
+// as fit; larger values are clamped to that), and of one fan launch, on `sms`
+// SMs (0, or more than the device has: all of them).
+int fast_col_ctas(const Geo& g, int per_sm, int col_kernel = kColDefault, int sms = 0);
+int fast_fan_ctas(const Geo& g, int col_kernel = kColDefault, int sms = 0);
 bool fast_row_kernel_ok(const Geo& g, int row_kernel);
 bool fast_col_kernel_ok(const Geo& g, int col_kernel);
-// Resident CTAs of the row (v-step) kernel.
-int fast_row_ctas(const Geo& g, int row_kernel = kRowDefault);
+// Resident CTAs of the row (v-step) kernel on `sms` SMs (0: all).
+int fast_row_ctas(const Geo& g, int row_kernel = kRowDefault, int sms = 0);
 // Host construction of the work list of K labels from the filters' column
 // ranges (ranges_host[eta]) for plan->wave_mib and plan->col_ctas; returns the
 // host arrays to upload (cta_begin holds one entry more per wave).

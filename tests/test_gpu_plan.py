@@ -64,7 +64,8 @@ def _check(o, g):
 
 FAST_PLANS = [dict(wave_mib=1, col_ctas_per_sm=1), dict(wave_mib=1, col_ctas_per_sm=0),
               dict(wave_mib=2, col_ctas_per_sm=3), dict(wave_mib=64, col_ctas_per_sm=2),
-              dict(wave_mib=4096, col_ctas_per_sm=32)]
+              dict(wave_mib=4096, col_ctas_per_sm=32),
+              dict(wave_mib=64, col_ctas_per_sm=0, sms=40)]  # grids sized for 40 SMs
 
 
 def test_fast_plans_match_oracle(torch_mod, oracle_mod):
@@ -78,6 +79,7 @@ def test_fast_plans_match_oracle(torch_mod, oracle_mod):
         g = _run(torch_mod, img, cb, 3, Lam, T, p)
         assert g["plan"]["fast"] == 1
         assert g["plan"]["wave_mib"] == p["wave_mib"] and g["plan"]["col_ctas_per_sm"] == p["col_ctas_per_sm"]
+        assert g["plan"]["sms"] == p.get("sms", 0)
         _check(o, g)
 
 
@@ -157,7 +159,7 @@ def test_bad_plans_are_rejected_and_keep_the_old_plan(torch_mod):
     from paper_1112_1805_gb300.api import FilterBank, ShearletSegmenter
 
     for H, W, bad in ((64, 64, dict(wave_mib=64, col_ctas_per_sm=-1)), (64, 64, dict(wave_mib=0, col_ctas_per_sm=0)),
-                      (64, 64, dict(wave_mib=64, col_ctas_per_sm=33)),
+                      (64, 64, dict(wave_mib=64, col_ctas_per_sm=33)), (64, 64, dict(sms=-1)),
                       (72, 120, dict(tile_cols=0, tile_rows=1, groups=1)),
                       (72, 120, dict(tile_cols=8, tile_rows=10000, groups=1))):
         img, cb, Lam = _problem(H, W, 3, 2, 34)
@@ -211,11 +213,19 @@ def test_batch_tune(torch_mod, oracle_mod):
     probs = [_problem(H, W, 3, 2, 40 + i) for i, (H, W) in enumerate(shapes)]
     batch = ShearletBatch([torch_mod.tensor(p[0], device="cuda") for p in probs], [p[1] for p in probs],
                           [p[2].tolist() for p in probs])
-    batch.tune(2)
+    batch.step(3)
+    batch.synchronize()
+    snap = [{k: batch.image(i).get(k).cpu().numpy() for k in (B.SEG_BV, B.SEG_U)} for i in range(4)]
+    batch.tune(2)  # per shape, then the batch-wide SM share: the iterates come back as they were
     plans = [batch.image(i).plan() for i in range(4)]
     assert [p["fast"] for p in plans] == [1, 0, 1, 1]
     assert plans[0] == plans[2]
-    batch.step(10)
+    assert len({p["sms"] for p in plans if p["fast"]}) == 1
+    for i in range(4):
+        assert int(batch.image(i).get(B.SEG_ITER)) == 3
+        for k, v in snap[i].items():
+            assert np.array_equal(batch.image(i).get(k).cpu().numpy(), v), (i, k)
+    batch.step(7)
     batch.synchronize()
     for i, p in enumerate(probs):
         u = batch.image(i).get(B.SEG_U).cpu().numpy()

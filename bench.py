@@ -715,6 +715,7 @@ def measure_batch(iters: int, steps: int, warmup_steps: int, warmup_iters: int, 
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms = float(t.item())
     plans = [batch.image(j).plan() for j in range(len(mine))]
+    lanes = batch.lanes
     batch.close()
     value = units * steps / (ms / 1000.0) / 1e6
     out = {"value": value, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
@@ -722,10 +723,12 @@ def measure_batch(iters: int, steps: int, warmup_steps: int, warmup_iters: int, 
                len(shard.share(shapes, r, world)) for r in range(world)),
            "workload": f"batch: {len(shapes)} images, sides 128..1024 (first 384x640), K 2..6, "
                        f"J = floor(log2(min side)/2), {iters} iterations per step, one graph per iteration "
-                       f"with a branch per image; {world} rank(s), images sharded whole by LPT on H W K eta "
+                       f"with the images in concurrent lanes (tuned; 0 = one per image); {world} rank(s), images "
+                       f"sharded whole by LPT on H W K eta "
                        f"(strong scaling of the fixed batch); sequential_value: the same images one after "
                        f"another through the single-image path with the batch's plans"}
     out["sms"] = sorted({p.get("sms", 0) for p in plans if p.get("fast")})
+    out["lanes"] = lanes
     if world == 1:
         seq = measure_sequential(shapes, imgs, [cbs[i] for i in mine], [lams[i] for i in mine], plans)
         out["sequential_value"] = seq
@@ -868,7 +871,7 @@ def run_batch(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": b["workload"], "images": 64, "iters_per_step": iters, "tuned": b["tuned"]},
             "sequential_value": b.get("sequential_value"), "speedup_vs_sequential": b.get("speedup_vs_sequential"),
-            "sms": b.get("sms")}
+            "sms": b.get("sms"), "lanes": b.get("lanes")}
     print(json.dumps(line))
     return 0
 

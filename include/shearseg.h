@@ -345,14 +345,26 @@ int seg_admm_batch_step(seg_batch* batch, int n_iters);
  * seg_admm_batch_sync first to order it after the batch's iterations. */
 int seg_admm_batch_image(seg_batch* batch, int i, seg_state** out);
 
+/* Lanes of a batch iteration: with lanes = L in [1, n) the n images form L
+ * chains that run side by side, each image (taken in decreasing order of
+ * H W K eta) joining the chain with the least such work so far and starting
+ * when the chain's previous image has finished its iteration; 0 (the
+ * default), or L >= n, runs every image concurrently.  Fewer images at once
+ * compete less for the L2 cache.  The results do not depend on it (every
+ * image runs the same kernels on its own buffers).  Takes effect at the next
+ * seg_admm_batch_step.  Errors: SHF_ERR_ARG (NULL batch, lanes < 0). */
+int seg_admm_batch_set_lanes(seg_batch* batch, int lanes);
+int seg_admm_batch_get_lanes(const seg_batch* batch, int* lanes);
+
 /* Runs seg_admm_tune on the first image of every distinct (path, H, W, J, K)
  * (with sms = 0) and installs its plan on the other images of that shape;
  * then times `iters` iterations of the whole batch (twice, the better time
- * kept) with every fast image's sms set to all SMs, a half, a third and a
- * quarter of them, and keeps the fastest share.  The iterates are saved
- * before and restored after the batch-wide trials (a copy of every image's
- * b_v, w, b_w, u and u-spectra; without memory for them that stage is
- * skipped).  The batch graph is recaptured at the next step.  Synchronises. */
+ * kept) for 0 to 4 lanes (seg_admm_batch_set_lanes), and at the fastest for
+ * every fast image's sms set to all SMs, a half, a third and a quarter of
+ * them, keeping the fastest of each.  The iterates are saved before and
+ * restored after the batch-wide trials (a copy of every image's b_v, w, b_w,
+ * u and u-spectra; without memory for them those trials are skipped).  The
+ * batch graph is recaptured at the next step.  Synchronises. */
 int seg_admm_batch_tune(seg_batch* batch, int iters);
 
 /* Waits for the batch's stream. */

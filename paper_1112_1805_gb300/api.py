@@ -208,7 +208,8 @@ class _BorrowedState(ShearletSegmenter):
 
 class ShearletBatch:
     """Independent images of uneven sizes and label counts solved together: one
-    CUDA graph per iteration with one concurrent branch per image.
+    CUDA graph per iteration with one concurrent branch per image, or the
+    images chained into `lanes` branches.
 
     images: list of float32 CUDA tensors [C, H, W] or [H, W]; codebooks: list of
     [K, C] host arrays; Lambdas: list of J+1 weight vectors; gammas: list or
@@ -257,9 +258,19 @@ class ShearletBatch:
         B.seg_admm_batch_step(self.handle, n)
 
     def tune(self, iters: int = 5) -> None:
-        """Autotunes one plan per distinct image shape."""
+        """Autotunes one plan per distinct image shape, then the batch's lanes
+        and SM share."""
         torch.cuda.current_stream().synchronize()
         B.seg_admm_batch_tune(self.handle, iters)
+
+    @property
+    def lanes(self) -> int:
+        """Chains of images run side by side (0: every image at once)."""
+        return B.seg_admm_batch_get_lanes(self.handle)
+
+    @lanes.setter
+    def lanes(self, n: int) -> None:
+        B.seg_admm_batch_set_lanes(self.handle, n)
 
     def synchronize(self) -> None:
         B.seg_admm_batch_sync(self.handle)

@@ -107,6 +107,8 @@ _SIG = {
     "seg_admm_set_plan": (_I, [_VP, ctypes.POINTER(seg_plan)]),
     "seg_admm_tune": (_I, [_VP, _I, ctypes.POINTER(seg_plan)]),
     "seg_admm_batch_tune": (_I, [_VP, _I]),
+    "seg_admm_batch_set_lanes": (_I, [_VP, _I]),
+    "seg_admm_batch_get_lanes": (_I, [_VP, ctypes.POINTER(_I)]),
     "seg_admm_unrolled_bwd_enqueue": (_I, [_VP, _VP]),
     "seg_admm_unrolled_grads": (_I, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _VP, _VP]),
     "seg_admm_sync": (_I, [_VP]),
@@ -301,6 +303,16 @@ def seg_admm_tune(state: int, iters: int = 5) -> dict:
 
 def seg_admm_batch_tune(batch: int, iters: int = 5) -> None:
     _call("seg_admm_batch_tune", batch, iters)
+
+
+def seg_admm_batch_set_lanes(batch: int, lanes: int) -> None:
+    _call("seg_admm_batch_set_lanes", _VP(batch), int(lanes))
+
+
+def seg_admm_batch_get_lanes(batch: int) -> int:
+    out = _I()
+    _call("seg_admm_batch_get_lanes", _VP(batch), ctypes.byref(out))
+    return int(out.value)
 
 
 def seg_admm_sync(state: int) -> None:

@@ -1545,6 +1545,7 @@ struct seg_batch {
   std::vector<cudaEvent_t> joins;
   cudaGraphExec_t exec = nullptr;
   bool graph_tried = false;
+  int lanes = 0;  // chains of images run side by side (0: one image per chain)
 };
 
 namespace {
@@ -1556,7 +1557,7 @@ void drop_batch_graphs(seg_batch* b) {
   b->graph_tried = false;
 }
 
-int tune_batch_share(seg_batch* b, int iters);
+int tune_batch_layout(seg_batch* b, int iters);
 
 void free_batch(seg_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
@@ -1575,17 +1576,39 @@ void free_batch(seg_batch* b) {
   delete b;
 }
 
-// Forks from the batch stream to every image stream, enqueues one iteration
-// of each image, joins back.
+// Forks from the batch stream, enqueues one iteration of every image on its
+// own stream and joins back.  With b->lanes = L in [1, n) the images form L
+// chains that run side by side: in decreasing order of their work (H W K eta)
+// each image joins the chain with the least work so far and starts after the
+// chain's previous image; with 0 (or L >= n) every image is a chain of its own.
 cudaError_t enqueue_batch_iteration(seg_batch* b) {
+  const int n = static_cast<int>(b->states.size());
+  const int nl = b->lanes > 0 && b->lanes < n ? b->lanes : n;
+  auto work = [&](int i) {
+    const seg_state* s = b->states[i];
+    return static_cast<double>(s->P()) * s->K * s->g.eta;
+  };
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  if (nl < n) std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work(x) > work(y); });
+  std::vector<double> load(nl, 0.0);
+  std::vector<int> last(nl, -1);  // the chain's latest image
   cudaError_t e = cudaEventRecord(b->fork, b->stream);
-  for (size_t i = 0; i < b->states.size() && e == cudaSuccess; ++i) {
+  for (int k = 0; k < n && e == cudaSuccess; ++k) {
+    const int i = order[k];
+    int l = nl < n ? 0 : k;
+    if (nl < n)
+      for (int c = 1; c < nl; ++c)
+        if (load[c] < load[l]) l = c;
+    load[l] += work(i);
     seg_state* st = b->states[i];
-    e = cudaStreamWaitEvent(st->stream, b->fork, 0);
+    e = cudaStreamWaitEvent(st->stream, last[l] < 0 ? b->fork : b->joins[last[l]], 0);
     if (e == cudaSuccess) e = enqueue_iteration(st, false);
     if (e == cudaSuccess) e = cudaEventRecord(b->joins[i], st->stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->joins[i], 0);
+    last[l] = i;
   }
+  for (int l = 0; l < nl && e == cudaSuccess; ++l)
+    if (last[l] >= 0) e = cudaStreamWaitEvent(b->stream, b->joins[last[l]], 0);
   return e;
 }
 
@@ -1676,6 +1699,21 @@ int seg_admm_batch_step(seg_batch* b, int n) {
   return SHF_OK;
 }
 
+int seg_admm_batch_set_lanes(seg_batch* b, int lanes) {
+  if (!b || lanes < 0) return fail(SHF_ERR_ARG, "seg_admm_batch_set_lanes: bad argument");
+  if (lanes != b->lanes) {
+    b->lanes = lanes;
+    drop_batch_graphs(b);
+  }
+  return SHF_OK;
+}
+
+int seg_admm_batch_get_lanes(const seg_batch* b, int* lanes) {
+  if (!b || !lanes) return fail(SHF_ERR_ARG, "seg_admm_batch_get_lanes: NULL argument");
+  *lanes = b->lanes;
+  return SHF_OK;
+}
+
 int seg_admm_batch_image(seg_batch* b, int i, seg_state** out) {
   if (!b || !out || i < 0 || i >= static_cast<int>(b->states.size()))
     return fail(SHF_ERR_ARG, "seg_admm_batch_image: bad argument");
@@ -1722,16 +1760,17 @@ int set_batch_share(seg_batch* b, int sms) {
   return SHF_OK;
 }
 
-// Batch-wide stage of the tuner: every fast image's persistent grids sized for
-// all SMs or for a half, a third or a quarter of them, so that the images of
-// the batch's graph run side by side instead of taking turns on the whole GPU;
-// each share timed twice on the batch's graph (the better time kept), the
-// iterates saved before and restored after.  Without memory for the copies
-// the stage is skipped.
-int tune_batch_share(seg_batch* b, int iters) {
+// Batch-wide stages of the tuner, timed on the batch's graph (each candidate
+// twice, the better time kept; the iterates saved before and restored after,
+// or the stages skipped without memory for the copies): first the number of
+// image chains (one image per chain, or 1 to 4 chains), then every fast
+// image's persistent grids sized for all SMs or for a half, a third or a
+// quarter of them.
+int tune_batch_layout(seg_batch* b, int iters) {
+  const int n = static_cast<int>(b->states.size());
+  if (n < 2) return SHF_OK;
   int nfast = 0;
   for (seg_state* st : b->states) nfast += st->fast ? 1 : 0;
-  if (nfast < 2) return SHF_OK;
   int dev = 0, nsm = 0;
   SHF_CK(cudaGetDevice(&dev));
   SHF_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -1739,28 +1778,41 @@ int tune_batch_share(seg_batch* b, int iters) {
   int rc = SHF_OK;
   for (size_t i = 0; i < b->states.size() && !rc; ++i) rc = snaps[i].save(b->states[i]);
   for (seg_state* st : b->states) cudaStreamSynchronize(st->stream);  // copies before the batch's streams
-  int best = 0;
+  auto timed = [&](float* best_us) {
+    float us = INFINITY;
+    for (int t = 0; t < 2 && !rc; ++t) {
+      float u = 0.f;
+      rc = time_batch_iterations(b, iters, &u);
+      us = std::min(us, u);
+    }
+    const bool better = !rc && us < *best_us;
+    if (better) *best_us = us;
+    return better;
+  };
+  int best_lanes = b->lanes, best_share = 0;
   if (!rc) {
     float best_us = INFINITY;
-    for (int share : {0, nsm / 2, nsm / 3, nsm / 4}) {
-      if (share < 0 || (share > 0 && share < 8)) continue;
-      rc = set_batch_share(b, share);
-      float us = INFINITY;
-      for (int t = 0; t < 2 && !rc; ++t) {
-        float u = 0.f;
-        rc = time_batch_iterations(b, iters, &u);
-        us = std::min(us, u);
-      }
+    for (int lanes : {0, 1, 2, 3, 4}) {
+      if (lanes >= n) continue;
+      b->lanes = lanes;
+      drop_batch_graphs(b);
+      if (timed(&best_us)) best_lanes = lanes;
       if (rc) break;
-      if (us < best_us) {
-        best_us = us;
-        best = share;
-      }
+    }
+    b->lanes = best_lanes;
+    drop_batch_graphs(b);
+    best_us = INFINITY;
+    for (int share : {0, nsm / 2, nsm / 3, nsm / 4}) {
+      if (rc || nfast == 0 || (share > 0 && share < 8)) continue;
+      rc = set_batch_share(b, share);
+      if (!rc && timed(&best_us)) best_share = share;
     }
   }
   const bool skipped = rc == SHF_ERR_OOM;
   if (skipped) rc = SHF_OK;
-  if (!rc) rc = set_batch_share(b, best);
+  b->lanes = best_lanes;
+  drop_batch_graphs(b);
+  if (!rc) rc = set_batch_share(b, best_share);
   if (b->stream) cudaStreamSynchronize(b->stream);
   for (IterateCopy& sn : snaps)
     if (sn.restore() != cudaSuccess && !rc) rc = fail(SHF_ERR_CUDA, "seg_admm_batch_tune: restoring an iterate failed");
@@ -1804,7 +1856,7 @@ int seg_admm_batch_tune(seg_batch* b, int iters) {
     if (rc) return rc;
   }
   drop_batch_graphs(b);
-  return tune_batch_share(b, iters);
+  return tune_batch_layout(b, iters);
 }
 
 int seg_admm_batch_sync(seg_batch* b) {

@@ -89,6 +89,38 @@ def test_uneven_batch_shapes_first_iterations():
     batch.close()
 
 
+def test_lanes_give_the_same_bits():
+    # the images chained into two or three lanes run the same kernels on the
+    # same buffers as with every image in a lane of its own
+    torch = need_cuda()
+    from paper_1112_1805_gb300 import binding as B
+    from paper_1112_1805_gb300.api import ShearletBatch
+
+    data = _images([(64, 96, 2, 2, 1), (48, 80, 3, 1, 1), (32, 32, 4, 2, 1), (40, 64, 3, 2, 3), (96, 128, 3, 2, 1)], 9)
+    res = []
+    for lanes in (0, 2, 3, 7):
+        batch = ShearletBatch([torch.tensor(d[0], device="cuda") for d in data], [d[1] for d in data],
+                              [d[2] for d in data], 1.0)
+        batch.lanes = lanes
+        assert batch.lanes == lanes
+        batch.step(4)
+        if lanes == 2:  # a change between steps: the graph is captured again
+            batch.lanes = 1
+        batch.step(4)
+        batch.synchronize()
+        res.append([{k: batch.image(i).get(getattr(B, "SEG_" + k)).cpu().numpy() for k in ("U", "BV")}
+                    for i in range(len(data))])
+        if lanes == 7:
+            with pytest.raises(B.ShearsegError) as e:
+                batch.lanes = -1
+            assert e.value.code == B.SHF_ERR_ARG
+        batch.close()
+    for r in res[1:]:
+        for i in range(len(data)):
+            for k in ("U", "BV"):
+                assert np.array_equal(res[0][i][k], r[i][k]), (i, k)
+
+
 def test_sharded_batch_solver_on_one_rank(oracle_mod):
     # the product's sharded batched solve (shard.solve_batch_sharded with the
     # GPU batch solver) on one rank: the label maps of every image, against

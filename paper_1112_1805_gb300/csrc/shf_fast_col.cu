@@ -207,8 +207,9 @@ __global__ void __launch_bounds__(Col16Geo<H>::NT, H == 512 ? 2 : 1)
     r16::batch_fft<H, +1, KB>(v, tt, b, b0, b1, pt);  // starts with a CTA barrier (also after the twiddle table)
     if (cok) {
       float2* dst = Y + Pp * fl + ccol;
+      const uint64_t keep = l2_evict_last_policy();
 #pragma unroll
-      for (int k = 0; k < 16; ++k) dst[static_cast<size_t>(tt + k * T) * Whp] = v[k];
+      for (int k = 0; k < 16; ++k) st_l2_hint(dst + static_cast<size_t>(tt + k * T) * Whp, v[k], keep);
     }
   }
 }
@@ -310,8 +311,10 @@ __global__ void __launch_bounds__(Col16Geo<H>::NT, H == 512 ? 2 : 1)
 #pragma unroll
   for (int k = 0; k < 16; ++k) acc[k] = make_float2(0.f, 0.f);
   auto load_y = [&](const float2* src, int c, bool o) {
+    const uint64_t last = l2_evict_first_policy();
 #pragma unroll
-    for (int k = 0; k < 16; ++k) y[k] = o ? src[static_cast<size_t>(tt + k * T) * Whp + c] : make_float2(0.f, 0.f);
+    for (int k = 0; k < 16; ++k)
+      y[k] = o ? ld_l2_hint(src + static_cast<size_t>(tt + k * T) * Whp + c, last) : make_float2(0.f, 0.f);
   };
   r16::build_pass_twiddles<H, 1>(pt, twH, threadIdx.x, blockDim.x);
   pdl_wait();
@@ -423,8 +426,9 @@ __global__ void __launch_bounds__(ColVGeo<H>::NT, ColVGeo<H>::MINB)
     rv::batch_fft<H, +1, KB>(v, tt, b, b0, b1, pt);  // starts with a CTA barrier (also after the twiddle table)
     if (cok) {
       float2* dst = Y + Pp * fl + ccol;
+      const uint64_t keep = l2_evict_last_policy();
 #pragma unroll
-      for (int k = 0; k < V; ++k) dst[static_cast<size_t>(tt + k * T) * Whp] = v[k];
+      for (int k = 0; k < V; ++k) st_l2_hint(dst + static_cast<size_t>(tt + k * T) * Whp, v[k], keep);
     }
   }
 }
@@ -457,13 +461,14 @@ __global__ void __launch_bounds__(ColVGeo<H>::NT, ColVGeo<H>::MINB)
 #pragma unroll
   for (int k = 0; k < V; ++k) acc[k] = make_float2(0.f, 0.f);
   auto tile_of = [&](const WorkItem& x) { return Y + Pp * ((x.label - l0) * nf + (x.filter - f0)); };
+  const uint64_t last = l2_evict_first_policy();  // the spectra's last reader
   rv::build_pass_twiddles<H, 1>(pt, twH, threadIdx.x, blockDim.x);
   pdl_wait();
   pdl_trigger();
   if constexpr (PREFETCH) {
     const float2* src = tile_of(it);
 #pragma unroll
-    for (int k = 0; k < V; ++k) y[k] = ok ? src[static_cast<size_t>(tt + k * T) * Whp + col] : make_float2(0.f, 0.f);
+    for (int k = 0; k < V; ++k) y[k] = ok ? ld_l2_hint(src + static_cast<size_t>(tt + k * T) * Whp + col, last) : make_float2(0.f, 0.f);
   }
   for (int i = ib; i < ie; ++i) {
     float2 v[V];
@@ -473,7 +478,7 @@ __global__ void __launch_bounds__(ColVGeo<H>::NT, ColVGeo<H>::MINB)
     } else {
       const float2* src = tile_of(it);
 #pragma unroll
-      for (int k = 0; k < V; ++k) v[k] = ok ? src[static_cast<size_t>(tt + k * T) * Whp + col] : make_float2(0.f, 0.f);
+      for (int k = 0; k < V; ++k) v[k] = ok ? ld_l2_hint(src + static_cast<size_t>(tt + k * T) * Whp + col, last) : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int k = 0; k < V; ++k)
@@ -489,7 +494,7 @@ __global__ void __launch_bounds__(ColVGeo<H>::NT, ColVGeo<H>::MINB)
         const float2* src = tile_of(nx);
 #pragma unroll
         for (int k = 0; k < V; ++k)
-          y[k] = nok ? src[static_cast<size_t>(tt + k * T) * Whp + ncol] : make_float2(0.f, 0.f);
+          y[k] = nok ? ld_l2_hint(src + static_cast<size_t>(tt + k * T) * Whp + ncol, last) : make_float2(0.f, 0.f);
       }
     }
     rv::batch_fft<H, -1, KB>(v, tt, b, b0, b1, pt);  // starts with a CTA barrier (also after the twiddle table)

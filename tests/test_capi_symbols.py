@@ -69,3 +69,36 @@ def test_argument_errors_without_gpu():
         B.seg_admm_step(None, 1)
     assert ei.value.code == B.SHF_ERR_ARG
     assert B.seg_admm_kernel_name(0) == "row_ustep" and B.seg_admm_kernel_name(99) == ""
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    # the ctypes mirrors of the header's parameter and plan structs: same size
+    # and same offset for every field (a C program compiled against the header
+    # prints them)
+    import shutil
+    import subprocess
+
+    from paper_1112_1805_gb300 import binding as B
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    structs = [B.seg_params, B.seg_plan, B.tv_params, B.nl_params]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "shearseg.h"', "int main(void) {"]
+    for st in structs:
+        lines.append(f'  printf("{st.__name__} size %zu\\n", sizeof({st.__name__}));')
+        for name, _ in st._fields_:
+            cname = name.rstrip("_")
+            lines.append(f'  printf("{st.__name__} {name} %zu\\n", offsetof({st.__name__}, {cname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True,
+                   capture_output=True, timeout=120)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True, timeout=60).stdout.split("\n")
+    got = {tuple(ln.split()[:2]): int(ln.split()[2]) for ln in out if ln.strip()}
+    for st in structs:
+        assert got[(st.__name__, "size")] == ctypes.sizeof(st), st.__name__
+        for name, _ in st._fields_:
+            assert got[(st.__name__, name)] == getattr(st, name).offset, (st.__name__, name)
